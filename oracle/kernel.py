@@ -1,0 +1,147 @@
+"""Oracle: descriptor, Jacobian and the Matern-5/2 force kernel K (FP64, CPU).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+The paper (Sec. 2.1) uses the sGDML kernel: geometries are encoded by a
+descriptor, K is PSD of size n = 3 d n_train and is made of 3d x 3d blocks,
+one per pair of training geometries.  The kernel function itself is only
+cited there; the reading used here is the GDML form without permutational
+symmetries:
+
+* descriptor  x_p = 1 / |R_i - R_j| for atom pairs i > j, p = i(i-1)/2 + j,
+  D = N(N-1)/2;
+* scalar kernel  kappa(x, x') = phi(|x - x'|), Matern-5/2
+  phi(r) = (1 + c r + c^2 r^2 / 3) exp(-c r),  c = sqrt(5) / sigma;
+* force kernel block  K_ab = grad_{R_a} grad_{R_b}^T kappa(x(R_a), x(R_b))
+  = J_a^T H_ab J_b with the descriptor Jacobian J_a = dx_a / dR_a (D x 3N) and
+  H_ab = d^2 kappa / dx_a dx_b^T = (c^2/3) e^{-c r} [(1 + c r) I - c^2 d d^T],
+  d = x_a - x_b, r = |d|.
+
+Vector index of a length-n vector: a*3N + 3*i + q (App. A, "Atomic
+contribution": n -> (n_train, d, 3)).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def pair_index(N: int) -> tuple[np.ndarray, np.ndarray]:
+    """Atom indices (i, j), i > j, of descriptor entry p = i(i-1)/2 + j."""
+    I, J = [], []
+    for i in range(N):
+        for j in range(i):
+            I.append(i)
+            J.append(j)
+    return np.asarray(I, dtype=np.int64), np.asarray(J, dtype=np.int64)
+
+
+def descriptor(R: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Inverse-distance descriptor X (M, D) and g (M, D, 3) = (R_i - R_j)/r^3.
+
+    dx_p/dR_i = -g_p and dx_p/dR_j = +g_p for p = (i, j).
+    """
+    R = np.asarray(R, dtype=np.float64)
+    I, J = pair_index(R.shape[1])
+    diff = R[:, I, :] - R[:, J, :]
+    r = np.sqrt(np.sum(diff * diff, axis=-1))
+    return 1.0 / r, diff / (r**3)[..., None]
+
+
+def jacobian(R: np.ndarray) -> np.ndarray:
+    """Dense descriptor Jacobian J (M, D, 3N): J[a, p, 3i+q] = dx_{a,p}/dR_{a,i,q}."""
+    M, N, _ = R.shape
+    I, J = pair_index(N)
+    _, g = descriptor(R)
+    D = I.size
+    Jac = np.zeros((M, D, 3 * N))
+    p = np.arange(D)
+    for q in range(3):
+        Jac[:, p, 3 * I + q] = -g[:, :, q]
+        Jac[:, p, 3 * J + q] = g[:, :, q]
+    return Jac
+
+
+def matern52(r, sigma: float):
+    """Scalar Matern-5/2 kernel phi(r), unit signal variance."""
+    c = np.sqrt(5.0) / sigma
+    r = np.asarray(r, dtype=np.float64)
+    return (1.0 + c * r + (c * r) ** 2 / 3.0) * np.exp(-c * r)
+
+
+def hessian_block(xa: np.ndarray, xb: np.ndarray, sigma: float) -> np.ndarray:
+    """H_ab = d^2 kappa(x_a, x_b) / dx_a dx_b^T (D x D)."""
+    c = np.sqrt(5.0) / sigma
+    d = xa - xb
+    r = np.sqrt(d @ d)
+    S = (c * c / 3.0) * np.exp(-c * r)
+    return S * ((1.0 + c * r) * np.eye(d.size) - c * c * np.outer(d, d))
+
+
+def force_kernel_dense(R: np.ndarray, sigma: float) -> np.ndarray:
+    """Assemble the n x n force kernel K block by block (Sec. 2.1): K_ab = J_a^T H_ab J_b."""
+    M, N, _ = R.shape
+    X, _ = descriptor(R)
+    Jac = jacobian(R)
+    B = 3 * N
+    K = np.empty((M * B, M * B))
+    for a in range(M):
+        for b in range(M):
+            H = hessian_block(X[a], X[b], sigma)
+            K[a * B:(a + 1) * B, b * B:(b + 1) * B] = Jac[a].T @ H @ Jac[b]
+    return K
+
+
+def force_kernel_column(R: np.ndarray, sigma: float, col: int) -> np.ndarray:
+    """One column K[:, col] from its definition (used as get_col in Alg. 1)."""
+    M, N, _ = R.shape
+    B = 3 * N
+    b, local = divmod(int(col), B)
+    X, _ = descriptor(R)
+    Jac = jacobian(R)
+    out = np.empty(M * B)
+    w = Jac[b][:, local]  # J_b e_local
+    for a in range(M):
+        out[a * B:(a + 1) * B] = Jac[a].T @ (hessian_block(X[a], X[b], sigma) @ w)
+    return out
+
+
+def force_kernel_diag(R: np.ndarray, sigma: float) -> np.ndarray:
+    """diag(K): K_aa = (c^2/3) J_a^T J_a since r = 0 on the diagonal block."""
+    c = np.sqrt(5.0) / sigma
+    Jac = jacobian(R)
+    return ((c * c / 3.0) * np.sum(Jac * Jac, axis=1)).reshape(-1)
+
+
+def matvec(R: np.ndarray, sigma: float, v: np.ndarray, lam: float = 0.0) -> np.ndarray:
+    """Matrix-free (K + lam I) v (Sec. 2.1: CG needs only matrix-vector products).
+
+    Steps: w_b = J_b v_b; u_a = sum_b H_ab w_b with H_ab applied from its
+    definition, H_ab w = S_ab [(1 + c r_ab) w - c^2 d_ab (d_ab . w)];
+    (K v)_a = J_a^T u_a.
+    """
+    M, N, _ = R.shape
+    B = 3 * N
+    c = np.sqrt(5.0) / sigma
+    X, _ = descriptor(R)
+    Jac = jacobian(R)
+    V = np.asarray(v, dtype=np.float64).reshape(M, B)
+    W = np.einsum("apk,ak->ap", Jac, V)
+    U = np.empty_like(W)
+    for a in range(M):
+        d = X[a][None, :] - X  # (M, D): d_ab = x_a - x_b
+        r = np.sqrt(np.sum(d * d, axis=1))
+        S = (c * c / 3.0) * np.exp(-c * r)
+        proj = np.sum(d * W, axis=1)  # d_ab . w_b
+        U[a] = (S * (1.0 + c * r)) @ W - c * c * ((S * proj) @ d)
+    out = np.einsum("apk,ap->ak", Jac, U).reshape(-1)
+    return out + lam * np.asarray(v, dtype=np.float64)
+
+
+def descriptor_distances(R: np.ndarray) -> np.ndarray:
+    """r_ab = |x_a - x_b| computed directly from differences (M x M)."""
+    X, _ = descriptor(R)
+    out = np.empty((X.shape[0], X.shape[0]))
+    for a in range(X.shape[0]):
+        d = X[a][None, :] - X
+        out[a] = np.sqrt(np.sum(d * d, axis=1))
+    return out
