@@ -1,0 +1,146 @@
+/*
+ * gdml.h -- C ABI of libgdml: preconditioned conjugate-gradient training of
+ * a GDML force-field kernel model on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem (Sec. 2.1, Eq. 1): given M training geometries of N atoms and
+ * force labels y, solve  (K + lambda I_n) alpha = y,  n = 3 N M, where K is
+ * the force kernel made of 3N x 3N blocks K_ab = J_a^T H_ab J_b:
+ *   descriptor  x_p = 1/|R_i - R_j| (pairs i > j, p = i(i-1)/2 + j, D = N(N-1)/2),
+ *   J_a = dx_a/dR_a,  H_ab = (c^2/3) e^{-c r} [(1 + c r) I - c^2 d d^T],
+ *   d = x_a - x_b, r = |d|, c = sqrt(5)/sigma  (Matern-5/2 kernel).
+ * The solve is PCG (Sec. 2.1, Eq. 2) with the Nystrom-type preconditioner
+ *   P = L_k L_k^T + lambda I                                (Eq. 3),
+ *   P^-1 = lambda^-1 [I - L_k (lambda I + L_k^T L_k)^-1 L_k^T]  (Eq. 4),
+ * whose k inducing columns are chosen by uniform sampling, ridge leverage
+ * scores, or the incomplete (pivoted) Cholesky of App. A.2, Algorithm 1.
+ *
+ * Conventions for every entry point
+ *  - Vector layout: index a*3N + 3*i + q (geometry a, atom i, coordinate q);
+ *    this is the reshape n -> (n_train, d, 3) of App. A.
+ *  - Pointers named *_dev are device pointers on the context's device, at
+ *    least 8-byte aligned; all work is ordered on the context's stream.
+ *    The caller owns every pointer it passes; the context keeps none of them
+ *    after the call returns.  The context owns its own device workspace.
+ *  - Nothing throws across the ABI.  Every call returns a gdml_status;
+ *    gdml_last_error() gives a message for the last failure on a context.
+ *  - Calls on one context must not run concurrently from several host threads.
+ */
+#ifndef GDML_H
+#define GDML_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gdml_ctx gdml_ctx;
+
+typedef enum {
+  GDML_OK = 0,
+  GDML_ERR_ARG = 1,           /* invalid argument (sizes, pointers, enum values) */
+  GDML_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  GDML_ERR_OOM = 3,           /* device allocation failed */
+  GDML_ERR_NOT_SPD = 4,       /* a Cholesky pivot was not positive (even after jitter) */
+  GDML_ERR_BREAKDOWN = 5,     /* PCG: p^T K p <= 0 or not finite */
+  GDML_ERR_NOT_CONVERGED = 6, /* PCG hit max_iter; alpha holds the last iterate */
+  GDML_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  GDML_ERR_STATE = 8          /* call order violated (e.g. apply before build) */
+} gdml_status;
+
+/* Arithmetic of the kernel matvec K v (Sec. 2.1: CG only needs matvecs).
+ * FP64: every step in IEEE double.
+ * TF32 / BF16: the two descriptor contractions of the matvec run on the
+ * tcgen05 tensor cores (TF32 or BF16 operands, FP32 accumulation); PCG then
+ * runs as the inner solver of an FP64 iterative refinement whose residual
+ * y - K_lambda alpha is recomputed with the FP64 matvec. */
+typedef enum { GDML_FP64 = 0, GDML_TF32 = 1, GDML_BF16 = 2 } gdml_precision;
+
+/* Inducing-column selection rule (Sec. 3, "Column selection strategies"). */
+typedef enum {
+  GDML_SEL_UNIFORM = 0, /* k distinct columns, uniformly at random */
+  GDML_SEL_RLS = 1,     /* sampled without replacement by estimated ridge leverage scores */
+  GDML_SEL_PIVCHOL = 2  /* incomplete Cholesky with greedy diagonal pivoting (Alg. 1) */
+} gdml_select;
+
+/* Build a context for one kernel system (Sec. 2.1, Eq. 1).
+ *  R_dev:  M*N*3 doubles, geometry a atom i coordinate q at (a*N + i)*3 + q, Angstrom.
+ *  M >= 1 geometries, 2 <= N <= 128 atoms, sigma > 0 (Matern length scale),
+ *  lambda > 0 (ridge), precision: a gdml_precision value.
+ *  cuda_stream: a cudaStream_t on the current device, or NULL for the legacy stream.
+ * Computes descriptors, Jacobians, the M x M descriptor-distance tables and
+ * diag(K) on the device.  On success *ctx owns that state until gdml_destroy.
+ * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA (then *ctx is NULL). */
+gdml_status gdml_kernel_setup(gdml_ctx** ctx, const double* R_dev, int64_t M, int32_t N,
+                              double sigma, double lambda, int32_t precision, void* cuda_stream);
+
+/* out = K v (+ lambda v if add_lambda), both length n = 3 N M, in the
+ * context's precision (FP64 contexts: FP64; TF32/BF16: tensor-core matvec
+ * with FP32 accumulation, result stored as double).  v_dev and out_dev must
+ * not overlap.  The matvec is matrix-free: w_b = J_b v_b, u_a = sum_b H_ab w_b,
+ * (K v)_a = J_a^T u_a (Sec. 2.1, "only relies on evaluations of
+ * matrix-vector products"). */
+gdml_status gdml_matvec(gdml_ctx* ctx, const double* v_dev, double* out_dev, int32_t add_lambda);
+
+/* Same as gdml_matvec but always in FP64, whatever the context precision. */
+gdml_status gdml_matvec_fp64(gdml_ctx* ctx, const double* v_dev, double* out_dev, int32_t add_lambda);
+
+/* Build the Nystrom-type preconditioner (Eqs. 3-5, Sec. 3, Alg. 1).
+ *  method: gdml_select; 1 <= k <= min(n, 16384); seed: Philox4x32-10 key
+ *  (uniform: counter (i, 0), rls pilot: (i, 1), rls sampling: (i, 2)).
+ *  pivots_dev (may be NULL): k int64 column indices in selection order
+ *    (uniform/rls: ascending key; pivchol: pivot order of Alg. 1).
+ *  resid_trace_dev (may be NULL): k doubles; for pivchol the sum of the
+ *    residual diagonal after each step (monotone, Sec. 3), else zeros.
+ * Uniform/RLS: L_k = K_nk L_kk^-T with K_kk = L_kk L_kk^T (Eq. 5); if that
+ * Cholesky fails, jitter eps = 1e-14 tr(K_kk)/k is added and multiplied by 10
+ * per retry up to 1e-6 tr(K_kk)/k.  Pivchol: L_k from Alg. 1 (stops early,
+ * with a smaller rank, if the largest residual diagonal is <= 0).
+ * Then C = lambda I + L_k^T L_k and its FP64 Cholesky factor (Eq. 4).
+ * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_NOT_SPD, GDML_ERR_CUDA. */
+gdml_status gdml_precond_build(gdml_ctx* ctx, int32_t method, int64_t k, uint64_t seed,
+                               int64_t* pivots_dev, double* resid_trace_dev);
+
+/* Rank actually built by the last gdml_precond_build (pivchol may stop early),
+ * and the jitter added to K_kk (0 if none).  Host outputs; either may be NULL. */
+gdml_status gdml_precond_info(const gdml_ctx* ctx, int64_t* rank_out, double* jitter_out);
+
+/* z = P^-1 r by the Woodbury identity (Eq. 4).  r_dev, z_dev: length n, may
+ * not overlap.  Errors: GDML_ERR_STATE if no preconditioner was built. */
+gdml_status gdml_precond_apply(gdml_ctx* ctx, const double* r_dev, double* z_dev);
+
+/* Solve K_lambda alpha = y by PCG (Sec. 2.1, Eq. 2), x0 = alpha_dev's
+ * contents on entry (pass zeros for the paper's cold start).  The stopping
+ * test is the TRUE relative residual |y - K_lambda alpha|_2 / |y|_2 <= rtol,
+ * recomputed in FP64 when the recurrence residual passes (restart from alpha
+ * if it has drifted, at most 3 times).  TF32/BF16 contexts run FP64 iterative
+ * refinement: the inner PCG uses the tensor-core matvec and stops at
+ * inner_rtol relative to its own right-hand side; the outer loop recomputes
+ * r = y - K_lambda alpha with the FP64 matvec (at most 20 outer steps).
+ * Uses the preconditioner if one was built, else P = I.
+ *  iters_out (host, may be NULL): total inner PCG iterations.
+ *  relres_out (host, may be NULL): final true relative residual (FP64).
+ * Synchronises the context's stream before returning.
+ * Errors: GDML_ERR_NOT_CONVERGED (alpha holds the best iterate),
+ * GDML_ERR_BREAKDOWN, GDML_ERR_ARG, GDML_ERR_CUDA. */
+gdml_status gdml_pcg_solve(gdml_ctx* ctx, const double* y_dev, double* alpha_dev, double rtol,
+                           int32_t max_iter, int32_t* iters_out, double* relres_out);
+
+/* Inner tolerance of the mixed-precision refinement (default 1e-3 for BF16,
+ * 1e-4 for TF32; ignored in FP64 contexts). */
+gdml_status gdml_set_inner_rtol(gdml_ctx* ctx, double inner_rtol);
+
+/* Outer refinement steps of the last gdml_pcg_solve (1 for FP64 contexts). */
+gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
+
+/* Message describing the last error on ctx (or the last failed setup when
+ * ctx is NULL).  Never NULL; valid until the next call on the context. */
+const char* gdml_last_error(const gdml_ctx* ctx);
+
+/* Release all device memory owned by ctx (NULL is allowed). */
+void gdml_destroy(gdml_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDML_H */

@@ -1,0 +1,31 @@
+/*
+ * gdml_testing.h -- diagnostic entry points of libgdml, used by the test suite.
+ * Same conventions as gdml.h (device pointers, status codes, no exceptions).
+ */
+#ifndef GDML_TESTING_H
+#define GDML_TESTING_H
+
+#include "gdml.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = A B^T on the tcgen05 tensor cores, the building block of the TF32/BF16
+ * matvec (Sec. 2.1: the matvec's descriptor contractions).  A: M x K, B: N x K,
+ * C: M x N, all row-major FP64 device arrays; A and B are rounded to TF32
+ * (bf16 = 0) or BF16 (bf16 = 1) and accumulated in FP32.  Synchronises the
+ * stream.  Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA, GDML_ERR_TIMEOUT
+ * (a bounded pipeline wait gave up). */
+gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B_dev, int32_t M, int32_t N,
+                              int32_t K, double* C_dev, void* cuda_stream);
+
+/* Reads and clears the error word of the tensor-core kernels of a TF32/BF16
+ * context (synchronises its stream); GDML_ERR_TIMEOUT if a tcgen05 pipeline
+ * wait gave up since the last check.  FP64 contexts: always GDML_OK. */
+gdml_status gdml_tc_check(gdml_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDML_TESTING_H */

@@ -105,6 +105,25 @@ def force_kernel_column(R: np.ndarray, sigma: float, col: int) -> np.ndarray:
     return out
 
 
+def column_getter(R: np.ndarray, sigma: float):
+    """get_col(i) -> K[:, i] as in force_kernel_column, with the descriptor and
+    Jacobian computed once (for Algorithm 1 on larger inputs)."""
+    M, N, _ = R.shape
+    B = 3 * N
+    X, _ = descriptor(R)
+    Jac = jacobian(R)
+
+    def get_col(col):
+        b, local = divmod(int(col), B)
+        w = Jac[b][:, local]
+        out = np.empty(M * B)
+        for a in range(M):
+            out[a * B:(a + 1) * B] = Jac[a].T @ (hessian_block(X[a], X[b], sigma) @ w)
+        return out
+
+    return get_col
+
+
 def force_kernel_diag(R: np.ndarray, sigma: float) -> np.ndarray:
     """diag(K): K_aa = (c^2/3) J_a^T J_a since r = 0 on the diagonal block."""
     c = np.sqrt(5.0) / sigma

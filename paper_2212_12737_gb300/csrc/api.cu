@@ -1,0 +1,654 @@
+// C ABI of libgdml (declared in include/gdml.h): context, matvec,
+// preconditioner build / apply and the PCG solve.  Every step runs in the
+// kernels of this library; the host only sequences launches.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+#include "../../include/gdml_testing.h"
+
+namespace gdml {
+
+static thread_local std::string g_msg;
+gdml_status fail(gdml_status st, const std::string& msg) {
+  g_msg = msg;
+  return st;
+}
+const std::string& last_msg() { return g_msg; }
+void clear_msg() { g_msg.clear(); }
+
+}  // namespace gdml
+
+using namespace gdml;
+
+struct gdml_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  int64_t M = 0, n = 0;
+  int N = 0, D = 0, B = 0;
+  double sigma = 0, lam = 0, c = 0;
+  int precision = GDML_FP64;
+  double inner_rtol = 1e-4;
+  int last_outer = 0;
+  std::string err;
+  std::vector<void*> allocs;
+
+  // kernel state
+  double* R = nullptr;    // M*N*3
+  double* X = nullptr;    // M*D
+  double* G = nullptr;    // M*D*3
+  double* S = nullptr;    // M*M
+  double* P64 = nullptr;  // M x 2M : [A | beta]
+  double* V64 = nullptr;  // 2M x D : [W ; Xc]
+  double* T = nullptr;    // M*M
+  double* tb = nullptr;   // M
+  double* rowsum = nullptr;
+  double* U = nullptr;  // M*D
+  double* diag = nullptr;  // n
+  double* Xc() const { return V64 + M * D; }
+  TcMatvec tc;  // tensor-core matvec state (TF32/BF16 contexts)
+
+  // preconditioner
+  int64_t k = 0;  // rank built (0: none)
+  double jitter = 0;
+  double* L = nullptr;    // n x k col-major
+  double* LC = nullptr;   // k x k lower (row-major)
+  double* wpart = nullptr;
+  double* wt = nullptr;
+  int64_t cap_k = 0;
+
+  // PCG state
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr, *ys = nullptr;
+  double* sc = nullptr;       // SC_COUNT scalars
+  double* partial = nullptr;  // dot partials
+  unsigned* ticket = nullptr;
+  int* status = nullptr;      // device status word
+  double* hsc = nullptr;      // pinned host mirror of scalars
+};
+
+namespace {
+
+gdml_status ctx_fail(gdml_ctx* c, gdml_status st, const std::string& m) {
+  if (c) c->err = m;
+  return fail(st, m);
+}
+
+template <typename T>
+gdml_status dalloc(gdml_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return ctx_fail(c, GDML_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  c->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return GDML_OK;
+}
+
+void dfree(gdml_ctx* c, void* p) {
+  if (!p) return;
+  for (auto& a : c->allocs)
+    if (a == p) {
+      cudaFree(a);
+      a = nullptr;
+    }
+}
+
+#define TRY(x)                          \
+  do {                                  \
+    gdml_status _s = (x);               \
+    if (_s != GDML_OK) return _s;       \
+  } while (0)
+#define CTRY(c, expr)                                                                           \
+  do {                                                                                          \
+    cudaError_t _e = (expr);                                                                    \
+    if (_e != cudaSuccess) return ctx_fail(c, GDML_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+gdml_status check_launch(gdml_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ctx_fail(c, GDML_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return GDML_OK;
+}
+
+// ----------------------------------------------------------------- matvec
+gdml_status matvec_fp64(gdml_ctx* c, const double* v, double* out, int add_lambda) {
+  const int64_t M = c->M;
+  const int D = c->D;
+  cudaStream_t st = c->st;
+  double* W = c->V64;
+  launch_proj(c->G, c->Xc(), v, M, c->N, D, W, D, c->tb, st);
+  // T = Xc W^T
+  launch_dgemm<double, double>(true, M, M, D, 1.0, c->Xc(), D, W, D, 0.0, c->T, M, false, st);
+  launch_beta(c->T, c->S, c->tb, M, c->c, c->P64 + M, 2 * M, c->rowsum, st);
+  // U = [A | beta] [W ; Xc]
+  launch_dgemm<double, double>(false, M, D, 2 * M, 1.0, c->P64, 2 * M, c->V64, D, 0.0, c->U, D, false, st);
+  launch_backproj<double>(c->U, D, c->rowsum, c->Xc(), c->G, v, M, c->N, D, c->lam, add_lambda, out, st);
+  return check_launch(c, "matvec_fp64");
+}
+
+gdml_status matvec_any(gdml_ctx* c, const double* v, double* out, int add_lambda, bool force_fp64) {
+  if (force_fp64 || c->precision == GDML_FP64) return matvec_fp64(c, v, out, add_lambda);
+  gdml_status s = tc_matvec(c->tc, c->G, v, out, add_lambda, c->lam, c->st);
+  if (s != GDML_OK) return ctx_fail(c, s, "tensor-core matvec: " + last_msg());
+  return check_launch(c, "matvec_tc");
+}
+
+// ------------------------------------------------------------ preconditioner
+__global__ void gather_kkk_kernel(const double* __restrict__ Knk, int64_t n, const int64_t* __restrict__ S,
+                                  int64_t k, double* __restrict__ Kkk) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  int64_t r = e / k, cc = e - r * k;
+  Kkk[e] = Knk[cc * n + S[r]];
+}
+
+__global__ void col_sqnorm_kernel(const double* __restrict__ Z, int64_t k, int64_t n, double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t r = 0; r < k; ++r) {
+    double v = Z[r * n + i];
+    s = fma(v, v, s);
+  }
+  out[i] = s;
+}
+
+__global__ void fill_kernel(double* p, int64_t n, double v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+gdml_status read_status(gdml_ctx* c, int* h) {
+  CTRY(c, cudaMemcpyAsync(h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  return GDML_OK;
+}
+
+gdml_status get_cols(gdml_ctx* c, const int64_t* cols, int64_t ncols, double* out) {
+  launch_kcol(cols, ncols, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, nullptr, c->st);
+  return check_launch(c, "kcol");
+}
+
+// In-place lower Cholesky of the k x k work matrix (copy of src) with the
+// jitter rule of Eq. 5's factorisation: eps = 1e-14 tr/k, x10 up to 1e-6 tr/k.
+gdml_status chol_jitter(gdml_ctx* c, const double* src, double* work, int64_t k, double* eps_out) {
+  std::vector<double> hdiag(k);
+  CTRY(c, cudaMemcpy2DAsync(hdiag.data(), sizeof(double), src, (k + 1) * sizeof(double), sizeof(double), k,
+                            cudaMemcpyDeviceToHost, c->st));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  double tr = 0.0;
+  for (double v : hdiag) tr += v;
+  const double scale = tr / (double)k;
+  double eps = 0.0;
+  for (;;) {
+    CTRY(c, cudaMemcpyAsync(work, src, k * k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    if (eps > 0.0) add_diag(work, k, k, eps, c->st);
+    CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+    cholesky_inplace(work, k, c->status, c->st);
+    TRY(check_launch(c, "cholesky"));
+    int h = 0;
+    TRY(read_status(c, &h));
+    if (h == 0) break;
+    eps = (eps == 0.0) ? 1e-14 * scale : eps * 10.0;
+    if (!(eps <= 1e-6 * scale * 1.0000001))
+      return ctx_fail(c, GDML_ERR_NOT_SPD, "Cholesky of the inducing block failed even with jitter 1e-6 tr/k");
+  }
+  *eps_out = eps;
+  return GDML_OK;
+}
+
+// L (k x n row-major = n x k col-major) <- Nystrom factor from columns S (Eq. 5)
+gdml_status nystrom(gdml_ctx* c, const int64_t* S, int64_t k, double* L, double* Kkk, double* work,
+                    double* eps_out) {
+  TRY(get_cols(c, S, k, L));
+  gather_kkk_kernel<<<(unsigned)cdiv(k * k, 256), 256, 0, c->st>>>(L, c->n, S, k, Kkk);
+  TRY(check_launch(c, "gather_kkk"));
+  TRY(chol_jitter(c, Kkk, work, k, eps_out));
+  trsm_left_lower(work, k, L, c->n, c->st);  // rows of K_nk^T -> rows of L_k^T
+  return check_launch(c, "trsm");
+}
+
+// LC <- chol(lambda I + L^T L)
+gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC) {
+  launch_dgemm<double, double>(true, k, k, c->n, 1.0, L, c->n, L, c->n, 0.0, LC, k, true, c->st);
+  add_diag(LC, k, k, c->lam, c->st);
+  CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+  cholesky_inplace(LC, k, c->status, c->st);
+  TRY(check_launch(c, "woodbury_core"));
+  int h = 0;
+  TRY(read_status(c, &h));
+  if (h) return ctx_fail(c, GDML_ERR_NOT_SPD, "Cholesky of lambda I + L^T L failed at column " + std::to_string(h - 1));
+  return GDML_OK;
+}
+
+gdml_status ensure_precond_buffers(gdml_ctx* c, int64_t k) {
+  if (k <= c->cap_k) return GDML_OK;
+  dfree(c, c->L);
+  dfree(c, c->LC);
+  dfree(c, c->wpart);
+  dfree(c, c->wt);
+  c->L = c->LC = c->wpart = c->wt = nullptr;
+  c->cap_k = 0;
+  TRY(dalloc(c, &c->L, (size_t)(c->n * k)));
+  TRY(dalloc(c, &c->LC, (size_t)(k * k)));
+  TRY(dalloc(c, &c->wpart, (size_t)woodbury_part_size(c->n, k)));
+  TRY(dalloc(c, &c->wt, (size_t)k));
+  c->cap_k = k;
+  return GDML_OK;
+}
+
+struct Scratch {
+  gdml_ctx* c;
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) dfree(c, p);
+  }
+  template <typename T>
+  gdml_status get(T** p, size_t count) {
+    gdml_status s = dalloc(c, p, count);
+    if (s == GDML_OK) ptrs.push_back(*p);
+    return s;
+  }
+};
+
+// ------------------------------------------------------------------ PCG
+gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
+  if (c->k == 0) {
+    CTRY(c, cudaMemcpyAsync(z, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return GDML_OK;
+  }
+  woodbury_apply<double>(c->L, c->n, c->k, c->LC, c->lam, r, z, c->wpart, c->wt, c->st);
+  return check_launch(c, "woodbury_apply");
+}
+
+gdml_status dot(gdml_ctx* c, const double* a, const double* b, int slot) {
+  launch_dot(a, b, c->n, c->partial, c->ticket, c->sc + slot, c->st);
+  return GDML_OK;
+}
+
+gdml_status fetch_scalars(gdml_ctx* c) {
+  CTRY(c, cudaMemcpyAsync(c->hsc, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  return GDML_OK;
+}
+
+// PCG on K_lambda x = b (x updated in place).  Stops when the recurrence
+// residual |r| <= tol_abs; with check_true, the true residual is recomputed
+// (FP64 or the context precision as given) and CG restarts if it drifted.
+// Returns iterations used through *iters; *res_out = final |r| (true if check_true).
+gdml_status pcg_core(gdml_ctx* c, const double* b, double* x, double tol_abs, int64_t max_iter, bool fp64_mv,
+                     bool check_true, int max_restarts, int64_t* iters, double* res_out) {
+  const int64_t n = c->n;
+  cudaStream_t st = c->st;
+  int64_t it = 0;
+  int restarts = 0;
+  // r = b - K x
+  TRY(matvec_any(c, x, c->r, 1, fp64_mv));
+  launch_axpby(c->r, b, 1.0, -1.0, n, st);
+  double res = 0.0;
+  for (;;) {
+    TRY(dot(c, c->r, c->r, SC_RR));
+    TRY(fetch_scalars(c));
+    res = std::sqrt(c->hsc[SC_RR]);
+    if (res <= tol_abs) break;
+    TRY(apply_precond(c, c->r, c->z));
+    CTRY(c, cudaMemcpyAsync(c->p, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TRY(dot(c, c->r, c->z, SC_RHO));
+    bool conv = false;
+    while (it < max_iter) {
+      TRY(matvec_any(c, c->p, c->q, 1, fp64_mv));
+      TRY(dot(c, c->p, c->q, SC_PQ));
+      CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), st));
+      launch_update_xr(x, c->r, c->p, c->q, n, c->sc, c->status, st);
+      TRY(dot(c, c->r, c->r, SC_RR));
+      ++it;
+      TRY(fetch_scalars(c));
+      int hst = 0;
+      TRY(read_status(c, &hst));
+      if (hst) {
+        *iters = it;
+        *res_out = res;
+        return ctx_fail(c, GDML_ERR_BREAKDOWN, "PCG breakdown: p^T K p <= 0 or not finite");
+      }
+      res = std::sqrt(c->hsc[SC_RR]);
+      if (!std::isfinite(res)) {
+        *iters = it;
+        *res_out = res;
+        return ctx_fail(c, GDML_ERR_BREAKDOWN, "PCG residual not finite");
+      }
+      if (res <= tol_abs) {
+        conv = true;
+        break;
+      }
+      TRY(apply_precond(c, c->r, c->z));
+      TRY(dot(c, c->r, c->z, SC_RHO_NEW));
+      launch_update_p(c->p, c->z, n, c->sc, st);
+      launch_copy_scalar(c->sc, SC_RHO, SC_RHO_NEW, st);
+      TRY(check_launch(c, "pcg iteration"));
+    }
+    if (!check_true) break;
+    // true residual
+    TRY(matvec_any(c, x, c->r, 1, true));
+    launch_axpby(c->r, b, 1.0, -1.0, n, st);
+    TRY(dot(c, c->r, c->r, SC_RR));
+    TRY(fetch_scalars(c));
+    res = std::sqrt(c->hsc[SC_RR]);
+    if (res <= tol_abs || it >= max_iter || restarts >= max_restarts || !conv) break;
+    ++restarts;
+  }
+  *iters = it;
+  *res_out = res;
+  return GDML_OK;
+}
+
+gdml_status validate(const gdml_ctx* c) {
+  if (!c) return fail(GDML_ERR_ARG, "null context");
+  return GDML_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, int32_t N, double sigma,
+                              double lambda, int32_t precision, void* cuda_stream) {
+  clear_msg();
+  if (!out) return fail(GDML_ERR_ARG, "ctx out-pointer is NULL");
+  *out = nullptr;
+  if (!R_dev) return fail(GDML_ERR_ARG, "R_dev is NULL");
+  if (M < 1 || N < 2 || N > 128) return fail(GDML_ERR_ARG, "need M >= 1 and 2 <= N <= 128");
+  if (!(sigma > 0.0) || !(lambda > 0.0) || !std::isfinite(sigma) || !std::isfinite(lambda))
+    return fail(GDML_ERR_ARG, "need sigma > 0 and lambda > 0");
+  if (precision < GDML_FP64 || precision > GDML_BF16) return fail(GDML_ERR_ARG, "unknown precision");
+  std::unique_ptr<gdml_ctx, void (*)(gdml_ctx*)> c(new gdml_ctx(), &gdml_destroy);
+  CTRY(c.get(), cudaGetDevice(&c->device));
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  c->M = M;
+  c->N = N;
+  c->D = N * (N - 1) / 2;
+  c->B = 3 * N;
+  c->n = 3 * (int64_t)N * M;
+  c->sigma = sigma;
+  c->lam = lambda;
+  c->c = std::sqrt(5.0) / sigma;
+  c->precision = precision;
+  c->inner_rtol = precision == GDML_BF16 ? 1e-3 : 1e-4;
+  const int64_t D = c->D, n = c->n;
+  gdml_ctx* C = c.get();
+  TRY(dalloc(C, &c->R, (size_t)(M * N * 3)));
+  TRY(dalloc(C, &c->X, (size_t)(M * D)));
+  TRY(dalloc(C, &c->G, (size_t)(M * D * 3)));
+  TRY(dalloc(C, &c->S, (size_t)(M * M)));
+  TRY(dalloc(C, &c->P64, (size_t)(2 * M * M)));
+  TRY(dalloc(C, &c->V64, (size_t)(2 * M * D)));
+  TRY(dalloc(C, &c->T, (size_t)(M * M)));
+  TRY(dalloc(C, &c->tb, (size_t)M));
+  TRY(dalloc(C, &c->rowsum, (size_t)M));
+  TRY(dalloc(C, &c->U, (size_t)(M * D)));
+  TRY(dalloc(C, &c->diag, (size_t)n));
+  for (double** v : {&c->r, &c->z, &c->p, &c->q, &c->x, &c->ys}) TRY(dalloc(C, v, (size_t)n));
+  TRY(dalloc(C, &c->sc, SC_COUNT));
+  TRY(dalloc(C, &c->partial, 4096));
+  TRY(dalloc(C, &c->ticket, 1));
+  TRY(dalloc(C, &c->status, 1));
+  CTRY(C, cudaMallocHost(&c->hsc, SC_COUNT * sizeof(double)));
+  CTRY(C, cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), c->st));
+  CTRY(C, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+  CTRY(C, cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), c->st));
+  CTRY(C, cudaMemcpyAsync(c->R, R_dev, M * N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  launch_desc_jac(c->R, M, N, (int)D, c->X, c->G, c->st);
+  launch_center(c->X, M, (int)D, c->Xc(), c->st);
+  launch_dist_tab(c->X, M, (int)D, c->c, c->S, c->P64, 2 * M, c->st);
+  launch_kdiag(c->G, M, N, (int)D, c->c, c->diag, c->st);
+  TRY(check_launch(C, "setup kernels"));
+  if (precision != GDML_FP64) {
+    gdml_status s = tc_setup(c->tc, precision, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->c, c->st);
+    if (s != GDML_OK) return ctx_fail(C, s, "tensor-core setup: " + last_msg());
+  }
+  CTRY(C, cudaStreamSynchronize(c->st));
+  *out = c.release();
+  return GDML_OK;
+}
+
+gdml_status gdml_matvec(gdml_ctx* c, const double* v, double* out, int32_t add_lambda) {
+  TRY(validate(c));
+  if (!v || !out || v == out) return ctx_fail(c, GDML_ERR_ARG, "matvec: bad pointers");
+  return matvec_any(c, v, out, add_lambda ? 1 : 0, false);
+}
+
+gdml_status gdml_matvec_fp64(gdml_ctx* c, const double* v, double* out, int32_t add_lambda) {
+  TRY(validate(c));
+  if (!v || !out || v == out) return ctx_fail(c, GDML_ERR_ARG, "matvec: bad pointers");
+  return matvec_fp64(c, v, out, add_lambda ? 1 : 0);
+}
+
+gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t seed, int64_t* pivots_dev,
+                               double* resid_trace_dev) {
+  TRY(validate(c));
+  const int64_t n = c->n;
+  if (k < 1 || k > n || k > 16384) return ctx_fail(c, GDML_ERR_ARG, "need 1 <= k <= min(n, 16384)");
+  if (method < GDML_SEL_UNIFORM || method > GDML_SEL_PIVCHOL) return ctx_fail(c, GDML_ERR_ARG, "unknown method");
+  c->k = 0;
+  c->jitter = 0.0;
+  TRY(ensure_precond_buffers(c, k));
+  Scratch s{c, {}};
+  int64_t* S = nullptr;
+  TRY(s.get(&S, (size_t)k));
+  double* trace = nullptr;
+  TRY(s.get(&trace, (size_t)k));
+  CTRY(c, cudaMemsetAsync(trace, 0, k * sizeof(double), c->st));
+  CTRY(c, cudaMemsetAsync(S, 0xFF, k * sizeof(int64_t), c->st));
+  int64_t rank = k;
+  if (method == GDML_SEL_PIVCHOL) {
+    double* d = nullptr;
+    int64_t* perm = nullptr;
+    unsigned char* chosen = nullptr;
+    PivState* ps = nullptr;
+    ArgMaxPart* part = nullptr;
+    unsigned* ticket = nullptr;
+    double* col = nullptr;
+    TRY(s.get(&d, (size_t)n));
+    TRY(s.get(&perm, (size_t)n));
+    TRY(s.get(&chosen, (size_t)n));
+    TRY(s.get(&ps, 1));
+    TRY(s.get(&part, (size_t)pivchol_part_blocks()));
+    TRY(s.get(&ticket, 1));
+    TRY(s.get(&col, (size_t)n));
+    CTRY(c, cudaMemcpyAsync(d, c->diag, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    std::vector<int64_t> hperm(n);
+    for (int64_t i = 0; i < n; ++i) hperm[i] = i;
+    CTRY(c, cudaMemcpyAsync(perm, hperm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+    CTRY(c, cudaMemsetAsync(chosen, 0, n, c->st));
+    CTRY(c, cudaMemsetAsync(ps, 0, sizeof(PivState), c->st));
+    CTRY(c, cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->st));
+    CTRY(c, cudaMemsetAsync(c->L, 0, n * k * sizeof(double), c->st));
+    PivCholArgs a;
+    a.n = n;
+    a.k = k;
+    a.d = d;
+    a.perm = perm;
+    a.chosen = chosen;
+    a.pivots = S;
+    a.trace = trace;
+    a.ps = ps;
+    a.part = part;
+    a.ticket = ticket;
+    a.col = col;
+    a.get_col = [c](const int64_t* cols, double* out, const int* stop, cudaStream_t st) {
+      launch_kcol(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, stop, st);
+    };
+    pivchol_run<double>(a, c->L, c->st);
+    TRY(check_launch(c, "pivoted cholesky"));
+    PivState hps;
+    CTRY(c, cudaMemcpyAsync(&hps, ps, sizeof(PivState), cudaMemcpyDeviceToHost, c->st));
+    CTRY(c, cudaStreamSynchronize(c->st));
+    rank = hps.rank;
+    if (rank < 1) return ctx_fail(c, GDML_ERR_NOT_SPD, "diag(K) has no positive entry");
+  } else {
+    uint64_t* key = nullptr;
+    int64_t* idx = nullptr;
+    const int64_t P = select_scratch_len(n);
+    TRY(s.get(&key, (size_t)P));
+    TRY(s.get(&idx, (size_t)P));
+    double* Kkk = nullptr;
+    double* work = nullptr;
+    TRY(s.get(&Kkk, (size_t)(k * k)));
+    TRY(s.get(&work, (size_t)(k * k)));
+    if (method == GDML_SEL_RLS) {
+      // pilot Nystrom estimate of the ridge leverage scores (pilot size k, Philox stream 1)
+      select_uniform(n, k, seed, 1u, key, idx, S, c->st);
+      double eps0 = 0.0;
+      TRY(nystrom(c, S, k, c->L, Kkk, work, &eps0));  // B (n x k col-major)
+      TRY(woodbury_core(c, c->L, k, c->LC));          // chol(B^T B + lambda I)
+      trsm_left_lower(c->LC, k, c->L, n, c->st);       // Z = L_C^-1 B^T
+      double* tau = nullptr;
+      TRY(s.get(&tau, (size_t)n));
+      col_sqnorm_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c->st>>>(c->L, k, n, tau);
+      TRY(check_launch(c, "rls scores"));
+      select_weighted(n, k, seed, 2u, tau, key, idx, S, c->st);
+    } else {
+      select_uniform(n, k, seed, 0u, key, idx, S, c->st);
+    }
+    TRY(check_launch(c, "selection"));
+    TRY(nystrom(c, S, k, c->L, Kkk, work, &c->jitter));
+  }
+  TRY(woodbury_core(c, c->L, rank, c->LC));
+  if (pivots_dev) CTRY(c, cudaMemcpyAsync(pivots_dev, S, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st));
+  if (resid_trace_dev)
+    CTRY(c, cudaMemcpyAsync(resid_trace_dev, trace, k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  c->k = rank;
+  return GDML_OK;
+}
+
+gdml_status gdml_precond_info(const gdml_ctx* c, int64_t* rank_out, double* jitter_out) {
+  TRY(validate(c));
+  if (rank_out) *rank_out = c->k;
+  if (jitter_out) *jitter_out = c->jitter;
+  return GDML_OK;
+}
+
+gdml_status gdml_precond_apply(gdml_ctx* c, const double* r, double* z) {
+  TRY(validate(c));
+  if (!r || !z || r == z) return ctx_fail(c, GDML_ERR_ARG, "precond_apply: bad pointers");
+  if (c->k == 0) return ctx_fail(c, GDML_ERR_STATE, "no preconditioner built");
+  return apply_precond(c, r, z);
+}
+
+gdml_status gdml_set_inner_rtol(gdml_ctx* c, double v) {
+  TRY(validate(c));
+  if (!(v > 0.0 && v < 1.0)) return ctx_fail(c, GDML_ERR_ARG, "inner_rtol must be in (0, 1)");
+  c->inner_rtol = v;
+  return GDML_OK;
+}
+
+gdml_status gdml_last_outer_steps(const gdml_ctx* c, int32_t* o) {
+  TRY(validate(c));
+  if (o) *o = c->last_outer;
+  return GDML_OK;
+}
+
+gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double rtol, int32_t max_iter,
+                           int32_t* iters_out, double* relres_out) {
+  TRY(validate(c));
+  if (!y || !alpha || y == alpha) return ctx_fail(c, GDML_ERR_ARG, "pcg_solve: bad pointers");
+  if (!(rtol > 0.0) || max_iter < 1) return ctx_fail(c, GDML_ERR_ARG, "need rtol > 0 and max_iter >= 1");
+  const int64_t n = c->n;
+  cudaStream_t st = c->st;
+  // |y|
+  CTRY(c, cudaMemcpyAsync(c->ys, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TRY(dot(c, c->ys, c->ys, SC_YY));
+  TRY(fetch_scalars(c));
+  const double ynorm = std::sqrt(c->hsc[SC_YY]);
+  int64_t iters = 0;
+  double res = 0.0;
+  gdml_status stat = GDML_OK;
+  if (ynorm == 0.0) {
+    CTRY(c, cudaMemsetAsync(alpha, 0, n * sizeof(double), st));
+    c->last_outer = 0;
+  } else if (c->precision == GDML_FP64) {
+    stat = pcg_core(c, c->ys, alpha, rtol * ynorm, max_iter, true, true, 3, &iters, &res);
+    c->last_outer = 1;
+  } else {
+    // FP64 iterative refinement around the tensor-core PCG
+    double* dx = c->x;
+    double* rhs = nullptr;
+    Scratch s{c, {}};
+    TRY(s.get(&rhs, (size_t)n));
+    // r = y - K alpha (FP64)
+    TRY(matvec_any(c, alpha, rhs, 1, true));
+    launch_axpby(rhs, c->ys, 1.0, -1.0, n, st);
+    int outer = 0;
+    for (;;) {
+      TRY(dot(c, rhs, rhs, SC_RR));
+      TRY(fetch_scalars(c));
+      res = std::sqrt(c->hsc[SC_RR]);
+      if (res <= rtol * ynorm || outer >= 20 || iters >= max_iter) break;
+      ++outer;
+      CTRY(c, cudaMemsetAsync(dx, 0, n * sizeof(double), st));
+      int64_t it_in = 0;
+      double res_in = 0.0;
+      const double tol_in = std::max(c->inner_rtol * res, 0.5 * rtol * ynorm);
+      stat = pcg_core(c, rhs, dx, tol_in, max_iter - iters, false, false, 0, &it_in, &res_in);
+      iters += it_in;
+      if (stat != GDML_OK) break;
+      launch_axpby(alpha, dx, 1.0, 1.0, n, st);
+      TRY(matvec_any(c, alpha, rhs, 1, true));
+      launch_axpby(rhs, c->ys, 1.0, -1.0, n, st);
+      TRY(check_launch(c, "refinement"));
+    }
+    c->last_outer = outer;
+  }
+  CTRY(c, cudaStreamSynchronize(st));
+  if (c->precision != GDML_FP64) {
+    gdml_status ts = tc_check(c->tc, st);
+    if (ts != GDML_OK) return ctx_fail(c, ts, last_msg());
+  }
+  if (iters_out) *iters_out = (int32_t)iters;
+  const double rel = ynorm > 0 ? res / ynorm : 0.0;
+  if (relres_out) *relres_out = rel;
+  if (stat != GDML_OK) return stat;
+  if (rel > rtol) return ctx_fail(c, GDML_ERR_NOT_CONVERGED, "PCG did not reach rtol within max_iter");
+  return GDML_OK;
+}
+
+gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B_dev, int32_t M, int32_t N,
+                              int32_t K, double* C_dev, void* stream) {
+  clear_msg();
+  if (!A_dev || !B_dev || !C_dev || M < 1 || N < 1 || K < 1) return fail(GDML_ERR_ARG, "bad gemm test arguments");
+  return tc_gemm_test(bf16, A_dev, B_dev, M, N, K, C_dev, static_cast<cudaStream_t>(stream));
+}
+
+gdml_status gdml_tc_check(gdml_ctx* c) {
+  TRY(validate(c));
+  if (c->precision == GDML_FP64) return GDML_OK;
+  gdml_status s = tc_check(c->tc, c->st);
+  if (s != GDML_OK) return ctx_fail(c, s, last_msg());
+  return GDML_OK;
+}
+
+const char* gdml_last_error(const gdml_ctx* c) {
+  if (c) return c->err.c_str();
+  return last_msg().c_str();
+}
+
+void gdml_destroy(gdml_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  tc_destroy(c->tc);
+  for (void* p : c->allocs)
+    if (p) cudaFree(p);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  delete c;
+}
+
+}  // extern "C"

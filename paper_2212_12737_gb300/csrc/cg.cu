@@ -1,0 +1,96 @@
+// CG vector kernels (Sec. 2.1, Eq. 2): deterministic dot products and the
+// fused PCG updates.  Scalars stay in device memory; no host round trip is
+// needed inside an iteration.
+//
+// Every reduction uses a fixed grid (kDotBlocks CTAs, each a contiguous
+// chunk) and a fixed combination order, so results are bitwise reproducible.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gdml {
+
+constexpr int kDotBlocks = 2 * kNumSMs;
+constexpr int kDotThreads = 256;
+
+// partial[blockIdx.x] = sum over the CTA's chunk of x*y; the last CTA to finish
+// sums the partials in index order into *out (and zeroes the ticket).
+__global__ void __launch_bounds__(kDotThreads) dot_kernel(const double* __restrict__ x,
+                                                          const double* __restrict__ y, int64_t n,
+                                                          double* __restrict__ partial,
+                                                          unsigned* __restrict__ ticket,
+                                                          double* __restrict__ out) {
+  __shared__ double red[kDotThreads / 32];
+  __shared__ bool last;
+  const int64_t chunk = cdiv_dev(n, gridDim.x);
+  const int64_t beg = blockIdx.x * chunk;
+  const int64_t end = beg + chunk < n ? beg + chunk : n;
+  double s = 0.0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += kDotThreads) s = fma(x[i], y[i], s);
+  s = block_sum<kDotThreads>(s, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double tot = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) tot += ((volatile double*)partial)[b];
+    *out = tot;
+    *ticket = 0u;
+  }
+}
+
+// x += gamma p; r -= gamma q with gamma = sc[RHO] / sc[PQ]; flags breakdown.
+__global__ void update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                                 const double* __restrict__ q, int64_t n, const double* __restrict__ sc,
+                                 int* __restrict__ status) {
+  const double pq = sc[SC_PQ];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 1;
+    return;
+  }
+  const double gamma = sc[SC_RHO] / pq;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(gamma, p[i], x[i]);
+    r[i] = fma(-gamma, q[i], r[i]);
+  }
+}
+
+// p = z + (rho_new / rho) p ; rho <- rho_new (done by one thread after use)
+__global__ void update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+                                const double* __restrict__ sc) {
+  const double beta = sc[SC_RHO_NEW] / sc[SC_RHO];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void copy_scalar_kernel(double* sc, int dst, int src) { sc[dst] = sc[src]; }
+
+__global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], b * y[i]);
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,
+                cudaStream_t st) {
+  dot_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(x, y, n, partial, ticket, out);
+}
+void launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const double* sc,
+                      int* status, cudaStream_t st) {
+  update_xr_kernel<<<4 * kNumSMs, 256, 0, st>>>(x, r, p, q, n, sc, status);
+}
+void launch_update_p(double* p, const double* z, int64_t n, const double* sc, cudaStream_t st) {
+  update_p_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc);
+}
+void launch_copy_scalar(double* sc, int dst, int src, cudaStream_t st) {
+  copy_scalar_kernel<<<1, 1, 0, st>>>(sc, dst, src);
+}
+void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st) {
+  axpby_kernel<<<4 * kNumSMs, 256, 0, st>>>(y, x, a, b, n);
+}
+
+}  // namespace gdml

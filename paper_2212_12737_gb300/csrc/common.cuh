@@ -1,0 +1,55 @@
+// Shared helpers for the libgdml CUDA sources (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/gdml.h"
+
+namespace gdml {
+
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs; grids are sized in multiples of it
+
+// Host-side error carrier: every internal call returns a gdml_status and
+// writes a message into the context.
+struct Err {
+  gdml_status st = GDML_OK;
+  std::string msg;
+};
+
+#define GDML_CUDA_TRY(expr)                                                              \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      return ::gdml::fail(GDML_ERR_CUDA, std::string(#expr " -> ") + cudaGetErrorString(_e)); \
+    }                                                                                    \
+  } while (0)
+
+// thread-local last error (used when no context exists yet)
+gdml_status fail(gdml_status st, const std::string& msg);
+const std::string& last_msg();
+void clear_msg();
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__device__ __forceinline__ int64_t cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Deterministic block reduction of one double (fixed tree order).
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < THREADS / 32 ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+}  // namespace gdml

@@ -1,0 +1,114 @@
+// FP64 SIMT GEMM (DFMA) for the FP64 form of the matvec contractions, the
+// Woodbury core C = lambda I + L_k^T L_k (Eq. 4) and the blocked Cholesky /
+// triangular-solve updates.
+//
+//   C[m, n] = alpha * sum_k A[m, k] * Bop[k, n] + beta * C[m, n]
+//   A row-major (lda); Bop[k, n] = B[n*ldb + k] (NT) or B[k*ldb + n] (NN).
+//   Operands may be stored as float (products are then exact in FP64).
+//   lower_only: tiles strictly above the diagonal are skipped (SYRK-style).
+//
+// 64x64 output tile per CTA, 256 threads x (4x4) outputs, K-steps of 16
+// staged through shared memory with a register prefetch of the next step.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gdml {
+
+template <typename TA, typename TB, bool NT>
+__global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                                                    const TA* __restrict__ A, int64_t lda,
+                                                    const TB* __restrict__ B, int64_t ldb, double beta,
+                                                    double* __restrict__ C, int64_t ldc, int lower_only) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  if (lower_only && n0 > m0 + BM - 1) return;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  // loader mapping: 256 threads load 64x16 = 1024 elements of each tile (4 each)
+  double ra[4], rb[4];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int e = tid + 256 * u;          // 0..1023
+      int am = e >> 4, ak = e & 15;   // A tile: row am, col ak  (k fastest -> coalesced rows)
+      int64_t gm = m0 + am, gk = k0 + ak;
+      ra[u] = (gm < M && gk < K) ? (double)A[gm * lda + gk] : 0.0;
+      if (NT) {
+        int bn = e >> 4, bk = e & 15;
+        int64_t gn = n0 + bn, gk2 = k0 + bk;
+        rb[u] = (gn < N && gk2 < K) ? (double)B[gn * ldb + gk2] : 0.0;
+      } else {
+        int bk = e >> 6, bn = e & 63;  // n fastest -> coalesced
+        int64_t gn = n0 + bn, gk2 = k0 + bk;
+        rb[u] = (gn < N && gk2 < K) ? (double)B[gk2 * ldb + gn] : 0.0;
+      }
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int e = tid + 256 * u;
+      As[e & 15][e >> 4] = ra[u];
+      if (NT) Bs[e & 15][e >> 4] = rb[u];
+      else Bs[e >> 6][e & 63] = rb[u];
+    }
+  };
+  load(0);
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    store();
+    __syncthreads();
+    if (k0 + BK < K) load(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double* c = C + gm * ldc + gn;
+      *c = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+    }
+  }
+}
+
+template <typename TA, typename TB>
+void launch_dgemm(bool nt, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t lda,
+                  const TB* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
+                  cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64));
+  if (nt)
+    dgemm_kernel<TA, TB, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only);
+  else
+    dgemm_kernel<TA, TB, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only);
+}
+
+template void launch_dgemm<double, double>(bool, int64_t, int64_t, int64_t, double, const double*, int64_t,
+                                           const double*, int64_t, double, double*, int64_t, bool, cudaStream_t);
+template void launch_dgemm<float, float>(bool, int64_t, int64_t, int64_t, double, const float*, int64_t,
+                                         const float*, int64_t, double, double*, int64_t, bool, cudaStream_t);
+
+}  // namespace gdml

@@ -1,0 +1,310 @@
+// Geometry-side kernels of the force-kernel matvec (Sec. 2.1), FP64.
+//
+//  desc_jac   x_{a,p} = 1/|R_i - R_j|,  g_{a,p} = (R_i - R_j)/|R_i - R_j|^3  (p <-> (i, j), i > j)
+//  center     xc_a = x_a - mean_b x_b   (the kernel only sees differences x_a - x_b,
+//             so centring is exact and keeps the low-precision contractions small)
+//  dist_tab   r_ab = |x_a - x_b|, S_ab = (c^2/3) e^{-c r_ab}, A_ab = S_ab (1 + c r_ab)
+//  kdiag      diag(K)_{a,(i,q)} = (c^2/3) sum_{p owns i} g_{a,p,q}^2   (K_aa = (c^2/3) J_a^T J_a)
+//  proj       w_a = J_a v_a:  w_{a,p} = -g_{a,p} . (v_{a,i} - v_{a,j});  t_a = xc_a . w_a
+//  beta       beta_ab = c^2 S_ab (T_ab - t_b), T = Xc W^T; rowsum_a = sum_b beta_ab
+//  backproj   (K v)_a = J_a^T u'_a with u'_a = U_a - rowsum_a xc_a, plus lambda v
+//  kcol       columns K[:, c] = J_a^T H_ab J_b e_l for a list of column indices c = b*3N + l
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gdml {
+
+// p = i(i-1)/2 + j with i > j  ->  (i, j)
+__device__ __forceinline__ void pair_of(int p, int& i, int& j) {
+  int ii = (int)((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+  while (ii * (ii - 1) / 2 > p) --ii;
+  while ((ii + 1) * ii / 2 <= p) ++ii;
+  i = ii;
+  j = p - ii * (ii - 1) / 2;
+}
+__device__ __forceinline__ int pair_idx(int i, int j) {  // requires i != j
+  return i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i;
+}
+
+__global__ void desc_jac_kernel(const double* __restrict__ R, int64_t M, int N, int D,
+                                double* __restrict__ X, double* __restrict__ G) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= M * D) return;
+  int64_t a = t / D;
+  int p = (int)(t - a * D);
+  int i, j;
+  pair_of(p, i, j);
+  const double* Ra = R + a * N * 3;
+  double dx = Ra[3 * i] - Ra[3 * j], dy = Ra[3 * i + 1] - Ra[3 * j + 1], dz = Ra[3 * i + 2] - Ra[3 * j + 2];
+  double r2 = dx * dx + dy * dy + dz * dz;
+  double r = sqrt(r2);
+  double inv_r = 1.0 / r;
+  double inv_r3 = inv_r / r2;
+  X[t] = inv_r;
+  G[3 * t] = dx * inv_r3;
+  G[3 * t + 1] = dy * inv_r3;
+  G[3 * t + 2] = dz * inv_r3;
+}
+
+// column means of X in a fixed order, then Xc = X - mean
+__global__ void center_kernel(const double* __restrict__ X, int64_t M, int D, double* __restrict__ Xc) {
+  __shared__ double part[8][33];
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int row0 = threadIdx.x >> 5;  // 0..7
+  double s = 0.0;
+  if (col < D)
+    for (int64_t a = row0; a < M; a += 8) s += X[a * D + col];
+  part[row0][threadIdx.x & 31] = s;
+  __syncthreads();
+  double mean = 0.0;
+  for (int r = 0; r < 8; ++r) mean += part[r][threadIdx.x & 31];
+  mean /= (double)M;
+  if (col < D)
+    for (int64_t a = row0; a < M; a += 8) Xc[a * D + col] = X[a * D + col] - mean;
+}
+
+// r_ab straight from differences (no Gram-matrix cancellation); S and A tables.
+// 32x32 output tile per CTA, 256 threads, 4 outputs per thread.
+__global__ void dist_tab_kernel(const double* __restrict__ X, int64_t M, int D, double c,
+                                double* __restrict__ S, double* __restrict__ A, int64_t ldA) {
+  __shared__ double xa[32][33], xb[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty 0..7
+  const int64_t a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
+  double acc[4] = {0, 0, 0, 0};
+  for (int p0 = 0; p0 < D; p0 += 32) {
+    for (int rr = ty; rr < 32; rr += 8) {
+      int64_t ra = a0 + rr, rb = b0 + rr;
+      int p = p0 + tx;
+      xa[rr][tx] = (ra < M && p < D) ? X[ra * D + p] : 0.0;
+      xb[rr][tx] = (rb < M && p < D) ? X[rb * D + p] : 0.0;
+    }
+    __syncthreads();
+    for (int q = 0; q < 32; ++q) {
+      double vb = xb[tx][q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        double d = xa[ty + 8 * u][q] - vb;
+        acc[u] = fma(d, d, acc[u]);
+      }
+    }
+    __syncthreads();
+  }
+  const double c2_3 = c * c / 3.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t a = a0 + ty + 8 * u, b = b0 + tx;
+    if (a < M && b < M) {
+      double r = (a == b) ? 0.0 : sqrt(acc[u]);
+      double s = c2_3 * exp(-c * r);
+      S[a * M + b] = s;
+      A[a * ldA + b] = s * (1.0 + c * r);
+    }
+  }
+}
+
+__global__ void kdiag_kernel(const double* __restrict__ G, int64_t M, int N, int D, double c2_3,
+                             double* __restrict__ diag) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int B = 3 * N;
+  if (t >= M * B) return;
+  int64_t a = t / B;
+  int l = (int)(t - a * B), i = l / 3, q = l - 3 * (l / 3);
+  const double* Ga = G + a * D * 3;
+  double s = 0.0;
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    double g = Ga[3 * pair_idx(i, j) + q];
+    s = fma(g, g, s);
+  }
+  diag[t] = c2_3 * s;
+}
+
+// one CTA per geometry; W row a written into W (ld = ldW); t_a = xc_a . w_a
+template <int THREADS>
+__global__ void proj_kernel(const double* __restrict__ G, const double* __restrict__ Xc,
+                            const double* __restrict__ v, int N, int D, double* __restrict__ W,
+                            int64_t ldW, double* __restrict__ t) {
+  extern __shared__ double sh_v[];  // 3N
+  __shared__ double red[THREADS / 32];
+  const int64_t a = blockIdx.x;
+  const int B = 3 * N;
+  for (int l = threadIdx.x; l < B; l += THREADS) sh_v[l] = v[a * B + l];
+  __syncthreads();
+  const double* Ga = G + a * D * 3;
+  double part = 0.0;
+  for (int p = threadIdx.x; p < D; p += THREADS) {
+    int i, j;
+    pair_of(p, i, j);
+    double w = -(Ga[3 * p] * (sh_v[3 * i] - sh_v[3 * j]) + Ga[3 * p + 1] * (sh_v[3 * i + 1] - sh_v[3 * j + 1]) +
+                 Ga[3 * p + 2] * (sh_v[3 * i + 2] - sh_v[3 * j + 2]));
+    W[a * ldW + p] = w;
+    part = fma(Xc[a * D + p], w, part);
+  }
+  double s = block_sum<THREADS>(part, red);
+  if (threadIdx.x == 0) t[a] = s;
+}
+
+// beta_ab = c^2 S_ab (T_ab - t_b) into Pb[a*ldP + b]; rowsum_a = sum_b beta_ab
+template <int THREADS>
+__global__ void beta_kernel(const double* __restrict__ T, const double* __restrict__ S,
+                            const double* __restrict__ t, int64_t M, double c2,
+                            double* __restrict__ Pb, int64_t ldP, double* __restrict__ rowsum) {
+  __shared__ double red[THREADS / 32];
+  const int64_t a = blockIdx.x;
+  double part = 0.0;
+  for (int64_t b = threadIdx.x; b < M; b += THREADS) {
+    double beta = c2 * S[a * M + b] * (T[a * M + b] - t[b]);
+    Pb[a * ldP + b] = beta;
+    part += beta;
+  }
+  double s = block_sum<THREADS>(part, red);
+  if (threadIdx.x == 0) rowsum[a] = s;
+}
+
+// (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a). One CTA per geometry.
+template <typename TU>
+__global__ void backproj_kernel(const TU* __restrict__ U, int64_t ldU, const double* __restrict__ rowsum,
+                                const double* __restrict__ Xc, const double* __restrict__ G,
+                                const double* __restrict__ v, int N, int D, double lam, int add_lambda,
+                                double* __restrict__ out) {
+  extern __shared__ double sh_u[];  // D
+  const int64_t a = blockIdx.x;
+  const double rs = rowsum[a];
+  for (int p = threadIdx.x; p < D; p += blockDim.x)
+    sh_u[p] = (double)U[a * ldU + p] - rs * Xc[a * D + p];
+  __syncthreads();
+  const int B = 3 * N;
+  const double* Ga = G + a * D * 3;
+  for (int l = threadIdx.x; l < B; l += blockDim.x) {
+    int i = l / 3, q = l - 3 * i;
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      int p = pair_idx(i, j);
+      double gj = Ga[3 * p + q] * sh_u[p];
+      s += (i > j) ? -gj : gj;  // dx_p/dR_i = -g_p if i is the first atom of p, else +g_p
+    }
+    if (add_lambda) s = fma(lam, v[a * B + l], s);
+    out[a * B + l] = s;
+  }
+}
+
+// Columns of K: out[c*n + a*3N + l'] = (J_a^T H_ab J_b e_l)_{l'} for cols[c] = b*3N + l.
+// grid (M, ceil(ncols/colsPerCta)); CTA handles target geometry a for several columns.
+__global__ void kcol_kernel(const int64_t* __restrict__ cols, int64_t ncols, int colsPerCta,
+                            const double* __restrict__ X, const double* __restrict__ G,
+                            const double* __restrict__ S, const double* __restrict__ A, int64_t ldA,
+                            int64_t M, int N, int D, double c2, double* __restrict__ out, int64_t ldo,
+                            const int* __restrict__ stop_flag) {
+  if (stop_flag && *stop_flag) return;
+  extern __shared__ double sh[];
+  double* delta = sh;       // D
+  double* u = sh + D;       // D
+  double* wsp = sh + 2 * D; // N (w on the pairs (i, j), indexed by partner j)
+  __shared__ double s_dot;
+  const int64_t a = blockIdx.x;
+  const int B = 3 * N;
+  const double* Xa = X + a * D;
+  const double* Ga = G + a * D * 3;
+  int64_t c_begin = (int64_t)blockIdx.y * colsPerCta;
+  int64_t c_end = c_begin + colsPerCta < ncols ? c_begin + colsPerCta : ncols;
+  int64_t last_b = -1;
+  for (int64_t c = c_begin; c < c_end; ++c) {
+    const int64_t col = cols[c];
+    const int64_t b = col / B;
+    const int l = (int)(col - b * B), i = l / 3, q = l - 3 * i;
+    const double* Xb = X + b * D;
+    const double* Gb = G + b * D * 3;
+    __syncthreads();
+    if (b != last_b) {
+      for (int p = threadIdx.x; p < D; p += blockDim.x) delta[p] = Xa[p] - Xb[p];
+      last_b = b;
+    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      double w = 0.0;
+      if (j != i) {
+        int p = pair_idx(i, j);
+        w = (i > j) ? -Gb[3 * p + q] : Gb[3 * p + q];  // (J_b e_l)_p
+      }
+      wsp[j] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int j = 0; j < N; ++j)
+        if (j != i) s = fma(delta[pair_idx(i, j)], wsp[j], s);
+      s_dot = s;
+    }
+    __syncthreads();
+    const double Sab = S[a * M + b], Aab = A[a * ldA + b];
+    const double coef = -c2 * Sab * s_dot;
+    for (int p = threadIdx.x; p < D; p += blockDim.x) u[p] = coef * delta[p];
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
+      if (j != i) u[pair_idx(i, j)] += Aab * wsp[j];
+    __syncthreads();
+    for (int l2 = threadIdx.x; l2 < B; l2 += blockDim.x) {
+      int i2 = l2 / 3, q2 = l2 - 3 * i2;
+      double s = 0.0;
+      for (int j = 0; j < N; ++j) {
+        if (j == i2) continue;
+        int p = pair_idx(i2, j);
+        double gj = Ga[3 * p + q2] * u[p];
+        s += (i2 > j) ? -gj : gj;
+      }
+      out[c * ldo + a * B + l2] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double* G, cudaStream_t st) {
+  int64_t tot = M * D;
+  desc_jac_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(R, M, N, D, X, G);
+}
+void launch_center(const double* X, int64_t M, int D, double* Xc, cudaStream_t st) {
+  center_kernel<<<(unsigned)cdiv(D, 32), 256, 0, st>>>(X, M, D, Xc);
+}
+void launch_dist_tab(const double* X, int64_t M, int D, double c, double* S, double* A, int64_t ldA,
+                     cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(M, 32), (unsigned)cdiv(M, 32));
+  dist_tab_kernel<<<grid, 256, 0, st>>>(X, M, D, c, S, A, ldA);
+}
+void launch_kdiag(const double* G, int64_t M, int N, int D, double c, double* diag, cudaStream_t st) {
+  int64_t tot = M * 3 * N;
+  kdiag_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(G, M, N, D, c * c / 3.0, diag);
+}
+void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, int N, int D, double* W,
+                 int64_t ldW, double* t, cudaStream_t st) {
+  proj_kernel<256><<<(unsigned)M, 256, 3 * N * sizeof(double), st>>>(G, Xc, v, N, D, W, ldW, t);
+}
+void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
+                 int64_t ldP, double* rowsum, cudaStream_t st) {
+  beta_kernel<256><<<(unsigned)M, 256, 0, st>>>(T, S, t, M, c * c, Pb, ldP, rowsum);
+}
+template <typename TU>
+void launch_backproj(const TU* U, int64_t ldU, const double* rowsum, const double* Xc, const double* G,
+                     const double* v, int64_t M, int N, int D, double lam, int add_lambda, double* out,
+                     cudaStream_t st) {
+  const size_t smem = D * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(backproj_kernel<TU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  backproj_kernel<TU><<<(unsigned)M, 128, smem, st>>>(U, ldU, rowsum, Xc, G, v, N, D, lam,
+                                                                     add_lambda, out);
+}
+template void launch_backproj<double>(const double*, int64_t, const double*, const double*, const double*,
+                                      const double*, int64_t, int, int, double, int, double*, cudaStream_t);
+template void launch_backproj<float>(const float*, int64_t, const double*, const double*, const double*,
+                                     const double*, int64_t, int, int, double, int, double*, cudaStream_t);
+
+void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* S,
+                 const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
+                 const int* stop_flag, cudaStream_t st) {
+  const int per = 8;
+  dim3 grid((unsigned)M, (unsigned)cdiv(ncols, per));
+  size_t smem = (2 * (size_t)D + N) * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kcol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kcol_kernel<<<grid, 128, smem, st>>>(cols, ncols, per, X, G, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag);
+}
+
+}  // namespace gdml

@@ -1,0 +1,95 @@
+// Internal launcher declarations shared by the libgdml translation units.
+#pragma once
+
+#include <functional>
+
+#include "common.cuh"
+
+namespace gdml {
+
+// scalar slots of the PCG state (device array of doubles)
+enum { SC_RHO = 0, SC_PQ = 1, SC_RR = 2, SC_RHO_NEW = 3, SC_YY = 4, SC_COUNT = 8 };
+
+// geom.cu
+void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double* G, cudaStream_t st);
+void launch_center(const double* X, int64_t M, int D, double* Xc, cudaStream_t st);
+void launch_dist_tab(const double* X, int64_t M, int D, double c, double* S, double* A, int64_t ldA,
+                     cudaStream_t st);
+void launch_kdiag(const double* G, int64_t M, int N, int D, double c, double* diag, cudaStream_t st);
+void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, int N, int D, double* W,
+                 int64_t ldW, double* t, cudaStream_t st);
+void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
+                 int64_t ldP, double* rowsum, cudaStream_t st);
+template <typename TU>
+void launch_backproj(const TU* U, int64_t ldU, const double* rowsum, const double* Xc, const double* G,
+                     const double* v, int64_t M, int N, int D, double lam, int add_lambda, double* out,
+                     cudaStream_t st);
+void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* S,
+                 const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
+                 const int* stop_flag, cudaStream_t st);
+
+// dgemm.cu
+template <typename TA, typename TB>
+void launch_dgemm(bool nt, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t lda,
+                  const TB* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
+                  cudaStream_t st);
+
+// linalg.cu
+void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st);
+void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st);
+void trsv_lower(const double* L, int64_t k, double* x, bool transpose, cudaStream_t st);
+void add_diag(double* A, int64_t lda, int64_t k, double eps, cudaStream_t st);
+
+// woodbury.cu
+template <typename TL>
+void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* LC, double lam, const double* r,
+                    double* z, double* part, double* t, cudaStream_t st);
+int64_t woodbury_part_size(int64_t n, int64_t k);
+
+// cg.cu
+void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,
+                cudaStream_t st);
+void launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const double* sc,
+                      int* status, cudaStream_t st);
+void launch_update_p(double* p, const double* z, int64_t n, const double* sc, cudaStream_t st);
+void launch_copy_scalar(double* sc, int dst, int src, cudaStream_t st);
+void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
+
+// select.cu
+int64_t select_scratch_len(int64_t n);
+void select_uniform(int64_t n, int64_t k, uint64_t seed, uint32_t stream, uint64_t* key, int64_t* idx,
+                    int64_t* out, cudaStream_t st);
+void select_weighted(int64_t n, int64_t k, uint64_t seed, uint32_t stream, const double* tau, uint64_t* key,
+                     int64_t* idx, int64_t* out, cudaStream_t st);
+
+// pivchol.cu
+struct PivState {
+  double lmm;
+  int64_t piv;
+  int64_t rank;
+  int stop;
+  int pad;
+};
+struct ArgMaxPart {
+  double v;
+  int64_t pos;
+  double sum;
+};
+struct PivCholArgs {
+  int64_t n, k;
+  double* d;
+  int64_t* perm;
+  unsigned char* chosen;
+  int64_t* pivots;
+  double* trace;
+  PivState* ps;
+  ArgMaxPart* part;
+  unsigned* ticket;
+  double* col;
+  std::function<void(const int64_t*, double*, const int*, cudaStream_t)> get_col;
+};
+template <typename TL>
+void pivchol_run(const PivCholArgs& a, TL* L, cudaStream_t st);
+int pivchol_part_blocks();
+
+}  // namespace gdml

@@ -1,0 +1,51 @@
+// Tensor-core (tcgen05) form of the force-kernel matvec for TF32 / BF16 contexts.
+//
+// The two descriptor contractions of K v run as tcgen05 GEMMs with FP32
+// accumulation (operands rounded to TF32 or BF16):
+//   GEMM 1:  T = Xc W^T                      (M x M, K = D)   epilogue: beta_ab = c^2 S_ab (T_ab - t_b)
+//   GEMM 2:  U = [A | beta] [W ; Xc]         (M x D, K = 2M)
+// with Xc the centred descriptors, W = J v, t_b = xc_b . w_b, A_ab = S_ab (1 + c r_ab);
+// projection and back-projection (J_a^T (U_a - rowsum_a xc_a)) stay in FP64.
+#pragma once
+#include <cuda.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace gdml {
+
+struct TcMatvec {
+  int precision = 0;  // GDML_TF32 or GDML_BF16
+  bool ready = false;
+  int64_t M = 0;
+  int N = 0, D = 0, Dp = 0;  // Dp: D padded to one 128-byte swizzle span
+  int64_t K2p = 0;           // 2M padded likewise
+  double c = 0;
+  void* Xc_lp = nullptr;  // M x Dp
+  void* W_lp = nullptr;   // M x Dp
+  void* P_lp = nullptr;   // M x K2p : [A | beta]
+  void* Vt_lp = nullptr;  // Dp x K2p : [W^T | Xc^T]
+  float* S32 = nullptr;   // M x M
+  float* U = nullptr;     // splits x M x Dp
+  double* rs_part = nullptr;  // rowsum partials: ceil(M/32) x M
+  double* tb = nullptr;       // t_b = xc~_b . w~_b
+  int* err = nullptr;
+  int bn2 = 256, splits2 = 1;
+  std::vector<void*> allocs;
+  CUtensorMap mapXc, mapW, mapP, mapVt;
+};
+
+gdml_status tc_setup(TcMatvec& tc, int precision, int64_t M, int N, int D, const double* Xc, const double* A,
+                     int64_t ldA, const double* S, double c, cudaStream_t st);
+gdml_status tc_matvec(TcMatvec& tc, const double* G, const double* v, double* out, int add_lambda, double lam,
+                      cudaStream_t st);
+// reads (and clears) the device error word of the tensor-core kernels; synchronises st
+gdml_status tc_check(TcMatvec& tc, cudaStream_t st);
+void tc_destroy(TcMatvec& tc);
+
+// test hook: C (M x N, fp64) = A (M x K) B (N x K)^T with operands rounded to TF32 / BF16
+gdml_status tc_gemm_test(int bf16, const double* A, const double* B, int M, int N, int K, double* C,
+                         cudaStream_t st);
+
+}  // namespace gdml
