@@ -25,6 +25,11 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
  * wait gave up since the last check.  FP64 contexts: always GDML_OK. */
 gdml_status gdml_tc_check(gdml_ctx* ctx);
 
+/* Kernel launches this library has executed since it was loaded (all
+ * contexts and threads; a kernel inside a CUDA graph counts once per replay).
+ * Host-side counter, never fails. */
+int64_t gdml_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // C ABI of libgdml (declared in include/gdml.h): context, matvec,
 // preconditioner build / apply and the PCG solve.  Every step runs in the
 // kernels of this library; the host only sequences launches.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -15,6 +16,9 @@
 namespace gdml {
 
 static thread_local std::string g_msg;
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 gdml_status fail(gdml_status st, const std::string& msg) {
   g_msg = msg;
   return st;
@@ -48,7 +52,8 @@ struct gdml_ctx {
   double* T = nullptr;    // M*M
   double* tb = nullptr;   // M
   double* rowsum = nullptr;
-  double* U = nullptr;  // M*D
+  double* U = nullptr;  // splitsU x M x D (split-K partials of the second contraction)
+  int splitsU = 1;
   double* diag = nullptr;  // n
   double* Xc() const { return V64 + M * D; }
   TcMatvec tc;  // tensor-core matvec state (TF32/BF16 contexts)
@@ -69,6 +74,12 @@ struct gdml_ctx {
   unsigned* ticket = nullptr;
   int* status = nullptr;      // device status word
   double* hsc = nullptr;      // pinned host mirror of scalars
+  int64_t* ictl = nullptr;    // device loop control (IC_*)
+  int64_t* hictl = nullptr;   // pinned host mirror
+  TrsvState ts;               // multi-CTA triangular solve state
+  cudaStream_t cap = nullptr;             // private stream used only to capture graphs
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // PCG loop graphs: [0] context precision, [1] FP64
+  int64_t gbody[2] = {0, 0};                       // kernels per captured iteration
 };
 
 namespace {
@@ -129,8 +140,10 @@ gdml_status matvec_fp64(gdml_ctx* c, const double* v, double* out, int add_lambd
   launch_dgemm<double, double>(true, M, M, D, 1.0, c->Xc(), D, W, D, 0.0, c->T, M, false, st);
   launch_beta(c->T, c->S, c->tb, M, c->c, c->P64 + M, 2 * M, c->rowsum, st);
   // U = [A | beta] [W ; Xc]
-  launch_dgemm<double, double>(false, M, D, 2 * M, 1.0, c->P64, 2 * M, c->V64, D, 0.0, c->U, D, false, st);
-  launch_backproj<double>(c->U, D, c->rowsum, c->Xc(), c->G, v, M, c->N, D, c->lam, add_lambda, out, st);
+  launch_dgemm<double, double>(false, M, D, 2 * M, 1.0, c->P64, 2 * M, c->V64, D, 0.0, c->U, D, false, st,
+                               c->splitsU, M * D);
+  launch_backproj<double>(c->U, D, c->splitsU, M * D, c->rowsum, c->Xc(), c->G, v, M, c->N, D, c->lam, add_lambda,
+                          out, st);
   return check_launch(c, "matvec_fp64");
 }
 
@@ -209,7 +222,7 @@ gdml_status chol_jitter(gdml_ctx* c, const double* src, double* work, int64_t k,
 gdml_status nystrom(gdml_ctx* c, const int64_t* S, int64_t k, double* L, double* Kkk, double* work,
                     double* eps_out) {
   TRY(get_cols(c, S, k, L));
-  gather_kkk_kernel<<<(unsigned)cdiv(k * k, 256), 256, 0, c->st>>>(L, c->n, S, k, Kkk);
+  { gather_kkk_kernel<<<(unsigned)cdiv(k * k, 256), 256, 0, c->st>>>(L, c->n, S, k, Kkk); count_launch(); }
   TRY(check_launch(c, "gather_kkk"));
   TRY(chol_jitter(c, Kkk, work, k, eps_out));
   trsm_left_lower(work, k, L, c->n, c->st);  // rows of K_nk^T -> rows of L_k^T
@@ -241,6 +254,9 @@ gdml_status ensure_precond_buffers(gdml_ctx* c, int64_t k) {
   TRY(dalloc(c, &c->LC, (size_t)(k * k)));
   TRY(dalloc(c, &c->wpart, (size_t)woodbury_part_size(c->n, k)));
   TRY(dalloc(c, &c->wt, (size_t)k));
+  dfree(c, c->ts.sync);
+  c->ts.sync = nullptr;
+  TRY(dalloc(c, &c->ts.sync, (size_t)trsv_sync_len(k)));
   c->cap_k = k;
   return GDML_OK;
 }
@@ -265,7 +281,7 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
     CTRY(c, cudaMemcpyAsync(z, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GDML_OK;
   }
-  woodbury_apply<double>(c->L, c->n, c->k, c->LC, c->lam, r, z, c->wpart, c->wt, c->st);
+  woodbury_apply<double>(c->L, c->n, c->k, c->LC, c->lam, r, z, c->wpart, c->wt, c->ts, c->st);
   return check_launch(c, "woodbury_apply");
 }
 
@@ -280,73 +296,138 @@ gdml_status fetch_scalars(gdml_ctx* c) {
   return GDML_OK;
 }
 
-// PCG on K_lambda x = b (x updated in place).  Stops when the recurrence
-// residual |r| <= tol_abs; with check_true, the true residual is recomputed
-// (FP64 or the context precision as given) and CG restarts if it drifted.
-// Returns iterations used through *iters; *res_out = final |r| (true if check_true).
+void drop_graphs(gdml_ctx* c) {
+  for (auto& g : c->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// Body of one PCG iteration, launched on c->st (captured into the WHILE node):
+//   q = K_lam p; pq = p.q; x += g p, r -= g q; rr = r.r; check; z = P^-1 r;
+//   rho' = r.z; p = z + (rho'/rho) p; rho = rho'.
+gdml_status pcg_body(gdml_ctx* c, double* x, bool fp64_mv, cudaGraphConditionalHandle h) {
+  const int64_t n = c->n;
+  TRY(matvec_any(c, c->p, c->q, 1, fp64_mv));
+  TRY(dot(c, c->p, c->q, SC_PQ));
+  launch_update_xr(x, c->r, c->p, c->q, n, c->sc, c->status, c->st);
+  TRY(dot(c, c->r, c->r, SC_RR));
+  launch_pcg_check(c->sc, c->ictl, c->status, h, c->st);
+  TRY(apply_precond(c, c->r, c->z));
+  TRY(dot(c, c->r, c->z, SC_RHO_NEW));
+  launch_update_p(c->p, c->z, n, c->sc, c->st);
+  launch_copy_scalar(c->sc, SC_RHO, SC_RHO_NEW, c->st);
+  return check_launch(c, "pcg body");
+}
+
+// Capture the PCG loop once as a graph with a conditional WHILE node whose
+// body is one iteration; the check kernel ends the loop on the device.
+gdml_status pcg_graph(gdml_ctx* c, double* x, bool fp64_mv, cudaGraphExec_t* out) {
+  const int slot = fp64_mv && c->precision != GDML_FP64 ? 1 : 0;
+  if (c->gexec[slot]) {
+    *out = c->gexec[slot];
+    return GDML_OK;
+  }
+  if (!c->cap) CTRY(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CTRY(c, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &prm);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(c->cap, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return ctx_fail(c, GDML_ERR_CUDA, std::string("building the PCG graph: ") + cudaGetErrorString(e));
+  }
+  cudaStream_t user = c->st;
+  c->st = c->cap;
+  const int64_t before = launch_count();
+  gdml_status bs = pcg_body(c, x, fp64_mv, h);
+  const int64_t body_n = launch_count() - before;
+  count_launch(-body_n);  // captured, not executed
+  c->gbody[slot] = body_n;
+  c->st = user;
+  cudaGraph_t body = nullptr;
+  e = cudaStreamEndCapture(c->cap, &body);
+  if (bs != GDML_OK || e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    return bs != GDML_OK ? bs : ctx_fail(c, GDML_ERR_CUDA, std::string("capturing the PCG body: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return ctx_fail(c, GDML_ERR_CUDA, std::string("instantiating the PCG graph: ") + cudaGetErrorString(e));
+  c->gexec[slot] = ex;
+  *out = ex;
+  return GDML_OK;
+}
+
+// PCG on K_lambda x = b (x updated in place; the graph is bound to this x).
+// Stops when the recurrence residual |r| <= tol_abs; with check_true, the
+// true residual is recomputed in FP64 and CG restarts from x if it drifted.
+// *iters = iterations used; *res_out = final |r| (the true one if check_true).
 gdml_status pcg_core(gdml_ctx* c, const double* b, double* x, double tol_abs, int64_t max_iter, bool fp64_mv,
                      bool check_true, int max_restarts, int64_t* iters, double* res_out) {
   const int64_t n = c->n;
   cudaStream_t st = c->st;
   int64_t it = 0;
   int restarts = 0;
-  // r = b - K x
-  TRY(matvec_any(c, x, c->r, 1, fp64_mv));
+  *iters = 0;
+  TRY(matvec_any(c, x, c->r, 1, fp64_mv));  // r = b - K x
   launch_axpby(c->r, b, 1.0, -1.0, n, st);
-  double res = 0.0;
-  for (;;) {
-    TRY(dot(c, c->r, c->r, SC_RR));
-    TRY(fetch_scalars(c));
-    res = std::sqrt(c->hsc[SC_RR]);
-    if (res <= tol_abs) break;
+  TRY(dot(c, c->r, c->r, SC_RR));
+  TRY(fetch_scalars(c));
+  double res = std::sqrt(c->hsc[SC_RR]);
+  gdml_status out = GDML_OK;
+  while (res > tol_abs && it < max_iter) {
     TRY(apply_precond(c, c->r, c->z));
     CTRY(c, cudaMemcpyAsync(c->p, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TRY(dot(c, c->r, c->z, SC_RHO));
-    bool conv = false;
-    while (it < max_iter) {
-      TRY(matvec_any(c, c->p, c->q, 1, fp64_mv));
-      TRY(dot(c, c->p, c->q, SC_PQ));
-      CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), st));
-      launch_update_xr(x, c->r, c->p, c->q, n, c->sc, c->status, st);
-      TRY(dot(c, c->r, c->r, SC_RR));
-      ++it;
-      TRY(fetch_scalars(c));
-      int hst = 0;
-      TRY(read_status(c, &hst));
-      if (hst) {
-        *iters = it;
-        *res_out = res;
-        return ctx_fail(c, GDML_ERR_BREAKDOWN, "PCG breakdown: p^T K p <= 0 or not finite");
-      }
-      res = std::sqrt(c->hsc[SC_RR]);
-      if (!std::isfinite(res)) {
-        *iters = it;
-        *res_out = res;
-        return ctx_fail(c, GDML_ERR_BREAKDOWN, "PCG residual not finite");
-      }
-      if (res <= tol_abs) {
-        conv = true;
-        break;
-      }
-      TRY(apply_precond(c, c->r, c->z));
-      TRY(dot(c, c->r, c->z, SC_RHO_NEW));
-      launch_update_p(c->p, c->z, n, c->sc, st);
-      launch_copy_scalar(c->sc, SC_RHO, SC_RHO_NEW, st);
-      TRY(check_launch(c, "pcg iteration"));
+    c->hictl[IC_ITER] = 0;
+    c->hictl[IC_MAXIT] = max_iter - it;
+    c->hsc[SC_TOL2] = tol_abs * tol_abs;
+    CTRY(c, cudaMemcpyAsync(c->ictl, c->hictl, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CTRY(c, cudaMemcpyAsync(c->sc + SC_TOL2, c->hsc + SC_TOL2, sizeof(double), cudaMemcpyHostToDevice, st));
+    CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), st));
+    cudaGraphExec_t ex = nullptr;
+    TRY(pcg_graph(c, x, fp64_mv, &ex));
+    CTRY(c, cudaGraphLaunch(ex, st));
+    CTRY(c, cudaMemcpyAsync(c->hictl, c->ictl, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    int hst = 0;
+    CTRY(c, cudaMemcpyAsync(&hst, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(fetch_scalars(c));  // synchronises
+    it += c->hictl[IC_ITER];
+    count_launch(c->hictl[IC_ITER] * c->gbody[fp64_mv && c->precision != GDML_FP64 ? 1 : 0]);
+    res = std::sqrt(c->hsc[SC_RR]);
+    if (hst || !std::isfinite(res)) {
+      // an inner solve of the refinement stops at the last good iterate (its
+      // operator is only approximately SPD); a plain FP64 solve reports it
+      if (!check_true && std::isfinite(res)) break;
+      out = ctx_fail(c, GDML_ERR_BREAKDOWN, "PCG breakdown: p^T K p <= 0 or a non-finite residual");
+      break;
     }
     if (!check_true) break;
-    // true residual
-    TRY(matvec_any(c, x, c->r, 1, true));
+    TRY(matvec_any(c, x, c->r, 1, true));  // true residual in FP64
     launch_axpby(c->r, b, 1.0, -1.0, n, st);
     TRY(dot(c, c->r, c->r, SC_RR));
     TRY(fetch_scalars(c));
     res = std::sqrt(c->hsc[SC_RR]);
-    if (res <= tol_abs || it >= max_iter || restarts >= max_restarts || !conv) break;
+    if (res <= tol_abs || restarts >= max_restarts) break;
     ++restarts;
   }
   *iters = it;
   *res_out = res;
-  return GDML_OK;
+  return out;
 }
 
 gdml_status validate(const gdml_ctx* c) {
@@ -393,14 +474,19 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   TRY(dalloc(C, &c->T, (size_t)(M * M)));
   TRY(dalloc(C, &c->tb, (size_t)M));
   TRY(dalloc(C, &c->rowsum, (size_t)M));
-  TRY(dalloc(C, &c->U, (size_t)(M * D)));
+  c->splitsU = dgemm_splits(M, D, 2 * M);
+  TRY(dalloc(C, &c->U, (size_t)(c->splitsU * M * D)));
   TRY(dalloc(C, &c->diag, (size_t)n));
   for (double** v : {&c->r, &c->z, &c->p, &c->q, &c->x, &c->ys}) TRY(dalloc(C, v, (size_t)n));
   TRY(dalloc(C, &c->sc, SC_COUNT));
   TRY(dalloc(C, &c->partial, 4096));
   TRY(dalloc(C, &c->ticket, 1));
   TRY(dalloc(C, &c->status, 1));
+  TRY(dalloc(C, &c->ictl, IC_COUNT));
+  TRY(dalloc(C, &c->ts.err, 1));
   CTRY(C, cudaMallocHost(&c->hsc, SC_COUNT * sizeof(double)));
+  CTRY(C, cudaMallocHost(&c->hictl, IC_COUNT * sizeof(int64_t)));
+  CTRY(C, cudaMemsetAsync(c->ts.err, 0, sizeof(int), c->st));
   CTRY(C, cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), c->st));
   CTRY(C, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
   CTRY(C, cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), c->st));
@@ -439,6 +525,7 @@ gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t 
   if (method < GDML_SEL_UNIFORM || method > GDML_SEL_PIVCHOL) return ctx_fail(c, GDML_ERR_ARG, "unknown method");
   c->k = 0;
   c->jitter = 0.0;
+  drop_graphs(c);
   TRY(ensure_precond_buffers(c, k));
   Scratch s{c, {}};
   int64_t* S = nullptr;
@@ -512,7 +599,7 @@ gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t 
       trsm_left_lower(c->LC, k, c->L, n, c->st);       // Z = L_C^-1 B^T
       double* tau = nullptr;
       TRY(s.get(&tau, (size_t)n));
-      col_sqnorm_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c->st>>>(c->L, k, n, tau);
+      { col_sqnorm_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c->st>>>(c->L, k, n, tau); count_launch(); }
       TRY(check_launch(c, "rls scores"));
       select_weighted(n, k, seed, 2u, tau, key, idx, S, c->st);
     } else {
@@ -576,7 +663,10 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
     CTRY(c, cudaMemsetAsync(alpha, 0, n * sizeof(double), st));
     c->last_outer = 0;
   } else if (c->precision == GDML_FP64) {
-    stat = pcg_core(c, c->ys, alpha, rtol * ynorm, max_iter, true, true, 3, &iters, &res);
+    // the captured loop is bound to the context's own x buffer
+    CTRY(c, cudaMemcpyAsync(c->x, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    stat = pcg_core(c, c->ys, c->x, rtol * ynorm, max_iter, true, true, 3, &iters, &res);
+    CTRY(c, cudaMemcpyAsync(alpha, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     c->last_outer = 1;
   } else {
     // FP64 iterative refinement around the tensor-core PCG
@@ -587,12 +677,11 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
     // r = y - K alpha (FP64)
     TRY(matvec_any(c, alpha, rhs, 1, true));
     launch_axpby(rhs, c->ys, 1.0, -1.0, n, st);
-    int outer = 0;
-    for (;;) {
-      TRY(dot(c, rhs, rhs, SC_RR));
-      TRY(fetch_scalars(c));
-      res = std::sqrt(c->hsc[SC_RR]);
-      if (res <= rtol * ynorm || outer >= 20 || iters >= max_iter) break;
+    TRY(dot(c, rhs, rhs, SC_RR));
+    TRY(fetch_scalars(c));
+    res = std::sqrt(c->hsc[SC_RR]);
+    int outer = 0, stalls = 0;
+    while (res > rtol * ynorm && outer < 20 && iters < max_iter) {
       ++outer;
       CTRY(c, cudaMemsetAsync(dx, 0, n * sizeof(double), st));
       int64_t it_in = 0;
@@ -602,9 +691,20 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
       iters += it_in;
       if (stat != GDML_OK) break;
       launch_axpby(alpha, dx, 1.0, 1.0, n, st);
-      TRY(matvec_any(c, alpha, rhs, 1, true));
+      TRY(matvec_any(c, alpha, rhs, 1, true));  // FP64 residual y - K_lambda alpha
       launch_axpby(rhs, c->ys, 1.0, -1.0, n, st);
+      TRY(dot(c, rhs, rhs, SC_RR));
+      TRY(fetch_scalars(c));
+      const double rnew = std::sqrt(c->hsc[SC_RR]);
       TRY(check_launch(c, "refinement"));
+      if (!(rnew < res)) {  // the correction did not help: undo it and stop
+        launch_axpby(alpha, dx, -1.0, 1.0, n, st);
+        break;
+      }
+      // stagnation: the low-precision operator cannot resolve what is left
+      stalls = rnew > 0.5 * res ? stalls + 1 : 0;
+      res = rnew;
+      if (stalls >= 3) break;
     }
     c->last_outer = outer;
   }
@@ -628,6 +728,8 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
   return tc_gemm_test(bf16, A_dev, B_dev, M, N, K, C_dev, static_cast<cudaStream_t>(stream));
 }
 
+int64_t gdml_launch_count(void) { return launch_count(); }
+
 gdml_status gdml_tc_check(gdml_ctx* c) {
   TRY(validate(c));
   if (c->precision == GDML_FP64) return GDML_OK;
@@ -644,10 +746,13 @@ const char* gdml_last_error(const gdml_ctx* c) {
 void gdml_destroy(gdml_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
   tc_destroy(c->tc);
   for (void* p : c->allocs)
     if (p) cudaFree(p);
   if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->hictl) cudaFreeHost(c->hictl);
   delete c;
 }
 

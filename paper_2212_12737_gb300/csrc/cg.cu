@@ -74,23 +74,39 @@ __global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ 
     y[i] = fma(a, x[i], b * y[i]);
 }
 
+// End-of-iteration test inside the graph-captured PCG loop: counts the
+// iteration and keeps the WHILE node running while |r|^2 > tol^2, the
+// residual is finite, no breakdown was flagged and the cap is not reached.
+__global__ void pcg_check_kernel(const double* __restrict__ sc, int64_t* __restrict__ ictl,
+                                 const int* __restrict__ status, cudaGraphConditionalHandle h) {
+  const int64_t it = ictl[IC_ITER] + 1;
+  ictl[IC_ITER] = it;
+  const double rr = sc[SC_RR];
+  const bool go = (rr > sc[SC_TOL2]) && isfinite(rr) && (it < ictl[IC_MAXIT]) && (*status == 0);
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------- launchers
+void launch_pcg_check(const double* sc, int64_t* ictl, const int* status, cudaGraphConditionalHandle h,
+                      cudaStream_t st) {
+  { pcg_check_kernel<<<1, 1, 0, st>>>(sc, ictl, status, h); count_launch(); }
+}
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,
                 cudaStream_t st) {
-  dot_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(x, y, n, partial, ticket, out);
+  { dot_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(x, y, n, partial, ticket, out); count_launch(); }
 }
 void launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const double* sc,
                       int* status, cudaStream_t st) {
-  update_xr_kernel<<<4 * kNumSMs, 256, 0, st>>>(x, r, p, q, n, sc, status);
+  { update_xr_kernel<<<4 * kNumSMs, 256, 0, st>>>(x, r, p, q, n, sc, status); count_launch(); }
 }
 void launch_update_p(double* p, const double* z, int64_t n, const double* sc, cudaStream_t st) {
-  update_p_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc);
+  { update_p_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc); count_launch(); }
 }
 void launch_copy_scalar(double* sc, int dst, int src, cudaStream_t st) {
-  copy_scalar_kernel<<<1, 1, 0, st>>>(sc, dst, src);
+  { copy_scalar_kernel<<<1, 1, 0, st>>>(sc, dst, src); count_launch(); }
 }
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st) {
-  axpby_kernel<<<4 * kNumSMs, 256, 0, st>>>(y, x, a, b, n);
+  { axpby_kernel<<<4 * kNumSMs, 256, 0, st>>>(y, x, a, b, n); count_launch(); }
 }
 
 }  // namespace gdml

@@ -33,6 +33,11 @@ gdml_status fail(gdml_status st, const std::string& msg);
 const std::string& last_msg();
 void clear_msg();
 
+// host-side count of kernel launches issued by this library (inside CUDA
+// graphs a captured launch counts once per replay; see count_graph_launches)
+void count_launch(int64_t n = 1);
+int64_t launch_count();
+
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __device__ __forceinline__ int64_t cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -6,6 +6,8 @@
 //   A row-major (lda); Bop[k, n] = B[n*ldb + k] (NT) or B[k*ldb + n] (NN).
 //   Operands may be stored as float (products are then exact in FP64).
 //   lower_only: tiles strictly above the diagonal are skipped (SYRK-style).
+//   split-K: grid.z splits of kchunk each; split z writes its partial product to
+//   C + z * split_stride (beta must be 0), and the consumer sums them in order.
 //
 // 64x64 output tile per CTA, 256 threads x (4x4) outputs, K-steps of 16
 // staged through shared memory with a register prefetch of the next step.
@@ -18,12 +20,16 @@ template <typename TA, typename TB, bool NT>
 __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
                                                     const TA* __restrict__ A, int64_t lda,
                                                     const TB* __restrict__ B, int64_t ldb, double beta,
-                                                    double* __restrict__ C, int64_t ldc, int lower_only) {
+                                                    double* __restrict__ C, int64_t ldc, int lower_only,
+                                                    int64_t kchunk, int64_t split_stride) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
   if (lower_only && n0 > m0 + BM - 1) return;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  C += (int64_t)blockIdx.z * split_stride;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   double acc[4][4];
@@ -40,15 +46,15 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
       int e = tid + 256 * u;          // 0..1023
       int am = e >> 4, ak = e & 15;   // A tile: row am, col ak  (k fastest -> coalesced rows)
       int64_t gm = m0 + am, gk = k0 + ak;
-      ra[u] = (gm < M && gk < K) ? (double)A[gm * lda + gk] : 0.0;
+      ra[u] = (gm < M && gk < kend) ? (double)A[gm * lda + gk] : 0.0;
       if (NT) {
         int bn = e >> 4, bk = e & 15;
         int64_t gn = n0 + bn, gk2 = k0 + bk;
-        rb[u] = (gn < N && gk2 < K) ? (double)B[gn * ldb + gk2] : 0.0;
+        rb[u] = (gn < N && gk2 < kend) ? (double)B[gn * ldb + gk2] : 0.0;
       } else {
         int bk = e >> 6, bn = e & 63;  // n fastest -> coalesced
         int64_t gn = n0 + bn, gk2 = k0 + bk;
-        rb[u] = (gn < N && gk2 < K) ? (double)B[gk2 * ldb + gn] : 0.0;
+        rb[u] = (gn < N && gk2 < kend) ? (double)B[gk2 * ldb + gn] : 0.0;
       }
     }
   };
@@ -61,11 +67,11 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
       else Bs[e >> 6][e & 63] = rb[u];
     }
   };
-  load(0);
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  load(kbeg);
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     store();
     __syncthreads();
-    if (k0 + BK < K) load(k0 + BK);
+    if (k0 + BK < kend) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       double av[4], bv[4];
@@ -97,18 +103,33 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
 template <typename TA, typename TB>
 void launch_dgemm(bool nt, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t lda,
                   const TB* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
-                  cudaStream_t st) {
+                  cudaStream_t st, int splits, int64_t split_stride) {
   if (M <= 0 || N <= 0) return;
-  dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64));
+  if (splits < 1) splits = 1;
+  const int64_t kchunk = cdiv(cdiv(K, splits), 16) * 16;
+  dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64), (unsigned)splits);
   if (nt)
-    dgemm_kernel<TA, TB, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only);
+    { dgemm_kernel<TA, TB, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only,
+                                                      kchunk, split_stride); count_launch(); }
   else
-    dgemm_kernel<TA, TB, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only);
+    { dgemm_kernel<TA, TB, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only,
+                                                       kchunk, split_stride); count_launch(); }
+}
+
+// number of K splits that brings an M x N tile grid to ~2 waves of the SMs
+int dgemm_splits(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = cdiv(M, 64) * cdiv(N, 64);
+  int64_t s = (2 * kNumSMs) / (tiles > 0 ? tiles : 1);
+  const int64_t kmax = cdiv(K, 64);  // keep >= 64 of K per split
+  if (s > kmax) s = kmax;
+  return (int)(s < 1 ? 1 : s);
 }
 
 template void launch_dgemm<double, double>(bool, int64_t, int64_t, int64_t, double, const double*, int64_t,
-                                           const double*, int64_t, double, double*, int64_t, bool, cudaStream_t);
+                                           const double*, int64_t, double, double*, int64_t, bool, cudaStream_t,
+                                           int, int64_t);
 template void launch_dgemm<float, float>(bool, int64_t, int64_t, int64_t, double, const float*, int64_t,
-                                         const float*, int64_t, double, double*, int64_t, bool, cudaStream_t);
+                                         const float*, int64_t, double, double*, int64_t, bool, cudaStream_t, int,
+                                         int64_t);
 
 }  // namespace gdml

@@ -163,15 +163,19 @@ __global__ void beta_kernel(const double* __restrict__ T, const double* __restri
 
 // (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a). One CTA per geometry.
 template <typename TU>
-__global__ void backproj_kernel(const TU* __restrict__ U, int64_t ldU, const double* __restrict__ rowsum,
+__global__ void backproj_kernel(const TU* __restrict__ U, int64_t ldU, int splits, int64_t split_stride,
+                                const double* __restrict__ rowsum,
                                 const double* __restrict__ Xc, const double* __restrict__ G,
                                 const double* __restrict__ v, int N, int D, double lam, int add_lambda,
                                 double* __restrict__ out) {
   extern __shared__ double sh_u[];  // D
   const int64_t a = blockIdx.x;
   const double rs = rowsum[a];
-  for (int p = threadIdx.x; p < D; p += blockDim.x)
-    sh_u[p] = (double)U[a * ldU + p] - rs * Xc[a * D + p];
+  for (int p = threadIdx.x; p < D; p += blockDim.x) {
+    double u = 0.0;
+    for (int s = 0; s < splits; ++s) u += (double)U[s * split_stride + a * ldU + p];
+    sh_u[p] = u - rs * Xc[a * D + p];
+  }
   __syncthreads();
   const int B = 3 * N;
   const double* Ga = G + a * D * 3;
@@ -260,42 +264,44 @@ __global__ void kcol_kernel(const int64_t* __restrict__ cols, int64_t ncols, int
 // ---------------------------------------------------------------- launchers
 void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double* G, cudaStream_t st) {
   int64_t tot = M * D;
-  desc_jac_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(R, M, N, D, X, G);
+  { desc_jac_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(R, M, N, D, X, G); count_launch(); }
 }
 void launch_center(const double* X, int64_t M, int D, double* Xc, cudaStream_t st) {
-  center_kernel<<<(unsigned)cdiv(D, 32), 256, 0, st>>>(X, M, D, Xc);
+  { center_kernel<<<(unsigned)cdiv(D, 32), 256, 0, st>>>(X, M, D, Xc); count_launch(); }
 }
 void launch_dist_tab(const double* X, int64_t M, int D, double c, double* S, double* A, int64_t ldA,
                      cudaStream_t st) {
   dim3 grid((unsigned)cdiv(M, 32), (unsigned)cdiv(M, 32));
-  dist_tab_kernel<<<grid, 256, 0, st>>>(X, M, D, c, S, A, ldA);
+  { dist_tab_kernel<<<grid, 256, 0, st>>>(X, M, D, c, S, A, ldA); count_launch(); }
 }
 void launch_kdiag(const double* G, int64_t M, int N, int D, double c, double* diag, cudaStream_t st) {
   int64_t tot = M * 3 * N;
-  kdiag_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(G, M, N, D, c * c / 3.0, diag);
+  { kdiag_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(G, M, N, D, c * c / 3.0, diag); count_launch(); }
 }
 void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, int N, int D, double* W,
                  int64_t ldW, double* t, cudaStream_t st) {
-  proj_kernel<256><<<(unsigned)M, 256, 3 * N * sizeof(double), st>>>(G, Xc, v, N, D, W, ldW, t);
+  { proj_kernel<256><<<(unsigned)M, 256, 3 * N * sizeof(double), st>>>(G, Xc, v, N, D, W, ldW, t); count_launch(); }
 }
 void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
                  int64_t ldP, double* rowsum, cudaStream_t st) {
-  beta_kernel<256><<<(unsigned)M, 256, 0, st>>>(T, S, t, M, c * c, Pb, ldP, rowsum);
+  { beta_kernel<256><<<(unsigned)M, 256, 0, st>>>(T, S, t, M, c * c, Pb, ldP, rowsum); count_launch(); }
 }
 template <typename TU>
-void launch_backproj(const TU* U, int64_t ldU, const double* rowsum, const double* Xc, const double* G,
-                     const double* v, int64_t M, int N, int D, double lam, int add_lambda, double* out,
-                     cudaStream_t st) {
+void launch_backproj(const TU* U, int64_t ldU, int splits, int64_t split_stride, const double* rowsum,
+                     const double* Xc, const double* G, const double* v, int64_t M, int N, int D, double lam,
+                     int add_lambda, double* out, cudaStream_t st) {
   const size_t smem = D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(backproj_kernel<TU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  backproj_kernel<TU><<<(unsigned)M, 128, smem, st>>>(U, ldU, rowsum, Xc, G, v, N, D, lam,
-                                                                     add_lambda, out);
+  { backproj_kernel<TU><<<(unsigned)M, 128, smem, st>>>(U, ldU, splits, split_stride, rowsum, Xc, G, v, N, D,
+                                                       lam, add_lambda, out); count_launch(); }
 }
-template void launch_backproj<double>(const double*, int64_t, const double*, const double*, const double*,
-                                      const double*, int64_t, int, int, double, int, double*, cudaStream_t);
-template void launch_backproj<float>(const float*, int64_t, const double*, const double*, const double*,
-                                     const double*, int64_t, int, int, double, int, double*, cudaStream_t);
+template void launch_backproj<double>(const double*, int64_t, int, int64_t, const double*, const double*,
+                                      const double*, const double*, int64_t, int, int, double, int, double*,
+                                      cudaStream_t);
+template void launch_backproj<float>(const float*, int64_t, int, int64_t, const double*, const double*,
+                                     const double*, const double*, int64_t, int, int, double, int, double*,
+                                     cudaStream_t);
 
 void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* S,
                  const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
@@ -304,7 +310,7 @@ void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const doub
   dim3 grid((unsigned)M, (unsigned)cdiv(ncols, per));
   size_t smem = (2 * (size_t)D + N) * sizeof(double);
   if (smem > 48 * 1024) cudaFuncSetAttribute(kcol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kcol_kernel<<<grid, 128, smem, st>>>(cols, ncols, per, X, G, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag);
+  { kcol_kernel<<<grid, 128, smem, st>>>(cols, ncols, per, X, G, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag); count_launch(); }
 }
 
 }  // namespace gdml

@@ -8,7 +8,9 @@
 namespace gdml {
 
 // scalar slots of the PCG state (device array of doubles)
-enum { SC_RHO = 0, SC_PQ = 1, SC_RR = 2, SC_RHO_NEW = 3, SC_YY = 4, SC_COUNT = 8 };
+enum { SC_RHO = 0, SC_PQ = 1, SC_RR = 2, SC_RHO_NEW = 3, SC_YY = 4, SC_TOL2 = 5, SC_COUNT = 8 };
+// integer control words of the PCG loop (device int64 array)
+enum { IC_ITER = 0, IC_MAXIT = 1, IC_COUNT = 4 };
 
 // geom.cu
 void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double* G, cudaStream_t st);
@@ -21,9 +23,9 @@ void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, 
 void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
                  int64_t ldP, double* rowsum, cudaStream_t st);
 template <typename TU>
-void launch_backproj(const TU* U, int64_t ldU, const double* rowsum, const double* Xc, const double* G,
-                     const double* v, int64_t M, int N, int D, double lam, int add_lambda, double* out,
-                     cudaStream_t st);
+void launch_backproj(const TU* U, int64_t ldU, int splits, int64_t split_stride, const double* rowsum,
+                     const double* Xc, const double* G, const double* v, int64_t M, int N, int D, double lam,
+                     int add_lambda, double* out, cudaStream_t st);
 void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* S,
                  const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
                  const int* stop_flag, cudaStream_t st);
@@ -32,18 +34,26 @@ void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const doub
 template <typename TA, typename TB>
 void launch_dgemm(bool nt, int64_t M, int64_t N, int64_t K, double alpha, const TA* A, int64_t lda,
                   const TB* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
-                  cudaStream_t st);
+                  cudaStream_t st, int splits = 1, int64_t split_stride = 0);
+int dgemm_splits(int64_t M, int64_t N, int64_t K);
 
 // linalg.cu
 void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st);
 void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st);
-void trsv_lower(const double* L, int64_t k, double* x, bool transpose, cudaStream_t st);
+// state of the multi-CTA triangular solve: sync = [ticket, flags...] (trsv_sync_len(k) ints), error word
+struct TrsvState {
+  int* sync = nullptr;
+  int* err = nullptr;
+};
+int64_t trsv_sync_len(int64_t k);
+void trsv_lower(const double* L, int64_t k, double* x, bool transpose, TrsvState& ts, cudaStream_t st);
+void trsv_lower_single_cta(const double* L, int64_t k, double* x, bool transpose, cudaStream_t st);
 void add_diag(double* A, int64_t lda, int64_t k, double eps, cudaStream_t st);
 
 // woodbury.cu
 template <typename TL>
 void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* LC, double lam, const double* r,
-                    double* z, double* part, double* t, cudaStream_t st);
+                    double* z, double* part, double* t, TrsvState& ts, cudaStream_t st);
 int64_t woodbury_part_size(int64_t n, int64_t k);
 
 // cg.cu
@@ -54,6 +64,8 @@ void launch_update_xr(double* x, double* r, const double* p, const double* q, in
 void launch_update_p(double* p, const double* z, int64_t n, const double* sc, cudaStream_t st);
 void launch_copy_scalar(double* sc, int dst, int src, cudaStream_t st);
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
+void launch_pcg_check(const double* sc, int64_t* ictl, const int* status, cudaGraphConditionalHandle h,
+                      cudaStream_t st);
 
 // select.cu
 int64_t select_scratch_len(int64_t n);

@@ -141,10 +141,10 @@ __global__ void add_diag_kernel(double* A, int64_t lda, int64_t k, double eps) {
 void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st) {
   for (int64_t j0 = 0; j0 < k; j0 += NB) {
     int nb = (int)((k - j0) < NB ? (k - j0) : NB);
-    potrf_diag_kernel<<<1, 256, 0, st>>>(A, k, j0, nb, status);
+    { potrf_diag_kernel<<<1, 256, 0, st>>>(A, k, j0, nb, status); count_launch(); }
     int64_t r0 = j0 + nb;
     if (r0 < k) {
-      trsm_right_kernel<<<(unsigned)cdiv(k - r0, 128), 128, 0, st>>>(A, k, j0, nb, r0, k, status);
+      { trsm_right_kernel<<<(unsigned)cdiv(k - r0, 128), 128, 0, st>>>(A, k, j0, nb, r0, k, status); count_launch(); }
       // A22 -= L21 L21^T (lower tiles only)
       launch_dgemm<double, double>(true, k - r0, k - r0, nb, -1.0, A + r0 * k + j0, k, A + r0 * k + j0, k,
                                    1.0, A + r0 * k + r0, k, true, st);
@@ -156,7 +156,7 @@ void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st) {
 void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st) {
   for (int64_t j0 = 0; j0 < k; j0 += NB) {
     int nb = (int)((k - j0) < NB ? (k - j0) : NB);
-    trsm_left_diag_kernel<<<(unsigned)cdiv(nrhs, 128), 128, 0, st>>>(Lkk, k, j0, nb, Bm, nrhs, nrhs);
+    { trsm_left_diag_kernel<<<(unsigned)cdiv(nrhs, 128), 128, 0, st>>>(Lkk, k, j0, nb, Bm, nrhs, nrhs); count_launch(); }
     int64_t r0 = j0 + nb;
     if (r0 < k)  // B[r0:, :] -= L[r0:, j0:j0+nb] * B[j0:j0+nb, :]
       launch_dgemm<double, double>(false, k - r0, nrhs, nb, -1.0, Lkk + r0 * k + j0, k, Bm + j0 * nrhs, nrhs,
@@ -164,20 +164,126 @@ void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cud
   }
 }
 
-void trsv_lower(const double* L, int64_t k, double* x, bool transpose, cudaStream_t st) {
+void trsv_lower_single_cta(const double* L, int64_t k, double* x, bool transpose, cudaStream_t st) {
   size_t smem = (size_t)k * sizeof(double);
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(trsv_lower_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(trsv_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   if (transpose)
-    trsv_lower_t_kernel<<<1, 1024, smem, st>>>(L, k, x);
+    { trsv_lower_t_kernel<<<1, 1024, smem, st>>>(L, k, x); count_launch(); }
   else
-    trsv_lower_kernel<<<1, 1024, smem, st>>>(L, k, x);
+    { trsv_lower_kernel<<<1, 1024, smem, st>>>(L, k, x); count_launch(); }
 }
 
+// Multi-CTA blocked substitution with decoupled look-back.
+// Solves L y = b (forward) or L^T y = b (backward) in place on x, L lower k x k
+// row-major.  Block rows of TB = 64; a CTA takes a ticket (launch order) and
+// solves block t (forward) or block nb-1-t (backward).  It folds in the
+// contributions of the already-solved blocks as their flags appear
+// (flags[j] == 1; ticket and flags are zeroed before every launch), then
+// solves its 64 x 64 diagonal block and publishes its y.  A CTA only waits on CTAs that took earlier tickets and are already
+// running, so the dependency chain always makes progress; every wait is still
+// bounded, and a timeout sets *err and leaves the block unsolved.
+constexpr int TB = 64;
+constexpr uint32_t kLookbackSpin = 1u << 24;
+
+__global__ void __launch_bounds__(256) trsv_lookback_kernel(const double* __restrict__ L, int64_t k,
+                                                            double* __restrict__ x, int* __restrict__ sync,
+                                                            int backward, int* __restrict__ err) {
+  unsigned* ticket = reinterpret_cast<unsigned*>(sync);
+  int* flags = sync + 1;
+  const int epoch = 1;
+  __shared__ double yprev[TB];
+  __shared__ double part[4][TB + 1];
+  __shared__ double ys[TB];
+  __shared__ double Ld[TB][TB + 1];
+  __shared__ unsigned s_t;
+  __shared__ int s_ok;
+  const int nb = (int)((k + TB - 1) / TB);
+  if (threadIdx.x == 0) {
+    s_t = atomicAdd(ticket, 1u);
+    s_ok = 1;
+  }
+  __syncthreads();
+  const int t = (int)s_t;
+  const int blk = backward ? nb - 1 - t : t;
+  const int64_t r0 = (int64_t)blk * TB;
+  const int rows = (int)((k - r0) < TB ? (k - r0) : TB);
+  const int r = threadIdx.x & (TB - 1), q = threadIdx.x >> 6;  // 4 threads per row, 16 columns each
+  double acc = 0.0;
+  // contributions of earlier blocks, in solve order
+  for (int jj = 0; jj < t; ++jj) {
+    const int jb = backward ? nb - 1 - jj : jj;
+    const int64_t c0 = (int64_t)jb * TB;
+    const int cols = (int)((k - c0) < TB ? (k - c0) : TB);
+    if (threadIdx.x == 0) {
+      uint32_t it = 0;
+      while (((volatile int*)flags)[jb] != epoch && it < kLookbackSpin) {
+        ++it;
+        if (it > 32) __nanosleep(128);
+      }
+      if (it >= kLookbackSpin) {
+        s_ok = 0;
+        atomicExch(err, 1);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    if (threadIdx.x < cols) yprev[threadIdx.x] = ((volatile double*)x)[c0 + threadIdx.x];
+    __syncthreads();
+    if (r < rows) {
+      for (int c = q * 16; c < q * 16 + 16 && c < cols; ++c) {
+        // forward: L[r0+r][c0+c]; backward (L^T): L[c0+c][r0+r]
+        const double l = backward ? L[(c0 + c) * k + r0 + r] : L[(r0 + r) * k + c0 + c];
+        acc = fma(l, yprev[c], acc);
+      }
+    }
+    __syncthreads();
+  }
+  part[q][r] = acc;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const int rr = e / TB, cc = e % TB;
+    double v = 0.0;
+    if (rr < rows && cc < rows) v = backward ? L[(r0 + cc) * k + r0 + rr] : L[(r0 + rr) * k + r0 + cc];
+    Ld[rr][cc] = v;  // Ld = diagonal block of the (possibly transposed) triangular factor
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i0 = 0; i0 < rows; ++i0) {
+      const int i = backward ? rows - 1 - i0 : i0;
+      double s = 0.0;
+      for (int c = lane; c < rows; c += 32) {
+        const bool dep = backward ? (c > i) : (c < i);
+        if (dep) s = fma(Ld[i][c], ys[c], s);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        const double b = x[r0 + i] - (part[0][i] + part[1][i] + part[2][i] + part[3][i]);
+        ys[i] = (b - s) / Ld[i][i];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < rows) x[r0 + threadIdx.x] = ys[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(&flags[blk], epoch);
+}
+
+void trsv_lower(const double* L, int64_t k, double* x, bool transpose, TrsvState& ts, cudaStream_t st) {
+  const int nb = (int)((k + TB - 1) / TB);
+  cudaMemsetAsync(ts.sync, 0, (nb + 1) * sizeof(int), st);
+  { trsv_lookback_kernel<<<nb, 256, 0, st>>>(L, k, x, ts.sync, transpose ? 1 : 0, ts.err); count_launch(); }
+}
+
+int64_t trsv_sync_len(int64_t k) { return (k + TB - 1) / TB + 1; }
+
 void add_diag(double* A, int64_t lda, int64_t k, double eps, cudaStream_t st) {
-  add_diag_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(A, lda, k, eps);
+  { add_diag_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(A, lda, k, eps); count_launch(); }
 }
 
 }  // namespace gdml

@@ -137,14 +137,14 @@ __global__ void __launch_bounds__(256) pc_update_kernel(int64_t m, int64_t n, TL
 template <typename TL>
 void pivchol_run(const PivCholArgs& a, TL* L, cudaStream_t st) {
   for (int64_t m = 0; m < a.k; ++m) {
-    pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(m, a.n, 1, a.d, a.perm, a.chosen, a.pivots, a.trace,
-                                                         a.ps, a.part, a.ticket);
+    { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(m, a.n, 1, a.d, a.perm, a.chosen, a.pivots, a.trace,
+                                                         a.ps, a.part, a.ticket); count_launch(); }
     a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
-    pc_update_kernel<TL><<<(unsigned)cdiv(a.n, 256), 256, 0, st>>>(m, a.n, L, a.col, a.d, a.chosen, a.ps);
+    { pc_update_kernel<TL><<<(unsigned)cdiv(a.n, 256), 256, 0, st>>>(m, a.n, L, a.col, a.d, a.chosen, a.ps); count_launch(); }
   }
   // trace after the last step
-  pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(a.k, a.n, 0, a.d, a.perm, a.chosen, a.pivots, a.trace,
-                                                       a.ps, a.part, a.ticket);
+  { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(a.k, a.n, 0, a.d, a.perm, a.chosen, a.pivots, a.trace,
+                                                       a.ps, a.part, a.ticket); count_launch(); }
 }
 
 template void pivchol_run<double>(const PivCholArgs&, double*, cudaStream_t);

@@ -89,7 +89,7 @@ __global__ void bitonic_step_kernel(uint64_t* __restrict__ key, int64_t* __restr
 static void bitonic_sort(uint64_t* key, int64_t* idx, int64_t P, cudaStream_t st) {
   const unsigned blocks = (unsigned)cdiv(P, 256);
   for (int64_t kk = 2; kk <= P; kk <<= 1)
-    for (int64_t jj = kk >> 1; jj > 0; jj >>= 1) bitonic_step_kernel<<<blocks, 256, 0, st>>>(key, idx, P, kk, jj);
+    for (int64_t jj = kk >> 1; jj > 0; jj >>= 1) { bitonic_step_kernel<<<blocks, 256, 0, st>>>(key, idx, P, kk, jj); count_launch(); }
 }
 
 int64_t select_scratch_len(int64_t n) {
@@ -102,7 +102,7 @@ int64_t select_scratch_len(int64_t n) {
 void select_uniform(int64_t n, int64_t k, uint64_t seed, uint32_t stream, uint64_t* key, int64_t* idx,
                     int64_t* out, cudaStream_t st) {
   const int64_t P = select_scratch_len(n);
-  uniform_keys_kernel<<<(unsigned)cdiv(P, 256), 256, 0, st>>>(n, P, seed, stream, key, idx);
+  { uniform_keys_kernel<<<(unsigned)cdiv(P, 256), 256, 0, st>>>(n, P, seed, stream, key, idx); count_launch(); }
   bitonic_sort(key, idx, P, st);
   cudaMemcpyAsync(out, idx, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
 }
@@ -110,7 +110,7 @@ void select_uniform(int64_t n, int64_t k, uint64_t seed, uint32_t stream, uint64
 void select_weighted(int64_t n, int64_t k, uint64_t seed, uint32_t stream, const double* tau, uint64_t* key,
                      int64_t* idx, int64_t* out, cudaStream_t st) {
   const int64_t P = select_scratch_len(n);
-  weighted_keys_kernel<<<(unsigned)cdiv(P, 256), 256, 0, st>>>(n, P, seed, stream, tau, key, idx);
+  { weighted_keys_kernel<<<(unsigned)cdiv(P, 256), 256, 0, st>>>(n, P, seed, stream, tau, key, idx); count_launch(); }
   bitonic_sort(key, idx, P, st);
   cudaMemcpyAsync(out, idx, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
 }

@@ -233,7 +233,7 @@ static gdml_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int
   const int kb_per_split = (int)cdiv(num_kb, splits);
   splits = (int)cdiv(num_kb, kb_per_split);
   dim3 grid((unsigned)cdiv(N, BN), (unsigned)cdiv(M, BM), (unsigned)splits);
-  kern<<<grid, NUM_THREADS, SM::TOTAL, st>>>(mA, mB, M, N, num_kb, kb_per_split, epi, err);
+  { kern<<<grid, NUM_THREADS, SM::TOTAL, st>>>(mA, mB, M, N, num_kb, kb_per_split, epi, err); count_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("tcgen05 gemm launch: ") + cudaGetErrorString(e));
   return GDML_OK;
@@ -303,7 +303,7 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
       cudaMemsetAsync(vt, 0, tc.Dp * tc.K2p * sizeof(T), st) != cudaSuccess ||
       cudaMemsetAsync(tc.err, 0, sizeof(int), st) != cudaSuccess)
     return fail(GDML_ERR_CUDA, "tensor-core buffer memset");
-  tc_setup_kernel<BF16><<<(unsigned)M, 256, 0, st>>>(Xc, A, ldA, S, M, tc.D, tc.Dp, tc.K2p, xc, p, vt, tc.S32);
+  { tc_setup_kernel<BF16><<<(unsigned)M, 256, 0, st>>>(Xc, A, ldA, S, M, tc.D, tc.Dp, tc.K2p, xc, p, vt, tc.S32); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "tensor-core setup kernel");
   bool ok = make_map(&tc.mapXc, xc, BF16, tc.Dp, M, tc.Dp, BM) && make_map(&tc.mapW, w, BF16, tc.Dp, M, tc.Dp, 128) &&
             make_map(&tc.mapP, p, BF16, tc.K2p, M, tc.K2p, BM) &&
@@ -330,8 +330,8 @@ static gdml_status matvec_impl(TcMatvec& tc, const double* G, const double* v, d
   using T = typename Lp<BF16>::T;
   const int64_t M = tc.M;
   const int span = BF16 ? 64 : 32;
-  tc_proj_kernel<BF16, 256><<<(unsigned)M, 256, 3 * tc.N * sizeof(double), st>>>(
-      G, v, tc.N, tc.D, tc.Dp, tc.K2p, (const T*)tc.Xc_lp, (T*)tc.W_lp, (T*)tc.Vt_lp, tc.tb);
+  { tc_proj_kernel<BF16, 256><<<(unsigned)M, 256, 3 * tc.N * sizeof(double), st>>>(
+      G, v, tc.N, tc.D, tc.Dp, tc.K2p, (const T*)tc.Xc_lp, (T*)tc.W_lp, (T*)tc.Vt_lp, tc.tb); count_launch(); }
   EpiBeta<BF16> e1{tc.S32, tc.tb, (T*)tc.P_lp, tc.K2p, (int)M, tc.c * tc.c, tc.rs_part};
   TC_TRY((launch_gemm<BF16, 128, 5>(tc.mapXc, tc.mapW, (int)M, (int)M, tc.Dp / span, 1, e1, tc.err, st)));
   EpiStore e2{tc.U, tc.Dp, M * tc.Dp};
@@ -342,9 +342,9 @@ static gdml_status matvec_impl(TcMatvec& tc, const double* G, const double* v, d
   const size_t smem = tc.D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(tc_backproj_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  tc_backproj_kernel<BF16><<<(unsigned)M, 128, smem, st>>>(tc.U, splits, M * tc.Dp, tc.Dp, tc.rs_part,
+  { tc_backproj_kernel<BF16><<<(unsigned)M, 128, smem, st>>>(tc.U, splits, M * tc.Dp, tc.Dp, tc.rs_part,
                                                            (int)cdiv(M, 32), M, (const T*)tc.Xc_lp, G, v, tc.N,
-                                                           tc.D, lam, add_lambda, out);
+                                                           tc.D, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "tensor-core matvec kernels");
   return GDML_OK;
 }
@@ -389,8 +389,8 @@ static gdml_status gemm_test_impl(const double* A, const double* B, int M, int N
     return fail(GDML_ERR_OOM, "gemm test buffers");
   }
   cudaMemsetAsync(err, 0, sizeof(int), st);
-  to_lp_padded_kernel<BF16><<<(unsigned)cdiv((int64_t)M * Kp, 256), 256, 0, st>>>(A, M, K, Kp, a);
-  to_lp_padded_kernel<BF16><<<(unsigned)cdiv((int64_t)N * Kp, 256), 256, 0, st>>>(B, N, K, Kp, b);
+  { to_lp_padded_kernel<BF16><<<(unsigned)cdiv((int64_t)M * Kp, 256), 256, 0, st>>>(A, M, K, Kp, a); count_launch(); }
+  { to_lp_padded_kernel<BF16><<<(unsigned)cdiv((int64_t)N * Kp, 256), 256, 0, st>>>(B, N, K, Kp, b); count_launch(); }
   CUtensorMap mA, mB;
   const int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
   gdml_status s = GDML_OK;

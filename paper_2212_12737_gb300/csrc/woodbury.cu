@@ -67,20 +67,20 @@ __global__ void __launch_bounds__(256) gemv_n_update_kernel(const TL* __restrict
 
 template <typename TL>
 void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* LC, double lam, const double* r,
-                    double* z, double* part, double* t, cudaStream_t st) {
+                    double* z, double* part, double* t, TrsvState& ts, cudaStream_t st) {
   const int64_t nchunks = cdiv(n, kRowsPerChunk);
   dim3 g1((unsigned)cdiv(k, kColsPerCta), (unsigned)nchunks);
-  gemv_t_partial_kernel<TL><<<g1, 256, 0, st>>>(L, n, k, r, part);
-  reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t);
-  trsv_lower(LC, k, t, false, st);
-  trsv_lower(LC, k, t, true, st);
-  gemv_n_update_kernel<TL><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(L, n, k, t, r, 1.0 / lam, z);
+  { gemv_t_partial_kernel<TL><<<g1, 256, 0, st>>>(L, n, k, r, part); count_launch(); }
+  { reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
+  trsv_lower(LC, k, t, false, ts, st);
+  trsv_lower(LC, k, t, true, ts, st);
+  { gemv_n_update_kernel<TL><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(L, n, k, t, r, 1.0 / lam, z); count_launch(); }
 }
 
 template void woodbury_apply<double>(const double*, int64_t, int64_t, const double*, double, const double*,
-                                     double*, double*, double*, cudaStream_t);
+                                     double*, double*, double*, TrsvState&, cudaStream_t);
 template void woodbury_apply<float>(const float*, int64_t, int64_t, const double*, double, const double*,
-                                    double*, double*, double*, cudaStream_t);
+                                    double*, double*, double*, TrsvState&, cudaStream_t);
 
 int64_t woodbury_part_size(int64_t n, int64_t k) { return cdiv(n, kRowsPerChunk) * k; }
 

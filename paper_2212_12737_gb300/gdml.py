@@ -25,7 +25,8 @@ SELECT = {"uniform": 0, "rls": 1, "pivchol": 2}
 
 EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
-           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_tc_check"]
+           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_tc_check",
+           "gdml_launch_count"]
 
 
 class GdmlError(RuntimeError):
@@ -62,6 +63,7 @@ def load() -> ctypes.CDLL:
         "gdml_destroy": [P],
         "gdml_test_tc_gemm": [I32, P, P, I32, I32, I32, P, P],
         "gdml_tc_check": [P],
+        "gdml_launch_count": [],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -69,6 +71,7 @@ def load() -> ctypes.CDLL:
         f.restype = ctypes.c_int
     lib.gdml_last_error.restype = ctypes.c_char_p
     lib.gdml_destroy.restype = None
+    lib.gdml_launch_count.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -202,3 +205,8 @@ def test_tc_gemm(A: torch.Tensor, B: torch.Tensor, bf16: bool = False) -> torch.
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())
     return C
+
+
+def launch_count() -> int:
+    """Kernel launches executed by the library so far (graph replays included)."""
+    return int(load().gdml_launch_count())
