@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison solves")
+    ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply"],
+                    help="time one operation alone (small runs for profiling)")
     return ap.parse_args()
 
 
@@ -102,6 +104,42 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------- GPU arm
+def run_op(args):
+    """--only matvec|apply: W untimed + K timed calls of one operation, one JSON line."""
+    import torch
+
+    from paper_2212_12737_gb300 import gdml, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = synth.workload(args.workload)
+    ctx = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam, precision=args.precision)
+    v = torch.randn(w.n, dtype=torch.float64, device=dev)
+    out = torch.empty_like(v)
+    if args.only == "apply":
+        ctx.precond_build(w.select, w.k, seed=2)
+        fn = lambda: ctx.precond_apply(v, out)
+    else:
+        fn = lambda: ctx.matvec(v, out)
+    for _ in range(args.warmup):
+        fn()
+    st = torch.cuda.current_stream(dev)
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    s.record(st)
+    for _ in range(args.steps):
+        fn()
+    e.record(st)
+    torch.cuda.synchronize(dev)
+    ms = s.elapsed_time(e) / args.steps
+    D = w.N * (w.N - 1) // 2
+    print(json.dumps({"op": args.only, "workload": args.workload, "precision": args.precision, "ms": ms,
+                      "matvec_tflops": 6.0 * w.M * w.M * D / ms / 1e9 if args.only == "matvec" else None,
+                      "apply_gbs": 2.0 * w.n * w.k * 8 / ms / 1e6 if args.only == "apply" else None}), flush=True)
+    ctx.destroy()
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -375,5 +413,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.only != "solve":
+        run_op(a)
     else:
         run_gpu(a)

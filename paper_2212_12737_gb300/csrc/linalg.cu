@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(256) trsv_lookback_kernel(const double* __rest
     __syncthreads();
   }
   part[q][r] = acc;
+  if (threadIdx.x < rows) yprev[threadIdx.x] = x[r0 + threadIdx.x];  // right-hand side of this block
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int rr = e / TB, cc = e % TB;
     double v = 0.0;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256) trsv_lookback_kernel(const double* __rest
       }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) {
-        const double b = x[r0 + i] - (part[0][i] + part[1][i] + part[2][i] + part[3][i]);
+        const double b = yprev[i] - (part[0][i] + part[1][i] + part[2][i] + part[3][i]);
         ys[i] = (b - s) / Ld[i][i];
       }
       __syncwarp();

@@ -226,7 +226,7 @@ def test_zero_rhs_and_iteration_cap_and_bad_args():
         ctx.pcg_solve(dev(w.y), rtol=1e-12, max_iter=3)
     assert e.value.name == "ERR_NOT_CONVERGED"
     alpha, iters, rel, _ = ctx.pcg_solve(dev(w.y), rtol=1e-12, max_iter=3, raise_on_nonconvergence=False)
-    assert iters == 3 and 0 < rel < 1
+    assert iters == 3 and np.isfinite(rel) and rel > 1e-12  # plain CG may raise |r| early on
     with pytest.raises(gdml.GdmlError):
         ctx.precond_apply(dev(w.y))  # nothing built yet
     for bad in (0, w.n + 1):
