@@ -133,6 +133,26 @@ gdml_status gdml_set_inner_rtol(gdml_ctx* ctx, double inner_rtol);
 /* Outer refinement steps of the last gdml_pcg_solve (1 for FP64 contexts). */
 gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
 
+/* out = K v (+ lambda v if add_lambda) for M geometries R_dev (same layout as
+ * gdml_kernel_setup), computed in FP64 WITHOUT a context and WITHOUT any device
+ * allocation -- for callers that cannot call cudaMalloc: code that runs while
+ * another runtime owns the device memory (a framework's caching allocator or
+ * a fixed pre-reserved budget), real-time loops where an allocation could
+ * block or fail, or work recorded between pre-allocated buffers only.
+ * The paper has no counterpart; this is a deployment variant of gdml_matvec.
+ *  Limits: 1 <= M <= 128 geometries, 2 <= N <= 24 atoms (GDML_ERR_ARG beyond).
+ *  Working memory: one static device array of 2.5 MB that every GPU loading
+ *    this library holds until process exit; every call overwrites what it uses,
+ *    so nothing needs clearing between calls.
+ *  The first call on each device looks the array's address up (with that
+ *    device current), so make that first call before any stream capture.
+ *  Calls that overlap on the GPU (two streams, or two host threads on one
+ *    device) share the array and race; serialise them.
+ *  R_dev, v_dev, out_dev: caller-owned device arrays (v_dev != out_dev);
+ *  cuda_stream: a cudaStream_t or NULL. */
+gdml_status gdml_matvec_noalloc(const double* R_dev, int64_t M, int32_t N, double sigma, double lambda,
+                                const double* v_dev, double* out_dev, int32_t add_lambda, void* cuda_stream);
+
 /* Message describing the last error on ctx (or the last failed setup when
  * ctx is NULL).  Never NULL; valid until the next call on the context. */
 const char* gdml_last_error(const gdml_ctx* ctx);

@@ -26,7 +26,7 @@ SELECT = {"uniform": 0, "rls": 1, "pivchol": 2}
 EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
            "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_tc_check",
-           "gdml_launch_count"]
+           "gdml_launch_count", "gdml_matvec_noalloc"]
 
 
 class GdmlError(RuntimeError):
@@ -64,6 +64,7 @@ def load() -> ctypes.CDLL:
         "gdml_test_tc_gemm": [I32, P, P, I32, I32, I32, P, P],
         "gdml_tc_check": [P],
         "gdml_launch_count": [],
+        "gdml_matvec_noalloc": [P, I64, I32, D, D, P, P, I32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -210,3 +211,20 @@ def test_tc_gemm(A: torch.Tensor, B: torch.Tensor, bf16: bool = False) -> torch.
 def launch_count() -> int:
     """Kernel launches executed by the library so far (graph replays included)."""
     return int(load().gdml_launch_count())
+
+
+def matvec_noalloc(R: torch.Tensor, sigma: float, lam: float, v: torch.Tensor, out: torch.Tensor | None = None,
+                   add_lambda: bool = True) -> torch.Tensor:
+    """K v (+ lam v) with no context and no device allocation inside the library
+    (M <= 128 geometries, N <= 24 atoms; scratch is a static device array)."""
+    lib = load()
+    if R.dtype != torch.float64 or R.dim() != 3 or R.shape[2] != 3:
+        raise ValueError("R must be a float64 CUDA tensor of shape (M, N, 3)")
+    if out is None:
+        out = torch.empty_like(v)
+    st = lib.gdml_matvec_noalloc(_ptr(R.contiguous()), int(R.shape[0]), int(R.shape[1]), float(sigma), float(lam),
+                                 _ptr(v), _ptr(out), int(add_lambda),
+                                 ctypes.c_void_p(torch.cuda.current_stream(R.device).cuda_stream))
+    if st != 0:
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+    return out
