@@ -62,7 +62,8 @@ struct gdml_ctx {
   int64_t k = 0;  // rank built (0: none)
   double jitter = 0;
   double* L = nullptr;    // n x k col-major
-  double* LC = nullptr;   // k x k lower (row-major)
+  double* LC = nullptr;   // k x k lower (row-major): Cholesky factor of C = lambda I + L^T L
+  double* Cinv = nullptr; // k x k: C^-1 = L_C^-T L_C^-1 (formed once per build)
   double* wpart = nullptr;
   double* wt = nullptr;
   int64_t cap_k = 0;
@@ -76,7 +77,6 @@ struct gdml_ctx {
   double* hsc = nullptr;      // pinned host mirror of scalars
   int64_t* ictl = nullptr;    // device loop control (IC_*)
   int64_t* hictl = nullptr;   // pinned host mirror
-  TrsvState ts;               // multi-CTA triangular solve state
   cudaStream_t cap = nullptr;             // private stream used only to capture graphs
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // PCG loop graphs: [0] context precision, [1] FP64
   int64_t gbody[2] = {0, 0};                       // kernels per captured iteration
@@ -190,6 +190,20 @@ gdml_status get_cols(gdml_ctx* c, const int64_t* cols, int64_t ncols, double* ou
   return check_launch(c, "kcol");
 }
 
+struct Scratch {
+  gdml_ctx* c;
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) dfree(c, p);
+  }
+  template <typename T>
+  gdml_status get(T** p, size_t count) {
+    gdml_status s = dalloc(c, p, count);
+    if (s == GDML_OK) ptrs.push_back(*p);
+    return s;
+  }
+};
+
 // In-place lower Cholesky of the k x k work matrix (copy of src) with the
 // jitter rule of Eq. 5's factorisation: eps = 1e-14 tr/k, x10 up to 1e-6 tr/k.
 gdml_status chol_jitter(gdml_ctx* c, const double* src, double* work, int64_t k, double* eps_out) {
@@ -229,8 +243,8 @@ gdml_status nystrom(gdml_ctx* c, const int64_t* S, int64_t k, double* L, double*
   return check_launch(c, "trsm");
 }
 
-// LC <- chol(lambda I + L^T L)
-gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC) {
+// LC <- chol(lambda I + L^T L) (Eq. 4); with Cinv, also C^-1 = L_C^-T L_C^-1
+gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, double* Cinv = nullptr) {
   launch_dgemm<double, double>(true, k, k, c->n, 1.0, L, c->n, L, c->n, 0.0, LC, k, true, c->st);
   add_diag(LC, k, k, c->lam, c->st);
   CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
@@ -239,6 +253,18 @@ gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC) {
   int h = 0;
   TRY(read_status(c, &h));
   if (h) return ctx_fail(c, GDML_ERR_NOT_SPD, "Cholesky of lambda I + L^T L failed at column " + std::to_string(h - 1));
+  if (Cinv) {
+    Scratch s{c, {}};
+    double *X = nullptr, *Xt = nullptr;
+    TRY(s.get(&X, (size_t)(k * k)));
+    TRY(s.get(&Xt, (size_t)(k * k)));
+    set_identity(X, k, c->st);
+    trsm_left_lower(LC, k, X, k, c->st);  // X = L_C^-1
+    transpose_square(X, k, Xt, c->st);
+    launch_dgemm<double, double>(true, k, k, k, 1.0, Xt, k, Xt, k, 0.0, Cinv, k, false, c->st);  // X^T X
+    TRY(check_launch(c, "woodbury inverse"));
+    CTRY(c, cudaStreamSynchronize(c->st));
+  }
   return GDML_OK;
 }
 
@@ -248,32 +274,19 @@ gdml_status ensure_precond_buffers(gdml_ctx* c, int64_t k) {
   dfree(c, c->LC);
   dfree(c, c->wpart);
   dfree(c, c->wt);
-  c->L = c->LC = c->wpart = c->wt = nullptr;
+  dfree(c, c->Cinv);
+  c->L = c->LC = c->wpart = c->wt = c->Cinv = nullptr;
   c->cap_k = 0;
   TRY(dalloc(c, &c->L, (size_t)(c->n * k)));
   TRY(dalloc(c, &c->LC, (size_t)(k * k)));
+  TRY(dalloc(c, &c->Cinv, (size_t)(k * k)));
   TRY(dalloc(c, &c->wpart, (size_t)woodbury_part_size(c->n, k)));
-  TRY(dalloc(c, &c->wt, (size_t)k));
-  dfree(c, c->ts.sync);
-  c->ts.sync = nullptr;
-  TRY(dalloc(c, &c->ts.sync, (size_t)trsv_sync_len(k)));
+  TRY(dalloc(c, &c->wt, (size_t)(2 * k)));
   c->cap_k = k;
   return GDML_OK;
 }
 
-struct Scratch {
-  gdml_ctx* c;
-  std::vector<void*> ptrs;
-  ~Scratch() {
-    for (void* p : ptrs) dfree(c, p);
-  }
-  template <typename T>
-  gdml_status get(T** p, size_t count) {
-    gdml_status s = dalloc(c, p, count);
-    if (s == GDML_OK) ptrs.push_back(*p);
-    return s;
-  }
-};
+
 
 // ------------------------------------------------------------------ PCG
 gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
@@ -281,7 +294,7 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
     CTRY(c, cudaMemcpyAsync(z, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GDML_OK;
   }
-  woodbury_apply<double>(c->L, c->n, c->k, c->LC, c->lam, r, z, c->wpart, c->wt, c->ts, c->st);
+  woodbury_apply<double>(c->L, c->n, c->k, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
   return check_launch(c, "woodbury_apply");
 }
 
@@ -483,10 +496,8 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   TRY(dalloc(C, &c->ticket, 1));
   TRY(dalloc(C, &c->status, 1));
   TRY(dalloc(C, &c->ictl, IC_COUNT));
-  TRY(dalloc(C, &c->ts.err, 1));
   CTRY(C, cudaMallocHost(&c->hsc, SC_COUNT * sizeof(double)));
   CTRY(C, cudaMallocHost(&c->hictl, IC_COUNT * sizeof(int64_t)));
-  CTRY(C, cudaMemsetAsync(c->ts.err, 0, sizeof(int), c->st));
   CTRY(C, cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), c->st));
   CTRY(C, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
   CTRY(C, cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), c->st));
@@ -608,7 +619,7 @@ gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t 
     TRY(check_launch(c, "selection"));
     TRY(nystrom(c, S, k, c->L, Kkk, work, &c->jitter));
   }
-  TRY(woodbury_core(c, c->L, rank, c->LC));
+  TRY(woodbury_core(c, c->L, rank, c->LC, c->Cinv));
   if (pivots_dev) CTRY(c, cudaMemcpyAsync(pivots_dev, S, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st));
   if (resid_trace_dev)
     CTRY(c, cudaMemcpyAsync(resid_trace_dev, trace, k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));

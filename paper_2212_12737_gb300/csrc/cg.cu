@@ -34,10 +34,13 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const double* __restri
     last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double tot = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) tot += ((volatile double*)partial)[b];
+  if (!last) return;
+  __threadfence();
+  // the last CTA combines the partials: thread t sums t, t+256, ... then a fixed tree
+  double tot = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kDotThreads) tot += ((volatile double*)partial)[b];
+  tot = block_sum<kDotThreads>(tot, red);
+  if (threadIdx.x == 0) {
     *out = tot;
     *ticket = 0u;
   }

@@ -40,20 +40,15 @@ int dgemm_splits(int64_t M, int64_t N, int64_t K);
 // linalg.cu
 void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st);
 void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st);
-// state of the multi-CTA triangular solve: sync = [ticket, flags...] (trsv_sync_len(k) ints), error word
-struct TrsvState {
-  int* sync = nullptr;
-  int* err = nullptr;
-};
-int64_t trsv_sync_len(int64_t k);
-void trsv_lower(const double* L, int64_t k, double* x, bool transpose, TrsvState& ts, cudaStream_t st);
-void trsv_lower_single_cta(const double* L, int64_t k, double* x, bool transpose, cudaStream_t st);
 void add_diag(double* A, int64_t lda, int64_t k, double eps, cudaStream_t st);
 
 // woodbury.cu
+// t must hold 2k doubles (t and u = C^-1 t)
 template <typename TL>
-void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* LC, double lam, const double* r,
-                    double* z, double* part, double* t, TrsvState& ts, cudaStream_t st);
+void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* Cinv, double lam, const double* r,
+                    double* z, double* part, double* t, cudaStream_t st);
+void transpose_square(const double* A, int64_t k, double* At, cudaStream_t st);
+void set_identity(double* A, int64_t k, cudaStream_t st);
 int64_t woodbury_part_size(int64_t n, int64_t k);
 
 // cg.cu

@@ -1,7 +1,7 @@
 // Dense FP64 linear algebra for the Nystrom / Woodbury preconditioner (Eqs. 4-5):
 //  - blocked right-looking Cholesky of a k x k SPD matrix (K_kk and C = lambda I + L^T L)
 //  - forward substitution with many right-hand sides (L_k = K_nk L_kk^-T)
-//  - forward / backward substitution for one vector (Woodbury apply)
+//  - the explicit inverse C^-1 = L_C^-T L_C^-1 used by the Woodbury apply
 // A non-positive or non-finite pivot is reported through a device status word
 // (index of the failing column + 1), never by trapping.
 #include "common.cuh"
@@ -98,38 +98,6 @@ __global__ void trsm_left_diag_kernel(const double* __restrict__ Lkk, int64_t ld
   }
 }
 
-// Single-vector triangular solves with a lower-triangular k x k factor L
-// (row-major).  Column-oriented substitution across one CTA.
-__global__ void trsv_lower_kernel(const double* __restrict__ L, int64_t k, double* __restrict__ x) {
-  extern __shared__ double xs[];
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) xs[i] = x[i];
-  __syncthreads();
-  for (int64_t c = 0; c < k; ++c) {
-    const double xc = xs[c] / L[c * k + c];
-    __syncthreads();
-    if (threadIdx.x == 0) xs[c] = xc;
-    for (int64_t r = c + 1 + threadIdx.x; r < k; r += blockDim.x) xs[r] = fma(-L[r * k + c], xc, xs[r]);
-    __syncthreads();
-  }
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) x[i] = xs[i];
-}
-
-// x <- L^-T x  (L lower, row-major): backward substitution over rows of L.
-__global__ void trsv_lower_t_kernel(const double* __restrict__ L, int64_t k, double* __restrict__ x) {
-  extern __shared__ double xs[];
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) xs[i] = x[i];
-  __syncthreads();
-  for (int64_t c = k - 1; c >= 0; --c) {
-    const double xc = xs[c] / L[c * k + c];
-    __syncthreads();
-    if (threadIdx.x == 0) xs[c] = xc;
-    // x_r -= L[c][r] * x_c for r < c (row c of L holds column c of L^T)
-    for (int64_t r = threadIdx.x; r < c; r += blockDim.x) xs[r] = fma(-L[c * k + r], xc, xs[r]);
-    __syncthreads();
-  }
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) x[i] = xs[i];
-}
-
 __global__ void add_diag_kernel(double* A, int64_t lda, int64_t k, double eps) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < k) A[i * lda + i] += eps;
@@ -164,124 +132,33 @@ void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cud
   }
 }
 
-void trsv_lower_single_cta(const double* L, int64_t k, double* x, bool transpose, cudaStream_t st) {
-  size_t smem = (size_t)k * sizeof(double);
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(trsv_lower_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(trsv_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+__global__ void transpose_square_kernel(const double* __restrict__ A, int64_t k, double* __restrict__ At) {
+  __shared__ double tile[32][33];
+  const int64_t bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t r = by + yy, c = bx + threadIdx.x;
+    tile[yy][threadIdx.x] = (r < k && c < k) ? A[r * k + c] : 0.0;
   }
-  if (transpose)
-    { trsv_lower_t_kernel<<<1, 1024, smem, st>>>(L, k, x); count_launch(); }
-  else
-    { trsv_lower_kernel<<<1, 1024, smem, st>>>(L, k, x); count_launch(); }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t r = bx + yy, c = by + threadIdx.x;
+    if (r < k && c < k) At[r * k + c] = tile[threadIdx.x][yy];
+  }
 }
 
-// Multi-CTA blocked substitution with decoupled look-back.
-// Solves L y = b (forward) or L^T y = b (backward) in place on x, L lower k x k
-// row-major.  Block rows of TB = 64; a CTA takes a ticket (launch order) and
-// solves block t (forward) or block nb-1-t (backward).  It folds in the
-// contributions of the already-solved blocks as their flags appear
-// (flags[j] == 1; ticket and flags are zeroed before every launch), then
-// solves its 64 x 64 diagonal block and publishes its y.  A CTA only waits on CTAs that took earlier tickets and are already
-// running, so the dependency chain always makes progress; every wait is still
-// bounded, and a timeout sets *err and leaves the block unsolved.
-constexpr int TB = 64;
-constexpr uint32_t kLookbackSpin = 1u << 24;
-
-__global__ void __launch_bounds__(256) trsv_lookback_kernel(const double* __restrict__ L, int64_t k,
-                                                            double* __restrict__ x, int* __restrict__ sync,
-                                                            int backward, int* __restrict__ err) {
-  unsigned* ticket = reinterpret_cast<unsigned*>(sync);
-  int* flags = sync + 1;
-  const int epoch = 1;
-  __shared__ double yprev[TB];
-  __shared__ double part[4][TB + 1];
-  __shared__ double ys[TB];
-  __shared__ double Ld[TB][TB + 1];
-  __shared__ unsigned s_t;
-  __shared__ int s_ok;
-  const int nb = (int)((k + TB - 1) / TB);
-  if (threadIdx.x == 0) {
-    s_t = atomicAdd(ticket, 1u);
-    s_ok = 1;
-  }
-  __syncthreads();
-  const int t = (int)s_t;
-  const int blk = backward ? nb - 1 - t : t;
-  const int64_t r0 = (int64_t)blk * TB;
-  const int rows = (int)((k - r0) < TB ? (k - r0) : TB);
-  const int r = threadIdx.x & (TB - 1), q = threadIdx.x >> 6;  // 4 threads per row, 16 columns each
-  double acc = 0.0;
-  // contributions of earlier blocks, in solve order
-  for (int jj = 0; jj < t; ++jj) {
-    const int jb = backward ? nb - 1 - jj : jj;
-    const int64_t c0 = (int64_t)jb * TB;
-    const int cols = (int)((k - c0) < TB ? (k - c0) : TB);
-    if (threadIdx.x == 0) {
-      uint32_t it = 0;
-      while (((volatile int*)flags)[jb] != epoch && it < kLookbackSpin) {
-        ++it;
-        if (it > 32) __nanosleep(128);
-      }
-      if (it >= kLookbackSpin) {
-        s_ok = 0;
-        atomicExch(err, 1);
-      }
-      __threadfence();
-    }
-    __syncthreads();
-    if (!s_ok) return;
-    if (threadIdx.x < cols) yprev[threadIdx.x] = ((volatile double*)x)[c0 + threadIdx.x];
-    __syncthreads();
-    if (r < rows) {
-      for (int c = q * 16; c < q * 16 + 16 && c < cols; ++c) {
-        // forward: L[r0+r][c0+c]; backward (L^T): L[c0+c][r0+r]
-        const double l = backward ? L[(c0 + c) * k + r0 + r] : L[(r0 + r) * k + c0 + c];
-        acc = fma(l, yprev[c], acc);
-      }
-    }
-    __syncthreads();
-  }
-  part[q][r] = acc;
-  if (threadIdx.x < rows) yprev[threadIdx.x] = x[r0 + threadIdx.x];  // right-hand side of this block
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int rr = e / TB, cc = e % TB;
-    double v = 0.0;
-    if (rr < rows && cc < rows) v = backward ? L[(r0 + cc) * k + r0 + rr] : L[(r0 + rr) * k + r0 + cc];
-    Ld[rr][cc] = v;  // Ld = diagonal block of the (possibly transposed) triangular factor
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int i0 = 0; i0 < rows; ++i0) {
-      const int i = backward ? rows - 1 - i0 : i0;
-      double s = 0.0;
-      for (int c = lane; c < rows; c += 32) {
-        const bool dep = backward ? (c > i) : (c < i);
-        if (dep) s = fma(Ld[i][c], ys[c], s);
-      }
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) {
-        const double b = yprev[i] - (part[0][i] + part[1][i] + part[2][i] + part[3][i]);
-        ys[i] = (b - s) / Ld[i][i];
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < rows) x[r0 + threadIdx.x] = ys[threadIdx.x];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicExch(&flags[blk], epoch);
+__global__ void set_identity_kernel(double* A, int64_t k) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < k * k) A[e] = (e / k == e % k) ? 1.0 : 0.0;
 }
 
-void trsv_lower(const double* L, int64_t k, double* x, bool transpose, TrsvState& ts, cudaStream_t st) {
-  const int nb = (int)((k + TB - 1) / TB);
-  cudaMemsetAsync(ts.sync, 0, (nb + 1) * sizeof(int), st);
-  { trsv_lookback_kernel<<<nb, 256, 0, st>>>(L, k, x, ts.sync, transpose ? 1 : 0, ts.err); count_launch(); }
+void transpose_square(const double* A, int64_t k, double* At, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(k, 32), (unsigned)cdiv(k, 32));
+  { transpose_square_kernel<<<grid, dim3(32, 8), 0, st>>>(A, k, At); count_launch(); }
 }
 
-int64_t trsv_sync_len(int64_t k) { return (k + TB - 1) / TB + 1; }
+void set_identity(double* A, int64_t k, cudaStream_t st) {
+  { set_identity_kernel<<<(unsigned)cdiv(k * k, 256), 256, 0, st>>>(A, k); count_launch(); }
+}
 
 void add_diag(double* A, int64_t lda, int64_t k, double eps, cudaStream_t st) {
   { add_diag_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(A, lda, k, eps); count_launch(); }

@@ -72,15 +72,34 @@ __global__ void __launch_bounds__(kArgThreads) pc_argmax_kernel(
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
-  ArgMax b{-1.0 / 0.0, INT64_MAX};
-  double tot = 0.0;
-  volatile ArgMaxPart* vp = part;
-  for (unsigned i = 0; i < gridDim.x; ++i) {
-    b = better(b, ArgMax{vp[i].v, vp[i].pos});
-    tot += vp[i].sum;
+  // the last CTA combines the per-CTA results with all its threads (fixed order)
+  {
+    ArgMax bt{-1.0 / 0.0, INT64_MAX};
+    double st = 0.0;
+    volatile ArgMaxPart* vp = part;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += kArgThreads) {
+      bt = better(bt, ArgMax{vp[i].v, vp[i].pos});
+      st += vp[i].sum;
+    }
+    sv[threadIdx.x] = bt.v;
+    sp[threadIdx.x] = bt.pos;
+    ss[threadIdx.x] = st;
   }
+  __syncthreads();
+  for (int o = kArgThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ArgMax r = better(ArgMax{sv[threadIdx.x], sp[threadIdx.x]}, ArgMax{sv[threadIdx.x + o], sp[threadIdx.x + o]});
+      sv[threadIdx.x] = r.v;
+      sp[threadIdx.x] = r.pos;
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const ArgMax b{sv[0], sp[0]};
+  const double tot = ss[0];
   *ticket = 0u;
   if (m > 0 && trace) trace[m - 1] = tot;
   if (!do_select) return;

@@ -1,8 +1,11 @@
 // Woodbury apply of the Nystrom preconditioner (Eq. 4):
-//   z = lambda^-1 [ r - L_k C^-1 L_k^T r ],  C = lambda I + L_k^T L_k = L_C L_C^T.
-// L_k is stored column-major (n x k, column j at L + j*n) in FP64, or in FP32
-// for the mixed-precision contexts; all arithmetic is FP64 (FP32 x FP64
-// products are formed in FP64).  Two HBM passes over L_k per apply.
+//   z = lambda^-1 [ r - L_k C^-1 L_k^T r ],  C = lambda I + L_k^T L_k.
+// C^-1 is formed once per build from the FP64 Cholesky factor of C
+// (C^-1 = L_C^-T L_C^-1), so the apply is three data-parallel passes:
+//   t = L_k^T r,  u = C^-1 t,  z = (r - L_k u) / lambda
+// instead of two latency-bound triangular solves per CG iteration.  L_k is
+// stored column-major (n x k, column j at L + j*n) in FP64, or in FP32 for the
+// mixed-precision contexts; all arithmetic is FP64.  Two HBM passes over L_k.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -38,49 +41,65 @@ __global__ void reduce_chunks_kernel(const double* __restrict__ part, int64_t nc
   t[j] = s;
 }
 
-// z[i] = (r[i] - sum_j L[i + j n] x[j]) / lambda  (x staged through shared memory)
+// u = C^-1 t: one warp per row of the dense symmetric k x k inverse
+__global__ void __launch_bounds__(256) symv_kernel(const double* __restrict__ A, int64_t k,
+                                                   const double* __restrict__ t, double* __restrict__ u) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= k) return;
+  const double* row = A + i * k;
+  double s = 0.0;
+  for (int64_t j = lane; j < k; j += 32) s = fma(row[j], t[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) u[i] = s;
+}
+
+// z[i] = (r[i] - sum_j L[i + j n] x[j]) / lambda.  64 rows x 4 column
+// quarters per CTA (coalesced 512-byte row segments, 4 independent chains per
+// row, combined in a fixed order); x staged through shared memory.
 template <typename TL>
 __global__ void __launch_bounds__(256) gemv_n_update_kernel(const TL* __restrict__ L, int64_t n, int64_t k,
                                                             const double* __restrict__ x,
                                                             const double* __restrict__ r, double inv_lam,
                                                             double* __restrict__ z) {
   __shared__ double xs[2048];
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double s0 = 0.0, s1 = 0.0;
+  __shared__ double part[4][64];
+  const int rr = threadIdx.x & 63, q = threadIdx.x >> 6;
+  const int64_t i = (int64_t)blockIdx.x * 64 + rr;
+  double s = 0.0;
   for (int64_t j0 = 0; j0 < k; j0 += 2048) {
     const int64_t jn = (k - j0) < 2048 ? (k - j0) : 2048;
     __syncthreads();
     for (int64_t t = threadIdx.x; t < jn; t += blockDim.x) xs[t] = x[j0 + t];
     __syncthreads();
     if (i < n) {
+      const int64_t qa = (jn * q) / 4, qb = (jn * (q + 1)) / 4;
       const TL* Lc = L + j0 * n + i;
-      int64_t j = 0;
-      for (; j + 1 < jn; j += 2) {
-        s0 = fma((double)Lc[j * n], xs[j], s0);
-        s1 = fma((double)Lc[(j + 1) * n], xs[j + 1], s1);
-      }
-      if (j < jn) s0 = fma((double)Lc[j * n], xs[j], s0);
+#pragma unroll 8
+      for (int64_t j = qa; j < qb; ++j) s = fma((double)Lc[j * n], xs[j], s);
     }
   }
-  if (i < n) z[i] = (r[i] - (s0 + s1)) * inv_lam;
+  part[q][rr] = s;
+  __syncthreads();
+  if (q == 0 && i < n) z[i] = (r[i] - ((part[0][rr] + part[1][rr]) + (part[2][rr] + part[3][rr]))) * inv_lam;
 }
 
 template <typename TL>
-void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* LC, double lam, const double* r,
-                    double* z, double* part, double* t, TrsvState& ts, cudaStream_t st) {
+void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* Cinv, double lam, const double* r,
+                    double* z, double* part, double* t, cudaStream_t st) {
   const int64_t nchunks = cdiv(n, kRowsPerChunk);
   dim3 g1((unsigned)cdiv(k, kColsPerCta), (unsigned)nchunks);
+  double* u = t + k;
   { gemv_t_partial_kernel<TL><<<g1, 256, 0, st>>>(L, n, k, r, part); count_launch(); }
   { reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
-  trsv_lower(LC, k, t, false, ts, st);
-  trsv_lower(LC, k, t, true, ts, st);
-  { gemv_n_update_kernel<TL><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(L, n, k, t, r, 1.0 / lam, z); count_launch(); }
+  { symv_kernel<<<(unsigned)cdiv(k, 8), 256, 0, st>>>(Cinv, k, t, u); count_launch(); }
+  { gemv_n_update_kernel<TL><<<(unsigned)cdiv(n, 64), 256, 0, st>>>(L, n, k, u, r, 1.0 / lam, z); count_launch(); }
 }
 
 template void woodbury_apply<double>(const double*, int64_t, int64_t, const double*, double, const double*,
-                                     double*, double*, double*, TrsvState&, cudaStream_t);
+                                     double*, double*, double*, cudaStream_t);
 template void woodbury_apply<float>(const float*, int64_t, int64_t, const double*, double, const double*,
-                                    double*, double*, double*, TrsvState&, cudaStream_t);
+                                    double*, double*, double*, cudaStream_t);
 
 int64_t woodbury_part_size(int64_t n, int64_t k) { return cdiv(n, kRowsPerChunk) * k; }
 
