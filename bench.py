@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison solves")
     ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply"],
                     help="time one operation alone (small runs for profiling)")
+    ap.add_argument("--suite", default=None, choices=["batched", "learned"],
+                    help="many uneven systems: per-system solves vs one batched graph solve")
+    ap.add_argument("--suite-count", type=int, default=64)
+    ap.add_argument("--suite-mmax", type=int, default=2000, help="cap on M (geometries) per system")
+    ap.add_argument("--suite-maxiter", type=int, default=2000, help="PCG iteration cap per system in the suite")
     return ap.parse_args()
 
 
@@ -138,6 +143,133 @@ def run_op(args):
                       "matvec_tflops": 6.0 * w.M * w.M * D / ms / 1e9 if args.only == "matvec" else None,
                       "apply_gbs": 2.0 * w.n * w.k * 8 / ms / 1e6 if args.only == "apply" else None}), flush=True)
     ctx.destroy()
+
+
+def run_suite(args):
+    """Many uneven systems (N in {9,12,15,21,42}, M in [100, mmax], sigma in
+    {5,10,20,40}, lambda in {1e-10,1e-8}, uniform k = M/10): per-system FP64
+    solves one after another vs one batched graph solve, after autotuning."""
+    import torch
+
+    from paper_2212_12737_gb300 import gdml, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    suite = synth.batched_suite(args.suite_count, mmax=args.suite_mmax)
+    cache = os.path.join(ROOT, "paper_2212_12737_gb300", "lib", "tuning.json")
+    ctxs, ys = [], []
+    t0 = time.perf_counter()
+    for w in suite:
+        c = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam)
+        c.autotune(cache)
+        c.precond_build("uniform", w.k, seed=2)
+        ctxs.append(c)
+        ys.append(torch.from_numpy(w.y).to(dev))
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t0
+    # warm both paths once (graph capture, instantiation)
+    def seq():
+        out = []
+        for c, y in zip(ctxs, ys):
+            _, it, rel, _ = c.pcg_solve(y, rtol=RTOL, max_iter=args.suite_maxiter, raise_on_nonconvergence=False)
+            out.append((it, rel))
+        return out
+    t0 = time.perf_counter()
+    res_seq = seq()
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, its, rels = gdml.pcg_solve_batched(ctxs, ys, rtol=RTOL, max_iter=args.suite_maxiter,
+                                          raise_on_nonconvergence=False)
+    torch.cuda.synchronize(dev)
+    t_bat = time.perf_counter() - t0
+    n_tot = sum(w.n for w in suite)
+    print(json.dumps({
+        "suite": "batched", "systems": len(suite), "total_unknowns": n_tot, "mmax": args.suite_mmax,
+        "max_iter": args.suite_maxiter,
+        "setup_and_build_s": t_setup, "per_system_solves_s": t_seq, "batched_graph_solve_s": t_bat,
+        "speedup": t_seq / t_bat, "iters_total": int(sum(its)),
+        "converged": int(sum(r <= RTOL for r in rels)), "max_relres": max(rels),
+        "same_iterations_as_per_system": all(a == b[0] for a, b in zip(its, res_seq))}), flush=True)
+    for c in ctxs:
+        c.destroy()
+
+
+def run_learned(args):
+    """Learned inducing-column scorer: train on per-geometry ridge-leverage
+    labels of --suite-count training systems of the same molecule (other noise
+    seeds), select k columns for the headline system, and compare PCG
+    iterations / solve time with pivoted Cholesky (the fallback and judge)."""
+    import torch
+
+    from paper_2212_12737_gb300 import gdml, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = dict(synth.WORKLOADS[args.workload])
+    k = base["k"]
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    for s in range(args.suite_count):
+        cfg = dict(base)
+        w = synth.make_workload(f"train{s}", cfg["N"], cfg["M"], cfg["noise"], cfg["sigma"], cfg["lam"], k,
+                                "uniform", template_seed=0, noise_seed=100 + s)
+        c = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam)
+        Xs.append(c.descriptors())
+        ys.append(gdml.geometry_labels(c, k))
+        c.destroy()
+    torch.cuda.synchronize(dev)
+    t_labels = time.perf_counter() - t0
+    X = torch.cat(Xs)
+    y = torch.cat(ys)
+    sc = gdml.Scorer(X.shape[1], 256, seed=0)
+    sc.fit_scaling(X, y)
+    t0 = time.perf_counter()
+    loss = sc.train(X, y, epochs=30, batch=256, lr=1e-3)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    w = synth.workload(args.workload)
+    R = torch.from_numpy(w.R).to(dev)
+    yv = torch.from_numpy(w.y).to(dev)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t, out
+
+    def pivchol():
+        c = gdml.kernel_setup(R, w.sigma, w.lam)
+        c.precond_build("pivchol", k)
+        _, it, rel, _ = c.pcg_solve(yv, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
+        c.destroy()
+        return it, rel
+
+    def learned(judge):
+        c = gdml.kernel_setup(R, w.sigma, w.lam)
+        _, it, rel, used = gdml.solve_learned(c, sc, yv, k, judge_iters=judge)
+        c.destroy()
+        return it, rel, used
+
+    t_pc, (it_pc, rel_pc) = timed(pivchol)
+    t_l, (it_l, rel_l, used) = timed(lambda: learned(it_pc))
+    # learned without the judge's cap, to report its own iteration count
+    c = gdml.kernel_setup(R, w.sigma, w.lam)
+    c.precond_build_scored(sc.predict(c.descriptors()), k)
+    _, it_raw, rel_raw, _ = c.pcg_solve(yv, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
+    c.destroy()
+    c = gdml.kernel_setup(R, w.sigma, w.lam)
+    c.precond_build("uniform", k, seed=2)
+    _, it_u, rel_u, _ = c.pcg_solve(yv, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
+    c.destroy()
+    print(json.dumps({"suite": "learned", "workload": args.workload, "k": k, "train_systems": args.suite_count,
+                      "label_s": t_labels, "train_s": t_train, "train_loss": loss,
+                      "pivchol": {"s": t_pc, "iters": it_pc, "relres": rel_pc},
+                      "learned": {"s": t_l, "iters": it_l, "relres": rel_l, "used": used,
+                                  "iters_without_judge": it_raw, "relres_without_judge": rel_raw},
+                      "uniform": {"iters": it_u, "relres": rel_u}}), flush=True)
+    sc.destroy()
 
 
 def run_gpu(args):
@@ -413,6 +545,10 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.suite == "learned":
+        run_learned(a)
+    elif a.suite:
+        run_suite(a)
     elif a.only != "solve":
         run_op(a)
     else:

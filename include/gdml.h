@@ -60,7 +60,8 @@ typedef enum { GDML_FP64 = 0, GDML_TF32 = 1, GDML_BF16 = 2 } gdml_precision;
 typedef enum {
   GDML_SEL_UNIFORM = 0, /* k distinct columns, uniformly at random */
   GDML_SEL_RLS = 1,     /* sampled without replacement by estimated ridge leverage scores */
-  GDML_SEL_PIVCHOL = 2  /* incomplete Cholesky with greedy diagonal pivoting (Alg. 1) */
+  GDML_SEL_PIVCHOL = 2, /* incomplete Cholesky with greedy diagonal pivoting (Alg. 1) */
+  GDML_SEL_WEIGHTED = 3 /* sampled without replacement by given per-geometry scores (learned scorer) */
 } gdml_select;
 
 /* Build a context for one kernel system (Sec. 2.1, Eq. 1).
@@ -101,6 +102,25 @@ gdml_status gdml_matvec_fp64(gdml_ctx* ctx, const double* v_dev, double* out_dev
 gdml_status gdml_precond_build(gdml_ctx* ctx, int32_t method, int64_t k, uint64_t seed,
                                int64_t* pivots_dev, double* resid_trace_dev);
 
+/* Preconditioner from k columns sampled without replacement with weights
+ * w_i = max(score_a, 0) * K_ii for column i of geometry a (keys -ln(u_i)/w_i,
+ * Philox stream 3), then the Nystrom factor and Woodbury core exactly as for
+ * GDML_SEL_UNIFORM / GDML_SEL_RLS (Eqs. 3-5).  geometry_scores_dev: M doubles,
+ * e.g. a learned scorer's prediction of each geometry's ridge leverage mass
+ * (the paper samples by the leverage scores themselves, Sec. 3).
+ * Errors as gdml_precond_build. */
+gdml_status gdml_precond_build_scored(gdml_ctx* ctx, const double* geometry_scores_dev, int64_t k, uint64_t seed,
+                                      int64_t* pivots_dev);
+
+/* The Nystrom estimate of the ridge leverage scores tau_i = (K (K + lambda I)^-1)_ii
+ * (Sec. 3) that GDML_SEL_RLS samples by: pilot of k uniform columns (Philox
+ * stream 1), B = K_nS L_S^-T, tau_i = b_i^T (B^T B + lambda I)^-1 b_i.
+ * tau_dev: n doubles.  Invalidates any built preconditioner (rank 0). */
+gdml_status gdml_rls_scores(gdml_ctx* ctx, int64_t k, uint64_t seed, double* tau_dev);
+
+/* The inverse-distance descriptors x_a (M x D doubles, row a = geometry a). */
+gdml_status gdml_descriptors(const gdml_ctx* ctx, double* X_dev);
+
 /* Rank actually built by the last gdml_precond_build (pivchol may stop early),
  * and the jitter added to K_kk (0 if none).  Host outputs; either may be NULL. */
 gdml_status gdml_precond_info(const gdml_ctx* ctx, int64_t* rank_out, double* jitter_out);
@@ -133,6 +153,31 @@ gdml_status gdml_set_inner_rtol(gdml_ctx* ctx, double inner_rtol);
 /* Outer refinement steps of the last gdml_pcg_solve (1 for FP64 contexts). */
 gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
 
+/* Solve count independent systems (each set up by its own FP64 context, any
+ * sizes, sigma and lambda) with ONE CUDA graph launch per round: the graph
+ * holds, per system, a gate kernel and a conditional WHILE node whose body is
+ * that system's PCG iteration (Sec. 2.1, Eq. 2, as in gdml_pcg_solve), so the
+ * loops of all systems run concurrently on the device.  Between rounds the
+ * host recomputes each active system's TRUE FP64 residual and restarts the
+ * ones that drifted (at most 3 restarts, as gdml_pcg_solve).
+ *  ctxs, y_dev, alpha_dev: host arrays of count entries (device vectors of
+ *    each context's length n_i; alpha_dev holds x0 on entry, the solution on exit).
+ *  iters_out, relres_out (host arrays of count entries, may be NULL).
+ * All contexts must be FP64 contexts on the current device, each at most once.
+ * Synchronises every context's stream.  Errors: GDML_ERR_ARG,
+ * GDML_ERR_NOT_CONVERGED (some system above rtol), GDML_ERR_BREAKDOWN, GDML_ERR_CUDA. */
+gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const double* const* y_dev,
+                                   double* const* alpha_dev, double rtol, int32_t max_iter,
+                                   int32_t* iters_out, double* relres_out);
+
+/* Tile autotuner for the matvec of this context's shapes: times every
+ * power-of-two K-split (1 .. 8 or more) of the second descriptor contraction
+ * (FP64 DGEMM or tcgen05 GEMM) and keeps the fastest.  *choice_out (host, may
+ * be NULL) receives it so that a caller can cache it and restore it later with
+ * gdml_set_tuning.  Synchronises the context's stream. */
+gdml_status gdml_autotune(gdml_ctx* ctx, int32_t* choice_out);
+gdml_status gdml_set_tuning(gdml_ctx* ctx, int32_t splits);
+
 /* out = K v (+ lambda v if add_lambda) for M geometries R_dev (same layout as
  * gdml_kernel_setup), computed in FP64 WITHOUT a context and WITHOUT any device
  * allocation -- for callers that cannot call cudaMalloc: code that runs while
@@ -152,6 +197,26 @@ gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
  *  cuda_stream: a cudaStream_t or NULL. */
 gdml_status gdml_matvec_noalloc(const double* R_dev, int64_t M, int32_t N, double sigma, double lambda,
                                 const double* v_dev, double* out_dev, int32_t add_lambda, void* cuda_stream);
+
+/* Learned inducing-column scorer: a BF16 MLP D -> hidden -> hidden -> 1 with
+ * exact-erf GELU, FP32 master weights and accumulation, trained by Adam
+ * (beta 0.9 / 0.999) on mean-squared error.  Its per-geometry scores feed
+ * gdml_precond_build_scored; pivoted Cholesky (Alg. 1) stays the fallback and
+ * the judge (by PCG iteration count) of its selections.  The paper has no
+ * learned selection; its leverage-score sampling (Sec. 3) supplies the labels. */
+typedef struct gdml_scorer gdml_scorer;
+gdml_status gdml_scorer_create(gdml_scorer** s, int32_t D, int32_t hidden, uint64_t seed, void* cuda_stream);
+/* feature mean/std per column and label mean/std from training data X (B x D), y (B) */
+gdml_status gdml_scorer_fit_scaling(gdml_scorer* s, const double* X_dev, const double* y_dev, int64_t B);
+gdml_status gdml_scorer_train(gdml_scorer* s, const double* X_dev, const double* y_dev, int64_t B, int32_t epochs,
+                              int32_t batch, double lr, double* last_loss_out);
+gdml_status gdml_scorer_predict(gdml_scorer* s, const double* X_dev, int64_t B, double* out_dev);
+/* flat FP32 parameters [W1 (h x D) | b1 | W2 (h x h) | b2 | w3 | b3]: get (set = 0) or set (set = 1) */
+gdml_status gdml_scorer_params(gdml_scorer* s, float* params_dev, int32_t set, int64_t* nparam_out);
+/* loss (host) and its gradient w.r.t. the flat parameters (device) on one batch */
+gdml_status gdml_scorer_grad(gdml_scorer* s, const double* X_dev, const double* y_dev, int64_t B, double* loss_out,
+                             float* grad_dev);
+void gdml_scorer_destroy(gdml_scorer* s);
 
 /* Message describing the last error on ctx (or the last failed setup when
  * ctx is NULL).  Never NULL; valid until the next call on the context. */

@@ -1,6 +1,7 @@
 // C ABI of libgdml (declared in include/gdml.h): context, matvec,
 // preconditioner build / apply and the PCG solve.  Every step runs in the
 // kernels of this library; the host only sequences launches.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -52,8 +53,9 @@ struct gdml_ctx {
   double* T = nullptr;    // M*M
   double* tb = nullptr;   // M
   double* rowsum = nullptr;
-  double* U = nullptr;  // splitsU x M x D (split-K partials of the second contraction)
+  double* U = nullptr;  // splits_cap x M x D (split-K partials of the second contraction)
   int splitsU = 1;
+  int splits_cap = 1;
   double* diag = nullptr;  // n
   double* Xc() const { return V64 + M * D; }
   TcMatvec tc;  // tensor-core matvec state (TF32/BF16 contexts)
@@ -64,6 +66,7 @@ struct gdml_ctx {
   double* L = nullptr;    // n x k col-major
   double* LC = nullptr;   // k x k lower (row-major): Cholesky factor of C = lambda I + L^T L
   double* Cinv = nullptr; // k x k: C^-1 = L_C^-T L_C^-1 (formed once per build)
+  double* Cfull = nullptr; // k x k: C itself (for the refinement step of the apply)
   double* wpart = nullptr;
   double* wt = nullptr;
   int64_t cap_k = 0;
@@ -244,9 +247,14 @@ gdml_status nystrom(gdml_ctx* c, const int64_t* S, int64_t k, double* L, double*
 }
 
 // LC <- chol(lambda I + L^T L) (Eq. 4); with Cinv, also C^-1 = L_C^-T L_C^-1
-gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, double* Cinv = nullptr) {
+gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, double* Cinv = nullptr,
+                          double* Cfull = nullptr) {
   launch_dgemm<double, double>(true, k, k, c->n, 1.0, L, c->n, L, c->n, 0.0, LC, k, true, c->st);
   add_diag(LC, k, k, c->lam, c->st);
+  if (Cfull) {
+    CTRY(c, cudaMemcpyAsync(Cfull, LC, k * k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    mirror_lower(Cfull, k, c->st);
+  }
   CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
   cholesky_inplace(LC, k, c->status, c->st);
   TRY(check_launch(c, "woodbury_core"));
@@ -275,18 +283,36 @@ gdml_status ensure_precond_buffers(gdml_ctx* c, int64_t k) {
   dfree(c, c->wpart);
   dfree(c, c->wt);
   dfree(c, c->Cinv);
-  c->L = c->LC = c->wpart = c->wt = c->Cinv = nullptr;
+  dfree(c, c->Cfull);
+  c->L = c->LC = c->wpart = c->wt = c->Cinv = c->Cfull = nullptr;
   c->cap_k = 0;
   TRY(dalloc(c, &c->L, (size_t)(c->n * k)));
   TRY(dalloc(c, &c->LC, (size_t)(k * k)));
   TRY(dalloc(c, &c->Cinv, (size_t)(k * k)));
+  TRY(dalloc(c, &c->Cfull, (size_t)(k * k)));
   TRY(dalloc(c, &c->wpart, (size_t)woodbury_part_size(c->n, k)));
-  TRY(dalloc(c, &c->wt, (size_t)(2 * k)));
+  TRY(dalloc(c, &c->wt, (size_t)(3 * k)));
   c->cap_k = k;
   return GDML_OK;
 }
 
 
+
+// Nystrom estimate of the ridge leverage scores from a uniform pilot set of
+// size k (Philox stream 1): B = K_nS L_S^-T, tau_i = |L_C^-1 b_i|^2 with
+// L_C L_C^T = B^T B + lambda I (Sec. 3, "Leverage score sampling").
+// Overwrites the context's L / LC buffers (capacity >= k).
+gdml_status rls_estimate(gdml_ctx* c, int64_t k, uint64_t seed, int64_t* S, double* Kkk, double* work,
+                         uint64_t* key, int64_t* idx, double* tau) {
+  const int64_t n = c->n;
+  select_uniform(n, k, seed, 1u, key, idx, S, c->st);
+  double eps0 = 0.0;
+  TRY(nystrom(c, S, k, c->L, Kkk, work, &eps0));  // B (n x k col-major)
+  TRY(woodbury_core(c, c->L, k, c->LC));          // chol(B^T B + lambda I)
+  trsm_left_lower(c->LC, k, c->L, n, c->st);       // Z = L_C^-1 B^T
+  { col_sqnorm_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c->st>>>(c->L, k, n, tau); count_launch(); }
+  return check_launch(c, "rls scores");
+}
 
 // ------------------------------------------------------------------ PCG
 gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
@@ -294,7 +320,7 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
     CTRY(c, cudaMemcpyAsync(z, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GDML_OK;
   }
-  woodbury_apply<double>(c->L, c->n, c->k, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
+  woodbury_apply<double>(c->L, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
   return check_launch(c, "woodbury_apply");
 }
 
@@ -488,7 +514,8 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   TRY(dalloc(C, &c->tb, (size_t)M));
   TRY(dalloc(C, &c->rowsum, (size_t)M));
   c->splitsU = dgemm_splits(M, D, 2 * M);
-  TRY(dalloc(C, &c->U, (size_t)(c->splitsU * M * D)));
+  c->splits_cap = std::max(c->splitsU, 8);
+  TRY(dalloc(C, &c->U, (size_t)(c->splits_cap * M * D)));
   TRY(dalloc(C, &c->diag, (size_t)n));
   for (double** v : {&c->r, &c->z, &c->p, &c->q, &c->x, &c->ys}) TRY(dalloc(C, v, (size_t)n));
   TRY(dalloc(C, &c->sc, SC_COUNT));
@@ -528,12 +555,13 @@ gdml_status gdml_matvec_fp64(gdml_ctx* c, const double* v, double* out, int32_t 
   return matvec_fp64(c, v, out, add_lambda ? 1 : 0);
 }
 
-gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t seed, int64_t* pivots_dev,
-                               double* resid_trace_dev) {
+static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, uint64_t seed, int64_t* pivots_dev,
+                                      double* resid_trace_dev, const double* geometry_scores) {
   TRY(validate(c));
   const int64_t n = c->n;
   if (k < 1 || k > n || k > 16384) return ctx_fail(c, GDML_ERR_ARG, "need 1 <= k <= min(n, 16384)");
-  if (method < GDML_SEL_UNIFORM || method > GDML_SEL_PIVCHOL) return ctx_fail(c, GDML_ERR_ARG, "unknown method");
+  if (method < GDML_SEL_UNIFORM || method > GDML_SEL_WEIGHTED) return ctx_fail(c, GDML_ERR_ARG, "unknown method");
+  if (method == GDML_SEL_WEIGHTED && !geometry_scores) return ctx_fail(c, GDML_ERR_ARG, "scores are NULL");
   c->k = 0;
   c->jitter = 0.0;
   drop_graphs(c);
@@ -546,6 +574,11 @@ gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t 
   CTRY(c, cudaMemsetAsync(trace, 0, k * sizeof(double), c->st));
   CTRY(c, cudaMemsetAsync(S, 0xFF, k * sizeof(int64_t), c->st));
   int64_t rank = k;
+  double* weights = nullptr;
+  if (method == GDML_SEL_WEIGHTED) {
+    TRY(s.get(&weights, (size_t)n));
+    launch_column_weights(geometry_scores, c->diag, n, c->B, weights, c->st);
+  }
   if (method == GDML_SEL_PIVCHOL) {
     double* d = nullptr;
     int64_t* perm = nullptr;
@@ -602,29 +635,68 @@ gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t 
     TRY(s.get(&Kkk, (size_t)(k * k)));
     TRY(s.get(&work, (size_t)(k * k)));
     if (method == GDML_SEL_RLS) {
-      // pilot Nystrom estimate of the ridge leverage scores (pilot size k, Philox stream 1)
-      select_uniform(n, k, seed, 1u, key, idx, S, c->st);
-      double eps0 = 0.0;
-      TRY(nystrom(c, S, k, c->L, Kkk, work, &eps0));  // B (n x k col-major)
-      TRY(woodbury_core(c, c->L, k, c->LC));          // chol(B^T B + lambda I)
-      trsm_left_lower(c->LC, k, c->L, n, c->st);       // Z = L_C^-1 B^T
       double* tau = nullptr;
       TRY(s.get(&tau, (size_t)n));
-      { col_sqnorm_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c->st>>>(c->L, k, n, tau); count_launch(); }
-      TRY(check_launch(c, "rls scores"));
+      TRY(rls_estimate(c, k, seed, S, Kkk, work, key, idx, tau));
       select_weighted(n, k, seed, 2u, tau, key, idx, S, c->st);
+    } else if (method == GDML_SEL_WEIGHTED) {
+      select_weighted(n, k, seed, 3u, weights, key, idx, S, c->st);
     } else {
       select_uniform(n, k, seed, 0u, key, idx, S, c->st);
     }
     TRY(check_launch(c, "selection"));
     TRY(nystrom(c, S, k, c->L, Kkk, work, &c->jitter));
   }
-  TRY(woodbury_core(c, c->L, rank, c->LC, c->Cinv));
+  TRY(woodbury_core(c, c->L, rank, c->LC, c->Cinv, c->Cfull));
   if (pivots_dev) CTRY(c, cudaMemcpyAsync(pivots_dev, S, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st));
   if (resid_trace_dev)
     CTRY(c, cudaMemcpyAsync(resid_trace_dev, trace, k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   CTRY(c, cudaStreamSynchronize(c->st));
   c->k = rank;
+  return GDML_OK;
+}
+
+gdml_status gdml_precond_build(gdml_ctx* c, int32_t method, int64_t k, uint64_t seed, int64_t* pivots_dev,
+                               double* resid_trace_dev) {
+  if (method == GDML_SEL_WEIGHTED) return ctx_fail(c, GDML_ERR_ARG, "use gdml_precond_build_scored for scores");
+  return precond_build_impl(c, method, k, seed, pivots_dev, resid_trace_dev, nullptr);
+}
+
+gdml_status gdml_precond_build_scored(gdml_ctx* c, const double* geometry_scores_dev, int64_t k, uint64_t seed,
+                                      int64_t* pivots_dev) {
+  return precond_build_impl(c, GDML_SEL_WEIGHTED, k, seed, pivots_dev, nullptr, geometry_scores_dev);
+}
+
+gdml_status gdml_rls_scores(gdml_ctx* c, int64_t k, uint64_t seed, double* tau_dev) {
+  TRY(validate(c));
+  const int64_t n = c->n;
+  if (!tau_dev) return ctx_fail(c, GDML_ERR_ARG, "tau_dev is NULL");
+  if (k < 1 || k > n || k > 16384) return ctx_fail(c, GDML_ERR_ARG, "need 1 <= k <= min(n, 16384)");
+  c->k = 0;
+  drop_graphs(c);
+  TRY(ensure_precond_buffers(c, k));
+  Scratch s{c, {}};
+  int64_t* S = nullptr;
+  uint64_t* key = nullptr;
+  int64_t* idx = nullptr;
+  double *Kkk = nullptr, *work = nullptr;
+  const int64_t P = select_scratch_len(n);
+  TRY(s.get(&S, (size_t)k));
+  TRY(s.get(&key, (size_t)P));
+  TRY(s.get(&idx, (size_t)P));
+  TRY(s.get(&Kkk, (size_t)(k * k)));
+  TRY(s.get(&work, (size_t)(k * k)));
+  TRY(rls_estimate(c, k, seed, S, Kkk, work, key, idx, tau_dev));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  return GDML_OK;
+}
+
+gdml_status gdml_descriptors(const gdml_ctx* c, double* X_dev) {
+  TRY(validate(c));
+  if (!X_dev) return fail(GDML_ERR_ARG, "X_dev is NULL");
+  if (cudaMemcpyAsync(X_dev, c->X, c->M * c->D * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return fail(GDML_ERR_CUDA, "copying descriptors");
   return GDML_OK;
 }
 
@@ -740,6 +812,208 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
 }
 
 int64_t gdml_launch_count(void) { return launch_count(); }
+
+// Many independent FP64 systems, one CUDA graph: per system a gate kernel and a
+// conditional WHILE node whose body is that system's PCG iteration.  The
+// systems are independent branches of the graph, so their loops run
+// concurrently on the device; the host only prepares each round and checks
+// the true residuals between launches (restarting drifted systems).
+gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const double* const* y_dev,
+                                   double* const* alpha_dev, double rtol, int32_t max_iter, int32_t* iters_out,
+                                   double* relres_out) {
+  clear_msg();
+  if (!ctxs || !y_dev || !alpha_dev || count < 1) return fail(GDML_ERR_ARG, "batched solve: bad arguments");
+  if (!(rtol > 0.0) || max_iter < 1) return fail(GDML_ERR_ARG, "batched solve: need rtol > 0 and max_iter >= 1");
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || !y_dev[i] || !alpha_dev[i]) return fail(GDML_ERR_ARG, "batched solve: null entry");
+    if (ctxs[i]->precision != GDML_FP64) return fail(GDML_ERR_ARG, "batched solve: FP64 contexts only");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(GDML_ERR_ARG, "batched solve: a context appears twice");
+  }
+  std::vector<double> ynorm(count), res(count);
+  std::vector<int64_t> iters(count, 0);
+  std::vector<int> restarts(count, 0), active(count, 0);
+  // initial residuals
+  for (int i = 0; i < count; ++i) {
+    gdml_ctx* c = ctxs[i];
+    const int64_t n = c->n;
+    CTRY(c, cudaMemcpyAsync(c->ys, y_dev[i], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    CTRY(c, cudaMemcpyAsync(c->x, alpha_dev[i], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    TRY(dot(c, c->ys, c->ys, SC_YY));
+    TRY(matvec_any(c, c->x, c->r, 1, true));
+    launch_axpby(c->r, c->ys, 1.0, -1.0, n, c->st);
+    TRY(dot(c, c->r, c->r, SC_RR));
+  }
+  for (int i = 0; i < count; ++i) {
+    gdml_ctx* c = ctxs[i];
+    TRY(fetch_scalars(c));
+    ynorm[i] = std::sqrt(c->hsc[SC_YY]);
+    res[i] = std::sqrt(c->hsc[SC_RR]);
+  }
+  // one graph for all systems
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return fail(GDML_ERR_CUDA, "cudaGraphCreate");
+  std::vector<int64_t> body_n(count, 0);
+  gdml_status bs = GDML_OK;
+  for (int i = 0; i < count && bs == GDML_OK; ++i) {
+    gdml_ctx* c = ctxs[i];
+    if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      bs = fail(GDML_ERR_CUDA, "capture stream");
+      break;
+    }
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    // gate kernel node, then the WHILE node depending on it
+    cudaGraphNode_t gate_tail = nullptr;
+    if (e == cudaSuccess) e = add_pcg_gate_node(g, &gate_tail, c->sc, c->ictl, h);
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, &gate_tail, nullptr, 1, &prm);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(c->cap, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      bs = fail(GDML_ERR_CUDA, std::string("building the batched graph: ") + cudaGetErrorString(e));
+      break;
+    }
+    cudaStream_t user = c->st;
+    c->st = c->cap;
+    const int64_t before = launch_count();
+    bs = pcg_body(c, c->x, true, h);
+    body_n[i] = launch_count() - before;
+    count_launch(-body_n[i]);
+    c->st = user;
+    cudaGraph_t body = nullptr;
+    e = cudaStreamEndCapture(c->cap, &body);
+    if (bs == GDML_OK && e != cudaSuccess) bs = fail(GDML_ERR_CUDA, "capturing a batched PCG body");
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (bs == GDML_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess)
+    bs = fail(GDML_ERR_CUDA, "instantiating the batched graph");
+  cudaGraphDestroy(g);
+  if (bs != GDML_OK) {
+    (void)cudaGetLastError();
+    return bs;
+  }
+  cudaStream_t st0 = ctxs[0]->st;
+  gdml_status out = GDML_OK;
+  for (int round = 0; round < 4; ++round) {
+    int n_active = 0;
+    for (int i = 0; i < count; ++i) {
+      gdml_ctx* c = ctxs[i];
+      const double tol = rtol * ynorm[i];
+      active[i] = ynorm[i] > 0.0 && res[i] > tol && iters[i] < max_iter && restarts[i] <= 3;
+      c->hictl[IC_ITER] = 0;
+      c->hictl[IC_MAXIT] = active[i] ? max_iter - iters[i] : 0;
+      c->hsc[SC_TOL2] = tol * tol;
+      if (active[i]) {
+        ++n_active;
+        TRY(apply_precond(c, c->r, c->z));
+        CTRY(c, cudaMemcpyAsync(c->p, c->z, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        TRY(dot(c, c->r, c->z, SC_RHO));
+      }
+      CTRY(c, cudaMemcpyAsync(c->ictl, c->hictl, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+      CTRY(c, cudaMemcpyAsync(c->sc + SC_TOL2, c->hsc + SC_TOL2, sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+      CTRY(c, cudaStreamSynchronize(c->st));
+    }
+    if (!n_active) break;
+    CTRY(ctxs[0], cudaGraphLaunch(ex, st0));
+    CTRY(ctxs[0], cudaStreamSynchronize(st0));
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      gdml_ctx* c = ctxs[i];
+      int hst = 0;
+      CTRY(c, cudaMemcpyAsync(c->hictl, c->ictl, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st));
+      CTRY(c, cudaMemcpyAsync(&hst, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      TRY(fetch_scalars(c));
+      iters[i] += c->hictl[IC_ITER];
+      count_launch(c->hictl[IC_ITER] * body_n[i] + 1);
+      if (hst) {
+        out = ctx_fail(c, GDML_ERR_BREAKDOWN, "PCG breakdown in a batched system");
+        restarts[i] = 99;
+        continue;
+      }
+      TRY(matvec_any(c, c->x, c->r, 1, true));  // true FP64 residual
+      launch_axpby(c->r, c->ys, 1.0, -1.0, c->n, c->st);
+      TRY(dot(c, c->r, c->r, SC_RR));
+      TRY(fetch_scalars(c));
+      res[i] = std::sqrt(c->hsc[SC_RR]);
+      if (res[i] > rtol * ynorm[i]) ++restarts[i];
+    }
+  }
+  cudaGraphExecDestroy(ex);
+  bool all = true;
+  for (int i = 0; i < count; ++i) {
+    gdml_ctx* c = ctxs[i];
+    if (ynorm[i] == 0.0) {
+      CTRY(c, cudaMemsetAsync(alpha_dev[i], 0, c->n * sizeof(double), c->st));
+    } else {
+      CTRY(c, cudaMemcpyAsync(alpha_dev[i], c->x, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    }
+    CTRY(c, cudaStreamSynchronize(c->st));
+    const double rel = ynorm[i] > 0 ? res[i] / ynorm[i] : 0.0;
+    if (iters_out) iters_out[i] = (int32_t)iters[i];
+    if (relres_out) relres_out[i] = rel;
+    c->last_outer = 1;
+    if (rel > rtol) all = false;
+  }
+  if (out != GDML_OK) return out;
+  if (!all) return fail(GDML_ERR_NOT_CONVERGED, "batched solve: some systems did not reach rtol");
+  return GDML_OK;
+}
+
+// Tile autotuner: time the candidate K-splits of the matvec's second
+// contraction (FP64: DGEMM split-K; TF32/BF16: tcgen05 split-K) on this
+// context's shapes and keep the fastest.  *choice_out = chosen split count.
+gdml_status gdml_autotune(gdml_ctx* c, int32_t* choice_out) {
+  TRY(validate(c));
+  double* v = c->z;
+  double* out = c->q;
+  CTRY(c, cudaMemsetAsync(v, 0, c->n * sizeof(double), c->st));
+  cudaEvent_t e0, e1;
+  CTRY(c, cudaEventCreate(&e0));
+  CTRY(c, cudaEventCreate(&e1));
+  int best = 1;
+  float best_ms = 1e30f;
+  const int max_s = c->precision == GDML_FP64 ? c->splits_cap : c->tc.splits_cap;
+  for (int s = 1; s <= max_s; s *= 2) {
+    if (c->precision == GDML_FP64) c->splitsU = s;
+    else c->tc.splits2 = s;
+    for (int w = 0; w < 2; ++w) TRY(matvec_any(c, v, out, 1, false));
+    CTRY(c, cudaEventRecord(e0, c->st));
+    for (int w = 0; w < 5; ++w) TRY(matvec_any(c, v, out, 1, false));
+    CTRY(c, cudaEventRecord(e1, c->st));
+    CTRY(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = s;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (c->precision == GDML_FP64) c->splitsU = best;
+  else c->tc.splits2 = best;
+  drop_graphs(c);
+  if (choice_out) *choice_out = best;
+  return GDML_OK;
+}
+
+gdml_status gdml_set_tuning(gdml_ctx* c, int32_t splits) {
+  TRY(validate(c));
+  const int cap = c->precision == GDML_FP64 ? c->splits_cap : c->tc.splits_cap;
+  if (splits < 1 || splits > cap) return ctx_fail(c, GDML_ERR_ARG, "split count out of range");
+  if (c->precision == GDML_FP64) c->splitsU = splits;
+  else c->tc.splits2 = splits;
+  drop_graphs(c);
+  return GDML_OK;
+}
 
 gdml_status gdml_tc_check(gdml_ctx* c) {
   TRY(validate(c));

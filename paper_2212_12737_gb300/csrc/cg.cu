@@ -89,7 +89,26 @@ __global__ void pcg_check_kernel(const double* __restrict__ sc, int64_t* __restr
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
+// Entry test of a batched PCG loop: run the WHILE body only if this system
+// still has work (|r|^2 > tol^2 and iterations left).
+__global__ void pcg_gate_kernel(const double* __restrict__ sc, const int64_t* __restrict__ ictl,
+                                cudaGraphConditionalHandle h) {
+  const bool go = (sc[SC_RR] > sc[SC_TOL2]) && (ictl[IC_ITER] < ictl[IC_MAXIT]);
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------- launchers
+cudaError_t add_pcg_gate_node(cudaGraph_t g, cudaGraphNode_t* node, const double* sc, const int64_t* ictl,
+                              cudaGraphConditionalHandle h) {
+  void* args[] = {(void*)&sc, (void*)&ictl, (void*)&h};
+  cudaKernelNodeParams p = {};
+  p.func = (void*)pcg_gate_kernel;
+  p.gridDim = dim3(1);
+  p.blockDim = dim3(1);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, nullptr, 0, &p);
+}
 void launch_pcg_check(const double* sc, int64_t* ictl, const int* status, cudaGraphConditionalHandle h,
                       cudaStream_t st) {
   { pcg_check_kernel<<<1, 1, 0, st>>>(sc, ictl, status, h); count_launch(); }

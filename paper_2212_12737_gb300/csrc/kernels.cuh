@@ -43,10 +43,11 @@ void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cud
 void add_diag(double* A, int64_t lda, int64_t k, double eps, cudaStream_t st);
 
 // woodbury.cu
-// t must hold 2k doubles (t and u = C^-1 t)
+// C: full symmetric k x k (lambda I + L^T L); t must hold 3k doubles (t, u = C^-1 t, residual)
 template <typename TL>
-void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* Cinv, double lam, const double* r,
-                    double* z, double* part, double* t, cudaStream_t st);
+void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
+                    const double* r, double* z, double* part, double* t, cudaStream_t st);
+void mirror_lower(double* A, int64_t k, cudaStream_t st);
 void transpose_square(const double* A, int64_t k, double* At, cudaStream_t st);
 void set_identity(double* A, int64_t k, cudaStream_t st);
 int64_t woodbury_part_size(int64_t n, int64_t k);
@@ -61,6 +62,8 @@ void launch_copy_scalar(double* sc, int dst, int src, cudaStream_t st);
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
 void launch_pcg_check(const double* sc, int64_t* ictl, const int* status, cudaGraphConditionalHandle h,
                       cudaStream_t st);
+cudaError_t add_pcg_gate_node(cudaGraph_t g, cudaGraphNode_t* node, const double* sc, const int64_t* ictl,
+                              cudaGraphConditionalHandle h);
 
 // select.cu
 int64_t select_scratch_len(int64_t n);
@@ -68,6 +71,10 @@ void select_uniform(int64_t n, int64_t k, uint64_t seed, uint32_t stream, uint64
                     int64_t* out, cudaStream_t st);
 void select_weighted(int64_t n, int64_t k, uint64_t seed, uint32_t stream, const double* tau, uint64_t* key,
                      int64_t* idx, int64_t* out, cudaStream_t st);
+
+// mlp.cu
+void launch_column_weights(const double* score, const double* diag, int64_t n, int B3, double* w, cudaStream_t st);
+void launch_destandardize(const float* out, int64_t B, float ym, float ysd, double* dst, cudaStream_t st);
 
 // pivchol.cu
 struct PivState {

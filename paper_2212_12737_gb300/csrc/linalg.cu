@@ -156,6 +156,18 @@ void transpose_square(const double* A, int64_t k, double* At, cudaStream_t st) {
   { transpose_square_kernel<<<grid, dim3(32, 8), 0, st>>>(A, k, At); count_launch(); }
 }
 
+// A[c][r] = A[r][c] for r > c (copy the lower triangle onto the upper one)
+__global__ void mirror_lower_kernel(double* A, int64_t k) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  const int64_t r = e / k, c = e % k;
+  if (r > c) A[c * k + r] = A[e];
+}
+
+void mirror_lower(double* A, int64_t k, cudaStream_t st) {
+  { mirror_lower_kernel<<<(unsigned)cdiv(k * k, 256), 256, 0, st>>>(A, k); count_launch(); }
+}
+
 void set_identity(double* A, int64_t k, cudaStream_t st) {
   { set_identity_kernel<<<(unsigned)cdiv(k * k, 256), 256, 0, st>>>(A, k); count_launch(); }
 }

@@ -296,7 +296,8 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
   const int64_t tiles = cdiv(tc.Dp, tc.bn2) * cdiv(M, BM);
   const int64_t num_kb2 = tc.K2p / span;
   tc.splits2 = (int)std::max<int64_t>(1, std::min<int64_t>(num_kb2 / 4, kNumSMs / std::max<int64_t>(tiles, 1)));
-  TC_TRY(tc_alloc(tc, &tc.U, (size_t)(tc.splits2 * M * tc.Dp)));
+  tc.splits_cap = std::max(tc.splits2, 8);
+  TC_TRY(tc_alloc(tc, &tc.U, (size_t)(tc.splits_cap * M * tc.Dp)));
   if (cudaMemsetAsync(xc, 0, M * tc.Dp * sizeof(T), st) != cudaSuccess ||
       cudaMemsetAsync(w, 0, M * tc.Dp * sizeof(T), st) != cudaSuccess ||
       cudaMemsetAsync(p, 0, M * tc.K2p * sizeof(T), st) != cudaSuccess ||

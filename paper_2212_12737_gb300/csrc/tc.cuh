@@ -31,7 +31,7 @@ struct TcMatvec {
   double* rs_part = nullptr;  // rowsum partials: ceil(M/32) x M
   double* tb = nullptr;       // t_b = xc~_b . w~_b
   int* err = nullptr;
-  int bn2 = 256, splits2 = 1;
+  int bn2 = 256, splits2 = 1, splits_cap = 1;
   std::vector<void*> allocs;
   CUtensorMap mapXc, mapW, mapP, mapVt;
 };

@@ -2,7 +2,7 @@
 //   z = lambda^-1 [ r - L_k C^-1 L_k^T r ],  C = lambda I + L_k^T L_k.
 // C^-1 is formed once per build from the FP64 Cholesky factor of C
 // (C^-1 = L_C^-T L_C^-1), so the apply is three data-parallel passes:
-//   t = L_k^T r,  u = C^-1 t,  z = (r - L_k u) / lambda
+//   t = L_k^T r,  u = C^-1 t (+ one refinement step),  z = (r - L_k u) / lambda
 // instead of two latency-bound triangular solves per CG iteration.  L_k is
 // stored column-major (n x k, column j at L + j*n) in FP64, or in FP32 for the
 // mixed-precision contexts; all arithmetic is FP64.  Two HBM passes over L_k.
@@ -84,22 +84,56 @@ __global__ void __launch_bounds__(256) gemv_n_update_kernel(const TL* __restrict
   if (q == 0 && i < n) z[i] = (r[i] - ((part[0][rr] + part[1][rr]) + (part[2][rr] + part[3][rr]))) * inv_lam;
 }
 
+// e = t - C u (one warp per row)
+__global__ void __launch_bounds__(256) residual_kernel(const double* __restrict__ C, int64_t k,
+                                                       const double* __restrict__ t, const double* __restrict__ u,
+                                                       double* __restrict__ e) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= k) return;
+  const double* row = C + i * k;
+  double s = 0.0;
+  for (int64_t j = lane; j < k; j += 32) s = fma(row[j], u[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) e[i] = t[i] - s;
+}
+
+// u += C^-1 e
+__global__ void __launch_bounds__(256) symv_add_kernel(const double* __restrict__ A, int64_t k,
+                                                       const double* __restrict__ e, double* __restrict__ u) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= k) return;
+  const double* row = A + i * k;
+  double s = 0.0;
+  for (int64_t j = lane; j < k; j += 32) s = fma(row[j], e[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) u[i] += s;
+}
+
 template <typename TL>
-void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* Cinv, double lam, const double* r,
-                    double* z, double* part, double* t, cudaStream_t st) {
+void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
+                    const double* r, double* z, double* part, double* t, cudaStream_t st) {
   const int64_t nchunks = cdiv(n, kRowsPerChunk);
   dim3 g1((unsigned)cdiv(k, kColsPerCta), (unsigned)nchunks);
   double* u = t + k;
+  double* e = t + 2 * k;
+  const unsigned gk = (unsigned)cdiv(k, 8);
   { gemv_t_partial_kernel<TL><<<g1, 256, 0, st>>>(L, n, k, r, part); count_launch(); }
   { reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
-  { symv_kernel<<<(unsigned)cdiv(k, 8), 256, 0, st>>>(Cinv, k, t, u); count_launch(); }
+  // u = C^-1 t, refined once with the FP64 residual t - C u: the explicit inverse
+  // alone is accurate only to ~cond(C) eps; one step restores the accuracy of a
+  // backward-stable solve at the cost of two more k x k passes
+  { symv_kernel<<<gk, 256, 0, st>>>(Cinv, k, t, u); count_launch(); }
+  { residual_kernel<<<gk, 256, 0, st>>>(C, k, t, u, e); count_launch(); }
+  { symv_add_kernel<<<gk, 256, 0, st>>>(Cinv, k, e, u); count_launch(); }
   { gemv_n_update_kernel<TL><<<(unsigned)cdiv(n, 64), 256, 0, st>>>(L, n, k, u, r, 1.0 / lam, z); count_launch(); }
 }
 
-template void woodbury_apply<double>(const double*, int64_t, int64_t, const double*, double, const double*,
-                                     double*, double*, double*, cudaStream_t);
-template void woodbury_apply<float>(const float*, int64_t, int64_t, const double*, double, const double*,
-                                    double*, double*, double*, cudaStream_t);
+template void woodbury_apply<double>(const double*, int64_t, int64_t, const double*, const double*, double,
+                                     const double*, double*, double*, double*, cudaStream_t);
+template void woodbury_apply<float>(const float*, int64_t, int64_t, const double*, const double*, double,
+                                    const double*, double*, double*, double*, cudaStream_t);
 
 int64_t woodbury_part_size(int64_t n, int64_t k) { return cdiv(n, kRowsPerChunk) * k; }
 

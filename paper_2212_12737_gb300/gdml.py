@@ -21,12 +21,15 @@ _lib = None
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 5: "ERR_BREAKDOWN",
           6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
 PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
-SELECT = {"uniform": 0, "rls": 1, "pivchol": 2}
+SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3}
 
 EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
            "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_tc_check",
-           "gdml_launch_count", "gdml_matvec_noalloc"]
+           "gdml_launch_count", "gdml_matvec_noalloc", "gdml_pcg_solve_batched", "gdml_autotune",
+           "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
+           "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
+           "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy"]
 
 
 class GdmlError(RuntimeError):
@@ -65,6 +68,19 @@ def load() -> ctypes.CDLL:
         "gdml_tc_check": [P],
         "gdml_launch_count": [],
         "gdml_matvec_noalloc": [P, I64, I32, D, D, P, P, I32, P],
+        "gdml_pcg_solve_batched": [P, I32, P, P, D, I32, P, P],
+        "gdml_autotune": [P, ctypes.POINTER(I32)],
+        "gdml_set_tuning": [P, I32],
+        "gdml_precond_build_scored": [P, P, I64, U64, P],
+        "gdml_rls_scores": [P, I64, U64, P],
+        "gdml_descriptors": [P, P],
+        "gdml_scorer_create": [ctypes.POINTER(P), I32, I32, U64, P],
+        "gdml_scorer_fit_scaling": [P, P, P, I64],
+        "gdml_scorer_train": [P, P, P, I64, I32, I32, D, ctypes.POINTER(D)],
+        "gdml_scorer_predict": [P, P, I64, P],
+        "gdml_scorer_params": [P, P, I32, ctypes.POINTER(I64)],
+        "gdml_scorer_grad": [P, P, P, I64, ctypes.POINTER(D), P],
+        "gdml_scorer_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -72,6 +88,7 @@ def load() -> ctypes.CDLL:
         f.restype = ctypes.c_int
     lib.gdml_last_error.restype = ctypes.c_char_p
     lib.gdml_destroy.restype = None
+    lib.gdml_scorer_destroy.restype = None
     lib.gdml_launch_count.restype = ctypes.c_int64
     _lib = lib
     return lib
@@ -128,6 +145,22 @@ class Context:
         self._check(load().gdml_precond_build(self._h, SELECT[method], int(k), int(seed), _ptr(piv), _ptr(tr)))
         return piv, tr
 
+    def precond_build_scored(self, geometry_scores: torch.Tensor, k: int, seed: int = 2, pivots: bool = False):
+        piv = torch.empty(k, dtype=torch.int64, device=self.device) if pivots else None
+        self._check(load().gdml_precond_build_scored(self._h, _ptr(geometry_scores.contiguous()), int(k), int(seed),
+                                                     _ptr(piv)))
+        return piv
+
+    def rls_scores(self, k: int, seed: int = 2) -> torch.Tensor:
+        tau = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        self._check(load().gdml_rls_scores(self._h, int(k), int(seed), _ptr(tau)))
+        return tau
+
+    def descriptors(self) -> torch.Tensor:
+        X = torch.empty(self.M, self.N * (self.N - 1) // 2, dtype=torch.float64, device=self.device)
+        self._check(load().gdml_descriptors(self._h, _ptr(X)))
+        return X
+
     def precond_info(self):
         r = ctypes.c_int64()
         j = ctypes.c_double()
@@ -156,6 +189,30 @@ class Context:
         if st != 0 and (raise_on_nonconvergence or st != 6):
             self._check(st)
         return alpha, int(it.value), float(rel.value), int(outer.value)
+
+    def autotune(self, cache: str | None = None) -> int:
+        """Pick the fastest K-split of the matvec's second contraction for this
+        context's shapes; with a cache file, reuse / record the choice there."""
+        import json
+        key = f"M{self.M}_N{self.N}_{self.precision}"
+        table = {}
+        if cache and os.path.exists(cache):
+            try:
+                table = json.load(open(cache))
+            except ValueError:
+                table = {}
+        if key in table:
+            self._check(load().gdml_set_tuning(self._h, int(table[key])))
+            return int(table[key])
+        ch = ctypes.c_int32()
+        self._check(load().gdml_autotune(self._h, ctypes.byref(ch)))
+        if cache:
+            table[key] = int(ch.value)
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return int(ch.value)
 
     def tc_check(self):
         """Raise if a tensor-core pipeline wait timed out since the last check."""
@@ -228,3 +285,118 @@ def matvec_noalloc(R: torch.Tensor, sigma: float, lam: float, v: torch.Tensor, o
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())
     return out
+
+
+def pcg_solve_batched(ctxs, ys, alphas=None, rtol: float = 1e-8, max_iter: int = 20000,
+                      raise_on_nonconvergence: bool = True):
+    """Solve many FP64 systems with one CUDA graph launch per round.
+    Returns (alphas, iterations list, relative residual list)."""
+    lib = load()
+    n = len(ctxs)
+    if alphas is None:
+        alphas = [torch.zeros(c.n, dtype=torch.float64, device=c.device) for c in ctxs]
+    H = (ctypes.c_void_p * n)(*[c._h for c in ctxs])
+    Y = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    A = (ctypes.c_void_p * n)(*[a.data_ptr() for a in alphas])
+    it = (ctypes.c_int32 * n)()
+    rel = (ctypes.c_double * n)()
+    st = lib.gdml_pcg_solve_batched(H, n, Y, A, float(rtol), int(max_iter), it, rel)
+    if st != 0 and (raise_on_nonconvergence or st != 6):
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+    return alphas, list(it), list(rel)
+
+
+class Scorer:
+    """Learned inducing-column scorer (BF16 MLP D -> hidden -> hidden -> 1, GELU)."""
+
+    def __init__(self, D: int, hidden: int = 256, seed: int = 0, device=None):
+        lib = load()
+        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        st = lib.gdml_scorer_create(ctypes.byref(h), int(D), int(hidden), int(seed),
+                                    ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+        if st != 0:
+            raise GdmlError(st, lib.gdml_last_error(None).decode())
+        self._h = h
+        self.D, self.hidden = D, hidden
+
+    def _check(self, st):
+        if st != 0:
+            raise GdmlError(st, load().gdml_last_error(None).decode())
+
+    def fit_scaling(self, X, y):
+        self._check(load().gdml_scorer_fit_scaling(self._h, _ptr(X.contiguous()), _ptr(y.contiguous()), X.shape[0]))
+
+    def train(self, X, y, epochs=200, batch=256, lr=1e-3) -> float:
+        loss = ctypes.c_double()
+        self._check(load().gdml_scorer_train(self._h, _ptr(X.contiguous()), _ptr(y.contiguous()), X.shape[0],
+                                             int(epochs), int(batch), float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def predict(self, X) -> torch.Tensor:
+        out = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+        self._check(load().gdml_scorer_predict(self._h, _ptr(X.contiguous()), X.shape[0], _ptr(out)))
+        return out
+
+    def nparam(self) -> int:
+        n = ctypes.c_int64()
+        self._check(load().gdml_scorer_params(self._h, None, 0, ctypes.byref(n)))
+        return int(n.value)
+
+    def params(self) -> torch.Tensor:
+        p = torch.empty(self.nparam(), dtype=torch.float32, device=self.device)
+        self._check(load().gdml_scorer_params(self._h, _ptr(p), 0, None))
+        return p
+
+    def set_params(self, p: torch.Tensor):
+        self._check(load().gdml_scorer_params(self._h, _ptr(p.contiguous()), 1, None))
+
+    def grad(self, X, y):
+        g = torch.empty(self.nparam(), dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double()
+        self._check(load().gdml_scorer_grad(self._h, _ptr(X.contiguous()), _ptr(y.contiguous()), X.shape[0],
+                                            ctypes.byref(loss), _ptr(g)))
+        return float(loss.value), g
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            load().gdml_scorer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def geometry_labels(ctx: Context, k: int, seed: int = 2) -> torch.Tensor:
+    """Per-geometry ridge-leverage mass: the sum of the estimated scores of the
+    geometry's 3N columns (the training label of the learned scorer)."""
+    tau = ctx.rls_scores(k, seed)
+    return tau.view(ctx.M, 3 * ctx.N).sum(dim=1)
+
+
+def solve_learned(ctx: Context, scorer: Scorer, y, k: int, seed: int = 2, rtol: float = 1e-8,
+                  max_iter: int = 20000, judge_iters: int | None = None):
+    """Learned selection with pivoted Cholesky (Alg. 1) as fallback and judge:
+    build from the scorer's per-geometry scores; fall back to Alg. 1 if the
+    inducing block is not SPD, or if PCG needs more than 1.5x the iterations of
+    the Alg. 1 preconditioner (judge_iters; measured here when not given).
+    Returns (alpha, iterations, relres, used) with used in {"learned", "pivchol"}."""
+    scores = scorer.predict(ctx.descriptors())
+    try:
+        ctx.precond_build_scored(scores, k, seed)
+    except GdmlError as e:
+        if e.name != "ERR_NOT_SPD":
+            raise
+        ctx.precond_build("pivchol", k)
+        a, it, rel, _ = ctx.pcg_solve(y, rtol=rtol, max_iter=max_iter)
+        return a, it, rel, "pivchol"
+    cap = max_iter if judge_iters is None else min(max_iter, int(1.5 * judge_iters) + 1)
+    a, it, rel, _ = ctx.pcg_solve(y, rtol=rtol, max_iter=cap, raise_on_nonconvergence=False)
+    if rel <= rtol and (judge_iters is None or it <= 1.5 * judge_iters):
+        return a, it, rel, "learned"
+    ctx.precond_build("pivchol", k)
+    a, it2, rel2, _ = ctx.pcg_solve(y, rtol=rtol, max_iter=max_iter)
+    return a, it + it2, rel2, "pivchol"

@@ -126,14 +126,15 @@ def workload(name: str, **override) -> Workload:
     return make_workload(name, **cfg)
 
 
-def batched_suite(count: int = 64, seed: int = 42) -> list[Workload]:
-    """Many uneven systems: N in {9,12,15,21,42}, M in [100, 2000],
+def batched_suite(count: int = 64, seed: int = 42, mmax: int = 2000) -> list[Workload]:
+    """Many uneven systems: N in {9,12,15,21,42}, M in [100, mmax] (2000 by default),
     sigma in {5,10,20,40}, lambda in {1e-10, 1e-8}, uniform k = M // 10."""
     rng = np.random.default_rng([seed, 0xBA7])
     out = []
     for s in range(count):
         N = int(rng.choice([9, 12, 15, 21, 42]))
         M = int(rng.integers(100, 2001))
+        M = 100 + (M - 100) * (mmax - 100) // 1900 if mmax < 2000 else M
         sigma = float(rng.choice([5.0, 10.0, 20.0, 40.0]))
         lam = float(rng.choice([1e-10, 1e-8]))
         out.append(make_workload(f"batch{s}", N, M, 0.05, sigma, lam, max(1, M // 10), "uniform",
