@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gdml", choices=["gdml", "reference"])
     ap.add_argument("--workload", default="aspirin21_m1000")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison solves")
     ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply"],
@@ -392,6 +392,11 @@ def run_gpu(args):
     peaks = measured_peaks()
     if args.precision == "fp64":
         peak, peak_src, bound = torch_peak(torch.float64), "of measured (torch FP64 matmul 4096^3, this run)", "alu"
+    elif args.precision == "df64":
+        # double-float on the FP32 lanes: ~15 FP32 operations per multiply-add;
+        # roofline = measured FP32 SIMT matmul rate x 2 flop / 15 ops
+        peak = torch_peak(torch.float32, tf32=False, size=8192) * 2.0 / 15.0
+        peak_src, bound = "of derived (torch FP32 SIMT matmul 8192^3 this run x 2/15 ops per double-float FMA)", "alu"
     elif args.precision == "tf32":
         peak, peak_src, bound = torch_peak(torch.float32, tf32=True, size=8192), \
             "of measured (torch TF32 matmul 8192^3, this run)", "tensor"
@@ -401,7 +406,7 @@ def run_gpu(args):
 
     forms = {}
     if not args.no_forms and rank == 0:
-        for prec in ("fp64", "tf32", "bf16"):
+        for prec in ("fp64", "df64", "tf32", "bf16"):
             if prec == args.precision:
                 forms[prec] = {"s": t_dev, "iters": iters, "relres": rel, "converged": rel <= RTOL,
                                "outer": outer, "matvec_ms": mv_sec * 1e3, "matvec_tflops": mv_tf}

@@ -54,7 +54,13 @@ typedef enum {
  * tcgen05 tensor cores (TF32 or BF16 operands, FP32 accumulation); PCG then
  * runs as the inner solver of an FP64 iterative refinement whose residual
  * y - K_lambda alpha is recomputed with the FP64 matvec. */
-typedef enum { GDML_FP64 = 0, GDML_TF32 = 1, GDML_BF16 = 2 } gdml_precision;
+/* DF64: the two descriptor contractions run in double-float arithmetic on
+ * the FP32 lanes (each FP64 operand split into two floats, exact products by
+ * FMA, (hi, lo) accumulation by TwoSum; ~2^-46 relative per term), i.e.
+ * FP64-class accuracy at the FP32 rate.  PCG uses it inside the loop and
+ * recomputes the TRUE residual with the FP64 matvec, restarting (refining)
+ * from the current iterate until it converges (at most 10 restarts). */
+typedef enum { GDML_FP64 = 0, GDML_TF32 = 1, GDML_BF16 = 2, GDML_DF64 = 3 } gdml_precision;
 
 /* Inducing-column selection rule (Sec. 3, "Column selection strategies"). */
 typedef enum {
@@ -163,7 +169,7 @@ gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
  *  ctxs, y_dev, alpha_dev: host arrays of count entries (device vectors of
  *    each context's length n_i; alpha_dev holds x0 on entry, the solution on exit).
  *  iters_out, relres_out (host arrays of count entries, may be NULL).
- * All contexts must be FP64 contexts on the current device, each at most once.
+ * All contexts must be FP64 or DF64 contexts on the current device, each at most once.
  * Synchronises every context's stream.  Errors: GDML_ERR_ARG,
  * GDML_ERR_NOT_CONVERGED (some system above rtol), GDML_ERR_BREAKDOWN, GDML_ERR_CUDA. */
 gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const double* const* y_dev,

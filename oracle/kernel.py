@@ -156,6 +156,28 @@ def matvec(R: np.ndarray, sigma: float, v: np.ndarray, lam: float = 0.0) -> np.n
     return out + lam * np.asarray(v, dtype=np.float64)
 
 
+def matvec_rows(R: np.ndarray, sigma: float, v: np.ndarray, rows, lam: float = 0.0) -> np.ndarray:
+    """Blocks a in `rows` of (K + lam I) v, from the same definition as matvec
+    (all w_b = J_b v_b are needed, but only the H_ab of the sampled a).
+    Returns an array of shape (len(rows), 3N)."""
+    M, N, _ = R.shape
+    B = 3 * N
+    c = np.sqrt(5.0) / sigma
+    X, _ = descriptor(R)
+    Jac = jacobian(R)
+    V = np.asarray(v, dtype=np.float64).reshape(M, B)
+    W = np.einsum("apk,ak->ap", Jac, V)
+    out = np.empty((len(rows), B))
+    for t, a in enumerate(rows):
+        d = X[a][None, :] - X
+        r = np.sqrt(np.sum(d * d, axis=1))
+        S = (c * c / 3.0) * np.exp(-c * r)
+        proj = np.sum(d * W, axis=1)
+        u = (S * (1.0 + c * r)) @ W - c * c * ((S * proj) @ d)
+        out[t] = Jac[a].T @ u + lam * V[a]
+    return out
+
+
 def descriptor_distances(R: np.ndarray) -> np.ndarray:
     """r_ab = |x_a - x_b| computed directly from differences (M x M)."""
     X, _ = descriptor(R)

@@ -64,6 +64,7 @@ struct gdml_ctx {
   int64_t k = 0;  // rank built (0: none)
   double jitter = 0;
   double* L = nullptr;    // n x k col-major
+  float* Lf = nullptr;    // n x k col-major FP32 copy used by DF64 contexts
   double* LC = nullptr;   // k x k lower (row-major): Cholesky factor of C = lambda I + L^T L
   double* Cinv = nullptr; // k x k: C^-1 = L_C^-T L_C^-1 (formed once per build)
   double* Cfull = nullptr; // k x k: C itself (for the refinement step of the apply)
@@ -150,8 +151,24 @@ gdml_status matvec_fp64(gdml_ctx* c, const double* v, double* out, int add_lambd
   return check_launch(c, "matvec_fp64");
 }
 
+// Same steps as matvec_fp64 with both contractions in double-float arithmetic.
+gdml_status matvec_df(gdml_ctx* c, const double* v, double* out, int add_lambda) {
+  const int64_t M = c->M;
+  const int D = c->D;
+  cudaStream_t st = c->st;
+  double* W = c->V64;
+  launch_proj(c->G, c->Xc(), v, M, c->N, D, W, D, c->tb, st);
+  launch_dfgemm(true, M, M, D, c->Xc(), D, W, D, c->T, M, st);
+  launch_beta(c->T, c->S, c->tb, M, c->c, c->P64 + M, 2 * M, c->rowsum, st);
+  launch_dfgemm(false, M, D, 2 * M, c->P64, 2 * M, c->V64, D, c->U, D, st, c->splitsU, M * D);
+  launch_backproj<double>(c->U, D, c->splitsU, M * D, c->rowsum, c->Xc(), c->G, v, M, c->N, D, c->lam, add_lambda,
+                          out, st);
+  return check_launch(c, "matvec_df");
+}
+
 gdml_status matvec_any(gdml_ctx* c, const double* v, double* out, int add_lambda, bool force_fp64) {
   if (force_fp64 || c->precision == GDML_FP64) return matvec_fp64(c, v, out, add_lambda);
+  if (c->precision == GDML_DF64) return matvec_df(c, v, out, add_lambda);
   gdml_status s = tc_matvec(c->tc, c->G, v, out, add_lambda, c->lam, c->st);
   if (s != GDML_OK) return ctx_fail(c, s, "tensor-core matvec: " + last_msg());
   return check_launch(c, "matvec_tc");
@@ -248,8 +265,11 @@ gdml_status nystrom(gdml_ctx* c, const int64_t* S, int64_t k, double* L, double*
 
 // LC <- chol(lambda I + L^T L) (Eq. 4); with Cinv, also C^-1 = L_C^-T L_C^-1
 gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, double* Cinv = nullptr,
-                          double* Cfull = nullptr) {
-  launch_dgemm<double, double>(true, k, k, c->n, 1.0, L, c->n, L, c->n, 0.0, LC, k, true, c->st);
+                          double* Cfull = nullptr, const float* Lf = nullptr) {
+  if (Lf)  // DF64: C from the FP32-stored factor, exact products, double-float sums
+    launch_dfsyrk(k, c->n, Lf, c->n, LC, k, c->st);
+  else
+    launch_dgemm<double, double>(true, k, k, c->n, 1.0, L, c->n, L, c->n, 0.0, LC, k, true, c->st);
   add_diag(LC, k, k, c->lam, c->st);
   if (Cfull) {
     CTRY(c, cudaMemcpyAsync(Cfull, LC, k * k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
@@ -284,9 +304,12 @@ gdml_status ensure_precond_buffers(gdml_ctx* c, int64_t k) {
   dfree(c, c->wt);
   dfree(c, c->Cinv);
   dfree(c, c->Cfull);
+  dfree(c, c->Lf);
   c->L = c->LC = c->wpart = c->wt = c->Cinv = c->Cfull = nullptr;
+  c->Lf = nullptr;
   c->cap_k = 0;
   TRY(dalloc(c, &c->L, (size_t)(c->n * k)));
+  if (c->precision == GDML_DF64) TRY(dalloc(c, &c->Lf, (size_t)(c->n * k)));
   TRY(dalloc(c, &c->LC, (size_t)(k * k)));
   TRY(dalloc(c, &c->Cinv, (size_t)(k * k)));
   TRY(dalloc(c, &c->Cfull, (size_t)(k * k)));
@@ -320,7 +343,10 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
     CTRY(c, cudaMemcpyAsync(z, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GDML_OK;
   }
-  woodbury_apply<double>(c->L, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
+  if (c->precision == GDML_DF64)
+    woodbury_apply_df(c->Lf, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
+  else
+    woodbury_apply<double>(c->L, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
   return check_launch(c, "woodbury_apply");
 }
 
@@ -488,7 +514,7 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   if (M < 1 || N < 2 || N > 128) return fail(GDML_ERR_ARG, "need M >= 1 and 2 <= N <= 128");
   if (!(sigma > 0.0) || !(lambda > 0.0) || !std::isfinite(sigma) || !std::isfinite(lambda))
     return fail(GDML_ERR_ARG, "need sigma > 0 and lambda > 0");
-  if (precision < GDML_FP64 || precision > GDML_BF16) return fail(GDML_ERR_ARG, "unknown precision");
+  if (precision < GDML_FP64 || precision > GDML_DF64) return fail(GDML_ERR_ARG, "unknown precision");
   std::unique_ptr<gdml_ctx, void (*)(gdml_ctx*)> c(new gdml_ctx(), &gdml_destroy);
   CTRY(c.get(), cudaGetDevice(&c->device));
   c->st = static_cast<cudaStream_t>(cuda_stream);
@@ -534,7 +560,7 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   launch_dist_tab(c->X, M, (int)D, c->c, c->S, c->P64, 2 * M, c->st);
   launch_kdiag(c->G, M, N, (int)D, c->c, c->diag, c->st);
   TRY(check_launch(C, "setup kernels"));
-  if (precision != GDML_FP64) {
+  if (precision == GDML_TF32 || precision == GDML_BF16) {
     gdml_status s = tc_setup(c->tc, precision, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->c, c->st);
     if (s != GDML_OK) return ctx_fail(C, s, "tensor-core setup: " + last_msg());
   }
@@ -601,7 +627,7 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     CTRY(c, cudaMemsetAsync(chosen, 0, n, c->st));
     CTRY(c, cudaMemsetAsync(ps, 0, sizeof(PivState), c->st));
     CTRY(c, cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->st));
-    CTRY(c, cudaMemsetAsync(c->L, 0, n * k * sizeof(double), c->st));
+    if (c->precision != GDML_DF64) CTRY(c, cudaMemsetAsync(c->L, 0, n * k * sizeof(double), c->st));
     PivCholArgs a;
     a.n = n;
     a.k = k;
@@ -617,7 +643,12 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     a.get_col = [c](const int64_t* cols, double* out, const int* stop, cudaStream_t st) {
       launch_kcol(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, stop, st);
     };
-    pivchol_run<double>(a, c->L, c->st);
+    if (c->precision == GDML_DF64) {
+      CTRY(c, cudaMemsetAsync(c->Lf, 0, n * k * sizeof(float), c->st));
+      pivchol_run_df(a, c->Lf, c->st);
+    } else {
+      pivchol_run<double>(a, c->L, c->st);
+    }
     TRY(check_launch(c, "pivoted cholesky"));
     PivState hps;
     CTRY(c, cudaMemcpyAsync(&hps, ps, sizeof(PivState), cudaMemcpyDeviceToHost, c->st));
@@ -646,8 +677,9 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     }
     TRY(check_launch(c, "selection"));
     TRY(nystrom(c, S, k, c->L, Kkk, work, &c->jitter));
+    if (c->precision == GDML_DF64) to_float(c->L, n * k, c->Lf, c->st);
   }
-  TRY(woodbury_core(c, c->L, rank, c->LC, c->Cinv, c->Cfull));
+  TRY(woodbury_core(c, c->L, rank, c->LC, c->Cinv, c->Cfull, c->precision == GDML_DF64 ? c->Lf : nullptr));
   if (pivots_dev) CTRY(c, cudaMemcpyAsync(pivots_dev, S, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st));
   if (resid_trace_dev)
     CTRY(c, cudaMemcpyAsync(resid_trace_dev, trace, k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
@@ -745,10 +777,12 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
   if (ynorm == 0.0) {
     CTRY(c, cudaMemsetAsync(alpha, 0, n * sizeof(double), st));
     c->last_outer = 0;
-  } else if (c->precision == GDML_FP64) {
-    // the captured loop is bound to the context's own x buffer
+  } else if (c->precision == GDML_FP64 || c->precision == GDML_DF64) {
+    // the captured loop is bound to the context's own x buffer; DF64 iterates
+    // with the double-float matvec and refines through FP64 true-residual restarts
+    const bool fp64 = c->precision == GDML_FP64;
     CTRY(c, cudaMemcpyAsync(c->x, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    stat = pcg_core(c, c->ys, c->x, rtol * ynorm, max_iter, true, true, 3, &iters, &res);
+    stat = pcg_core(c, c->ys, c->x, rtol * ynorm, max_iter, fp64, true, fp64 ? 3 : 10, &iters, &res);
     CTRY(c, cudaMemcpyAsync(alpha, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     c->last_outer = 1;
   } else {
@@ -792,7 +826,7 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
     c->last_outer = outer;
   }
   CTRY(c, cudaStreamSynchronize(st));
-  if (c->precision != GDML_FP64) {
+  if (c->precision == GDML_TF32 || c->precision == GDML_BF16) {
     gdml_status ts = tc_check(c->tc, st);
     if (ts != GDML_OK) return ctx_fail(c, ts, last_msg());
   }
@@ -826,7 +860,8 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
   if (!(rtol > 0.0) || max_iter < 1) return fail(GDML_ERR_ARG, "batched solve: need rtol > 0 and max_iter >= 1");
   for (int i = 0; i < count; ++i) {
     if (!ctxs[i] || !y_dev[i] || !alpha_dev[i]) return fail(GDML_ERR_ARG, "batched solve: null entry");
-    if (ctxs[i]->precision != GDML_FP64) return fail(GDML_ERR_ARG, "batched solve: FP64 contexts only");
+    if (ctxs[i]->precision != GDML_FP64 && ctxs[i]->precision != GDML_DF64)
+      return fail(GDML_ERR_ARG, "batched solve: FP64 or DF64 contexts only");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(GDML_ERR_ARG, "batched solve: a context appears twice");
   }
@@ -883,7 +918,7 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
     cudaStream_t user = c->st;
     c->st = c->cap;
     const int64_t before = launch_count();
-    bs = pcg_body(c, c->x, true, h);
+    bs = pcg_body(c, c->x, c->precision == GDML_FP64, h);
     body_n[i] = launch_count() - before;
     count_launch(-body_n[i]);
     c->st = user;
@@ -901,12 +936,13 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
   }
   cudaStream_t st0 = ctxs[0]->st;
   gdml_status out = GDML_OK;
-  for (int round = 0; round < 4; ++round) {
+  for (int round = 0; round < 12; ++round) {
     int n_active = 0;
     for (int i = 0; i < count; ++i) {
       gdml_ctx* c = ctxs[i];
       const double tol = rtol * ynorm[i];
-      active[i] = ynorm[i] > 0.0 && res[i] > tol && iters[i] < max_iter && restarts[i] <= 3;
+      const int max_rs = c->precision == GDML_FP64 ? 3 : 10;
+      active[i] = ynorm[i] > 0.0 && res[i] > tol && iters[i] < max_iter && restarts[i] <= max_rs;
       c->hictl[IC_ITER] = 0;
       c->hictl[IC_MAXIT] = active[i] ? max_iter - iters[i] : 0;
       c->hsc[SC_TOL2] = tol * tol;
@@ -980,9 +1016,10 @@ gdml_status gdml_autotune(gdml_ctx* c, int32_t* choice_out) {
   CTRY(c, cudaEventCreate(&e1));
   int best = 1;
   float best_ms = 1e30f;
-  const int max_s = c->precision == GDML_FP64 ? c->splits_cap : c->tc.splits_cap;
+  const bool tcm = c->precision == GDML_TF32 || c->precision == GDML_BF16;
+  const int max_s = tcm ? c->tc.splits_cap : c->splits_cap;
   for (int s = 1; s <= max_s; s *= 2) {
-    if (c->precision == GDML_FP64) c->splitsU = s;
+    if (!tcm) c->splitsU = s;
     else c->tc.splits2 = s;
     for (int w = 0; w < 2; ++w) TRY(matvec_any(c, v, out, 1, false));
     CTRY(c, cudaEventRecord(e0, c->st));
@@ -998,7 +1035,7 @@ gdml_status gdml_autotune(gdml_ctx* c, int32_t* choice_out) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (c->precision == GDML_FP64) c->splitsU = best;
+  if (!tcm) c->splitsU = best;
   else c->tc.splits2 = best;
   drop_graphs(c);
   if (choice_out) *choice_out = best;
@@ -1007,9 +1044,10 @@ gdml_status gdml_autotune(gdml_ctx* c, int32_t* choice_out) {
 
 gdml_status gdml_set_tuning(gdml_ctx* c, int32_t splits) {
   TRY(validate(c));
-  const int cap = c->precision == GDML_FP64 ? c->splits_cap : c->tc.splits_cap;
+  const bool tcm = c->precision == GDML_TF32 || c->precision == GDML_BF16;
+  const int cap = tcm ? c->tc.splits_cap : c->splits_cap;
   if (splits < 1 || splits > cap) return ctx_fail(c, GDML_ERR_ARG, "split count out of range");
-  if (c->precision == GDML_FP64) c->splitsU = splits;
+  if (!tcm) c->splitsU = splits;
   else c->tc.splits2 = splits;
   drop_graphs(c);
   return GDML_OK;
@@ -1017,7 +1055,7 @@ gdml_status gdml_set_tuning(gdml_ctx* c, int32_t splits) {
 
 gdml_status gdml_tc_check(gdml_ctx* c) {
   TRY(validate(c));
-  if (c->precision == GDML_FP64) return GDML_OK;
+  if (c->precision != GDML_TF32 && c->precision != GDML_BF16) return GDML_OK;
   gdml_status s = tc_check(c->tc, c->st);
   if (s != GDML_OK) return ctx_fail(c, s, last_msg());
   return GDML_OK;

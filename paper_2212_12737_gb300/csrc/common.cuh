@@ -41,6 +41,20 @@ int64_t launch_count();
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __device__ __forceinline__ int64_t cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// (sh, sl) += a * (bh + bl) in double-float: a * bh formed exactly by FMA
+// (TwoProduct), the a * bl term folded into the low part, summed by TwoSum.
+__device__ __forceinline__ void df_add_prod(float& sh, float& sl, float a, float bh, float bl) {
+  const float ph = a * bh;
+  float pl = fmaf(a, bh, -ph);
+  pl = fmaf(a, bl, pl);
+  const float t = sh + ph;
+  const float v = t - sh;
+  float e = (sh - (t - v)) + (ph - v);
+  e += sl + pl;
+  sh = t + e;
+  sl = e - (sh - t);
+}
+
 // Deterministic block reduction of one double (fixed tree order).
 template <int THREADS>
 __device__ __forceinline__ double block_sum(double v, double* sh) {

@@ -36,6 +36,9 @@ void launch_dgemm(bool nt, int64_t M, int64_t N, int64_t K, double alpha, const 
                   const TB* B, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
                   cudaStream_t st, int splits = 1, int64_t split_stride = 0);
 int dgemm_splits(int64_t M, int64_t N, int64_t K);
+// double-float (FP32-pair) GEMM, same layouts as launch_dgemm with alpha = 1, beta = 0
+void launch_dfgemm(bool nt, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+                   int64_t ldb, double* C, int64_t ldc, cudaStream_t st, int splits = 1, int64_t split_stride = 0);
 
 // linalg.cu
 void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st);
@@ -48,6 +51,12 @@ template <typename TL>
 void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                     const double* r, double* z, double* part, double* t, cudaStream_t st);
 void mirror_lower(double* A, int64_t k, cudaStream_t st);
+// DF64 contexts: FP32-stored L_k, double-float accumulation (t holds 3k doubles)
+void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
+                       const double* r, double* z, double* part, double* t, cudaStream_t st);
+void to_float(const double* a, int64_t n, float* b, cudaStream_t st);
+// lower-triangle-only double-float SYRK of an FP32 matrix: C = A A^T, A (k x n row-major, ld)
+void launch_dfsyrk(int64_t k, int64_t n, const float* A, int64_t lda, double* C, int64_t ldc, cudaStream_t st);
 void transpose_square(const double* A, int64_t k, double* At, cudaStream_t st);
 void set_identity(double* A, int64_t k, cudaStream_t st);
 int64_t woodbury_part_size(int64_t n, int64_t k);
@@ -104,6 +113,8 @@ struct PivCholArgs {
 };
 template <typename TL>
 void pivchol_run(const PivCholArgs& a, TL* L, cudaStream_t st);
+// Alg. 1 with FP32-stored L and double-float Schur sums (DF64 contexts)
+void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st);
 int pivchol_part_blocks();
 
 }  // namespace gdml

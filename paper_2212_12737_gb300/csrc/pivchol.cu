@@ -152,6 +152,54 @@ __global__ void __launch_bounds__(256) pc_update_kernel(int64_t m, int64_t n, TL
   }
 }
 
+// Alg. 1 step with FP32-stored L (DF64 contexts): the Schur correction is a
+// double-float sum of exact FP32 products, the new column is formed in FP64
+// and stored in FP32, and the residual diagonal is updated with the stored value.
+__global__ void __launch_bounds__(256) pc_update_df_kernel(int64_t m, int64_t n, float* __restrict__ L,
+                                                           const double* __restrict__ col, double* __restrict__ d,
+                                                           const unsigned char* __restrict__ chosen,
+                                                           const PivState* __restrict__ ps) {
+  if (ps->stop) return;
+  __shared__ float lp[4096];
+  const int64_t piv = ps->piv;
+  const double lmm = ps->lmm;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = i < n && !chosen[i];
+  float sh = 0.f, sl = 0.f;
+  for (int64_t j0 = 0; j0 < m; j0 += 4096) {
+    const int64_t jn = (m - j0) < 4096 ? (m - j0) : 4096;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < jn; t += blockDim.x) lp[t] = L[piv + (j0 + t) * n];
+    __syncthreads();
+    if (active) {
+      const float* Li = L + i + j0 * n;
+#pragma unroll 4
+      for (int64_t j = 0; j < jn; ++j) df_add_prod(sh, sl, Li[j * n], lp[j], 0.f);
+    }
+  }
+  if (i >= n) return;
+  if (active) {
+    const double l = (col[i] - ((double)sh + (double)sl)) / lmm;
+    const float lst = (float)l;
+    L[i + m * n] = lst;
+    const double lr = (double)lst;
+    d[i] = __dsub_rn(d[i], __dmul_rn(lr, lr));
+  } else if (i == piv) {
+    L[i + m * n] = (float)lmm;
+  }
+}
+
+void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
+  for (int64_t m = 0; m < a.k; ++m) {
+    { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(m, a.n, 1, a.d, a.perm, a.chosen, a.pivots, a.trace,
+                                                         a.ps, a.part, a.ticket); count_launch(); }
+    a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
+    { pc_update_df_kernel<<<(unsigned)cdiv(a.n, 256), 256, 0, st>>>(m, a.n, L, a.col, a.d, a.chosen, a.ps); count_launch(); }
+  }
+  { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(a.k, a.n, 0, a.d, a.perm, a.chosen, a.pivots, a.trace,
+                                                       a.ps, a.part, a.ticket); count_launch(); }
+}
+
 // ---------------------------------------------------------------- host driver
 template <typename TL>
 void pivchol_run(const PivCholArgs& a, TL* L, cudaStream_t st) {

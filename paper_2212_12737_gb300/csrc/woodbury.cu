@@ -138,3 +138,85 @@ template void woodbury_apply<float>(const float*, int64_t, int64_t, const double
 int64_t woodbury_part_size(int64_t n, int64_t k) { return cdiv(n, kRowsPerChunk) * k; }
 
 }  // namespace gdml
+
+// ---------------------------------------------------------------------------
+// DF64 contexts: L_k stored in FP32 (half the bytes); every product of an FP32
+// factor entry with an FP64 vector entry is formed exactly as a pair of floats
+// (TwoProduct by FMA on the vector's hi part, plus the lo part) and summed in
+// double-float (TwoSum), so the passes are bandwidth-bound on the FP32 lanes
+// instead of bound by the FP64 pipe.
+namespace gdml {
+
+__global__ void __launch_bounds__(256) gemv_t_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
+                                                        const double* __restrict__ r, double* __restrict__ part) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kColsPerCta + warp;
+  const int64_t i0 = (int64_t)blockIdx.y * kRowsPerChunk;
+  const int64_t i1 = i0 + kRowsPerChunk < n ? i0 + kRowsPerChunk : n;
+  if (j >= k) return;
+  const float* col = L + j * n;
+  float sh = 0.f, sl = 0.f;
+  for (int64_t i = i0 + lane; i < i1; i += 32) {
+    const double ri = r[i];
+    const float rh = (float)ri;
+    df_add_prod(sh, sl, col[i], rh, (float)(ri - (double)rh));
+  }
+  double s = (double)sh + (double)sl;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) part[blockIdx.y * k + j] = s;
+}
+
+__global__ void __launch_bounds__(256) gemv_n_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
+                                                        const double* __restrict__ x, const double* __restrict__ r,
+                                                        double inv_lam, double* __restrict__ z) {
+  __shared__ float2 xs[2048];
+  __shared__ double part[4][64];
+  const int rr = threadIdx.x & 63, q = threadIdx.x >> 6;
+  const int64_t i = (int64_t)blockIdx.x * 64 + rr;
+  float sh = 0.f, sl = 0.f;
+  for (int64_t j0 = 0; j0 < k; j0 += 2048) {
+    const int64_t jn = (k - j0) < 2048 ? (k - j0) : 2048;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < jn; t += blockDim.x) {
+      const double xv = x[j0 + t];
+      const float hi = (float)xv;
+      xs[t] = make_float2(hi, (float)(xv - (double)hi));
+    }
+    __syncthreads();
+    if (i < n) {
+      const int64_t qa = (jn * q) / 4, qb = (jn * (q + 1)) / 4;
+      const float* Lc = L + j0 * n + i;
+#pragma unroll 4
+      for (int64_t j = qa; j < qb; ++j) df_add_prod(sh, sl, Lc[j * n], xs[j].x, xs[j].y);
+    }
+  }
+  part[q][rr] = (double)sh + (double)sl;
+  __syncthreads();
+  if (q == 0 && i < n) z[i] = (r[i] - ((part[0][rr] + part[1][rr]) + (part[2][rr] + part[3][rr]))) * inv_lam;
+}
+
+void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
+                       const double* r, double* z, double* part, double* t, cudaStream_t st) {
+  const int64_t nchunks = cdiv(n, kRowsPerChunk);
+  dim3 g1((unsigned)cdiv(k, kColsPerCta), (unsigned)nchunks);
+  double* u = t + k;
+  double* e = t + 2 * k;
+  const unsigned gk = (unsigned)cdiv(k, 8);
+  { gemv_t_df_kernel<<<g1, 256, 0, st>>>(L, n, k, r, part); count_launch(); }
+  { reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
+  { symv_kernel<<<gk, 256, 0, st>>>(Cinv, k, t, u); count_launch(); }
+  { residual_kernel<<<gk, 256, 0, st>>>(C, k, t, u, e); count_launch(); }
+  { symv_add_kernel<<<gk, 256, 0, st>>>(Cinv, k, e, u); count_launch(); }
+  { gemv_n_df_kernel<<<(unsigned)cdiv(n, 64), 256, 0, st>>>(L, n, k, u, r, 1.0 / lam, z); count_launch(); }
+}
+
+__global__ void to_float_kernel(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+void to_float(const double* a, int64_t n, float* b, cudaStream_t st) {
+  { to_float_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(a, n, b); count_launch(); }
+}
+
+}  // namespace gdml

@@ -20,7 +20,7 @@ _lib = None
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 5: "ERR_BREAKDOWN",
           6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
-PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
+PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "df64": 3}
 SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3}
 
 EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",

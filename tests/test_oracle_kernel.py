@@ -135,3 +135,11 @@ def test_planted_sign_error_is_caught(tiny, monkeypatch):
     monkeypatch.setattr(ok, "hessian_block", bad)
     with pytest.raises(AssertionError):
         test_force_kernel_matches_mixed_second_differences((R, None))
+
+
+def test_sampled_rows_equal_full_matvec(tiny):
+    R, _ = tiny
+    v = np.random.default_rng(4).standard_normal(R.size)
+    full = ok.matvec(R, 1.3, v, 1e-4).reshape(R.shape[0], -1)
+    np.testing.assert_allclose(ok.matvec_rows(R, 1.3, v, [2, 0], 1e-4), full[[2, 0]], rtol=0,
+                               atol=1e-14 * np.abs(full).max())
