@@ -404,23 +404,33 @@ def run_gpu(args):
         peak = peaks.get("bf16_tflops", 1900.0)
         peak_src, bound = "of measured (MEASURED_PEAKS.json bf16_tflops)" if peaks else "of fallback", "tensor"
 
+    def phases(prec):
+        """one solve with host-synchronised phase times (setup / build / PCG)"""
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx = gdml.kernel_setup(R_d, w.sigma, w.lam, precision=prec)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        ctx.precond_build(w.select, k, seed=2)
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        _, it2, rel2, out2 = ctx.pcg_solve(y_d, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
+        torch.cuda.synchronize(dev)
+        t3 = time.perf_counter()
+        ctx.destroy()
+        return {"setup_s": t1 - t0, "build_s": t2 - t1, "solve_s": t3 - t2, "total_s": t3 - t0, "iters": it2,
+                "relres": rel2, "outer": out2}
+
     forms = {}
     if not args.no_forms and rank == 0:
         for prec in ("fp64", "df64", "tf32", "bf16"):
-            if prec == args.precision:
-                forms[prec] = {"s": t_dev, "iters": iters, "relres": rel, "converged": rel <= RTOL,
-                               "outer": outer, "matvec_ms": mv_sec * 1e3, "matvec_tflops": mv_tf}
-                continue
-            torch.cuda.synchronize(dev)
-            s = torch.cuda.Event(enable_timing=True)
-            e = torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            it2, rel2, out2 = step(prec, R_d, y_d)
-            e.record(stream)
-            torch.cuda.synchronize(dev)
+
+            ph = phases(prec)
             ms2, tf2 = matvec_rate(prec)
-            forms[prec] = {"s": s.elapsed_time(e) / 1e3, "iters": it2, "relres": rel2, "converged": rel2 <= RTOL,
-                           "outer": out2, "matvec_ms": ms2 * 1e3, "matvec_tflops": tf2}
+            forms[prec] = {"s": ph["total_s"], "iters": ph["iters"], "relres": ph["relres"],
+                           "converged": ph["relres"] <= RTOL, "outer": ph["outer"], "setup_s": ph["setup_s"],
+                           "build_s": ph["build_s"], "solve_s": ph["solve_s"], "matvec_ms": ms2 * 1e3,
+                           "matvec_tflops": tf2}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

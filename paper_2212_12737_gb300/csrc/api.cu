@@ -65,6 +65,7 @@ struct gdml_ctx {
   double jitter = 0;
   double* L = nullptr;    // n x k col-major
   float* Lf = nullptr;    // n x k col-major FP32 copy used by DF64 contexts
+  double* rsplit = nullptr;  // n float pairs (DF64 apply)
   double* LC = nullptr;   // k x k lower (row-major): Cholesky factor of C = lambda I + L^T L
   double* Cinv = nullptr; // k x k: C^-1 = L_C^-T L_C^-1 (formed once per build)
   double* Cfull = nullptr; // k x k: C itself (for the refinement step of the apply)
@@ -344,7 +345,8 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
     return GDML_OK;
   }
   if (c->precision == GDML_DF64)
-    woodbury_apply_df(c->Lf, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
+    woodbury_apply_df(c->Lf, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt,
+                      reinterpret_cast<float2*>(c->rsplit), c->st);
   else
     woodbury_apply<double>(c->L, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
   return check_launch(c, "woodbury_apply");
@@ -543,7 +545,7 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   c->splits_cap = std::max(c->splitsU, 8);
   TRY(dalloc(C, &c->U, (size_t)(c->splits_cap * M * D)));
   TRY(dalloc(C, &c->diag, (size_t)n));
-  for (double** v : {&c->r, &c->z, &c->p, &c->q, &c->x, &c->ys}) TRY(dalloc(C, v, (size_t)n));
+  for (double** v : {&c->r, &c->z, &c->p, &c->q, &c->x, &c->ys, &c->rsplit}) TRY(dalloc(C, v, (size_t)n));
   TRY(dalloc(C, &c->sc, SC_COUNT));
   TRY(dalloc(C, &c->partial, 4096));
   TRY(dalloc(C, &c->ticket, 1));
@@ -561,7 +563,7 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   launch_kdiag(c->G, M, N, (int)D, c->c, c->diag, c->st);
   TRY(check_launch(C, "setup kernels"));
   if (precision == GDML_TF32 || precision == GDML_BF16) {
-    gdml_status s = tc_setup(c->tc, precision, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->c, c->st);
+    gdml_status s = tc_setup(c->tc, precision, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->G, c->c, c->st);
     if (s != GDML_OK) return ctx_fail(C, s, "tensor-core setup: " + last_msg());
   }
   CTRY(C, cudaStreamSynchronize(c->st));

@@ -53,7 +53,7 @@ void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* C, const do
 void mirror_lower(double* A, int64_t k, cudaStream_t st);
 // DF64 contexts: FP32-stored L_k, double-float accumulation (t holds 3k doubles)
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
-                       const double* r, double* z, double* part, double* t, cudaStream_t st);
+                       const double* r, double* z, double* part, double* t, float2* rs, cudaStream_t st);
 void to_float(const double* a, int64_t n, float* b, cudaStream_t st);
 // lower-triangle-only double-float SYRK of an FP32 matrix: C = A A^T, A (k x n row-major, ld)
 void launch_dfsyrk(int64_t k, int64_t n, const float* A, int64_t lda, double* C, int64_t ldc, cudaStream_t st);

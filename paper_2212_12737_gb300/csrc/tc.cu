@@ -43,9 +43,10 @@ struct Lp<true> {
 // ------------------------------------------------------------ setup kernels
 template <bool BF16>
 __global__ void tc_setup_kernel(const double* __restrict__ Xc, const double* __restrict__ A, int64_t ldA,
-                                const double* __restrict__ S, int64_t M, int D, int Dp, int64_t K2p,
-                                typename Lp<BF16>::T* __restrict__ Xc_lp, typename Lp<BF16>::T* __restrict__ P_lp,
-                                typename Lp<BF16>::T* __restrict__ Vt_lp, float* __restrict__ S32) {
+                                const double* __restrict__ S, const double* __restrict__ G, int64_t M, int D, int Dp,
+                                int64_t K2p, typename Lp<BF16>::T* __restrict__ Xc_lp,
+                                typename Lp<BF16>::T* __restrict__ P_lp, typename Lp<BF16>::T* __restrict__ Vt_lp,
+                                float* __restrict__ S32, float* __restrict__ G32) {
   using L = Lp<BF16>;
   const int64_t a = blockIdx.x;
   for (int p = threadIdx.x; p < D; p += blockDim.x) {
@@ -53,68 +54,94 @@ __global__ void tc_setup_kernel(const double* __restrict__ Xc, const double* __r
     Xc_lp[a * Dp + p] = x;
     Vt_lp[(int64_t)p * K2p + M + a] = x;
   }
+  for (int e = threadIdx.x; e < 3 * D; e += blockDim.x) G32[a * 3 * D + e] = (float)G[a * 3 * D + e];
   for (int64_t b = threadIdx.x; b < M; b += blockDim.x) {
     P_lp[a * K2p + b] = L::from(A[a * ldA + b]);
     S32[a * M + b] = (float)S[a * M + b];
   }
 }
 
-// w_a = J_a v_a rounded to the operand type (both layouts); t_a = xc~_a . w~_a (FP64)
+// w_a = J_a v_a (FP32) rounded to the operand type; t_a = xc~_a . w~_a (FP32).
+// Row-major W only; the transposed copy for GEMM 2 is written by tc_transpose_kernel.
 template <bool BF16, int THREADS>
-__global__ void tc_proj_kernel(const double* __restrict__ G, const double* __restrict__ v, int N, int D, int Dp,
-                               int64_t K2p, const typename Lp<BF16>::T* __restrict__ Xc_lp,
-                               typename Lp<BF16>::T* __restrict__ W_lp, typename Lp<BF16>::T* __restrict__ Vt_lp,
-                               double* __restrict__ t) {
+__global__ void tc_proj_kernel(const float* __restrict__ G, const double* __restrict__ v, int N, int D, int Dp,
+                               const typename Lp<BF16>::T* __restrict__ Xc_lp, typename Lp<BF16>::T* __restrict__ W_lp,
+                               float* __restrict__ t) {
   using L = Lp<BF16>;
-  extern __shared__ double sh_v[];
-  __shared__ double red[THREADS / 32];
+  extern __shared__ float sh_vf[];
+  __shared__ float red[THREADS / 32];
   const int64_t a = blockIdx.x;
   const int B = 3 * N;
-  for (int l = threadIdx.x; l < B; l += THREADS) sh_v[l] = v[a * B + l];
+  for (int l = threadIdx.x; l < B; l += THREADS) sh_vf[l] = (float)v[a * B + l];
   __syncthreads();
-  const double* Ga = G + a * D * 3;
-  double part = 0.0;
+  const float* Ga = G + a * D * 3;
+  float part = 0.f;
   for (int p = threadIdx.x; p < D; p += THREADS) {
-    int i = (int)((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+    int i = (int)((1.f + sqrtf(1.f + 8.f * (float)p)) * 0.5f);
     while (i * (i - 1) / 2 > p) --i;
     while ((i + 1) * i / 2 <= p) ++i;
     const int j = p - i * (i - 1) / 2;
-    const double w = -(Ga[3 * p] * (sh_v[3 * i] - sh_v[3 * j]) + Ga[3 * p + 1] * (sh_v[3 * i + 1] - sh_v[3 * j + 1]) +
-                       Ga[3 * p + 2] * (sh_v[3 * i + 2] - sh_v[3 * j + 2]));
-    const auto wl = L::from(w);
+    const float w = -(Ga[3 * p] * (sh_vf[3 * i] - sh_vf[3 * j]) + Ga[3 * p + 1] * (sh_vf[3 * i + 1] - sh_vf[3 * j + 1]) +
+                      Ga[3 * p + 2] * (sh_vf[3 * i + 2] - sh_vf[3 * j + 2]));
+    const auto wl = L::from((double)w);
     W_lp[a * Dp + p] = wl;
-    Vt_lp[(int64_t)p * K2p + a] = wl;
-    part = fma(L::to(Xc_lp[a * Dp + p]), L::to(wl), part);
+    part = fmaf((float)L::to(Xc_lp[a * Dp + p]), (float)L::to(wl), part);
   }
-  const double s = block_sum<THREADS>(part, red);
-  if (threadIdx.x == 0) t[a] = s;
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int q = 0; q < THREADS / 32; ++q) s += red[q];
+    t[a] = s;
+  }
+}
+
+// Vt[p][a] = W[a][p] for a < M, p < D (32 x 32 tiles through shared memory)
+template <typename T>
+__global__ void tc_transpose_kernel(const T* __restrict__ W, int64_t M, int D, int Dp, int64_t K2p,
+                                    T* __restrict__ Vt) {
+  __shared__ T tile[32][33];
+  const int64_t a0 = (int64_t)blockIdx.y * 32;
+  const int p0 = blockIdx.x * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t a = a0 + yy;
+    const int p = p0 + threadIdx.x;
+    if (a < M && p < D) tile[yy][threadIdx.x] = W[a * Dp + p];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int p = p0 + yy;
+    const int64_t a = a0 + threadIdx.x;
+    if (a < M && p < D) Vt[(int64_t)p * K2p + a] = tile[threadIdx.x][yy];
+  }
 }
 
 // GEMM 1 epilogue: beta_ab = c^2 S_ab (T_ab - t_b) -> P[:, M + b]; per-32-column row sums
 template <bool BF16>
 struct EpiBeta {
   const float* S32;
-  const double* t;
+  const float* t;
   typename Lp<BF16>::T* P;
   int64_t K2p;
   int M;
-  double c2;
+  float c2;
   double* rs_part;
   __device__ __forceinline__ void operator()(int row, int col0, float (&v)[32], int valid, int) const {
-    double s = 0.0;
+    float s = 0.f;
     const float* Srow = S32 + (int64_t)row * M;
     auto* Prow = P + (int64_t)row * K2p + M;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       if (j < valid) {
         const int b = col0 + j;
-        const double beta = c2 * (double)Srow[b] * ((double)v[j] - t[b]);
-        const auto bl = Lp<BF16>::from(beta);
+        const float beta = c2 * Srow[b] * (v[j] - t[b]);
+        const auto bl = Lp<BF16>::from((double)beta);
         Prow[b] = bl;
-        s += Lp<BF16>::to(bl);
+        s += (float)Lp<BF16>::to(bl);
       }
     }
-    rs_part[(int64_t)(col0 >> 5) * M + row] = s;
+    rs_part[(int64_t)(col0 >> 5) * M + row] = (double)s;
   }
 };
 
@@ -125,9 +152,14 @@ struct EpiStore {
   int64_t split_stride;
   __device__ __forceinline__ void operator()(int row, int col0, float (&v)[32], int valid, int split) const {
     float* dst = U + split * split_stride + (int64_t)row * ld + col0;
+    if (valid == 32) {  // ld and col0 are multiples of 32 floats: 16-byte aligned
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < valid) dst[j] = v[j];
+      for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < valid) dst[j] = v[j];
+    }
   }
 };
 
@@ -142,41 +174,43 @@ struct EpiStoreD {
   }
 };
 
-// (K v)_a = J_a^T (sum_s U_s[a] - rowsum_a xc~_a) (+ lambda v_a)
+// (K v)_a = J_a^T (sum_s U_s[a] - rowsum_a xc~_a) (+ lambda v_a); FP32 arithmetic, FP64 output
 template <bool BF16>
 __global__ void tc_backproj_kernel(const float* __restrict__ U, int splits, int64_t split_stride, int Dp,
                                    const double* __restrict__ rs_part, int nslots, int64_t M,
-                                   const typename Lp<BF16>::T* __restrict__ Xc_lp, const double* __restrict__ G,
+                                   const typename Lp<BF16>::T* __restrict__ Xc_lp, const float* __restrict__ G,
                                    const double* __restrict__ v, int N, int D, double lam, int add_lambda,
                                    double* __restrict__ out) {
-  extern __shared__ double sh_u[];
-  __shared__ double rs;
+  extern __shared__ float sh_uf[];
+  __shared__ float rs;
   const int64_t a = blockIdx.x;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     double s = 0.0;
-    for (int k = 0; k < nslots; ++k) s += rs_part[(int64_t)k * M + a];
-    rs = s;
+    for (int k = threadIdx.x; k < nslots; k += 32) s += rs_part[(int64_t)k * M + a];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) rs = (float)s;
   }
   __syncthreads();
   for (int p = threadIdx.x; p < D; p += blockDim.x) {
-    double u = 0.0;
-    for (int s = 0; s < splits; ++s) u += (double)U[s * split_stride + a * Dp + p];
-    sh_u[p] = u - rs * Lp<BF16>::to(Xc_lp[a * Dp + p]);
+    float u = 0.f;
+    for (int s = 0; s < splits; ++s) u += U[s * split_stride + a * Dp + p];
+    sh_uf[p] = u - rs * (float)Lp<BF16>::to(Xc_lp[a * Dp + p]);
   }
   __syncthreads();
   const int B = 3 * N;
-  const double* Ga = G + a * D * 3;
+  const float* Ga = G + a * D * 3;
   for (int l = threadIdx.x; l < B; l += blockDim.x) {
     const int i = l / 3, q = l - 3 * i;
-    double s = 0.0;
+    float s = 0.f;
     for (int j = 0; j < N; ++j) {
       if (j == i) continue;
       const int p = i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i;
-      const double gj = Ga[3 * p + q] * sh_u[p];
+      const float gj = Ga[3 * p + q] * sh_uf[p];
       s += (i > j) ? -gj : gj;
     }
-    if (add_lambda) s = fma(lam, v[a * B + l], s);
-    out[a * B + l] = s;
+    double o = (double)s;
+    if (add_lambda) o = fma(lam, v[a * B + l], o);
+    out[a * B + l] = o;
   }
 }
 
@@ -272,7 +306,7 @@ static gdml_status tc_alloc(TcMatvec& tc, T** p, size_t count) {
 
 template <bool BF16>
 static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, int64_t ldA, const double* S,
-                              cudaStream_t st) {
+                              const double* G, cudaStream_t st) {
   using T = typename Lp<BF16>::T;
   const int64_t M = tc.M;
   const int span = BF16 ? 64 : 32;  // elements per 128-byte swizzle span
@@ -287,6 +321,7 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
   TC_TRY(tc_alloc(tc, &tc.rs_part, (size_t)(cdiv(M, 32) * M)));
   TC_TRY(tc_alloc(tc, &tc.err, 1));
   TC_TRY(tc_alloc(tc, &tc.tb, (size_t)M));
+  TC_TRY(tc_alloc(tc, &tc.G32, (size_t)(M * tc.D * 3)));
   tc.Xc_lp = xc;
   tc.W_lp = w;
   tc.P_lp = p;
@@ -295,7 +330,8 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
   tc.bn2 = tc.Dp <= 64 ? 64 : (tc.Dp <= 128 ? 128 : 256);
   const int64_t tiles = cdiv(tc.Dp, tc.bn2) * cdiv(M, BM);
   const int64_t num_kb2 = tc.K2p / span;
-  tc.splits2 = (int)std::max<int64_t>(1, std::min<int64_t>(num_kb2 / 4, kNumSMs / std::max<int64_t>(tiles, 1)));
+  // split K until the grid covers ~3 waves of the SMs (the autotuner can refine it)
+  tc.splits2 = (int)std::max<int64_t>(1, std::min<int64_t>(num_kb2 / 8, cdiv(3 * kNumSMs, std::max<int64_t>(tiles, 1))));
   tc.splits_cap = std::max(tc.splits2, 8);
   TC_TRY(tc_alloc(tc, &tc.U, (size_t)(tc.splits_cap * M * tc.Dp)));
   if (cudaMemsetAsync(xc, 0, M * tc.Dp * sizeof(T), st) != cudaSuccess ||
@@ -304,7 +340,7 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
       cudaMemsetAsync(vt, 0, tc.Dp * tc.K2p * sizeof(T), st) != cudaSuccess ||
       cudaMemsetAsync(tc.err, 0, sizeof(int), st) != cudaSuccess)
     return fail(GDML_ERR_CUDA, "tensor-core buffer memset");
-  { tc_setup_kernel<BF16><<<(unsigned)M, 256, 0, st>>>(Xc, A, ldA, S, M, tc.D, tc.Dp, tc.K2p, xc, p, vt, tc.S32); count_launch(); }
+  { tc_setup_kernel<BF16><<<(unsigned)M, 256, 0, st>>>(Xc, A, ldA, S, G, M, tc.D, tc.Dp, tc.K2p, xc, p, vt, tc.S32, tc.G32); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "tensor-core setup kernel");
   bool ok = make_map(&tc.mapXc, xc, BF16, tc.Dp, M, tc.Dp, BM) && make_map(&tc.mapW, w, BF16, tc.Dp, M, tc.Dp, 128) &&
             make_map(&tc.mapP, p, BF16, tc.K2p, M, tc.K2p, BM) &&
@@ -315,37 +351,41 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
 }
 
 gdml_status tc_setup(TcMatvec& tc, int precision, int64_t M, int N, int D, const double* Xc, const double* A,
-                     int64_t ldA, const double* S, double c, cudaStream_t st) {
+                     int64_t ldA, const double* S, const double* G, double c, cudaStream_t st) {
   if (M > (int64_t)1 << 30) return fail(GDML_ERR_ARG, "M too large for the tensor-core path");
   tc.precision = precision;
   tc.M = M;
   tc.N = N;
   tc.D = D;
   tc.c = c;
-  return precision == GDML_BF16 ? setup_impl<true>(tc, Xc, A, ldA, S, st) : setup_impl<false>(tc, Xc, A, ldA, S, st);
+  return precision == GDML_BF16 ? setup_impl<true>(tc, Xc, A, ldA, S, G, st)
+                                : setup_impl<false>(tc, Xc, A, ldA, S, G, st);
 }
 
 template <bool BF16>
 static gdml_status matvec_impl(TcMatvec& tc, const double* G, const double* v, double* out, int add_lambda,
                                double lam, cudaStream_t st) {
   using T = typename Lp<BF16>::T;
+  (void)G;
   const int64_t M = tc.M;
   const int span = BF16 ? 64 : 32;
-  { tc_proj_kernel<BF16, 256><<<(unsigned)M, 256, 3 * tc.N * sizeof(double), st>>>(
-      G, v, tc.N, tc.D, tc.Dp, tc.K2p, (const T*)tc.Xc_lp, (T*)tc.W_lp, (T*)tc.Vt_lp, tc.tb); count_launch(); }
-  EpiBeta<BF16> e1{tc.S32, tc.tb, (T*)tc.P_lp, tc.K2p, (int)M, tc.c * tc.c, tc.rs_part};
-  TC_TRY((launch_gemm<BF16, 128, 5>(tc.mapXc, tc.mapW, (int)M, (int)M, tc.Dp / span, 1, e1, tc.err, st)));
+  { tc_proj_kernel<BF16, 256><<<(unsigned)M, 256, 3 * tc.N * sizeof(float), st>>>(tc.G32, v, tc.N, tc.D, tc.Dp, (const T*)tc.Xc_lp, (T*)tc.W_lp, tc.tb); count_launch(); }
+  {
+    dim3 g((unsigned)cdiv(tc.D, 32), (unsigned)cdiv(M, 32));
+    { tc_transpose_kernel<T><<<g, dim3(32, 8), 0, st>>>((const T*)tc.W_lp, M, tc.D, tc.Dp, tc.K2p, (T*)tc.Vt_lp); count_launch(); }
+  }
+  EpiBeta<BF16> e1{tc.S32, tc.tb, (T*)tc.P_lp, tc.K2p, (int)M, (float)(tc.c * tc.c), tc.rs_part};
+  // short K: 3 stages (97 KB) so that two CTAs share an SM and epilogues overlap mainloops
+  TC_TRY((launch_gemm<BF16, 128, 3>(tc.mapXc, tc.mapW, (int)M, (int)M, tc.Dp / span, 1, e1, tc.err, st)));
   EpiStore e2{tc.U, tc.Dp, M * tc.Dp};
   TC_TRY((gemm_dispatch_bn<BF16>(tc.bn2, tc.mapP, tc.mapVt, (int)M, tc.D, (int)(tc.K2p / span), tc.splits2, e2,
                                  tc.err, st)));
   const int kb_per_split = (int)cdiv(tc.K2p / span, tc.splits2);
   const int splits = (int)cdiv(tc.K2p / span, kb_per_split);
-  const size_t smem = tc.D * sizeof(double);
+  const size_t smem = tc.D * sizeof(float);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(tc_backproj_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { tc_backproj_kernel<BF16><<<(unsigned)M, 128, smem, st>>>(tc.U, splits, M * tc.Dp, tc.Dp, tc.rs_part,
-                                                           (int)cdiv(M, 32), M, (const T*)tc.Xc_lp, G, v, tc.N,
-                                                           tc.D, lam, add_lambda, out); count_launch(); }
+  { tc_backproj_kernel<BF16><<<(unsigned)M, 128, smem, st>>>(tc.U, splits, M * tc.Dp, tc.Dp, tc.rs_part, (int)cdiv(M, 32), M, (const T*)tc.Xc_lp, tc.G32, v, tc.N, tc.D, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "tensor-core matvec kernels");
   return GDML_OK;
 }

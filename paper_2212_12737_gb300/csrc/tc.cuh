@@ -5,7 +5,9 @@
 //   GEMM 1:  T = Xc W^T                      (M x M, K = D)   epilogue: beta_ab = c^2 S_ab (T_ab - t_b)
 //   GEMM 2:  U = [A | beta] [W ; Xc]         (M x D, K = 2M)
 // with Xc the centred descriptors, W = J v, t_b = xc_b . w_b, A_ab = S_ab (1 + c r_ab);
-// projection and back-projection (J_a^T (U_a - rowsum_a xc_a)) stay in FP64.
+// projection, the beta epilogue and back-projection (J_a^T (U_a - rowsum_a xc_a))
+// run in FP32: the contractions' operands carry 8-11 bits, so FP64 there would
+// only add GB300's slow FP64 pipe to the critical path.
 #pragma once
 #include <cuda.h>
 
@@ -29,7 +31,8 @@ struct TcMatvec {
   float* S32 = nullptr;   // M x M
   float* U = nullptr;     // splits x M x Dp
   double* rs_part = nullptr;  // rowsum partials: ceil(M/32) x M
-  double* tb = nullptr;       // t_b = xc~_b . w~_b
+  float* tb = nullptr;        // t_b = xc~_b . w~_b
+  float* G32 = nullptr;       // M x D x 3 FP32 copy of the Jacobian factors
   int* err = nullptr;
   int bn2 = 256, splits2 = 1, splits_cap = 1;
   std::vector<void*> allocs;
@@ -37,7 +40,7 @@ struct TcMatvec {
 };
 
 gdml_status tc_setup(TcMatvec& tc, int precision, int64_t M, int N, int D, const double* Xc, const double* A,
-                     int64_t ldA, const double* S, double c, cudaStream_t st);
+                     int64_t ldA, const double* S, const double* G, double c, cudaStream_t st);
 gdml_status tc_matvec(TcMatvec& tc, const double* G, const double* v, double* out, int add_lambda, double lam,
                       cudaStream_t st);
 // reads (and clears) the device error word of the tensor-core kernels; synchronises st

@@ -147,8 +147,17 @@ int64_t woodbury_part_size(int64_t n, int64_t k) { return cdiv(n, kRowsPerChunk)
 // instead of bound by the FP64 pipe.
 namespace gdml {
 
+// r split once per apply into float pairs (n FP64 operations instead of n k)
+__global__ void split_df_kernel(const double* __restrict__ r, int64_t n, float2* __restrict__ rs) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = r[i];
+  const float hi = (float)v;
+  rs[i] = make_float2(hi, (float)(v - (double)hi));
+}
+
 __global__ void __launch_bounds__(256) gemv_t_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
-                                                        const double* __restrict__ r, double* __restrict__ part) {
+                                                        const float2* __restrict__ rs, double* __restrict__ part) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kColsPerCta + warp;
   const int64_t i0 = (int64_t)blockIdx.y * kRowsPerChunk;
@@ -156,10 +165,10 @@ __global__ void __launch_bounds__(256) gemv_t_df_kernel(const float* __restrict_
   if (j >= k) return;
   const float* col = L + j * n;
   float sh = 0.f, sl = 0.f;
+#pragma unroll 4
   for (int64_t i = i0 + lane; i < i1; i += 32) {
-    const double ri = r[i];
-    const float rh = (float)ri;
-    df_add_prod(sh, sl, col[i], rh, (float)(ri - (double)rh));
+    const float2 ri = rs[i];
+    df_add_prod(sh, sl, col[i], ri.x, ri.y);
   }
   double s = (double)sh + (double)sl;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -196,13 +205,14 @@ __global__ void __launch_bounds__(256) gemv_n_df_kernel(const float* __restrict_
 }
 
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
-                       const double* r, double* z, double* part, double* t, cudaStream_t st) {
+                       const double* r, double* z, double* part, double* t, float2* rs, cudaStream_t st) {
   const int64_t nchunks = cdiv(n, kRowsPerChunk);
   dim3 g1((unsigned)cdiv(k, kColsPerCta), (unsigned)nchunks);
   double* u = t + k;
   double* e = t + 2 * k;
   const unsigned gk = (unsigned)cdiv(k, 8);
-  { gemv_t_df_kernel<<<g1, 256, 0, st>>>(L, n, k, r, part); count_launch(); }
+  { split_df_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(r, n, rs); count_launch(); }
+  { gemv_t_df_kernel<<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
   { reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
   { symv_kernel<<<gk, 256, 0, st>>>(Cinv, k, t, u); count_launch(); }
   { residual_kernel<<<gk, 256, 0, st>>>(C, k, t, u, e); count_launch(); }
