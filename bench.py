@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gdml", choices=["gdml", "reference"])
     ap.add_argument("--workload", default="aspirin21_m1000")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16", "df64"])
+    ap.add_argument("--precision", default="df64", choices=["fp64", "tf32", "bf16", "df64"],
+                    help="headline form (df64: double-float contractions on the FP32 lanes, FP64 refinement)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison solves")
     ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply"],
@@ -440,7 +441,9 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": t_dev, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_dev * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision, "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "df64": "f32x2 (double-float) contractions + f64", "tf32": "tf32 + f64",
+                      "bf16": "bf16 + f64"}[args.precision], "data": "synthetic",
             "config": {"workload": f"{args.workload}: N={N} atoms, M={M} geometries, n={n}, D={D}, "
                                    f"{w.select} k={k}, sigma={w.sigma}, lambda={w.lam}, rtol={RTOL}",
                        "precision": args.precision, "select": w.select, "k": k, "n": n,
@@ -450,7 +453,7 @@ def run_gpu(args):
             "solve": {"iters": iters, "relres": rel, "outer_steps": outer, "converged": rel <= RTOL},
             "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(R_h.numel() * 8 + y_h.numel() * 8),
                     "d2h_bytes_per_step": int(n * 8)},
-            "roofline": {"kernel": "force-kernel matvec (proj + 2 contractions + back-projection)",
+            "roofline": {"kernel": f"force-kernel matvec, {args.precision} (proj + 2 contractions + back-projection)",
                          "bound": bound, "achieved": mv_tf, "peak": peak, "unit": "TFLOP/s",
                          "frac": mv_tf / peak, "peak_source": peak_src, "traffic": None,
                          "algorithmic_flop_per_launch": 6.0 * M * M * D, "matvec_ms": mv_sec * 1e3},
