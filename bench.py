@@ -394,10 +394,11 @@ def run_gpu(args):
     if args.precision == "fp64":
         peak, peak_src, bound = torch_peak(torch.float64), "of measured (torch FP64 matmul 4096^3, this run)", "alu"
     elif args.precision == "df64":
-        # double-float on the FP32 lanes: ~15 FP32 operations per multiply-add;
-        # roofline = measured FP32 SIMT matmul rate x 2 flop / 15 ops
-        peak = torch_peak(torch.float32, tf32=False, size=8192) * 2.0 / 15.0
-        peak_src, bound = "of derived (torch FP32 SIMT matmul 8192^3 this run x 2/15 ops per double-float FMA)", "alu"
+        # double-float on the FP32 lanes: one multiply-add (2 flop) costs ~15 FP32
+        # instructions where an FP32 FMA (also 2 flop) costs one, so the ceiling is
+        # the measured FP32 SIMT matmul rate / 15
+        peak = torch_peak(torch.float32, tf32=False, size=8192) / 15.0
+        peak_src, bound = "of derived (torch FP32 SIMT matmul 8192^3 this run / 15 FP32 ops per double-float FMA)", "alu"
     elif args.precision == "tf32":
         peak, peak_src, bound = torch_peak(torch.float32, tf32=True, size=8192), \
             "of measured (torch TF32 matmul 8192^3, this run)", "tensor"
