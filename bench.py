@@ -39,8 +39,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gdml", choices=["gdml", "reference"])
     ap.add_argument("--workload", default="aspirin21_m1000")
-    ap.add_argument("--precision", default="df64", choices=["fp64", "tf32", "bf16", "df64"],
-                    help="headline form (df64: double-float contractions on the FP32 lanes, FP64 refinement)")
+    ap.add_argument("--precision", default="df64", choices=["fp64", "tf32", "bf16", "df64", "ozaki"],
+                    help="headline form (df64: double-float contractions on the FP32 lanes; ozaki: exact "
+                         "BF16 slices on the tensor cores; both FP64-class, FP64 true-residual restarts)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison solves")
     ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply"],
@@ -51,6 +52,11 @@ def parse():
     ap.add_argument("--suite-mmax", type=int, default=2000, help="cap on M (geometries) per system")
     ap.add_argument("--suite-maxiter", type=int, default=2000, help="PCG iteration cap per system in the suite")
     return ap.parse_args()
+
+
+# tensor-core products per FP64-equivalent product: the sliced form multiplies
+# 28 BF16 slice pairs (7 slices per operand, pairs i + j <= 8) for each one
+SLICE_PAIRS = {"fp64": 1, "df64": 1, "tf32": 1, "bf16": 1, "ozaki": 28}
 
 
 # ----------------------------------------------------------------- helpers
@@ -399,6 +405,10 @@ def run_gpu(args):
         # the measured FP32 SIMT matmul rate / 15
         peak = torch_peak(torch.float32, tf32=False, size=8192) / 15.0
         peak_src, bound = "of derived (torch FP32 SIMT matmul 8192^3 this run / 15 FP32 ops per double-float FMA)", "alu"
+    elif args.precision == "ozaki":
+        # 7 BF16 slices per operand, 28 slice-pair products per contraction on tcgen05
+        peak = peaks.get("bf16_tflops", 1900.0)
+        peak_src, bound = "of measured (MEASURED_PEAKS.json bf16_tflops)" if peaks else "of fallback", "tensor"
     elif args.precision == "tf32":
         peak, peak_src, bound = torch_peak(torch.float32, tf32=True, size=8192), \
             "of measured (torch TF32 matmul 8192^3, this run)", "tensor"
@@ -425,7 +435,7 @@ def run_gpu(args):
 
     forms = {}
     if not args.no_forms and rank == 0:
-        for prec in ("fp64", "df64", "tf32", "bf16"):
+        for prec in ("fp64", "df64", "ozaki", "tf32", "bf16"):
 
             ph = phases(prec)
             ms2, tf2 = matvec_rate(prec)
@@ -443,7 +453,8 @@ def run_gpu(args):
             "metric": METRIC, "value": t_dev, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_dev * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"fp64": "f64", "df64": "f32x2 (double-float) contractions + f64", "tf32": "tf32 + f64",
+            "dtype": {"fp64": "f64", "df64": "f32x2 (double-float) contractions + f64",
+                      "ozaki": "bf16 x7 exact slices (FP32 accumulate) + f32x2 + f64", "tf32": "tf32 + f64",
                       "bf16": "bf16 + f64"}[args.precision], "data": "synthetic",
             "config": {"workload": f"{args.workload}: N={N} atoms, M={M} geometries, n={n}, D={D}, "
                                    f"{w.select} k={k}, sigma={w.sigma}, lambda={w.lam}, rtol={RTOL}",
@@ -455,9 +466,11 @@ def run_gpu(args):
             "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(R_h.numel() * 8 + y_h.numel() * 8),
                     "d2h_bytes_per_step": int(n * 8)},
             "roofline": {"kernel": f"force-kernel matvec, {args.precision} (proj + 2 contractions + back-projection)",
-                         "bound": bound, "achieved": mv_tf, "peak": peak, "unit": "TFLOP/s",
-                         "frac": mv_tf / peak, "peak_source": peak_src, "traffic": None,
-                         "algorithmic_flop_per_launch": 6.0 * M * M * D, "matvec_ms": mv_sec * 1e3},
+                         "bound": bound, "achieved": mv_tf * SLICE_PAIRS[args.precision], "peak": peak,
+                         "unit": "TFLOP/s", "frac": mv_tf * SLICE_PAIRS[args.precision] / peak,
+                         "peak_source": peak_src, "traffic": None,
+                         "algorithmic_flop_per_launch": 6.0 * M * M * D * SLICE_PAIRS[args.precision],
+                         "fp64_equivalent_tflops": mv_tf, "matvec_ms": mv_sec * 1e3},
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),
             "clocks": clocks,

@@ -60,7 +60,15 @@ typedef enum {
  * FP64-class accuracy at the FP32 rate.  PCG uses it inside the loop and
  * recomputes the TRUE residual with the FP64 matvec, restarting (refining)
  * from the current iterate until it converges (at most 10 restarts). */
-typedef enum { GDML_FP64 = 0, GDML_TF32 = 1, GDML_BF16 = 2, GDML_DF64 = 3 } gdml_precision;
+/* OZAKI: the two descriptor contractions run on the BF16 tensor cores with
+ * FP64-class accuracy.  Each 256-entry chunk of an operand row is scaled by a
+ * power of two and cut into 7 exact BF16 integer slices of 7 bits (49 bits);
+ * slice pairs whose products are kept (i + j <= 8) are accumulated exactly in
+ * FP32 per level, combined in double-float and summed across chunks (the
+ * error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012; ~1e-14 relative
+ * matvec error).  Preconditioner and PCG as for DF64.  Operand magnitudes must
+ * stay inside the FP32 range (|x| < 1e38). */
+typedef enum { GDML_FP64 = 0, GDML_TF32 = 1, GDML_BF16 = 2, GDML_DF64 = 3, GDML_OZAKI = 4 } gdml_precision;
 
 /* Inducing-column selection rule (Sec. 3, "Column selection strategies"). */
 typedef enum {
@@ -83,7 +91,8 @@ gdml_status gdml_kernel_setup(gdml_ctx** ctx, const double* R_dev, int64_t M, in
 
 /* out = K v (+ lambda v if add_lambda), both length n = 3 N M, in the
  * context's precision (FP64 contexts: FP64; TF32/BF16: tensor-core matvec
- * with FP32 accumulation, result stored as double).  v_dev and out_dev must
+ * with FP32 accumulation, result stored as double; DF64: double-float
+ * contractions; OZAKI: sliced-BF16 tensor-core contractions).  v_dev and out_dev must
  * not overlap.  The matvec is matrix-free: w_b = J_b v_b, u_a = sum_b H_ab w_b,
  * (K v)_a = J_a^T u_a (Sec. 2.1, "only relies on evaluations of
  * matrix-vector products"). */

@@ -20,7 +20,17 @@ extern "C" {
 gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B_dev, int32_t M, int32_t N,
                               int32_t K, double* C_dev, void* cuda_stream);
 
-/* Reads and clears the error word of the tensor-core kernels of a TF32/BF16
+/* C = A B^T through the sliced-BF16 tensor-core GEMM of OZAKI contexts (the
+ * matvec's descriptor contractions, Sec. 2.1, at FP64-class accuracy).  A: M x K,
+ * B: N x K, C: M x N, row-major FP64 device arrays, 1 <= M, N, K <= 2^24; every
+ * 256-entry chunk of a row of A and B is split into 7 BF16 slices of 7 bits,
+ * chunk products are accumulated exactly in FP32 per slice level and the result
+ * is returned as FP64.  Synchronises the stream.  Errors: GDML_ERR_ARG,
+ * GDML_ERR_OOM, GDML_ERR_CUDA, GDML_ERR_TIMEOUT (a bounded pipeline wait gave up). */
+gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
+                              double* C_dev, void* cuda_stream);
+
+/* Reads and clears the error word of the tensor-core kernels of a TF32/BF16/OZAKI
  * context (synchronises its stream); GDML_ERR_TIMEOUT if a tcgen05 pipeline
  * wait gave up since the last check.  FP64 contexts: always GDML_OK. */
 gdml_status gdml_tc_check(gdml_ctx* ctx);

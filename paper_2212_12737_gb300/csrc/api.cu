@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "oz.cuh"
 #include "tc.cuh"
 #include "../../include/gdml_testing.h"
 
@@ -59,6 +60,7 @@ struct gdml_ctx {
   double* diag = nullptr;  // n
   double* Xc() const { return V64 + M * D; }
   TcMatvec tc;  // tensor-core matvec state (TF32/BF16 contexts)
+  OzMatvec oz;  // sliced-BF16 tensor-core matvec state (OZAKI contexts)
 
   // preconditioner
   int64_t k = 0;  // rank built (0: none)
@@ -134,6 +136,11 @@ gdml_status check_launch(gdml_ctx* c, const char* what) {
   return GDML_OK;
 }
 
+// FP32-stored L_k with double-float sums (DF64 and OZAKI contexts)
+inline bool df_precond(const gdml_ctx* c) { return c->precision == GDML_DF64 || c->precision == GDML_OZAKI; }
+// FP64-class matvec: plain PCG with true-residual restarts, no refinement loop
+inline bool direct_pcg(const gdml_ctx* c) { return c->precision != GDML_TF32 && c->precision != GDML_BF16; }
+
 // ----------------------------------------------------------------- matvec
 gdml_status matvec_fp64(gdml_ctx* c, const double* v, double* out, int add_lambda) {
   const int64_t M = c->M;
@@ -170,6 +177,11 @@ gdml_status matvec_df(gdml_ctx* c, const double* v, double* out, int add_lambda)
 gdml_status matvec_any(gdml_ctx* c, const double* v, double* out, int add_lambda, bool force_fp64) {
   if (force_fp64 || c->precision == GDML_FP64) return matvec_fp64(c, v, out, add_lambda);
   if (c->precision == GDML_DF64) return matvec_df(c, v, out, add_lambda);
+  if (c->precision == GDML_OZAKI) {
+    gdml_status s = oz_matvec(c->oz, c->G, c->Xc(), v, out, add_lambda, c->lam, c->st);
+    if (s != GDML_OK) return ctx_fail(c, s, "sliced tensor-core matvec: " + last_msg());
+    return check_launch(c, "matvec_oz");
+  }
   gdml_status s = tc_matvec(c->tc, c->G, v, out, add_lambda, c->lam, c->st);
   if (s != GDML_OK) return ctx_fail(c, s, "tensor-core matvec: " + last_msg());
   return check_launch(c, "matvec_tc");
@@ -310,7 +322,7 @@ gdml_status ensure_precond_buffers(gdml_ctx* c, int64_t k) {
   c->Lf = nullptr;
   c->cap_k = 0;
   TRY(dalloc(c, &c->L, (size_t)(c->n * k)));
-  if (c->precision == GDML_DF64) TRY(dalloc(c, &c->Lf, (size_t)(c->n * k)));
+  if (df_precond(c)) TRY(dalloc(c, &c->Lf, (size_t)(c->n * k)));
   TRY(dalloc(c, &c->LC, (size_t)(k * k)));
   TRY(dalloc(c, &c->Cinv, (size_t)(k * k)));
   TRY(dalloc(c, &c->Cfull, (size_t)(k * k)));
@@ -344,7 +356,7 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
     CTRY(c, cudaMemcpyAsync(z, r, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GDML_OK;
   }
-  if (c->precision == GDML_DF64)
+  if (df_precond(c))
     woodbury_apply_df(c->Lf, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt,
                       reinterpret_cast<float2*>(c->rsplit), c->st);
   else
@@ -516,7 +528,7 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   if (M < 1 || N < 2 || N > 128) return fail(GDML_ERR_ARG, "need M >= 1 and 2 <= N <= 128");
   if (!(sigma > 0.0) || !(lambda > 0.0) || !std::isfinite(sigma) || !std::isfinite(lambda))
     return fail(GDML_ERR_ARG, "need sigma > 0 and lambda > 0");
-  if (precision < GDML_FP64 || precision > GDML_DF64) return fail(GDML_ERR_ARG, "unknown precision");
+  if (precision < GDML_FP64 || precision > GDML_OZAKI) return fail(GDML_ERR_ARG, "unknown precision");
   std::unique_ptr<gdml_ctx, void (*)(gdml_ctx*)> c(new gdml_ctx(), &gdml_destroy);
   CTRY(c.get(), cudaGetDevice(&c->device));
   c->st = static_cast<cudaStream_t>(cuda_stream);
@@ -565,6 +577,10 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   if (precision == GDML_TF32 || precision == GDML_BF16) {
     gdml_status s = tc_setup(c->tc, precision, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->G, c->c, c->st);
     if (s != GDML_OK) return ctx_fail(C, s, "tensor-core setup: " + last_msg());
+  }
+  if (precision == GDML_OZAKI) {
+    gdml_status s = oz_setup(c->oz, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->c, c->st);
+    if (s != GDML_OK) return ctx_fail(C, s, "sliced tensor-core setup: " + last_msg());
   }
   CTRY(C, cudaStreamSynchronize(c->st));
   *out = c.release();
@@ -629,7 +645,7 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     CTRY(c, cudaMemsetAsync(chosen, 0, n, c->st));
     CTRY(c, cudaMemsetAsync(ps, 0, sizeof(PivState), c->st));
     CTRY(c, cudaMemsetAsync(ticket, 0, sizeof(unsigned), c->st));
-    if (c->precision != GDML_DF64) CTRY(c, cudaMemsetAsync(c->L, 0, n * k * sizeof(double), c->st));
+    if (!df_precond(c)) CTRY(c, cudaMemsetAsync(c->L, 0, n * k * sizeof(double), c->st));
     PivCholArgs a;
     a.n = n;
     a.k = k;
@@ -645,7 +661,7 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     a.get_col = [c](const int64_t* cols, double* out, const int* stop, cudaStream_t st) {
       launch_kcol(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, stop, st);
     };
-    if (c->precision == GDML_DF64) {
+    if (df_precond(c)) {
       CTRY(c, cudaMemsetAsync(c->Lf, 0, n * k * sizeof(float), c->st));
       pivchol_run_df(a, c->Lf, c->st);
     } else {
@@ -679,9 +695,9 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     }
     TRY(check_launch(c, "selection"));
     TRY(nystrom(c, S, k, c->L, Kkk, work, &c->jitter));
-    if (c->precision == GDML_DF64) to_float(c->L, n * k, c->Lf, c->st);
+    if (df_precond(c)) to_float(c->L, n * k, c->Lf, c->st);
   }
-  TRY(woodbury_core(c, c->L, rank, c->LC, c->Cinv, c->Cfull, c->precision == GDML_DF64 ? c->Lf : nullptr));
+  TRY(woodbury_core(c, c->L, rank, c->LC, c->Cinv, c->Cfull, df_precond(c) ? c->Lf : nullptr));
   if (pivots_dev) CTRY(c, cudaMemcpyAsync(pivots_dev, S, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st));
   if (resid_trace_dev)
     CTRY(c, cudaMemcpyAsync(resid_trace_dev, trace, k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
@@ -779,9 +795,9 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
   if (ynorm == 0.0) {
     CTRY(c, cudaMemsetAsync(alpha, 0, n * sizeof(double), st));
     c->last_outer = 0;
-  } else if (c->precision == GDML_FP64 || c->precision == GDML_DF64) {
-    // the captured loop is bound to the context's own x buffer; DF64 iterates
-    // with the double-float matvec and refines through FP64 true-residual restarts
+  } else if (direct_pcg(c)) {
+    // the captured loop is bound to the context's own x buffer; DF64 / OZAKI
+    // iterate with their FP64-class matvec and refine through FP64 true-residual restarts
     const bool fp64 = c->precision == GDML_FP64;
     CTRY(c, cudaMemcpyAsync(c->x, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     stat = pcg_core(c, c->ys, c->x, rtol * ynorm, max_iter, fp64, true, fp64 ? 3 : 10, &iters, &res);
@@ -828,8 +844,8 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
     c->last_outer = outer;
   }
   CTRY(c, cudaStreamSynchronize(st));
-  if (c->precision == GDML_TF32 || c->precision == GDML_BF16) {
-    gdml_status ts = tc_check(c->tc, st);
+  if (c->precision == GDML_TF32 || c->precision == GDML_BF16 || c->precision == GDML_OZAKI) {
+    gdml_status ts = c->precision == GDML_OZAKI ? oz_check(c->oz, st) : tc_check(c->tc, st);
     if (ts != GDML_OK) return ctx_fail(c, ts, last_msg());
   }
   if (iters_out) *iters_out = (int32_t)iters;
@@ -847,6 +863,15 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
   return tc_gemm_test(bf16, A_dev, B_dev, M, N, K, C_dev, static_cast<cudaStream_t>(stream));
 }
 
+gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
+                              double* C_dev, void* stream) {
+  clear_msg();
+  if (!A_dev || !B_dev || !C_dev || M < 1 || N < 1 || K < 1) return fail(GDML_ERR_ARG, "bad gemm test arguments");
+  if (M > ((int64_t)1 << 24) || N > ((int64_t)1 << 24) || K > ((int64_t)1 << 24))
+    return fail(GDML_ERR_ARG, "gemm test sizes too large");
+  return oz_gemm_test(A_dev, B_dev, M, N, K, C_dev, static_cast<cudaStream_t>(stream));
+}
+
 int64_t gdml_launch_count(void) { return launch_count(); }
 
 // Many independent FP64 systems, one CUDA graph: per system a gate kernel and a
@@ -862,8 +887,8 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
   if (!(rtol > 0.0) || max_iter < 1) return fail(GDML_ERR_ARG, "batched solve: need rtol > 0 and max_iter >= 1");
   for (int i = 0; i < count; ++i) {
     if (!ctxs[i] || !y_dev[i] || !alpha_dev[i]) return fail(GDML_ERR_ARG, "batched solve: null entry");
-    if (ctxs[i]->precision != GDML_FP64 && ctxs[i]->precision != GDML_DF64)
-      return fail(GDML_ERR_ARG, "batched solve: FP64 or DF64 contexts only");
+    if (!direct_pcg(ctxs[i]))
+      return fail(GDML_ERR_ARG, "batched solve: FP64, DF64 or OZAKI contexts only");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(GDML_ERR_ARG, "batched solve: a context appears twice");
   }
@@ -1057,8 +1082,8 @@ gdml_status gdml_set_tuning(gdml_ctx* c, int32_t splits) {
 
 gdml_status gdml_tc_check(gdml_ctx* c) {
   TRY(validate(c));
-  if (c->precision != GDML_TF32 && c->precision != GDML_BF16) return GDML_OK;
-  gdml_status s = tc_check(c->tc, c->st);
+  if (c->precision != GDML_TF32 && c->precision != GDML_BF16 && c->precision != GDML_OZAKI) return GDML_OK;
+  gdml_status s = c->precision == GDML_OZAKI ? oz_check(c->oz, c->st) : tc_check(c->tc, c->st);
   if (s != GDML_OK) return ctx_fail(c, s, last_msg());
   return GDML_OK;
 }
@@ -1074,6 +1099,7 @@ void gdml_destroy(gdml_ctx* c) {
   drop_graphs(c);
   if (c->cap) cudaStreamDestroy(c->cap);
   tc_destroy(c->tc);
+  oz_destroy(c->oz);
   for (void* p : c->allocs)
     if (p) cudaFree(p);
   if (c->hsc) cudaFreeHost(c->hsc);

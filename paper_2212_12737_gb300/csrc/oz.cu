@@ -1,0 +1,602 @@
+// Sliced-BF16 tensor-core matvec (see oz.cuh for the scheme).  Data layout in HBM:
+//   <op>.slices  BF16 [7][Rp][Kp]   K-major, zero padded (A operands Rp % 128 == 0, B operands % 64)
+//   <op>.e       int  [chunk][rows] power-of-two exponent of each 256-entry chunk of a row
+//   Tp           float2 [D-chunks][M][M]    double-float partials of T = Xc W^T
+//   Up           float2 [2 M-chunks][M][D]  double-float partials of U = A W + beta Xc
+//   rs2          float2 [M-chunks][M]       partial row sums of beta
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.cuh"
+#include "oz.cuh"
+#include "tc.cuh"
+#include "tc_gemm.cuh"
+
+namespace gdml {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kAStages = 6;
+constexpr int kATile = oz::BM * 128;     // 16 KB: 128 rows x one 128-byte K span
+constexpr int kBTile = oz::BN * 128;     // 8 KB
+constexpr int kBGroup = oz::S * kBTile;  // all slices of one B k-block
+constexpr int kSmemData = 2 * kBGroup + kAStages * kATile;
+constexpr int kSmemTotal = kSmemData + 1024 + 256;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kKbPerChunk = oz::KC / oz::KB;
+static_assert(oz::S * oz::BN <= (int)kTmemCols, "one TMEM accumulator per level");
+static_assert(kSmemTotal <= 227 * 1024, "shared memory per CTA");
+
+// ------------------------------------------------------------ double-float helpers
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // needs |a| >= |b| or a == 0
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (h, l) += x
+__device__ __forceinline__ void df_add_f(float& h, float& l, float x) {
+  float s, e;
+  two_sum(h, x, s, e);
+  e = __fadd_rn(e, l);
+  fast_two_sum(s, e, h, l);
+}
+// (h, l) += (bh, bl)
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  fast_two_sum(s, e, h, l);
+}
+// (h, l) = (ah, al) * (bh, bl)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  fast_two_sum(p, e, h, l);
+}
+__device__ __forceinline__ float2 split_d(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+// 2^k for -126 <= k <= 127
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// Slices of one entry (hi + lo) of a chunk whose magnitudes are all below 2^ex:
+// s_i = rint(y), y <- (y - s_i) * 2^7, starting from y = x 2^(7 - ex).  All
+// steps are exact; |s_1| <= 128 and |s_i| <= 64 for i > 1.
+__device__ __forceinline__ void slice_write(float2 xs, int ex, bf16* __restrict__ sl, int64_t row, int64_t k,
+                                            int64_t Rp, int64_t Kp) {
+  if (k >= Kp) return;
+  float yh = ldexpf(xs.x, oz::BITS - ex), yl = ldexpf(xs.y, oz::BITS - ex);
+  const float up = (float)(1 << oz::BITS);
+#pragma unroll
+  for (int i = 0; i < oz::S; ++i) {
+    const float s = rintf(yh);
+    sl[((int64_t)i * Rp + row) * Kp + k] = __float2bfloat16_rn(s);
+    float h, l;
+    two_sum(__fsub_rn(yh, s), yl, h, l);
+    yh = __fmul_rn(h, up);
+    yl = __fmul_rn(l, up);
+  }
+}
+
+// largest |x| of the CTA (256 threads), and the exponent ex with every |x| < 2^ex
+__device__ __forceinline__ int chunk_exponent(float m, float* red) {
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+  int ex = 0;
+  if (m > 0.f) (void)frexpf(m, &ex);
+  return ex;
+}
+
+// ------------------------------------------------------------ slicing kernels
+// One CTA per (row, 256-entry chunk) of X (rows x K, row stride ldx).  Optionally
+// also converts t[row] into a double-float pair (first chunk only).
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t K,
+                                                            int64_t rows, int64_t Rp, int64_t Kp,
+                                                            bf16* __restrict__ sl, int* __restrict__ e,
+                                                            const double* __restrict__ t, float2* __restrict__ t2) {
+  __shared__ float red[8];
+  const int64_t row = blockIdx.x, q = blockIdx.y;
+  const int64_t k = q * oz::KC + threadIdx.x;
+  const float2 xs = split_d(k < K ? X[row * ldx + k] : 0.0);
+  const int ex = chunk_exponent(fabsf(xs.x), red);
+  if (threadIdx.x == 0) {
+    e[q * rows + row] = ex;
+    if (t2 && q == 0) t2[row] = split_d(t[row]);
+  }
+  slice_write(xs, ex, sl, row, k, Rp, Kp);
+}
+
+// XT (cols x rows) = X^T, X rows x cols with row stride ldx (32 x 32 tiles)
+__global__ void oz_transpose_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                    double* __restrict__ XT) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t r = r0 + yy, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[yy][threadIdx.x] = X[r * ldx + c];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int64_t c = c0 + yy, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) XT[c * rows + r] = tile[threadIdx.x][yy];
+  }
+}
+
+__global__ void oz_s2_kernel(const double* __restrict__ S, int64_t count, double c2, float2* __restrict__ S2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < count) S2[i] = split_d(c2 * S[i]);
+}
+
+// ------------------------------------------------------------ sliced GEMM
+// grid (ceil(N/64), ceil(M/128), K-chunks).  CTA z accumulates the 4 k-blocks of
+// chunk z: per k-block the producer loads the 7 B slices (one group) and then the
+// 7 A slices one by one; the MMA warp multiplies A slice i with B slices
+// j = 0..6-i into TMEM accumulator i + j.  The epilogue combines the 7 levels in
+// double-float arithmetic, scales by 2^(eA + eB) and stores the chunk's partial.
+__global__ void __launch_bounds__(kThreads, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
+                   int Bp, int M, int N, int num_kb, const int* __restrict__ eA, const int* __restrict__ eB,
+                   float2* __restrict__ out, int64_t ldo, int64_t split_stride, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + 2 * kBGroup;
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + kSmemData);
+  uint64_t* bempty = bfull + 2;
+  uint64_t* afull = bempty + 2;
+  uint64_t* aempty = afull + kAStages;
+  uint64_t* done = aempty + kAStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * oz::BN, m0 = blockIdx.y * oz::BM;
+  const int kb_begin = blockIdx.z * kKbPerChunk;
+  const int kb_end = min(num_kb, kb_begin + kKbPerChunk);
+  const int nk = kb_end - kb_begin;
+
+  if (threadIdx.x == 0) {
+    for (int g = 0; g < 2; ++g) {
+      tc::mbar_init(&bfull[g], 1);
+      tc::mbar_init(&bempty[g], 1);
+    }
+    for (int s = 0; s < kAStages; ++s) {
+      tc::mbar_init(&afull[s], 1);
+      tc::mbar_init(&aempty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int g = kb & 1;
+      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
+      if (!tc::mbar_wait(&bempty[g], gph ^ 1u)) {
+        atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const int kx = (kb_begin + kb) * oz::KB;
+      tc::mbar_expect_tx(&bfull[g], kBGroup);
+      for (int j = 0; j < oz::S; ++j)
+        tc::tma_load_2d(sB + (g * oz::S + j) * kBTile, &mapB, &bfull[g], kx, j * Bp + n0);
+      bool ok = true;
+      for (int i = 0; i < oz::S; ++i) {
+        const int ai = kb * oz::S + i;
+        const int s = ai % kAStages;
+        const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
+        if (!tc::mbar_wait(&aempty[s], ph ^ 1u)) {
+          atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        tc::mbar_expect_tx(&afull[s], kATile);
+        tc::tma_load_2d(sA + s * kATile, &mapA, &afull[s], kx, i * Ap + m0);
+      }
+      if (!ok) break;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int g = kb & 1;
+      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
+      if (!tc::mbar_wait(&bfull[g], gph)) {
+        atomicExch(err, tc::ERR_TIMEOUT_FULL);
+        *abort_flag = 1;
+        break;
+      }
+      for (int i = 0; i < oz::S; ++i) {
+        const int ai = kb * oz::S + i;
+        const int s = ai % kAStages;
+        const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
+        if (!tc::mbar_wait(&afull[s], ph)) {
+          atomicExch(err, tc::ERR_TIMEOUT_FULL);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t a_addr = tc::smem_u32(sA + s * kATile);
+        for (int j = 0; i + j < oz::S; ++j) {
+          const uint32_t b_addr = tc::smem_u32(sB + (g * oz::S + j) * kBTile);
+          const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_issue<true>(d, tc::make_sw128_desc(a_addr + kk * 32), tc::make_sw128_desc(b_addr + kk * 32),
+                                idesc, (kb > 0 || i > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&aempty[s]);
+      }
+      if (ok) tc::mma_commit(&bempty[g]);
+    }
+    tc::mma_commit(done);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: combine the levels, scale, store the chunk partial
+    const int quarter = warp & 3;
+    const int row = m0 + quarter * 32 + lane;
+    int go = 0;
+    if (lane == 0) {
+      const bool ok = tc::mbar_wait(done, 0);
+      if (!ok) {
+        atomicExch(err, tc::ERR_TIMEOUT_DONE);
+        *abort_flag = 1;
+      }
+      go = ok && !*abort_flag;
+    }
+    go = __shfl_sync(0xffffffffu, go, 0);
+    tc::fence_after_sync();
+    if (go) {
+      const int64_t z = blockIdx.z;
+      const int ea = row < M ? eA[z * M + row] : 0;
+      float2* orow = out + z * split_stride + (int64_t)row * ldo;
+#pragma unroll 1
+      for (int c0 = 0; c0 < oz::BN; c0 += 16) {
+        float h[16], l[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) h[t] = l[t] = 0.f;
+#pragma unroll 1
+        for (int L = oz::S - 1; L >= 0; --L) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * oz::BN + c0), v);
+          const float sc = pow2f(-oz::BITS * (L + 2));
+          if (nk > 0) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) df_add_f(h[t], l[t], __fmul_rn(v[t], sc));
+          }
+        }
+        if (row < M) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int col = n0 + c0 + t;
+            if (col < N) {
+              const int ex = ea + eB[z * N + col];
+              orow[col] = make_float2(ldexpf(h[t], ex), ldexpf(l[t], ex));
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    if (lane == 0) (void)tc::mbar_wait(done, 0);
+    __syncwarp();
+    tc::fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+// ------------------------------------------------------------ nonlinear step and back-projection
+// beta_ab = c^2 S_ab (T_ab - t_b) for the 256 b of chunk q of row a, in double-float;
+// written as GEMM 2's sliced A operand, plus the chunk's row sum.
+__global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__ Tp, int nsplit, int64_t M,
+                                                      const float2* __restrict__ S2, const float2* __restrict__ t2,
+                                                      int64_t Rp, int64_t Kp, bf16* __restrict__ sl,
+                                                      int* __restrict__ e, float2* __restrict__ rs2) {
+  __shared__ float red[8];
+  __shared__ float2 redp[8];
+  const int64_t a = blockIdx.x, q = blockIdx.y;
+  const int64_t b = q * oz::KC + threadIdx.x;
+  float bh = 0.f, bl = 0.f;
+  if (b < M) {
+    float th = 0.f, tl = 0.f;
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 p = Tp[((int64_t)s * M + a) * M + b];
+      df_add(th, tl, p.x, p.y);
+    }
+    const float2 tb = t2[b];
+    df_add(th, tl, -tb.x, -tb.y);
+    const float2 sab = S2[a * M + b];
+    df_mul(sab.x, sab.y, th, tl, bh, bl);
+  }
+  // row sum of the chunk (fixed reduction order)
+  float sh = bh, sl_ = bl;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl_, o);
+    df_add(sh, sl_, oh, ol);
+  }
+  if ((threadIdx.x & 31) == 0) redp[threadIdx.x >> 5] = make_float2(sh, sl_);
+  const int ex = chunk_exponent(fabsf(bh), red);  // contains a __syncthreads
+  if (threadIdx.x == 0) {
+    float h = redp[0].x, l = redp[0].y;
+    for (int w = 1; w < 8; ++w) df_add(h, l, redp[w].x, redp[w].y);
+    rs2[q * M + a] = make_float2(h, l);
+    e[q * M + a] = ex;
+  }
+  slice_write(make_float2(bh, bl), ex, sl, a, b, Rp, Kp);
+}
+
+// (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a); U_a and rowsum_a summed from
+// their double-float partials, the rest in FP64.  One CTA per geometry.
+__global__ void __launch_bounds__(128) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
+                                                          const float2* __restrict__ rs2, int nrs,
+                                                          const double* __restrict__ Xc, const double* __restrict__ G,
+                                                          const double* __restrict__ v, int N, double lam,
+                                                          int add_lambda, double* __restrict__ out) {
+  extern __shared__ double sh_u[];
+  __shared__ double rs;
+  const int64_t a = blockIdx.x;
+  if (threadIdx.x < 32) {
+    float h = 0.f, l = 0.f;
+    for (int q = threadIdx.x; q < nrs; q += 32) {
+      const float2 p = rs2[(int64_t)q * M + a];
+      df_add(h, l, p.x, p.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      df_add(h, l, oh, ol);
+    }
+    if (threadIdx.x == 0) rs = (double)h + (double)l;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < D; p += blockDim.x) {
+    float h = 0.f, l = 0.f;
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 u = Up[((int64_t)s * M + a) * D + p];
+      df_add(h, l, u.x, u.y);
+    }
+    sh_u[p] = ((double)h + (double)l) - rs * Xc[a * D + p];
+  }
+  __syncthreads();
+  const int B = 3 * N;
+  const double* Ga = G + a * D * 3;
+  for (int l = threadIdx.x; l < B; l += blockDim.x) {
+    const int i = l / 3, qd = l - 3 * i;
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      const int p = i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i;
+      const double gj = Ga[3 * p + qd] * sh_u[p];
+      s += (i > j) ? -gj : gj;  // d x_p / d R_i = -g_p when i is the first atom of pair p
+    }
+    if (add_lambda) s = fma(lam, v[a * B + l], s);
+    out[a * B + l] = s;
+  }
+}
+
+// C = sum of the double-float partials, as FP64 (test hook)
+__global__ void oz_sum_partials_kernel(const float2* __restrict__ P, int nsplit, int64_t count, double* __restrict__ C) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float h = 0.f, l = 0.f;
+  for (int s = 0; s < nsplit; ++s) {
+    const float2 p = P[(int64_t)s * count + i];
+    df_add(h, l, p.x, p.y);
+  }
+  C[i] = (double)h + (double)l;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+#define OZ_TRY(x)                 \
+  do {                            \
+    gdml_status _s = (x);         \
+    if (_s != GDML_OK) return _s; \
+  } while (0)
+
+template <typename T>
+static gdml_status oz_alloc(OzMatvec& oz, T** p, size_t count, cudaStream_t st) {
+  void* v = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (cudaMalloc(&v, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(GDML_ERR_OOM, "sliced tensor-core buffers: cudaMalloc failed");
+  }
+  oz.allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  if (cudaMemsetAsync(v, 0, bytes, st) != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced buffer memset");
+  return GDML_OK;
+}
+
+static gdml_status make_operand(OzMatvec& oz, OzOperand& op, int64_t rows, int64_t K, int box_rows,
+                                cudaStream_t st) {
+  op.rows = rows;
+  op.Rp = cdiv(rows, box_rows) * box_rows;
+  op.K = K;
+  op.Kp = cdiv(K, oz::KB) * oz::KB;
+  op.nchunks = cdiv(K, oz::KC);
+  bf16* s = nullptr;
+  OZ_TRY(oz_alloc(oz, &s, (size_t)(oz::S * op.Rp * op.Kp), st));
+  OZ_TRY(oz_alloc(oz, &op.e, (size_t)(op.nchunks * rows), st));
+  op.slices = s;
+  if (!make_kmajor_map(&op.map, s, true, (uint64_t)op.Kp, (uint64_t)(oz::S * op.Rp), (uint64_t)op.Kp,
+                       (uint32_t)box_rows))
+    return fail(GDML_ERR_CUDA, "cuTensorMapEncodeTiled failed (sliced operand)");
+  return GDML_OK;
+}
+
+static void slice_rows(const double* X, int64_t ldx, OzOperand& op, cudaStream_t st, const double* t = nullptr,
+                       float2* t2 = nullptr) {
+  dim3 g((unsigned)op.rows, (unsigned)op.nchunks);
+  { oz_slice_rows_kernel<<<g, 256, 0, st>>>(X, ldx, op.K, op.rows, op.Rp, op.Kp, (bf16*)op.slices, op.e, t, t2); count_launch(); }
+}
+
+static void transpose(const double* X, int64_t rows, int64_t cols, int64_t ldx, double* XT, cudaStream_t st) {
+  dim3 g((unsigned)cdiv(cols, 32), (unsigned)cdiv(rows, 32));
+  { oz_transpose_kernel<<<g, dim3(32, 8), 0, st>>>(X, rows, cols, ldx, XT); count_launch(); }
+}
+
+static gdml_status oz_gemm(const OzOperand& A, const OzOperand& B, float2* out, int64_t ldo, int64_t split_stride,
+                           int* err, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal) != cudaSuccess)
+      return fail(GDML_ERR_CUDA, "cudaFuncSetAttribute(sliced gemm)");
+    attr_set = true;
+  }
+  if (A.Kp != B.Kp) return fail(GDML_ERR_ARG, "sliced gemm: K mismatch");
+  dim3 grid((unsigned)cdiv(B.rows, oz::BN), (unsigned)cdiv(A.rows, oz::BM), (unsigned)A.nchunks);
+  { oz_gemm_kernel<<<grid, kThreads, kSmemTotal, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / oz::KB), A.e, B.e, out, ldo, split_stride, err); count_launch(); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("sliced gemm launch: ") + cudaGetErrorString(e));
+  return GDML_OK;
+}
+
+gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, const double* A, int64_t ldA,
+                     const double* S, double c, cudaStream_t st) {
+  if (M > (int64_t)1 << 24 || D > (1 << 20)) return fail(GDML_ERR_ARG, "system too large for the sliced path");
+  oz.M = M;
+  oz.N = N;
+  oz.D = D;
+  OZ_TRY(make_operand(oz, oz.Xc1, M, D, oz::BM, st));
+  OZ_TRY(make_operand(oz, oz.W1, M, D, oz::BN, st));
+  OZ_TRY(make_operand(oz, oz.A2, M, M, oz::BM, st));
+  OZ_TRY(make_operand(oz, oz.WT2, D, M, oz::BN, st));
+  OZ_TRY(make_operand(oz, oz.B2, M, M, oz::BM, st));
+  OZ_TRY(make_operand(oz, oz.XT2, D, M, oz::BN, st));
+  OZ_TRY(oz_alloc(oz, &oz.W, (size_t)(M * D), st));
+  OZ_TRY(oz_alloc(oz, &oz.WT, (size_t)(M * D), st));
+  OZ_TRY(oz_alloc(oz, &oz.t, (size_t)M, st));
+  OZ_TRY(oz_alloc(oz, &oz.t2, (size_t)M, st));
+  OZ_TRY(oz_alloc(oz, &oz.S2, (size_t)(M * M), st));
+  OZ_TRY(oz_alloc(oz, &oz.Tp, (size_t)(oz.W1.nchunks * M * M), st));
+  OZ_TRY(oz_alloc(oz, &oz.Up, (size_t)(2 * oz.A2.nchunks * M * D), st));
+  OZ_TRY(oz_alloc(oz, &oz.rs2, (size_t)(oz.A2.nchunks * M), st));
+  OZ_TRY(oz_alloc(oz, &oz.err, 1, st));
+  // fixed operands: Xc (GEMM 1 A), A (GEMM 2 A, segment 1), Xc^T (GEMM 2 B, segment 2), c^2 S
+  slice_rows(Xc, D, oz.Xc1, st);
+  slice_rows(A, ldA, oz.A2, st);
+  transpose(Xc, M, D, D, oz.WT, st);
+  slice_rows(oz.WT, M, oz.XT2, st);
+  { oz_s2_kernel<<<(unsigned)cdiv(M * M, 256), 256, 0, st>>>(S, M * M, c * c, oz.S2); count_launch(); }
+  if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced setup kernels");
+  oz.ready = true;
+  return GDML_OK;
+}
+
+gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
+                      int add_lambda, double lam, cudaStream_t st) {
+  if (!oz.ready) return fail(GDML_ERR_STATE, "sliced matvec not set up");
+  const int64_t M = oz.M;
+  const int D = oz.D;
+  launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
+  slice_rows(oz.W, D, oz.W1, st, oz.t, oz.t2);
+  transpose(oz.W, M, D, D, oz.WT, st);
+  slice_rows(oz.WT, M, oz.WT2, st);
+  OZ_TRY(oz_gemm(oz.Xc1, oz.W1, oz.Tp, M, M * M, oz.err, st));
+  {
+    dim3 g((unsigned)M, (unsigned)oz.B2.nchunks);
+    { oz_beta_kernel<<<g, 256, 0, st>>>(oz.Tp, (int)oz.W1.nchunks, M, oz.S2, oz.t2, oz.B2.Rp, oz.B2.Kp, (bf16*)oz.B2.slices, oz.B2.e, oz.rs2); count_launch(); }
+  }
+  const int64_t nch = oz.A2.nchunks;
+  OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st));
+  OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + nch * M * D, D, M * D, oz.err, st));
+  const size_t smem = (size_t)D * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  { oz_backproj_kernel<<<(unsigned)M, 128, smem, st>>>(oz.Up, (int)(2 * nch), M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
+  if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced matvec kernels");
+  return GDML_OK;
+}
+
+gdml_status oz_check(OzMatvec& oz, cudaStream_t st) {
+  if (!oz.ready) return GDML_OK;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, oz.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(GDML_ERR_CUDA, "reading the sliced-gemm error word");
+  if (h) {
+    cudaMemsetAsync(oz.err, 0, sizeof(int), st);
+    return fail(GDML_ERR_TIMEOUT, "a sliced tcgen05 pipeline wait timed out (code " + std::to_string(h) + ")");
+  }
+  return GDML_OK;
+}
+
+void oz_destroy(OzMatvec& oz) {
+  for (void* p : oz.allocs) cudaFree(p);
+  oz.allocs.clear();
+  oz.ready = false;
+}
+
+gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,
+                         cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return fail(GDML_ERR_ARG, "oz_gemm_test: empty sizes");
+  OzMatvec t;
+  OzOperand a, b;
+  float2* part = nullptr;
+  gdml_status s = make_operand(t, a, M, K, oz::BM, st);
+  if (s == GDML_OK) s = make_operand(t, b, N, K, oz::BN, st);
+  if (s == GDML_OK) s = oz_alloc(t, &part, (size_t)(a.nchunks * M * N), st);
+  if (s == GDML_OK) s = oz_alloc(t, &t.err, 1, st);
+  if (s == GDML_OK) {
+    slice_rows(A, K, a, st);
+    slice_rows(B, K, b, st);
+    s = oz_gemm(a, b, part, N, M * N, t.err, st);
+  }
+  if (s == GDML_OK) {
+    { oz_sum_partials_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(part, (int)a.nchunks, M * N, C); count_launch(); }
+    int h = 0;
+    if (cudaMemcpyAsync(&h, t.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      s = fail(GDML_ERR_CUDA, "oz_gemm_test: synchronise");
+    else if (h)
+      s = fail(GDML_ERR_TIMEOUT, "sliced tcgen05 pipeline wait timed out");
+  }
+  cudaStreamSynchronize(st);
+  oz_destroy(t);
+  return s;
+}
+
+}  // namespace gdml

@@ -1,0 +1,86 @@
+// FP64-accurate force-kernel matvec on the BF16 tensor cores (GDML_OZAKI contexts).
+//
+// The two descriptor contractions of K v (the same algebra as the FP64 path),
+//   GEMM 1:  T = Xc W^T                              (M x M, K = D)
+//   GEMM 2:  U = A W + beta Xc                       (M x D, K = M, two segments)
+// are computed by an error-free splitting in the manner of Ozaki, Ogita, Oishi and
+// Rump (2012), "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications":
+//
+//   * every operand row is cut into chunks of KC = 256 entries along K; within a
+//     chunk the row is scaled by a power of two 2^e (e from the chunk's largest
+//     magnitude) and written as  x = 2^e * sum_{i<7} s_i 2^{-7(i+1)}  with integer
+//     slices |s_1| <= 128, |s_i| <= 65 (i > 1), each exact in BF16 (49 bits in all);
+//   * the product of one slice pair is an integer below 2^14, so the FP32
+//     tensor-core accumulation of one chunk is exact: every level sum
+//     sum_{i+j=l} s_i t_j over 256 K entries stays below 2^24;
+//   * slice pairs with i + j <= 8 (1-based) are kept, one TMEM accumulator per
+//     level i + j; the levels are combined in double-float arithmetic and scaled by
+//     2^(eA + eB), giving one double-float partial per chunk; partials are summed
+//     by the consumer.
+//
+// The nonlinear step between the GEMMs (beta = c^2 S (T - t)) and the
+// back-projection run in double-float / FP64.  Relative error of the matvec is
+// ~1e-14 (FP64-class), so the plain PCG reaches 1e-8 at lambda = 1e-10.
+#pragma once
+#include <cuda.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace gdml {
+
+namespace oz {
+constexpr int S = 7;         // slices per operand
+constexpr int BITS = 7;      // bits per slice
+constexpr int KC = 256;      // K entries per exactly accumulated chunk
+constexpr int KB = 64;       // K entries per k-block (one 128-byte BF16 span)
+constexpr int BM = 128;      // rows per tile (UMMA M)
+constexpr int BN = 64;       // columns per tile (UMMA N)
+}  // namespace oz
+
+// one operand in sliced form: S slice matrices of rows x Kp BF16 (zero padded),
+// stacked as S * Rp rows, plus an exponent per (chunk, row)
+struct OzOperand {
+  void* slices = nullptr;  // __nv_bfloat16[S][Rp][Kp]
+  int* e = nullptr;        // [nchunks][rows]
+  int64_t rows = 0, Rp = 0, K = 0, Kp = 0, nchunks = 0;
+  CUtensorMap map;
+};
+
+struct OzMatvec {
+  bool ready = false;
+  int64_t M = 0;
+  int N = 0, D = 0;
+  OzOperand Xc1;  // GEMM 1 A: Xc (rows a, K = D), fixed
+  OzOperand W1;   // GEMM 1 B: W (rows b, K = D), per matvec
+  OzOperand A2;   // GEMM 2 segment 1 A: A (rows a, K = b), fixed
+  OzOperand WT2;  // GEMM 2 segment 1 B: W^T (rows d, K = b), per matvec
+  OzOperand B2;   // GEMM 2 segment 2 A: beta (rows a, K = b), per matvec
+  OzOperand XT2;  // GEMM 2 segment 2 B: Xc^T (rows d, K = b), fixed
+  double* W = nullptr;    // M x D (FP64 projection)
+  double* WT = nullptr;   // D x M
+  double* t = nullptr;    // M: t_b = xc_b . w_b
+  float2* t2 = nullptr;   // M: t_b as a double-float pair
+  float2* S2 = nullptr;   // M x M: c^2 S_ab as double-float pairs
+  float2* Tp = nullptr;   // [W1.nchunks][M][M] partials of T
+  float2* Up = nullptr;   // [2 * A2.nchunks][M][D] partials of U
+  float2* rs2 = nullptr;  // [A2.nchunks][M] partial row sums of beta
+  int* err = nullptr;
+  std::vector<void*> allocs;
+};
+
+gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, const double* A, int64_t ldA,
+                     const double* S, double c, cudaStream_t st);
+// out = K v (+ lambda v); G, Xc: the context's FP64 Jacobian factors and centred descriptors
+gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
+                      int add_lambda, double lam, cudaStream_t st);
+gdml_status oz_check(OzMatvec& oz, cudaStream_t st);
+void oz_destroy(OzMatvec& oz);
+
+// test hook: C (M x N, FP64) = A (M x K) B (N x K)^T through the sliced tensor-core GEMM
+gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,
+                         cudaStream_t st);
+
+}  // namespace gdml

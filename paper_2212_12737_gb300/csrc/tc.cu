@@ -238,7 +238,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2D K-major map: inner dim K (elements), outer dim rows; box = one 128-byte span x box_rows
-static bool make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t K, uint64_t rows, uint64_t ld_elems,
+bool make_kmajor_map(CUtensorMap* m, const void* base, bool bf16, uint64_t K, uint64_t rows, uint64_t ld_elems,
                      uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -342,9 +342,9 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
     return fail(GDML_ERR_CUDA, "tensor-core buffer memset");
   { tc_setup_kernel<BF16><<<(unsigned)M, 256, 0, st>>>(Xc, A, ldA, S, G, M, tc.D, tc.Dp, tc.K2p, xc, p, vt, tc.S32, tc.G32); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "tensor-core setup kernel");
-  bool ok = make_map(&tc.mapXc, xc, BF16, tc.Dp, M, tc.Dp, BM) && make_map(&tc.mapW, w, BF16, tc.Dp, M, tc.Dp, 128) &&
-            make_map(&tc.mapP, p, BF16, tc.K2p, M, tc.K2p, BM) &&
-            make_map(&tc.mapVt, vt, BF16, tc.K2p, tc.Dp, tc.K2p, tc.bn2);
+  bool ok = make_kmajor_map(&tc.mapXc, xc, BF16, tc.Dp, M, tc.Dp, BM) && make_kmajor_map(&tc.mapW, w, BF16, tc.Dp, M, tc.Dp, 128) &&
+            make_kmajor_map(&tc.mapP, p, BF16, tc.K2p, M, tc.K2p, BM) &&
+            make_kmajor_map(&tc.mapVt, vt, BF16, tc.K2p, tc.Dp, tc.K2p, tc.bn2);
   if (!ok) return fail(GDML_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   tc.ready = true;
   return GDML_OK;
@@ -435,7 +435,7 @@ static gdml_status gemm_test_impl(const double* A, const double* B, int M, int N
   CUtensorMap mA, mB;
   const int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
   gdml_status s = GDML_OK;
-  if (!make_map(&mA, a, BF16, Kp, M, Kp, BM) || !make_map(&mB, b, BF16, Kp, N, Kp, bn)) {
+  if (!make_kmajor_map(&mA, a, BF16, Kp, M, Kp, BM) || !make_kmajor_map(&mB, b, BF16, Kp, N, Kp, bn)) {
     s = fail(GDML_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   } else {
     EpiStoreD e{C, N};

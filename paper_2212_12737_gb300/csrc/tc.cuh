@@ -47,6 +47,11 @@ gdml_status tc_matvec(TcMatvec& tc, const double* G, const double* v, double* ou
 gdml_status tc_check(TcMatvec& tc, cudaStream_t st);
 void tc_destroy(TcMatvec& tc);
 
+// 2D K-major TMA map with 128-byte swizzle: inner dim K (elements), outer dim rows, row stride
+// ld_elems; box = one 128-byte span of K x box_rows rows.  False if the driver rejects it.
+bool make_kmajor_map(CUtensorMap* m, const void* base, bool bf16, uint64_t K, uint64_t rows, uint64_t ld_elems,
+                     uint32_t box_rows);
+
 // test hook: C (M x N, fp64) = A (M x K) B (N x K)^T with operands rounded to TF32 / BF16
 gdml_status tc_gemm_test(int bf16, const double* A, const double* B, int M, int N, int K, double* C,
                          cudaStream_t st);

@@ -20,12 +20,12 @@ _lib = None
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 5: "ERR_BREAKDOWN",
           6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
-PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "df64": 3}
+PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "df64": 3, "ozaki": 4}
 SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3}
 
 EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
-           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_tc_check",
+           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_test_oz_gemm", "gdml_tc_check",
            "gdml_launch_count", "gdml_matvec_noalloc", "gdml_pcg_solve_batched", "gdml_autotune",
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
@@ -65,6 +65,7 @@ def load() -> ctypes.CDLL:
         "gdml_last_error": [P],
         "gdml_destroy": [P],
         "gdml_test_tc_gemm": [I32, P, P, I32, I32, I32, P, P],
+        "gdml_test_oz_gemm": [P, P, I64, I64, I64, P, P],
         "gdml_tc_check": [P],
         "gdml_launch_count": [],
         "gdml_matvec_noalloc": [P, I64, I32, D, D, P, P, I32, P],
@@ -259,6 +260,21 @@ def test_tc_gemm(A: torch.Tensor, B: torch.Tensor, bf16: bool = False) -> torch.
     N = B.shape[0]
     C = torch.empty(M, N, dtype=torch.float64, device=A.device)
     st = lib.gdml_test_tc_gemm(int(bf16), _ptr(A), _ptr(B), M, N, K, _ptr(C),
+                               ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
+    if st != 0:
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+    return C
+
+
+def test_oz_gemm(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """C = A B^T through the sliced-BF16 tensor-core GEMM (FP64-class accuracy)."""
+    lib = load()
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty(M, N, dtype=torch.float64, device=A.device)
+    st = lib.gdml_test_oz_gemm(_ptr(A), _ptr(B), M, N, K, _ptr(C),
                                ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())

@@ -1,0 +1,109 @@
+"""OZAKI form: the matvec's descriptor contractions on the BF16 tensor cores with
+FP64-class accuracy (operands split into exact 7-bit BF16 slices per 256-entry
+chunk, exact FP32 accumulation per slice level, double-float combination).
+Like DF64 it must reach the FP64 target at the paper's lambda = 1e-10."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kernel as ok
+from paper_2212_12737_gb300 import gdml, synth
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(float).eps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    from paper_2212_12737_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    gdml.load()
+
+
+def _gemm(A, B):
+    return gdml.test_oz_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 64, 256), (130, 70, 300), (257, 65, 1000), (200, 200, 64)])
+def test_sliced_gemm_matches_fp64(M, N, K):
+    """Several tiles, ragged edges in every dimension, 1-4 K-chunks."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    C = _gemm(A, B)
+    ref = A @ B.T
+    scale = (np.abs(A) @ np.abs(B).T).max()
+    err = np.abs(C - ref).max() / scale
+    print(f"sliced gemm {M}x{N}x{K}: max error / max(|A||B|^T) = {err:.2e}")
+    assert err <= 1e-14
+
+
+def test_sliced_gemm_is_exact_on_small_integers():
+    """Integer operands |a| <= 100 are exact in the slices and every partial sum is
+    an integer below 2^48, so the result must equal the exact product bit for bit."""
+    rng = np.random.default_rng(7)
+    A = rng.integers(-100, 101, size=(190, 1500)).astype(np.float64)
+    B = rng.integers(-100, 101, size=(75, 1500)).astype(np.float64)
+    C = _gemm(A, B)
+    assert np.array_equal(C, A @ B.T)
+
+
+def test_sliced_gemm_row_scales_and_zero_rows():
+    """Per-row/column power-of-two scaling: rows spanning 1e-25..1e25 keep their
+    own relative accuracy; an all-zero row and column give exact zeros."""
+    rng = np.random.default_rng(8)
+    M, N, K = 140, 66, 520
+    ra = 10.0 ** rng.uniform(-25, 25, size=M)
+    cb = 10.0 ** rng.uniform(-5, 5, size=N)
+    A = rng.standard_normal((M, K)) * ra[:, None]
+    B = rng.standard_normal((N, K)) * cb[:, None]
+    A[3] = 0.0
+    B[5] = 0.0
+    C = _gemm(A, B)
+    ref = A @ B.T
+    assert np.all(C[3] == 0.0) and np.all(C[:, 5] == 0.0)
+    scale = np.abs(A) @ np.abs(B).T
+    rel = np.abs(C - ref) / np.maximum(scale.max(axis=1, keepdims=True), 1e-300)
+    assert rel.max() <= 1e-14
+
+
+@pytest.mark.parametrize("name,N,M,sigma", [("ragged_N7_M150", 7, 150, 3.0), ("ethanol9_m200", 9, 200, 10.0),
+                                            ("aspirin21_m1000", 21, 1000, 20.0)])
+def test_ozaki_matvec_is_fp64_class(name, N, M, sigma):
+    if name.startswith("aspirin"):
+        R = synth.workload("aspirin21_m1000").R
+    else:
+        R = synth.geometries(synth.template(N, 5), M, 0.1, 6)
+    ctx = gdml.kernel_setup(torch.from_numpy(R).cuda(), sigma, 1e-6, precision="ozaki")
+    v = np.random.default_rng(0).standard_normal(R.size)
+    got = ctx.matvec(torch.from_numpy(v).cuda()).cpu().numpy()
+    ctx.tc_check()
+    ref = ok.matvec(R, sigma, v, 1e-6)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"ozaki matvec relative error vs FP64 oracle ({name}): {err:.2e}")
+    assert err <= 1e-12
+    ctx.destroy()
+
+
+def test_ozaki_pcg_reaches_fp64_target_at_tiny_lambda():
+    w = synth.workload("ethanol9_m200")
+    y = torch.from_numpy(w.y).cuda()
+    ctx = gdml.kernel_setup(torch.from_numpy(w.R).cuda(), w.sigma, w.lam, precision="ozaki")
+    ctx.precond_build("uniform", 400, seed=2)
+    alpha, iters, rel, _ = ctx.pcg_solve(y, rtol=1e-8)
+    a = alpha.cpu().numpy()
+    K = ok.force_kernel_dense(w.R, w.sigma)
+    res = np.linalg.norm(w.y - K @ a - w.lam * a) / np.linalg.norm(w.y)
+    bound = 8 * EPS * np.linalg.norm(K, 2) * np.linalg.norm(a) / np.linalg.norm(w.y)
+    ref = gdml.kernel_setup(torch.from_numpy(w.R).cuda(), w.sigma, w.lam, precision="df64")
+    ref.precond_build("uniform", 400, seed=2)
+    _, itdf, _, _ = ref.pcg_solve(y, rtol=1e-8)
+    print(f"ozaki: {iters} iterations (df64: {itdf}), FP64 residual {res:.2e}")
+    assert rel <= 1e-8 and res <= 1e-8 + bound
+    assert iters <= 1.5 * itdf
+    ctx.destroy()
+    ref.destroy()
