@@ -20,7 +20,7 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kThreads = 352;  // warp 0 TMA (A), warp 1 MMA, warp 2 TMA (B), warps 3..10 epilogue
 constexpr int kAStages = 6;
 constexpr int kATile = oz::BM * 128;     // 16 KB: 128 rows x one 128-byte K span
 constexpr int kBTile = oz::BN * 128;     // 8 KB
@@ -90,6 +90,16 @@ __device__ __forceinline__ void slice_write(float2 xs, int ex, bf16* __restrict_
   }
 }
 
+// 16 columns of one TMEM lane quarter (32x32b.x16), without waiting for completion
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 // largest |x| of the CTA (256 threads), and the exponent ex with every |x| < 2^ex
 __device__ __forceinline__ int chunk_exponent(float m, float* red) {
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -144,11 +154,41 @@ __global__ void oz_s2_kernel(const double* __restrict__ S, int64_t count, double
 }
 
 // ------------------------------------------------------------ sliced GEMM
+// Bounded wait without back-off, for the producer and MMA threads on the
+// critical path (try_wait already suspends in hardware for a short while).
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = tc::smem_u32(bar);
+  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// x * 2^e, exact unless the result leaves the FP32 range
+__device__ __forceinline__ float scale2(float x, int e) {
+  while (e > 127) {
+    x *= pow2f(127);
+    e -= 127;
+  }
+  while (e < -126) {
+    x *= pow2f(-126);
+    e += 126;
+  }
+  return x * pow2f(e);
+}
+
 // grid (ceil(N/64), ceil(M/128), K-chunks).  CTA z accumulates the 4 k-blocks of
-// chunk z: per k-block the producer loads the 7 B slices (one group) and then the
-// 7 A slices one by one; the MMA warp multiplies A slice i with B slices
-// j = 0..6-i into TMEM accumulator i + j.  The epilogue combines the 7 levels in
-// double-float arithmetic, scales by 2^(eA + eB) and stores the chunk's partial.
+// chunk z.  Warp 0 loads the 7 A slices of each k-block one by one into a ring,
+// warp 2 loads the 7 B slices of each k-block as one group (double buffered);
+// warp 1 multiplies A slice i with B slices j = 0..6-i into TMEM accumulator
+// i + j.  Warps 3..10 (two per TMEM lane quarter, 32 columns each) combine the
+// 7 levels, scale by 2^(eA + eB) and store the chunk's double-float partial.
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
                    int Bp, int M, int N, int num_kb, const int* __restrict__ eA, const int* __restrict__ eB,
@@ -195,26 +235,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer, A slices
     for (int kb = 0; kb < nk; ++kb) {
-      const int g = kb & 1;
-      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
-      if (!tc::mbar_wait(&bempty[g], gph ^ 1u)) {
-        atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
-        *abort_flag = 1;
-        break;
-      }
-      if (*abort_flag) break;
       const int kx = (kb_begin + kb) * oz::KB;
-      tc::mbar_expect_tx(&bfull[g], kBGroup);
-      for (int j = 0; j < oz::S; ++j)
-        tc::tma_load_2d(sB + (g * oz::S + j) * kBTile, &mapB, &bfull[g], kx, j * Bp + n0);
       bool ok = true;
       for (int i = 0; i < oz::S; ++i) {
         const int ai = kb * oz::S + i;
         const int s = ai % kAStages;
         const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
-        if (!tc::mbar_wait(&aempty[s], ph ^ 1u)) {
+        if (!mbar_wait_spin(&aempty[s], ph ^ 1u)) {
           atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
           *abort_flag = 1;
           ok = false;
@@ -229,6 +258,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
     }
+  } else if (warp == 2 && lane == 0) {
+    // ---------------- TMA producer, B slice groups
+    for (int kb = 0; kb < nk; ++kb) {
+      const int g = kb & 1;
+      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
+      if (!mbar_wait_spin(&bempty[g], gph ^ 1u)) {
+        atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const int kx = (kb_begin + kb) * oz::KB;
+      tc::mbar_expect_tx(&bfull[g], kBGroup);
+      for (int j = 0; j < oz::S; ++j)
+        tc::tma_load_2d(sB + (g * oz::S + j) * kBTile, &mapB, &bfull[g], kx, j * Bp + n0);
+    }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
@@ -236,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int kb = 0; kb < nk && ok; ++kb) {
       const int g = kb & 1;
       const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
-      if (!tc::mbar_wait(&bfull[g], gph)) {
+      if (!mbar_wait_spin(&bfull[g], gph)) {
         atomicExch(err, tc::ERR_TIMEOUT_FULL);
         *abort_flag = 1;
         break;
@@ -245,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ai = kb * oz::S + i;
         const int s = ai % kAStages;
         const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
-        if (!tc::mbar_wait(&afull[s], ph)) {
+        if (!mbar_wait_spin(&afull[s], ph)) {
           atomicExch(err, tc::ERR_TIMEOUT_FULL);
           *abort_flag = 1;
           ok = false;
@@ -270,9 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (ok) tc::mma_commit(&bempty[g]);
     }
     tc::mma_commit(done);
-  } else if (warp >= 2) {
+  } else if (warp >= 3) {
     // ---------------- epilogue: combine the levels, scale, store the chunk partial
     const int quarter = warp & 3;
+    const int cbase = ((warp - 3) >> 2) * 32;  // this warp's 32 of the tile's 64 columns
     const int row = m0 + quarter * 32 + lane;
     int go = 0;
     if (lane == 0) {
@@ -290,19 +336,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int ea = row < M ? eA[z * M + row] : 0;
       float2* orow = out + z * split_stride + (int64_t)row * ldo;
 #pragma unroll 1
-      for (int c0 = 0; c0 < oz::BN; c0 += 16) {
+      for (int c0 = cbase; c0 < cbase + 32; c0 += 16) {
+        // all 7 levels of these 16 columns in flight at once, one wait
+        uint32_t v[oz::S][16];
+#pragma unroll
+        for (int L = 0; L < oz::S; ++L)
+          tmem_ld16_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * oz::BN + c0), v[L]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float h[16], l[16];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) h[t] = l[t] = 0.f;
-#pragma unroll 1
-        for (int L = oz::S - 1; L >= 0; --L) {
-          float v[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * oz::BN + c0), v);
-          const float sc = pow2f(-oz::BITS * (L + 2));
-          if (nk > 0) {
-#pragma unroll
-            for (int t = 0; t < 16; ++t) df_add_f(h[t], l[t], __fmul_rn(v[t], sc));
-          }
+        for (int t = 0; t < 16; ++t) {
+          // levels 4..6 are scaled by 2^-42..2^-56 against the leading level's 2^-14, so a
+          // plain FP32 sum of them errs by < 2^-48 of the leading level's range; levels
+          // 3..0 are added in double-float
+          const float f4 = __uint_as_float(v[4][t]), f5 = __uint_as_float(v[5][t]), f6 = __uint_as_float(v[6][t]);
+          float tail = __fmul_rn(f6, pow2f(-oz::BITS * 8));
+          tail = __fadd_rn(tail, __fmul_rn(f5, pow2f(-oz::BITS * 7)));
+          tail = __fadd_rn(tail, __fmul_rn(f4, pow2f(-oz::BITS * 6)));
+          float hh = tail, ll = 0.f;
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[3][t]), pow2f(-oz::BITS * 5)));
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[2][t]), pow2f(-oz::BITS * 4)));
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[1][t]), pow2f(-oz::BITS * 3)));
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[0][t]), pow2f(-oz::BITS * 2)));
+          h[t] = nk > 0 ? hh : 0.f;
+          l[t] = nk > 0 ? ll : 0.f;
         }
         if (row < M) {
 #pragma unroll
@@ -310,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int col = n0 + c0 + t;
             if (col < N) {
               const int ex = ea + eB[z * N + col];
-              orow[col] = make_float2(ldexpf(h[t], ex), ldexpf(l[t], ex));
+              orow[col] = make_float2(scale2(h[t], ex), scale2(l[t], ex));
             }
           }
         }

@@ -14,7 +14,7 @@ namespace gdml {
 constexpr int kRowsPerChunk = 4096;
 constexpr int kColsPerCta = 8;
 
-// part[chunk * k + j] = sum_{i in chunk} L[i + j n] r[i]; one warp per column.
+// part[j * nchunks + chunk] = sum_{i in chunk} L[i + j n] r[i]; one warp per column.
 template <typename TL>
 __global__ void __launch_bounds__(256) gemv_t_partial_kernel(const TL* __restrict__ L, int64_t n, int64_t k,
                                                              const double* __restrict__ r,
@@ -28,17 +28,21 @@ __global__ void __launch_bounds__(256) gemv_t_partial_kernel(const TL* __restric
   double s = 0.0;
   for (int64_t i = i0 + lane; i < i1; i += 32) s = fma((double)col[i], r[i], s);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) part[blockIdx.y * k + j] = s;
+  if (lane == 0) part[j * gridDim.y + blockIdx.y] = s;
 }
 
-// t[j] = sum over chunks (fixed order)
-__global__ void reduce_chunks_kernel(const double* __restrict__ part, int64_t nchunks, int64_t k,
-                                     double* __restrict__ t) {
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// t[j] = sum over the chunk partials part[j * nchunks + c]: one warp per column,
+// lanes stride over the chunks, then a fixed shuffle tree
+__global__ void __launch_bounds__(256) reduce_chunks_kernel(const double* __restrict__ part, int64_t nchunks,
+                                                            int64_t k, double* __restrict__ t) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * 8 + warp;
   if (j >= k) return;
+  const double* pj = part + j * nchunks;
   double s = 0.0;
-  for (int64_t c = 0; c < nchunks; ++c) s += part[c * k + j];
-  t[j] = s;
+  for (int64_t c = lane; c < nchunks; c += 32) s += pj[c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) t[j] = s;
 }
 
 // u = C^-1 t: one warp per row of the dense symmetric k x k inverse
@@ -120,7 +124,7 @@ void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* C, const do
   double* e = t + 2 * k;
   const unsigned gk = (unsigned)cdiv(k, 8);
   { gemv_t_partial_kernel<TL><<<g1, 256, 0, st>>>(L, n, k, r, part); count_launch(); }
-  { reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
+  { reduce_chunks_kernel<<<(unsigned)cdiv(k, 8), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
   // u = C^-1 t, refined once with the FP64 residual t - C u: the explicit inverse
   // alone is accurate only to ~cond(C) eps; one step restores the accuracy of a
   // backward-stable solve at the cost of two more k x k passes
@@ -135,7 +139,12 @@ template void woodbury_apply<double>(const double*, int64_t, int64_t, const doub
 template void woodbury_apply<float>(const float*, int64_t, int64_t, const double*, const double*, double,
                                     const double*, double*, double*, double*, cudaStream_t);
 
-int64_t woodbury_part_size(int64_t n, int64_t k) { return cdiv(n, kRowsPerChunk) * k; }
+// doubles of the apply's partial buffer: the L^T r chunk partials of either layout
+// (4096- or 512-row chunks) or the 16 column-group partials of the DF64 L u pass
+int64_t woodbury_part_size(int64_t n, int64_t k) {
+  const int64_t a = cdiv(n, 512) * k, b = 16 * n;
+  return a > b ? a : b;
+}
 
 }  // namespace gdml
 
@@ -156,68 +165,191 @@ __global__ void split_df_kernel(const double* __restrict__ r, int64_t n, float2*
   rs[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
-__global__ void __launch_bounds__(256) gemv_t_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
-                                                        const float2* __restrict__ rs, double* __restrict__ part) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * kColsPerCta + warp;
-  const int64_t i0 = (int64_t)blockIdx.y * kRowsPerChunk;
-  const int64_t i1 = i0 + kRowsPerChunk < n ? i0 + kRowsPerChunk : n;
-  if (j >= k) return;
-  const float* col = L + j * n;
-  float sh = 0.f, sl = 0.f;
-#pragma unroll 4
-  for (int64_t i = i0 + lane; i < i1; i += 32) {
-    const float2 ri = rs[i];
-    df_add_prod(sh, sl, col[i], ri.x, ri.y);
-  }
-  double s = (double)sh + (double)sl;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) part[blockIdx.y * k + j] = s;
+// (h, l) += (bh, bl) in double-float
+__device__ __forceinline__ void df_add_pair(float& h, float& l, float bh, float bl) {
+  const float s = h + bh;
+  const float v = s - h;
+  float e = (h - (s - v)) + (bh - v);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
 }
 
-__global__ void __launch_bounds__(256) gemv_n_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
-                                                        const double* __restrict__ x, const double* __restrict__ r,
-                                                        double inv_lam, double* __restrict__ z) {
-  __shared__ float2 xs[2048];
-  __shared__ double part[4][64];
-  const int rr = threadIdx.x & 63, q = threadIdx.x >> 6;
-  const int64_t i = (int64_t)blockIdx.x * 64 + rr;
-  float sh = 0.f, sl = 0.f;
-  for (int64_t j0 = 0; j0 < k; j0 += 2048) {
-    const int64_t jn = (k - j0) < 2048 ? (k - j0) : 2048;
-    __syncthreads();
-    for (int64_t t = threadIdx.x; t < jn; t += blockDim.x) {
-      const double xv = x[j0 + t];
-      const float hi = (float)xv;
-      xs[t] = make_float2(hi, (float)(xv - (double)hi));
+// rows [i0 + base, i0 + base + 4) of one column as a float4 (zero past n)
+template <bool VEC>
+__device__ __forceinline__ float4 load4(const float* __restrict__ col, int64_t base, int64_t rem) {
+  if (VEC && base + 3 < rem) return __ldg(reinterpret_cast<const float4*>(col + base));
+  float4 v;
+  v.x = base < rem ? col[base] : 0.f;
+  v.y = base + 1 < rem ? col[base + 1] : 0.f;
+  v.z = base + 2 < rem ? col[base + 2] : 0.f;
+  v.w = base + 3 < rem ? col[base + 3] : 0.f;
+  return v;
+}
+
+constexpr int kDfRows = 512;     // rows per CTA of both passes (4 float4 per lane, 2 KB per warp and column)
+constexpr int kDfTCols = 64;     // columns per CTA of the L^T r pass (8 warps x 8)
+constexpr int kDfNGroups = 16;   // column groups of the L u pass (one partial per group)
+
+template <bool VEC>
+__device__ __forceinline__ void load_col(const float* __restrict__ col, int lane, int64_t rem, float4 (&v)[4]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) v[t] = load4<VEC>(col, 128 * t + 4 * lane, rem);
+}
+
+// part[j * nchunks + chunk] = sum over the chunk's 512 rows of L[i + j n] r[i]; r is
+// held in registers as float pairs, each warp streams 8 columns two at a time with
+// the next pair's loads issued before the current pair's arithmetic.
+// VEC: n % 4 == 0 (aligned float4 loads).
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2) gemv_t_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
+                                                           const float2* __restrict__ rs, double* __restrict__ part) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.y * kDfRows;
+  const int64_t rem = n - i0;
+  float2 rv[4][4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t i = 128 * t + 4 * lane + e;
+      rv[t][e] = i < rem ? rs[i0 + i] : make_float2(0.f, 0.f);
     }
-    __syncthreads();
-    if (i < n) {
-      const int64_t qa = (jn * q) / 4, qb = (jn * (q + 1)) / 4;
-      const float* Lc = L + j0 * n + i;
-#pragma unroll 4
-      for (int64_t j = qa; j < qb; ++j) df_add_prod(sh, sl, Lc[j * n], xs[j].x, xs[j].y);
+  const int64_t jw = (int64_t)blockIdx.x * kDfTCols + warp * 8;
+  if (jw >= k) return;
+  const int64_t jend = jw + 8 < k ? jw + 8 : k;
+  float4 a[4], b[4];
+  load_col<VEC>(L + jw * n + i0, lane, rem, a);
+  load_col<VEC>(L + (jw + 1 < jend ? jw + 1 : jw) * n + i0, lane, rem, b);
+#pragma unroll 1
+  for (int64_t j = jw; j < jend; j += 2) {
+    float4 na[4], nb[4];
+    const bool more = j + 2 < jend;
+    if (more) {
+      load_col<VEC>(L + (j + 2) * n + i0, lane, rem, na);
+      load_col<VEC>(L + (j + 3 < jend ? j + 3 : j + 2) * n + i0, lane, rem, nb);
+    }
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      df_add_prod(h0, l0, a[t].x, rv[t][0].x, rv[t][0].y);
+      df_add_prod(h1, l1, b[t].x, rv[t][0].x, rv[t][0].y);
+      df_add_prod(h0, l0, a[t].y, rv[t][1].x, rv[t][1].y);
+      df_add_prod(h1, l1, b[t].y, rv[t][1].x, rv[t][1].y);
+      df_add_prod(h0, l0, a[t].z, rv[t][2].x, rv[t][2].y);
+      df_add_prod(h1, l1, b[t].z, rv[t][2].x, rv[t][2].y);
+      df_add_prod(h0, l0, a[t].w, rv[t][3].x, rv[t][3].y);
+      df_add_prod(h1, l1, b[t].w, rv[t][3].x, rv[t][3].y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float a0 = __shfl_xor_sync(0xffffffffu, h0, o), b0 = __shfl_xor_sync(0xffffffffu, l0, o);
+      const float a1 = __shfl_xor_sync(0xffffffffu, h1, o), b1 = __shfl_xor_sync(0xffffffffu, l1, o);
+      df_add_pair(h0, l0, a0, b0);
+      df_add_pair(h1, l1, a1, b1);
+    }
+    if (lane == 0) {
+      part[j * gridDim.y + blockIdx.y] = (double)h0 + (double)l0;
+      if (j + 1 < jend) part[(j + 1) * gridDim.y + blockIdx.y] = (double)h1 + (double)l1;
+    }
+    if (more) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        a[t] = na[t];
+        b[t] = nb[t];
+      }
     }
   }
-  part[q][rr] = (double)sh + (double)sl;
+}
+
+// zp[g * n + i] = sum over column group g of L[i + j n] u[j]: CTA (row block of 512,
+// group g); warp w takes every 8th column of the group, each lane 16 rows (4 float4,
+// 2 KB contiguous per warp and column), next column's loads issued first; the 8
+// warps' partials are combined in a fixed order through shared memory.
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2) gemv_n_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
+                                                           const float2* __restrict__ us, float2* __restrict__ zp) {
+  __shared__ float2 part[8][kDfRows];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * kDfRows;
+  const int64_t rem = n - i0;
+  const int64_t g = blockIdx.y;
+  const int64_t ja = k * g / kDfNGroups, jb = k * (g + 1) / kDfNGroups;
+  float h[16], l[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) h[e] = l[e] = 0.f;
+  int64_t j = ja + warp;
+  float4 a[4];
+  if (j < jb) load_col<VEC>(L + j * n + i0, lane, rem, a);
+#pragma unroll 1
+  for (; j < jb; j += 8) {
+    float4 na[4];
+    const bool more = j + 8 < jb;
+    if (more) load_col<VEC>(L + (j + 8) * n + i0, lane, rem, na);
+    const float2 x = us[j];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      df_add_prod(h[4 * t + 0], l[4 * t + 0], a[t].x, x.x, x.y);
+      df_add_prod(h[4 * t + 1], l[4 * t + 1], a[t].y, x.x, x.y);
+      df_add_prod(h[4 * t + 2], l[4 * t + 2], a[t].z, x.x, x.y);
+      df_add_prod(h[4 * t + 3], l[4 * t + 3], a[t].w, x.x, x.y);
+    }
+    if (more) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) a[t] = na[t];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) part[warp][128 * t + 4 * lane + e] = make_float2(h[4 * t + e], l[4 * t + e]);
   __syncthreads();
-  if (q == 0 && i < n) z[i] = (r[i] - ((part[0][rr] + part[1][rr]) + (part[2][rr] + part[3][rr]))) * inv_lam;
+  for (int rr = threadIdx.x; rr < kDfRows; rr += 256) {
+    if (rr >= rem) break;
+    float hh = part[0][rr].x, ll = part[0][rr].y;
+#pragma unroll
+    for (int w = 1; w < 8; ++w) df_add_pair(hh, ll, part[w][rr].x, part[w][rr].y);
+    zp[g * n + i0 + rr] = make_float2(hh, ll);
+  }
+}
+
+// z[i] = (r[i] - sum_g zp[g][i]) / lambda (groups in a fixed order)
+__global__ void gemv_n_df_finish_kernel(const float2* __restrict__ zp, int64_t n, const double* __restrict__ r,
+                                        double inv_lam, double* __restrict__ z) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float hh = zp[i].x, ll = zp[i].y;
+#pragma unroll
+  for (int g = 1; g < kDfNGroups; ++g) df_add_pair(hh, ll, zp[g * n + i].x, zp[g * n + i].y);
+  z[i] = (r[i] - ((double)hh + (double)ll)) * inv_lam;
 }
 
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                        const double* r, double* z, double* part, double* t, float2* rs, cudaStream_t st) {
-  const int64_t nchunks = cdiv(n, kRowsPerChunk);
-  dim3 g1((unsigned)cdiv(k, kColsPerCta), (unsigned)nchunks);
+  const int64_t nchunks = cdiv(n, kDfRows);
+  dim3 g1((unsigned)cdiv(k, kDfTCols), (unsigned)nchunks);
   double* u = t + k;
   double* e = t + 2 * k;
   const unsigned gk = (unsigned)cdiv(k, 8);
+  const bool vec = (n % 4) == 0;
   { split_df_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(r, n, rs); count_launch(); }
-  { gemv_t_df_kernel<<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
-  { reduce_chunks_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
+  if (vec)
+    { gemv_t_df_kernel<true><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
+  else
+    { gemv_t_df_kernel<false><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
+  { reduce_chunks_kernel<<<gk, 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
   { symv_kernel<<<gk, 256, 0, st>>>(Cinv, k, t, u); count_launch(); }
   { residual_kernel<<<gk, 256, 0, st>>>(C, k, t, u, e); count_launch(); }
   { symv_add_kernel<<<gk, 256, 0, st>>>(Cinv, k, e, u); count_launch(); }
-  { gemv_n_df_kernel<<<(unsigned)cdiv(n, 64), 256, 0, st>>>(L, n, k, u, r, 1.0 / lam, z); count_launch(); }
+  // rs (the split of r) is dead after the first pass: it takes the split of u; the
+  // chunk partials are dead too: their buffer takes the column-group partials
+  { split_df_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(u, k, rs); count_launch(); }
+  float2* zp = reinterpret_cast<float2*>(part);
+  dim3 g2((unsigned)nchunks, (unsigned)kDfNGroups);
+  if (vec)
+    { gemv_n_df_kernel<true><<<g2, 256, 0, st>>>(L, n, k, rs, zp); count_launch(); }
+  else
+    { gemv_n_df_kernel<false><<<g2, 256, 0, st>>>(L, n, k, rs, zp); count_launch(); }
+  { gemv_n_df_finish_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(zp, n, r, 1.0 / lam, z); count_launch(); }
 }
 
 __global__ void to_float_kernel(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
