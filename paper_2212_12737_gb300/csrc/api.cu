@@ -304,6 +304,11 @@ gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, d
     transpose_square(X, k, Xt, c->st);
     launch_dgemm<double, double>(true, k, k, k, 1.0, Xt, k, Xt, k, 0.0, Cinv, k, false, c->st);  // X^T X
     TRY(check_launch(c, "woodbury inverse"));
+    if (Lf && Cfull) {  // DF64 apply: the two k x k operators as float pairs
+      split_df_inplace(Cinv, k * k, c->st);
+      split_df_inplace(Cfull, k * k, c->st);
+      TRY(check_launch(c, "woodbury split"));
+    }
     CTRY(c, cudaStreamSynchronize(c->st));
   }
   return GDML_OK;
@@ -327,7 +332,7 @@ gdml_status ensure_precond_buffers(gdml_ctx* c, int64_t k) {
   TRY(dalloc(c, &c->Cinv, (size_t)(k * k)));
   TRY(dalloc(c, &c->Cfull, (size_t)(k * k)));
   TRY(dalloc(c, &c->wpart, (size_t)woodbury_part_size(c->n, k)));
-  TRY(dalloc(c, &c->wt, (size_t)(3 * k)));
+  TRY(dalloc(c, &c->wt, (size_t)(6 * k)));
   c->cap_k = k;
   return GDML_OK;
 }
@@ -662,6 +667,8 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
       launch_kcol(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, stop, st);
     };
     if (df_precond(c)) {
+      TRY(s.get(&a.schur, (size_t)(pivchol_schur_groups() * n)));
+      TRY(s.get(&a.prow, (size_t)k));
       CTRY(c, cudaMemsetAsync(c->Lf, 0, n * k * sizeof(float), c->st));
       pivchol_run_df(a, c->Lf, c->st);
     } else {

@@ -261,6 +261,68 @@ __global__ void kcol_kernel(const int64_t* __restrict__ cols, int64_t ncols, int
   }
 }
 
+// Same columns, one warp per geometry a (8 per CTA, grid (ceil(M/8), ncols)): the
+// warp forms s = delta_(i,.) . w (shuffle reduction), u = coef delta + A_ab w on the
+// pairs of atom i (in its own shared-memory slice of D doubles), then the 3N outputs
+// J_a^T u.  w = J_b e_l depends only on the column and is built once per CTA.
+__global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restrict__ cols,
+                                                        const double* __restrict__ X, const double* __restrict__ G,
+                                                        const double* __restrict__ S, const double* __restrict__ A,
+                                                        int64_t ldA, int64_t M, int N, int D, double c2,
+                                                        double* __restrict__ out, int64_t ldo,
+                                                        const int* __restrict__ stop_flag) {
+  if (stop_flag && *stop_flag) return;
+  extern __shared__ double shw[];
+  double* wsp = shw;                     // N: (J_b e_l) on the pairs (i, j), indexed by partner j
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* u = shw + N + warp * D;        // this warp's u
+  const int64_t c = blockIdx.y;
+  const int64_t col = cols[c];
+  const int B = 3 * N;
+  const int64_t b = col / B;
+  const int l = (int)(col - b * B), i = l / 3, q = l - 3 * i;
+  const double* Xb = X + b * D;
+  const double* Gb = G + b * D * 3;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double w = 0.0;
+    if (j != i) {
+      const int p = pair_idx(i, j);
+      w = (i > j) ? -Gb[3 * p + q] : Gb[3 * p + q];
+    }
+    wsp[j] = w;
+  }
+  __syncthreads();
+  const int64_t a = (int64_t)blockIdx.x * 8 + warp;
+  if (a >= M) return;
+  const double* Xa = X + a * D;
+  const double* Ga = G + a * D * 3;
+  double sd = 0.0;
+  for (int j = lane; j < N; j += 32)
+    if (j != i) {
+      const int p = pair_idx(i, j);
+      sd = fma(Xa[p] - Xb[p], wsp[j], sd);
+    }
+  for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  const double Aab = A[a * ldA + b];
+  const double coef = -c2 * S[a * M + b] * sd;
+  for (int p = lane; p < D; p += 32) u[p] = coef * (Xa[p] - Xb[p]);
+  __syncwarp();
+  for (int j = lane; j < N; j += 32)
+    if (j != i) u[pair_idx(i, j)] += Aab * wsp[j];
+  __syncwarp();
+  for (int l2 = lane; l2 < B; l2 += 32) {
+    const int i2 = l2 / 3, q2 = l2 - 3 * i2;
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (j == i2) continue;
+      const int p = pair_idx(i2, j);
+      const double gj = Ga[3 * p + q2] * u[p];
+      s += (i2 > j) ? -gj : gj;
+    }
+    out[c * ldo + a * B + l2] = s;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double* G, cudaStream_t st) {
   int64_t tot = M * D;
@@ -306,6 +368,14 @@ template void launch_backproj<float>(const float*, int64_t, int, int64_t, const 
 void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* S,
                  const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
                  const int* stop_flag, cudaStream_t st) {
+  const size_t wsmem = ((size_t)N + 8 * (size_t)D) * sizeof(double);
+  if (wsmem <= 96 * 1024 && ncols <= 65535) {
+    if (wsmem > 48 * 1024)
+      cudaFuncSetAttribute(kcol_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+    dim3 g((unsigned)cdiv(M, 8), (unsigned)ncols);
+    { kcol_warp_kernel<<<g, 256, wsmem, st>>>(cols, X, G, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag); count_launch(); }
+    return;
+  }
   const int per = 8;
   dim3 grid((unsigned)M, (unsigned)cdiv(ncols, per));
   size_t smem = (2 * (size_t)D + N) * sizeof(double);

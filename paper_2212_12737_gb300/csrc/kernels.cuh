@@ -51,7 +51,9 @@ template <typename TL>
 void woodbury_apply(const TL* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                     const double* r, double* z, double* part, double* t, cudaStream_t st);
 void mirror_lower(double* A, int64_t k, cudaStream_t st);
-// DF64 contexts: FP32-stored L_k, double-float accumulation (t holds 3k doubles)
+// DF64 contexts: FP32-stored L_k, double-float accumulation; C and Cinv hold float
+// pairs (split_df_inplace); t holds 6k doubles (t, u, e and three float-pair vectors)
+void split_df_inplace(double* a, int64_t count, cudaStream_t st);
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                        const double* r, double* z, double* part, double* t, float2* rs, cudaStream_t st);
 void to_float(const double* a, int64_t n, float* b, cudaStream_t st);
@@ -110,7 +112,11 @@ struct PivCholArgs {
   unsigned* ticket;
   double* col;
   std::function<void(const int64_t*, double*, const int*, cudaStream_t)> get_col;
+  // DF64 form only: pivot-row gather (k floats) and Schur partials (pivchol_schur_groups() * n pairs)
+  float* prow = nullptr;
+  float2* schur = nullptr;
 };
+int pivchol_schur_groups();
 template <typename TL>
 void pivchol_run(const PivCholArgs& a, TL* L, cudaStream_t st);
 // Alg. 1 with FP32-stored L and double-float Schur sums (DF64 contexts)

@@ -29,6 +29,8 @@ constexpr int kSmemData = 2 * kBGroup + kAStages * kATile;
 constexpr int kSmemTotal = kSmemData + 1024 + 256;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kKbPerChunk = oz::KC / oz::KB;
+constexpr int kStageLd = oz::BN + 1;  // padded row of the staged output tile (float2)
+static_assert(oz::BM * kStageLd * 8 <= kSmemData, "output staging fits the operand buffers");
 static_assert(oz::S * oz::BN <= (int)kTmemCols, "one TMEM accumulator per level");
 static_assert(kSmemTotal <= 227 * 1024, "shared memory per CTA");
 
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* done = aempty + kAStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float2* stage = reinterpret_cast<float2*>(smem);  // output tile, reuses the operand buffers after the MMAs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * oz::BN, m0 = blockIdx.y * oz::BM;
@@ -277,6 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
+    const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
+    const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
     bool ok = true;
     for (int kb = 0; kb < nk && ok; ++kb) {
       const int g = kb & 1;
@@ -301,14 +306,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc::fence_after_sync();
-        const uint32_t a_addr = tc::smem_u32(sA + s * kATile);
-        for (int j = 0; i + j < oz::S; ++j) {
-          const uint32_t b_addr = tc::smem_u32(sB + (g * oz::S + j) * kBTile);
-          const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
+        // descriptors are linear in the start address (bits 0..13 = address / 16), so a
+        // K step of 32 bytes adds 2 and the B slice j of the group adds j * kBTile / 16
+        const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
+        const uint64_t bd = bdesc0 + (uint64_t)(g * oz::S * (kBTile >> 4));
+        const uint32_t first = (kb > 0 || i > 0) ? 1u : 0u;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_issue<true>(d, tc::make_sw128_desc(a_addr + kk * 32), tc::make_sw128_desc(b_addr + kk * 32),
-                                idesc, (kb > 0 || i > 0 || kk > 0) ? 1u : 0u);
+        for (int j = 0; j < oz::S; ++j) {
+          if (i + j < oz::S) {
+            const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
+            const uint64_t bj = bd + (uint64_t)(j * (kBTile >> 4));
+            tc::mma_issue<true>(d, ad, bj, idesc, first);
+            tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
+            tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
+            tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+          }
         }
         tc::mma_commit(&aempty[s]);
       }
@@ -334,7 +346,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (go) {
       const int64_t z = blockIdx.z;
       const int ea = row < M ? eA[z * M + row] : 0;
-      float2* orow = out + z * split_stride + (int64_t)row * ldo;
 #pragma unroll 1
       for (int c0 = cbase; c0 < cbase + 32; c0 += 16) {
         // all 7 levels of these 16 columns in flight at once, one wait
@@ -361,16 +372,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           h[t] = nk > 0 ? hh : 0.f;
           l[t] = nk > 0 ? ll : 0.f;
         }
-        if (row < M) {
+        // stage the scaled tile in the (now idle) operand buffers
+        float2* srow = stage + (quarter * 32 + lane) * kStageLd;
 #pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            const int col = n0 + c0 + t;
-            if (col < N) {
-              const int ex = ea + eB[z * N + col];
-              orow[col] = make_float2(scale2(h[t], ex), scale2(l[t], ex));
-            }
-          }
+        for (int t = 0; t < 16; ++t) {
+          const int col = n0 + c0 + t;
+          const int ex = ea + (col < N ? eB[z * N + col] : 0);
+          srow[c0 + t] = make_float2(scale2(h[t], ex), scale2(l[t], ex));
         }
+      }
+    }
+    // coalesced write-out: the 8 epilogue warps sync among themselves (barrier 1)
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    if (go) {
+      const int et = threadIdx.x - 96;
+      for (int idx = et; idx < oz::BM * oz::BN; idx += 256) {
+        const int rr = idx / oz::BN, cc = idx % oz::BN;
+        const int grow = m0 + rr, gcol = n0 + cc;
+        if (grow < M && gcol < N) out[blockIdx.z * split_stride + (int64_t)grow * ldo + gcol] = stage[rr * kStageLd + cc];
       }
     }
   }

@@ -11,6 +11,8 @@
 //      l_{i,m} = (k_{m,i} - s_i) / l_{pivot,m},  d_i -= l_{i,m}^2;  l_{pivot,m} = sqrt(d_pivot).
 // If the largest residual diagonal is not positive the factorisation stops
 // (rank = m) and every later kernel of the loop returns immediately.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -152,49 +154,146 @@ __global__ void __launch_bounds__(256) pc_update_kernel(int64_t m, int64_t n, TL
   }
 }
 
-// Alg. 1 step with FP32-stored L (DF64 contexts): the Schur correction is a
-// double-float sum of exact FP32 products, the new column is formed in FP64
-// and stored in FP32, and the residual diagonal is updated with the stored value.
-__global__ void __launch_bounds__(256) pc_update_df_kernel(int64_t m, int64_t n, float* __restrict__ L,
+// Alg. 1 step with FP32-stored L (DF64 contexts), three kernels:
+//   gather:  prow[j] = l_{pivot, j}, j < m (contiguous copy of the pivot row)
+//   schur:   partial Schur sums over column groups, s_g(i) = sum_{j in g} l_{pivot,j} l_{i,j},
+//            exact FP32 products summed in double-float; 512 rows per CTA, each warp
+//            streams whole 2 KB column segments with the next column's loads in flight
+//   finish:  s_i = sum_g s_g(i) (fixed order), l_{i,m} = (k_{m,i} - s_i) / l_{pivot,m} in FP64,
+//            stored in FP32; the residual diagonal is updated with the stored value.
+constexpr int kSchurRows = 512;
+constexpr int kSchurMaxGroups = 16;
+
+__device__ __forceinline__ void df_add_pair_pc(float& h, float& l, float bh, float bl) {
+  const float s = h + bh;
+  const float v = s - h;
+  float e = (h - (s - v)) + (bh - v);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
+__global__ void pc_gather_row_kernel(int64_t m, int64_t n, const float* __restrict__ L, const PivState* __restrict__ ps,
+                                     float* __restrict__ prow) {
+  if (ps->stop) return;
+  const int64_t piv = ps->piv;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+    prow[j] = L[piv + j * n];
+}
+
+template <bool VEC>
+__device__ __forceinline__ float4 pc_load4(const float* __restrict__ col, int64_t base, int64_t rem) {
+  if (VEC && base + 3 < rem) return __ldg(reinterpret_cast<const float4*>(col + base));
+  float4 v;
+  v.x = base < rem ? col[base] : 0.f;
+  v.y = base + 1 < rem ? col[base + 1] : 0.f;
+  v.z = base + 2 < rem ? col[base + 2] : 0.f;
+  v.w = base + 3 < rem ? col[base + 3] : 0.f;
+  return v;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2) pc_schur_df_kernel(int64_t m, int64_t n, const float* __restrict__ L,
+                                                             const float* __restrict__ prow,
+                                                             const PivState* __restrict__ ps,
+                                                             float2* __restrict__ schur) {
+  if (ps->stop) return;
+  __shared__ float2 part[8][kSchurRows];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * kSchurRows;
+  const int64_t rem = n - i0;
+  const int64_t g = blockIdx.y;
+  const int64_t ja = m * g / gridDim.y, jb = m * (g + 1) / gridDim.y;
+  float h[16], l[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) h[e] = l[e] = 0.f;
+  int64_t j = ja + warp;
+  float4 a[4];
+  if (j < jb) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a[t] = pc_load4<VEC>(L + j * n + i0, 128 * t + 4 * lane, rem);
+  }
+#pragma unroll 1
+  for (; j < jb; j += 8) {
+    float4 na[4];
+    const bool more = j + 8 < jb;
+    if (more) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) na[t] = pc_load4<VEC>(L + (j + 8) * n + i0, 128 * t + 4 * lane, rem);
+    }
+    const float p = prow[j];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      df_add_prod(h[4 * t + 0], l[4 * t + 0], a[t].x, p, 0.f);
+      df_add_prod(h[4 * t + 1], l[4 * t + 1], a[t].y, p, 0.f);
+      df_add_prod(h[4 * t + 2], l[4 * t + 2], a[t].z, p, 0.f);
+      df_add_prod(h[4 * t + 3], l[4 * t + 3], a[t].w, p, 0.f);
+    }
+    if (more) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) a[t] = na[t];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) part[warp][128 * t + 4 * lane + e] = make_float2(h[4 * t + e], l[4 * t + e]);
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < kSchurRows && rr < rem; rr += 256) {
+    float hh = part[0][rr].x, ll = part[0][rr].y;
+#pragma unroll
+    for (int w = 1; w < 8; ++w) df_add_pair_pc(hh, ll, part[w][rr].x, part[w][rr].y);
+    schur[g * n + i0 + rr] = make_float2(hh, ll);
+  }
+}
+
+__global__ void __launch_bounds__(256) pc_finish_df_kernel(int64_t m, int64_t n, int groups, float* __restrict__ L,
+                                                           const float2* __restrict__ schur,
                                                            const double* __restrict__ col, double* __restrict__ d,
                                                            const unsigned char* __restrict__ chosen,
                                                            const PivState* __restrict__ ps) {
   if (ps->stop) return;
-  __shared__ float lp[4096];
-  const int64_t piv = ps->piv;
-  const double lmm = ps->lmm;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool active = i < n && !chosen[i];
-  float sh = 0.f, sl = 0.f;
-  for (int64_t j0 = 0; j0 < m; j0 += 4096) {
-    const int64_t jn = (m - j0) < 4096 ? (m - j0) : 4096;
-    __syncthreads();
-    for (int64_t t = threadIdx.x; t < jn; t += blockDim.x) lp[t] = L[piv + (j0 + t) * n];
-    __syncthreads();
-    if (active) {
-      const float* Li = L + i + j0 * n;
-#pragma unroll 4
-      for (int64_t j = 0; j < jn; ++j) df_add_prod(sh, sl, Li[j * n], lp[j], 0.f);
-    }
-  }
   if (i >= n) return;
-  if (active) {
-    const double l = (col[i] - ((double)sh + (double)sl)) / lmm;
-    const float lst = (float)l;
+  const int64_t piv = ps->piv;
+  if (!chosen[i]) {
+    float sh = 0.f, sl = 0.f;
+    for (int g = 0; g < groups; ++g) {
+      const float2 v = schur[(int64_t)g * n + i];
+      df_add_pair_pc(sh, sl, v.x, v.y);
+    }
+    const double lv = (col[i] - ((double)sh + (double)sl)) / ps->lmm;
+    const float lst = (float)lv;
     L[i + m * n] = lst;
     const double lr = (double)lst;
     d[i] = __dsub_rn(d[i], __dmul_rn(lr, lr));
   } else if (i == piv) {
-    L[i + m * n] = (float)lmm;
+    L[i + m * n] = (float)ps->lmm;
   }
 }
 
+int pivchol_schur_groups() { return kSchurMaxGroups; }
+
 void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
+  const int64_t rblocks = cdiv(a.n, kSchurRows);
+  const bool vec = (a.n % 4) == 0;
   for (int64_t m = 0; m < a.k; ++m) {
     { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(m, a.n, 1, a.d, a.perm, a.chosen, a.pivots, a.trace,
                                                          a.ps, a.part, a.ticket); count_launch(); }
     a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
-    { pc_update_df_kernel<<<(unsigned)cdiv(a.n, 256), 256, 0, st>>>(m, a.n, L, a.col, a.d, a.chosen, a.ps); count_launch(); }
+    // column groups: enough CTAs for ~4 per SM, at least 32 columns per group
+    int groups = 0;
+    if (m > 0) {
+      const int64_t want = cdiv(4 * kNumSMs, rblocks);
+      groups = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)kSchurMaxGroups, std::max<int64_t>(1, m / 32)}));
+      { pc_gather_row_kernel<<<(unsigned)std::min<int64_t>(cdiv(m, 256), 64), 256, 0, st>>>(m, a.n, L, a.ps, a.prow); count_launch(); }
+      dim3 g((unsigned)rblocks, (unsigned)groups);
+      if (vec)
+        { pc_schur_df_kernel<true><<<g, 256, 0, st>>>(m, a.n, L, a.prow, a.ps, a.schur); count_launch(); }
+      else
+        { pc_schur_df_kernel<false><<<g, 256, 0, st>>>(m, a.n, L, a.prow, a.ps, a.schur); count_launch(); }
+    }
+    { pc_finish_df_kernel<<<(unsigned)cdiv(a.n, 256), 256, 0, st>>>(m, a.n, groups, L, a.schur, a.col, a.d, a.chosen, a.ps); count_launch(); }
   }
   { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(a.k, a.n, 0, a.d, a.perm, a.chosen, a.pivots, a.trace,
                                                        a.ps, a.part, a.ticket); count_launch(); }

@@ -178,7 +178,7 @@ __device__ __forceinline__ void df_add_pair(float& h, float& l, float bh, float 
 // rows [i0 + base, i0 + base + 4) of one column as a float4 (zero past n)
 template <bool VEC>
 __device__ __forceinline__ float4 load4(const float* __restrict__ col, int64_t base, int64_t rem) {
-  if (VEC && base + 3 < rem) return __ldg(reinterpret_cast<const float4*>(col + base));
+  if (VEC && base + 3 < rem) return __ldcs(reinterpret_cast<const float4*>(col + base));  // streamed once
   float4 v;
   v.x = base < rem ? col[base] : 0.f;
   v.y = base + 1 < rem ? col[base + 1] : 0.f;
@@ -323,12 +323,104 @@ __global__ void gemv_n_df_finish_kernel(const float2* __restrict__ zp, int64_t n
   z[i] = (r[i] - ((double)hh + (double)ll)) * inv_lam;
 }
 
+// Dense k x k products of the apply's core in double-float (DF64 contexts store C^-1
+// and C as float pairs): one warp per row, 16-byte loads (two entries), each term
+// (a_h + a_l)(x_h + x_l) formed by TwoProduct with the cross terms folded in, sums
+// in double-float, fixed shuffle tree.
+//   mode 0:  y = A x,       y2 = split(y)          (u = C^-1 t)
+//   mode 1:  y2 = split(t - A x)                   (e = t - C u)
+//   mode 2:  y += A x,      y2 = split(y)          (u += C^-1 e)
+__device__ __forceinline__ void df_term(float& h, float& l, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  float e = fmaf(ah, xh, -p);
+  e = fmaf(ah, xl, e);
+  e = fmaf(al, xh, e);
+  df_add_pair(h, l, p, e);
+}
+
+// EVEN: k even, so every row and the vector start on 16-byte boundaries (float4 loads)
+template <bool EVEN>
+__global__ void __launch_bounds__(256) symv_df_kernel(const float2* __restrict__ A, int64_t k,
+                                                      const float2* __restrict__ x, int mode,
+                                                      const double* __restrict__ t, double* __restrict__ y,
+                                                      float2* __restrict__ y2) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= k) return;
+  const float2* row = A + i * k;
+  float h = 0.f, l = 0.f;
+  if (EVEN) {
+#pragma unroll 4
+    for (int64_t j = 2 * lane; j < k; j += 64) {
+      const float4 a = *reinterpret_cast<const float4*>(row + j);
+      const float4 xv = *reinterpret_cast<const float4*>(x + j);
+      df_term(h, l, a.x, a.y, xv.x, xv.y);
+      df_term(h, l, a.z, a.w, xv.z, xv.w);
+    }
+  } else {
+#pragma unroll 4
+    for (int64_t j = lane; j < k; j += 32) {
+      const float2 a = row[j], xv = x[j];
+      df_term(h, l, a.x, a.y, xv.x, xv.y);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add_pair(h, l, oh, ol);
+  }
+  if (lane != 0) return;
+  const double s = (double)h + (double)l;
+  double v;
+  if (mode == 0) {
+    v = s;
+    y[i] = v;
+  } else if (mode == 1) {
+    v = t[i] - s;
+  } else {
+    v = y[i] + s;
+    y[i] = v;
+  }
+  const float vh = (float)v;
+  y2[i] = make_float2(vh, (float)(v - (double)vh));
+}
+
+static void symv_df(const float2* A, int64_t k, const float2* x, int mode, const double* t, double* y, float2* y2,
+                    cudaStream_t st) {
+  const unsigned gk = (unsigned)cdiv(k, 8);
+  if ((k & 1) == 0)
+    { symv_df_kernel<true><<<gk, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
+  else
+    { symv_df_kernel<false><<<gk, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
+}
+
+// t[j] = sum of the chunk partials (as reduce_chunks_kernel), also split into t2[j]
+__global__ void __launch_bounds__(256) reduce_chunks_df_kernel(const double* __restrict__ part, int64_t nchunks,
+                                                               int64_t k, double* __restrict__ t,
+                                                               float2* __restrict__ t2) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * 8 + warp;
+  if (j >= k) return;
+  const double* pj = part + j * nchunks;
+  double s = 0.0;
+  for (int64_t c = lane; c < nchunks; c += 32) s += pj[c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    t[j] = s;
+    const float sh = (float)s;
+    t2[j] = make_float2(sh, (float)(s - (double)sh));
+  }
+}
+
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                        const double* r, double* z, double* part, double* t, float2* rs, cudaStream_t st) {
   const int64_t nchunks = cdiv(n, kDfRows);
   dim3 g1((unsigned)cdiv(k, kDfTCols), (unsigned)nchunks);
   double* u = t + k;
-  double* e = t + 2 * k;
+  float2* t2 = reinterpret_cast<float2*>(t + 3 * k);
+  float2* e2 = reinterpret_cast<float2*>(t + 4 * k);
+  float2* u2 = reinterpret_cast<float2*>(t + 5 * k);
+  const float2* Ci2 = reinterpret_cast<const float2*>(Cinv);
+  const float2* C2 = reinterpret_cast<const float2*>(C);
   const unsigned gk = (unsigned)cdiv(k, 8);
   const bool vec = (n % 4) == 0;
   { split_df_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(r, n, rs); count_launch(); }
@@ -336,20 +428,33 @@ void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, co
     { gemv_t_df_kernel<true><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
   else
     { gemv_t_df_kernel<false><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
-  { reduce_chunks_kernel<<<gk, 256, 0, st>>>(part, nchunks, k, t); count_launch(); }
-  { symv_kernel<<<gk, 256, 0, st>>>(Cinv, k, t, u); count_launch(); }
-  { residual_kernel<<<gk, 256, 0, st>>>(C, k, t, u, e); count_launch(); }
-  { symv_add_kernel<<<gk, 256, 0, st>>>(Cinv, k, e, u); count_launch(); }
-  // rs (the split of r) is dead after the first pass: it takes the split of u; the
-  // chunk partials are dead too: their buffer takes the column-group partials
-  { split_df_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(u, k, rs); count_launch(); }
+  { reduce_chunks_df_kernel<<<gk, 256, 0, st>>>(part, nchunks, k, t, t2); count_launch(); }
+  // u = C^-1 t, refined once with the residual t - C u (see woodbury_apply)
+  symv_df(Ci2, k, t2, 0, t, u, u2, st);
+  symv_df(C2, k, u2, 1, t, nullptr, e2, st);
+  symv_df(Ci2, k, e2, 2, t, u, u2, st);
+  // the chunk partials are dead: their buffer takes the column-group partials of L u
   float2* zp = reinterpret_cast<float2*>(part);
   dim3 g2((unsigned)nchunks, (unsigned)kDfNGroups);
   if (vec)
-    { gemv_n_df_kernel<true><<<g2, 256, 0, st>>>(L, n, k, rs, zp); count_launch(); }
+    { gemv_n_df_kernel<true><<<g2, 256, 0, st>>>(L, n, k, u2, zp); count_launch(); }
   else
-    { gemv_n_df_kernel<false><<<g2, 256, 0, st>>>(L, n, k, rs, zp); count_launch(); }
+    { gemv_n_df_kernel<false><<<g2, 256, 0, st>>>(L, n, k, u2, zp); count_launch(); }
   { gemv_n_df_finish_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(zp, n, r, 1.0 / lam, z); count_launch(); }
+}
+
+// each double becomes the float pair (hi, lo) in the same 8 bytes
+__global__ void split_df_inplace_kernel(double* a, int64_t count) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double v = a[i];
+  const float hi = (float)v;
+  reinterpret_cast<float2*>(a)[i] = make_float2(hi, (float)(v - (double)hi));
+}
+
+// DF64 contexts keep C^-1 and C as float pairs (in place of the doubles)
+void split_df_inplace(double* a, int64_t count, cudaStream_t st) {
+  { split_df_inplace_kernel<<<(unsigned)cdiv(count, 256), 256, 0, st>>>(a, count); count_launch(); }
 }
 
 __global__ void to_float_kernel(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
