@@ -279,7 +279,10 @@ gdml_status nystrom(gdml_ctx* c, const int64_t* S, int64_t k, double* L, double*
 // LC <- chol(lambda I + L^T L) (Eq. 4); with Cinv, also C^-1 = L_C^-T L_C^-1
 gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, double* Cinv = nullptr,
                           double* Cfull = nullptr, const float* Lf = nullptr) {
-  if (Lf)  // DF64: C from the FP32-stored factor, exact products, double-float sums
+  if (Lf && c->precision == GDML_OZAKI) {  // C from the FP32 factor on the sliced tensor cores
+    gdml_status s = oz_syrk_lower(Lf, c->n, k, LC, k, c->st);
+    if (s != GDML_OK) return ctx_fail(c, s, "sliced syrk: " + last_msg());
+  } else if (Lf)  // DF64: C from the FP32-stored factor, exact products, double-float sums
     launch_dfsyrk(k, c->n, Lf, c->n, LC, k, c->st);
   else
     launch_dgemm<double, double>(true, k, k, c->n, 1.0, L, c->n, L, c->n, 0.0, LC, k, true, c->st);

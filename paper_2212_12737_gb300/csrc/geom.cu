@@ -111,9 +111,12 @@ __global__ void kdiag_kernel(const double* __restrict__ G, int64_t M, int N, int
   int l = (int)(t - a * B), i = l / 3, q = l - 3 * (l / 3);
   const double* Ga = G + a * D * 3;
   double s = 0.0;
+  // branch-free so that the loads of successive j are independent and in flight together
+#pragma unroll 4
   for (int j = 0; j < N; ++j) {
-    if (j == i) continue;
-    double g = Ga[3 * pair_idx(i, j) + q];
+    const bool skip = j == i;
+    const double gl = Ga[3 * (skip ? 0 : pair_idx(i, j)) + q];  // always a valid address
+    const double g = skip ? 0.0 : gl;
     s = fma(g, g, s);
   }
   diag[t] = c2_3 * s;
@@ -182,11 +185,12 @@ __global__ void backproj_kernel(const TU* __restrict__ U, int64_t ldU, int split
   for (int l = threadIdx.x; l < B; l += blockDim.x) {
     int i = l / 3, q = l - 3 * i;
     double s = 0.0;
-    for (int j = 0; j < N; ++j) {
-      if (j == i) continue;
-      int p = pair_idx(i, j);
-      double gj = Ga[3 * p + q] * sh_u[p];
-      s += (i > j) ? -gj : gj;  // dx_p/dR_i = -g_p if i is the first atom of p, else +g_p
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) {  // branch-free: independent loads of successive j
+      const bool skip = j == i;
+      const int p = skip ? 0 : pair_idx(i, j);
+      const double gj = Ga[3 * p + q] * sh_u[p];
+      s += skip ? 0.0 : ((i > j) ? -gj : gj);  // dx_p/dR_i = -g_p if i is the first atom of p, else +g_p
     }
     if (add_lambda) s = fma(lam, v[a * B + l], s);
     out[a * B + l] = s;
@@ -250,11 +254,12 @@ __global__ void kcol_kernel(const int64_t* __restrict__ cols, int64_t ncols, int
     for (int l2 = threadIdx.x; l2 < B; l2 += blockDim.x) {
       int i2 = l2 / 3, q2 = l2 - 3 * i2;
       double s = 0.0;
+#pragma unroll 4
       for (int j = 0; j < N; ++j) {
-        if (j == i2) continue;
-        int p = pair_idx(i2, j);
-        double gj = Ga[3 * p + q2] * u[p];
-        s += (i2 > j) ? -gj : gj;
+        const bool skip = j == i2;
+        const int p = skip ? 0 : pair_idx(i2, j);
+        const double gj = Ga[3 * p + q2] * u[p];
+        s += skip ? 0.0 : ((i2 > j) ? -gj : gj);
       }
       out[c * ldo + a * B + l2] = s;
     }
@@ -313,11 +318,12 @@ __global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restric
   for (int l2 = lane; l2 < B; l2 += 32) {
     const int i2 = l2 / 3, q2 = l2 - 3 * i2;
     double s = 0.0;
-    for (int j = 0; j < N; ++j) {
-      if (j == i2) continue;
-      const int p = pair_idx(i2, j);
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) {  // branch-free: independent loads of successive j
+      const bool skip = j == i2;
+      const int p = skip ? 0 : pair_idx(i2, j);
       const double gj = Ga[3 * p + q2] * u[p];
-      s += (i2 > j) ? -gj : gj;
+      s += skip ? 0.0 : ((i2 > j) ? -gj : gj);
     }
     out[c * ldo + a * B + l2] = s;
   }

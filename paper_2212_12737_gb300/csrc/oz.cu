@@ -102,6 +102,13 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
       : "r"(taddr));
 }
 
+// 8 columns of one TMEM lane quarter (32x32b.x8), without waiting for completion
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
 // largest |x| of the CTA (256 threads), and the exponent ex with every |x| < 2^ex
 __device__ __forceinline__ int chunk_exponent(float m, float* red) {
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -132,6 +139,19 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(const double* __rest
     if (t2 && q == 0) t2[row] = split_d(t[row]);
   }
   slice_write(xs, ex, sl, row, k, Rp, Kp);
+}
+
+// Same slicing for FP32 input rows (the FP32-stored Nystrom factor): hi = x, lo = 0.
+__global__ void __launch_bounds__(256) oz_slice_rows_f32_kernel(const float* __restrict__ X, int64_t ldx, int64_t K,
+                                                                int64_t rows, int64_t Rp, int64_t Kp,
+                                                                bf16* __restrict__ sl, int* __restrict__ e) {
+  __shared__ float red[8];
+  const int64_t row = blockIdx.x, q = blockIdx.y;
+  const int64_t k = q * oz::KC + threadIdx.x;
+  const float x = k < K ? X[row * ldx + k] : 0.f;
+  const int ex = chunk_exponent(fabsf(x), red);
+  if (threadIdx.x == 0) e[q * rows + row] = ex;
+  slice_write(make_float2(x, 0.f), ex, sl, row, k, Rp, Kp);
 }
 
 // XT (cols x rows) = X^T, X rows x cols with row stride ldx (32 x 32 tiles)
@@ -403,6 +423,228 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Same sliced product accumulated over ALL K chunks inside the CTA, FP64 output:
+//   C[m][n] = sum_chunks 2^(eA + eB) sum_levels acc_level 2^-7(level + 2)
+// The MMA warp signals the end of each chunk on cdone; the 8 epilogue warps read the 7
+// level accumulators of their 32 columns, add the scaled chunk value into a running
+// double-float sum held in registers, and release the TMEM on tfree before the MMA
+// warp starts the next chunk (whose first MMA per level overwrites).  lower_only:
+// tiles wholly above the diagonal exit at once (symmetric products).
+__global__ void __launch_bounds__(kThreads, 1)
+    oz_gemm_acc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
+                       int Bp, int M, int N, int num_kb, const int* __restrict__ eA, const int* __restrict__ eB,
+                       double* __restrict__ C, int64_t ldc, int lower_only, int* __restrict__ err) {
+  const int n0 = blockIdx.x * oz::BN, m0 = blockIdx.y * oz::BM;
+  if (lower_only && n0 >= m0 + oz::BM) return;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + 2 * kBGroup;
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + kSmemData);
+  uint64_t* bempty = bfull + 2;
+  uint64_t* afull = bempty + 2;
+  uint64_t* aempty = afull + kAStages;
+  uint64_t* cdone = aempty + kAStages;
+  uint64_t* tfree = cdone + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfree + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (num_kb + kKbPerChunk - 1) / kKbPerChunk;
+
+  if (threadIdx.x == 0) {
+    for (int g = 0; g < 2; ++g) {
+      tc::mbar_init(&bfull[g], 1);
+      tc::mbar_init(&bempty[g], 1);
+    }
+    for (int s = 0; s < kAStages; ++s) {
+      tc::mbar_init(&afull[s], 1);
+      tc::mbar_init(&aempty[s], 1);
+    }
+    tc::mbar_init(cdone, 1);
+    tc::mbar_init(tfree, 8);  // one arrival per epilogue warp
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer, A slices (all k-blocks)
+    for (int kb = 0; kb < num_kb; ++kb) {
+      bool ok = true;
+      for (int i = 0; i < oz::S; ++i) {
+        const int ai = kb * oz::S + i;
+        const int s = ai % kAStages;
+        const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
+        if (!mbar_wait_spin(&aempty[s], ph ^ 1u)) {
+          atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        tc::mbar_expect_tx(&afull[s], kATile);
+        tc::tma_load_2d(sA + s * kATile, &mapA, &afull[s], kb * oz::KB, i * Ap + m0);
+      }
+      if (!ok) break;
+    }
+  } else if (warp == 2 && lane == 0) {
+    // ---------------- TMA producer, B slice groups
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int g = kb & 1;
+      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
+      if (!mbar_wait_spin(&bempty[g], gph ^ 1u)) {
+        atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      tc::mbar_expect_tx(&bfull[g], kBGroup);
+      for (int j = 0; j < oz::S; ++j)
+        tc::tma_load_2d(sB + (g * oz::S + j) * kBTile, &mapB, &bfull[g], kb * oz::KB, j * Bp + n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
+    const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
+    const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
+    bool ok = true;
+    for (int kb = 0; kb < num_kb && ok; ++kb) {
+      const int q = kb / kKbPerChunk;
+      const bool chunk_start = (kb % kKbPerChunk) == 0;
+      if (chunk_start && q > 0) {  // the epilogue must have read chunk q-1
+        if (!mbar_wait_spin(tfree, (uint32_t)(q - 1) & 1u)) {
+          atomicExch(err, tc::ERR_TIMEOUT_DONE);
+          *abort_flag = 1;
+          break;
+        }
+        tc::fence_after_sync();
+      }
+      const int g = kb & 1;
+      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
+      if (!mbar_wait_spin(&bfull[g], gph)) {
+        atomicExch(err, tc::ERR_TIMEOUT_FULL);
+        *abort_flag = 1;
+        break;
+      }
+      for (int i = 0; i < oz::S; ++i) {
+        const int ai = kb * oz::S + i;
+        const int s = ai % kAStages;
+        const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
+        if (!mbar_wait_spin(&afull[s], ph)) {
+          atomicExch(err, tc::ERR_TIMEOUT_FULL);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
+        const uint64_t bd = bdesc0 + (uint64_t)(g * oz::S * (kBTile >> 4));
+        const uint32_t first = (!chunk_start || i > 0) ? 1u : 0u;
+#pragma unroll
+        for (int j = 0; j < oz::S; ++j) {
+          if (i + j < oz::S) {
+            const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
+            const uint64_t bj = bd + (uint64_t)(j * (kBTile >> 4));
+            tc::mma_issue<true>(d, ad, bj, idesc, first);
+            tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
+            tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
+            tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+          }
+        }
+        tc::mma_commit(&aempty[s]);
+      }
+      if (!ok) break;
+      tc::mma_commit(&bempty[g]);
+      if ((kb % kKbPerChunk) == kKbPerChunk - 1 || kb == num_kb - 1) tc::mma_commit(cdone);
+    }
+  } else if (warp >= 3) {
+    // ---------------- epilogue: running double-float sums of 32 columns per thread
+    const int quarter = warp & 3;
+    const int cbase = ((warp - 3) >> 2) * 32;
+    const int row = m0 + quarter * 32 + lane;
+    float rh[32], rl[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) rh[t] = rl[t] = 0.f;
+    bool go = true;
+    for (int q = 0; q < nchunks && go; ++q) {
+      int okw = 1;
+      if (lane == 0) {
+        okw = tc::mbar_wait(cdone, (uint32_t)q & 1u) ? 1 : 0;
+        if (!okw) {
+          atomicExch(err, tc::ERR_TIMEOUT_DONE);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) okw = 0;
+      }
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
+        go = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const int ea = row < M ? eA[(int64_t)q * M + row] : 0;
+#pragma unroll
+      for (int c8 = 0; c8 < 32; c8 += 8) {
+        uint32_t v[oz::S][8];
+#pragma unroll
+        for (int L = 0; L < oz::S; ++L) tmem_ld8_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * oz::BN + cbase + c8), v[L]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float f4 = __uint_as_float(v[4][t]), f5 = __uint_as_float(v[5][t]), f6 = __uint_as_float(v[6][t]);
+          float tail = __fmul_rn(f6, pow2f(-oz::BITS * 8));
+          tail = __fadd_rn(tail, __fmul_rn(f5, pow2f(-oz::BITS * 7)));
+          tail = __fadd_rn(tail, __fmul_rn(f4, pow2f(-oz::BITS * 6)));
+          float hh = tail, ll = 0.f;
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[3][t]), pow2f(-oz::BITS * 5)));
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[2][t]), pow2f(-oz::BITS * 4)));
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[1][t]), pow2f(-oz::BITS * 3)));
+          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[0][t]), pow2f(-oz::BITS * 2)));
+          const int col = n0 + cbase + c8 + t;
+          const int ex = ea + (col < N ? eB[(int64_t)q * N + col] : 0);
+          df_add(rh[c8 + t], rl[c8 + t], scale2(hh, ex), scale2(ll, ex));
+        }
+      }
+      // this warp has read chunk q: release the accumulators
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
+    }
+    if (go && row < M) {
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int col = n0 + cbase + t;
+        if (col < N) C[(int64_t)row * ldc + col] = (double)rh[t] + (double)rl[t];
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    // all MMAs have completed once the last chunk was signalled (or a wait gave up)
+    if (lane == 0 && nchunks > 0) (void)tc::mbar_wait(cdone, (uint32_t)(nchunks - 1) & 1u);
+    __syncwarp();
+    tc::fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
 // ------------------------------------------------------------ nonlinear step and back-projection
 // beta_ab = c^2 S_ab (T_ab - t_b) for the 256 b of chunk q of row a, in double-float;
 // written as GEMM 2's sliced A operand, plus the chunk's row sum.
@@ -480,11 +722,12 @@ __global__ void __launch_bounds__(128) oz_backproj_kernel(const float2* __restri
   for (int l = threadIdx.x; l < B; l += blockDim.x) {
     const int i = l / 3, qd = l - 3 * i;
     double s = 0.0;
-    for (int j = 0; j < N; ++j) {
-      if (j == i) continue;
-      const int p = i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i;
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) {  // branch-free: independent loads of successive j
+      const bool skip = j == i;
+      const int p = skip ? 0 : (i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i);
       const double gj = Ga[3 * p + qd] * sh_u[p];
-      s += (i > j) ? -gj : gj;  // d x_p / d R_i = -g_p when i is the first atom of pair p
+      s += skip ? 0.0 : ((i > j) ? -gj : gj);  // d x_p / d R_i = -g_p when i is the first atom of pair p
     }
     if (add_lambda) s = fma(lam, v[a * B + l], s);
     out[a * B + l] = s;
@@ -644,6 +887,45 @@ void oz_destroy(OzMatvec& oz) {
   for (void* p : oz.allocs) cudaFree(p);
   oz.allocs.clear();
   oz.ready = false;
+}
+
+gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64_t ldc, cudaStream_t st) {
+  if (n <= 0 || k <= 0) return fail(GDML_ERR_ARG, "oz_syrk_lower: empty sizes");
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(oz_gemm_acc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal) !=
+        cudaSuccess)
+      return fail(GDML_ERR_CUDA, "cudaFuncSetAttribute(sliced syrk)");
+    attr_set = true;
+  }
+  OzMatvec t;
+  OzOperand a;
+  // the k columns of L (stride n) are the rows of L^T: one operand serves as A and B
+  gdml_status s = make_operand(t, a, k, n, oz::BM, st);
+  CUtensorMap mapB;
+  if (s == GDML_OK && !make_kmajor_map(&mapB, a.slices, true, (uint64_t)a.Kp, (uint64_t)(oz::S * a.Rp),
+                                       (uint64_t)a.Kp, (uint32_t)oz::BN))
+    s = fail(GDML_ERR_CUDA, "cuTensorMapEncodeTiled failed (sliced syrk)");
+  if (s == GDML_OK) s = oz_alloc(t, &t.err, 1, st);
+  if (s == GDML_OK) {
+    dim3 g((unsigned)k, (unsigned)a.nchunks);
+    { oz_slice_rows_f32_kernel<<<g, 256, 0, st>>>(L, n, n, k, a.Rp, a.Kp, (bf16*)a.slices, a.e); count_launch(); }
+    dim3 grid((unsigned)cdiv(k, oz::BN), (unsigned)cdiv(k, oz::BM));
+    { oz_gemm_acc_kernel<<<grid, kThreads, kSmemTotal, st>>>(a.map, mapB, (int)a.Rp, (int)a.Rp, (int)k, (int)k, (int)(a.Kp / oz::KB), a.e, a.e, C, ldc, 1, t.err); count_launch(); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = fail(GDML_ERR_CUDA, std::string("sliced syrk launch: ") + cudaGetErrorString(e));
+  }
+  if (s == GDML_OK) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, t.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      s = fail(GDML_ERR_CUDA, "sliced syrk: synchronise");
+    else if (h)
+      s = fail(GDML_ERR_TIMEOUT, "sliced syrk: a tcgen05 pipeline wait timed out");
+  }
+  cudaStreamSynchronize(st);
+  oz_destroy(t);
+  return s;
 }
 
 gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,

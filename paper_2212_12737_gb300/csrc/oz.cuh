@@ -79,6 +79,11 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
 gdml_status oz_check(OzMatvec& oz, cudaStream_t st);
 void oz_destroy(OzMatvec& oz);
 
+// lower triangle of C = L^T L (k x k, FP64, row stride ldc) for the FP32 n x k factor L
+// (column j at L + j n), through the sliced tensor-core GEMM with in-CTA accumulation
+// over all 256-entry chunks of n.  Synchronises the stream.
+gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64_t ldc, cudaStream_t st);
+
 // test hook: C (M x N, FP64) = A (M x K) B (N x K)^T through the sliced tensor-core GEMM
 gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,
                          cudaStream_t st);

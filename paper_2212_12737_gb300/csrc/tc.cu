@@ -202,11 +202,12 @@ __global__ void tc_backproj_kernel(const float* __restrict__ U, int splits, int6
   for (int l = threadIdx.x; l < B; l += blockDim.x) {
     const int i = l / 3, q = l - 3 * i;
     float s = 0.f;
-    for (int j = 0; j < N; ++j) {
-      if (j == i) continue;
-      const int p = i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i;
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) {  // branch-free: independent loads of successive j
+      const bool skip = j == i;
+      const int p = skip ? 0 : (i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i);
       const float gj = Ga[3 * p + q] * sh_uf[p];
-      s += (i > j) ? -gj : gj;
+      s += skip ? 0.f : ((i > j) ? -gj : gj);
     }
     double o = (double)s;
     if (add_lambda) o = fma(lam, v[a * B + l], o);
