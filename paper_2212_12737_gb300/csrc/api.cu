@@ -672,6 +672,8 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     if (df_precond(c)) {
       TRY(s.get(&a.schur, (size_t)(pivchol_schur_groups() * n)));
       TRY(s.get(&a.prow, (size_t)k));
+      TRY(s.get(&a.posof, (size_t)n));
+      CTRY(c, cudaMemcpyAsync(a.posof, hperm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
       CTRY(c, cudaMemsetAsync(c->Lf, 0, n * k * sizeof(float), c->st));
       pivchol_run_df(a, c->Lf, c->st);
     } else {

@@ -9,6 +9,8 @@
 //  beta       beta_ab = c^2 S_ab (T_ab - t_b), T = Xc W^T; rowsum_a = sum_b beta_ab
 //  backproj   (K v)_a = J_a^T u'_a with u'_a = U_a - rowsum_a xc_a, plus lambda v
 //  kcol       columns K[:, c] = J_a^T H_ab J_b e_l for a list of column indices c = b*3N + l
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -266,10 +268,12 @@ __global__ void kcol_kernel(const int64_t* __restrict__ cols, int64_t ncols, int
   }
 }
 
-// Same columns, one warp per geometry a (8 per CTA, grid (ceil(M/8), ncols)): the
-// warp forms s = delta_(i,.) . w (shuffle reduction), u = coef delta + A_ab w on the
-// pairs of atom i (in its own shared-memory slice of D doubles), then the 3N outputs
-// J_a^T u.  w = J_b e_l depends only on the column and is built once per CTA.
+// Same columns, one warp per geometry a (W warps per CTA, grid (ceil(M/W), ncols)).
+// All operands of a geometry (x_a, its Jacobian factors g_a) and of the column's
+// geometry b (x_b, w = J_b e_l) are first staged in shared memory with independent,
+// coalesced loads; the warp then forms s = delta_(i,.) . w (shuffle reduction),
+// u = coef delta + A_ab w on the pairs of atom i, and the 3N outputs J_a^T u from
+// shared memory only.  Shared memory: D + N doubles per CTA plus 5 D per warp.
 __global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restrict__ cols,
                                                         const double* __restrict__ X, const double* __restrict__ G,
                                                         const double* __restrict__ S, const double* __restrict__ A,
@@ -278,9 +282,13 @@ __global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restric
                                                         const int* __restrict__ stop_flag) {
   if (stop_flag && *stop_flag) return;
   extern __shared__ double shw[];
-  double* wsp = shw;                     // N: (J_b e_l) on the pairs (i, j), indexed by partner j
+  const int W = blockDim.x >> 5;
+  double* wsp = shw;            // N: (J_b e_l) on the pairs (i, j), indexed by partner j
+  double* sxb = shw + N;        // D: x_b
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* u = shw + N + warp * D;        // this warp's u
+  double* sxa = shw + N + D + (size_t)warp * 5 * D;  // D: x_a
+  double* u = sxa + D;                                 // D
+  double* sga = u + D;                                 // 3 D: g_a
   const int64_t c = blockIdx.y;
   const int64_t col = cols[c];
   const int B = 3 * N;
@@ -296,21 +304,27 @@ __global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restric
     }
     wsp[j] = w;
   }
+  for (int p = threadIdx.x; p < D; p += blockDim.x) sxb[p] = Xb[p];
+  const int64_t a = (int64_t)blockIdx.x * W + warp;
+  const bool live = a < M;
+  if (live) {
+    const double* Xa = X + a * D;
+    const double* Ga = G + a * D * 3;
+    for (int p = lane; p < D; p += 32) sxa[p] = Xa[p];
+    for (int e = lane; e < 3 * D; e += 32) sga[e] = Ga[e];
+  }
   __syncthreads();
-  const int64_t a = (int64_t)blockIdx.x * 8 + warp;
-  if (a >= M) return;
-  const double* Xa = X + a * D;
-  const double* Ga = G + a * D * 3;
+  if (!live) return;
   double sd = 0.0;
   for (int j = lane; j < N; j += 32)
     if (j != i) {
       const int p = pair_idx(i, j);
-      sd = fma(Xa[p] - Xb[p], wsp[j], sd);
+      sd = fma(sxa[p] - sxb[p], wsp[j], sd);
     }
   for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
   const double Aab = A[a * ldA + b];
   const double coef = -c2 * S[a * M + b] * sd;
-  for (int p = lane; p < D; p += 32) u[p] = coef * (Xa[p] - Xb[p]);
+  for (int p = lane; p < D; p += 32) u[p] = coef * (sxa[p] - sxb[p]);
   __syncwarp();
   for (int j = lane; j < N; j += 32)
     if (j != i) u[pair_idx(i, j)] += Aab * wsp[j];
@@ -318,11 +332,10 @@ __global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restric
   for (int l2 = lane; l2 < B; l2 += 32) {
     const int i2 = l2 / 3, q2 = l2 - 3 * i2;
     double s = 0.0;
-#pragma unroll 4
-    for (int j = 0; j < N; ++j) {  // branch-free: independent loads of successive j
+    for (int j = 0; j < N; ++j) {
       const bool skip = j == i2;
       const int p = skip ? 0 : pair_idx(i2, j);
-      const double gj = Ga[3 * p + q2] * u[p];
+      const double gj = sga[3 * p + q2] * u[p];
       s += skip ? 0.0 : ((i2 > j) ? -gj : gj);
     }
     out[c * ldo + a * B + l2] = s;
@@ -374,12 +387,18 @@ template void launch_backproj<float>(const float*, int64_t, int, int64_t, const 
 void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* S,
                  const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
                  const int* stop_flag, cudaStream_t st) {
-  const size_t wsmem = ((size_t)N + 8 * (size_t)D) * sizeof(double);
-  if (wsmem <= 96 * 1024 && ncols <= 65535) {
-    if (wsmem > 48 * 1024)
+  // warps per CTA so that the staged operands fit in 200 KB of shared memory
+  const size_t per_warp = 5 * (size_t)D * sizeof(double), fixed = ((size_t)N + D) * sizeof(double);
+  const int W = (int)std::min<size_t>(8, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / per_warp);
+  if (W >= 1 && ncols <= 65535) {
+    const size_t wsmem = fixed + W * per_warp;
+    static size_t attr = 0;
+    if (wsmem > 48 * 1024 && wsmem > attr) {
       cudaFuncSetAttribute(kcol_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
-    dim3 g((unsigned)cdiv(M, 8), (unsigned)ncols);
-    { kcol_warp_kernel<<<g, 256, wsmem, st>>>(cols, X, G, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag); count_launch(); }
+      attr = wsmem;
+    }
+    dim3 g((unsigned)cdiv(M, W), (unsigned)ncols);
+    { kcol_warp_kernel<<<g, 32 * W, wsmem, st>>>(cols, X, G, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag); count_launch(); }
     return;
   }
   const int per = 8;

@@ -115,6 +115,7 @@ struct PivCholArgs {
   // DF64 form only: pivot-row gather (k floats) and Schur partials (pivchol_schur_groups() * n pairs)
   float* prow = nullptr;
   float2* schur = nullptr;
+  int64_t* posof = nullptr;  // inverse of perm (position of each index)
 };
 int pivchol_schur_groups();
 template <typename TL>

@@ -36,7 +36,8 @@ __device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
 __global__ void __launch_bounds__(kArgThreads) pc_argmax_kernel(
     int64_t m, int64_t n, int do_select, const double* __restrict__ d, int64_t* __restrict__ perm,
     unsigned char* __restrict__ chosen, int64_t* __restrict__ pivots, double* __restrict__ trace,
-    PivState* __restrict__ ps, ArgMaxPart* __restrict__ part, unsigned* __restrict__ ticket) {
+    PivState* __restrict__ ps, ArgMaxPart* __restrict__ part, unsigned* __restrict__ ticket,
+    int64_t* __restrict__ posof = nullptr) {
   if (ps->stop) return;
   __shared__ double sv[kArgThreads];
   __shared__ int64_t sp[kArgThreads];
@@ -111,8 +112,13 @@ __global__ void __launch_bounds__(kArgThreads) pc_argmax_kernel(
     return;
   }
   const int64_t piv = perm[b.pos];
-  perm[b.pos] = perm[m];
+  const int64_t other = perm[m];
+  perm[b.pos] = other;
   perm[m] = piv;
+  if (posof) {
+    posof[other] = b.pos;
+    posof[piv] = m;
+  }
   pivots[m] = piv;
   chosen[piv] = 1;
   ps->lmm = sqrt(d[piv]);
@@ -154,13 +160,13 @@ __global__ void __launch_bounds__(256) pc_update_kernel(int64_t m, int64_t n, TL
   }
 }
 
-// Alg. 1 step with FP32-stored L (DF64 contexts), three kernels:
-//   gather:  prow[j] = l_{pivot, j}, j < m (contiguous copy of the pivot row)
+// Alg. 1 step with FP32-stored L (DF64 contexts): the kernel column, then two kernels:
 //   schur:   partial Schur sums over column groups, s_g(i) = sum_{j in g} l_{pivot,j} l_{i,j},
 //            exact FP32 products summed in double-float; 512 rows per CTA, each warp
 //            streams whole 2 KB column segments with the next column's loads in flight
 //   finish:  s_i = sum_g s_g(i) (fixed order), l_{i,m} = (k_{m,i} - s_i) / l_{pivot,m} in FP64,
-//            stored in FP32; the residual diagonal is updated with the stored value.
+//            stored in FP32; the residual diagonal is updated with the stored value, and
+//            the pivot of step m + 1 is selected and its row gathered (prow) in the same pass.
 constexpr int kSchurRows = 512;
 constexpr int kSchurMaxGroups = 16;
 
@@ -171,14 +177,6 @@ __device__ __forceinline__ void df_add_pair_pc(float& h, float& l, float bh, flo
   e += l + bl;
   h = s + e;
   l = e - (h - s);
-}
-
-__global__ void pc_gather_row_kernel(int64_t m, int64_t n, const float* __restrict__ L, const PivState* __restrict__ ps,
-                                     float* __restrict__ prow) {
-  if (ps->stop) return;
-  const int64_t piv = ps->piv;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
-    prow[j] = L[piv + j * n];
 }
 
 template <bool VEC>
@@ -247,29 +245,123 @@ __global__ void __launch_bounds__(256, 2) pc_schur_df_kernel(int64_t m, int64_t 
   }
 }
 
-__global__ void __launch_bounds__(256) pc_finish_df_kernel(int64_t m, int64_t n, int groups, float* __restrict__ L,
-                                                           const float2* __restrict__ schur,
-                                                           const double* __restrict__ col, double* __restrict__ d,
-                                                           const unsigned char* __restrict__ chosen,
-                                                           const PivState* __restrict__ ps) {
+// Finish step m and select the pivot of step m + 1 in one kernel: every unchosen row i
+// forms l_{i,m} = (k_{m,i} - s_i) / l_{pivot,m} (s_i from the Schur partials, FP64
+// division, FP32 storage), updates its residual diagonal and offers (d_i, position of i)
+// to the argmax of step m + 1 (ties -> lowest position, as pc_argmax_kernel); the
+// per-CTA results are combined by the last CTA in a fixed order, which records the
+// residual trace after step m, performs the swap of Alg. 1 and gathers the new pivot's
+// row of L (columns 0..m) for the next Schur pass.  select = 0 on the last step.
+__global__ void __launch_bounds__(kArgThreads) pc_finish_select_df_kernel(
+    int64_t m, int64_t n, int groups, int select, float* __restrict__ L, const float2* __restrict__ schur,
+    const double* __restrict__ col, double* __restrict__ d, unsigned char* __restrict__ chosen,
+    int64_t* __restrict__ perm, int64_t* __restrict__ posof, int64_t* __restrict__ pivots,
+    double* __restrict__ trace, PivState* __restrict__ ps, ArgMaxPart* __restrict__ part,
+    unsigned* __restrict__ ticket, float* __restrict__ prow) {
   if (ps->stop) return;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  __shared__ double sv[kArgThreads];
+  __shared__ int64_t sp[kArgThreads];
+  __shared__ double ss[kArgThreads];
+  __shared__ bool last;
+  __shared__ int64_t s_piv;
   const int64_t piv = ps->piv;
-  if (!chosen[i]) {
-    float sh = 0.f, sl = 0.f;
-    for (int g = 0; g < groups; ++g) {
-      const float2 v = schur[(int64_t)g * n + i];
-      df_add_pair_pc(sh, sl, v.x, v.y);
+  const double lmm = ps->lmm;
+  ArgMax best{-1.0 / 0.0, INT64_MAX};
+  double sum = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kArgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kArgThreads) {
+    if (!chosen[i]) {
+      float sh = 0.f, sl = 0.f;
+      for (int g = 0; g < groups; ++g) {
+        const float2 v = schur[(int64_t)g * n + i];
+        df_add_pair_pc(sh, sl, v.x, v.y);
+      }
+      const double lv = (col[i] - ((double)sh + (double)sl)) / lmm;
+      const float lst = (float)lv;
+      L[i + m * n] = lst;
+      const double lr = (double)lst;
+      const double dn = __dsub_rn(d[i], __dmul_rn(lr, lr));
+      d[i] = dn;
+      sum += dn;
+      best = better(best, ArgMax{dn, posof[i]});
+    } else if (i == piv) {
+      L[i + m * n] = (float)lmm;
     }
-    const double lv = (col[i] - ((double)sh + (double)sl)) / ps->lmm;
-    const float lst = (float)lv;
-    L[i + m * n] = lst;
-    const double lr = (double)lst;
-    d[i] = __dsub_rn(d[i], __dmul_rn(lr, lr));
-  } else if (i == piv) {
-    L[i + m * n] = (float)ps->lmm;
   }
+  sv[threadIdx.x] = best.v;
+  sp[threadIdx.x] = best.pos;
+  ss[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = kArgThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ArgMax r = better(ArgMax{sv[threadIdx.x], sp[threadIdx.x]}, ArgMax{sv[threadIdx.x + o], sp[threadIdx.x + o]});
+      sv[threadIdx.x] = r.v;
+      sp[threadIdx.x] = r.pos;
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x].v = sv[0];
+    part[blockIdx.x].pos = sp[0];
+    part[blockIdx.x].sum = ss[0];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  {
+    ArgMax bt{-1.0 / 0.0, INT64_MAX};
+    double st = 0.0;
+    volatile ArgMaxPart* vp = part;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += kArgThreads) {
+      bt = better(bt, ArgMax{vp[q].v, vp[q].pos});
+      st += vp[q].sum;
+    }
+    sv[threadIdx.x] = bt.v;
+    sp[threadIdx.x] = bt.pos;
+    ss[threadIdx.x] = st;
+  }
+  __syncthreads();
+  for (int o = kArgThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ArgMax r = better(ArgMax{sv[threadIdx.x], sp[threadIdx.x]}, ArgMax{sv[threadIdx.x + o], sp[threadIdx.x + o]});
+      sv[threadIdx.x] = r.v;
+      sp[threadIdx.x] = r.pos;
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const ArgMax b{sv[0], sp[0]};
+    *ticket = 0u;
+    if (trace) trace[m] = ss[0];
+    s_piv = -1;
+    if (select) {
+      const int64_t m1 = m + 1;
+      if (!(b.v > 0.0) || b.pos >= n) {
+        ps->stop = 1;
+        ps->rank = m1;
+      } else {
+        const int64_t p = perm[b.pos];
+        const int64_t other = perm[m1];
+        perm[b.pos] = other;
+        perm[m1] = p;
+        posof[other] = b.pos;
+        posof[p] = m1;
+        pivots[m1] = p;
+        chosen[p] = 1;
+        ps->lmm = sqrt(d[p]);
+        ps->piv = p;
+        ps->rank = m1 + 1;
+        s_piv = p;
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t p = s_piv;
+  if (p >= 0)  // the next pivot's row of L, columns 0..m (column m written above, fenced)
+    for (int64_t j = threadIdx.x; j <= m; j += kArgThreads) prow[j] = L[p + j * n];
 }
 
 int pivchol_schur_groups() { return kSchurMaxGroups; }
@@ -277,26 +369,25 @@ int pivchol_schur_groups() { return kSchurMaxGroups; }
 void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
   const int64_t rblocks = cdiv(a.n, kSchurRows);
   const bool vec = (a.n % 4) == 0;
+  const unsigned fblocks = (unsigned)std::min<int64_t>(cdiv(a.n, kArgThreads), kArgBlocks);
+  // step 0's pivot
+  { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(0, a.n, 1, a.d, a.perm, a.chosen, a.pivots, nullptr,
+                                                       a.ps, a.part, a.ticket, a.posof); count_launch(); }
   for (int64_t m = 0; m < a.k; ++m) {
-    { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(m, a.n, 1, a.d, a.perm, a.chosen, a.pivots, a.trace,
-                                                         a.ps, a.part, a.ticket); count_launch(); }
     a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
     // column groups: enough CTAs for ~4 per SM, at least 32 columns per group
     int groups = 0;
     if (m > 0) {
       const int64_t want = cdiv(4 * kNumSMs, rblocks);
       groups = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)kSchurMaxGroups, std::max<int64_t>(1, m / 32)}));
-      { pc_gather_row_kernel<<<(unsigned)std::min<int64_t>(cdiv(m, 256), 64), 256, 0, st>>>(m, a.n, L, a.ps, a.prow); count_launch(); }
       dim3 g((unsigned)rblocks, (unsigned)groups);
       if (vec)
         { pc_schur_df_kernel<true><<<g, 256, 0, st>>>(m, a.n, L, a.prow, a.ps, a.schur); count_launch(); }
       else
         { pc_schur_df_kernel<false><<<g, 256, 0, st>>>(m, a.n, L, a.prow, a.ps, a.schur); count_launch(); }
     }
-    { pc_finish_df_kernel<<<(unsigned)cdiv(a.n, 256), 256, 0, st>>>(m, a.n, groups, L, a.schur, a.col, a.d, a.chosen, a.ps); count_launch(); }
+    { pc_finish_select_df_kernel<<<fblocks, kArgThreads, 0, st>>>(m, a.n, groups, m + 1 < a.k ? 1 : 0, L, a.schur, a.col, a.d, a.chosen, a.perm, a.posof, a.pivots, a.trace, a.ps, a.part, a.ticket, a.prow); count_launch(); }
   }
-  { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(a.k, a.n, 0, a.d, a.perm, a.chosen, a.pivots, a.trace,
-                                                       a.ps, a.part, a.ticket); count_launch(); }
 }
 
 // ---------------------------------------------------------------- host driver

@@ -197,10 +197,57 @@ __device__ __forceinline__ void load_col(const float* __restrict__ col, int lane
   for (int t = 0; t < 4; ++t) v[t] = load4<VEC>(col, 128 * t + 4 * lane, rem);
 }
 
+// 8 per-lane double-float partials (one per column) -> column sums: a reduce-scatter
+// across the warp (xor 16, 8, 4 halve the columns a lane keeps; xor 2, 1 finish the
+// one left), 9 exchanges instead of 8 x 5.  Lane l ends with column
+// ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1) summed over all 32 lanes.
+__device__ __forceinline__ void reduce_scatter8(float (&h)[8], float (&l)[8], int lane, float& oh, float& ol) {
+  const bool up4 = lane & 16, up2 = lane & 8, up1 = lane & 4;
+  float h4[4], l4[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float sh = up4 ? h[q] : h[4 + q], sl = up4 ? l[q] : l[4 + q];
+    float kh = up4 ? h[4 + q] : h[q], kl = up4 ? l[4 + q] : l[q];
+    df_add_pair(kh, kl, __shfl_xor_sync(0xffffffffu, sh, 16), __shfl_xor_sync(0xffffffffu, sl, 16));
+    h4[q] = kh;
+    l4[q] = kl;
+  }
+  float h2[2], l2[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float sh = up2 ? h4[q] : h4[2 + q], sl = up2 ? l4[q] : l4[2 + q];
+    float kh = up2 ? h4[2 + q] : h4[q], kl = up2 ? l4[2 + q] : l4[q];
+    df_add_pair(kh, kl, __shfl_xor_sync(0xffffffffu, sh, 8), __shfl_xor_sync(0xffffffffu, sl, 8));
+    h2[q] = kh;
+    l2[q] = kl;
+  }
+  {
+    const float sh = up1 ? h2[0] : h2[1], sl = up1 ? l2[0] : l2[1];
+    oh = up1 ? h2[1] : h2[0];
+    ol = up1 ? l2[1] : l2[0];
+    df_add_pair(oh, ol, __shfl_xor_sync(0xffffffffu, sh, 4), __shfl_xor_sync(0xffffffffu, sl, 4));
+  }
+  for (int o = 2; o > 0; o >>= 1) {
+    const float sh = __shfl_xor_sync(0xffffffffu, oh, o), sl = __shfl_xor_sync(0xffffffffu, ol, o);
+    df_add_pair(oh, ol, sh, sl);
+  }
+}
+
+__device__ __forceinline__ void dot_col(const float4 (&a)[4], const float2 (&rv)[4][4], float& h, float& l) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    df_add_prod(h, l, a[t].x, rv[t][0].x, rv[t][0].y);
+    df_add_prod(h, l, a[t].y, rv[t][1].x, rv[t][1].y);
+    df_add_prod(h, l, a[t].z, rv[t][2].x, rv[t][2].y);
+    df_add_prod(h, l, a[t].w, rv[t][3].x, rv[t][3].y);
+  }
+}
+
 // part[j * nchunks + chunk] = sum over the chunk's 512 rows of L[i + j n] r[i]; r is
-// held in registers as float pairs, each warp streams 8 columns two at a time with
-// the next pair's loads issued before the current pair's arithmetic.
-// VEC: n % 4 == 0 (aligned float4 loads).
+// held in registers as float pairs.  Each warp streams its 8 columns (2 KB contiguous
+// per column) two at a time with the next pair's loads in flight (fully unrolled, two
+// register buffers), keeps one per-lane partial per column and reduces all 8 at the
+// end.  VEC: n % 4 == 0 (aligned float4 loads).
 template <bool VEC>
 __global__ void __launch_bounds__(256, 2) gemv_t_df_kernel(const float* __restrict__ L, int64_t n, int64_t k,
                                                            const float2* __restrict__ rs, double* __restrict__ part) {
@@ -217,48 +264,31 @@ __global__ void __launch_bounds__(256, 2) gemv_t_df_kernel(const float* __restri
     }
   const int64_t jw = (int64_t)blockIdx.x * kDfTCols + warp * 8;
   if (jw >= k) return;
-  const int64_t jend = jw + 8 < k ? jw + 8 : k;
-  float4 a[4], b[4];
-  load_col<VEC>(L + jw * n + i0, lane, rem, a);
-  load_col<VEC>(L + (jw + 1 < jend ? jw + 1 : jw) * n + i0, lane, rem, b);
-#pragma unroll 1
-  for (int64_t j = jw; j < jend; j += 2) {
-    float4 na[4], nb[4];
-    const bool more = j + 2 < jend;
-    if (more) {
-      load_col<VEC>(L + (j + 2) * n + i0, lane, rem, na);
-      load_col<VEC>(L + (j + 3 < jend ? j + 3 : j + 2) * n + i0, lane, rem, nb);
-    }
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+  const int ncol = (int)(jw + 8 < k ? 8 : k - jw);  // warp-uniform
+  const float* base = L + jw * n + i0;
+  float h[8], l[8];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      df_add_prod(h0, l0, a[t].x, rv[t][0].x, rv[t][0].y);
-      df_add_prod(h1, l1, b[t].x, rv[t][0].x, rv[t][0].y);
-      df_add_prod(h0, l0, a[t].y, rv[t][1].x, rv[t][1].y);
-      df_add_prod(h1, l1, b[t].y, rv[t][1].x, rv[t][1].y);
-      df_add_prod(h0, l0, a[t].z, rv[t][2].x, rv[t][2].y);
-      df_add_prod(h1, l1, b[t].z, rv[t][2].x, rv[t][2].y);
-      df_add_prod(h0, l0, a[t].w, rv[t][3].x, rv[t][3].y);
-      df_add_prod(h1, l1, b[t].w, rv[t][3].x, rv[t][3].y);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const float a0 = __shfl_xor_sync(0xffffffffu, h0, o), b0 = __shfl_xor_sync(0xffffffffu, l0, o);
-      const float a1 = __shfl_xor_sync(0xffffffffu, h1, o), b1 = __shfl_xor_sync(0xffffffffu, l1, o);
-      df_add_pair(h0, l0, a0, b0);
-      df_add_pair(h1, l1, a1, b1);
-    }
-    if (lane == 0) {
-      part[j * gridDim.y + blockIdx.y] = (double)h0 + (double)l0;
-      if (j + 1 < jend) part[(j + 1) * gridDim.y + blockIdx.y] = (double)h1 + (double)l1;
-    }
-    if (more) {
+  for (int c = 0; c < 8; ++c) h[c] = l[c] = 0.f;
+  float4 a0[4], b0[4], a1[4], b1[4];
+  // column c of this warp is loaded only when c < ncol (never past the matrix)
+  load_col<VEC>(base, lane, rem, a0);
+  if (1 < ncol) load_col<VEC>(base + n, lane, rem, b0);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        a[t] = na[t];
-        b[t] = nb[t];
-      }
-    }
+  for (int p = 0; p < 4; p += 2) {
+    const int c = 2 * p;  // columns c, c+1 in (a0, b0); c+2, c+3 go to (a1, b1)
+    if (c + 2 < ncol) load_col<VEC>(base + (int64_t)(c + 2) * n, lane, rem, a1);
+    if (c + 3 < ncol) load_col<VEC>(base + (int64_t)(c + 3) * n, lane, rem, b1);
+    if (c < ncol) dot_col(a0, rv, h[c], l[c]);
+    if (c + 1 < ncol) dot_col(b0, rv, h[c + 1], l[c + 1]);
+    if (c + 4 < ncol) load_col<VEC>(base + (int64_t)(c + 4) * n, lane, rem, a0);
+    if (c + 5 < ncol) load_col<VEC>(base + (int64_t)(c + 5) * n, lane, rem, b0);
+    if (c + 2 < ncol) dot_col(a1, rv, h[c + 2], l[c + 2]);
+    if (c + 3 < ncol) dot_col(b1, rv, h[c + 3], l[c + 3]);
   }
+  float oh, ol;
+  reduce_scatter8(h, l, lane, oh, ol);
+  const int col = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  if ((lane & 3) == 0 && col < ncol) part[(jw + col) * gridDim.y + blockIdx.y] = (double)oh + (double)ol;
 }
 
 // zp[g * n + i] = sum over column group g of L[i + j n] u[j]: CTA (row block of 512,
@@ -277,14 +307,16 @@ __global__ void __launch_bounds__(256, 2) gemv_n_df_kernel(const float* __restri
   float h[16], l[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) h[e] = l[e] = 0.f;
+  // two columns in flight ahead of the one being summed
   int64_t j = ja + warp;
-  float4 a[4];
+  float4 a[4], b[4];
   if (j < jb) load_col<VEC>(L + j * n + i0, lane, rem, a);
+  if (j + 8 < jb) load_col<VEC>(L + (j + 8) * n + i0, lane, rem, b);
 #pragma unroll 1
   for (; j < jb; j += 8) {
     float4 na[4];
-    const bool more = j + 8 < jb;
-    if (more) load_col<VEC>(L + (j + 8) * n + i0, lane, rem, na);
+    const bool more = j + 16 < jb;
+    if (more) load_col<VEC>(L + (j + 16) * n + i0, lane, rem, na);
     const float2 x = us[j];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -293,9 +325,10 @@ __global__ void __launch_bounds__(256, 2) gemv_n_df_kernel(const float* __restri
       df_add_prod(h[4 * t + 2], l[4 * t + 2], a[t].z, x.x, x.y);
       df_add_prod(h[4 * t + 3], l[4 * t + 3], a[t].w, x.x, x.y);
     }
-    if (more) {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) a[t] = na[t];
+    for (int t = 0; t < 4; ++t) {
+      a[t] = b[t];
+      if (more) b[t] = na[t];
     }
   }
 #pragma unroll
@@ -349,21 +382,49 @@ __global__ void __launch_bounds__(256) symv_df_kernel(const float2* __restrict__
   if (i >= k) return;
   const float2* row = A + i * k;
   float h = 0.f, l = 0.f;
+  // full groups of 8 unconditional loads of A and x per lane ahead of the arithmetic,
+  // spread over 4 independent double-float chains; then the remainder one by one
+  float hq[4] = {0.f, 0.f, 0.f, 0.f}, lq[4] = {0.f, 0.f, 0.f, 0.f};
   if (EVEN) {
-#pragma unroll 4
-    for (int64_t j = 2 * lane; j < k; j += 64) {
-      const float4 a = *reinterpret_cast<const float4*>(row + j);
-      const float4 xv = *reinterpret_cast<const float4*>(x + j);
+    int64_t j0 = 2 * lane;
+    for (; j0 + 7 * 64 < k; j0 += 8 * 64) {
+      float4 a[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a[u] = __ldg(reinterpret_cast<const float4*>(row + j0 + 64 * u));
+        xv[u] = __ldg(reinterpret_cast<const float4*>(x + j0 + 64 * u));
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        df_term(hq[u & 3], lq[u & 3], a[u].x, a[u].y, xv[u].x, xv[u].y);
+        df_term(hq[u & 3], lq[u & 3], a[u].z, a[u].w, xv[u].z, xv[u].w);
+      }
+    }
+    for (; j0 < k; j0 += 64) {
+      const float4 a = *reinterpret_cast<const float4*>(row + j0);
+      const float4 xv = *reinterpret_cast<const float4*>(x + j0);
       df_term(h, l, a.x, a.y, xv.x, xv.y);
       df_term(h, l, a.z, a.w, xv.z, xv.w);
     }
   } else {
-#pragma unroll 4
-    for (int64_t j = lane; j < k; j += 32) {
-      const float2 a = row[j], xv = x[j];
+    int64_t j0 = lane;
+    for (; j0 + 7 * 32 < k; j0 += 8 * 32) {
+      float2 a[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a[u] = row[j0 + 32 * u];
+        xv[u] = x[j0 + 32 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) df_term(hq[u & 3], lq[u & 3], a[u].x, a[u].y, xv[u].x, xv[u].y);
+    }
+    for (; j0 < k; j0 += 32) {
+      const float2 a = row[j0], xv = x[j0];
       df_term(h, l, a.x, a.y, xv.x, xv.y);
     }
   }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) df_add_pair(h, l, hq[q], lq[q]);
   for (int o = 16; o > 0; o >>= 1) {
     const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
     df_add_pair(h, l, oh, ol);
