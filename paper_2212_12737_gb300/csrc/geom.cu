@@ -18,7 +18,8 @@ namespace gdml {
 
 // p = i(i-1)/2 + j with i > j  ->  (i, j)
 __device__ __forceinline__ void pair_of(int p, int& i, int& j) {
-  int ii = (int)((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+  // FP32 estimate (GB300's FP64 pipe is slow), then exact integer correction
+  int ii = (int)((1.f + sqrtf(1.f + 8.f * (float)p)) * 0.5f);
   while (ii * (ii - 1) / 2 > p) --ii;
   while ((ii + 1) * ii / 2 <= p) ++ii;
   i = ii;
@@ -124,29 +125,31 @@ __global__ void kdiag_kernel(const double* __restrict__ G, int64_t M, int N, int
   diag[t] = c2_3 * s;
 }
 
-// one CTA per geometry; W row a written into W (ld = ldW); t_a = xc_a . w_a
-template <int THREADS>
-__global__ void proj_kernel(const double* __restrict__ G, const double* __restrict__ Xc,
-                            const double* __restrict__ v, int N, int D, double* __restrict__ W,
-                            int64_t ldW, double* __restrict__ t) {
-  extern __shared__ double sh_v[];  // 3N
-  __shared__ double red[THREADS / 32];
-  const int64_t a = blockIdx.x;
+// W row a (ld = ldW) and t_a = xc_a . w_a, one warp per geometry (8 per CTA): v_a in
+// the warp's slice of shared memory, lanes over the pairs, t_a by a fixed shuffle tree.
+__global__ void __launch_bounds__(256) proj_warp_kernel(const double* __restrict__ G, const double* __restrict__ Xc,
+                                                        const double* __restrict__ v, int64_t M, int N, int D,
+                                                        double* __restrict__ W, int64_t ldW, double* __restrict__ t) {
+  extern __shared__ double sh_vw[];  // 8 x 3N
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t a = (int64_t)blockIdx.x * 8 + warp;
+  if (a >= M) return;
   const int B = 3 * N;
-  for (int l = threadIdx.x; l < B; l += THREADS) sh_v[l] = v[a * B + l];
-  __syncthreads();
+  double* sv = sh_vw + warp * B;
+  for (int l = lane; l < B; l += 32) sv[l] = v[a * B + l];
+  __syncwarp();
   const double* Ga = G + a * D * 3;
   double part = 0.0;
-  for (int p = threadIdx.x; p < D; p += THREADS) {
+  for (int p = lane; p < D; p += 32) {
     int i, j;
     pair_of(p, i, j);
-    double w = -(Ga[3 * p] * (sh_v[3 * i] - sh_v[3 * j]) + Ga[3 * p + 1] * (sh_v[3 * i + 1] - sh_v[3 * j + 1]) +
-                 Ga[3 * p + 2] * (sh_v[3 * i + 2] - sh_v[3 * j + 2]));
+    const double w = -(Ga[3 * p] * (sv[3 * i] - sv[3 * j]) + Ga[3 * p + 1] * (sv[3 * i + 1] - sv[3 * j + 1]) +
+                       Ga[3 * p + 2] * (sv[3 * i + 2] - sv[3 * j + 2]));
     W[a * ldW + p] = w;
     part = fma(Xc[a * D + p], w, part);
   }
-  double s = block_sum<THREADS>(part, red);
-  if (threadIdx.x == 0) t[a] = s;
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) t[a] = part;
 }
 
 // beta_ab = c^2 S_ab (T_ab - t_b) into Pb[a*ldP + b]; rowsum_a = sum_b beta_ab
@@ -361,7 +364,7 @@ void launch_kdiag(const double* G, int64_t M, int N, int D, double c, double* di
 }
 void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, int N, int D, double* W,
                  int64_t ldW, double* t, cudaStream_t st) {
-  { proj_kernel<256><<<(unsigned)M, 256, 3 * N * sizeof(double), st>>>(G, Xc, v, N, D, W, ldW, t); count_launch(); }
+  { proj_warp_kernel<<<(unsigned)cdiv(M, 8), 256, 8 * 3 * N * sizeof(double), st>>>(G, Xc, v, M, N, D, W, ldW, t); count_launch(); }
 }
 void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
                  int64_t ldP, double* rowsum, cudaStream_t st) {

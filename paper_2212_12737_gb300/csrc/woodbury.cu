@@ -371,65 +371,46 @@ __device__ __forceinline__ void df_term(float& h, float& l, float ah, float al, 
   df_add_pair(h, l, p, e);
 }
 
-// EVEN: k even, so every row and the vector start on 16-byte boundaries (float4 loads)
+// One CTA (256 threads) per row i: every thread loads its share of the row and of x
+// at once (16-byte loads when EVEN: k even, so rows and vectors start on 16-byte
+// boundaries), so the 2000 CTAs keep the L2 busy; per-thread double-float partials
+// are reduced by a fixed shuffle tree and then across the 8 warps in order.
 template <bool EVEN>
 __global__ void __launch_bounds__(256) symv_df_kernel(const float2* __restrict__ A, int64_t k,
                                                       const float2* __restrict__ x, int mode,
                                                       const double* __restrict__ t, double* __restrict__ y,
                                                       float2* __restrict__ y2) {
+  __shared__ float2 red[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-  if (i >= k) return;
+  const int64_t i = blockIdx.x;
   const float2* row = A + i * k;
   float h = 0.f, l = 0.f;
-  // full groups of 8 unconditional loads of A and x per lane ahead of the arithmetic,
-  // spread over 4 independent double-float chains; then the remainder one by one
-  float hq[4] = {0.f, 0.f, 0.f, 0.f}, lq[4] = {0.f, 0.f, 0.f, 0.f};
   if (EVEN) {
-    int64_t j0 = 2 * lane;
-    for (; j0 + 7 * 64 < k; j0 += 8 * 64) {
-      float4 a[8], xv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        a[u] = __ldg(reinterpret_cast<const float4*>(row + j0 + 64 * u));
-        xv[u] = __ldg(reinterpret_cast<const float4*>(x + j0 + 64 * u));
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        df_term(hq[u & 3], lq[u & 3], a[u].x, a[u].y, xv[u].x, xv[u].y);
-        df_term(hq[u & 3], lq[u & 3], a[u].z, a[u].w, xv[u].z, xv[u].w);
-      }
-    }
-    for (; j0 < k; j0 += 64) {
-      const float4 a = *reinterpret_cast<const float4*>(row + j0);
-      const float4 xv = *reinterpret_cast<const float4*>(x + j0);
+#pragma unroll 4
+    for (int64_t j = 2 * (int64_t)threadIdx.x; j < k; j += 512) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(row + j));
+      const float4 xv = __ldg(reinterpret_cast<const float4*>(x + j));
       df_term(h, l, a.x, a.y, xv.x, xv.y);
       df_term(h, l, a.z, a.w, xv.z, xv.w);
     }
   } else {
-    int64_t j0 = lane;
-    for (; j0 + 7 * 32 < k; j0 += 8 * 32) {
-      float2 a[8], xv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        a[u] = row[j0 + 32 * u];
-        xv[u] = x[j0 + 32 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) df_term(hq[u & 3], lq[u & 3], a[u].x, a[u].y, xv[u].x, xv[u].y);
-    }
-    for (; j0 < k; j0 += 32) {
-      const float2 a = row[j0], xv = x[j0];
+#pragma unroll 4
+    for (int64_t j = threadIdx.x; j < k; j += 256) {
+      const float2 a = row[j], xv = x[j];
       df_term(h, l, a.x, a.y, xv.x, xv.y);
     }
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) df_add_pair(h, l, hq[q], lq[q]);
   for (int o = 16; o > 0; o >>= 1) {
     const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
     df_add_pair(h, l, oh, ol);
   }
-  if (lane != 0) return;
+  if (lane == 0) red[warp] = make_float2(h, l);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  h = red[0].x;
+  l = red[0].y;
+#pragma unroll
+  for (int w = 1; w < 8; ++w) df_add_pair(h, l, red[w].x, red[w].y);
   const double s = (double)h + (double)l;
   double v;
   if (mode == 0) {
@@ -447,11 +428,10 @@ __global__ void __launch_bounds__(256) symv_df_kernel(const float2* __restrict__
 
 static void symv_df(const float2* A, int64_t k, const float2* x, int mode, const double* t, double* y, float2* y2,
                     cudaStream_t st) {
-  const unsigned gk = (unsigned)cdiv(k, 8);
   if ((k & 1) == 0)
-    { symv_df_kernel<true><<<gk, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
+    { symv_df_kernel<true><<<(unsigned)k, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
   else
-    { symv_df_kernel<false><<<gk, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
+    { symv_df_kernel<false><<<(unsigned)k, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
 }
 
 // t[j] = sum of the chunk partials (as reduce_chunks_kernel), also split into t2[j]
