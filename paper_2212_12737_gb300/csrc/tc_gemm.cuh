@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         ok = false;
         break;
       }
-      fence_after_sync();
+      // the mbarrier's TMA completion orders the stage for the tensor core: no tcgen05 fence
       const uint32_t sa = smem_u32(smem + s * SM::STAGE_BYTES);
       const uint32_t sb = sa + SM::A_BYTES;
 #pragma unroll
