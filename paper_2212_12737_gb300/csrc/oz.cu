@@ -1,5 +1,6 @@
 // Sliced-BF16 tensor-core matvec (see oz.cuh for the scheme).  Data layout in HBM:
-//   <op>.slices  BF16 [7][Rp][Kp]   K-major, zero padded (A operands Rp % 128 == 0, B operands % 64)
+//   <op>.slices  BF16 [7][Rp][Kp]   K-major, zero padded (A operands Rp % 128 == 0, B operands % 64,
+//                                   Kp % 128 == 0)
 //   <op>.e       int  [chunk][rows] power-of-two exponent of each 256-entry chunk of a row
 //   Tp           float2 [D-chunks][M][M]    double-float partials of T = Xc W^T
 //   Up           float2 [2 M-chunks][M][D]  double-float partials of U = A W + beta Xc
@@ -30,6 +31,18 @@ constexpr int kSmemTotal = kSmemData + 1024 + 256;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kKbPerChunk = oz::KC / oz::KB;
 constexpr int kStageLd = oz::BN + 1;  // padded row of the staged output tile (float2)
+// matvec GEMM: k-blocks of 128 (two 128-byte swizzle spans per tile), so each mbarrier
+// wait of the MMA thread covers 8 MMAs per slice pair; one B group, 3-deep A ring
+constexpr int kKB2 = 2 * oz::KB;                 // 128 K entries per k-block
+constexpr int kATile2 = 2 * kATile;              // 32 KB: two spans of 128 rows
+constexpr int kBTile2 = 2 * kBTile;              // 16 KB: two spans of 64 rows
+constexpr int kBGroup2 = oz::S * kBTile2;        // 112 KB
+constexpr int kAStages2 = 3;
+constexpr int kSmemData2 = kBGroup2 + kAStages2 * kATile2;  // 208 KB
+constexpr int kSmemTotal2 = kSmemData2 + 1024 + 256;
+constexpr int kKbPerChunk2 = oz::KC / kKB2;      // 2
+static_assert(oz::BM * kStageLd * 8 <= kSmemData2, "output staging fits the operand buffers");
+static_assert(kSmemTotal2 <= 227 * 1024, "shared memory per CTA");
 static_assert(oz::BM * kStageLd * 8 <= kSmemData, "output staging fits the operand buffers");
 static_assert(oz::S * oz::BN <= (int)kTmemCols, "one TMEM accumulator per level");
 static_assert(kSmemTotal <= 227 * 1024, "shared memory per CTA");
@@ -205,11 +218,13 @@ __device__ __forceinline__ float scale2(float x, int e) {
   return x * pow2f(e);
 }
 
-// grid (ceil(N/64), ceil(M/128), K-chunks).  CTA z accumulates the 4 k-blocks of
-// chunk z.  Warp 0 loads the 7 A slices of each k-block one by one into a ring,
-// warp 2 loads the 7 B slices of each k-block as one group (double buffered);
-// warp 1 multiplies A slice i with B slices j = 0..6-i into TMEM accumulator
-// i + j.  Warps 3..10 (two per TMEM lane quarter, 32 columns each) combine the
+// grid (ceil(N/64), ceil(M/128), K-chunks).  CTA z accumulates the 2 k-blocks (of
+// 128 K entries, two 128-byte swizzle spans per tile) of chunk z.  Warp 0 loads the 7
+// A slices of each k-block one by one into a 3-deep ring, warp 2 loads the 7 B slices
+// of each k-block as one group; warp 1 multiplies A slice i with B slices j = 0..6-i
+// (8 MMAs per pair) into TMEM accumulator i + j.  Each mbarrier wait of the MMA
+// thread stalls the tensor pipe for a fixed ~2k cycles, so wide k-blocks halve that
+// cost per MMA.  Warps 3..10 (two per TMEM lane quarter, 32 columns each) combine the
 // 7 levels, scale by 2^(eA + eB) and store the chunk's double-float partial.
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
@@ -218,28 +233,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sB = smem;
-  uint8_t* sA = smem + 2 * kBGroup;
-  uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + kSmemData);
-  uint64_t* bempty = bfull + 2;
-  uint64_t* afull = bempty + 2;
-  uint64_t* aempty = afull + kAStages;
-  uint64_t* done = aempty + kAStages;
+  uint8_t* sA = smem + kBGroup2;
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + kSmemData2);
+  uint64_t* bempty = bfull + 1;
+  uint64_t* afull = bempty + 1;
+  uint64_t* aempty = afull + kAStages2;
+  uint64_t* done = aempty + kAStages2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float2* stage = reinterpret_cast<float2*>(smem);  // output tile, reuses the operand buffers after the MMAs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * oz::BN, m0 = blockIdx.y * oz::BM;
-  const int kb_begin = blockIdx.z * kKbPerChunk;
-  const int kb_end = min(num_kb, kb_begin + kKbPerChunk);
+  const int kb_begin = blockIdx.z * kKbPerChunk2;
+  const int kb_end = min(num_kb, kb_begin + kKbPerChunk2);
   const int nk = kb_end - kb_begin;
 
   if (threadIdx.x == 0) {
-    for (int g = 0; g < 2; ++g) {
-      tc::mbar_init(&bfull[g], 1);
-      tc::mbar_init(&bempty[g], 1);
-    }
-    for (int s = 0; s < kAStages; ++s) {
+    tc::mbar_init(bfull, 1);
+    tc::mbar_init(bempty, 1);
+    for (int s = 0; s < kAStages2; ++s) {
       tc::mbar_init(&afull[s], 1);
       tc::mbar_init(&aempty[s], 1);
     }
@@ -260,12 +273,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer, A slices
     for (int kb = 0; kb < nk; ++kb) {
-      const int kx = (kb_begin + kb) * oz::KB;
+      const int kx = (kb_begin + kb) * kKB2;
       bool ok = true;
       for (int i = 0; i < oz::S; ++i) {
         const int ai = kb * oz::S + i;
-        const int s = ai % kAStages;
-        const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
+        const int s = ai % kAStages2;
+        const uint32_t ph = (uint32_t)(ai / kAStages2) & 1u;
         if (!mbar_wait_spin(&aempty[s], ph ^ 1u)) {
           atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
           *abort_flag = 1;
@@ -276,26 +289,27 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        tc::mbar_expect_tx(&afull[s], kATile);
-        tc::tma_load_2d(sA + s * kATile, &mapA, &afull[s], kx, i * Ap + m0);
+        tc::mbar_expect_tx(&afull[s], kATile2);
+        tc::tma_load_2d(sA + s * kATile2, &mapA, &afull[s], kx, i * Ap + m0);
+        tc::tma_load_2d(sA + s * kATile2 + kATile, &mapA, &afull[s], kx + oz::KB, i * Ap + m0);
       }
       if (!ok) break;
     }
   } else if (warp == 2 && lane == 0) {
     // ---------------- TMA producer, B slice groups
     for (int kb = 0; kb < nk; ++kb) {
-      const int g = kb & 1;
-      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
-      if (!mbar_wait_spin(&bempty[g], gph ^ 1u)) {
+      if (!mbar_wait_spin(bempty, ((uint32_t)kb & 1u) ^ 1u)) {
         atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
         *abort_flag = 1;
         break;
       }
       if (*abort_flag) break;
-      const int kx = (kb_begin + kb) * oz::KB;
-      tc::mbar_expect_tx(&bfull[g], kBGroup);
-      for (int j = 0; j < oz::S; ++j)
-        tc::tma_load_2d(sB + (g * oz::S + j) * kBTile, &mapB, &bfull[g], kx, j * Bp + n0);
+      const int kx = (kb_begin + kb) * kKB2;
+      tc::mbar_expect_tx(bfull, kBGroup2);
+      for (int j = 0; j < oz::S; ++j) {
+        tc::tma_load_2d(sB + j * kBTile2, &mapB, bfull, kx, j * Bp + n0);
+        tc::tma_load_2d(sB + j * kBTile2 + kBTile, &mapB, bfull, kx + oz::KB, j * Bp + n0);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -304,17 +318,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
     bool ok = true;
     for (int kb = 0; kb < nk && ok; ++kb) {
-      const int g = kb & 1;
-      const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
-      if (!mbar_wait_spin(&bfull[g], gph)) {
+      if (!mbar_wait_spin(bfull, (uint32_t)kb & 1u)) {
         atomicExch(err, tc::ERR_TIMEOUT_FULL);
         *abort_flag = 1;
         break;
       }
       for (int i = 0; i < oz::S; ++i) {
         const int ai = kb * oz::S + i;
-        const int s = ai % kAStages;
-        const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
+        const int s = ai % kAStages2;
+        const uint32_t ph = (uint32_t)(ai / kAStages2) & 1u;
         if (!mbar_wait_spin(&afull[s], ph)) {
           atomicExch(err, tc::ERR_TIMEOUT_FULL);
           *abort_flag = 1;
@@ -327,25 +339,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         // (no tcgen05 fence here: the mbarrier's TMA completion already orders the tile for
         // the tensor core, and a fence per tile costs ~35 cycles per MMA)
-        // descriptors are linear in the start address (bits 0..13 = address / 16), so a
-        // K step of 32 bytes adds 2 and the B slice j of the group adds j * kBTile / 16
-        const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
-        const uint64_t bd = bdesc0 + (uint64_t)(g * oz::S * (kBTile >> 4));
+        // descriptors are linear in the start address (bits 0..13 = address / 16): a K
+        // step of 32 bytes adds 2, the second 128-byte span of a tile adds span / 16, and
+        // B slice j adds j * kBTile2 / 16
+        const uint64_t ad = adesc0 + (uint64_t)(s * (kATile2 >> 4));
         const uint32_t first = (kb > 0 || i > 0) ? 1u : 0u;
 #pragma unroll
         for (int j = 0; j < oz::S; ++j) {
           if (i + j < oz::S) {
             const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
-            const uint64_t bj = bd + (uint64_t)(j * (kBTile >> 4));
+            const uint64_t bj = bdesc0 + (uint64_t)(j * (kBTile2 >> 4));
+            constexpr uint64_t a1 = kATile >> 4, b1 = kBTile >> 4;
             tc::mma_issue<true>(d, ad, bj, idesc, first);
             tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
             tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
             tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+            tc::mma_issue<true>(d, ad + a1, bj + b1, idesc, 1u);
+            tc::mma_issue<true>(d, ad + a1 + 2, bj + b1 + 2, idesc, 1u);
+            tc::mma_issue<true>(d, ad + a1 + 4, bj + b1 + 4, idesc, 1u);
+            tc::mma_issue<true>(d, ad + a1 + 6, bj + b1 + 6, idesc, 1u);
           }
         }
         tc::mma_commit(&aempty[s]);
       }
-      if (ok) tc::mma_commit(&bempty[g]);
+      if (ok) tc::mma_commit(bempty);
     }
     tc::mma_commit(done);
   } else if (warp >= 3) {
@@ -774,7 +791,7 @@ static gdml_status make_operand(OzMatvec& oz, OzOperand& op, int64_t rows, int64
   op.rows = rows;
   op.Rp = cdiv(rows, box_rows) * box_rows;
   op.K = K;
-  op.Kp = cdiv(K, oz::KB) * oz::KB;
+  op.Kp = cdiv(K, 2 * oz::KB) * (2 * oz::KB);  // k-blocks of 128 for the matvec GEMM
   op.nchunks = cdiv(K, oz::KC);
   bf16* s = nullptr;
   OZ_TRY(oz_alloc(oz, &s, (size_t)(oz::S * op.Rp * op.Kp), st));
@@ -801,13 +818,14 @@ static gdml_status oz_gemm(const OzOperand& A, const OzOperand& B, float2* out, 
                            int* err, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal) != cudaSuccess)
+    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal2) != cudaSuccess)
       return fail(GDML_ERR_CUDA, "cudaFuncSetAttribute(sliced gemm)");
     attr_set = true;
   }
   if (A.Kp != B.Kp) return fail(GDML_ERR_ARG, "sliced gemm: K mismatch");
   dim3 grid((unsigned)cdiv(B.rows, oz::BN), (unsigned)cdiv(A.rows, oz::BM), (unsigned)A.nchunks);
-  { oz_gemm_kernel<<<grid, kThreads, kSmemTotal, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / oz::KB), A.e, B.e, out, ldo, split_stride, err); count_launch(); }
+  if (A.Kp % kKB2 != 0) return fail(GDML_ERR_ARG, "sliced gemm: K padding");
+  { oz_gemm_kernel<<<grid, kThreads, kSmemTotal2, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / kKB2), A.e, B.e, out, ldo, split_stride, err); count_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("sliced gemm launch: ") + cudaGetErrorString(e));
   return GDML_OK;
