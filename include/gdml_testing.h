@@ -30,9 +30,23 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
 gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
                               double* C_dev, void* cuda_stream);
 
-/* Reads and clears the error word of the tensor-core kernels of a TF32/BF16/OZAKI
- * context (synchronises its stream); GDML_ERR_TIMEOUT if a tcgen05 pipeline
- * wait gave up since the last check.  FP64 contexts: always GDML_OK. */
+/* The two passes over the FP32-stored factor L_k of the Woodbury apply (Eq. 4) in
+ * DF64/OZAKI contexts: t = L^T r and z = (r - L u) / lambda, with exact FP32
+ * products of L and the float-pair split of r (u) and double-float sums.  L: n x k
+ * FP32 column-major (column j at L + j n), r, z: n FP64, u, t: k FP64, all device
+ * arrays owned by the caller.  staged = 1: the TMA-staged kernels the contexts use
+ * when n % 4 == 0 (GDML_ERR_ARG otherwise), with their automatic row-chunk size;
+ * staged = 128 or 256: the same kernels with that chunk size; staged = 0: the
+ * register-streamed kernels used for other n.  Synchronises the stream.  Errors: GDML_ERR_ARG
+ * (NULL pointers, n < 1, k < 1 or k > 16384, lambda <= 0), GDML_ERR_OOM,
+ * GDML_ERR_CUDA, GDML_ERR_TIMEOUT (a bounded pipeline wait gave up). */
+gdml_status gdml_test_df_passes(const float* L_dev, int64_t n, int64_t k, const double* r_dev, const double* u_dev,
+                                double lambda, int32_t staged, double* t_dev, double* z_dev, void* cuda_stream);
+
+/* Reads and clears the error word of the tensor-core kernels/* Reads and clears the error words of the tensor-core kernels of a TF32/BF16/OZAKI
+ * context and of the staged Woodbury passes of a DF64/OZAKI context (synchronises
+ * its stream); GDML_ERR_TIMEOUT if a pipeline wait gave up since the last check.
+ * FP64 contexts: always GDML_OK. */
 gdml_status gdml_tc_check(gdml_ctx* ctx);
 
 /* Kernel launches this library has executed since it was loaded (all

@@ -73,6 +73,8 @@ struct gdml_ctx {
   double* Cfull = nullptr; // k x k: C itself (for the refinement step of the apply)
   double* wpart = nullptr;
   double* wt = nullptr;
+  WsPlan ws;              // TMA-staged passes over Lf (DF64/OZAKI contexts)
+  int* werr = nullptr;    // error word of the staged passes
   int64_t cap_k = 0;
 
   // PCG state
@@ -358,6 +360,18 @@ gdml_status rls_estimate(gdml_ctx* c, int64_t k, uint64_t seed, int64_t* S, doub
   return check_launch(c, "rls scores");
 }
 
+// reads (and clears) the error word of the staged Woodbury passes; synchronises the stream
+gdml_status ws_check(gdml_ctx* c) {
+  int h = 0;
+  CTRY(c, cudaMemcpyAsync(&h, c->werr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  if (h) {
+    (void)cudaMemsetAsync(c->werr, 0, sizeof(int), c->st);
+    return ctx_fail(c, GDML_ERR_TIMEOUT, "a staged Woodbury pass wait timed out (code " + std::to_string(h) + ")");
+  }
+  return GDML_OK;
+}
+
 // ------------------------------------------------------------------ PCG
 gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
   if (c->k == 0) {
@@ -366,7 +380,7 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
   }
   if (df_precond(c))
     woodbury_apply_df(c->Lf, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt,
-                      reinterpret_cast<float2*>(c->rsplit), c->st);
+                      reinterpret_cast<float2*>(c->rsplit), &c->ws, c->werr, c->st);
   else
     woodbury_apply<double>(c->L, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
   return check_launch(c, "woodbury_apply");
@@ -570,6 +584,8 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   TRY(dalloc(C, &c->partial, 4096));
   TRY(dalloc(C, &c->ticket, 1));
   TRY(dalloc(C, &c->status, 1));
+  TRY(dalloc(C, &c->werr, 1));
+  CTRY(C, cudaMemsetAsync(c->werr, 0, sizeof(int), c->st));
   TRY(dalloc(C, &c->ictl, IC_COUNT));
   CTRY(C, cudaMallocHost(&c->hsc, SC_COUNT * sizeof(double)));
   CTRY(C, cudaMallocHost(&c->hictl, IC_COUNT * sizeof(int64_t)));
@@ -615,6 +631,7 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
   if (method < GDML_SEL_UNIFORM || method > GDML_SEL_WEIGHTED) return ctx_fail(c, GDML_ERR_ARG, "unknown method");
   if (method == GDML_SEL_WEIGHTED && !geometry_scores) return ctx_fail(c, GDML_ERR_ARG, "scores are NULL");
   c->k = 0;
+  c->ws = WsPlan();
   c->jitter = 0.0;
   drop_graphs(c);
   TRY(ensure_precond_buffers(c, k));
@@ -675,6 +692,7 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
       TRY(s.get(&a.posof, (size_t)n));
       CTRY(c, cudaMemcpyAsync(a.posof, hperm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
       CTRY(c, cudaMemsetAsync(c->Lf, 0, n * k * sizeof(float), c->st));
+      a.err = c->werr;
       pivchol_run_df(a, c->Lf, c->st);
     } else {
       pivchol_run<double>(a, c->L, c->st);
@@ -714,7 +732,9 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
   if (resid_trace_dev)
     CTRY(c, cudaMemcpyAsync(resid_trace_dev, trace, k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   CTRY(c, cudaStreamSynchronize(c->st));
+  if (df_precond(c)) TRY(ws_check(c));
   c->k = rank;
+  if (df_precond(c)) ws_plan(c->ws, c->Lf, n, rank);
   return GDML_OK;
 }
 
@@ -735,6 +755,7 @@ gdml_status gdml_rls_scores(gdml_ctx* c, int64_t k, uint64_t seed, double* tau_d
   if (!tau_dev) return ctx_fail(c, GDML_ERR_ARG, "tau_dev is NULL");
   if (k < 1 || k > n || k > 16384) return ctx_fail(c, GDML_ERR_ARG, "need 1 <= k <= min(n, 16384)");
   c->k = 0;
+  c->ws = WsPlan();
   drop_graphs(c);
   TRY(ensure_precond_buffers(c, k));
   Scratch s{c, {}};
@@ -860,6 +881,7 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
     gdml_status ts = c->precision == GDML_OZAKI ? oz_check(c->oz, st) : tc_check(c->tc, st);
     if (ts != GDML_OK) return ctx_fail(c, ts, last_msg());
   }
+  if (df_precond(c)) TRY(ws_check(c));
   if (iters_out) *iters_out = (int32_t)iters;
   const double rel = ynorm > 0 ? res / ynorm : 0.0;
   if (relres_out) *relres_out = rel;
@@ -873,6 +895,47 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
   clear_msg();
   if (!A_dev || !B_dev || !C_dev || M < 1 || N < 1 || K < 1) return fail(GDML_ERR_ARG, "bad gemm test arguments");
   return tc_gemm_test(bf16, A_dev, B_dev, M, N, K, C_dev, static_cast<cudaStream_t>(stream));
+}
+
+gdml_status gdml_test_df_passes(const float* L_dev, int64_t n, int64_t k, const double* r_dev, const double* u_dev,
+                                double lambda, int32_t staged, double* t_dev, double* z_dev, void* stream) {
+  clear_msg();
+  if (!L_dev || !r_dev || !u_dev || !t_dev || !z_dev || n < 1 || k < 1 || !(lambda > 0.0))
+    return fail(GDML_ERR_ARG, "bad apply-pass test arguments");
+  if (n > ((int64_t)1 << 30) || k > 16384) return fail(GDML_ERR_ARG, "apply-pass test sizes too large");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsPlan plan;
+  if (staged) {
+    ws_plan(plan, L_dev, n, k, staged);
+    if (!plan.ok) return fail(GDML_ERR_ARG, "staged passes need n % 4 == 0 and a valid TMA map");
+  }
+  const size_t part_b = (size_t)woodbury_part_size(n, k) * sizeof(double);
+  const size_t rs_b = (size_t)n * sizeof(float2), kv_b = (size_t)k * sizeof(float2);
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, part_b + rs_b + 2 * kv_b + 256) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(GDML_ERR_OOM, "apply-pass test scratch");
+  }
+  char* b = static_cast<char*>(buf);
+  double* part = reinterpret_cast<double*>(b);
+  float2* rs = reinterpret_cast<float2*>(b + part_b);
+  float2* t2 = reinterpret_cast<float2*>(b + part_b + rs_b);
+  float2* u2 = reinterpret_cast<float2*>(b + part_b + rs_b + kv_b);
+  int* err = reinterpret_cast<int*>(b + part_b + rs_b + 2 * kv_b);
+  gdml_status s = GDML_OK;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) s = fail(GDML_ERR_CUDA, "apply-pass test memset");
+  if (s == GDML_OK) {
+    df_passes(L_dev, n, k, r_dev, u_dev, lambda, t_dev, z_dev, part, rs, t2, u2, staged ? &plan : nullptr, err, st);
+    int h = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      s = fail(GDML_ERR_CUDA, "apply-pass test launch");
+    else if (h)
+      s = fail(GDML_ERR_TIMEOUT, "a staged Woodbury pass wait timed out (code " + std::to_string(h) + ")");
+  }
+  cudaFree(buf);
+  return s;
 }
 
 gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
@@ -1094,6 +1157,7 @@ gdml_status gdml_set_tuning(gdml_ctx* c, int32_t splits) {
 
 gdml_status gdml_tc_check(gdml_ctx* c) {
   TRY(validate(c));
+  if (df_precond(c)) TRY(ws_check(c));
   if (c->precision != GDML_TF32 && c->precision != GDML_BF16 && c->precision != GDML_OZAKI) return GDML_OK;
   gdml_status s = c->precision == GDML_OZAKI ? oz_check(c->oz, c->st) : tc_check(c->tc, c->st);
   if (s != GDML_OK) return ctx_fail(c, s, last_msg());

@@ -1,6 +1,8 @@
 // Internal launcher declarations shared by the libgdml translation units.
 #pragma once
 
+#include <cuda.h>
+
 #include <functional>
 
 #include "common.cuh"
@@ -54,8 +56,32 @@ void mirror_lower(double* A, int64_t k, cudaStream_t st);
 // DF64 contexts: FP32-stored L_k, double-float accumulation; C and Cinv hold float
 // pairs (split_df_inplace); t holds 6k doubles (t, u, e and three float-pair vectors)
 void split_df_inplace(double* a, int64_t count, cudaStream_t st);
+// TMA-staged passes over the FP32 factor (n x k, column j at L + j n): rows in chunks of rc
+// = 128 or 256; valid only for n % 4 == 0
+struct WsPlan {
+  bool ok = false;
+  const float* L = nullptr;
+  int64_t n = 0, k = 0, nch = 0;
+  int rc = 0, grid = 0;
+  CUtensorMap map;  // box rc rows x (32 * 128 / rc) columns
+};
+// fills plan for L (plan.ok = false where the staged passes do not apply: n % 4 != 0, k = 0,
+// or the driver rejects the map); rows: 128 or 256 to force the chunk size, else automatic
+void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows = 0);
+struct PivState;
+// Algorithm 1 step m's Schur sums through the staged pass: schur[i] = sum_{j < m} L[i + j n]
+// prow[j] (double-float pairs); plan made by ws_plan for the factor; nothing runs once
+// ps->stop is set
+void ws_schur(const WsPlan& plan, int64_t m, const float* prow, const PivState* ps, float2* schur, int* err,
+              cudaStream_t st);
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
-                       const double* r, double* z, double* part, double* t, float2* rs, cudaStream_t st);
+                       const double* r, double* z, double* part, double* t, float2* rs, const WsPlan* plan,
+                       int* err, cudaStream_t st);
+// the two L passes alone (test hook): t = L^T r and z = (r - L u) / lambda, staged (plan) or
+// register-streamed (plan == nullptr); part: woodbury_part_size(n, k) doubles, t2: k float pairs
+void df_passes(const float* L, int64_t n, int64_t k, const double* r, const double* u, double lam, double* t,
+               double* z, double* part, float2* rs, float2* t2, float2* u2, const WsPlan* plan, int* err,
+               cudaStream_t st);
 void to_float(const double* a, int64_t n, float* b, cudaStream_t st);
 // lower-triangle-only double-float SYRK of an FP32 matrix: C = A A^T, A (k x n row-major, ld)
 void launch_dfsyrk(int64_t k, int64_t n, const float* A, int64_t lda, double* C, int64_t ldc, cudaStream_t st);
@@ -116,6 +142,7 @@ struct PivCholArgs {
   float* prow = nullptr;
   float2* schur = nullptr;
   int64_t* posof = nullptr;  // inverse of perm (position of each index)
+  int* err = nullptr;        // error word of the staged Schur pass
 };
 int pivchol_schur_groups();
 template <typename TL>

@@ -370,6 +370,9 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
   const int64_t rblocks = cdiv(a.n, kSchurRows);
   const bool vec = (a.n % 4) == 0;
   const unsigned fblocks = (unsigned)std::min<int64_t>(cdiv(a.n, kArgThreads), kArgBlocks);
+  // n % 4 == 0: the Schur sums run through the TMA-staged pass (one partial per row)
+  WsPlan plan;
+  if (a.err) ws_plan(plan, L, a.n, a.k);
   // step 0's pivot
   { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(0, a.n, 1, a.d, a.perm, a.chosen, a.pivots, nullptr,
                                                        a.ps, a.part, a.ticket, a.posof); count_launch(); }
@@ -377,7 +380,10 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
     a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
     // column groups: enough CTAs for ~4 per SM, at least 32 columns per group
     int groups = 0;
-    if (m > 0) {
+    if (m > 0 && plan.ok) {
+      groups = 1;
+      ws_schur(plan, m, a.prow, a.ps, a.schur, a.err, st);
+    } else if (m > 0) {
       const int64_t want = cdiv(4 * kNumSMs, rblocks);
       groups = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)kSchurMaxGroups, std::max<int64_t>(1, m / 32)}));
       dim3 g((unsigned)rblocks, (unsigned)groups);

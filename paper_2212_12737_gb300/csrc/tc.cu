@@ -254,6 +254,22 @@ bool make_kmajor_map(CUtensorMap* m, const void* base, bool bf16, uint64_t K, ui
   return r == CUDA_SUCCESS;
 }
 
+// 2D FP32 map without swizzle: inner dim contiguous, outer stride ld_elems (a multiple
+// of 4 elements); box = box_inner x box_outer; zero fill outside the tensor
+bool make_f32_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                  uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld_elems * 4};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <bool BF16, int BN, int STAGES, typename Epi>
 static gdml_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, int M, int N, int num_kb, int splits,
                                const Epi& epi, int* err, cudaStream_t st) {

@@ -52,6 +52,12 @@ void tc_destroy(TcMatvec& tc);
 bool make_kmajor_map(CUtensorMap* m, const void* base, bool bf16, uint64_t K, uint64_t rows, uint64_t ld_elems,
                      uint32_t box_rows);
 
+// 2D FP32 TMA map without swizzle: inner dim (contiguous elements), outer dim, outer stride
+// ld_elems (ld_elems * 4 a multiple of 16 bytes); box = box_inner x box_outer elements,
+// zero fill outside the tensor.  False if the driver rejects it.
+bool make_f32_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                  uint32_t box_inner, uint32_t box_outer);
+
 // test hook: C (M x N, fp64) = A (M x K) B (N x K)^T with operands rounded to TF32 / BF16
 gdml_status tc_gemm_test(int bf16, const double* A, const double* B, int M, int N, int K, double* C,
                          cudaStream_t st);

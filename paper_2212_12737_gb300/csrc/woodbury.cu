@@ -6,8 +6,12 @@
 // instead of two latency-bound triangular solves per CG iteration.  L_k is
 // stored column-major (n x k, column j at L + j*n) in FP64, or in FP32 for the
 // mixed-precision contexts; all arithmetic is FP64.  Two HBM passes over L_k.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc.cuh"
+#include "tc_gemm.cuh"
 
 namespace gdml {
 
@@ -142,7 +146,7 @@ template void woodbury_apply<float>(const float*, int64_t, int64_t, const double
 // doubles of the apply's partial buffer: the L^T r chunk partials of either layout
 // (4096- or 512-row chunks) or the 16 column-group partials of the DF64 L u pass
 int64_t woodbury_part_size(int64_t n, int64_t k) {
-  const int64_t a = cdiv(n, 512) * k, b = 16 * n;
+  const int64_t a = cdiv(n, 128) * k, b = 16 * n;  // row chunks of >= 128 rows (staged passes)
   return a > b ? a : b;
 }
 
@@ -356,6 +360,458 @@ __global__ void gemv_n_df_finish_kernel(const float2* __restrict__ zp, int64_t n
   z[i] = (r[i] - ((double)hh + (double)ll)) * inv_lam;
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged passes.  One producer thread keeps a ring of 16 KB column tiles of
+// L in flight (cp.async.bulk.tensor with an L2 evict-first hint, zero fill past
+// n and k); eight consumer warps do the double-float arithmetic out of shared
+// memory.  The bytes in flight per SM then no longer depend on how many loads
+// each warp holds in registers.  Rows are cut into chunks of RC = 128 NT rows
+// (NT = 1 or 2, so every lane is busy); CTA b takes chunks b, b + grid, ... and
+// streams all k columns of each.  A tile is RC rows x 32 / NT columns, the same
+// shape for both passes; warp w takes tile columns w CPW .. w CPW + CPW - 1
+// (CPW = 4 / NT) and lane l rows 4 l + 128 t + e (t < NT, e < 4): one float4
+// per column and t, 16 products per lane and tile.
+//
+// Sums are double-float with the low part accumulated lazily: each exact
+// product enters the high word through TwoSum and its rounding errors go
+// straight into the low word; the pair is renormalised (Fast2Sum) once per tile
+// instead of once per product, so the low word gathers at most 4 terms in
+// between.  The arithmetic runs on packed FP32 pairs (add/sub/mul/fma .f32x2):
+// 11 instructions per two products instead of 14 per product.
+constexpr int kWsWarps = 8;                      // consumer warps
+constexpr int kWsThreads = 32 * (kWsWarps + 1);  // + one producer warp
+constexpr int kWsTile = 16384;                   // bytes per tile (RC x 32/NT floats)
+constexpr int kWsStages = 6;
+constexpr int kWsAlign = 128;  // TMA destination alignment (no swizzle)
+constexpr int kWsSmemT = kWsAlign + kWsStages * kWsTile + 2 * kWsStages * 8 + 16;
+constexpr int kWsSmemN = kWsAlign + kWsStages * kWsTile + kWsWarps * 256 * 8 + (2 * kWsStages + 2) * 8 + 16;
+static_assert(2 * kWsSmemT <= 227 * 1024 && 2 * kWsSmemN <= 227 * 1024, "two CTAs per SM");
+
+namespace {
+
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = tc::smem_u32(bar);
+  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void ws_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// 2D tile load that marks the lines evict-first in L2 (L is streamed once per pass; the
+// k x k matrices of the apply's core should stay resident)
+__device__ __forceinline__ void ws_tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(tc::smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+      : "memory");
+}
+
+// Packed FP32 arithmetic (two independent lanes per instruction, round to nearest even):
+// the double-float sums below run on row pairs (x, y) and (z, w) of each float4.
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(*reinterpret_cast<const uint64_t*>(&a)),
+      "l"(*reinterpret_cast<const uint64_t*>(&b)));
+  return *reinterpret_cast<const float2*>(&d);
+}
+
+// (sh, sl) += a (bh + bl) on both lanes, low word not renormalised; nbh = -bh.  The
+// product's rounding error comes exactly from one FMA, the high word's from TwoSum.
+__device__ __forceinline__ void df2_add_prod_lazy(float2& sh, float2& sl, float2 a, float2 bh, float2 nbh,
+                                                  float2 bl) {
+  const float2 ph = f2mul(a, bh);
+  const float2 pn = f2fma(a, nbh, ph);  // ph - a bh: minus the rounding error of ph, exact
+  const float2 t = f2add(sh, ph);
+  const float2 v = f2sub(t, sh);
+  const float2 e = f2add(f2sub(sh, f2sub(t, v)), f2sub(ph, v));
+  const float2 q = f2fma(a, bl, e);  // e + a bl
+  sl = f2add(sl, f2sub(q, pn));
+  sh = t;
+}
+
+// the same with bl = 0 (an FP32 multiplier)
+__device__ __forceinline__ void df2_add_prod_lazy(float2& sh, float2& sl, float2 a, float2 bh, float2 nbh) {
+  const float2 ph = f2mul(a, bh);
+  const float2 pn = f2fma(a, nbh, ph);
+  const float2 t = f2add(sh, ph);
+  const float2 v = f2sub(t, sh);
+  const float2 e = f2add(f2sub(sh, f2sub(t, v)), f2sub(ph, v));
+  sl = f2add(sl, f2sub(e, pn));
+  sh = t;
+}
+
+__device__ __forceinline__ void df2_renorm(float2& sh, float2& sl) {
+  const float2 t = f2add(sh, sl);
+  sl = f2sub(sl, f2sub(t, sh));
+  sh = t;
+}
+
+__device__ __forceinline__ float2 lo_pair(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi_pair(const float4& v) { return make_float2(v.z, v.w); }
+
+// Bounded barrier of the 256 consumer threads (the producer warp does not take part) on an
+// mbarrier with 256 arrivals per phase; false (warp-uniform) on timeout or abort.
+__device__ __forceinline__ bool ws_consumer_sync(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  ws_arrive(bar);
+  bool ok = ws_wait(bar, parity);
+  if (!ok) {
+    atomicExch(err, tc::ERR_TIMEOUT_DONE);
+    *abort_flag = 1;
+  }
+  ok = ok && !*abort_flag;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Bounded wait of a whole consumer warp on a full slot; false (warp-uniform) on timeout or abort.
+__device__ __forceinline__ bool ws_consume_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  bool ok = ws_wait(bar, parity);
+  if (!ok) {
+    atomicExch(err, tc::ERR_TIMEOUT_FULL);
+    *abort_flag = 1;
+  }
+  ok = ok && !*abort_flag;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// ring position: slot and phase parity advance together
+struct WsRing {
+  uint32_t slot = 0, phase = 0;
+  __device__ __forceinline__ void next() {
+    if (++slot == kWsStages) {
+      slot = 0;
+      phase ^= 1u;
+    }
+  }
+};
+
+// The producer: tile (chunk, s) = rows [chunk RC, chunk RC + RC) x columns [s COLS, s COLS + COLS).
+// Returns the number of tiles issued.
+template <int NT, bool EVICT_FIRST>
+__device__ uint32_t ws_produce(const CUtensorMap* map, uint8_t* ring, uint64_t* full, uint64_t* empty,
+                               volatile int* abort_flag, int64_t nch, int ntiles, int* err) {
+  constexpr int RC = 128 * NT, COLS = 32 / NT;
+  uint64_t policy;
+  if (EVICT_FIRST)
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+  else
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(policy));
+  WsRing rp;
+  uint32_t issued = 0;
+  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x)
+    for (int s = 0; s < ntiles; ++s, ++issued, rp.next()) {
+      if (!ws_wait(&empty[rp.slot], rp.phase ^ 1u)) {
+        atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+        *abort_flag = 1;
+        return issued;
+      }
+      if (*abort_flag) return issued;
+      tc::mbar_expect_tx(&full[rp.slot], kWsTile);
+      ws_tma_load(ring + rp.slot * kWsTile, map, &full[rp.slot], (int)(ch * RC), s * COLS, policy);
+    }
+  return issued;
+}
+
+// After an abort: wait (bounded) until the last copy issued into each slot has landed, so
+// that no TMA write is in flight when the CTA exits.
+__device__ void ws_drain(uint64_t* full, uint32_t issued) {
+  for (uint32_t s = 0; s < kWsStages && s < issued; ++s) {
+    const uint32_t last = s + ((issued - 1 - s) / kWsStages) * kWsStages;
+    (void)ws_wait(&full[s], (last / kWsStages) & 1u);
+  }
+}
+
+__device__ __forceinline__ void ws_init(uint64_t* full, uint64_t* empty, uint64_t* cbar, volatile int* abort_flag) {
+  for (int s = 0; s < kWsStages; ++s) {
+    tc::mbar_init(&full[s], 1);
+    tc::mbar_init(&empty[s], kWsWarps);
+  }
+  if (cbar) {
+    tc::mbar_init(&cbar[0], 32 * kWsWarps);
+    tc::mbar_init(&cbar[1], 32 * kWsWarps);
+  }
+  *abort_flag = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+}  // namespace
+
+// part[j * nch + chunk] = sum over the chunk's rows of L[i + j n] r[i] (a double-float pair;
+// the FP64 combination is left to the chunk reduction, off this kernel's critical path).  Per lane and column
+// two packed chains (even and odd rows); every 8 / CPW tiles a warp folds them into one
+// double-float partial per lane for 8 columns and reduces those with one reduce-scatter.
+template <int NT>
+__global__ void __launch_bounds__(kWsThreads, 2)
+    ws_gemv_t_kernel(const __grid_constant__ CUtensorMap map, int64_t n, int64_t k, int64_t nch,
+                     const float2* __restrict__ rs, float2* __restrict__ part, int* __restrict__ err) {
+  constexpr int RC = 128 * NT, COLS = 32 / NT, CPW = 4 / NT, TPG = 8 / CPW;  // TPG: tiles per 8 columns
+  extern __shared__ uint8_t ws_smem_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws_smem_raw) + kWsAlign - 1) &
+                                             ~uintptr_t(kWsAlign - 1));
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + kWsStages * kWsTile);
+  uint64_t* empty = full + kWsStages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kWsStages);
+  __shared__ uint32_t issued_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = (int)((k + COLS - 1) / COLS);
+  if (threadIdx.x == 0) {
+    ws_init(full, empty, nullptr, abort_flag);
+    issued_s = 0;
+  }
+  __syncthreads();
+  if (warp == kWsWarps) {
+    if (lane == 0) issued_s = ws_produce<NT, true>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
+  } else {
+    WsRing rp;
+    bool go = true;
+    for (int64_t ch = blockIdx.x; ch < nch && go; ch += gridDim.x) {
+      const int64_t i0 = ch * RC;
+      // r of the lane's rows as packed pairs (rows 4 l + 128 t + {0,1} and {2,3})
+      float2 rh[NT][2], rn[NT][2], rl[NT][2];
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const int64_t i = i0 + 128 * t + 4 * lane + 2 * p;
+          const float2 r0 = i < n ? rs[i] : make_float2(0.f, 0.f);
+          const float2 r1 = i + 1 < n ? rs[i + 1] : make_float2(0.f, 0.f);
+          rh[t][p] = make_float2(r0.x, r1.x);
+          rn[t][p] = make_float2(-r0.x, -r1.x);
+          rl[t][p] = make_float2(r0.y, r1.y);
+        }
+      for (int g = 0; g < ntiles && go; g += TPG) {
+        float2 h2[8], l2[8];  // per column: (even rows, odd rows) chains
+#pragma unroll
+        for (int c = 0; c < 8; ++c) h2[c] = l2[c] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < TPG; ++q) {
+          if (g + q < ntiles) {
+            if (!ws_consume_wait(&full[rp.slot], rp.phase, abort_flag, err)) {
+              go = false;
+              break;
+            }
+            const float* tile = reinterpret_cast<const float*>(ring + rp.slot * kWsTile) + warp * CPW * RC;
+            float4 a[CPW][NT];
+#pragma unroll
+            for (int c = 0; c < CPW; ++c)
+#pragma unroll
+              for (int t = 0; t < NT; ++t) a[c][t] = *reinterpret_cast<const float4*>(tile + c * RC + 128 * t + 4 * lane);
+            __syncwarp();
+            if (lane == 0) ws_arrive(&empty[rp.slot]);
+            rp.next();
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+#pragma unroll
+              for (int c = 0; c < CPW; ++c) {
+                df2_add_prod_lazy(h2[q * CPW + c], l2[q * CPW + c], lo_pair(a[c][t]), rh[t][0], rn[t][0], rl[t][0]);
+                df2_add_prod_lazy(h2[q * CPW + c], l2[q * CPW + c], hi_pair(a[c][t]), rh[t][1], rn[t][1], rl[t][1]);
+              }
+          }
+        }
+        if (!go) break;
+        float h[8], l[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          df2_renorm(h2[c], l2[c]);
+          h[c] = h2[c].x;
+          l[c] = l2[c].x;
+          df_add_pair(h[c], l[c], h2[c].y, l2[c].y);
+        }
+        float oh, ol;
+        reduce_scatter8(h, l, lane, oh, ol);
+        // reduce-scatter slot c = q CPW + cc holds column (g + q) COLS + w CPW + cc
+        const int c = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        const int64_t col = (int64_t)(g + c / CPW) * COLS + warp * CPW + (c % CPW);
+        if ((lane & 3) == 0 && col < k) part[col * nch + ch] = make_float2(oh, ol);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) ws_drain(full, issued_s);
+}
+
+// z[i] = (r[i] - sum_j L[i + j n] u[j]) / lambda for the chunk's rows: 4 NT double-float
+// chains per lane (its rows, packed in pairs), CPW products each per tile; the 8 warps' sums
+// are combined in a fixed order through shared memory at the end of the chunk.
+// SCHUR: the Schur sums of Algorithm 1 step m instead, schur[i] = sum_{j < k} L[i + j n]
+// prow[j] as a double-float pair (k = m, prow: the pivot's row of L in FP32); L is read
+// with the normal L2 policy (the first columns are re-read every step); nothing runs once
+// ps->stop is set.
+template <int NT, bool SCHUR>
+__global__ void __launch_bounds__(kWsThreads, 2)
+    ws_gemv_n_kernel(const __grid_constant__ CUtensorMap map, int64_t n, int64_t k, int64_t nch,
+                     const float2* __restrict__ us, const float* __restrict__ prow, const double* __restrict__ r,
+                     double inv_lam, double* __restrict__ z, float2* __restrict__ schur,
+                     const PivState* __restrict__ ps, int* __restrict__ err) {
+  constexpr int RC = 128 * NT, COLS = 32 / NT, CPW = 4 / NT;
+  if (SCHUR && ps->stop) return;
+  extern __shared__ uint8_t ws_smem_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws_smem_raw) + kWsAlign - 1) &
+                                             ~uintptr_t(kWsAlign - 1));
+  float2* cmb = reinterpret_cast<float2*>(ring + kWsStages * kWsTile);  // [warp][RC rows]
+  uint64_t* full = reinterpret_cast<uint64_t*>(cmb + kWsWarps * 256);
+  uint64_t* empty = full + kWsStages;
+  uint64_t* cbar = empty + kWsStages;  // [2]: combine buffer written / read
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(cbar + 2);
+  __shared__ uint32_t issued_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = (int)((k + COLS - 1) / COLS);
+  if (threadIdx.x == 0) {
+    ws_init(full, empty, cbar, abort_flag);
+    issued_s = 0;
+  }
+  __syncthreads();
+  if (warp == kWsWarps) {
+    if (lane == 0) issued_s = ws_produce<NT, !SCHUR>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
+  } else {
+    WsRing rp;
+    uint32_t ci = 0;
+    bool go = true;
+    for (int64_t ch = blockIdx.x; ch < nch && go; ch += gridDim.x, ++ci) {
+      float2 h2[NT][2], l2[NT][2];  // rows 4 l + 128 t + {0,1} and {2,3}
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) h2[t][p] = l2[t][p] = make_float2(0.f, 0.f);
+      for (int s = 0; s < ntiles; ++s) {
+        float2 x[CPW];
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+          const int64_t j = (int64_t)s * COLS + warp * CPW + c;
+          if (SCHUR)
+            x[c] = make_float2(j < k ? prow[j] : 0.f, 0.f);
+          else
+            x[c] = j < k ? us[j] : make_float2(0.f, 0.f);
+        }
+        if (!ws_consume_wait(&full[rp.slot], rp.phase, abort_flag, err)) {
+          go = false;
+          break;
+        }
+        const float* tile = reinterpret_cast<const float*>(ring + rp.slot * kWsTile) + warp * CPW * RC;
+        float4 a[CPW][NT];
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+#pragma unroll
+          for (int t = 0; t < NT; ++t) a[c][t] = *reinterpret_cast<const float4*>(tile + c * RC + 128 * t + 4 * lane);
+        __syncwarp();
+        if (lane == 0) ws_arrive(&empty[rp.slot]);
+        rp.next();
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+          const float2 uh = make_float2(x[c].x, x[c].x), un = make_float2(-x[c].x, -x[c].x),
+                       ul = make_float2(x[c].y, x[c].y);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            if (SCHUR) {
+              df2_add_prod_lazy(h2[t][0], l2[t][0], lo_pair(a[c][t]), uh, un);
+              df2_add_prod_lazy(h2[t][1], l2[t][1], hi_pair(a[c][t]), uh, un);
+            } else {
+              df2_add_prod_lazy(h2[t][0], l2[t][0], lo_pair(a[c][t]), uh, un, ul);
+              df2_add_prod_lazy(h2[t][1], l2[t][1], hi_pair(a[c][t]), uh, un, ul);
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+          for (int p = 0; p < 2; ++p) df2_renorm(h2[t][p], l2[t][p]);
+      }
+      if (!go) break;
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          cmb[warp * 256 + 128 * t + 4 * lane + 2 * p] = make_float2(h2[t][p].x, l2[t][p].x);
+          cmb[warp * 256 + 128 * t + 4 * lane + 2 * p + 1] = make_float2(h2[t][p].y, l2[t][p].y);
+        }
+      if (!ws_consumer_sync(&cbar[0], ci & 1u, abort_flag, err)) break;
+      const int64_t i0 = ch * RC;
+      const int rr = threadIdx.x;  // 256 consumer threads, one row each
+      if (rr < RC && i0 + rr < n) {
+        float hh = cmb[rr].x, ll = cmb[rr].y;
+#pragma unroll
+        for (int w = 1; w < kWsWarps; ++w) df_add_pair(hh, ll, cmb[w * 256 + rr].x, cmb[w * 256 + rr].y);
+        if (SCHUR)
+          schur[i0 + rr] = make_float2(hh, ll);
+        else
+          z[i0 + rr] = (r[i0 + rr] - ((double)hh + (double)ll)) * inv_lam;
+      }
+      if (!ws_consumer_sync(&cbar[1], ci & 1u, abort_flag, err)) break;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) ws_drain(full, issued_s);
+}
+
+void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows) {
+  plan = WsPlan();
+  if (!L || n < 4 || k < 1 || n % 4 != 0 || n > (int64_t(1) << 30) || k > (int64_t(1) << 30)) return;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  // 256-row chunks (measured faster for both passes) once there is at least one per SM
+  const int rc = rows == 128 || rows == 256 ? rows : (cdiv(n, 256) >= (int64_t)sms ? 256 : 128);
+  plan.rc = rc;
+  plan.nch = cdiv(n, rc);
+  plan.L = L;
+  plan.n = n;
+  plan.k = k;
+  if (!make_f32_map(&plan.map, L, (uint64_t)n, (uint64_t)k, (uint64_t)n, (uint32_t)rc, (uint32_t)(32 * 128 / rc)))
+    return;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(ws_gemv_t_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemT) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(ws_gemv_t_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemT) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(ws_gemv_n_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(ws_gemv_n_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(ws_gemv_n_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(ws_gemv_n_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
+            cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
+    attr = true;
+  }
+  // resident CTAs per SM (two by design; fewer if the shared-memory carve-out says so)
+  int occ = 0, occ_n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ws_gemv_t_kernel<2>, kWsThreads, kWsSmemT) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_n, ws_gemv_n_kernel<2, false>, kWsThreads, kWsSmemN) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    occ = occ_n = 1;
+  }
+  occ = std::max(1, std::min(occ, occ_n));
+  plan.grid = (int)std::min<int64_t>(plan.nch, (int64_t)occ * sms);
+  plan.ok = true;
+}
+
+static bool ws_usable(const WsPlan* plan, const float* L, int64_t n, int64_t k) {
+  return plan && plan->ok && plan->L == L && plan->n == n && plan->k == k;
+}
+
 // Dense k x k products of the apply's core in double-float (DF64 contexts store C^-1
 // and C as float pairs): one warp per row, 16-byte loads (two entries), each term
 // (a_h + a_l)(x_h + x_l) formed by TwoProduct with the cross terms folded in, sums
@@ -434,16 +890,26 @@ static void symv_df(const float2* A, int64_t k, const float2* x, int mode, const
     { symv_df_kernel<false><<<(unsigned)k, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
 }
 
-// t[j] = sum of the chunk partials (as reduce_chunks_kernel), also split into t2[j]
+// t[j] = sum of the chunk partials (as reduce_chunks_kernel), also split into t2[j]; PAIRS:
+// the partials are double-float pairs (float2) rather than doubles
+template <bool PAIRS>
 __global__ void __launch_bounds__(256) reduce_chunks_df_kernel(const double* __restrict__ part, int64_t nchunks,
                                                                int64_t k, double* __restrict__ t,
                                                                float2* __restrict__ t2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * 8 + warp;
   if (j >= k) return;
-  const double* pj = part + j * nchunks;
   double s = 0.0;
-  for (int64_t c = lane; c < nchunks; c += 32) s += pj[c];
+  if (PAIRS) {
+    const float2* pj = reinterpret_cast<const float2*>(part) + j * nchunks;
+    for (int64_t c = lane; c < nchunks; c += 32) {
+      const float2 v = pj[c];
+      s += (double)v.x + (double)v.y;
+    }
+  } else {
+    const double* pj = part + j * nchunks;
+    for (int64_t c = lane; c < nchunks; c += 32) s += pj[c];
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {
     t[j] = s;
@@ -452,36 +918,80 @@ __global__ void __launch_bounds__(256) reduce_chunks_df_kernel(const double* __r
   }
 }
 
-void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
-                       const double* r, double* z, double* part, double* t, float2* rs, cudaStream_t st) {
+// t = L^T r (t2: its float pairs) from the float pairs rs of r
+static void df_pass_t(const float* L, int64_t n, int64_t k, const float2* rs, double* part, double* t, float2* t2,
+                      const WsPlan* plan, int* err, cudaStream_t st) {
+  const unsigned gk = (unsigned)cdiv(k, 8);
+  if (ws_usable(plan, L, n, k)) {
+    if (plan->rc == 256)
+      { ws_gemv_t_kernel<2><<<plan->grid, kWsThreads, kWsSmemT, st>>>(plan->map, n, k, plan->nch, rs, reinterpret_cast<float2*>(part), err); count_launch(); }
+    else
+      { ws_gemv_t_kernel<1><<<plan->grid, kWsThreads, kWsSmemT, st>>>(plan->map, n, k, plan->nch, rs, reinterpret_cast<float2*>(part), err); count_launch(); }
+    { reduce_chunks_df_kernel<true><<<gk, 256, 0, st>>>(part, plan->nch, k, t, t2); count_launch(); }
+    return;
+  }
   const int64_t nchunks = cdiv(n, kDfRows);
   dim3 g1((unsigned)cdiv(k, kDfTCols), (unsigned)nchunks);
+  if (n % 4 == 0)
+    { gemv_t_df_kernel<true><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
+  else
+    { gemv_t_df_kernel<false><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
+  { reduce_chunks_df_kernel<false><<<gk, 256, 0, st>>>(part, nchunks, k, t, t2); count_launch(); }
+}
+
+// z = (r - L u) / lambda from the float pairs u2 of u; part: scratch of 16 n float pairs
+static void df_pass_n(const float* L, int64_t n, int64_t k, const float2* u2, const double* r, double inv_lam,
+                      double* z, double* part, const WsPlan* plan, int* err, cudaStream_t st) {
+  if (ws_usable(plan, L, n, k)) {
+    if (plan->rc == 256)
+      { ws_gemv_n_kernel<2, false><<<plan->grid, kWsThreads, kWsSmemN, st>>>(plan->map, n, k, plan->nch, u2, nullptr, r, inv_lam, z, nullptr, nullptr, err); count_launch(); }
+    else
+      { ws_gemv_n_kernel<1, false><<<plan->grid, kWsThreads, kWsSmemN, st>>>(plan->map, n, k, plan->nch, u2, nullptr, r, inv_lam, z, nullptr, nullptr, err); count_launch(); }
+    return;
+  }
+  float2* zp = reinterpret_cast<float2*>(part);
+  dim3 g2((unsigned)cdiv(n, kDfRows), (unsigned)kDfNGroups);
+  if (n % 4 == 0)
+    { gemv_n_df_kernel<true><<<g2, 256, 0, st>>>(L, n, k, u2, zp); count_launch(); }
+  else
+    { gemv_n_df_kernel<false><<<g2, 256, 0, st>>>(L, n, k, u2, zp); count_launch(); }
+  { gemv_n_df_finish_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(zp, n, r, inv_lam, z); count_launch(); }
+}
+
+void ws_schur(const WsPlan& plan, int64_t m, const float* prow, const PivState* ps, float2* schur, int* err,
+              cudaStream_t st) {
+  if (plan.rc == 256)
+    { ws_gemv_n_kernel<2, true><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, plan.n, m, plan.nch, nullptr, prow, nullptr, 0.0, nullptr, schur, ps, err); count_launch(); }
+  else
+    { ws_gemv_n_kernel<1, true><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, plan.n, m, plan.nch, nullptr, prow, nullptr, 0.0, nullptr, schur, ps, err); count_launch(); }
+}
+
+void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
+                       const double* r, double* z, double* part, double* t, float2* rs, const WsPlan* plan,
+                       int* err, cudaStream_t st) {
   double* u = t + k;
   float2* t2 = reinterpret_cast<float2*>(t + 3 * k);
   float2* e2 = reinterpret_cast<float2*>(t + 4 * k);
   float2* u2 = reinterpret_cast<float2*>(t + 5 * k);
   const float2* Ci2 = reinterpret_cast<const float2*>(Cinv);
   const float2* C2 = reinterpret_cast<const float2*>(C);
-  const unsigned gk = (unsigned)cdiv(k, 8);
-  const bool vec = (n % 4) == 0;
   { split_df_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(r, n, rs); count_launch(); }
-  if (vec)
-    { gemv_t_df_kernel<true><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
-  else
-    { gemv_t_df_kernel<false><<<g1, 256, 0, st>>>(L, n, k, rs, part); count_launch(); }
-  { reduce_chunks_df_kernel<<<gk, 256, 0, st>>>(part, nchunks, k, t, t2); count_launch(); }
+  df_pass_t(L, n, k, rs, part, t, t2, plan, err, st);
   // u = C^-1 t, refined once with the residual t - C u (see woodbury_apply)
   symv_df(Ci2, k, t2, 0, t, u, u2, st);
   symv_df(C2, k, u2, 1, t, nullptr, e2, st);
   symv_df(Ci2, k, e2, 2, t, u, u2, st);
-  // the chunk partials are dead: their buffer takes the column-group partials of L u
-  float2* zp = reinterpret_cast<float2*>(part);
-  dim3 g2((unsigned)nchunks, (unsigned)kDfNGroups);
-  if (vec)
-    { gemv_n_df_kernel<true><<<g2, 256, 0, st>>>(L, n, k, u2, zp); count_launch(); }
-  else
-    { gemv_n_df_kernel<false><<<g2, 256, 0, st>>>(L, n, k, u2, zp); count_launch(); }
-  { gemv_n_df_finish_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(zp, n, r, 1.0 / lam, z); count_launch(); }
+  // the chunk partials are dead: their buffer is the scratch of the register-streamed L u pass
+  df_pass_n(L, n, k, u2, r, 1.0 / lam, z, part, plan, err, st);
+}
+
+void df_passes(const float* L, int64_t n, int64_t k, const double* r, const double* u, double lam, double* t,
+               double* z, double* part, float2* rs, float2* t2, float2* u2, const WsPlan* plan, int* err,
+               cudaStream_t st) {
+  { split_df_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(r, n, rs); count_launch(); }
+  df_pass_t(L, n, k, rs, part, t, t2, plan, err, st);
+  { split_df_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(u, k, u2); count_launch(); }
+  df_pass_n(L, n, k, u2, r, 1.0 / lam, z, part, plan, err, st);
 }
 
 // each double becomes the float pair (hi, lo) in the same 8 bytes

@@ -25,7 +25,7 @@ SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3}
 
 EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
-           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_test_oz_gemm", "gdml_tc_check",
+           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_test_oz_gemm", "gdml_test_df_passes", "gdml_tc_check",
            "gdml_launch_count", "gdml_matvec_noalloc", "gdml_pcg_solve_batched", "gdml_autotune",
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
@@ -66,6 +66,7 @@ def load() -> ctypes.CDLL:
         "gdml_destroy": [P],
         "gdml_test_tc_gemm": [I32, P, P, I32, I32, I32, P, P],
         "gdml_test_oz_gemm": [P, P, I64, I64, I64, P, P],
+        "gdml_test_df_passes": [P, I64, I64, P, P, D, I32, P, P, P],
         "gdml_tc_check": [P],
         "gdml_launch_count": [],
         "gdml_matvec_noalloc": [P, I64, I32, D, D, P, P, I32, P],
@@ -279,6 +280,27 @@ def test_oz_gemm(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())
     return C
+
+
+def test_df_passes(L: torch.Tensor, r: torch.Tensor, u: torch.Tensor, lam: float, staged=True):
+    """The two passes over the FP32 factor of the DF64/OZAKI Woodbury apply:
+    returns (t, z) with t = L^T r and z = (r - L u) / lam.  L: n x k FP32 (its columns
+    are stored contiguously, i.e. L.t().contiguous() is passed), r: n, u: k FP64.
+    staged: True (TMA-staged, automatic chunk size), 128 or 256 (that chunk size),
+    False (register-streamed)."""
+    lib = load()
+    n, k = L.shape
+    Lc = L.t().contiguous()  # column j at offset j n
+    r = r.contiguous()
+    u = u.contiguous()
+    t = torch.empty(k, dtype=torch.float64, device=L.device)
+    z = torch.empty(n, dtype=torch.float64, device=L.device)
+    mode = int(staged) if not isinstance(staged, bool) else int(staged)
+    st = lib.gdml_test_df_passes(_ptr(Lc), n, k, _ptr(r), _ptr(u), float(lam), mode, _ptr(t), _ptr(z),
+                                 ctypes.c_void_p(torch.cuda.current_stream(L.device).cuda_stream))
+    if st != 0:
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+    return t, z
 
 
 def launch_count() -> int:
