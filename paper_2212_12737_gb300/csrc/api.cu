@@ -909,8 +909,9 @@ gdml_status gdml_test_df_passes(const float* L_dev, int64_t n, int64_t k, const 
     ws_plan(plan, L_dev, n, k, staged);
     if (!plan.ok) return fail(GDML_ERR_ARG, "staged passes need n % 4 == 0 and a valid TMA map");
   }
-  const size_t part_b = (size_t)woodbury_part_size(n, k) * sizeof(double);
-  const size_t rs_b = (size_t)n * sizeof(float2), kv_b = (size_t)k * sizeof(float2);
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };  // 256-byte aligned sub-buffers
+  const size_t part_b = al((size_t)woodbury_part_size(n, k) * sizeof(double));
+  const size_t rs_b = al((size_t)n * sizeof(float2)), kv_b = al((size_t)k * sizeof(float2));
   void* buf = nullptr;
   if (cudaMalloc(&buf, part_b + rs_b + 2 * kv_b + 256) != cudaSuccess) {
     (void)cudaGetLastError();

@@ -56,14 +56,16 @@ void mirror_lower(double* A, int64_t k, cudaStream_t st);
 // DF64 contexts: FP32-stored L_k, double-float accumulation; C and Cinv hold float
 // pairs (split_df_inplace); t holds 6k doubles (t, u, e and three float-pair vectors)
 void split_df_inplace(double* a, int64_t count, cudaStream_t st);
-// TMA-staged passes over the FP32 factor (n x k, column j at L + j n): rows in chunks of rc
-// = 128 or 256; valid only for n % 4 == 0
+// TMA-staged passes over the FP32 factor (n x k, column j at L + j n); valid only for
+// n % 4 == 0
 struct WsPlan {
   bool ok = false;
   const float* L = nullptr;
-  int64_t n = 0, k = 0, nch = 0;
-  int rc = 0, grid = 0;
-  CUtensorMap map;  // box rc rows x (32 * 128 / rc) columns
+  int64_t n = 0, k = 0, nch = 0, nru = 0;
+  int rc = 0, grid = 0;                 // L u pass: chunks of rc rows
+  int ru = 0, ncr = 0, cpr = 0, grid_t = 0;  // L^T r pass: units of ru rows x cpr columns
+  CUtensorMap map;   // box rc rows x (32 * 128 / rc) columns
+  CUtensorMap mapT;  // box 256 rows x 16 columns
 };
 // fills plan for L (plan.ok = false where the staged passes do not apply: n % 4 != 0, k = 0,
 // or the driver rejects the map); rows: 128 or 256 to force the chunk size, else automatic

@@ -383,7 +383,7 @@ constexpr int kWsThreads = 32 * (kWsWarps + 1);  // + one producer warp
 constexpr int kWsTile = 16384;                   // bytes per tile (RC x 32/NT floats)
 constexpr int kWsStages = 6;
 constexpr int kWsAlign = 128;  // TMA destination alignment (no swizzle)
-constexpr int kWsSmemT = kWsAlign + kWsStages * kWsTile + 2 * kWsStages * 8 + 16;
+constexpr int kWsSmemT = kWsAlign + kWsStages * kWsTile + 3 * 256 * 16 + (2 * kWsStages + 2) * 8 + 16;
 constexpr int kWsSmemN = kWsAlign + kWsStages * kWsTile + kWsWarps * 256 * 8 + (2 * kWsStages + 2) * 8 + 16;
 static_assert(2 * kWsSmemT <= 227 * 1024 && 2 * kWsSmemN <= 227 * 1024, "two CTAs per SM");
 
@@ -550,94 +550,151 @@ __device__ __forceinline__ void ws_init(uint64_t* full, uint64_t* empty, uint64_
 
 }  // namespace
 
-// part[j * nch + chunk] = sum over the chunk's rows of L[i + j n] r[i] (a double-float pair;
-// the FP64 combination is left to the chunk reduction, off this kernel's critical path).  Per lane and column
-// two packed chains (even and odd rows); every 8 / CPW tiles a warp folds them into one
-// double-float partial per lane for 8 columns and reduces those with one reduce-scatter.
-template <int NT>
+// L^T r over units of RU rows (a multiple of 256, at most 1024) x a range of CPR columns (a
+// multiple of 64): part[j * nru + ru] = sum over row unit ru of L[i + j n] r[i] as a
+// double-float pair (the FP64 combination is left to the chunk reduction).  Tiles are
+// 256 rows x 16 columns, taken column tile by column tile, the unit's RU / 256 row tiles
+// of each in turn.  Warp w sums columns 2w, 2w + 1 of each tile over all RU rows of the unit
+// (lane l: rows 4 l + 128 t + 256 rt + e, two packed chains per column: even and odd rows);
+// every 4 column tiles it holds 8 columns and reduces them with one reduce-scatter, so the
+// cross-lane reduction is paid once per 32 RU / 256 products per lane and column.  r of the
+// unit's rows sits in shared memory as packed quads (hi, -hi, lo), loaded once per unit.
 __global__ void __launch_bounds__(kWsThreads, 2)
-    ws_gemv_t_kernel(const __grid_constant__ CUtensorMap map, int64_t n, int64_t k, int64_t nch,
-                     const float2* __restrict__ rs, float2* __restrict__ part, int* __restrict__ err) {
-  constexpr int RC = 128 * NT, COLS = 32 / NT, CPW = 4 / NT, TPG = 8 / CPW;  // TPG: tiles per 8 columns
+    ws_gemv_t_kernel(const __grid_constant__ CUtensorMap map, int64_t n, int64_t k, int ru_rows, int64_t nru,
+                     int ncr, int cpr, const float2* __restrict__ rs, float2* __restrict__ part,
+                     int* __restrict__ err) {
+  constexpr int RC = 256, COLS = 16;
   extern __shared__ uint8_t ws_smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws_smem_raw) + kWsAlign - 1) &
                                              ~uintptr_t(kWsAlign - 1));
-  uint64_t* full = reinterpret_cast<uint64_t*>(ring + kWsStages * kWsTile);
+  float4* rh4 = reinterpret_cast<float4*>(ring + kWsStages * kWsTile);  // [256] quads of rows
+  float4* rn4 = rh4 + 256;
+  float4* rl4 = rn4 + 256;
+  uint64_t* full = reinterpret_cast<uint64_t*>(rl4 + 256);
   uint64_t* empty = full + kWsStages;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kWsStages);
+  uint64_t* cbar = empty + kWsStages;  // [2]: r quads written / unit finished
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(cbar + 2);
   __shared__ uint32_t issued_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = (int)((k + COLS - 1) / COLS);
+  const int rtiles = ru_rows / RC;
+  const int64_t units = nru * ncr;
   if (threadIdx.x == 0) {
-    ws_init(full, empty, nullptr, abort_flag);
+    ws_init(full, empty, cbar, abort_flag);
     issued_s = 0;
   }
   __syncthreads();
   if (warp == kWsWarps) {
-    if (lane == 0) issued_s = ws_produce<NT, true>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
-  } else {
-    WsRing rp;
-    bool go = true;
-    for (int64_t ch = blockIdx.x; ch < nch && go; ch += gridDim.x) {
-      const int64_t i0 = ch * RC;
-      // r of the lane's rows as packed pairs (rows 4 l + 128 t + {0,1} and {2,3})
-      float2 rh[NT][2], rn[NT][2], rl[NT][2];
-#pragma unroll
-      for (int t = 0; t < NT; ++t)
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          const int64_t i = i0 + 128 * t + 4 * lane + 2 * p;
-          const float2 r0 = i < n ? rs[i] : make_float2(0.f, 0.f);
-          const float2 r1 = i + 1 < n ? rs[i + 1] : make_float2(0.f, 0.f);
-          rh[t][p] = make_float2(r0.x, r1.x);
-          rn[t][p] = make_float2(-r0.x, -r1.x);
-          rl[t][p] = make_float2(r0.y, r1.y);
-        }
-      for (int g = 0; g < ntiles && go; g += TPG) {
-        float2 h2[8], l2[8];  // per column: (even rows, odd rows) chains
-#pragma unroll
-        for (int c = 0; c < 8; ++c) h2[c] = l2[c] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < TPG; ++q) {
-          if (g + q < ntiles) {
-            if (!ws_consume_wait(&full[rp.slot], rp.phase, abort_flag, err)) {
+    if (lane == 0) {
+      uint64_t policy;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+      WsRing rp;
+      uint32_t issued = 0;
+      bool go = true;
+      for (int64_t u = blockIdx.x; u < units && go; u += gridDim.x) {
+        const int64_t ru = u / ncr;
+        const int64_t c0 = (u % ncr) * cpr;
+        const int64_t c1 = c0 + cpr < k ? c0 + cpr : k;
+        const int ntc = (int)((c1 - c0 + COLS - 1) / COLS);
+        for (int ct = 0; ct < ntc && go; ++ct)
+          for (int rt = 0; rt < rtiles; ++rt, ++issued, rp.next()) {
+            if (!ws_wait(&empty[rp.slot], rp.phase ^ 1u)) {
+              atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+              *abort_flag = 1;
               go = false;
               break;
             }
-            const float* tile = reinterpret_cast<const float*>(ring + rp.slot * kWsTile) + warp * CPW * RC;
-            float4 a[CPW][NT];
+            if (*abort_flag) {
+              go = false;
+              break;
+            }
+            tc::mbar_expect_tx(&full[rp.slot], kWsTile);
+            ws_tma_load(ring + rp.slot * kWsTile, &map, &full[rp.slot], (int)(ru * ru_rows + rt * RC),
+                        (int)(c0 + ct * COLS), policy);
+          }
+      }
+      issued_s = issued;
+    }
+  } else {
+    WsRing rp;
+    uint32_t ui = 0;
+    bool go = true;
+    for (int64_t u = blockIdx.x; u < units && go; u += gridDim.x, ++ui) {
+      const int64_t ru = u / ncr;
+      const int64_t c0 = (u % ncr) * cpr;
+      const int64_t c1 = c0 + cpr < k ? c0 + cpr : k;
+      const int ntc = (int)((c1 - c0 + COLS - 1) / COLS);
+      const int64_t i0 = ru * ru_rows;
+      {  // r of the unit's rows as packed quads
+        const int g = threadIdx.x;  // 256 consumer threads, 4 rows each
+        if (4 * g < ru_rows) {
+          float4 h = make_float4(0.f, 0.f, 0.f, 0.f), lo = h;
+          const int64_t i = i0 + 4 * g;
+          if (i + 3 < n) {
+            const float4 p0 = *reinterpret_cast<const float4*>(rs + i);  // n % 4 == 0: 16-byte aligned
+            const float4 p1 = *reinterpret_cast<const float4*>(rs + i + 2);
+            h = make_float4(p0.x, p0.z, p1.x, p1.z);
+            lo = make_float4(p0.y, p0.w, p1.y, p1.w);
+          }
+          rh4[g] = h;
+          rn4[g] = make_float4(-h.x, -h.y, -h.z, -h.w);
+          rl4[g] = lo;
+        }
+      }
+      if (!ws_consumer_sync(&cbar[0], ui & 1u, abort_flag, err)) break;
+      for (int g = 0; g < ntc && go; g += 4) {
+        float2 h2[8], l2[8];
 #pragma unroll
-            for (int c = 0; c < CPW; ++c)
+        for (int c = 0; c < 8; ++c) h2[c] = l2[c] = make_float2(0.f, 0.f);
 #pragma unroll
-              for (int t = 0; t < NT; ++t) a[c][t] = *reinterpret_cast<const float4*>(tile + c * RC + 128 * t + 4 * lane);
-            __syncwarp();
-            if (lane == 0) ws_arrive(&empty[rp.slot]);
-            rp.next();
-#pragma unroll
-            for (int t = 0; t < NT; ++t)
-#pragma unroll
-              for (int c = 0; c < CPW; ++c) {
-                df2_add_prod_lazy(h2[q * CPW + c], l2[q * CPW + c], lo_pair(a[c][t]), rh[t][0], rn[t][0], rl[t][0]);
-                df2_add_prod_lazy(h2[q * CPW + c], l2[q * CPW + c], hi_pair(a[c][t]), rh[t][1], rn[t][1], rl[t][1]);
+        for (int q = 0; q < 4; ++q) {
+          if (g + q < ntc && go) {
+#pragma unroll 1
+            for (int rt = 0; rt < rtiles; ++rt) {
+              if (!ws_consume_wait(&full[rp.slot], rp.phase, abort_flag, err)) {
+                go = false;
+                break;
               }
+              const float* tile = reinterpret_cast<const float*>(ring + rp.slot * kWsTile) + 2 * warp * RC;
+              float4 a[2][2];
+#pragma unroll
+              for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int t = 0; t < 2; ++t) a[c][t] = *reinterpret_cast<const float4*>(tile + c * RC + 128 * t + 4 * lane);
+              __syncwarp();
+              if (lane == 0) ws_arrive(&empty[rp.slot]);
+              rp.next();
+#pragma unroll
+              for (int t = 0; t < 2; ++t) {
+                const int gq = rt * 64 + 32 * t + lane;
+                const float4 h = rh4[gq], ng = rn4[gq], lo = rl4[gq];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  df2_add_prod_lazy(h2[2 * q + c], l2[2 * q + c], lo_pair(a[c][t]), lo_pair(h), lo_pair(ng), lo_pair(lo));
+                  df2_add_prod_lazy(h2[2 * q + c], l2[2 * q + c], hi_pair(a[c][t]), hi_pair(h), hi_pair(ng), hi_pair(lo));
+                }
+              }
+              df2_renorm(h2[2 * q], l2[2 * q]);
+              df2_renorm(h2[2 * q + 1], l2[2 * q + 1]);
+            }
           }
         }
         if (!go) break;
         float h[8], l[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          df2_renorm(h2[c], l2[c]);
           h[c] = h2[c].x;
           l[c] = l2[c].x;
           df_add_pair(h[c], l[c], h2[c].y, l2[c].y);
         }
         float oh, ol;
         reduce_scatter8(h, l, lane, oh, ol);
-        // reduce-scatter slot c = q CPW + cc holds column (g + q) COLS + w CPW + cc
+        // reduce-scatter slot c = 2 q + b holds column c0 + (g + q) 16 + 2 w + b
         const int c = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        const int64_t col = (int64_t)(g + c / CPW) * COLS + warp * CPW + (c % CPW);
-        if ((lane & 3) == 0 && col < k) part[col * nch + ch] = make_float2(oh, ol);
+        const int64_t col = c0 + (int64_t)(g + (c >> 1)) * COLS + 2 * warp + (c & 1);
+        if ((lane & 3) == 0 && col < c1) part[col * nru + ru] = make_float2(oh, ol);
       }
+      if (!go) break;
+      if (!ws_consumer_sync(&cbar[1], ui & 1u, abort_flag, err)) break;  // r quads free for the next unit
     }
   }
   __syncthreads();
@@ -767,21 +824,9 @@ void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
       sms = 1;
   }
-  // 256-row chunks (measured faster for both passes) once there is at least one per SM
-  const int rc = rows == 128 || rows == 256 ? rows : (cdiv(n, 256) >= (int64_t)sms ? 256 : 128);
-  plan.rc = rc;
-  plan.nch = cdiv(n, rc);
-  plan.L = L;
-  plan.n = n;
-  plan.k = k;
-  if (!make_f32_map(&plan.map, L, (uint64_t)n, (uint64_t)k, (uint64_t)n, (uint32_t)rc, (uint32_t)(32 * 128 / rc)))
-    return;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(ws_gemv_t_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemT) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(ws_gemv_t_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemT) !=
-            cudaSuccess ||
+    if (cudaFuncSetAttribute(ws_gemv_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemT) != cudaSuccess ||
         cudaFuncSetAttribute(ws_gemv_n_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
             cudaSuccess ||
         cudaFuncSetAttribute(ws_gemv_n_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
@@ -796,15 +841,46 @@ void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows) {
     attr = true;
   }
   // resident CTAs per SM (two by design; fewer if the shared-memory carve-out says so)
-  int occ = 0, occ_n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ws_gemv_t_kernel<2>, kWsThreads, kWsSmemT) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_n, ws_gemv_n_kernel<2, false>, kWsThreads, kWsSmemN) !=
-          cudaSuccess) {
+  int occ = 0, occ_t = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ws_gemv_n_kernel<2, false>, kWsThreads, kWsSmemN) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, ws_gemv_t_kernel, kWsThreads, kWsSmemT) != cudaSuccess) {
     (void)cudaGetLastError();
-    occ = occ_n = 1;
+    occ = occ_t = 1;
   }
-  occ = std::max(1, std::min(occ, occ_n));
-  plan.grid = (int)std::min<int64_t>(plan.nch, (int64_t)occ * sms);
+  const int64_t G = (int64_t)std::max(1, std::min(occ, occ_t)) * sms;
+  // L u pass (and Schur sums): 256-row chunks (measured faster) once there is one per SM
+  const int rc = rows == 128 || rows == 256 ? rows : (cdiv(n, 256) >= (int64_t)sms ? 256 : 128);
+  plan.rc = rc;
+  plan.nch = cdiv(n, rc);
+  plan.grid = (int)std::min<int64_t>(plan.nch, G);
+  // L^T r pass: row units of up to 1024 rows; column ranges fill the CTAs when the row units
+  // alone do not; whole waves when they do
+  const int64_t kg = cdiv(k, 64);  // 64-column groups
+  int64_t ru = 1024;
+  if (cdiv(n, 1024) >= G) {
+    const int64_t waves = cdiv(cdiv(n, 1024), G);
+    ru = 256 * cdiv(n, 256 * waves * G);
+    ru = std::min<int64_t>(1024, std::max<int64_t>(256, ru));
+  } else {
+    for (int64_t cand : {1024, 512, 256}) {
+      ru = cand;
+      const int64_t nr = cdiv(n, cand);
+      if (nr * std::min<int64_t>(kg, std::max<int64_t>(1, G / nr)) * 4 >= 3 * G) break;
+    }
+  }
+  plan.ru = (int)ru;
+  plan.nru = cdiv(n, ru);
+  plan.ncr = (int)std::min<int64_t>(kg, std::max<int64_t>(1, G / plan.nru));
+  plan.cpr = (int)(64 * cdiv(kg, plan.ncr));
+  plan.ncr = (int)cdiv(k, plan.cpr);
+  plan.grid_t = (int)std::min<int64_t>(plan.nru * plan.ncr, G);
+  plan.L = L;
+  plan.n = n;
+  plan.k = k;
+  if (!make_f32_map(&plan.map, L, (uint64_t)n, (uint64_t)k, (uint64_t)n, (uint32_t)rc, (uint32_t)(32 * 128 / rc)) ||
+      !make_f32_map(&plan.mapT, L, (uint64_t)n, (uint64_t)k, (uint64_t)n, 256u, 16u))
+    return;
   plan.ok = true;
 }
 
@@ -923,11 +999,8 @@ static void df_pass_t(const float* L, int64_t n, int64_t k, const float2* rs, do
                       const WsPlan* plan, int* err, cudaStream_t st) {
   const unsigned gk = (unsigned)cdiv(k, 8);
   if (ws_usable(plan, L, n, k)) {
-    if (plan->rc == 256)
-      { ws_gemv_t_kernel<2><<<plan->grid, kWsThreads, kWsSmemT, st>>>(plan->map, n, k, plan->nch, rs, reinterpret_cast<float2*>(part), err); count_launch(); }
-    else
-      { ws_gemv_t_kernel<1><<<plan->grid, kWsThreads, kWsSmemT, st>>>(plan->map, n, k, plan->nch, rs, reinterpret_cast<float2*>(part), err); count_launch(); }
-    { reduce_chunks_df_kernel<true><<<gk, 256, 0, st>>>(part, plan->nch, k, t, t2); count_launch(); }
+    { ws_gemv_t_kernel<<<plan->grid_t, kWsThreads, kWsSmemT, st>>>(plan->mapT, n, k, plan->ru, plan->nru, plan->ncr, plan->cpr, rs, reinterpret_cast<float2*>(part), err); count_launch(); }
+    { reduce_chunks_df_kernel<true><<<gk, 256, 0, st>>>(part, plan->nru, k, t, t2); count_launch(); }
     return;
   }
   const int64_t nchunks = cdiv(n, kDfRows);
