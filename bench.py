@@ -44,8 +44,11 @@ def parse():
                          "BF16 slices on the tensor cores; both FP64-class, FP64 true-residual restarts)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison solves")
-    ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply"],
-                    help="time one operation alone (small runs for profiling)")
+    ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply", "passes"],
+                    help="time one operation alone (small runs for profiling); passes: the two staged "
+                         "passes of the DF64/OZAKI apply on a random FP32 factor of the workload's n x k")
+    ap.add_argument("--rows", type=int, default=1, choices=[1, 128, 256],
+                    help="--only passes: row-chunk size of the staged passes (1: automatic)")
     ap.add_argument("--suite", default=None, choices=["batched", "learned"],
                     help="many uneven systems: per-system solves vs one batched graph solve")
     ap.add_argument("--suite-count", type=int, default=64)
@@ -125,6 +128,24 @@ def run_op(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     w = synth.workload(args.workload)
+    if args.only == "passes":  # the library's test hook on a random factor (its columns contiguous)
+        g = torch.Generator(device=dev).manual_seed(0)
+        Lc = torch.randn(w.k, w.n, device=dev, generator=g).float()
+        r = torch.randn(w.n, dtype=torch.float64, device=dev, generator=g)
+        u = torch.randn(w.k, dtype=torch.float64, device=dev, generator=g)
+        fn = lambda: gdml.test_df_passes(Lc.t(), r, u, w.lam, staged=args.rows)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn()
+        torch.cuda.synchronize(dev)
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        print(json.dumps({"op": "passes", "workload": args.workload, "rows": args.rows, "n": w.n, "k": w.k,
+                          "host_ms_per_call": ms, "note": "includes the hook's scratch allocation; use ncu "
+                          "kernel durations"}), flush=True)
+        return
     ctx = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam, precision=args.precision)
     v = torch.randn(w.n, dtype=torch.float64, device=dev)
     out = torch.empty_like(v)
@@ -148,7 +169,9 @@ def run_op(args):
     D = w.N * (w.N - 1) // 2
     print(json.dumps({"op": args.only, "workload": args.workload, "precision": args.precision, "ms": ms,
                       "matvec_tflops": 6.0 * w.M * w.M * D / ms / 1e9 if args.only == "matvec" else None,
-                      "apply_gbs": 2.0 * w.n * w.k * 8 / ms / 1e6 if args.only == "apply" else None}), flush=True)
+                      "apply_gbs": (2.0 * w.n * w.k * (4 if args.precision in ("df64", "ozaki") else 8)
+                                    + 3.0 * w.k * w.k * 8) / ms / 1e6 if args.only == "apply" else None}),
+          flush=True)
     ctx.destroy()
 
 

@@ -307,7 +307,14 @@ gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, d
     set_identity(X, k, c->st);
     trsm_left_lower(LC, k, X, k, c->st);  // X = L_C^-1
     transpose_square(X, k, Xt, c->st);
-    launch_dgemm<double, double>(true, k, k, k, 1.0, Xt, k, Xt, k, 0.0, Cinv, k, false, c->st);  // X^T X
+    if (df_precond(c)) {  // X^T X on the sliced tensor cores (FP64-class), lower triangle mirrored
+      TRY(check_launch(c, "woodbury inverse"));
+      gdml_status so = oz_syrk_lower_f64(Xt, k, k, k, Cinv, k, c->st);
+      if (so != GDML_OK) return ctx_fail(c, so, "sliced X^T X: " + last_msg());
+      mirror_lower(Cinv, k, c->st);
+    } else {
+      launch_dgemm<double, double>(true, k, k, k, 1.0, Xt, k, Xt, k, 0.0, Cinv, k, false, c->st);  // X^T X
+    }
     TRY(check_launch(c, "woodbury inverse"));
     if (Lf && Cfull) {  // DF64 apply: the two k x k operators as float pairs
       split_df_inplace(Cinv, k * k, c->st);

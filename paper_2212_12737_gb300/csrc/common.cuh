@@ -71,4 +71,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
+// p = i(i-1)/2 + j with i > j  ->  (i, j)
+__device__ __forceinline__ void pair_of(int p, int& i, int& j) {
+  // FP32 estimate (GB300's FP64 pipe is slow), then exact integer correction
+  int ii = (int)((1.f + sqrtf(1.f + 8.f * (float)p)) * 0.5f);
+  while (ii * (ii - 1) / 2 > p) --ii;
+  while ((ii + 1) * ii / 2 <= p) ++ii;
+  i = ii;
+  j = p - ii * (ii - 1) / 2;
+}
+__device__ __forceinline__ int pair_idx(int i, int j) {  // requires i != j
+  return i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i;
+}
+
+
 }  // namespace gdml

@@ -16,19 +16,6 @@
 
 namespace gdml {
 
-// p = i(i-1)/2 + j with i > j  ->  (i, j)
-__device__ __forceinline__ void pair_of(int p, int& i, int& j) {
-  // FP32 estimate (GB300's FP64 pipe is slow), then exact integer correction
-  int ii = (int)((1.f + sqrtf(1.f + 8.f * (float)p)) * 0.5f);
-  while (ii * (ii - 1) / 2 > p) --ii;
-  while ((ii + 1) * ii / 2 <= p) ++ii;
-  i = ii;
-  j = p - ii * (ii - 1) / 2;
-}
-__device__ __forceinline__ int pair_idx(int i, int j) {  // requires i != j
-  return i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i;
-}
-
 __global__ void desc_jac_kernel(const double* __restrict__ R, int64_t M, int N, int D,
                                 double* __restrict__ X, double* __restrict__ G) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -125,31 +112,51 @@ __global__ void kdiag_kernel(const double* __restrict__ G, int64_t M, int N, int
   diag[t] = c2_3 * s;
 }
 
-// W row a (ld = ldW) and t_a = xc_a . w_a, one warp per geometry (8 per CTA): v_a in
-// the warp's slice of shared memory, lanes over the pairs, t_a by a fixed shuffle tree.
-__global__ void __launch_bounds__(256) proj_warp_kernel(const double* __restrict__ G, const double* __restrict__ Xc,
+// W_a = J_a v_a and t_a = xc_a . w_a; one CTA per geometry, one descriptor p per thread (a
+// second round when D exceeds the block): the G loads are issued before v_a is staged, the
+// pair (i, j) of p decoded in FP32, and t_a reduced in a fixed order (shuffle tree, then warps).
+__global__ void __launch_bounds__(1024) proj_cta_kernel(const double* __restrict__ G, const double* __restrict__ Xc,
                                                         const double* __restrict__ v, int64_t M, int N, int D,
                                                         double* __restrict__ W, int64_t ldW, double* __restrict__ t) {
-  extern __shared__ double sh_vw[];  // 8 x 3N
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t a = (int64_t)blockIdx.x * 8 + warp;
-  if (a >= M) return;
+  extern __shared__ double sv[];  // 3N
+  __shared__ double red[32];
+  const int64_t a = blockIdx.x;
   const int B = 3 * N;
-  double* sv = sh_vw + warp * B;
-  for (int l = lane; l < B; l += 32) sv[l] = v[a * B + l];
-  __syncwarp();
   const double* Ga = G + a * D * 3;
+  int p = threadIdx.x;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0, xc = 0.0;
+  if (p < D) {
+    g0 = Ga[3 * p];
+    g1 = Ga[3 * p + 1];
+    g2 = Ga[3 * p + 2];
+    xc = Xc[a * D + p];
+  }
+  for (int l = threadIdx.x; l < B; l += blockDim.x) sv[l] = v[a * B + l];
+  __syncthreads();
   double part = 0.0;
-  for (int p = lane; p < D; p += 32) {
+  for (; p < D; p += blockDim.x) {
+    if (p >= (int)blockDim.x) {  // later rounds (D > blockDim)
+      g0 = Ga[3 * p];
+      g1 = Ga[3 * p + 1];
+      g2 = Ga[3 * p + 2];
+      xc = Xc[a * D + p];
+    }
     int i, j;
     pair_of(p, i, j);
-    const double w = -(Ga[3 * p] * (sv[3 * i] - sv[3 * j]) + Ga[3 * p + 1] * (sv[3 * i + 1] - sv[3 * j + 1]) +
-                       Ga[3 * p + 2] * (sv[3 * i + 2] - sv[3 * j + 2]));
+    const double w = -(g0 * (sv[3 * i] - sv[3 * j]) + g1 * (sv[3 * i + 1] - sv[3 * j + 1]) +
+                       g2 * (sv[3 * i + 2] - sv[3 * j + 2]));
     W[a * ldW + p] = w;
-    part = fma(Xc[a * D + p], w, part);
+    part = fma(xc, w, part);
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (lane == 0) t[a] = part;
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    t[a] = s;
+  }
 }
 
 // beta_ab = c^2 S_ab (T_ab - t_b) into Pb[a*ldP + b]; rowsum_a = sum_b beta_ab
@@ -310,11 +317,25 @@ __global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restric
   for (int p = threadIdx.x; p < D; p += blockDim.x) sxb[p] = Xb[p];
   const int64_t a = (int64_t)blockIdx.x * W + warp;
   const bool live = a < M;
-  if (live) {
+  if (live) {  // eight independent loads in flight per lane, then the shared-memory stores
     const double* Xa = X + a * D;
     const double* Ga = G + a * D * 3;
-    for (int p = lane; p < D; p += 32) sxa[p] = Xa[p];
-    for (int e = lane; e < 3 * D; e += 32) sga[e] = Ga[e];
+    for (int e0 = lane; e0 < 4 * D; e0 += 32 * 8) {
+      double tmp[8];
+#pragma unroll
+      for (int u8 = 0; u8 < 8; ++u8) {
+        const int e = e0 + 32 * u8;
+        tmp[u8] = e < D ? Xa[e] : (e < 4 * D ? Ga[e - D] : 0.0);
+      }
+#pragma unroll
+      for (int u8 = 0; u8 < 8; ++u8) {
+        const int e = e0 + 32 * u8;
+        if (e < D)
+          sxa[e] = tmp[u8];
+        else if (e < 4 * D)
+          sga[e - D] = tmp[u8];
+      }
+    }
   }
   __syncthreads();
   if (!live) return;
@@ -364,7 +385,8 @@ void launch_kdiag(const double* G, int64_t M, int N, int D, double c, double* di
 }
 void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, int N, int D, double* W,
                  int64_t ldW, double* t, cudaStream_t st) {
-  { proj_warp_kernel<<<(unsigned)cdiv(M, 8), 256, 8 * 3 * N * sizeof(double), st>>>(G, Xc, v, M, N, D, W, ldW, t); count_launch(); }
+  const unsigned threads = (unsigned)std::min<int64_t>(1024, 32 * cdiv(D, 32));
+  { proj_cta_kernel<<<(unsigned)M, threads, 3 * N * sizeof(double), st>>>(G, Xc, v, M, N, D, W, ldW, t); count_launch(); }
 }
 void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
                  int64_t ldP, double* rowsum, cudaStream_t st) {
@@ -392,7 +414,18 @@ void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const doub
                  const int* stop_flag, cudaStream_t st) {
   // warps per CTA so that the staged operands fit in 200 KB of shared memory
   const size_t per_warp = 5 * (size_t)D * sizeof(double), fixed = ((size_t)N + D) * sizeof(double);
-  const int W = (int)std::min<size_t>(8, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / per_warp);
+  int W = (int)std::min<size_t>(8, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / per_warp);
+  {  // few columns (one per Algorithm 1 step): fewer warps per CTA so the grid covers every SM twice
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    }
+    const int64_t want = std::max<int64_t>(1, M * ncols / (2 * (int64_t)sms));
+    if (want < W) W = (int)want;
+  }
   if (W >= 1 && ncols <= 65535) {
     const size_t wsmem = fixed + W * per_warp;
     static size_t attr = 0;

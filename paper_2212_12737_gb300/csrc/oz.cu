@@ -86,13 +86,26 @@ __device__ __forceinline__ float2 split_d(double x) {
 // 2^k for -126 <= k <= 127
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
 
+// x * 2^e, exact unless the result leaves the FP32 range
+__device__ __forceinline__ float scale2(float x, int e) {
+  while (e > 127) {
+    x *= pow2f(127);
+    e -= 127;
+  }
+  while (e < -126) {
+    x *= pow2f(-126);
+    e += 126;
+  }
+  return x * pow2f(e);
+}
+
 // Slices of one entry (hi + lo) of a chunk whose magnitudes are all below 2^ex:
 // s_i = rint(y), y <- (y - s_i) * 2^7, starting from y = x 2^(7 - ex).  All
 // steps are exact; |s_1| <= 128 and |s_i| <= 64 for i > 1.
 __device__ __forceinline__ void slice_write(float2 xs, int ex, bf16* __restrict__ sl, int64_t row, int64_t k,
                                             int64_t Rp, int64_t Kp) {
   if (k >= Kp) return;
-  float yh = ldexpf(xs.x, oz::BITS - ex), yl = ldexpf(xs.y, oz::BITS - ex);
+  float yh = scale2(xs.x, oz::BITS - ex), yl = scale2(xs.y, oz::BITS - ex);
   const float up = (float)(1 << oz::BITS);
 #pragma unroll
   for (int i = 0; i < oz::S; ++i) {
@@ -167,6 +180,53 @@ __global__ void __launch_bounds__(256) oz_slice_rows_f32_kernel(const float* __r
   slice_write(make_float2(x, 0.f), ex, sl, row, k, Rp, Kp);
 }
 
+// W_a = J_a v_a and t_a = xc_a . w_a (as the FP64 projection), fused with the slicing of
+// row a of W into GEMM 1's B operand when it is one chunk (Kp <= 256): one CTA per geometry,
+// thread p holds w_p, the chunk exponent and t_a are CTA reductions; t_a is also written as
+// a double-float pair.
+__global__ void __launch_bounds__(256) oz_proj_slice_kernel(const double* __restrict__ G, const double* __restrict__ Xc,
+                                                            const double* __restrict__ v, int64_t M, int N, int D,
+                                                            double* __restrict__ W, double* __restrict__ t,
+                                                            float2* __restrict__ t2, int64_t Rp, int64_t Kp,
+                                                            bf16* __restrict__ sl, int* __restrict__ e) {
+  extern __shared__ double sv[];  // 3N
+  __shared__ float red[8];
+  __shared__ double redt[8];
+  const int64_t a = blockIdx.x;
+  const int p = threadIdx.x, warp = p >> 5, lane = p & 31;
+  const int B = 3 * N;
+  const double* Ga = G + a * D * 3;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0, xc = 0.0;
+  if (p < D) {
+    g0 = Ga[3 * p];
+    g1 = Ga[3 * p + 1];
+    g2 = Ga[3 * p + 2];
+    xc = Xc[a * D + p];
+  }
+  for (int l = p; l < B; l += blockDim.x) sv[l] = v[a * B + l];
+  __syncthreads();
+  double w = 0.0;
+  if (p < D) {
+    int i, j;
+    pair_of(p, i, j);
+    w = -(g0 * (sv[3 * i] - sv[3 * j]) + g1 * (sv[3 * i + 1] - sv[3 * j + 1]) + g2 * (sv[3 * i + 2] - sv[3 * j + 2]));
+    W[a * D + p] = w;
+  }
+  double part = xc * w;
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) redt[warp] = part;
+  const float2 xs = split_d(w);
+  const int ex = chunk_exponent(fabsf(xs.x), red);  // contains a __syncthreads (redt visible)
+  if (p == 0) {
+    double s = redt[0];
+    for (int k = 1; k < 8; ++k) s += redt[k];
+    t[a] = s;
+    t2[a] = split_d(s);
+    e[a] = ex;  // chunk 0 of row a
+  }
+  slice_write(xs, ex, sl, a, p, Rp, Kp);
+}
+
 // XT (cols x rows) = X^T, X rows x cols with row stride ldx (32 x 32 tiles)
 __global__ void oz_transpose_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                                     double* __restrict__ XT) {
@@ -205,18 +265,6 @@ __device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// x * 2^e, exact unless the result leaves the FP32 range
-__device__ __forceinline__ float scale2(float x, int e) {
-  while (e > 127) {
-    x *= pow2f(127);
-    e -= 127;
-  }
-  while (e < -126) {
-    x *= pow2f(-126);
-    e += 126;
-  }
-  return x * pow2f(e);
-}
 
 // grid (ceil(N/64), ceil(M/128), K-chunks).  CTA z accumulates the 2 k-blocks (of
 // 128 K entries, two 128-byte swizzle spans per tile) of chunk z.  Warp 0 loads the 7
@@ -663,53 +711,135 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------ nonlinear step and back-projection
-// beta_ab = c^2 S_ab (T_ab - t_b) for the 256 b of chunk q of row a, in double-float;
-// written as GEMM 2's sliced A operand, plus the chunk's row sum.
+// beta_ab = c^2 S_ab (T_ab - t_b) in double-float (T from its chunk partials), sliced
+// row-wise into the A operand of segment 2, with the row sums of each 256-column chunk.
+// One CTA (256 threads) per row a and 1024-column block: thread u takes columns 4u .. 4u + 3
+// (16- and 32-byte loads, one 8-byte store of four BF16 per slice); the 64 threads of a
+// chunk share its exponent and reduce its row sum in a fixed order.
 __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__ Tp, int nsplit, int64_t M,
                                                       const float2* __restrict__ S2, const float2* __restrict__ t2,
                                                       int64_t Rp, int64_t Kp, bf16* __restrict__ sl,
                                                       int* __restrict__ e, float2* __restrict__ rs2) {
-  __shared__ float red[8];
+  __shared__ float redm[8];
   __shared__ float2 redp[8];
-  const int64_t a = blockIdx.x, q = blockIdx.y;
-  const int64_t b = q * oz::KC + threadIdx.x;
-  float bh = 0.f, bl = 0.f;
-  if (b < M) {
-    float th = 0.f, tl = 0.f;
-    for (int s = 0; s < nsplit; ++s) {
-      const float2 p = Tp[((int64_t)s * M + a) * M + b];
-      df_add(th, tl, p.x, p.y);
+  const int64_t a = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t b0 = (int64_t)blockIdx.y * 1024 + 4 * threadIdx.x; b0 - 4 * threadIdx.x < Kp; b0 += 1024 * gridDim.y) {
+    float bh[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
+    if ((M & 3) == 0 && b0 + 3 < M) {  // 16-byte aligned rows; otherwise the scalar path below
+      float th[4] = {0.f, 0.f, 0.f, 0.f}, tl[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int s = 0; s < nsplit; ++s) {
+        const float4* pp = reinterpret_cast<const float4*>(Tp + ((int64_t)s * M + a) * M + b0);
+        const float4 p0 = pp[0], p1 = pp[1];
+        df_add(th[0], tl[0], p0.x, p0.y);
+        df_add(th[1], tl[1], p0.z, p0.w);
+        df_add(th[2], tl[2], p1.x, p1.y);
+        df_add(th[3], tl[3], p1.z, p1.w);
+      }
+      const float4* tp = reinterpret_cast<const float4*>(t2 + b0);
+      const float4* sp = reinterpret_cast<const float4*>(S2 + a * M + b0);
+      const float4 t0 = tp[0], t1 = tp[1], s0 = sp[0], s1 = sp[1];
+      const float tbh[4] = {t0.x, t0.z, t1.x, t1.z}, tbl[4] = {t0.y, t0.w, t1.y, t1.w};
+      const float sh[4] = {s0.x, s0.z, s1.x, s1.z}, slo[4] = {s0.y, s0.w, s1.y, s1.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        df_add(th[q], tl[q], -tbh[q], -tbl[q]);
+        df_mul(sh[q], slo[q], th[q], tl[q], bh[q], bl[q]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t b = b0 + q;
+        if (b < M) {
+          float th = 0.f, tl = 0.f;
+          for (int s = 0; s < nsplit; ++s) {
+            const float2 p = Tp[((int64_t)s * M + a) * M + b];
+            df_add(th, tl, p.x, p.y);
+          }
+          const float2 tb = t2[b];
+          df_add(th, tl, -tb.x, -tb.y);
+          const float2 sab = S2[a * M + b];
+          df_mul(sab.x, sab.y, th, tl, bh[q], bl[q]);
+        }
+      }
     }
-    const float2 tb = t2[b];
-    df_add(th, tl, -tb.x, -tb.y);
-    const float2 sab = S2[a * M + b];
-    df_mul(sab.x, sab.y, th, tl, bh, bl);
+    // chunk of these columns: threads 64 c .. 64 c + 63 (warps 2c, 2c + 1)
+    float mx = fmaxf(fmaxf(fabsf(bh[0]), fabsf(bh[1])), fmaxf(fabsf(bh[2]), fabsf(bh[3])));
+    float rh = bh[0], rl = bl[0];
+    df_add(rh, rl, bh[1], bl[1]);
+    df_add(rh, rl, bh[2], bl[2]);
+    df_add(rh, rl, bh[3], bl[3]);
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const float oh = __shfl_xor_sync(0xffffffffu, rh, o), ol = __shfl_xor_sync(0xffffffffu, rl, o);
+      df_add(rh, rl, oh, ol);
+    }
+    if (lane == 0) {
+      redm[warp] = mx;
+      redp[warp] = make_float2(rh, rl);
+    }
+    __syncthreads();
+    const int c = warp >> 1;
+    const float m = fmaxf(redm[2 * c], redm[2 * c + 1]);
+    int ex = 0;
+    if (m > 0.f) {
+      const int bits = __float_as_int(m);
+      ex = (bits >> 23) != 0 ? (bits >> 23) - 126 : 0;  // m = f 2^ex, f in [0.5, 1), for normal m
+      if ((bits >> 23) == 0) (void)frexpf(m, &ex);
+    }
+    const int64_t q = (b0 - 4 * (threadIdx.x & 63)) / oz::KC;  // this chunk
+    if ((threadIdx.x & 63) == 0 && q * oz::KC < M) {
+      float h = redp[2 * c].x, l = redp[2 * c].y;
+      df_add(h, l, redp[2 * c + 1].x, redp[2 * c + 1].y);
+      rs2[q * M + a] = make_float2(h, l);
+      e[q * M + a] = ex;
+    }
+    // 7 slices of the four entries, one 8-byte store each
+    if (b0 < Kp) {
+      float yh[4], yl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        yh[u] = scale2(bh[u], oz::BITS - ex);
+        yl[u] = scale2(bl[u], oz::BITS - ex);
+      }
+      const float up = (float)(1 << oz::BITS);
+      bf16* dst = sl + a * Kp + b0;
+      const int64_t stride = Rp * Kp;
+#pragma unroll
+      for (int i = 0; i < oz::S; ++i) {
+        float sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sv[u] = rintf(yh[u]);
+          float h, l;
+          two_sum(__fsub_rn(yh[u], sv[u]), yl[u], h, l);
+          yh[u] = __fmul_rn(h, up);
+          yl[u] = __fmul_rn(l, up);
+        }
+        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(sv[0], sv[1]), hi2 = __floats2bfloat162_rn(sv[2], sv[3]);
+        uint2 pk;
+        pk.x = *reinterpret_cast<const uint32_t*>(&lo2);
+        pk.y = *reinterpret_cast<const uint32_t*>(&hi2);
+        *reinterpret_cast<uint2*>(dst + i * stride) = pk;
+      }
+    }
+    __syncthreads();  // redm / redp reused by the next block of columns
   }
-  // row sum of the chunk (fixed reduction order)
-  float sh = bh, sl_ = bl;
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl_, o);
-    df_add(sh, sl_, oh, ol);
-  }
-  if ((threadIdx.x & 31) == 0) redp[threadIdx.x >> 5] = make_float2(sh, sl_);
-  const int ex = chunk_exponent(fabsf(bh), red);  // contains a __syncthreads
-  if (threadIdx.x == 0) {
-    float h = redp[0].x, l = redp[0].y;
-    for (int w = 1; w < 8; ++w) df_add(h, l, redp[w].x, redp[w].y);
-    rs2[q * M + a] = make_float2(h, l);
-    e[q * M + a] = ex;
-  }
-  slice_write(make_float2(bh, bl), ex, sl, a, b, Rp, Kp);
 }
 
 // (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a); U_a and rowsum_a summed from
-// their double-float partials, the rest in FP64.  One CTA per geometry.
-__global__ void __launch_bounds__(128) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
+// their double-float partials, the rest in FP64.  One CTA per geometry: thread p forms the
+// descriptor's term w_p = g_p u_p (its three coordinate derivatives times u_p; coalesced
+// loads of G), then thread (i, c) sums the N - 1 pair terms of atom i from shared memory
+// (the derivative of x_p with respect to its first atom i > j carries the minus sign).
+__global__ void __launch_bounds__(256) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
                                                           const float2* __restrict__ rs2, int nrs,
                                                           const double* __restrict__ Xc, const double* __restrict__ G,
                                                           const double* __restrict__ v, int N, double lam,
                                                           int add_lambda, double* __restrict__ out) {
-  extern __shared__ double sh_u[];
+  extern __shared__ double w3[];  // [D][3] terms, then U_a [D] and xc_a [D]
+  double* ua = w3 + 3 * D;
+  double* xa = ua + D;
   __shared__ double rs;
   const int64_t a = blockIdx.x;
   if (threadIdx.x < 32) {
@@ -724,27 +854,38 @@ __global__ void __launch_bounds__(128) oz_backproj_kernel(const float2* __restri
     }
     if (threadIdx.x == 0) rs = (double)h + (double)l;
   }
-  __syncthreads();
+  // every load of the geometry in one round: U partials, g_p, xc_p
+  const double* Ga = G + a * D * 3;
   for (int p = threadIdx.x; p < D; p += blockDim.x) {
     float h = 0.f, l = 0.f;
     for (int s = 0; s < nsplit; ++s) {
       const float2 u = Up[((int64_t)s * M + a) * D + p];
       df_add(h, l, u.x, u.y);
     }
-    sh_u[p] = ((double)h + (double)l) - rs * Xc[a * D + p];
+    ua[p] = (double)h + (double)l;
+    xa[p] = Xc[a * D + p];
+    w3[3 * p] = Ga[3 * p];
+    w3[3 * p + 1] = Ga[3 * p + 1];
+    w3[3 * p + 2] = Ga[3 * p + 2];
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < D; p += blockDim.x) {
+    const double u = ua[p] - rs * xa[p];
+    w3[3 * p] *= u;
+    w3[3 * p + 1] *= u;
+    w3[3 * p + 2] *= u;
   }
   __syncthreads();
   const int B = 3 * N;
-  const double* Ga = G + a * D * 3;
   for (int l = threadIdx.x; l < B; l += blockDim.x) {
     const int i = l / 3, qd = l - 3 * i;
     double s = 0.0;
 #pragma unroll 4
-    for (int j = 0; j < N; ++j) {  // branch-free: independent loads of successive j
+    for (int j = 0; j < N; ++j) {
       const bool skip = j == i;
       const int p = skip ? 0 : (i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i);
-      const double gj = Ga[3 * p + qd] * sh_u[p];
-      s += skip ? 0.0 : ((i > j) ? -gj : gj);  // d x_p / d R_i = -g_p when i is the first atom of pair p
+      const double wj = w3[3 * p + qd];
+      s += skip ? 0.0 : ((i > j) ? -wj : wj);
     }
     if (add_lambda) s = fma(lam, v[a * B + l], s);
     out[a * B + l] = s;
@@ -868,22 +1009,26 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
   if (!oz.ready) return fail(GDML_ERR_STATE, "sliced matvec not set up");
   const int64_t M = oz.M;
   const int D = oz.D;
-  launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
-  slice_rows(oz.W, D, oz.W1, st, oz.t, oz.t2);
+  if (oz.W1.Kp <= oz::KC) {  // one chunk per row: projection and slicing in one kernel
+    { oz_proj_slice_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(double), st>>>(G, Xc, v, M, oz.N, D, oz.W, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
+  } else {
+    launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
+    slice_rows(oz.W, D, oz.W1, st, oz.t, oz.t2);
+  }
   transpose(oz.W, M, D, D, oz.WT, st);
   slice_rows(oz.WT, M, oz.WT2, st);
   OZ_TRY(oz_gemm(oz.Xc1, oz.W1, oz.Tp, M, M * M, oz.err, st));
   {
-    dim3 g((unsigned)M, (unsigned)oz.B2.nchunks);
+    dim3 g((unsigned)M, (unsigned)cdiv(oz.B2.Kp, 1024));
     { oz_beta_kernel<<<g, 256, 0, st>>>(oz.Tp, (int)oz.W1.nchunks, M, oz.S2, oz.t2, oz.B2.Rp, oz.B2.Kp, (bf16*)oz.B2.slices, oz.B2.e, oz.rs2); count_launch(); }
   }
   const int64_t nch = oz.A2.nchunks;
   OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st));
   OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + nch * M * D, D, M * D, oz.err, st));
-  const size_t smem = (size_t)D * sizeof(double);
+  const size_t smem = 5 * (size_t)D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { oz_backproj_kernel<<<(unsigned)M, 128, smem, st>>>(oz.Up, (int)(2 * nch), M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
+  { oz_backproj_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, (int)(2 * nch), M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced matvec kernels");
   return GDML_OK;
 }
@@ -907,8 +1052,9 @@ void oz_destroy(OzMatvec& oz) {
   oz.ready = false;
 }
 
-gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64_t ldc, cudaStream_t st) {
-  if (n <= 0 || k <= 0) return fail(GDML_ERR_ARG, "oz_syrk_lower: empty sizes");
+// C (lower triangle) = X X^T for the k rows of X, each of K entries, sliced by `slice`
+template <typename SliceFn>
+static gdml_status syrk_sliced(int64_t k, int64_t K, double* C, int64_t ldc, const SliceFn& slice, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(oz_gemm_acc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal) !=
@@ -918,16 +1064,15 @@ gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64
   }
   OzMatvec t;
   OzOperand a;
-  // the k columns of L (stride n) are the rows of L^T: one operand serves as A and B
-  gdml_status s = make_operand(t, a, k, n, oz::BM, st);
+  // one operand serves as A and B (a second map with the B box height)
+  gdml_status s = make_operand(t, a, k, K, oz::BM, st);
   CUtensorMap mapB;
   if (s == GDML_OK && !make_kmajor_map(&mapB, a.slices, true, (uint64_t)a.Kp, (uint64_t)(oz::S * a.Rp),
                                        (uint64_t)a.Kp, (uint32_t)oz::BN))
     s = fail(GDML_ERR_CUDA, "cuTensorMapEncodeTiled failed (sliced syrk)");
   if (s == GDML_OK) s = oz_alloc(t, &t.err, 1, st);
   if (s == GDML_OK) {
-    dim3 g((unsigned)k, (unsigned)a.nchunks);
-    { oz_slice_rows_f32_kernel<<<g, 256, 0, st>>>(L, n, n, k, a.Rp, a.Kp, (bf16*)a.slices, a.e); count_launch(); }
+    slice(a);
     dim3 grid((unsigned)cdiv(k, oz::BN), (unsigned)cdiv(k, oz::BM));
     { oz_gemm_acc_kernel<<<grid, kThreads, kSmemTotal, st>>>(a.map, mapB, (int)a.Rp, (int)a.Rp, (int)k, (int)k, (int)(a.Kp / oz::KB), a.e, a.e, C, ldc, 1, t.err); count_launch(); }
     cudaError_t e = cudaGetLastError();
@@ -944,6 +1089,24 @@ gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64
   cudaStreamSynchronize(st);
   oz_destroy(t);
   return s;
+}
+
+gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64_t ldc, cudaStream_t st) {
+  if (n <= 0 || k <= 0) return fail(GDML_ERR_ARG, "oz_syrk_lower: empty sizes");
+  // the k columns of L (stride n) are the rows of L^T
+  return syrk_sliced(k, n, C, ldc, [&](OzOperand& a) {
+    dim3 g((unsigned)k, (unsigned)a.nchunks);
+    { oz_slice_rows_f32_kernel<<<g, 256, 0, st>>>(L, n, n, k, a.Rp, a.Kp, (bf16*)a.slices, a.e); count_launch(); }
+  }, st);
+}
+
+gdml_status oz_syrk_lower_f64(const double* X, int64_t rows, int64_t K, int64_t ldx, double* C, int64_t ldc,
+                              cudaStream_t st) {
+  if (rows <= 0 || K <= 0) return fail(GDML_ERR_ARG, "oz_syrk_lower_f64: empty sizes");
+  return syrk_sliced(rows, K, C, ldc, [&](OzOperand& a) {
+    dim3 g((unsigned)rows, (unsigned)a.nchunks);
+    { oz_slice_rows_kernel<<<g, 256, 0, st>>>(X, ldx, K, rows, a.Rp, a.Kp, (bf16*)a.slices, a.e, nullptr, nullptr); count_launch(); }
+  }, st);
 }
 
 gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,

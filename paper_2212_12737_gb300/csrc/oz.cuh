@@ -83,6 +83,10 @@ void oz_destroy(OzMatvec& oz);
 // (column j at L + j n), through the sliced tensor-core GEMM with in-CTA accumulation
 // over all 256-entry chunks of n.  Synchronises the stream.
 gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64_t ldc, cudaStream_t st);
+// lower triangle of C = X X^T (rows x rows, FP64, row stride ldc) for FP64 X (rows x K, row
+// stride ldx), through the same sliced GEMM.  Synchronises the stream.
+gdml_status oz_syrk_lower_f64(const double* X, int64_t rows, int64_t K, int64_t ldx, double* C, int64_t ldc,
+                              cudaStream_t st);
 
 // test hook: C (M x N, FP64) = A (M x K) B (N x K)^T through the sliced tensor-core GEMM
 gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,

@@ -360,8 +360,21 @@ __global__ void __launch_bounds__(kArgThreads) pc_finish_select_df_kernel(
   }
   __syncthreads();
   const int64_t p = s_piv;
-  if (p >= 0)  // the next pivot's row of L, columns 0..m (column m written above, fenced)
-    for (int64_t j = threadIdx.x; j <= m; j += kArgThreads) prow[j] = L[p + j * n];
+  if (p >= 0)  // the next pivot's row of L, columns 0..m (column m written above, fenced);
+                // eight independent loads per thread in flight before the stores
+    for (int64_t j0 = threadIdx.x; j0 <= m; j0 += 8 * kArgThreads) {
+      float pv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = j0 + (int64_t)u * kArgThreads;
+        pv[u] = j <= m ? L[p + j * n] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = j0 + (int64_t)u * kArgThreads;
+        if (j <= m) prow[j] = pv[u];
+      }
+    }
 }
 
 int pivchol_schur_groups() { return kSchurMaxGroups; }

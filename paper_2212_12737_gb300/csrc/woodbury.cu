@@ -958,9 +958,67 @@ __global__ void __launch_bounds__(256) symv_df_kernel(const float2* __restrict__
   y2[i] = make_float2(vh, (float)(v - (double)vh));
 }
 
+// The same products with one warp per row and x staged once per CTA in shared memory (k
+// even, k <= kSymvRowsMaxK): 8 rows per CTA, each lane streams 16-byte pieces of its row
+// (eight in flight; the k x k matrices stay in L2 between applies) against x from shared
+// memory, then a fixed shuffle tree.
+constexpr int kSymvRowsMaxK = 4096;
+__global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restrict__ A, int64_t k,
+                                                           const float2* __restrict__ x, int mode,
+                                                           const double* __restrict__ t, double* __restrict__ y,
+                                                           float2* __restrict__ y2) {
+  __shared__ __align__(16) float2 xs[kSymvRowsMaxK];
+  for (int64_t j = threadIdx.x; j < k; j += 256) xs[j] = x[j];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= k) return;
+  const float4* row = reinterpret_cast<const float4*>(A + i * k);  // k even: 16-byte aligned rows
+  const float4* xv4 = reinterpret_cast<const float4*>(xs);
+  const int64_t nq = k / 2;  // float4 pieces per row (two entries each)
+  float h = 0.f, l = 0.f;
+  int64_t q = lane;
+  for (; q + 224 < nq; q += 256) {  // eight 16-byte loads in flight per lane
+    float4 av[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) av[u] = __ldg(row + q + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float4 xq = xv4[q + 32 * u];
+      df_term(h, l, av[u].x, av[u].y, xq.x, xq.y);
+      df_term(h, l, av[u].z, av[u].w, xq.z, xq.w);
+    }
+  }
+  for (; q < nq; q += 32) {
+    const float4 a = __ldg(row + q), xq = xv4[q];
+    df_term(h, l, a.x, a.y, xq.x, xq.y);
+    df_term(h, l, a.z, a.w, xq.z, xq.w);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add_pair(h, l, oh, ol);
+  }
+  if (lane != 0) return;
+  const double s = (double)h + (double)l;
+  double v;
+  if (mode == 0) {
+    v = s;
+    y[i] = v;
+  } else if (mode == 1) {
+    v = t[i] - s;
+  } else {
+    v = y[i] + s;
+    y[i] = v;
+  }
+  const float vh = (float)v;
+  y2[i] = make_float2(vh, (float)(v - (double)vh));
+}
+
 static void symv_df(const float2* A, int64_t k, const float2* x, int mode, const double* t, double* y, float2* y2,
                     cudaStream_t st) {
-  if ((k & 1) == 0)
+  if ((k & 1) == 0 && k <= kSymvRowsMaxK)
+    { symv_df_rows_kernel<<<(unsigned)cdiv(k, 8), 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
+  else if ((k & 1) == 0)
     { symv_df_kernel<true><<<(unsigned)k, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
   else
     { symv_df_kernel<false><<<(unsigned)k, 256, 0, st>>>(A, k, x, mode, t, y, y2); count_launch(); }
