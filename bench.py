@@ -44,7 +44,7 @@ def parse():
                          "BF16 slices on the tensor cores; both FP64-class, FP64 true-residual restarts)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison solves")
-    ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply", "passes"],
+    ap.add_argument("--only", default="solve", choices=["solve", "matvec", "apply", "passes", "build"],
                     help="time one operation alone (small runs for profiling); passes: the two staged "
                          "passes of the DF64/OZAKI apply on a random FP32 factor of the workload's n x k")
     ap.add_argument("--rows", type=int, default=1, choices=[1, 128, 256],
@@ -147,6 +147,19 @@ def run_op(args):
                           "kernel durations"}), flush=True)
         return
     ctx = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam, precision=args.precision)
+    if args.only == "build":  # preconditioner builds (Algorithm 1 / Nystrom + Woodbury core), host-timed
+        ts = []
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ctx.precond_build(w.select, w.k, seed=2)
+            torch.cuda.synchronize(dev)
+            if it >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+        print(json.dumps({"op": "build", "workload": args.workload, "precision": args.precision,
+                          "select": w.select, "k": w.k, "s": min(ts) if ts else None}), flush=True)
+        ctx.destroy()
+        return
     v = torch.randn(w.n, dtype=torch.float64, device=dev)
     out = torch.empty_like(v)
     if args.only == "apply":

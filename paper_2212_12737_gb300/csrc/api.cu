@@ -58,6 +58,8 @@ struct gdml_ctx {
   int splitsU = 1;
   int splits_cap = 1;
   double* diag = nullptr;  // n
+  float2* X2 = nullptr;    // M*D: X as float pairs (DF64/OZAKI kernel columns)
+  float2* G2 = nullptr;    // M*D*3: G as float pairs
   double* Xc() const { return V64 + M * D; }
   TcMatvec tc;  // tensor-core matvec state (TF32/BF16 contexts)
   OzMatvec oz;  // sliced-BF16 tensor-core matvec state (OZAKI contexts)
@@ -604,6 +606,12 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   launch_center(c->X, M, (int)D, c->Xc(), c->st);
   launch_dist_tab(c->X, M, (int)D, c->c, c->S, c->P64, 2 * M, c->st);
   launch_kdiag(c->G, M, N, (int)D, c->c, c->diag, c->st);
+  if (df_precond(c.get())) {
+    TRY(dalloc(C, &c->X2, (size_t)(M * D)));
+    TRY(dalloc(C, &c->G2, (size_t)(M * D * 3)));
+    launch_split_df(c->X, M * D, c->X2, c->st);
+    launch_split_df(c->G, M * D * 3, c->G2, c->st);
+  }
   TRY(check_launch(C, "setup kernels"));
   if (precision == GDML_TF32 || precision == GDML_BF16) {
     gdml_status s = tc_setup(c->tc, precision, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->G, c->c, c->st);
@@ -691,7 +699,9 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     a.ticket = ticket;
     a.col = col;
     a.get_col = [c](const int64_t* cols, double* out, const int* stop, cudaStream_t st) {
-      launch_kcol(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, stop, st);
+      if (!c->X2 || !launch_kcol_df(cols, 1, c->X2, c->G2, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out,
+                                    c->n, stop, st))
+        launch_kcol(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, stop, st);
     };
     if (df_precond(c)) {
       TRY(s.get(&a.schur, (size_t)(pivchol_schur_groups() * n)));

@@ -366,6 +366,152 @@ __global__ void __launch_bounds__(256) kcol_warp_kernel(const int64_t* __restric
   }
 }
 
+// ---- double-float helpers for the kernel column (pairs (hi, lo) of FP32 on the FP32 lanes)
+__device__ __forceinline__ float2 dfk_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ float2 dfk_add(float2 a, float2 b) {  // a + b
+  const float s = __fadd_rn(a.x, b.x);
+  const float v = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 dfk_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 dfk_mul(float2 a, float2 b) {  // a b
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// Kernel columns in double-float on the FP32 lanes (DF64/OZAKI contexts): the algebra of
+// kcol_warp_kernel with x and g read as float pairs (split once per context) and c^2 S_ab,
+// A_ab split on the fly.  GB300's FP64 pipe is a small fraction of its FP32 lanes and the
+// FP64 form of this kernel was bound by it; the column is accurate to ~1e-14 of its terms,
+// the class of the double-float Schur sums it meets in Algorithm 1.  S and A are symmetric:
+// column b is read as row b.  One warp per geometry a, W warps per CTA.
+__global__ void __launch_bounds__(256) kcol_df_kernel(const int64_t* __restrict__ cols,
+                                                      const float2* __restrict__ X2, const float2* __restrict__ G2,
+                                                      const double* __restrict__ S, const double* __restrict__ A,
+                                                      int64_t ldA, int64_t M, int N, int D, double c2,
+                                                      double* __restrict__ out, int64_t ldo,
+                                                      const int* __restrict__ stop_flag) {
+  if (stop_flag && *stop_flag) return;
+  extern __shared__ float2 shf[];
+  const int W = blockDim.x >> 5;
+  float2* wsp = shf;        // N: +-g_b on the pairs (i, j), indexed by partner j
+  float2* sxb = shf + N;    // D: x_b
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* sxa = shf + N + D + (size_t)warp * 5 * D;  // D: x_a - x_b
+  float2* u = sxa + D;                                 // D
+  float2* sga = u + D;                                 // 3 D: g_a
+  const int64_t c = blockIdx.y;
+  const int64_t col = cols[c];
+  const int B = 3 * N;
+  const int64_t b = col / B;
+  const int l = (int)(col - b * B), i = l / 3, q = l - 3 * i;
+  const float2* Xb = X2 + b * D;
+  const float2* Gb = G2 + b * D * 3;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float2 w = make_float2(0.f, 0.f);
+    if (j != i) {
+      const float2 g = Gb[3 * pair_idx(i, j) + q];
+      w = (i > j) ? dfk_neg(g) : g;
+    }
+    wsp[j] = w;
+  }
+  for (int p = threadIdx.x; p < D; p += blockDim.x) sxb[p] = Xb[p];
+  const int64_t a = (int64_t)blockIdx.x * W + warp;
+  const bool live = a < M;
+  float2 sab = make_float2(0.f, 0.f), aab = sab;
+  if (live) {  // eight independent loads in flight per lane, then the shared-memory stores
+    const float2* Xa = X2 + a * D;
+    const float2* Ga = G2 + a * D * 3;
+    for (int e0 = lane; e0 < 4 * D; e0 += 32 * 8) {
+      float2 tmp[8];
+#pragma unroll
+      for (int u8 = 0; u8 < 8; ++u8) {
+        const int e = e0 + 32 * u8;
+        tmp[u8] = e < D ? Xa[e] : (e < 4 * D ? Ga[e - D] : make_float2(0.f, 0.f));
+      }
+#pragma unroll
+      for (int u8 = 0; u8 < 8; ++u8) {
+        const int e = e0 + 32 * u8;
+        if (e < D)
+          sxa[e] = tmp[u8];
+        else if (e < 4 * D)
+          sga[e - D] = tmp[u8];
+      }
+    }
+    if (lane == 0) {
+      sab = dfk_mul(dfk_split(c2), dfk_split(S[b * M + a]));
+      aab = dfk_split(A[b * ldA + a]);
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  sab = make_float2(__shfl_sync(0xffffffffu, sab.x, 0), __shfl_sync(0xffffffffu, sab.y, 0));
+  aab = make_float2(__shfl_sync(0xffffffffu, aab.x, 0), __shfl_sync(0xffffffffu, aab.y, 0));
+  for (int p = lane; p < D; p += 32) sxa[p] = dfk_add(sxa[p], dfk_neg(sxb[p]));  // x_a - x_b
+  __syncwarp();
+  float2 sd = make_float2(0.f, 0.f);
+  for (int j = lane; j < N; j += 32)
+    if (j != i) sd = dfk_add(sd, dfk_mul(sxa[pair_idx(i, j)], wsp[j]));
+  for (int o = 16; o > 0; o >>= 1)
+    sd = dfk_add(sd, make_float2(__shfl_xor_sync(0xffffffffu, sd.x, o), __shfl_xor_sync(0xffffffffu, sd.y, o)));
+  const float2 coef = dfk_neg(dfk_mul(sab, sd));
+  for (int p = lane; p < D; p += 32) u[p] = dfk_mul(coef, sxa[p]);
+  __syncwarp();
+  for (int j = lane; j < N; j += 32)
+    if (j != i) {
+      const int p = pair_idx(i, j);
+      u[p] = dfk_add(u[p], dfk_mul(aab, wsp[j]));
+    }
+  __syncwarp();
+  for (int l2 = lane; l2 < B; l2 += 32) {
+    const int i2 = l2 / 3, q2 = l2 - 3 * i2;
+    float2 s2 = make_float2(0.f, 0.f);
+    for (int j = 0; j < N; ++j) {
+      if (j == i2) continue;
+      const int p = pair_idx(i2, j);
+      const float2 gj = dfk_mul(sga[3 * p + q2], u[p]);
+      s2 = dfk_add(s2, (i2 > j) ? dfk_neg(gj) : gj);
+    }
+    out[c * ldo + a * B + l2] = (double)s2.x + (double)s2.y;
+  }
+}
+
+bool launch_kcol_df(const int64_t* cols, int64_t ncols, const float2* X2, const float2* G2, const double* S,
+                    const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
+                    const int* stop_flag, cudaStream_t st) {
+  const size_t per_warp = 5 * (size_t)D * sizeof(float2), fixed = ((size_t)N + D) * sizeof(float2);
+  int W = (int)std::min<size_t>(8, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / per_warp);
+  if (W < 1 || ncols > 65535) return false;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  const int64_t want = std::max<int64_t>(1, M * ncols / (2 * (int64_t)sms));
+  if (want < W) W = (int)want;
+  const size_t wsmem = fixed + W * per_warp;
+  static size_t attr = 0;
+  if (wsmem > 48 * 1024 && wsmem > attr) {
+    cudaFuncSetAttribute(kcol_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+    attr = wsmem;
+  }
+  dim3 g((unsigned)cdiv(M, W), (unsigned)ncols);
+  { kcol_df_kernel<<<g, 32 * W, wsmem, st>>>(cols, X2, G2, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag); count_launch(); }
+  return true;
+}
+
 // ---------------------------------------------------------------- launchers
 void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double* G, cudaStream_t st) {
   int64_t tot = M * D;

@@ -19,6 +19,14 @@ void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double
 void launch_center(const double* X, int64_t M, int D, double* Xc, cudaStream_t st);
 void launch_dist_tab(const double* X, int64_t M, int D, double c, double* S, double* A, int64_t ldA,
                      cudaStream_t st);
+// kernel columns in double-float (DF64/OZAKI contexts): X2, G2 the float-pair copies of X, G;
+// false (nothing launched) when the per-warp staging of 5 D float pairs does not fit in 200 KB
+// or ncols > 65535
+bool launch_kcol_df(const int64_t* cols, int64_t ncols, const float2* X2, const float2* G2, const double* S,
+                    const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
+                    const int* stop_flag, cudaStream_t st);
+// each double of x as the float pair (hi, lo)
+void launch_split_df(const double* x, int64_t count, float2* out, cudaStream_t st);
 void launch_kdiag(const double* G, int64_t M, int N, int D, double c, double* diag, cudaStream_t st);
 void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, int N, int D, double* W,
                  int64_t ldW, double* t, cudaStream_t st);
@@ -117,7 +125,8 @@ void launch_destandardize(const float* out, int64_t B, float ym, float ysd, doub
 
 // pivchol.cu
 struct PivState {
-  double lmm;
+  double lmm;   // l_{pivot, m} = sqrt(d_pivot)
+  double ilmm;  // 1 / lmm
   int64_t piv;
   int64_t rank;
   int stop;

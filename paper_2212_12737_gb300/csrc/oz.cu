@@ -266,14 +266,28 @@ __device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
 }
 
 
+// Named barrier 2 between the MMA warp and the waiter warp (64 threads), with the OR of
+// the participants' flags: the MMA warp learns of a failed wait without reading shared memory.
+__device__ __forceinline__ bool handoff(bool failed) {
+  uint32_t any;
+  asm volatile(
+      "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.or.pred pout, 2, 64, pin;\n"
+      " selp.u32 %0, 1, 0, pout;\n}\n"
+      : "=r"(any)
+      : "r"(failed ? 1u : 0u)
+      : "memory");
+  return any != 0;
+}
+
 // grid (ceil(N/64), ceil(M/128), K-chunks).  CTA z accumulates the 2 k-blocks (of
 // 128 K entries, two 128-byte swizzle spans per tile) of chunk z.  Warp 0 loads the 7
 // A slices of each k-block one by one into a 3-deep ring, warp 2 loads the 7 B slices
-// of each k-block as one group; warp 1 multiplies A slice i with B slices j = 0..6-i
-// (8 MMAs per pair) into TMEM accumulator i + j.  Each mbarrier wait of the MMA
-// thread stalls the tensor pipe for a fixed ~2k cycles, so wide k-blocks halve that
-// cost per MMA.  Warps 3..10 (two per TMEM lane quarter, 32 columns each) combine the
-// 7 levels, scale by 2^(eA + eB) and store the chunk's double-float partial.
+// of each k-block as one group and waits on the TMA barriers; warp 1 multiplies A slice
+// i with B slices j = 0..6-i (8 MMAs per pair) into TMEM accumulator i + j, taking each
+// A tile from warp 2 at a named barrier (a wait or any shared-memory read in the
+// MMA-issuing thread stalls the tensor pipe; wide k-blocks halve the handoffs per MMA).
+// Warps 3..10 (two per TMEM lane quarter, 32 columns each) combine the 7 levels, scale
+// by 2^(eA + eB) and store the chunk's double-float partial.
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
                    int Bp, int M, int N, int num_kb, const int* __restrict__ eA, const int* __restrict__ eB,
@@ -343,76 +357,100 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
     }
-  } else if (warp == 2 && lane == 0) {
-    // ---------------- TMA producer, B slice groups
+  } else if (warp == 2) {
+    // ---------------- B producer (lane 0) and waiter (whole warp): the MMA warp never touches
+    // shared memory in its loop (any shared-memory access of the MMA-issuing thread stalls
+    // the tensor pipe, ~35 cycles per MMA here); this warp waits on the TMA mbarriers and
+    // hands each A tile over through named barrier 2, whose OR-reduction also carries a
+    // failed wait.  It arrives exactly nk * 7 times whatever happens.
+    bool failed = false;
     for (int kb = 0; kb < nk; ++kb) {
-      if (!mbar_wait_spin(bempty, ((uint32_t)kb & 1u) ^ 1u)) {
-        atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
-        *abort_flag = 1;
-        break;
+      int okw = 1;
+      if (lane == 0 && !failed) {
+        if (!mbar_wait_spin(bempty, ((uint32_t)kb & 1u) ^ 1u)) {
+          atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+          *abort_flag = 1;
+          okw = 0;
+        } else if (*abort_flag) {
+          okw = 0;
+        } else {
+          const int kx = (kb_begin + kb) * kKB2;
+          tc::mbar_expect_tx(bfull, kBGroup2);
+          for (int j = 0; j < oz::S; ++j) {
+            tc::tma_load_2d(sB + j * kBTile2, &mapB, bfull, kx, j * Bp + n0);
+            tc::tma_load_2d(sB + j * kBTile2 + kBTile, &mapB, bfull, kx + oz::KB, j * Bp + n0);
+          }
+          if (!mbar_wait_spin(bfull, (uint32_t)kb & 1u)) {
+            atomicExch(err, tc::ERR_TIMEOUT_FULL);
+            *abort_flag = 1;
+            okw = 0;
+          }
+        }
       }
-      if (*abort_flag) break;
-      const int kx = (kb_begin + kb) * kKB2;
-      tc::mbar_expect_tx(bfull, kBGroup2);
-      for (int j = 0; j < oz::S; ++j) {
-        tc::tma_load_2d(sB + j * kBTile2, &mapB, bfull, kx, j * Bp + n0);
-        tc::tma_load_2d(sB + j * kBTile2 + kBTile, &mapB, bfull, kx + oz::KB, j * Bp + n0);
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
-    const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
-    const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
-    bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      if (!mbar_wait_spin(bfull, (uint32_t)kb & 1u)) {
-        atomicExch(err, tc::ERR_TIMEOUT_FULL);
-        *abort_flag = 1;
-        break;
-      }
+      failed = failed || !__shfl_sync(0xffffffffu, okw, 0);
       for (int i = 0; i < oz::S; ++i) {
         const int ai = kb * oz::S + i;
         const int s = ai % kAStages2;
         const uint32_t ph = (uint32_t)(ai / kAStages2) & 1u;
-        if (!mbar_wait_spin(&afull[s], ph)) {
-          atomicExch(err, tc::ERR_TIMEOUT_FULL);
-          *abort_flag = 1;
-          ok = false;
-          break;
-        }
-        if (*abort_flag) {
-          ok = false;
-          break;
-        }
-        // (no tcgen05 fence here: the mbarrier's TMA completion already orders the tile for
-        // the tensor core, and a fence per tile costs ~35 cycles per MMA)
-        // descriptors are linear in the start address (bits 0..13 = address / 16): a K
-        // step of 32 bytes adds 2, the second 128-byte span of a tile adds span / 16, and
-        // B slice j adds j * kBTile2 / 16
-        const uint64_t ad = adesc0 + (uint64_t)(s * (kATile2 >> 4));
-        const uint32_t first = (kb > 0 || i > 0) ? 1u : 0u;
-#pragma unroll
-        for (int j = 0; j < oz::S; ++j) {
-          if (i + j < oz::S) {
-            const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
-            const uint64_t bj = bdesc0 + (uint64_t)(j * (kBTile2 >> 4));
-            constexpr uint64_t a1 = kATile >> 4, b1 = kBTile >> 4;
-            tc::mma_issue<true>(d, ad, bj, idesc, first);
-            tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
-            tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
-            tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
-            tc::mma_issue<true>(d, ad + a1, bj + b1, idesc, 1u);
-            tc::mma_issue<true>(d, ad + a1 + 2, bj + b1 + 2, idesc, 1u);
-            tc::mma_issue<true>(d, ad + a1 + 4, bj + b1 + 4, idesc, 1u);
-            tc::mma_issue<true>(d, ad + a1 + 6, bj + b1 + 6, idesc, 1u);
+        int oka = 1;
+        if (lane == 0 && !failed) {
+          if (!mbar_wait_spin(&afull[s], ph)) {
+            atomicExch(err, tc::ERR_TIMEOUT_FULL);
+            *abort_flag = 1;
+            oka = 0;
+          } else if (*abort_flag) {
+            oka = 0;
           }
         }
-        tc::mma_commit(&aempty[s]);
+        failed = failed || !__shfl_sync(0xffffffffu, oka, 0);
+        (void)handoff(failed);
       }
-      if (ok) tc::mma_commit(bempty);
     }
-    tc::mma_commit(done);
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (lane 0; the whole warp meets the waiter at barrier 2)
+    constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
+    const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
+    const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
+    bool failed = false;
+    for (int kb = 0; kb < nk; ++kb) {
+      for (int i = 0; i < oz::S; ++i) {
+        failed = handoff(false) || failed;
+        tc::fence_after_sync();
+        const int ai = kb * oz::S + i;
+        const int s = ai % kAStages2;
+        if (lane == 0) {
+          if (!failed) {
+            // descriptors are linear in the start address (bits 0..13 = address / 16): a K
+            // step of 32 bytes adds 2, the second 128-byte span of a tile adds span / 16, and
+            // B slice j adds j * kBTile2 / 16
+            const uint64_t ad = adesc0 + (uint64_t)(s * (kATile2 >> 4));
+            const uint32_t first = (kb > 0 || i > 0) ? 1u : 0u;
+#pragma unroll
+            for (int j = 0; j < oz::S; ++j) {
+              if (i + j < oz::S) {
+                const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
+                const uint64_t bj = bdesc0 + (uint64_t)(j * (kBTile2 >> 4));
+                constexpr uint64_t a1 = kATile >> 4, b1 = kBTile >> 4;
+                tc::mma_issue<true>(d, ad, bj, idesc, first);
+                tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
+                tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
+                tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+                tc::mma_issue<true>(d, ad + a1, bj + b1, idesc, 1u);
+                tc::mma_issue<true>(d, ad + a1 + 2, bj + b1 + 2, idesc, 1u);
+                tc::mma_issue<true>(d, ad + a1 + 4, bj + b1 + 4, idesc, 1u);
+                tc::mma_issue<true>(d, ad + a1 + 6, bj + b1 + 6, idesc, 1u);
+              }
+            }
+          }
+          tc::mma_commit(&aempty[s]);  // also after a failure: the A producer never starves
+        }
+        __syncwarp();
+      }
+      if (lane == 0) tc::mma_commit(bempty);
+      __syncwarp();
+    }
+    if (lane == 0) tc::mma_commit(done);
+    __syncwarp();
   } else if (warp >= 3) {
     // ---------------- epilogue: combine the levels, scale, store the chunk partial
     const int quarter = warp & 3;

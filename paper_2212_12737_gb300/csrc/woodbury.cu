@@ -169,6 +169,10 @@ __global__ void split_df_kernel(const double* __restrict__ r, int64_t n, float2*
   rs[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
+void launch_split_df(const double* x, int64_t count, float2* out, cudaStream_t st) {
+  { split_df_kernel<<<(unsigned)cdiv(count, 256), 256, 0, st>>>(x, count, out); count_launch(); }
+}
+
 // (h, l) += (bh, bl) in double-float
 __device__ __forceinline__ void df_add_pair(float& h, float& l, float bh, float bl) {
   const float s = h + bh;
