@@ -421,13 +421,11 @@ gdml_status pcg_body(gdml_ctx* c, double* x, bool fp64_mv, cudaGraphConditionalH
   const int64_t n = c->n;
   TRY(matvec_any(c, c->p, c->q, 1, fp64_mv));
   TRY(dot(c, c->p, c->q, SC_PQ));
-  launch_update_xr(x, c->r, c->p, c->q, n, c->sc, c->status, c->st);
-  TRY(dot(c, c->r, c->r, SC_RR));
-  launch_pcg_check(c->sc, c->ictl, c->status, h, c->st);
+  // x, r update fused with r.r and the loop's end test
+  launch_update_xr_rr(x, c->r, c->p, c->q, n, c->sc, c->status, c->partial, c->ticket, c->ictl, h, 1, c->st);
   TRY(apply_precond(c, c->r, c->z));
   TRY(dot(c, c->r, c->z, SC_RHO_NEW));
-  launch_update_p(c->p, c->z, n, c->sc, c->st);
-  launch_copy_scalar(c->sc, SC_RHO, SC_RHO_NEW, c->st);
+  launch_update_p_rho(c->p, c->z, n, c->sc, c->ticket, c->st);
   return check_launch(c, "pcg body");
 }
 

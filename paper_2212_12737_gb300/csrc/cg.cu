@@ -62,6 +62,80 @@ __global__ void update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
   }
 }
 
+// x += gamma p; r -= gamma q (gamma = sc[RHO] / sc[PQ]), fused with sc[RR] = r.r over the same
+// contiguous chunks and combination order as dot_kernel (bitwise the same r.r), and with the
+// end-of-iteration test of the graph-captured loop in the last CTA (pcg_check_kernel's logic).
+// A breakdown (pq not positive and finite) flags status and leaves x, r untouched.
+__global__ void __launch_bounds__(kDotThreads) update_xr_rr_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                                   const double* __restrict__ p,
+                                                                   const double* __restrict__ q, int64_t n,
+                                                                   double* __restrict__ sc, int* __restrict__ status,
+                                                                   double* __restrict__ partial,
+                                                                   unsigned* __restrict__ ticket, int64_t* ictl,
+                                                                   cudaGraphConditionalHandle h, int check) {
+  __shared__ double red[kDotThreads / 32];
+  __shared__ bool last;
+  const double pq = sc[SC_PQ];
+  const bool ok = pq > 0.0 && isfinite(pq);
+  const double gamma = ok ? sc[SC_RHO] / pq : 0.0;
+  const int64_t chunk = cdiv_dev(n, gridDim.x);
+  const int64_t beg = blockIdx.x * chunk;
+  const int64_t end = beg + chunk < n ? beg + chunk : n;
+  double s = 0.0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += kDotThreads) {
+    double ri = r[i];
+    if (ok) {
+      x[i] = fma(gamma, p[i], x[i]);
+      ri = fma(-gamma, q[i], ri);
+      r[i] = ri;
+    }
+    s = fma(ri, ri, s);
+  }
+  s = block_sum<kDotThreads>(s, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kDotThreads) tot += ((volatile double*)partial)[b];
+  tot = block_sum<kDotThreads>(tot, red);
+  if (threadIdx.x == 0) {
+    if (!ok) *status = 1;
+    sc[SC_RR] = tot;
+    *ticket = 0u;
+    if (check) {
+      const int64_t it = ictl[IC_ITER] + 1;
+      ictl[IC_ITER] = it;
+      const bool go = (tot > sc[SC_TOL2]) && isfinite(tot) && (it < ictl[IC_MAXIT]) && ok && (*status == 0);
+      cudaGraphSetConditional(h, go ? 1u : 0u);
+    }
+  }
+}
+
+// p = z + (rho_new / rho) p, then rho <- rho_new in the last CTA (after every CTA has read it)
+__global__ void __launch_bounds__(256) update_p_rho_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                                           int64_t n, double* __restrict__ sc,
+                                                           unsigned* __restrict__ ticket) {
+  __shared__ bool last;
+  const double beta = sc[SC_RHO_NEW] / sc[SC_RHO];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    sc[SC_RHO] = sc[SC_RHO_NEW];
+    *ticket = 0u;
+  }
+}
+
 // p = z + (rho_new / rho) p ; rho <- rho_new (done by one thread after use)
 __global__ void update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
                                 const double* __restrict__ sc) {
@@ -120,6 +194,14 @@ void launch_dot(const double* x, const double* y, int64_t n, double* partial, un
 void launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const double* sc,
                       int* status, cudaStream_t st) {
   { update_xr_kernel<<<4 * kNumSMs, 256, 0, st>>>(x, r, p, q, n, sc, status); count_launch(); }
+}
+void launch_update_xr_rr(double* x, double* r, const double* p, const double* q, int64_t n, double* sc, int* status,
+                         double* partial, unsigned* ticket, int64_t* ictl, cudaGraphConditionalHandle h, int check,
+                         cudaStream_t st) {
+  { update_xr_rr_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, p, q, n, sc, status, partial, ticket, ictl, h, check); count_launch(); }
+}
+void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, cudaStream_t st) {
+  { update_p_rho_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc, ticket); count_launch(); }
 }
 void launch_update_p(double* p, const double* z, int64_t n, const double* sc, cudaStream_t st) {
   { update_p_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc); count_launch(); }
