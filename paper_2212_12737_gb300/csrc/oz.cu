@@ -30,6 +30,8 @@ constexpr int kSmemData = 2 * kBGroup + kAStages * kATile;
 constexpr int kSmemTotal = kSmemData + 1024 + 256;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kKbPerChunk = oz::KC / oz::KB;
+constexpr int kWaiterWarp = 11;           // the accumulating GEMM's extra warp: mbarrier waits
+constexpr int kThreadsAcc = 32 * 12;
 constexpr int kStageLd = oz::BN + 1;  // padded row of the staged output tile (float2)
 // matvec GEMM: k-blocks of 128 (two 128-byte swizzle spans per tile), so each mbarrier
 // wait of the MMA thread covers 8 MMAs per slice pair; one B group, 3-deep A ring
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // double-float sum held in registers, and release the TMEM on tfree before the MMA
 // warp starts the next chunk (whose first MMA per level overwrites).  lower_only:
 // tiles wholly above the diagonal exit at once (symmetric products).
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsAcc, 1)
     oz_gemm_acc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
                        int Bp, int M, int N, int num_kb, const int* __restrict__ eA, const int* __restrict__ eB,
                        double* __restrict__ C, int64_t ldc, int lower_only, int* __restrict__ err) {
@@ -618,63 +620,86 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < oz::S; ++j)
         tc::tma_load_2d(sB + (g * oz::S + j) * kBTile, &mapB, &bfull[g], kb * oz::KB, j * Bp + n0);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
-    const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
-    const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
-    bool ok = true;
-    for (int kb = 0; kb < num_kb && ok; ++kb) {
+  } else if (warp == kWaiterWarp) {
+    // ---------------- waiter: every mbarrier wait on behalf of the MMA warp (see
+    // oz_gemm_kernel), one handoff per A tile at named barrier 2, num_kb * 7 in all
+    bool failed = false;
+    for (int kb = 0; kb < num_kb; ++kb) {
       const int q = kb / kKbPerChunk;
       const bool chunk_start = (kb % kKbPerChunk) == 0;
-      if (chunk_start && q > 0) {  // the epilogue must have read chunk q-1
-        if (!mbar_wait_spin(tfree, (uint32_t)(q - 1) & 1u)) {
-          atomicExch(err, tc::ERR_TIMEOUT_DONE);
-          *abort_flag = 1;
-          break;
-        }
-        tc::fence_after_sync();
-      }
       const int g = kb & 1;
       const uint32_t gph = (uint32_t)(kb >> 1) & 1u;
-      if (!mbar_wait_spin(&bfull[g], gph)) {
-        atomicExch(err, tc::ERR_TIMEOUT_FULL);
-        *abort_flag = 1;
-        break;
+      int okw = 1;
+      if (lane == 0 && !failed) {
+        if (chunk_start && q > 0 && !mbar_wait_spin(tfree, (uint32_t)(q - 1) & 1u)) {  // chunk q-1 read out
+          atomicExch(err, tc::ERR_TIMEOUT_DONE);
+          *abort_flag = 1;
+          okw = 0;
+        } else if (!mbar_wait_spin(&bfull[g], gph)) {
+          atomicExch(err, tc::ERR_TIMEOUT_FULL);
+          *abort_flag = 1;
+          okw = 0;
+        }
       }
+      failed = failed || !__shfl_sync(0xffffffffu, okw, 0);
       for (int i = 0; i < oz::S; ++i) {
         const int ai = kb * oz::S + i;
         const int s = ai % kAStages;
         const uint32_t ph = (uint32_t)(ai / kAStages) & 1u;
-        if (!mbar_wait_spin(&afull[s], ph)) {
-          atomicExch(err, tc::ERR_TIMEOUT_FULL);
-          *abort_flag = 1;
-          ok = false;
-          break;
-        }
-        if (*abort_flag) {
-          ok = false;
-          break;
-        }
-        const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
-        const uint64_t bd = bdesc0 + (uint64_t)(g * oz::S * (kBTile >> 4));
-        const uint32_t first = (!chunk_start || i > 0) ? 1u : 0u;
-#pragma unroll
-        for (int j = 0; j < oz::S; ++j) {
-          if (i + j < oz::S) {
-            const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
-            const uint64_t bj = bd + (uint64_t)(j * (kBTile >> 4));
-            tc::mma_issue<true>(d, ad, bj, idesc, first);
-            tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
-            tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
-            tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+        int oka = 1;
+        if (lane == 0 && !failed) {
+          if (!mbar_wait_spin(&afull[s], ph)) {
+            atomicExch(err, tc::ERR_TIMEOUT_FULL);
+            *abort_flag = 1;
+            oka = 0;
+          } else if (*abort_flag) {
+            oka = 0;
           }
         }
-        tc::mma_commit(&aempty[s]);
+        failed = failed || !__shfl_sync(0xffffffffu, oka, 0);
+        (void)handoff(failed);
       }
-      if (!ok) break;
-      tc::mma_commit(&bempty[g]);
-      if ((kb % kKbPerChunk) == kKbPerChunk - 1 || kb == num_kb - 1) tc::mma_commit(cdone);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (lane 0; the whole warp meets the waiter at barrier 2)
+    constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
+    const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
+    const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
+    bool failed = false;
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const bool chunk_start = (kb % kKbPerChunk) == 0;
+      const int g = kb & 1;
+      for (int i = 0; i < oz::S; ++i) {
+        failed = handoff(false) || failed;
+        tc::fence_after_sync();
+        const int ai = kb * oz::S + i;
+        const int s = ai % kAStages;
+        if (lane == 0) {
+          if (!failed) {
+            const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
+            const uint64_t bd = bdesc0 + (uint64_t)(g * oz::S * (kBTile >> 4));
+            const uint32_t first = (!chunk_start || i > 0) ? 1u : 0u;
+#pragma unroll
+            for (int j = 0; j < oz::S; ++j) {
+              if (i + j < oz::S) {
+                const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
+                const uint64_t bj = bd + (uint64_t)(j * (kBTile >> 4));
+                tc::mma_issue<true>(d, ad, bj, idesc, first);
+                tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
+                tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
+                tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+              }
+            }
+          }
+          tc::mma_commit(&aempty[s]);  // also after a failure: the A producer never starves
+        }
+        __syncwarp();
+      }
+      if (lane == 0) {
+        tc::mma_commit(&bempty[g]);
+        if ((kb % kKbPerChunk) == kKbPerChunk - 1 || kb == num_kb - 1) tc::mma_commit(cdone);
+      }
+      __syncwarp();
     }
   } else if (warp >= 3) {
     // ---------------- epilogue: running double-float sums of 32 columns per thread
@@ -1112,7 +1137,7 @@ static gdml_status syrk_sliced(int64_t k, int64_t K, double* C, int64_t ldc, con
   if (s == GDML_OK) {
     slice(a);
     dim3 grid((unsigned)cdiv(k, oz::BN), (unsigned)cdiv(k, oz::BM));
-    { oz_gemm_acc_kernel<<<grid, kThreads, kSmemTotal, st>>>(a.map, mapB, (int)a.Rp, (int)a.Rp, (int)k, (int)k, (int)(a.Kp / oz::KB), a.e, a.e, C, ldc, 1, t.err); count_launch(); }
+    { oz_gemm_acc_kernel<<<grid, kThreadsAcc, kSmemTotal, st>>>(a.map, mapB, (int)a.Rp, (int)a.Rp, (int)k, (int)k, (int)(a.Kp / oz::KB), a.e, a.e, C, ldc, 1, t.err); count_launch(); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) s = fail(GDML_ERR_CUDA, std::string("sliced syrk launch: ") + cudaGetErrorString(e));
   }

@@ -260,53 +260,67 @@ __global__ void __launch_bounds__(kArgThreads) pc_finish_select_df_kernel(
     double* __restrict__ trace, PivState* __restrict__ ps, ArgMaxPart* __restrict__ part,
     unsigned* __restrict__ ticket, float* __restrict__ prow) {
   if (ps->stop) return;
-  __shared__ double sv[kArgThreads];
-  __shared__ int64_t sp[kArgThreads];
-  __shared__ double ss[kArgThreads];
+  constexpr int kW = kArgThreads / 32;
+  __shared__ double sv[kW];
+  __shared__ int64_t sp[kW];
+  __shared__ double ss[kW];
   __shared__ bool last;
   __shared__ int64_t s_piv;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t piv = ps->piv;
   const double lmm = ps->lmm, ilmm = ps->ilmm;  // one FP64 multiply per row instead of a division
   ArgMax best{-1.0 / 0.0, INT64_MAX};
   double sum = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kArgThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kArgThreads) {
-    if (!chosen[i]) {
-      float sh = 0.f, sl = 0.f;
-      for (int g = 0; g < groups; ++g) {
-        const float2 v = schur[(int64_t)g * n + i];
-        df_add_pair_pc(sh, sl, v.x, v.y);
-      }
-      const double lv = (col[i] - ((double)sh + (double)sl)) * ilmm;
+    // every operand of the row in one round of loads, before the branch
+    const bool ch = chosen[i] != 0;
+    const double ci = col[i], di = d[i];
+    const int64_t pi = posof[i];
+    float sh = 0.f, sl = 0.f;
+    for (int g = 0; g < groups; ++g) {
+      const float2 v = schur[(int64_t)g * n + i];
+      df_add_pair_pc(sh, sl, v.x, v.y);
+    }
+    if (!ch) {
+      const double lv = (ci - ((double)sh + (double)sl)) * ilmm;
       const float lst = (float)lv;
       L[i + m * n] = lst;
       const double lr = (double)lst;
-      const double dn = __dsub_rn(d[i], __dmul_rn(lr, lr));
+      const double dn = __dsub_rn(di, __dmul_rn(lr, lr));
       d[i] = dn;
       sum += dn;
-      best = better(best, ArgMax{dn, posof[i]});
+      best = better(best, ArgMax{dn, pi});
     } else if (i == piv) {
       L[i + m * n] = (float)lmm;
     }
   }
-  sv[threadIdx.x] = best.v;
-  sp[threadIdx.x] = best.pos;
-  ss[threadIdx.x] = sum;
-  __syncthreads();
-  for (int o = kArgThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      ArgMax r = better(ArgMax{sv[threadIdx.x], sp[threadIdx.x]}, ArgMax{sv[threadIdx.x + o], sp[threadIdx.x + o]});
-      sv[threadIdx.x] = r.v;
-      sp[threadIdx.x] = r.pos;
-      ss[threadIdx.x] += ss[threadIdx.x + o];
-    }
-    __syncthreads();
+  // CTA reduction: xor butterflies within warps (better() is commutative), then warp 0
+  for (int o = 16; o > 0; o >>= 1) {
+    const ArgMax ob{__shfl_xor_sync(0xffffffffu, best.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)best.pos, o)};
+    best = better(best, ob);
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
   }
-  if (threadIdx.x == 0) {
-    part[blockIdx.x].v = sv[0];
-    part[blockIdx.x].pos = sp[0];
-    part[blockIdx.x].sum = ss[0];
-    __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (lane == 0) {
+    sv[warp] = best.v;
+    sp[warp] = best.pos;
+    ss[warp] = sum;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    ArgMax bw = lane < kW ? ArgMax{sv[lane], sp[lane]} : ArgMax{-1.0 / 0.0, INT64_MAX};
+    double sw = lane < kW ? ss[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const ArgMax ob{__shfl_xor_sync(0xffffffffu, bw.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)bw.pos, o)};
+      bw = better(bw, ob);
+      sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    if (lane == 0) {
+      part[blockIdx.x].v = bw.v;
+      part[blockIdx.x].pos = bw.pos;
+      part[blockIdx.x].sum = sw;
+      __threadfence();
+      last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
   }
   __syncthreads();
   if (!last) return;
@@ -319,20 +333,33 @@ __global__ void __launch_bounds__(kArgThreads) pc_finish_select_df_kernel(
       bt = better(bt, ArgMax{vp[q].v, vp[q].pos});
       st += vp[q].sum;
     }
-    sv[threadIdx.x] = bt.v;
-    sp[threadIdx.x] = bt.pos;
-    ss[threadIdx.x] = st;
+    for (int o = 16; o > 0; o >>= 1) {
+      const ArgMax ob{__shfl_xor_sync(0xffffffffu, bt.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)bt.pos, o)};
+      bt = better(bt, ob);
+      st += __shfl_xor_sync(0xffffffffu, st, o);
+    }
+    if (lane == 0) {
+      sv[warp] = bt.v;
+      sp[warp] = bt.pos;
+      ss[warp] = st;
+    }
   }
   __syncthreads();
-  for (int o = kArgThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      ArgMax r = better(ArgMax{sv[threadIdx.x], sp[threadIdx.x]}, ArgMax{sv[threadIdx.x + o], sp[threadIdx.x + o]});
-      sv[threadIdx.x] = r.v;
-      sp[threadIdx.x] = r.pos;
-      ss[threadIdx.x] += ss[threadIdx.x + o];
+  if (warp == 0) {
+    ArgMax bw = lane < kW ? ArgMax{sv[lane], sp[lane]} : ArgMax{-1.0 / 0.0, INT64_MAX};
+    double sw = lane < kW ? ss[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const ArgMax ob{__shfl_xor_sync(0xffffffffu, bw.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)bw.pos, o)};
+      bw = better(bw, ob);
+      sw += __shfl_xor_sync(0xffffffffu, sw, o);
     }
-    __syncthreads();
+    if (lane == 0) {
+      sv[0] = bw.v;
+      sp[0] = bw.pos;
+      ss[0] = sw;
+    }
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const ArgMax b{sv[0], sp[0]};
     *ticket = 0u;
