@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "ws_stage.cuh"
 
 namespace gdml {
 
@@ -406,6 +407,234 @@ __global__ void __launch_bounds__(kArgThreads) pc_finish_select_df_kernel(
     }
 }
 
+// Algorithm 1 step m in one TMA-staged pass: the Schur sums s_i = sum_{j<m} L[i + j n] prow[j]
+// of ws_gemv_n_kernel's SCHUR mode, followed row by row (as each chunk's sums are combined)
+// by pc_finish_select_df_kernel's work: l_{i,m}, column m of L, the residual diagonal, the
+// argmax and the trace.  The last CTA to finish selects the pivot of step m + 1, performs
+// the swap and gathers that pivot's row of L into prow (every CTA has read prow by then).
+template <int NT>
+__global__ void __launch_bounds__(kWsThreads, 2) pc_schur_finish_ws_kernel(
+    const __grid_constant__ CUtensorMap map, int64_t n, int64_t m, int64_t nch, int select, float* __restrict__ L,
+    float* __restrict__ prow, const double* __restrict__ col, double* __restrict__ d,
+    unsigned char* __restrict__ chosen, int64_t* __restrict__ perm, int64_t* __restrict__ posof,
+    int64_t* __restrict__ pivots, double* __restrict__ trace, PivState* __restrict__ ps,
+    ArgMaxPart* __restrict__ part, unsigned* __restrict__ ticket, int* __restrict__ err) {
+  constexpr int RC = 128 * NT, COLS = 32 / NT, CPW = 4 / NT;
+  constexpr int kW = kWsWarps + 1;
+  if (ps->stop) return;
+  extern __shared__ uint8_t ws_smem_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws_smem_raw) + kWsAlign - 1) &
+                                             ~uintptr_t(kWsAlign - 1));
+  float2* cmb = reinterpret_cast<float2*>(ring + kWsStages * kWsTile);  // [warp][RC rows]
+  uint64_t* full = reinterpret_cast<uint64_t*>(cmb + kWsWarps * 256);
+  uint64_t* empty = full + kWsStages;
+  uint64_t* cbar = empty + kWsStages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(cbar + 2);
+  __shared__ uint32_t issued_s;
+  __shared__ double sv[kW];
+  __shared__ int64_t sp[kW];
+  __shared__ double ss[kW];
+  __shared__ bool last;
+  __shared__ int64_t s_piv;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = (int)((m + COLS - 1) / COLS);
+  const int64_t piv = ps->piv;
+  const double lmm = ps->lmm, ilmm = ps->ilmm;
+  if (threadIdx.x == 0) {
+    ws_init(full, empty, cbar, abort_flag);
+    issued_s = 0;
+  }
+  __syncthreads();
+  ArgMax best{-1.0 / 0.0, INT64_MAX};
+  double sum = 0.0;
+  if (warp == kWsWarps) {
+    if (lane == 0) issued_s = ws_produce<NT, false>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
+  } else {
+    WsRing rp;
+    uint32_t ci = 0;
+    bool go = true;
+    for (int64_t ch = blockIdx.x; ch < nch && go; ch += gridDim.x, ++ci) {
+      float2 h2[NT][2], l2[NT][2];
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) h2[t][q] = l2[t][q] = make_float2(0.f, 0.f);
+      for (int s = 0; s < ntiles; ++s) {
+        float xv[CPW];
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+          const int64_t j = (int64_t)s * COLS + warp * CPW + c;
+          xv[c] = j < m ? prow[j] : 0.f;
+        }
+        if (!ws_consume_wait(&full[rp.slot], rp.phase, abort_flag, err)) {
+          go = false;
+          break;
+        }
+        const float* tile = reinterpret_cast<const float*>(ring + rp.slot * kWsTile) + warp * CPW * RC;
+        float4 a[CPW][NT];
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+#pragma unroll
+          for (int t = 0; t < NT; ++t) a[c][t] = *reinterpret_cast<const float4*>(tile + c * RC + 128 * t + 4 * lane);
+        __syncwarp();
+        if (lane == 0) ws_arrive(&empty[rp.slot]);
+        rp.next();
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+          const float2 uh = make_float2(xv[c], xv[c]), un = make_float2(-xv[c], -xv[c]);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            df2_add_prod_lazy(h2[t][0], l2[t][0], lo_pair(a[c][t]), uh, un);
+            df2_add_prod_lazy(h2[t][1], l2[t][1], hi_pair(a[c][t]), uh, un);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) df2_renorm(h2[t][q], l2[t][q]);
+      }
+      if (!go) break;
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          cmb[warp * 256 + 128 * t + 4 * lane + 2 * q] = make_float2(h2[t][q].x, l2[t][q].x);
+          cmb[warp * 256 + 128 * t + 4 * lane + 2 * q + 1] = make_float2(h2[t][q].y, l2[t][q].y);
+        }
+      if (!ws_consumer_sync(&cbar[0], ci & 1u, abort_flag, err)) break;
+      const int64_t i0 = ch * RC;
+      const int rr = threadIdx.x;  // 256 consumer threads, one row each
+      if (rr < RC && i0 + rr < n) {
+        const int64_t i = i0 + rr;
+        const bool chs = chosen[i] != 0;
+        const double ci_ = col[i], di = d[i];
+        const int64_t pi = posof[i];
+        float hh = cmb[rr].x, ll = cmb[rr].y;
+#pragma unroll
+        for (int w = 1; w < kWsWarps; ++w) df_add_pair_pc(hh, ll, cmb[w * 256 + rr].x, cmb[w * 256 + rr].y);
+        if (!chs) {
+          const double lv = (ci_ - ((double)hh + (double)ll)) * ilmm;
+          const float lst = (float)lv;
+          L[i + m * n] = lst;
+          const double lr = (double)lst;
+          const double dn = __dsub_rn(di, __dmul_rn(lr, lr));
+          d[i] = dn;
+          sum += dn;
+          best = better(best, ArgMax{dn, pi});
+        } else if (i == piv) {
+          L[i + m * n] = (float)lmm;
+        }
+      }
+      if (!ws_consumer_sync(&cbar[1], ci & 1u, abort_flag, err)) break;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) ws_drain(full, issued_s);
+  // CTA reduction (the producer warp holds neutral values), then the grid's through part[]
+  for (int o = 16; o > 0; o >>= 1) {
+    const ArgMax ob{__shfl_xor_sync(0xffffffffu, best.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)best.pos, o)};
+    best = better(best, ob);
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  }
+  if (lane == 0) {
+    sv[warp] = best.v;
+    sp[warp] = best.pos;
+    ss[warp] = sum;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    ArgMax bw = lane < kW ? ArgMax{sv[lane], sp[lane]} : ArgMax{-1.0 / 0.0, INT64_MAX};
+    double sw = lane < kW ? ss[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const ArgMax ob{__shfl_xor_sync(0xffffffffu, bw.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)bw.pos, o)};
+      bw = better(bw, ob);
+      sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    if (lane == 0) {
+      part[blockIdx.x].v = bw.v;
+      part[blockIdx.x].pos = bw.pos;
+      part[blockIdx.x].sum = sw;
+      __threadfence();
+      last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  {
+    ArgMax bt{-1.0 / 0.0, INT64_MAX};
+    double st = 0.0;
+    volatile ArgMaxPart* vp = part;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+      bt = better(bt, ArgMax{vp[q].v, vp[q].pos});
+      st += vp[q].sum;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const ArgMax ob{__shfl_xor_sync(0xffffffffu, bt.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)bt.pos, o)};
+      bt = better(bt, ob);
+      st += __shfl_xor_sync(0xffffffffu, st, o);
+    }
+    if (lane == 0) {
+      sv[warp] = bt.v;
+      sp[warp] = bt.pos;
+      ss[warp] = st;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    ArgMax bw = lane < kW ? ArgMax{sv[lane], sp[lane]} : ArgMax{-1.0 / 0.0, INT64_MAX};
+    double sw = lane < kW ? ss[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const ArgMax ob{__shfl_xor_sync(0xffffffffu, bw.v, o), (int64_t)__shfl_xor_sync(0xffffffffu, (long long)bw.pos, o)};
+      bw = better(bw, ob);
+      sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    if (lane == 0) {
+      const ArgMax b = bw;
+      *ticket = 0u;
+      if (trace) trace[m] = sw;
+      s_piv = -1;
+      if (select) {
+        const int64_t m1 = m + 1;
+        if (!(b.v > 0.0) || b.pos >= n) {
+          ps->stop = 1;
+          ps->rank = m1;
+        } else {
+          const int64_t p = perm[b.pos];
+          const int64_t other = perm[m1];
+          perm[b.pos] = other;
+          perm[m1] = p;
+          posof[other] = b.pos;
+          posof[p] = m1;
+          pivots[m1] = p;
+          chosen[p] = 1;
+          ps->lmm = sqrt(d[p]);
+          ps->ilmm = 1.0 / ps->lmm;
+          ps->piv = p;
+          ps->rank = m1 + 1;
+          s_piv = p;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t p = s_piv;
+  if (p >= 0)  // the next pivot's row of L, columns 0..m (column m written above, fenced)
+    for (int64_t j0 = threadIdx.x; j0 <= m; j0 += 8 * (int64_t)blockDim.x) {
+      float pv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = j0 + (int64_t)u * blockDim.x;
+        pv[u] = j <= m ? L[p + j * n] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = j0 + (int64_t)u * blockDim.x;
+        if (j <= m) prow[j] = pv[u];
+      }
+    }
+}
+
 int pivchol_schur_groups() { return kSchurMaxGroups; }
 
 void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
@@ -418,14 +647,28 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
   // step 0's pivot
   { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(0, a.n, 1, a.d, a.perm, a.chosen, a.pivots, nullptr,
                                                        a.ps, a.part, a.ticket, a.posof); count_launch(); }
+  if (plan.ok) {  // two launches per step: the kernel column, then Schur sums + finish
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(pc_schur_finish_ws_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN);
+      cudaFuncSetAttribute(pc_schur_finish_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN);
+      attr = true;
+    }
+    for (int64_t m = 0; m < a.k; ++m) {
+      a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
+      const int select = m + 1 < a.k ? 1 : 0;
+      if (plan.rc == 256)
+        { pc_schur_finish_ws_kernel<2><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, a.n, m, plan.nch, select, L, a.prow, a.col, a.d, a.chosen, a.perm, a.posof, a.pivots, a.trace, a.ps, a.part, a.ticket, a.err); count_launch(); }
+      else
+        { pc_schur_finish_ws_kernel<1><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, a.n, m, plan.nch, select, L, a.prow, a.col, a.d, a.chosen, a.perm, a.posof, a.pivots, a.trace, a.ps, a.part, a.ticket, a.err); count_launch(); }
+    }
+    return;
+  }
   for (int64_t m = 0; m < a.k; ++m) {
     a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
     // column groups: enough CTAs for ~4 per SM, at least 32 columns per group
     int groups = 0;
-    if (m > 0 && plan.ok) {
-      groups = 1;
-      ws_schur(plan, m, a.prow, a.ps, a.schur, a.err, st);
-    } else if (m > 0) {
+    if (m > 0) {
       const int64_t want = cdiv(4 * kNumSMs, rblocks);
       groups = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)kSchurMaxGroups, std::max<int64_t>(1, m / 32)}));
       dim3 g((unsigned)rblocks, (unsigned)groups);
