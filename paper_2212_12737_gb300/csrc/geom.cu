@@ -413,22 +413,10 @@ __global__ void __launch_bounds__(256) kcol_df_kernel(const int64_t* __restrict_
   const int64_t c = blockIdx.y;
   const int64_t col = cols[c];
   const int B = 3 * N;
-  const int64_t b = col / B;
-  const int l = (int)(col - b * B), i = l / 3, q = l - 3 * i;
-  const float2* Xb = X2 + b * D;
-  const float2* Gb = G2 + b * D * 3;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    float2 w = make_float2(0.f, 0.f);
-    if (j != i) {
-      const float2 g = Gb[3 * pair_idx(i, j) + q];
-      w = (i > j) ? dfk_neg(g) : g;
-    }
-    wsp[j] = w;
-  }
-  for (int p = threadIdx.x; p < D; p += blockDim.x) sxb[p] = Xb[p];
   const int64_t a = (int64_t)blockIdx.x * W + warp;
   const bool live = a < M;
   float2 sab = make_float2(0.f, 0.f), aab = sab;
+  // geometry a's operands do not depend on the pivot: their loads go first
   if (live) {  // eight independent loads in flight per lane, then the shared-memory stores
     const float2* Xa = X2 + a * D;
     const float2* Ga = G2 + a * D * 3;
@@ -448,10 +436,23 @@ __global__ void __launch_bounds__(256) kcol_df_kernel(const int64_t* __restrict_
           sga[e - D] = tmp[u8];
       }
     }
-    if (lane == 0) {
-      sab = dfk_mul(dfk_split(c2), dfk_split(S[b * M + a]));
-      aab = dfk_split(A[b * ldA + a]);
+  }
+  const int64_t b = col / B;
+  const int l = (int)(col - b * B), i = l / 3, q = l - 3 * i;
+  const float2* Xb = X2 + b * D;
+  const float2* Gb = G2 + b * D * 3;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float2 w = make_float2(0.f, 0.f);
+    if (j != i) {
+      const float2 g = Gb[3 * pair_idx(i, j) + q];
+      w = (i > j) ? dfk_neg(g) : g;
     }
+    wsp[j] = w;
+  }
+  for (int p = threadIdx.x; p < D; p += blockDim.x) sxb[p] = Xb[p];
+  if (live && lane == 0) {
+    sab = dfk_mul(dfk_split(c2), dfk_split(S[b * M + a]));
+    aab = dfk_split(A[b * ldA + a]);
   }
   __syncthreads();
   if (!live) return;

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kWsThreads, 2) pc_schur_finish_ws_kernel(
     float* __restrict__ prow, const double* __restrict__ col, double* __restrict__ d,
     unsigned char* __restrict__ chosen, int64_t* __restrict__ perm, int64_t* __restrict__ posof,
     int64_t* __restrict__ pivots, double* __restrict__ trace, PivState* __restrict__ ps,
-    ArgMaxPart* __restrict__ part, unsigned* __restrict__ ticket, int* __restrict__ err) {
+    ArgMaxPart* __restrict__ part, unsigned* __restrict__ ticket, int* __restrict__ err, int evict_first) {
   constexpr int RC = 128 * NT, COLS = 32 / NT, CPW = 4 / NT;
   constexpr int kW = kWsWarps + 1;
   if (ps->stop) return;
@@ -448,7 +448,9 @@ __global__ void __launch_bounds__(kWsThreads, 2) pc_schur_finish_ws_kernel(
   ArgMax best{-1.0 / 0.0, INT64_MAX};
   double sum = 0.0;
   if (warp == kWsWarps) {
-    if (lane == 0) issued_s = ws_produce<NT, false>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
+    if (lane == 0)
+      issued_s = evict_first ? ws_produce<NT, true>(&map, ring, full, empty, abort_flag, nch, ntiles, err)
+                             : ws_produce<NT, false>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
   } else {
     WsRing rp;
     uint32_t ci = 0;
@@ -657,10 +659,13 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
     for (int64_t m = 0; m < a.k; ++m) {
       a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
       const int select = m + 1 < a.k ? 1 : 0;
+      // once the first m columns no longer fit in L2 they are streamed evict-first, so the
+      // kernel column's operands (X, G as float pairs) and the per-row state stay resident
+      const int ef = (double)m * (double)a.n * 4.0 > 96.0 * 1024 * 1024 ? 1 : 0;
       if (plan.rc == 256)
-        { pc_schur_finish_ws_kernel<2><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, a.n, m, plan.nch, select, L, a.prow, a.col, a.d, a.chosen, a.perm, a.posof, a.pivots, a.trace, a.ps, a.part, a.ticket, a.err); count_launch(); }
+        { pc_schur_finish_ws_kernel<2><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, a.n, m, plan.nch, select, L, a.prow, a.col, a.d, a.chosen, a.perm, a.posof, a.pivots, a.trace, a.ps, a.part, a.ticket, a.err, ef); count_launch(); }
       else
-        { pc_schur_finish_ws_kernel<1><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, a.n, m, plan.nch, select, L, a.prow, a.col, a.d, a.chosen, a.perm, a.posof, a.pivots, a.trace, a.ps, a.part, a.ticket, a.err); count_launch(); }
+        { pc_schur_finish_ws_kernel<1><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, a.n, m, plan.nch, select, L, a.prow, a.col, a.d, a.chosen, a.perm, a.posof, a.pivots, a.trace, a.ps, a.part, a.ticket, a.err, ef); count_launch(); }
     }
     return;
   }
