@@ -515,11 +515,16 @@ def run_gpu(args):
                    "algorithmic_flop_per_launch": 6.0 * M * M * D * SLICE_PAIRS[args.precision],
                    "fp64_equivalent_tflops": mv_tf, "matvec_ms": mv_sec * 1e3}
     hbm = peaks.get("hbm_gbs", 6800.0)
+    # DRAM bytes of one apply (dram__bytes_read.sum + dram__bytes_write.sum over its 7 launches,
+    # one ncu capture of `bench.py --only apply --precision ozaki` at this workload; see
+    # profiles/woodbury_apply_aspirin21_m1000_k2000_ozaki.md).  Only that configuration has one.
+    ap_traffic = (1040180736.0 if args.workload == "aspirin21_m1000" and args.precision in ("ozaki", "df64")
+                  and w.k == 2000 else None)
     roof_apply = {"kernel": f"Woodbury apply (Eq. 4), {args.precision}: L_k^T r and L_k u passes + k x k core",
                   "bound": "hbm", "achieved": ap_bytes / ap_sec / 1e9, "peak": hbm, "unit": "GB/s",
                   "frac": ap_bytes / ap_sec / 1e9 / hbm,
                   "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
-                  "traffic": None, "algorithmic_bytes_per_launch": ap_bytes, "apply_ms": ap_sec * 1e3}
+                  "traffic": ap_traffic, "algorithmic_bytes_per_launch": ap_bytes, "apply_ms": ap_sec * 1e3}
 
     if rank == 0:
         line = {

@@ -307,7 +307,7 @@ gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, d
     TRY(s.get(&X, (size_t)(k * k)));
     TRY(s.get(&Xt, (size_t)(k * k)));
     set_identity(X, k, c->st);
-    trsm_left_lower(LC, k, X, k, c->st);  // X = L_C^-1
+    trsm_left_lower(LC, k, X, k, c->st, true);  // X = L_C^-1 (lower triangular)
     transpose_square(X, k, Xt, c->st);
     if (df_precond(c)) {  // X^T X on the sliced tensor cores (FP64-class), lower triangle mirrored
       TRY(check_launch(c, "woodbury inverse"));

@@ -52,7 +52,7 @@ void launch_dfgemm(bool nt, int64_t M, int64_t N, int64_t K, const double* A, in
 
 // linalg.cu
 void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st);
-void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st);
+void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st, bool lower_rhs = false);
 void add_diag(double* A, int64_t lda, int64_t k, double eps, cudaStream_t st);
 
 // woodbury.cu

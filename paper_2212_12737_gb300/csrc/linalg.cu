@@ -4,6 +4,8 @@
 //  - the explicit inverse C^-1 = L_C^-T L_C^-1 used by the Woodbury apply
 // A non-positive or non-finite pivot is reported through a device status word
 // (index of the failing column + 1), never by trapping.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -120,14 +122,18 @@ void cholesky_inplace(double* A, int64_t k, int* status, cudaStream_t st) {
   }
 }
 
-// B (k x nrhs row-major) <- Lkk^-1 B  (blocked forward substitution)
-void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st) {
+// B (k x nrhs row-major) <- Lkk^-1 B  (blocked forward substitution).  lower_rhs: B is lower
+// triangular (the identity, for Lkk^-1 itself), so row block j0 and everything it updates
+// have no nonzeros past column j0 + nb and only those columns are touched (a third of the
+// flops).
+void trsm_left_lower(const double* Lkk, int64_t k, double* Bm, int64_t nrhs, cudaStream_t st, bool lower_rhs) {
   for (int64_t j0 = 0; j0 < k; j0 += NB) {
     int nb = (int)((k - j0) < NB ? (k - j0) : NB);
-    { trsm_left_diag_kernel<<<(unsigned)cdiv(nrhs, 128), 128, 0, st>>>(Lkk, k, j0, nb, Bm, nrhs, nrhs); count_launch(); }
+    const int64_t ncols = lower_rhs ? std::min<int64_t>(nrhs, j0 + nb) : nrhs;
+    { trsm_left_diag_kernel<<<(unsigned)cdiv(ncols, 128), 128, 0, st>>>(Lkk, k, j0, nb, Bm, nrhs, ncols); count_launch(); }
     int64_t r0 = j0 + nb;
-    if (r0 < k)  // B[r0:, :] -= L[r0:, j0:j0+nb] * B[j0:j0+nb, :]
-      launch_dgemm<double, double>(false, k - r0, nrhs, nb, -1.0, Lkk + r0 * k + j0, k, Bm + j0 * nrhs, nrhs,
+    if (r0 < k)  // B[r0:, :ncols] -= L[r0:, j0:j0+nb] * B[j0:j0+nb, :ncols]
+      launch_dgemm<double, double>(false, k - r0, ncols, nb, -1.0, Lkk + r0 * k + j0, k, Bm + j0 * nrhs, nrhs,
                                    1.0, Bm + r0 * nrhs, nrhs, false, st);
   }
 }

@@ -779,6 +779,16 @@ __global__ void __launch_bounds__(256) symv_df_kernel(const float2* __restrict__
 // (eight in flight; the k x k matrices stay in L2 between applies) against x from shared
 // memory, then a fixed shuffle tree.
 constexpr int kSymvRowsMaxK = 4096;
+
+// 16-byte load marked evict-last in L2: the k x k matrices of the apply's core are re-read
+// every apply and should outlive the matvec's operands in L2 (the L_k tiles are evict-first)
+__device__ __forceinline__ float4 ld_evict_last(const float4* p, uint64_t policy) {
+  float4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(policy));
+  return v;
+}
 __global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restrict__ A, int64_t k,
                                                            const float2* __restrict__ x, int mode,
                                                            const double* __restrict__ t, double* __restrict__ y,
@@ -793,11 +803,13 @@ __global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restr
   const float4* xv4 = reinterpret_cast<const float4*>(xs);
   const int64_t nq = k / 2;  // float4 pieces per row (two entries each)
   float h = 0.f, l = 0.f;
+  uint64_t policy;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
   int64_t q = lane;
   for (; q + 224 < nq; q += 256) {  // eight 16-byte loads in flight per lane
     float4 av[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) av[u] = __ldg(row + q + 32 * u);
+    for (int u = 0; u < 8; ++u) av[u] = ld_evict_last(row + q + 32 * u, policy);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const float4 xq = xv4[q + 32 * u];
@@ -806,7 +818,7 @@ __global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restr
     }
   }
   for (; q < nq; q += 32) {
-    const float4 a = __ldg(row + q), xq = xv4[q];
+    const float4 a = ld_evict_last(row + q, policy), xq = xv4[q];
     df_term(h, l, a.x, a.y, xq.x, xq.y);
     df_term(h, l, a.z, a.w, xq.z, xq.w);
   }
