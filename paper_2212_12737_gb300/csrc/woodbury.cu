@@ -802,26 +802,44 @@ __global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restr
   const float4* row = reinterpret_cast<const float4*>(A + i * k);  // k even: 16-byte aligned rows
   const float4* xv4 = reinterpret_cast<const float4*>(xs);
   const int64_t nq = k / 2;  // float4 pieces per row (two entries each)
-  float h = 0.f, l = 0.f;
+  // two independent double-float chains (even and odd entries of each piece) and the next
+  // eight pieces' loads issued before the current eight are summed
+  float h = 0.f, l = 0.f, h1 = 0.f, l1 = 0.f;
   uint64_t policy;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
   int64_t q = lane;
-  for (; q + 224 < nq; q += 256) {  // eight 16-byte loads in flight per lane
-    float4 av[8];
+  float4 av[8];
+  const bool full8 = q + 224 < nq;
+  if (full8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) av[u] = ld_evict_last(row + q + 32 * u, policy);
+  }
+  while (q + 224 < nq) {
+    float4 nv[8];
+    const int64_t qn = q + 256;
+    const bool more = qn + 224 < nq;
+    if (more) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) nv[u] = ld_evict_last(row + qn + 32 * u, policy);
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const float4 xq = xv4[q + 32 * u];
       df_term(h, l, av[u].x, av[u].y, xq.x, xq.y);
-      df_term(h, l, av[u].z, av[u].w, xq.z, xq.w);
+      df_term(h1, l1, av[u].z, av[u].w, xq.z, xq.w);
+    }
+    q = qn;
+    if (more) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) av[u] = nv[u];
     }
   }
   for (; q < nq; q += 32) {
     const float4 a = ld_evict_last(row + q, policy), xq = xv4[q];
     df_term(h, l, a.x, a.y, xq.x, xq.y);
-    df_term(h, l, a.z, a.w, xq.z, xq.w);
+    df_term(h1, l1, a.z, a.w, xq.z, xq.w);
   }
+  df_add_pair(h, l, h1, l1);
   for (int o = 16; o > 0; o >>= 1) {
     const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
     df_add_pair(h, l, oh, ol);
