@@ -78,12 +78,6 @@ struct WsPlan {
 // fills plan for L (plan.ok = false where the staged passes do not apply: n % 4 != 0, k = 0,
 // or the driver rejects the map); rows: 128 or 256 to force the chunk size, else automatic
 void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows = 0);
-struct PivState;
-// Algorithm 1 step m's Schur sums through the staged pass: schur[i] = sum_{j < m} L[i + j n]
-// prow[j] (double-float pairs); plan made by ws_plan for the factor; nothing runs once
-// ps->stop is set
-void ws_schur(const WsPlan& plan, int64_t m, const float* prow, const PivState* ps, float2* schur, int* err,
-              cudaStream_t st);
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                        const double* r, double* z, double* part, double* t, float2* rs, const WsPlan* plan,
                        int* err, cudaStream_t st);

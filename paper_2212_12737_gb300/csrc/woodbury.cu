@@ -520,18 +520,12 @@ __global__ void __launch_bounds__(kWsThreads, 2)
 // z[i] = (r[i] - sum_j L[i + j n] u[j]) / lambda for the chunk's rows: 4 NT double-float
 // chains per lane (its rows, packed in pairs), CPW products each per tile; the 8 warps' sums
 // are combined in a fixed order through shared memory at the end of the chunk.
-// SCHUR: the Schur sums of Algorithm 1 step m instead, schur[i] = sum_{j < k} L[i + j n]
-// prow[j] as a double-float pair (k = m, prow: the pivot's row of L in FP32); L is read
-// with the normal L2 policy (the first columns are re-read every step); nothing runs once
-// ps->stop is set.
-template <int NT, bool SCHUR>
+template <int NT>
 __global__ void __launch_bounds__(kWsThreads, 2)
     ws_gemv_n_kernel(const __grid_constant__ CUtensorMap map, int64_t n, int64_t k, int64_t nch,
-                     const float2* __restrict__ us, const float* __restrict__ prow, const double* __restrict__ r,
-                     double inv_lam, double* __restrict__ z, float2* __restrict__ schur,
-                     const PivState* __restrict__ ps, int* __restrict__ err) {
+                     const float2* __restrict__ us, const double* __restrict__ r, double inv_lam,
+                     double* __restrict__ z, int* __restrict__ err) {
   constexpr int RC = 128 * NT, COLS = 32 / NT, CPW = 4 / NT;
-  if (SCHUR && ps->stop) return;
   extern __shared__ uint8_t ws_smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws_smem_raw) + kWsAlign - 1) &
                                              ~uintptr_t(kWsAlign - 1));
@@ -549,7 +543,7 @@ __global__ void __launch_bounds__(kWsThreads, 2)
   }
   __syncthreads();
   if (warp == kWsWarps) {
-    if (lane == 0) issued_s = ws_produce<NT, !SCHUR>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
+    if (lane == 0) issued_s = ws_produce<NT, true>(&map, ring, full, empty, abort_flag, nch, ntiles, err);
   } else {
     WsRing rp;
     uint32_t ci = 0;
@@ -565,10 +559,7 @@ __global__ void __launch_bounds__(kWsThreads, 2)
 #pragma unroll
         for (int c = 0; c < CPW; ++c) {
           const int64_t j = (int64_t)s * COLS + warp * CPW + c;
-          if (SCHUR)
-            x[c] = make_float2(j < k ? prow[j] : 0.f, 0.f);
-          else
-            x[c] = j < k ? us[j] : make_float2(0.f, 0.f);
+          x[c] = j < k ? us[j] : make_float2(0.f, 0.f);
         }
         if (!ws_consume_wait(&full[rp.slot], rp.phase, abort_flag, err)) {
           go = false;
@@ -589,13 +580,8 @@ __global__ void __launch_bounds__(kWsThreads, 2)
                        ul = make_float2(x[c].y, x[c].y);
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
-            if (SCHUR) {
-              df2_add_prod_lazy(h2[t][0], l2[t][0], lo_pair(a[c][t]), uh, un);
-              df2_add_prod_lazy(h2[t][1], l2[t][1], hi_pair(a[c][t]), uh, un);
-            } else {
-              df2_add_prod_lazy(h2[t][0], l2[t][0], lo_pair(a[c][t]), uh, un, ul);
-              df2_add_prod_lazy(h2[t][1], l2[t][1], hi_pair(a[c][t]), uh, un, ul);
-            }
+            df2_add_prod_lazy(h2[t][0], l2[t][0], lo_pair(a[c][t]), uh, un, ul);
+            df2_add_prod_lazy(h2[t][1], l2[t][1], hi_pair(a[c][t]), uh, un, ul);
           }
         }
 #pragma unroll
@@ -618,10 +604,7 @@ __global__ void __launch_bounds__(kWsThreads, 2)
         float hh = cmb[rr].x, ll = cmb[rr].y;
 #pragma unroll
         for (int w = 1; w < kWsWarps; ++w) df_add_pair(hh, ll, cmb[w * 256 + rr].x, cmb[w * 256 + rr].y);
-        if (SCHUR)
-          schur[i0 + rr] = make_float2(hh, ll);
-        else
-          z[i0 + rr] = (r[i0 + rr] - ((double)hh + (double)ll)) * inv_lam;
+        z[i0 + rr] = (r[i0 + rr] - ((double)hh + (double)ll)) * inv_lam;
       }
       if (!ws_consumer_sync(&cbar[1], ci & 1u, abort_flag, err)) break;
     }
@@ -643,13 +626,9 @@ void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows) {
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(ws_gemv_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemT) != cudaSuccess ||
-        cudaFuncSetAttribute(ws_gemv_n_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
+        cudaFuncSetAttribute(ws_gemv_n_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(ws_gemv_n_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(ws_gemv_n_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(ws_gemv_n_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
+        cudaFuncSetAttribute(ws_gemv_n_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemN) !=
             cudaSuccess) {
       (void)cudaGetLastError();
       return;
@@ -658,7 +637,7 @@ void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows) {
   }
   // resident CTAs per SM (two by design; fewer if the shared-memory carve-out says so)
   int occ = 0, occ_t = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ws_gemv_n_kernel<2, false>, kWsThreads, kWsSmemN) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ws_gemv_n_kernel<2>, kWsThreads, kWsSmemN) !=
           cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, ws_gemv_t_kernel, kWsThreads, kWsSmemT) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -921,9 +900,9 @@ static void df_pass_n(const float* L, int64_t n, int64_t k, const float2* u2, co
                       double* z, double* part, const WsPlan* plan, int* err, cudaStream_t st) {
   if (ws_usable(plan, L, n, k)) {
     if (plan->rc == 256)
-      { ws_gemv_n_kernel<2, false><<<plan->grid, kWsThreads, kWsSmemN, st>>>(plan->map, n, k, plan->nch, u2, nullptr, r, inv_lam, z, nullptr, nullptr, err); count_launch(); }
+      { ws_gemv_n_kernel<2><<<plan->grid, kWsThreads, kWsSmemN, st>>>(plan->map, n, k, plan->nch, u2, r, inv_lam, z, err); count_launch(); }
     else
-      { ws_gemv_n_kernel<1, false><<<plan->grid, kWsThreads, kWsSmemN, st>>>(plan->map, n, k, plan->nch, u2, nullptr, r, inv_lam, z, nullptr, nullptr, err); count_launch(); }
+      { ws_gemv_n_kernel<1><<<plan->grid, kWsThreads, kWsSmemN, st>>>(plan->map, n, k, plan->nch, u2, r, inv_lam, z, err); count_launch(); }
     return;
   }
   float2* zp = reinterpret_cast<float2*>(part);
@@ -933,14 +912,6 @@ static void df_pass_n(const float* L, int64_t n, int64_t k, const float2* u2, co
   else
     { gemv_n_df_kernel<false><<<g2, 256, 0, st>>>(L, n, k, u2, zp); count_launch(); }
   { gemv_n_df_finish_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(zp, n, r, inv_lam, z); count_launch(); }
-}
-
-void ws_schur(const WsPlan& plan, int64_t m, const float* prow, const PivState* ps, float2* schur, int* err,
-              cudaStream_t st) {
-  if (plan.rc == 256)
-    { ws_gemv_n_kernel<2, true><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, plan.n, m, plan.nch, nullptr, prow, nullptr, 0.0, nullptr, schur, ps, err); count_launch(); }
-  else
-    { ws_gemv_n_kernel<1, true><<<plan.grid, kWsThreads, kWsSmemN, st>>>(plan.map, plan.n, m, plan.nch, nullptr, prow, nullptr, 0.0, nullptr, schur, ps, err); count_launch(); }
 }
 
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
