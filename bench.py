@@ -242,7 +242,7 @@ def run_learned(args):
     """Learned inducing-column scorer: train on per-geometry ridge-leverage
     labels of --suite-count training systems of the same molecule (other noise
     seeds), select k columns for the headline system, and compare PCG
-    iterations / solve time with pivoted Cholesky (the fallback and judge)."""
+    iterations / solve time with pivoted Cholesky (the fallback and referee)."""
     import torch
 
     from paper_2212_12737_gb300 import gdml, synth
@@ -289,15 +289,15 @@ def run_learned(args):
         c.destroy()
         return it, rel
 
-    def learned(judge):
+    def learned(referee):
         c = gdml.kernel_setup(R, w.sigma, w.lam)
-        _, it, rel, used = gdml.solve_learned(c, sc, yv, k, judge_iters=judge)
+        _, it, rel, used = gdml.solve_learned(c, sc, yv, k, referee_iters=referee)
         c.destroy()
         return it, rel, used
 
     t_pc, (it_pc, rel_pc) = timed(pivchol)
     t_l, (it_l, rel_l, used) = timed(lambda: learned(it_pc))
-    # learned without the judge's cap, to report its own iteration count
+    # learned without the referee's cap, to report its own iteration count
     c = gdml.kernel_setup(R, w.sigma, w.lam)
     c.precond_build_scored(sc.predict(c.descriptors()), k)
     _, it_raw, rel_raw, _ = c.pcg_solve(yv, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
@@ -310,7 +310,7 @@ def run_learned(args):
                       "label_s": t_labels, "train_s": t_train, "train_loss": loss,
                       "pivchol": {"s": t_pc, "iters": it_pc, "relres": rel_pc},
                       "learned": {"s": t_l, "iters": it_l, "relres": rel_l, "used": used,
-                                  "iters_without_judge": it_raw, "relres_without_judge": rel_raw},
+                                  "iters_without_referee": it_raw, "relres_without_referee": rel_raw},
                       "uniform": {"iters": it_u, "relres": rel_u}}), flush=True)
     sc.destroy()
 

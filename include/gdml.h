@@ -217,7 +217,7 @@ gdml_status gdml_matvec_noalloc(const double* R_dev, int64_t M, int32_t N, doubl
  * exact-erf GELU, FP32 master weights and accumulation, trained by Adam
  * (beta 0.9 / 0.999) on mean-squared error.  Its per-geometry scores feed
  * gdml_precond_build_scored; pivoted Cholesky (Alg. 1) stays the fallback and
- * the judge (by PCG iteration count) of its selections.  The paper has no
+ * the referee (by PCG iteration count) of its selections.  The paper has no
  * learned selection; its leverage-score sampling (Sec. 3) supplies the labels. */
 typedef struct gdml_scorer gdml_scorer;
 gdml_status gdml_scorer_create(gdml_scorer** s, int32_t D, int32_t hidden, uint64_t seed, void* cuda_stream);

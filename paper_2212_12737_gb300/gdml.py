@@ -416,11 +416,11 @@ def geometry_labels(ctx: Context, k: int, seed: int = 2) -> torch.Tensor:
 
 
 def solve_learned(ctx: Context, scorer: Scorer, y, k: int, seed: int = 2, rtol: float = 1e-8,
-                  max_iter: int = 20000, judge_iters: int | None = None):
-    """Learned selection with pivoted Cholesky (Alg. 1) as fallback and judge:
+                  max_iter: int = 20000, referee_iters: int | None = None):
+    """Learned selection with pivoted Cholesky (Alg. 1) as fallback and referee:
     build from the scorer's per-geometry scores; fall back to Alg. 1 if the
     inducing block is not SPD, or if PCG needs more than 1.5x the iterations of
-    the Alg. 1 preconditioner (judge_iters; measured here when not given).
+    the Alg. 1 preconditioner (referee_iters; measured here when not given).
     Returns (alpha, iterations, relres, used) with used in {"learned", "pivchol"}."""
     scores = scorer.predict(ctx.descriptors())
     try:
@@ -431,9 +431,9 @@ def solve_learned(ctx: Context, scorer: Scorer, y, k: int, seed: int = 2, rtol: 
         ctx.precond_build("pivchol", k)
         a, it, rel, _ = ctx.pcg_solve(y, rtol=rtol, max_iter=max_iter)
         return a, it, rel, "pivchol"
-    cap = max_iter if judge_iters is None else min(max_iter, int(1.5 * judge_iters) + 1)
+    cap = max_iter if referee_iters is None else min(max_iter, int(1.5 * referee_iters) + 1)
     a, it, rel, _ = ctx.pcg_solve(y, rtol=rtol, max_iter=cap, raise_on_nonconvergence=False)
-    if rel <= rtol and (judge_iters is None or it <= 1.5 * judge_iters):
+    if rel <= rtol and (referee_iters is None or it <= 1.5 * referee_iters):
         return a, it, rel, "learned"
     ctx.precond_build("pivchol", k)
     a, it2, rel2, _ = ctx.pcg_solve(y, rtol=rtol, max_iter=max_iter)

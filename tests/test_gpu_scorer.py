@@ -1,7 +1,7 @@
 """Learned inducing-column scorer: BF16 MLP kernels against a PyTorch CPU FP32
 reference with the same BF16 roundings (straight-through gradients), the
 RLS labels against the oracle, and the learned selection with pivoted
-Cholesky as fallback and judge."""
+Cholesky as fallback and referee."""
 import numpy as np
 import pytest
 import torch
@@ -106,7 +106,7 @@ def test_rls_scores_match_oracle_estimate():
     ctx.destroy()
 
 
-def test_learned_selection_solves_with_pivchol_as_judge():
+def test_learned_selection_solves_with_pivchol_as_referee():
     train = [synth.make_workload(f"t{s}", 9, 200, 0.05, 10.0, 1e-10, 200, "uniform", template_seed=0,
                                  noise_seed=100 + s) for s in range(4)]
     Xs, ys = [], []
@@ -127,7 +127,7 @@ def test_learned_selection_solves_with_pivchol_as_judge():
     _, it_pc, rel_pc, _ = ctx.pcg_solve(yd)
     piv = ctx.precond_build_scored(s.predict(ctx.descriptors()), 200, pivots=True)
     assert len(set(piv.cpu().tolist())) == 200
-    a, it, rel, used = gdml.solve_learned(ctx, s, yd, 200, judge_iters=it_pc)
+    a, it, rel, used = gdml.solve_learned(ctx, s, yd, 200, referee_iters=it_pc)
     assert rel <= 1e-8 and used in ("learned", "pivchol")
     if used == "learned":
         assert it <= 1.5 * it_pc
