@@ -46,25 +46,11 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const double* __restri
   }
 }
 
-// x += gamma p; r -= gamma q with gamma = sc[RHO] / sc[PQ]; flags breakdown.
-__global__ void update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                                 const double* __restrict__ q, int64_t n, const double* __restrict__ sc,
-                                 int* __restrict__ status) {
-  const double pq = sc[SC_PQ];
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 1;
-    return;
-  }
-  const double gamma = sc[SC_RHO] / pq;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(gamma, p[i], x[i]);
-    r[i] = fma(-gamma, q[i], r[i]);
-  }
-}
-
 // x += gamma p; r -= gamma q (gamma = sc[RHO] / sc[PQ]), fused with sc[RR] = r.r over the same
 // contiguous chunks and combination order as dot_kernel (bitwise the same r.r), and with the
-// end-of-iteration test of the graph-captured loop in the last CTA (pcg_check_kernel's logic).
+// end-of-iteration test of the graph-captured loop in the last CTA: count the iteration and
+// keep the WHILE node running while |r|^2 > tol^2, the residual is finite, no breakdown was
+// flagged and the iteration cap is not reached.
 // A breakdown (pq not positive and finite) flags status and leaves x, r untouched.
 __global__ void __launch_bounds__(kDotThreads) update_xr_rr_kernel(double* __restrict__ x, double* __restrict__ r,
                                                                    const double* __restrict__ p,
@@ -136,31 +122,9 @@ __global__ void __launch_bounds__(256) update_p_rho_kernel(double* __restrict__ 
   }
 }
 
-// p = z + (rho_new / rho) p ; rho <- rho_new (done by one thread after use)
-__global__ void update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
-                                const double* __restrict__ sc) {
-  const double beta = sc[SC_RHO_NEW] / sc[SC_RHO];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], z[i]);
-}
-
-__global__ void copy_scalar_kernel(double* sc, int dst, int src) { sc[dst] = sc[src]; }
-
 __global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a, double b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fma(a, x[i], b * y[i]);
-}
-
-// End-of-iteration test inside the graph-captured PCG loop: counts the
-// iteration and keeps the WHILE node running while |r|^2 > tol^2, the
-// residual is finite, no breakdown was flagged and the cap is not reached.
-__global__ void pcg_check_kernel(const double* __restrict__ sc, int64_t* __restrict__ ictl,
-                                 const int* __restrict__ status, cudaGraphConditionalHandle h) {
-  const int64_t it = ictl[IC_ITER] + 1;
-  ictl[IC_ITER] = it;
-  const double rr = sc[SC_RR];
-  const bool go = (rr > sc[SC_TOL2]) && isfinite(rr) && (it < ictl[IC_MAXIT]) && (*status == 0);
-  cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 // Entry test of a batched PCG loop: run the WHILE body only if this system
@@ -183,17 +147,9 @@ cudaError_t add_pcg_gate_node(cudaGraph_t g, cudaGraphNode_t* node, const double
   p.kernelParams = args;
   return cudaGraphAddKernelNode(node, g, nullptr, 0, &p);
 }
-void launch_pcg_check(const double* sc, int64_t* ictl, const int* status, cudaGraphConditionalHandle h,
-                      cudaStream_t st) {
-  { pcg_check_kernel<<<1, 1, 0, st>>>(sc, ictl, status, h); count_launch(); }
-}
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,
                 cudaStream_t st) {
   { dot_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(x, y, n, partial, ticket, out); count_launch(); }
-}
-void launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const double* sc,
-                      int* status, cudaStream_t st) {
-  { update_xr_kernel<<<4 * kNumSMs, 256, 0, st>>>(x, r, p, q, n, sc, status); count_launch(); }
 }
 void launch_update_xr_rr(double* x, double* r, const double* p, const double* q, int64_t n, double* sc, int* status,
                          double* partial, unsigned* ticket, int64_t* ictl, cudaGraphConditionalHandle h, int check,
@@ -202,12 +158,6 @@ void launch_update_xr_rr(double* x, double* r, const double* p, const double* q,
 }
 void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, cudaStream_t st) {
   { update_p_rho_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc, ticket); count_launch(); }
-}
-void launch_update_p(double* p, const double* z, int64_t n, const double* sc, cudaStream_t st) {
-  { update_p_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc); count_launch(); }
-}
-void launch_copy_scalar(double* sc, int dst, int src, cudaStream_t st) {
-  { copy_scalar_kernel<<<1, 1, 0, st>>>(sc, dst, src); count_launch(); }
 }
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st) {
   { axpby_kernel<<<4 * kNumSMs, 256, 0, st>>>(y, x, a, b, n); count_launch(); }

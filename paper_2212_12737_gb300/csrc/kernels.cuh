@@ -96,8 +96,6 @@ int64_t woodbury_part_size(int64_t n, int64_t k);
 // cg.cu
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,
                 cudaStream_t st);
-void launch_update_xr(double* x, double* r, const double* p, const double* q, int64_t n, const double* sc,
-                      int* status, cudaStream_t st);
 // x += gamma p; r -= gamma q; sc[RR] = r.r (dot_kernel's partition and order); check != 0: also
 // the end-of-iteration test of the graph-captured loop (conditional handle h)
 void launch_update_xr_rr(double* x, double* r, const double* p, const double* q, int64_t n, double* sc, int* status,
@@ -105,11 +103,7 @@ void launch_update_xr_rr(double* x, double* r, const double* p, const double* q,
                          cudaStream_t st);
 // p = z + (rho_new / rho) p; rho <- rho_new
 void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, cudaStream_t st);
-void launch_update_p(double* p, const double* z, int64_t n, const double* sc, cudaStream_t st);
-void launch_copy_scalar(double* sc, int dst, int src, cudaStream_t st);
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
-void launch_pcg_check(const double* sc, int64_t* ictl, const int* status, cudaGraphConditionalHandle h,
-                      cudaStream_t st);
 cudaError_t add_pcg_gate_node(cudaGraph_t g, cudaGraphNode_t* node, const double* sc, const int64_t* ictl,
                               cudaGraphConditionalHandle h);
 
