@@ -900,9 +900,7 @@ __global__ void __launch_bounds__(256) oz_backproj_kernel(const float2* __restri
                                                           const double* __restrict__ Xc, const double* __restrict__ G,
                                                           const double* __restrict__ v, int N, double lam,
                                                           int add_lambda, double* __restrict__ out) {
-  extern __shared__ double w3[];  // [D][3] terms, then U_a [D] and xc_a [D]
-  double* ua = w3 + 3 * D;
-  double* xa = ua + D;
+  extern __shared__ double w3[];  // [D][3]: first (U_ap, xc_ap, -), then the terms g_p u_p
   __shared__ double rs;
   const int64_t a = blockIdx.x;
   if (threadIdx.x < 32) {
@@ -917,26 +915,35 @@ __global__ void __launch_bounds__(256) oz_backproj_kernel(const float2* __restri
     }
     if (threadIdx.x == 0) rs = (double)h + (double)l;
   }
-  // every load of the geometry in one round: U partials, g_p, xc_p
+  // every load of the geometry in one round: U partials, xc_p and (first descriptor of each
+  // thread, the only one when D <= blockDim) g_p into registers
   const double* Ga = G + a * D * 3;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  if ((int)threadIdx.x < D) {
+    g0 = Ga[3 * threadIdx.x];
+    g1 = Ga[3 * threadIdx.x + 1];
+    g2 = Ga[3 * threadIdx.x + 2];
+  }
   for (int p = threadIdx.x; p < D; p += blockDim.x) {
     float h = 0.f, l = 0.f;
     for (int s = 0; s < nsplit; ++s) {
       const float2 u = Up[((int64_t)s * M + a) * D + p];
       df_add(h, l, u.x, u.y);
     }
-    ua[p] = (double)h + (double)l;
-    xa[p] = Xc[a * D + p];
-    w3[3 * p] = Ga[3 * p];
-    w3[3 * p + 1] = Ga[3 * p + 1];
-    w3[3 * p + 2] = Ga[3 * p + 2];
+    w3[3 * p] = (double)h + (double)l;
+    w3[3 * p + 1] = Xc[a * D + p];
   }
   __syncthreads();
   for (int p = threadIdx.x; p < D; p += blockDim.x) {
-    const double u = ua[p] - rs * xa[p];
-    w3[3 * p] *= u;
-    w3[3 * p + 1] *= u;
-    w3[3 * p + 2] *= u;
+    const double u = w3[3 * p] - rs * w3[3 * p + 1];
+    if (p >= (int)blockDim.x) {  // later descriptors of this thread (D > blockDim)
+      g0 = Ga[3 * p];
+      g1 = Ga[3 * p + 1];
+      g2 = Ga[3 * p + 2];
+    }
+    w3[3 * p] = g0 * u;
+    w3[3 * p + 1] = g1 * u;
+    w3[3 * p + 2] = g2 * u;
   }
   __syncthreads();
   const int B = 3 * N;
@@ -1088,7 +1095,7 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
   const int64_t nch = oz.A2.nchunks;
   OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st));
   OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + nch * M * D, D, M * D, oz.err, st));
-  const size_t smem = 5 * (size_t)D * sizeof(double);
+  const size_t smem = 3 * (size_t)D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   { oz_backproj_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, (int)(2 * nch), M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }

@@ -646,6 +646,8 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
   // n % 4 == 0: the Schur sums run through the TMA-staged pass (one partial per row)
   WsPlan plan;
   if (a.err) ws_plan(plan, L, a.n, a.k);
+  // one argmax partial per CTA: the staged kernel's grid-stride loop takes any grid size
+  if (plan.grid > kArgBlocks) plan.grid = kArgBlocks;
   // step 0's pivot
   { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(0, a.n, 1, a.d, a.perm, a.chosen, a.pivots, nullptr,
                                                        a.ps, a.part, a.ticket, a.posof); count_launch(); }

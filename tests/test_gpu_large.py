@@ -31,7 +31,8 @@ def sampled(big):
     return v, rows, ref
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-12), ("tf32", 5e-3), ("bf16", 5e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-12), ("ozaki", 1e-12), ("tf32", 5e-3),
+                                      ("bf16", 5e-2)])
 def test_full_size_matvec_on_sampled_blocks(big, sampled, prec, tol):
     w = big
     v, rows, ref = sampled

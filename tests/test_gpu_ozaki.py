@@ -72,8 +72,11 @@ def test_sliced_gemm_row_scales_and_zero_rows():
 
 
 @pytest.mark.parametrize("name,N,M,sigma", [("ragged_N7_M150", 7, 150, 3.0), ("ethanol9_m200", 9, 200, 10.0),
-                                            ("aspirin21_m1000", 21, 1000, 20.0)])
+                                            ("wide_N30_M64", 30, 64, 15.0), ("aspirin21_m1000", 21, 1000, 20.0)])
 def test_ozaki_matvec_is_fp64_class(name, N, M, sigma):
+    """D = N(N - 1)/2 up to 435: one and several 256-entry chunks per descriptor row (the
+    projection fused with the slicing of W, or not), one or two descriptors per thread in
+    the back-projection."""
     if name.startswith("aspirin"):
         R = synth.workload("aspirin21_m1000").R
     else:
