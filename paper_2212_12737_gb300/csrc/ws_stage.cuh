@@ -13,15 +13,18 @@ namespace gdml {
 
 // ---------------------------------------------------------------------------
 // TMA-staged passes.  One producer thread keeps a ring of 16 KB column tiles of
-// L in flight (cp.async.bulk.tensor with an L2 evict-first hint, zero fill past
-// n and k); eight consumer warps do the double-float arithmetic out of shared
-// memory.  The bytes in flight per SM then no longer depend on how many loads
-// each warp holds in registers.  Rows are cut into chunks of RC = 128 NT rows
+// L in flight (cp.async.bulk.tensor, zero fill past n and k; an L2 evict-first
+// hint where L is streamed once: the apply's passes, and the Schur sums once the
+// columns no longer fit in L2); eight consumer warps do the double-float
+// arithmetic out of shared memory.  The bytes in flight per SM then no longer
+// depend on how many loads each warp holds in registers.
+// The L u pass and the Schur sums cut the rows into chunks of RC = 128 NT rows
 // (NT = 1 or 2, so every lane is busy); CTA b takes chunks b, b + grid, ... and
-// streams all k columns of each.  A tile is RC rows x 32 / NT columns, the same
-// shape for both passes; warp w takes tile columns w CPW .. w CPW + CPW - 1
-// (CPW = 4 / NT) and lane l rows 4 l + 128 t + e (t < NT, e < 4): one float4
-// per column and t, 16 products per lane and tile.
+// streams all k columns of each.  A tile is RC rows x 32 / NT columns; warp w
+// takes tile columns w CPW .. w CPW + CPW - 1 (CPW = 4 / NT) and lane l rows
+// 4 l + 128 t + e (t < NT, e < 4): one float4 per column and t, 16 products per
+// lane and tile.  The L^T r pass uses 256-row x 16-column tiles over larger row
+// units (see its kernel).
 //
 // Sums are double-float with the low part accumulated lazily: each exact
 // product enters the high word through TwoSum and its rounding errors go
