@@ -234,3 +234,24 @@ def test_zero_rhs_and_iteration_cap_and_bad_args():
             ctx.precond_build("uniform", bad)
         assert e.value.name == "ERR_ARG"
     ctx.destroy()
+
+
+@pytest.mark.parametrize("prec", ["ozaki"])
+def test_df_pivoted_cholesky_at_full_size_matches_oracle(prec):
+    """The DF64/OZAKI Algorithm 1 at n = 63,000: 256-row chunks of the fused Schur + finish
+    pass.  L is stored in FP32 there, which perturbs the residual diagonal by ~1e-7 of its
+    scale: pivots must agree up to a first divergence at a near-tie of that size, and the
+    trace to 1e-6 up to it."""
+    w = synth.workload("aspirin21_m1000")
+    k = 48
+    ctx = gdml.kernel_setup(dev(w.R), w.sigma, w.lam, precision=prec)
+    piv, tr = ctx.precond_build("pivchol", k, pivots=True, trace=True)
+    get_col = ok.column_getter(w.R, w.sigma)
+    L, rpiv, rtr, diags = oracle_pivchol_with_diags(get_col, ok.force_kernel_diag(w.R, w.sigma), k)
+    gp = piv.cpu().numpy()
+    m = len(rpiv) if np.array_equal(gp, rpiv) else int(np.argmax(gp != rpiv))
+    if m < len(rpiv):
+        assert abs(diags[m][gp[m]] - diags[m][rpiv[m]]) <= 1e-6 * diags[0].max(), f"pivot {m} differs"
+    assert m >= 8
+    np.testing.assert_allclose(tr.cpu().numpy()[:m], rtr[:m], rtol=1e-6, atol=1e-9 * rtr[0])
+    ctx.destroy()
