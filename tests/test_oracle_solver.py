@@ -45,7 +45,7 @@ def test_pcg_iterates_match_scipy_cg(system):
 
 
 def test_pcg_with_p_equal_k_lambda_converges_in_one_step(system):
-    """App. A.1: a fully flattened spectrum needs a single search direction."""
+    """App. A.1: when all eigenvalues are equal, CG converges after one step."""
     R, y, K = system
     lam = 1e-4
     Kl = K + lam * np.eye(K.shape[0])
