@@ -76,7 +76,7 @@ struct WsPlan {
   CUtensorMap mapT;  // box 256 rows x 16 columns
 };
 // fills plan for L (plan.ok = false where the staged passes do not apply: n % 4 != 0, k = 0,
-// or the driver rejects the map); rows: 128 or 256 to force the chunk size, else automatic
+// or the CUDA driver rejects the map); rows: 128 or 256 to force the chunk size, else automatic
 void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows = 0);
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                        const double* r, double* z, double* part, double* t, float2* rs, const WsPlan* plan,

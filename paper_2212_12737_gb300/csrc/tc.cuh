@@ -48,13 +48,13 @@ gdml_status tc_check(TcMatvec& tc, cudaStream_t st);
 void tc_destroy(TcMatvec& tc);
 
 // 2D K-major TMA map with 128-byte swizzle: inner dim K (elements), outer dim rows, row stride
-// ld_elems; box = one 128-byte span of K x box_rows rows.  False if the driver rejects it.
+// ld_elems; box = one 128-byte span of K x box_rows rows.  False if the CUDA driver rejects it.
 bool make_kmajor_map(CUtensorMap* m, const void* base, bool bf16, uint64_t K, uint64_t rows, uint64_t ld_elems,
                      uint32_t box_rows);
 
 // 2D FP32 TMA map without swizzle: inner dim (contiguous elements), outer dim, outer stride
 // ld_elems (ld_elems * 4 a multiple of 16 bytes); box = box_inner x box_outer elements,
-// zero fill outside the tensor.  False if the driver rejects it.
+// zero fill outside the tensor.  False if the CUDA driver rejects it.
 bool make_f32_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
                   uint32_t box_inner, uint32_t box_outer);
 
