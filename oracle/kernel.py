@@ -176,13 +176,3 @@ def matvec_rows(R: np.ndarray, sigma: float, v: np.ndarray, rows, lam: float = 0
         u = (S * (1.0 + c * r)) @ W - c * c * ((S * proj) @ d)
         out[t] = Jac[a].T @ u + lam * V[a]
     return out
-
-
-def descriptor_distances(R: np.ndarray) -> np.ndarray:
-    """r_ab = |x_a - x_b| computed directly from differences (M x M)."""
-    X, _ = descriptor(R)
-    out = np.empty((X.shape[0], X.shape[0]))
-    for a in range(X.shape[0]):
-        d = X[a][None, :] - X
-        out[a] = np.sqrt(np.sum(d * d, axis=1))
-    return out
