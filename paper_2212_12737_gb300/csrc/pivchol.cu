@@ -688,7 +688,7 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
   }
 }
 
-// ---------------------------------------------------------------- host side
+// ---------------------------------------------------------------- host loop (FP64 and FP32 sums)
 template <typename TL>
 void pivchol_run(const PivCholArgs& a, TL* L, cudaStream_t st) {
   for (int64_t m = 0; m < a.k; ++m) {
