@@ -24,7 +24,8 @@ def _lib():
     gdml.load()
 
 
-@pytest.mark.parametrize("name,N,M,sigma", [("ragged_N7_M150", 7, 150, 3.0), ("ethanol9_m200", 9, 200, 10.0),
+@pytest.mark.parametrize("name,N,M,sigma", [("tiny_N5_M3", 5, 3, 1.0), ("single_geometry_N6_M1", 6, 1, 2.0),
+                                            ("two_atoms_N2_M7", 2, 7, 1.5), ("ragged_N7_M150", 7, 150, 3.0), ("ethanol9_m200", 9, 200, 10.0),
                                             ("aspirin21_m1000", 21, 1000, 20.0)])
 def test_df64_matvec_is_fp64_class(name, N, M, sigma):
     if name.startswith("aspirin"):

@@ -71,7 +71,8 @@ def test_sliced_gemm_row_scales_and_zero_rows():
     assert rel.max() <= 1e-14
 
 
-@pytest.mark.parametrize("name,N,M,sigma", [("ragged_N7_M150", 7, 150, 3.0), ("ethanol9_m200", 9, 200, 10.0),
+@pytest.mark.parametrize("name,N,M,sigma", [("tiny_N5_M3", 5, 3, 1.0), ("single_geometry_N6_M1", 6, 1, 2.0),
+                                            ("two_atoms_N2_M7", 2, 7, 1.5), ("ragged_N7_M150", 7, 150, 3.0), ("ethanol9_m200", 9, 200, 10.0),
                                             ("wide_N30_M64", 30, 64, 15.0), ("aspirin21_m1000", 21, 1000, 20.0)])
 def test_ozaki_matvec_is_fp64_class(name, N, M, sigma):
     """D = N(N - 1)/2 up to 435: one and several 256-entry chunks per descriptor row (the
