@@ -222,9 +222,10 @@ def test_full_rank_nystrom_converges_in_few_iterations(prec, max_iters):
     ctx.destroy()
 
 
-def test_zero_rhs_and_iteration_cap_and_bad_args():
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_zero_rhs_and_iteration_cap_and_bad_args(prec):
     w = synth.workload("ethanol9_m200", M=20)
-    ctx = gdml.kernel_setup(dev(w.R), w.sigma, w.lam)
+    ctx = gdml.kernel_setup(dev(w.R), w.sigma, w.lam, precision=prec)
     alpha, iters, rel, _ = ctx.pcg_solve(torch.zeros(w.n, dtype=torch.float64, device="cuda"))
     assert iters == 0 and rel == 0 and float(alpha.abs().max()) == 0.0
     with pytest.raises(gdml.GdmlError) as e:
