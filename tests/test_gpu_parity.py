@@ -127,10 +127,12 @@ def test_pivoted_cholesky_pivots_and_trace_match_oracle(name, k):
     ctx.destroy()
 
 
-def test_rls_selection_matches_oracle():
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_rls_selection_matches_oracle(prec):
+    """The scores come from the FP64 Nystrom factor of the pilot set in every form."""
     w = synth.workload("ethanol9_m200")
     k = 100
-    ctx = gdml.kernel_setup(dev(w.R), w.sigma, w.lam)
+    ctx = gdml.kernel_setup(dev(w.R), w.sigma, w.lam, precision=prec)
     piv, _ = ctx.precond_build("rls", k, seed=3, pivots=True)
     K = ok.force_kernel_dense(w.R, w.sigma)
     S, tau = op.select_rls(lambda idx: K[:, idx], w.n, k, w.lam, 3)
