@@ -315,6 +315,17 @@ def run_learned(args):
     sc.destroy()
 
 
+def max_over_ranks(t: float, world: int, device) -> float:
+    """The job takes as long as its slowest rank: all-reduce MAX of t over the process group."""
+    if world == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -370,11 +381,7 @@ def run_gpu(args):
                 torch.cuda.synchronize(dev)
                 ts.append(s.elapsed_time(e) / 1e3)
         barrier()
-        t = sum(ts) / len(ts)
-        if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(sum(ts) / len(ts), world, dev)
         return t, info, clk.summary()
 
     # headline: device-resident inputs
