@@ -94,8 +94,8 @@ gdml_status gdml_kernel_setup(gdml_ctx** ctx, const double* R_dev, int64_t M, in
  * with FP32 accumulation, result stored as double; DF64: double-float
  * contractions; OZAKI: sliced-BF16 tensor-core contractions).  v_dev and out_dev must
  * not overlap.  The matvec is matrix-free: w_b = J_b v_b, u_a = sum_b H_ab w_b,
- * (K v)_a = J_a^T u_a (Sec. 2.1, "only relies on evaluations of
- * matrix-vector products"). */
+ * (K v)_a = J_a^T u_a (Sec. 2.1: CG touches K only through such products,
+ * so K is never formed). */
 gdml_status gdml_matvec(gdml_ctx* ctx, const double* v_dev, double* out_dev, int32_t add_lambda);
 
 /* Same as gdml_matvec but always in FP64, whatever the context precision. */
