@@ -430,7 +430,7 @@ gdml_status pcg_body(gdml_ctx* c, double* x, bool fp64_mv, cudaGraphConditionalH
 }
 
 // Capture the PCG loop once as a graph with a conditional WHILE node whose
-// body is one iteration; the check kernel ends the loop on the device.
+// body is one iteration; the fused x, r update (with r.r) ends the loop on the device.
 gdml_status pcg_graph(gdml_ctx* c, double* x, bool fp64_mv, cudaGraphExec_t* out) {
   const int slot = fp64_mv && c->precision != GDML_FP64 ? 1 : 0;
   if (c->gexec[slot]) {
