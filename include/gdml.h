@@ -117,6 +117,17 @@ gdml_status gdml_matvec_fp64(gdml_ctx* ctx, const double* v_dev, double* out_dev
 gdml_status gdml_precond_build(gdml_ctx* ctx, int32_t method, int64_t k, uint64_t seed,
                                int64_t* pivots_dev, double* resid_trace_dev);
 
+/* Number of inducing columns k for gdml_precond_build by the rule of thumb of
+ * Sec. 4.3 (Eqs. 7-8): the integer k in [1, n] that minimises the runtime model
+ *   (k_min / k)^m + (k / n)^2,
+ * a PCG cost that falls as a power law in k plus a k^2 n build cost.  A tie
+ * between two integers goes to the smaller k.  m and k_min are the molecule's
+ * fitted parameters (Table 1); the default row is m = 1, k_min = 100.
+ * Host arithmetic only (no context, no device); *k_out is a host int64.
+ * Errors: GDML_ERR_ARG unless n >= 1, m and k_min finite and > 0, k_out != NULL
+ * (message through gdml_last_error(NULL)). */
+gdml_status gdml_rule_of_thumb_k(int64_t n, double m, double k_min, int64_t* k_out);
+
 /* Preconditioner from k columns sampled without replacement with weights
  * w_i = max(score_a, 0) * K_ii for column i of geometry a (keys -ln(u_i)/w_i,
  * Philox stream 3), then the Nystrom factor and Woodbury core exactly as for
@@ -233,8 +244,9 @@ gdml_status gdml_scorer_grad(gdml_scorer* s, const double* X_dev, const double* 
                              float* grad_dev);
 void gdml_scorer_destroy(gdml_scorer* s);
 
-/* Message describing the last error on ctx (or the last failed setup when
- * ctx is NULL).  Never NULL; valid until the next call on the context. */
+/* Message describing the last error on ctx (or, when ctx is NULL, the last
+ * failed call without a context on this thread: setup, rule_of_thumb_k).
+ * Never NULL; valid until the next call on the context. */
 const char* gdml_last_error(const gdml_ctx* ctx);
 
 /* Release all device memory owned by ctx (NULL is allowed). */

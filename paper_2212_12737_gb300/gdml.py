@@ -29,7 +29,13 @@ EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond
            "gdml_launch_count", "gdml_matvec_noalloc", "gdml_pcg_solve_batched", "gdml_autotune",
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
-           "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy"]
+           "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy", "gdml_rule_of_thumb_k"]
+
+# Table 1 (Sec. 4.3): molecule -> (m, k_min) of the rule of thumb, fitted at n = 31k;
+# "default" is the row for molecules without fitted parameters.
+ROT_PARAMS = {"default": (1.0, 100.0), "ethanol": (0.87, 10.0), "uracil": (1.07, 32.0), "toluene": (1.01, 44.0),
+              "aspirin": (1.14, 236.0), "azobenzene": (1.02, 62.0), "catcher": (1.02, 316.0),
+              "nanotube": (0.73, 89.0)}
 
 
 class GdmlError(RuntimeError):
@@ -83,6 +89,7 @@ def load() -> ctypes.CDLL:
         "gdml_scorer_params": [P, P, I32, ctypes.POINTER(I64)],
         "gdml_scorer_grad": [P, P, P, I64, ctypes.POINTER(D), P],
         "gdml_scorer_destroy": [P],
+        "gdml_rule_of_thumb_k": [I64, D, D, ctypes.POINTER(I64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -94,6 +101,19 @@ def load() -> ctypes.CDLL:
     lib.gdml_launch_count.restype = ctypes.c_int64
     _lib = lib
     return lib
+
+
+def rule_of_thumb_k(n: int, molecule: str = "default", m: float | None = None, k_min: float | None = None) -> int:
+    """Inducing-column count for precond_build by the rule of thumb (Sec. 4.3, Eqs. 7-8):
+    Table 1's (m, k_min) for ``molecule``, either overridden by ``m`` / ``k_min``."""
+    lib = load()
+    m0, k0 = ROT_PARAMS[molecule]
+    out = ctypes.c_int64()
+    st = lib.gdml_rule_of_thumb_k(int(n), float(m0 if m is None else m), float(k0 if k_min is None else k_min),
+                                  ctypes.byref(out))
+    if st != 0:
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+    return out.value
 
 
 def _ptr(t: torch.Tensor | None):
