@@ -8,7 +8,8 @@ never does, and shares no code with it.
 
 Modules
 -------
-kernel    descriptor, Jacobian, Matern-5/2 force kernel (dense and matrix-free)
+kernel    descriptor, Jacobian, Matern-5/2 force kernel (dense and matrix-free),
+          force prediction for query geometries from alpha
 philox    Philox4x32-10 counter-based generator (Salmon et al., SC'11)
 precond   column selection (uniform, ridge leverage, pivoted Cholesky / Alg. 1),
           Nystrom factor (Eq. 5), Woodbury core and apply (Eqs. 3-4)

@@ -176,3 +176,27 @@ def matvec_rows(R: np.ndarray, sigma: float, v: np.ndarray, rows, lam: float = 0
         u = (S * (1.0 + c * r)) @ W - c * c * ((S * proj) @ d)
         out[t] = Jac[a].T @ u + lam * V[a]
     return out
+
+
+def predict_forces(R_query: np.ndarray, R: np.ndarray, sigma: float, alpha: np.ndarray) -> np.ndarray:
+    """Forces the trained model predicts for query geometries (Sec. 2.1: queried at a cost
+    linear in the training set): f_q = sum_b K(q, b) alpha_b with the force-kernel block
+    K(q, b) = J_q^T H(x_q, x_b) J_b of the query q against training geometry b.
+
+    R_query: (Q, N, 3); R: (M, N, 3) training geometries; alpha: length 3 N M, the
+    solution of Eq. 1.  Returns (Q, N, 3).
+    """
+    R_query = np.asarray(R_query, dtype=np.float64)
+    M, N, _ = R.shape
+    Q = R_query.shape[0]
+    B = 3 * N
+    Xq, _ = descriptor(R_query)
+    Jq = jacobian(R_query)
+    X, _ = descriptor(R)
+    Jb = jacobian(R)
+    A = np.asarray(alpha, dtype=np.float64).reshape(M, B)
+    out = np.zeros((Q, B))
+    for q in range(Q):
+        for b in range(M):
+            out[q] += Jq[q].T @ (hessian_block(Xq[q], X[b], sigma) @ (Jb[b] @ A[b]))
+    return out.reshape(Q, N, 3)
