@@ -101,6 +101,20 @@ gdml_status gdml_matvec(gdml_ctx* ctx, const double* v_dev, double* out_dev, int
 /* Same as gdml_matvec but always in FP64, whatever the context precision. */
 gdml_status gdml_matvec_fp64(gdml_ctx* ctx, const double* v_dev, double* out_dev, int32_t add_lambda);
 
+/* Forces the trained model predicts for Q query geometries of the context's molecule
+ * (Sec. 2.1: predictions cost time linear in the training set):
+ *   f_q = sum_b J_q^T H(x_q, x_b) J_b alpha_b,
+ * the force-kernel blocks of the queries against the M training geometries applied to
+ * alpha, the solution of Eq. 1 (for example from gdml_pcg_solve).  Computed in FP64 in
+ * every context precision.  No lambda term: at a training geometry f = (K alpha)_q.
+ *  R_query_dev: Q*N*3 doubles, layout as R_dev of gdml_kernel_setup (same N).
+ *  alpha_dev: n = 3 N M doubles.  f_dev: Q*N*3 doubles (layout as R_query_dev),
+ *  must not overlap alpha_dev.  1 <= Q <= 2^20; temporary device memory of about
+ *  8 Q (4 M + 6 D) bytes is allocated and freed inside the call.
+ * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA. */
+gdml_status gdml_predict_forces(gdml_ctx* ctx, const double* R_query_dev, int64_t Q, const double* alpha_dev,
+                                double* f_dev);
+
 /* Build the Nystrom-type preconditioner (Eqs. 3-5, Sec. 3, Alg. 1).
  *  method: gdml_select; 1 <= k <= min(n, 16384); seed: Philox4x32-10 key
  *  (uniform: counter (i, 0), rls pilot: (i, 1), rls sampling: (i, 2)).

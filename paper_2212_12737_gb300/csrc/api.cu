@@ -636,6 +636,38 @@ gdml_status gdml_matvec_fp64(gdml_ctx* c, const double* v, double* out, int32_t 
   return matvec_fp64(c, v, out, add_lambda ? 1 : 0);
 }
 
+// f_q = sum_b J_q^T H(x_q, x_b) J_b alpha_b: the FP64 matvec's steps with query rows against
+// the training columns (T = Xq_c W^T is Q x M, U = [A | beta] [W ; Xc] is Q x D).
+gdml_status gdml_predict_forces(gdml_ctx* c, const double* R_query, int64_t Q, const double* alpha, double* f) {
+  TRY(validate(c));
+  if (!R_query || !alpha || !f || alpha == f) return ctx_fail(c, GDML_ERR_ARG, "predict_forces: bad pointers");
+  if (Q < 1 || Q > ((int64_t)1 << 20)) return ctx_fail(c, GDML_ERR_ARG, "predict_forces: need 1 <= Q <= 2^20");
+  const int64_t M = c->M;
+  const int N = c->N, D = c->D;
+  cudaStream_t st = c->st;
+  Scratch s{c, {}};
+  double *Xq = nullptr, *Gq = nullptr, *Xqc = nullptr, *Sq = nullptr, *Tq = nullptr, *Pq = nullptr, *Uq = nullptr,
+         *rs = nullptr;
+  TRY(s.get(&Xq, (size_t)(Q * D)));
+  TRY(s.get(&Gq, (size_t)(Q * D * 3)));
+  TRY(s.get(&Xqc, (size_t)(Q * D)));
+  TRY(s.get(&Sq, (size_t)(Q * M)));
+  TRY(s.get(&Tq, (size_t)(Q * M)));
+  TRY(s.get(&Pq, (size_t)(Q * 2 * M)));
+  TRY(s.get(&Uq, (size_t)(Q * D)));
+  TRY(s.get(&rs, (size_t)Q));
+  double* W = c->V64;  // [W ; Xc]: W_b = J_b alpha_b over the training set
+  launch_desc_jac(R_query, Q, N, D, Xq, Gq, st);
+  launch_center_like(Xq, Q, D, c->X, c->Xc(), Xqc, st);
+  launch_dist_tab_cross(Xq, Q, c->X, M, D, c->c, Sq, Pq, 2 * M, st);
+  launch_proj(c->G, c->Xc(), alpha, M, N, D, W, D, c->tb, st);
+  launch_dgemm<double, double>(true, Q, M, D, 1.0, Xqc, D, W, D, 0.0, Tq, M, false, st);
+  launch_beta_rows(Tq, Sq, c->tb, Q, M, c->c, Pq + M, 2 * M, rs, st);
+  launch_dgemm<double, double>(false, Q, D, 2 * M, 1.0, Pq, 2 * M, c->V64, D, 0.0, Uq, D, false, st);
+  launch_backproj<double>(Uq, D, 1, Q * D, rs, Xqc, Gq, nullptr, Q, N, D, 0.0, 0, f, st);
+  return check_launch(c, "predict_forces");
+}
+
 static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, uint64_t seed, int64_t* pivots_dev,
                                       double* resid_trace_dev, const double* geometry_scores) {
   TRY(validate(c));

@@ -9,6 +9,8 @@
 //  beta       beta_ab = c^2 S_ab (T_ab - t_b), T = Xc W^T; rowsum_a = sum_b beta_ab
 //  backproj   (K v)_a = J_a^T u'_a with u'_a = U_a - rowsum_a xc_a, plus lambda v
 //  kcol       columns K[:, c] = J_a^T H_ab J_b e_l for a list of column indices c = b*3N + l
+//  dist_tab_cross, center_like   the same tables for query geometries against the training
+//             set, and query descriptors centred on the training centre (force prediction)
 #include <algorithm>
 
 #include "common.cuh"
@@ -90,6 +92,56 @@ __global__ void dist_tab_kernel(const double* __restrict__ X, int64_t M, int D, 
       A[a * ldA + b] = s * (1.0 + c * r);
     }
   }
+}
+
+// S_qb, A_qb from r_qb = |x_q - x_b| for query rows x_q against training rows x_b, tiled as
+// dist_tab_kernel (32 x 32 outputs per CTA); S has row stride M, A row stride ldA.
+__global__ void dist_tab_cross_kernel(const double* __restrict__ Xq, int64_t Q, const double* __restrict__ X,
+                                      int64_t M, int D, double c, double* __restrict__ S, double* __restrict__ A,
+                                      int64_t ldA) {
+  __shared__ double xa[32][33], xb[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty 0..7
+  const int64_t a0 = (int64_t)blockIdx.y * 32, b0 = (int64_t)blockIdx.x * 32;
+  double acc[4] = {0, 0, 0, 0};
+  for (int p0 = 0; p0 < D; p0 += 32) {
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int64_t ra = a0 + rr, rb = b0 + rr;
+      const int p = p0 + tx;
+      xa[rr][tx] = (ra < Q && p < D) ? Xq[ra * D + p] : 0.0;
+      xb[rr][tx] = (rb < M && p < D) ? X[rb * D + p] : 0.0;
+    }
+    __syncthreads();
+    for (int q = 0; q < 32; ++q) {
+      const double vb = xb[tx][q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double d = xa[ty + 8 * u][q] - vb;
+        acc[u] = fma(d, d, acc[u]);
+      }
+    }
+    __syncthreads();
+  }
+  const double c2_3 = c * c / 3.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t a = a0 + ty + 8 * u, b = b0 + tx;
+    if (a < Q && b < M) {
+      const double r = sqrt(acc[u]);
+      const double s = c2_3 * exp(-c * r);
+      S[a * M + b] = s;
+      A[a * ldA + b] = s * (1.0 + c * r);
+    }
+  }
+}
+
+// Xqc = Xq - mu, mu = X_0 - Xc_0: query descriptors centred on the training set's centre,
+// so that (xq - mu) . w_b - xc_b . w_b = (x_q - x_b) . w_b
+__global__ void center_like_kernel(const double* __restrict__ Xq, int64_t Q, int D, const double* __restrict__ X,
+                                   const double* __restrict__ Xc, double* __restrict__ Xqc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= Q * D) return;
+  const int p = (int)(t % D);
+  Xqc[t] = Xq[t] - (X[p] - Xc[p]);
 }
 
 __global__ void kdiag_kernel(const double* __restrict__ G, int64_t M, int N, int D, double c2_3,
@@ -538,6 +590,19 @@ void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, 
 void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
                  int64_t ldP, double* rowsum, cudaStream_t st) {
   { beta_kernel<256><<<(unsigned)M, 256, 0, st>>>(T, S, t, M, c * c, Pb, ldP, rowsum); count_launch(); }
+}
+void launch_beta_rows(const double* T, const double* S, const double* t, int64_t rows, int64_t M, double c,
+                      double* Pb, int64_t ldP, double* rowsum, cudaStream_t st) {
+  { beta_kernel<256><<<(unsigned)rows, 256, 0, st>>>(T, S, t, M, c * c, Pb, ldP, rowsum); count_launch(); }
+}
+void launch_dist_tab_cross(const double* Xq, int64_t Q, const double* X, int64_t M, int D, double c, double* S,
+                           double* A, int64_t ldA, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(M, 32), (unsigned)cdiv(Q, 32));
+  { dist_tab_cross_kernel<<<grid, 256, 0, st>>>(Xq, Q, X, M, D, c, S, A, ldA); count_launch(); }
+}
+void launch_center_like(const double* Xq, int64_t Q, int D, const double* X, const double* Xc, double* Xqc,
+                        cudaStream_t st) {
+  { center_like_kernel<<<(unsigned)cdiv(Q * D, 256), 256, 0, st>>>(Xq, Q, D, X, Xc, Xqc); count_launch(); }
 }
 template <typename TU>
 void launch_backproj(const TU* U, int64_t ldU, int splits, int64_t split_stride, const double* rowsum,

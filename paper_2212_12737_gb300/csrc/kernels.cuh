@@ -32,6 +32,14 @@ void launch_proj(const double* G, const double* Xc, const double* v, int64_t M, 
                  int64_t ldW, double* t, cudaStream_t st);
 void launch_beta(const double* T, const double* S, const double* t, int64_t M, double c, double* Pb,
                  int64_t ldP, double* rowsum, cudaStream_t st);
+// beta for `rows` rows of T, S (row stride M) against the M training columns
+void launch_beta_rows(const double* T, const double* S, const double* t, int64_t rows, int64_t M, double c,
+                      double* Pb, int64_t ldP, double* rowsum, cudaStream_t st);
+// force prediction: query-vs-training S, A tables, and query descriptors on the training centre
+void launch_dist_tab_cross(const double* Xq, int64_t Q, const double* X, int64_t M, int D, double c, double* S,
+                           double* A, int64_t ldA, cudaStream_t st);
+void launch_center_like(const double* Xq, int64_t Q, int D, const double* X, const double* Xc, double* Xqc,
+                        cudaStream_t st);
 template <typename TU>
 void launch_backproj(const TU* U, int64_t ldU, int splits, int64_t split_stride, const double* rowsum,
                      const double* Xc, const double* G, const double* v, int64_t M, int N, int D, double lam,

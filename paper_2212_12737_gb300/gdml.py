@@ -29,7 +29,8 @@ EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond
            "gdml_launch_count", "gdml_matvec_noalloc", "gdml_pcg_solve_batched", "gdml_autotune",
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
-           "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy", "gdml_rule_of_thumb_k"]
+           "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy", "gdml_rule_of_thumb_k",
+           "gdml_predict_forces"]
 
 # Table 1 (Sec. 4.3): molecule -> (m, k_min) of the rule of thumb, fitted at n = 31k;
 # "default" is the row for molecules without fitted parameters.
@@ -90,6 +91,7 @@ def load() -> ctypes.CDLL:
         "gdml_scorer_grad": [P, P, P, I64, ctypes.POINTER(D), P],
         "gdml_scorer_destroy": [P],
         "gdml_rule_of_thumb_k": [I64, D, D, ctypes.POINTER(I64)],
+        "gdml_predict_forces": [P, P, I64, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -159,6 +161,19 @@ class Context:
     def matvec_fp64(self, v: torch.Tensor, out: torch.Tensor | None = None, add_lambda: bool = True) -> torch.Tensor:
         out = self._vec(out)
         self._check(load().gdml_matvec_fp64(self._h, _ptr(v), _ptr(out), int(add_lambda)))
+        return out
+
+    def predict_forces(self, R_query: torch.Tensor, alpha: torch.Tensor,
+                       out: torch.Tensor | None = None) -> torch.Tensor:
+        """Forces (Q, N, 3) the model with coefficients alpha predicts for query geometries (Q, N, 3)."""
+        if R_query.dtype != torch.float64 or R_query.dim() != 3 or tuple(R_query.shape[1:]) != (self.N, 3):
+            raise ValueError(f"R_query must be a float64 CUDA tensor of shape (Q, {self.N}, 3)")
+        if alpha.dtype != torch.float64 or alpha.numel() != self.n:
+            raise ValueError(f"alpha must be {self.n} float64 values")
+        R_query = R_query.contiguous()
+        Q = int(R_query.shape[0])
+        out = torch.empty((Q, self.N, 3), dtype=torch.float64, device=self.device) if out is None else out
+        self._check(load().gdml_predict_forces(self._h, _ptr(R_query), Q, _ptr(alpha), _ptr(out)))
         return out
 
     def precond_build(self, method: str, k: int, seed: int = 2, pivots: bool = False, trace: bool = False):
