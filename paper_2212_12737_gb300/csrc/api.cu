@@ -211,11 +211,6 @@ __global__ void col_sqnorm_kernel(const double* __restrict__ Z, int64_t k, int64
   out[i] = s;
 }
 
-__global__ void fill_kernel(double* p, int64_t n, double v) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
-}
-
 gdml_status read_status(gdml_ctx* c, int* h) {
   CTRY(c, cudaMemcpyAsync(h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CTRY(c, cudaStreamSynchronize(c->st));
