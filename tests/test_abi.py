@@ -47,3 +47,14 @@ def test_library_loads_and_binding_knows_every_symbol(lib_path):
         assert hasattr(lib, s)
     from paper_2212_12737_gb300 import gdml
     assert sorted(gdml.EXPORTS) == declared_symbols()
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the shared library absent, the first call raises."""
+    from paper_2212_12737_gb300 import gdml
+    monkeypatch.setattr(gdml, "_lib", None)
+    monkeypatch.setattr(gdml, "_LIB_PATH", str(tmp_path / "libgdml.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        gdml.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        gdml.rule_of_thumb_k(1000)
