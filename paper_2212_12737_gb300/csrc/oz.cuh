@@ -10,7 +10,7 @@
 //   * every operand row is cut into chunks of KC = 256 entries along K; within a
 //     chunk the row is scaled by a power of two 2^e (e from the chunk's largest
 //     magnitude) and written as  x = 2^e * sum_{i<7} s_i 2^{-7(i+1)}  with integer
-//     slices |s_1| <= 128, |s_i| <= 65 (i > 1), each exact in BF16 (49 bits in all);
+//     slices |s_1| <= 128, |s_i| <= 64 (i > 1), each exact in BF16 (49 bits in all);
 //   * the product of one slice pair is an integer below 2^14, so the FP32
 //     tensor-core accumulation of one chunk is exact: every level sum
 //     sum_{i+j=l} s_i t_j over 256 K entries stays below 2^24;
