@@ -11,7 +11,7 @@
 //     chunk the row is scaled by a power of two 2^e (e from the chunk's largest
 //     magnitude) and written as  x = 2^e * sum_{i<7} s_i 2^{-7(i+1)}  with integer
 //     slices |s_1| <= 128, |s_i| <= 64 (i > 1), each exact in BF16 (49 bits in all);
-//   * the product of one slice pair is an integer below 2^14, so the FP32
+//   * the product of one slice pair is an integer of magnitude at most 2^14, so the FP32
 //     tensor-core accumulation of one chunk is exact: every level sum
 //     sum_{i+j=l} s_i t_j over 256 K entries stays below 2^24;
 //   * slice pairs with i + j <= 8 (1-based) are kept, one TMEM accumulator per
