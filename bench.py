@@ -546,7 +546,7 @@ def run_gpu(args):
                        "precision": args.precision, "select": w.select, "k": k, "n": n,
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps (L2 129 MB); L_k working set "
-                             f"{n * k * 8 / 1e9:.2f} GB"},
+                             f"{n * k * (4 if args.precision in ('df64', 'ozaki') else 8) / 1e9:.2f} GB"},
             "solve": {"iters": iters, "relres": rel, "outer_steps": outer, "converged": rel <= RTOL},
             "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(R_h.numel() * 8 + y_h.numel() * 8),
                     "d2h_bytes_per_step": int(n * 8)},
