@@ -26,7 +26,7 @@ import numpy as np
 
 
 def pair_index(N: int) -> tuple[np.ndarray, np.ndarray]:
-    """Atom indices (i, j), i > j, of descriptor entry p = i(i-1)/2 + j."""
+    """Atom indices (i, j), i > j, of descriptor entry p = i(i-1)/2 + j (Sec. 2.1 descriptor)."""
     I, J = [], []
     for i in range(N):
         for j in range(i):
@@ -36,7 +36,7 @@ def pair_index(N: int) -> tuple[np.ndarray, np.ndarray]:
 
 
 def descriptor(R: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
-    """Inverse-distance descriptor X (M, D) and g (M, D, 3) = (R_i - R_j)/r^3.
+    """Inverse-distance descriptor X (M, D) and g (M, D, 3) = (R_i - R_j)/r^3 (Sec. 2.1).
 
     dx_p/dR_i = -g_p and dx_p/dR_j = +g_p for p = (i, j).
     """
@@ -48,7 +48,8 @@ def descriptor(R: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
 
 
 def jacobian(R: np.ndarray) -> np.ndarray:
-    """Dense descriptor Jacobian J (M, D, 3N): J[a, p, 3i+q] = dx_{a,p}/dR_{a,i,q}."""
+    """Dense descriptor Jacobian J (M, D, 3N): J[a, p, 3i+q] = dx_{a,p}/dR_{a,i,q}; the J_a of
+    K_ab = J_a^T H_ab J_b (Sec. 2.1)."""
     M, N, _ = R.shape
     I, J = pair_index(N)
     _, g = descriptor(R)
@@ -62,14 +63,14 @@ def jacobian(R: np.ndarray) -> np.ndarray:
 
 
 def matern52(r, sigma: float):
-    """Scalar Matern-5/2 kernel phi(r), unit signal variance."""
+    """Scalar Matern-5/2 kernel phi(r), unit signal variance (the sGDML kernel cited in Sec. 2.1)."""
     c = np.sqrt(5.0) / sigma
     r = np.asarray(r, dtype=np.float64)
     return (1.0 + c * r + (c * r) ** 2 / 3.0) * np.exp(-c * r)
 
 
 def hessian_block(xa: np.ndarray, xb: np.ndarray, sigma: float) -> np.ndarray:
-    """H_ab = d^2 kappa(x_a, x_b) / dx_a dx_b^T (D x D)."""
+    """H_ab = d^2 kappa(x_a, x_b) / dx_a dx_b^T (D x D), the middle factor of K_ab (Sec. 2.1)."""
     c = np.sqrt(5.0) / sigma
     d = xa - xb
     r = np.sqrt(d @ d)
@@ -125,7 +126,8 @@ def column_getter(R: np.ndarray, sigma: float):
 
 
 def force_kernel_diag(R: np.ndarray, sigma: float) -> np.ndarray:
-    """diag(K): K_aa = (c^2/3) J_a^T J_a since r = 0 on the diagonal block."""
+    """diag(K) (Sec. 2.1; the starting residual diagonal of Algorithm 1): K_aa = (c^2/3) J_a^T J_a
+    since r = 0 on the diagonal block."""
     c = np.sqrt(5.0) / sigma
     Jac = jacobian(R)
     return ((c * c / 3.0) * np.sum(Jac * Jac, axis=1)).reshape(-1)
@@ -157,7 +159,7 @@ def matvec(R: np.ndarray, sigma: float, v: np.ndarray, lam: float = 0.0) -> np.n
 
 
 def matvec_rows(R: np.ndarray, sigma: float, v: np.ndarray, rows, lam: float = 0.0) -> np.ndarray:
-    """Blocks a in `rows` of (K + lam I) v, from the same definition as matvec
+    """Blocks a in `rows` of (K + lam I) v (Sec. 2.1), from the same definition as matvec
     (all w_b = J_b v_b are needed, but only the H_ab of the sampled a).
     Returns an array of shape (len(rows), 3N)."""
     M, N, _ = R.shape

@@ -50,7 +50,8 @@ def philox4x32_10(ctr, key):
 
 
 def uniforms(n: int, seed: int, stream: int) -> np.ndarray:
-    """u_i in (0, 1] for i = 0..n-1 from counter (i, stream)."""
+    """u_i in (0, 1] for i = 0..n-1 from counter (i, stream): the random draws of the column
+    sampling of Sec. 3, from Philox4x32-10 (Salmon et al., SC'11)."""
     idx = np.arange(n, dtype=np.uint64)
     ctr = np.stack([idx & np.uint64(MASK), idx >> np.uint64(32),
                     np.full(n, stream, dtype=np.uint64), np.zeros(n, dtype=np.uint64)], axis=-1)

@@ -31,7 +31,8 @@ from . import philox
 
 
 def select_uniform(n: int, k: int, seed: int, stream: int = philox.STREAM_UNIFORM) -> np.ndarray:
-    """k distinct columns: indices of the k smallest uniforms, ordered by key then index."""
+    """Uniform column sampling (Sec. 3), without replacement: k distinct columns, the indices
+    of the k smallest uniforms, ordered by key then index."""
     if not 0 < k <= n:
         raise ValueError("need 0 < k <= n")
     u = philox.uniforms(n, seed, stream)
@@ -124,7 +125,8 @@ def rls_exact(K: np.ndarray, lam: float) -> np.ndarray:
 
 
 def rls_nystrom(K_nS: np.ndarray, S: np.ndarray, lam: float) -> np.ndarray:
-    """Nystrom estimate of the ridge leverage scores from pilot columns S.
+    """Nystrom estimate of the ridge leverage scores from pilot columns S (Sec. 3, leverage
+    score sampling).
 
     B = K_nS L_S^-T (so B B^T is the Nystrom approximation of K) and
     tau~_i = b_i^T (B^T B + lam I)^-1 b_i.
@@ -137,7 +139,8 @@ def rls_nystrom(K_nS: np.ndarray, S: np.ndarray, lam: float) -> np.ndarray:
 
 def select_weighted(tau: np.ndarray, k: int, seed: int,
                     stream: int = philox.STREAM_RLS_SAMPLE) -> np.ndarray:
-    """k distinct indices sampled without replacement with weights tau (Efraimidis-Spirakis).
+    """Weighted column sampling (Sec. 3): k distinct indices sampled without replacement with
+    weights tau (Efraimidis-Spirakis).
 
     Key_i = -ln(u_i) / tau_i (inf if tau_i <= 0); the k smallest keys, ties by index.
     """

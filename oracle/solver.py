@@ -38,7 +38,7 @@ class PCGResult:
 
 def pcg(apply_A, apply_Pinv, y: np.ndarray, rtol: float = 1e-8, max_iter: int | None = None,
         max_restarts: int = 3) -> PCGResult:
-    """Preconditioned CG on A x = y (A = K_lam SPD, P^-1 SPD), x0 = 0."""
+    """Preconditioned CG (Sec. 2.1, Eq. 2) on A x = y (A = K_lam SPD, P^-1 SPD), x0 = 0."""
     y = np.asarray(y, dtype=np.float64)
     n = y.size
     if max_iter is None:
