@@ -43,7 +43,7 @@ gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t 
 gdml_status gdml_test_df_passes(const float* L_dev, int64_t n, int64_t k, const double* r_dev, const double* u_dev,
                                 double lambda, int32_t staged, double* t_dev, double* z_dev, void* cuda_stream);
 
-/* Reads and clears the error word of the tensor-core kernels/* Reads and clears the error words of the tensor-core kernels of a TF32/BF16/OZAKI
+/* Reads and clears the error words of the tensor-core kernels of a TF32/BF16/OZAKI
  * context and of the staged Woodbury passes of a DF64/OZAKI context (synchronises
  * its stream); GDML_ERR_TIMEOUT if a pipeline wait gave up since the last check.
  * FP64 contexts: always GDML_OK. */
