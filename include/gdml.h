@@ -95,10 +95,13 @@ gdml_status gdml_kernel_setup(gdml_ctx** ctx, const double* R_dev, int64_t M, in
  * contractions; OZAKI: sliced-BF16 tensor-core contractions).  v_dev and out_dev must
  * not overlap.  The matvec is matrix-free: w_b = J_b v_b, u_a = sum_b H_ab w_b,
  * (K v)_a = J_a^T u_a (Sec. 2.1: CG touches K only through such products,
- * so K is never formed). */
+ * so K is never formed).
+ * Errors: GDML_ERR_ARG (NULL context, NULL or equal pointers), GDML_ERR_CUDA; a timed-out
+ * tensor-core pipeline wait is reported by gdml_tc_check. */
 gdml_status gdml_matvec(gdml_ctx* ctx, const double* v_dev, double* out_dev, int32_t add_lambda);
 
-/* Same as gdml_matvec but always in FP64, whatever the context precision. */
+/* Same as gdml_matvec but always in FP64, whatever the context precision.
+ * Errors as gdml_matvec. */
 gdml_status gdml_matvec_fp64(gdml_ctx* ctx, const double* v_dev, double* out_dev, int32_t add_lambda);
 
 /* Forces the trained model predicts for Q query geometries of the context's molecule
@@ -155,14 +158,18 @@ gdml_status gdml_precond_build_scored(gdml_ctx* ctx, const double* geometry_scor
 /* The Nystrom estimate of the ridge leverage scores tau_i = (K (K + lambda I)^-1)_ii
  * (Sec. 3) that GDML_SEL_RLS samples by: pilot of k uniform columns (Philox
  * stream 1), B = K_nS L_S^-T, tau_i = b_i^T (B^T B + lambda I)^-1 b_i.
- * tau_dev: n doubles.  Invalidates any built preconditioner (rank 0). */
+ * tau_dev: n doubles.  Invalidates any built preconditioner (rank 0).
+ * Errors: GDML_ERR_ARG (NULL tau_dev, k outside [1, min(n, 16384)]), GDML_ERR_OOM,
+ * GDML_ERR_NOT_SPD, GDML_ERR_CUDA. */
 gdml_status gdml_rls_scores(gdml_ctx* ctx, int64_t k, uint64_t seed, double* tau_dev);
 
-/* The inverse-distance descriptors x_a (M x D doubles, row a = geometry a). */
+/* The inverse-distance descriptors x_a (M x D doubles, row a = geometry a).
+ * Errors: GDML_ERR_ARG (NULL context or X_dev), GDML_ERR_CUDA. */
 gdml_status gdml_descriptors(const gdml_ctx* ctx, double* X_dev);
 
 /* Rank actually built by the last gdml_precond_build (pivchol may stop early),
- * and the jitter added to K_kk (0 if none).  Host outputs; either may be NULL. */
+ * and the jitter added to K_kk (0 if none).  Host outputs; either may be NULL.
+ * Errors: GDML_ERR_ARG (NULL context). */
 gdml_status gdml_precond_info(const gdml_ctx* ctx, int64_t* rank_out, double* jitter_out);
 
 /* z = P^-1 r by the Woodbury identity (Eq. 4).  r_dev, z_dev: length n, may
@@ -187,10 +194,12 @@ gdml_status gdml_pcg_solve(gdml_ctx* ctx, const double* y_dev, double* alpha_dev
                            int32_t max_iter, int32_t* iters_out, double* relres_out);
 
 /* Inner tolerance of the mixed-precision refinement (default 1e-3 for BF16,
- * 1e-4 for TF32; ignored in FP64 contexts). */
+ * 1e-4 for TF32; ignored in FP64 contexts).
+ * Errors: GDML_ERR_ARG unless 0 < inner_rtol < 1. */
 gdml_status gdml_set_inner_rtol(gdml_ctx* ctx, double inner_rtol);
 
-/* Outer refinement steps of the last gdml_pcg_solve (1 for FP64 contexts). */
+/* Outer refinement steps of the last gdml_pcg_solve (1 for FP64 contexts).
+ * Errors: GDML_ERR_ARG (NULL context). */
 gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
 
 /* Solve count independent systems (each set up by its own FP64 context, any
@@ -214,7 +223,8 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
  * power-of-two K-split (1 .. 8 or more) of the second descriptor contraction
  * (FP64 DGEMM or tcgen05 GEMM) and keeps the fastest.  *choice_out (host, may
  * be NULL) receives it so that a caller can cache it and restore it later with
- * gdml_set_tuning.  Synchronises the context's stream. */
+ * gdml_set_tuning.  Synchronises the context's stream.
+ * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA. */
 gdml_status gdml_autotune(gdml_ctx* ctx, int32_t* choice_out);
 gdml_status gdml_set_tuning(gdml_ctx* ctx, int32_t splits);
 
@@ -234,7 +244,8 @@ gdml_status gdml_set_tuning(gdml_ctx* ctx, int32_t splits);
  *  Calls that overlap on the GPU (two streams, or two host threads on one
  *    device) share the array and race; serialise them.
  *  R_dev, v_dev, out_dev: caller-owned device arrays (v_dev != out_dev);
- *  cuda_stream: a cudaStream_t or NULL. */
+ *  cuda_stream: a cudaStream_t or NULL.
+ * Errors: GDML_ERR_ARG (sizes beyond the limits, NULL or equal pointers), GDML_ERR_CUDA. */
 gdml_status gdml_matvec_noalloc(const double* R_dev, int64_t M, int32_t N, double sigma, double lambda,
                                 const double* v_dev, double* out_dev, int32_t add_lambda, void* cuda_stream);
 
@@ -245,25 +256,42 @@ gdml_status gdml_matvec_noalloc(const double* R_dev, int64_t M, int32_t N, doubl
  * the referee (by PCG iteration count) of its selections.  The paper has no
  * learned selection; its leverage-score sampling (Sec. 3) supplies the labels. */
 typedef struct gdml_scorer gdml_scorer;
+/* A scorer for D descriptor features with two hidden layers of width `hidden`, weights drawn
+ * from `seed`; *s owns its device memory until gdml_scorer_destroy.
+ * Errors: GDML_ERR_ARG (NULL s, D outside [1, 65536], hidden outside [1, 4096]), GDML_ERR_OOM,
+ * GDML_ERR_CUDA. */
 gdml_status gdml_scorer_create(gdml_scorer** s, int32_t D, int32_t hidden, uint64_t seed, void* cuda_stream);
-/* feature mean/std per column and label mean/std from training data X (B x D), y (B) */
+/* feature mean/std per column and label mean/std from training data X (B x D), y (B)
+ * Errors: GDML_ERR_ARG (NULL arguments, B < 2), GDML_ERR_CUDA. */
 gdml_status gdml_scorer_fit_scaling(gdml_scorer* s, const double* X_dev, const double* y_dev, int64_t B);
+/* `epochs` passes of Adam (learning rate lr) over the B rows of X (B x D) and labels y (B) in
+ * mini-batches of `batch`; last_loss_out (host, may be NULL) gets the last mini-batch's
+ * mean-squared error on standardised labels.
+ * Errors: GDML_ERR_ARG (NULL arguments, B, epochs or batch < 1, lr <= 0), GDML_ERR_OOM,
+ * GDML_ERR_CUDA. */
 gdml_status gdml_scorer_train(gdml_scorer* s, const double* X_dev, const double* y_dev, int64_t B, int32_t epochs,
                               int32_t batch, double lr, double* last_loss_out);
+/* out (B doubles) = the scorer's prediction for the B rows of X (B x D), in label units.
+ * Errors: GDML_ERR_ARG (NULL arguments, B < 1), GDML_ERR_OOM, GDML_ERR_CUDA. */
 gdml_status gdml_scorer_predict(gdml_scorer* s, const double* X_dev, int64_t B, double* out_dev);
-/* flat FP32 parameters [W1 (h x D) | b1 | W2 (h x h) | b2 | w3 | b3]: get (set = 0) or set (set = 1) */
+/* flat FP32 parameters [W1 (h x D) | b1 | W2 (h x h) | b2 | w3 | b3]: get (set = 0) or set (set = 1)
+ * params_dev = NULL only reports the count. Errors: GDML_ERR_ARG (NULL scorer), GDML_ERR_CUDA. */
 gdml_status gdml_scorer_params(gdml_scorer* s, float* params_dev, int32_t set, int64_t* nparam_out);
-/* loss (host) and its gradient w.r.t. the flat parameters (device) on one batch */
+/* loss (host) and its gradient w.r.t. the flat parameters (device) on one batch
+ * Errors: GDML_ERR_ARG (NULL arguments, B < 1), GDML_ERR_OOM, GDML_ERR_CUDA. */
 gdml_status gdml_scorer_grad(gdml_scorer* s, const double* X_dev, const double* y_dev, int64_t B, double* loss_out,
                              float* grad_dev);
+/* Waits for the scorer's stream and frees its device memory (NULL is allowed). Never fails. */
 void gdml_scorer_destroy(gdml_scorer* s);
 
 /* Message describing the last error on ctx (or, when ctx is NULL, the last
  * failed call without a context on this thread: setup, rule_of_thumb_k).
- * Never NULL; valid until the next call on the context. */
+ * Never NULL; valid until the next call on the context.
+ * Never fails. */
 const char* gdml_last_error(const gdml_ctx* ctx);
 
-/* Release all device memory owned by ctx (NULL is allowed). */
+/* Release all device memory owned by ctx (NULL is allowed).
+ * Never fails. */
 void gdml_destroy(gdml_ctx* ctx);
 
 #ifdef __cplusplus
