@@ -58,3 +58,31 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
         gdml.load()
     with pytest.raises(RuntimeError, match="not built"):
         gdml.rule_of_thumb_k(1000)
+
+
+def test_plain_c_program_uses_the_abi(lib_path, tmp_path):
+    """The headers compile as C99 and a C program links against the library and calls a
+    host-only entry point (the rule of thumb: 5833 columns for n = 63000, m = 1, k_min = 100)."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "gdml.h"\n#include "gdml_testing.h"\n'
+        "int main(void) {\n"
+        "  int64_t k = 0;\n"
+        "  if (gdml_rule_of_thumb_k(63000, 1.0, 100.0, &k) != GDML_OK) return 1;\n"
+        "  if (gdml_rule_of_thumb_k(0, 1.0, 100.0, &k) != GDML_ERR_ARG) return 2;\n"
+        '  printf("%lld %s\\n", (long long)k, gdml_last_error(NULL));\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib_path)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lgdml",
+                    f"-Wl,-rpath,{libdir}"], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    if out.returncode != 0 and "error while loading shared libraries" in out.stderr:
+        pytest.skip(f"cannot load the CUDA runtime: {out.stderr.strip()}")
+    assert out.returncode == 0, out.stderr
+    k, msg = out.stdout.split(" ", 1)
+    assert int(k) == 5833 and "rule_of_thumb_k" in msg
