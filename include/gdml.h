@@ -180,7 +180,8 @@ gdml_status gdml_precond_apply(gdml_ctx* ctx, const double* r_dev, double* z_dev
  * contents on entry (pass zeros for the paper's cold start).  The stopping
  * test is the TRUE relative residual |y - K_lambda alpha|_2 / |y|_2 <= rtol,
  * recomputed in FP64 when the recurrence residual passes (restart from alpha
- * if it has drifted, at most 3 times).  TF32/BF16 contexts run FP64 iterative
+ * if it has drifted: at most 3 times in FP64 contexts, 10 times in DF64 and
+ * OZAKI contexts, whose FP64-class matvec drifts more).  TF32/BF16 contexts run FP64 iterative
  * refinement: the inner PCG uses the tensor-core matvec and stops at
  * inner_rtol relative to its own right-hand side; the outer loop recomputes
  * r = y - K_lambda alpha with the FP64 matvec (at most 20 outer steps).
@@ -202,17 +203,19 @@ gdml_status gdml_set_inner_rtol(gdml_ctx* ctx, double inner_rtol);
  * Errors: GDML_ERR_ARG (NULL context). */
 gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
 
-/* Solve count independent systems (each set up by its own FP64 context, any
- * sizes, sigma and lambda) with ONE CUDA graph launch per round: the graph
+/* Solve count independent systems (each set up by its own FP64, DF64 or OZAKI
+ * context, any sizes, sigma and lambda) with ONE CUDA graph launch per round: the graph
  * holds, per system, a gate kernel and a conditional WHILE node whose body is
  * that system's PCG iteration (Sec. 2.1, Eq. 2, as in gdml_pcg_solve), so the
  * loops of all systems run concurrently on the device.  Between rounds the
  * host recomputes each active system's TRUE FP64 residual and restarts the
- * ones that drifted (at most 3 restarts, as gdml_pcg_solve).
+ * ones that drifted (at most 3 restarts for FP64 contexts, 10 for DF64 and
+ * OZAKI, as gdml_pcg_solve; at most 12 rounds in all).
  *  ctxs, y_dev, alpha_dev: host arrays of count entries (device vectors of
  *    each context's length n_i; alpha_dev holds x0 on entry, the solution on exit).
  *  iters_out, relres_out (host arrays of count entries, may be NULL).
- * All contexts must be FP64 or DF64 contexts on the current device, each at most once.
+ * All contexts must be FP64, DF64 or OZAKI contexts on the current device, each at most once
+ * (TF32 / BF16 contexts, whose solve is an iterative refinement, are rejected).
  * Synchronises every context's stream.  Errors: GDML_ERR_ARG,
  * GDML_ERR_NOT_CONVERGED (some system above rtol), GDML_ERR_BREAKDOWN, GDML_ERR_CUDA. */
 gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const double* const* y_dev,
@@ -241,11 +244,16 @@ gdml_status gdml_set_tuning(gdml_ctx* ctx, int32_t splits);
  *    so nothing needs clearing between calls.
  *  The first call on each device looks the array's address up (with that
  *    device current), so make that first call before any stream capture.
+ *  The looked-up address belongs to the device's primary context: it does not
+ *    survive cudaDeviceReset, and code running under another context of the
+ *    device must not call this entry point.
  *  Calls that overlap on the GPU (two streams, or two host threads on one
  *    device) share the array and race; serialise them.
- *  R_dev, v_dev, out_dev: caller-owned device arrays (v_dev != out_dev);
- *  cuda_stream: a cudaStream_t or NULL.
- * Errors: GDML_ERR_ARG (sizes beyond the limits, NULL or equal pointers), GDML_ERR_CUDA. */
+ *  R_dev, v_dev, out_dev: caller-owned device arrays on the current device
+ *    (v_dev != out_dev), v_dev and out_dev holding 3 N M doubles each;
+ *  cuda_stream: a cudaStream_t of the current device, or NULL.
+ * Errors: GDML_ERR_ARG (sizes beyond the limits, NULL or equal pointers, a stream
+ * of another device), GDML_ERR_CUDA. */
 gdml_status gdml_matvec_noalloc(const double* R_dev, int64_t M, int32_t N, double sigma, double lambda,
                                 const double* v_dev, double* out_dev, int32_t add_lambda, void* cuda_stream);
 

@@ -30,6 +30,21 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
 gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
                               double* C_dev, void* cuda_stream);
 
+/* The tall product of the OZAKI preconditioner build (Eq. 5's L_k = K_nk L_kk^-T as K_nk
+ * times the transposed triangular inverse, and the leverage-score row norms of Sec. 3's
+ * estimate): C = A B^T on the sliced-BF16 tensor cores, accumulated over all of K inside
+ * each output tile (FP64-class).  A: n x K FP64, COLUMN-major (entry (r, j) at A[j n + r]);
+ * B: NB x K FP64, row-major with row stride ldb >= K; tri_b != 0 declares B lower
+ * triangular (zero above its diagonal, which must hold: whole K blocks past each tile's
+ * diagonal are skipped).  rowsq = 0: out (n x NB, column-major: C[r][c] at out[c n + r])
+ * and, if out32 is not NULL, the same as FP32 at out32; out may equal A.  rowsq != 0:
+ * out[r] = sum_c C[r][c]^2 (n doubles), out32 unused.  1 <= n <= 2^31, 1 <= K, NB <= 2^24.
+ * Synchronises the stream.  Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA,
+ * GDML_ERR_TIMEOUT (a bounded pipeline wait gave up). */
+gdml_status gdml_test_oz_gemm_tall(const double* A_dev, int64_t n, int64_t K, const double* B_dev, int64_t NB,
+                                   int64_t ldb, int32_t tri_b, int32_t rowsq, double* out_dev, float* out32_dev,
+                                   void* cuda_stream);
+
 /* The two passes over the FP32-stored factor L_k of the Woodbury apply (Eq. 4) in
  * DF64/OZAKI contexts: t = L^T r and z = (r - L u) / lambda, with exact FP32
  * products of L and the float-pair split of r (u) and double-float sums.  L: n x k
@@ -42,6 +57,13 @@ gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t 
  * GDML_ERR_CUDA, GDML_ERR_TIMEOUT (a bounded pipeline wait gave up). */
 gdml_status gdml_test_df_passes(const float* L_dev, int64_t n, int64_t k, const double* r_dev, const double* u_dev,
                                 double lambda, int32_t staged, double* t_dev, double* z_dev, void* cuda_stream);
+
+/* The built preconditioner's factor L_k (Eqs. 3-5) as FP64: n x rank, column-major (column
+ * j at L_out_dev + j n, columns in selection / pivot order; rank from gdml_precond_info).
+ * DF64 and OZAKI contexts store L_k in FP32; it is widened exactly.  L_out_dev: n * rank
+ * doubles owned by the caller.  Synchronises the context's stream.
+ * Errors: GDML_ERR_ARG (NULL arguments), GDML_ERR_STATE (nothing built), GDML_ERR_CUDA. */
+gdml_status gdml_test_precond_factor(gdml_ctx* ctx, double* L_out_dev);
 
 /* Reads and clears the error words of the tensor-core kernels of a TF32/BF16/OZAKI
  * context and of the staged Woodbury passes of a DF64/OZAKI context (synchronises

@@ -158,26 +158,62 @@ def matvec(R: np.ndarray, sigma: float, v: np.ndarray, lam: float = 0.0) -> np.n
     return out + lam * np.asarray(v, dtype=np.float64)
 
 
+def project(R: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """w_a = J_a v_a for every geometry (Sec. 2.1), from the two nonzeros of each row of J_a:
+    w_{a,p} = -g_{a,p} . (v_{a,i} - v_{a,j}) for p = (i, j) (the entries jacobian() places).
+    Returns W (M, D)."""
+    M, N, _ = R.shape
+    I, J = pair_index(N)
+    _, g = descriptor(R)
+    V = np.asarray(v, dtype=np.float64).reshape(M, N, 3)
+    return -np.einsum("apq,apq->ap", g, V[:, I, :] - V[:, J, :])
+
+
 def matvec_rows(R: np.ndarray, sigma: float, v: np.ndarray, rows, lam: float = 0.0) -> np.ndarray:
     """Blocks a in `rows` of (K + lam I) v (Sec. 2.1), from the same definition as matvec
-    (all w_b = J_b v_b are needed, but only the H_ab of the sampled a).
+    (all w_b = J_b v_b are needed, but only the H_ab of the sampled a):
+    u_a = sum_b S_ab [(1 + c r_ab) w_b - c^2 d_ab (d_ab . w_b)], (K v)_a = J_a^T u_a.
     Returns an array of shape (len(rows), 3N)."""
     M, N, _ = R.shape
     B = 3 * N
     c = np.sqrt(5.0) / sigma
     X, _ = descriptor(R)
-    Jac = jacobian(R)
+    W = project(R, v)
     V = np.asarray(v, dtype=np.float64).reshape(M, B)
-    W = np.einsum("apk,ak->ap", Jac, V)
     out = np.empty((len(rows), B))
     for t, a in enumerate(rows):
-        d = X[a][None, :] - X
-        r = np.sqrt(np.sum(d * d, axis=1))
+        d = X[a][None, :] - X  # (M, D): d_ab = x_a - x_b
+        r = np.sqrt(np.einsum("bp,bp->b", d, d))
         S = (c * c / 3.0) * np.exp(-c * r)
-        proj = np.sum(d * W, axis=1)
+        proj = np.einsum("bp,bp->b", d, W)  # d_ab . w_b
         u = (S * (1.0 + c * r)) @ W - c * c * ((S * proj) @ d)
-        out[t] = Jac[a].T @ u + lam * V[a]
+        out[t] = jacobian(R[a:a + 1])[0].T @ u + lam * V[a]
     return out
+
+
+def matvec_parallel(R: np.ndarray, sigma: float, v: np.ndarray, lam: float = 0.0,
+                    workers: int | None = None) -> np.ndarray:
+    """(K + lam I) v, the geometry blocks of matvec_rows shared out over worker processes
+    (spawn start method: safe after a CUDA context exists in the caller; one BLAS thread per
+    worker).  For the large systems where the single-process matvec takes minutes."""
+    import multiprocessing as mp
+    import os
+    M = R.shape[0]
+    workers = max(1, min(workers or os.cpu_count() or 1, M))
+    chunks = [list(ch) for ch in np.array_split(np.arange(M), 2 * workers) if len(ch)]
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    try:
+        for k in saved:
+            os.environ[k] = "1"
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.starmap(matvec_rows, [(R, sigma, v, ch, lam) for ch in chunks])
+    finally:
+        for k, val in saved.items():
+            if val is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = val
+    return np.concatenate(parts).reshape(-1)
 
 
 def predict_forces(R_query: np.ndarray, R: np.ndarray, sigma: float, alpha: np.ndarray) -> np.ndarray:

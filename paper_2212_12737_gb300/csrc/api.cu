@@ -28,6 +28,18 @@ gdml_status fail(gdml_status st, const std::string& msg) {
 const std::string& last_msg() { return g_msg; }
 void clear_msg() { g_msg.clear(); }
 
+int num_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 }  // namespace gdml
 
 using namespace gdml;
@@ -264,13 +276,28 @@ gdml_status chol_jitter(gdml_ctx* c, const double* src, double* work, int64_t k,
   return GDML_OK;
 }
 
-// L (k x n row-major = n x k col-major) <- Nystrom factor from columns S (Eq. 5)
+// L (k x n row-major = n x k col-major) <- Nystrom factor from columns S (Eq. 5).
+// FP64 / DF64 contexts: forward substitution on the FP64 pipe.  OZAKI contexts: the same
+// L_k = K_nk L_kk^-T as K_nk times the transposed triangular inverse of L_kk, on the sliced
+// BF16 tensor cores (FP64-class products, accumulated over all of k in each tile); only the
+// k x k inverse runs on the FP64 pipe.  On return `work` holds L_kk (lower, row-major).
 gdml_status nystrom(gdml_ctx* c, const int64_t* S, int64_t k, double* L, double* Kkk, double* work,
                     double* eps_out) {
   TRY(get_cols(c, S, k, L));
   { gather_kkk_kernel<<<(unsigned)cdiv(k * k, 256), 256, 0, c->st>>>(L, c->n, S, k, Kkk); count_launch(); }
   TRY(check_launch(c, "gather_kkk"));
   TRY(chol_jitter(c, Kkk, work, k, eps_out));
+  if (c->precision == GDML_OZAKI) {
+    Scratch s{c, {}};
+    double* Linv = nullptr;
+    TRY(s.get(&Linv, (size_t)(k * k)));
+    set_identity(Linv, k, c->st);
+    trsm_left_lower(work, k, Linv, k, c->st, true);  // L_kk^-1 (lower triangular)
+    TRY(check_launch(c, "inducing-block inverse"));
+    gdml_status so = oz_gemm_tall(L, c->n, k, Linv, k, k, true, false, L, nullptr, c->st);
+    if (so != GDML_OK) return ctx_fail(c, so, "sliced K_nk L_kk^-T: " + last_msg());
+    return GDML_OK;
+  }
   trsm_left_lower(work, k, L, c->n, c->st);  // rows of K_nk^T -> rows of L_k^T
   return check_launch(c, "trsm");
 }
@@ -280,6 +307,9 @@ gdml_status woodbury_core(gdml_ctx* c, const double* L, int64_t k, double* LC, d
                           double* Cfull = nullptr, const float* Lf = nullptr) {
   if (Lf && c->precision == GDML_OZAKI) {  // C from the FP32 factor on the sliced tensor cores
     gdml_status s = oz_syrk_lower(Lf, c->n, k, LC, k, c->st);
+    if (s != GDML_OK) return ctx_fail(c, s, "sliced syrk: " + last_msg());
+  } else if (c->precision == GDML_OZAKI) {  // C from the FP64 factor (columns = rows of L^T), sliced
+    gdml_status s = oz_syrk_lower_f64(L, k, c->n, c->n, LC, k, c->st);
     if (s != GDML_OK) return ctx_fail(c, s, "sliced syrk: " + last_msg());
   } else if (Lf)  // DF64: C from the FP32-stored factor, exact products, double-float sums
     launch_dfsyrk(k, c->n, Lf, c->n, LC, k, c->st);
@@ -359,6 +389,16 @@ gdml_status rls_estimate(gdml_ctx* c, int64_t k, uint64_t seed, int64_t* S, doub
   double eps0 = 0.0;
   TRY(nystrom(c, S, k, c->L, Kkk, work, &eps0));  // B (n x k col-major)
   TRY(woodbury_core(c, c->L, k, c->LC));          // chol(B^T B + lambda I)
+  if (c->precision == GDML_OZAKI) {
+    // tau_i = |L_C^-1 b_i|^2: the row square sums of B X^T with X = L_C^-1 (lower
+    // triangular, formed on the FP64 pipe), the product on the sliced tensor cores
+    set_identity(work, k, c->st);
+    trsm_left_lower(c->LC, k, work, k, c->st, true);
+    TRY(check_launch(c, "rls core inverse"));
+    gdml_status so = oz_gemm_tall(c->L, n, k, work, k, k, true, true, tau, nullptr, c->st);
+    if (so != GDML_OK) return ctx_fail(c, so, "sliced leverage scores: " + last_msg());
+    return GDML_OK;
+  }
   trsm_left_lower(c->LC, k, c->L, n, c->st);       // Z = L_C^-1 B^T
   { col_sqnorm_kernel<<<(unsigned)cdiv(n, 256), 256, 0, c->st>>>(c->L, k, n, tau); count_launch(); }
   return check_launch(c, "rls scores");
@@ -988,6 +1028,32 @@ gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t 
   if (M > ((int64_t)1 << 24) || N > ((int64_t)1 << 24) || K > ((int64_t)1 << 24))
     return fail(GDML_ERR_ARG, "gemm test sizes too large");
   return oz_gemm_test(A_dev, B_dev, M, N, K, C_dev, static_cast<cudaStream_t>(stream));
+}
+
+gdml_status gdml_test_oz_gemm_tall(const double* A_dev, int64_t n, int64_t K, const double* B_dev, int64_t NB,
+                                   int64_t ldb, int32_t tri_b, int32_t rowsq, double* out_dev, float* out32_dev,
+                                   void* stream) {
+  clear_msg();
+  if (!A_dev || !B_dev || !out_dev || n < 1 || K < 1 || NB < 1 || ldb < K)
+    return fail(GDML_ERR_ARG, "bad tall gemm test arguments");
+  if (n > ((int64_t)1 << 31)) return fail(GDML_ERR_ARG, "tall gemm test: n too large");
+  return oz_gemm_tall(A_dev, n, K, B_dev, NB, ldb, tri_b != 0, rowsq != 0, out_dev, rowsq ? nullptr : out32_dev,
+                      static_cast<cudaStream_t>(stream));
+}
+
+gdml_status gdml_test_precond_factor(gdml_ctx* c, double* L_out) {
+  TRY(validate(c));
+  if (!L_out) return ctx_fail(c, GDML_ERR_ARG, "precond_factor: NULL output");
+  if (c->k == 0) return ctx_fail(c, GDML_ERR_STATE, "no preconditioner built");
+  const int64_t count = c->n * c->k;
+  if (df_precond(c)) {
+    widen_float(c->Lf, count, L_out, c->st);
+    TRY(check_launch(c, "precond_factor"));
+  } else {
+    CTRY(c, cudaMemcpyAsync(L_out, c->L, count * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  }
+  CTRY(c, cudaStreamSynchronize(c->st));
+  return GDML_OK;
 }
 
 int64_t gdml_launch_count(void) { return launch_count(); }

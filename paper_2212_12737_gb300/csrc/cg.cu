@@ -2,14 +2,19 @@
 // fused PCG updates.  Scalars stay in device memory; no host round trip is
 // needed inside an iteration.
 //
-// Every reduction uses a fixed grid (kDotBlocks CTAs, each a contiguous
-// chunk) and a fixed combination order, so results are bitwise reproducible.
+// Every reduction uses a fixed grid (dot_blocks() CTAs, each a contiguous
+// chunk) and a fixed combination order, so results are bitwise reproducible
+// on a given device.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace gdml {
 
-constexpr int kDotBlocks = 2 * kNumSMs;
+constexpr int kDotMaxBlocks = 2048;  // the context's partial buffer holds 4096 doubles
+// two CTAs per SM; the same grid for every reduction of the loop (bitwise-equal r.r)
+inline int dot_blocks() { return std::min(2 * num_sms(), kDotMaxBlocks); }
 constexpr int kDotThreads = 256;
 
 // partial[blockIdx.x] = sum over the CTA's chunk of x*y; the last CTA to finish
@@ -149,18 +154,18 @@ cudaError_t add_pcg_gate_node(cudaGraph_t g, cudaGraphNode_t* node, const double
 }
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,
                 cudaStream_t st) {
-  { dot_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(x, y, n, partial, ticket, out); count_launch(); }
+  { dot_kernel<<<dot_blocks(), kDotThreads, 0, st>>>(x, y, n, partial, ticket, out); count_launch(); }
 }
 void launch_update_xr_rr(double* x, double* r, const double* p, const double* q, int64_t n, double* sc, int* status,
                          double* partial, unsigned* ticket, int64_t* ictl, cudaGraphConditionalHandle h, int check,
                          cudaStream_t st) {
-  { update_xr_rr_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(x, r, p, q, n, sc, status, partial, ticket, ictl, h, check); count_launch(); }
+  { update_xr_rr_kernel<<<dot_blocks(), kDotThreads, 0, st>>>(x, r, p, q, n, sc, status, partial, ticket, ictl, h, check); count_launch(); }
 }
 void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, cudaStream_t st) {
-  { update_p_rho_kernel<<<4 * kNumSMs, 256, 0, st>>>(p, z, n, sc, ticket); count_launch(); }
+  { update_p_rho_kernel<<<4 * num_sms(), 256, 0, st>>>(p, z, n, sc, ticket); count_launch(); }
 }
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st) {
-  { axpby_kernel<<<4 * kNumSMs, 256, 0, st>>>(y, x, a, b, n); count_launch(); }
+  { axpby_kernel<<<4 * num_sms(), 256, 0, st>>>(y, x, a, b, n); count_launch(); }
 }
 
 }  // namespace gdml

@@ -11,7 +11,9 @@
 
 namespace gdml {
 
-constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs; grids are sized in multiples of it
+// Streaming multiprocessors of the current device (152 on GB300: 2 dies x 76), queried once per
+// device; grids are sized in multiples of it.
+int num_sms();
 
 // Host-side error carrier: every internal call returns a gdml_status and
 // writes a message into the context.

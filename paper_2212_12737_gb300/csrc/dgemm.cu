@@ -119,7 +119,7 @@ void launch_dgemm(bool nt, int64_t M, int64_t N, int64_t K, double alpha, const 
 // number of K splits that brings an M x N tile grid to ~2 waves of the SMs
 int dgemm_splits(int64_t M, int64_t N, int64_t K) {
   const int64_t tiles = cdiv(M, 64) * cdiv(N, 64);
-  int64_t s = (2 * kNumSMs) / (tiles > 0 ? tiles : 1);
+  int64_t s = (2 * (int64_t)num_sms()) / (tiles > 0 ? tiles : 1);
   const int64_t kmax = cdiv(K, 64);  // keep >= 64 of K per split
   if (s > kmax) s = kmax;
   return (int)(s < 1 ? 1 : s);

@@ -545,13 +545,7 @@ bool launch_kcol_df(const int64_t* cols, int64_t ncols, const float2* X2, const 
   const size_t per_warp = 5 * (size_t)D * sizeof(float2), fixed = ((size_t)N + D) * sizeof(float2);
   int W = (int)std::min<size_t>(8, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / per_warp);
   if (W < 1 || ncols > 65535) return false;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-      sms = 1;
-  }
+  const int sms = num_sms();
   const int64_t want = std::max<int64_t>(1, M * ncols / (2 * (int64_t)sms));
   if (want < W) W = (int)want;
   const size_t wsmem = fixed + W * per_warp;
@@ -628,13 +622,7 @@ void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const doub
   const size_t per_warp = 5 * (size_t)D * sizeof(double), fixed = ((size_t)N + D) * sizeof(double);
   int W = (int)std::min<size_t>(8, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / per_warp);
   {  // few columns (one per Algorithm 1 step): fewer warps per CTA so the grid covers every SM twice
-    static int sms = 0;
-    if (!sms) {
-      int dev = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-        sms = 1;
-    }
+    const int sms = num_sms();
     const int64_t want = std::max<int64_t>(1, M * ncols / (2 * (int64_t)sms));
     if (want < W) W = (int)want;
   }

@@ -95,6 +95,7 @@ void df_passes(const float* L, int64_t n, int64_t k, const double* r, const doub
                double* z, double* part, float2* rs, float2* t2, float2* u2, const WsPlan* plan, int* err,
                cudaStream_t st);
 void to_float(const double* a, int64_t n, float* b, cudaStream_t st);
+void widen_float(const float* a, int64_t n, double* b, cudaStream_t st);
 // lower-triangle-only double-float SYRK of an FP32 matrix: C = A A^T, A (k x n row-major, ld)
 void launch_dfsyrk(int64_t k, int64_t n, const float* A, int64_t lda, double* C, int64_t ldc, cudaStream_t st);
 void transpose_square(const double* A, int64_t k, double* At, cudaStream_t st);

@@ -7,9 +7,13 @@
 // names the array directly: the first call on a device looks up its device
 // address with cudaGetSymbolAddress (with that device current) and caches it
 // per device; that first call should therefore happen before any stream
-// capture.  Every call overwrites the whole region it uses before reading it,
-// so nothing has to start at zero; calls that overlap on the GPU (different
-// streams, or different host threads on one device) race on the array.
+// capture.  The cached address belongs to the device's primary context: it
+// does not survive cudaDeviceReset, and calls made under another context of
+// the same device must not use this entry point.  A stream of another device
+// than the current one is rejected.  Every call overwrites the whole region
+// it uses before reading it, so nothing has to start at zero; calls that
+// overlap on the GPU (different streams, or different host threads on one
+// device) race on the array.
 #include <mutex>
 
 #include "common.cuh"
@@ -62,10 +66,19 @@ extern "C" gdml_status gdml_matvec_noalloc(const double* R_dev, int64_t M, int32
     return fail(GDML_ERR_ARG, "matvec_noalloc: needs 1 <= M <= " + std::to_string(kNoAllocMaxM) +
                                   " geometries and 2 <= N <= " + std::to_string(kNoAllocMaxN) + " atoms");
   if (!(sigma > 0.0) || !(lambda >= 0.0)) return fail(GDML_ERR_ARG, "matvec_noalloc: need sigma > 0, lambda >= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (st) {  // the scratch address is the current device's: the stream must belong to it
+    int cur = 0, sdev = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess) e = cudaStreamGetDevice(st, &sdev);
+    if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("matvec_noalloc: ") + cudaGetErrorString(e));
+    if (sdev != cur)
+      return fail(GDML_ERR_ARG, "matvec_noalloc: the stream belongs to device " + std::to_string(sdev) +
+                                    " but device " + std::to_string(cur) + " is current");
+  }
   double* base = nullptr;
   gdml_status s = scratch_address(&base);
   if (s != GDML_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int D = N * (N - 1) / 2;
   const double c = std::sqrt(5.0) / sigma;
   double* X = base;

@@ -182,6 +182,59 @@ __global__ void __launch_bounds__(256) oz_slice_rows_f32_kernel(const float* __r
   slice_write(make_float2(x, 0.f), ex, sl, row, k, Rp, Kp);
 }
 
+// Slicing of a COLUMN-major source: operand row r (r < rows) is row r0 + r of the n x K
+// matrix whose column j starts at src + j ld, i.e. entry (r, j) = src[j ld + r0 + r].  One
+// CTA per 16 rows and one 256-entry chunk: coalesced reads down the columns into a shared
+// tile, a per-row exponent, then slice rows written along K (coalesced).
+template <typename T>
+__global__ void __launch_bounds__(256) oz_slice_cols_kernel(const T* __restrict__ src, int64_t ld, int64_t r0,
+                                                            int64_t rows, int64_t K, int64_t Rp, int64_t Kp,
+                                                            bf16* __restrict__ sl, int* __restrict__ e) {
+  constexpr int RB = 16;
+  __shared__ float2 tile[oz::KC][RB + 1];
+  __shared__ int ex_s[RB];
+  const int64_t rb = (int64_t)blockIdx.x * RB, q = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {  // load: 16 threads per column read 16 consecutive rows
+    const int r = tid % RB;
+#pragma unroll 4
+    for (int jj = tid / RB; jj < oz::KC; jj += 256 / RB) {
+      const int64_t j = q * oz::KC + jj;
+      const int64_t row = rb + r;
+      double x = 0.0;
+      if (j < K && row < rows) x = (double)src[j * ld + r0 + row];
+      tile[jj][r] = split_d(x);
+    }
+  }
+  __syncthreads();
+  {  // exponent of each row: warp w takes rows 2w and 2w + 1, 16 lanes per row
+    const int r = 2 * warp + (lane >> 4);
+    float m = 0.f;
+    for (int jj = lane & 15; jj < oz::KC; jj += 16) m = fmaxf(m, fabsf(tile[jj][r].x));
+    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((lane & 15) == 0) {
+      int ex = 0;
+      if (m > 0.f) (void)frexpf(m, &ex);
+      ex_s[r] = ex;
+      if (rb + r < rows) e[q * rows + rb + r] = ex;
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < RB; ++r) {
+    if (rb + r >= rows) break;
+    slice_write(tile[tid][r], ex_s[r], sl, rb + r, q * oz::KC + tid, Rp, Kp);
+  }
+}
+
+// sum of the square-sum partials of each row, in a fixed slot order
+__global__ void oz_rowsq_reduce_kernel(const double* __restrict__ sq, int slots, int64_t n, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < slots; ++k) s += sq[(int64_t)k * n + i];
+  out[i] = s;
+}
+
 // W_a = J_a v_a and t_a = xc_a . w_a (as the FP64 projection), fused with the slicing of
 // row a of W into GEMM 1's B operand when it is one chunk (Kp <= 256): one CTA per geometry,
 // thread p holds w_p, the chunk exponent and t_a are CTA reductions; t_a is also written as
@@ -529,19 +582,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+enum { ACC_ROWMAJOR = 0, ACC_COLMAJOR = 1, ACC_ROWSQ = 2 };
+struct AccOut {  // what the accumulating GEMM stores (see oz_gemm_acc_kernel)
+  int mode;
+  int lower_only;
+  int tri_b;
+  double* C;
+  float* C32;
+  double* sq;
+  int64_t ldc;
+};
+
 // Same sliced product accumulated over ALL K chunks inside the CTA, FP64 output:
 //   C[m][n] = sum_chunks 2^(eA + eB) sum_levels acc_level 2^-7(level + 2)
 // The MMA warp signals the end of each chunk on cdone; the 8 epilogue warps read the 7
 // level accumulators of their 32 columns, add the scaled chunk value into a running
 // double-float sum held in registers, and release the TMEM on tfree before the MMA
-// warp starts the next chunk (whose first MMA per level overwrites).  lower_only:
-// tiles wholly above the diagonal exit at once (symmetric products).
+// warp starts the next chunk (whose first MMA per level overwrites).
+//  o.lower_only: tiles wholly above the diagonal exit at once (symmetric products);
+//  o.tri_b: row c of B is zero beyond column c (lower triangular B), so the CTA of B rows
+//    [n0, n0 + 64) stops after K entry n0 + 63;
+//  o.mode: ACC_ROWMAJOR  C[m][n] at C[m ldc + n];
+//          ACC_COLMAJOR  C[m][n] at C[n ldc + m] (and as FP32 at C32[n ldc + m] if C32);
+//          ACC_ROWSQ     sq[(2 blockIdx.x + half) ldc + m] = sum over the half tile's 32
+//                        columns n of C[m][n]^2 (no C is stored).
 __global__ void __launch_bounds__(kThreadsAcc, 1)
     oz_gemm_acc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
-                       int Bp, int M, int N, int num_kb, const int* __restrict__ eA, const int* __restrict__ eB,
-                       double* __restrict__ C, int64_t ldc, int lower_only, int* __restrict__ err) {
+                       int Bp, int M, int N, int num_kb_all, const int* __restrict__ eA, const int* __restrict__ eB,
+                       const AccOut o, int* __restrict__ err) {
   const int n0 = blockIdx.x * oz::BN, m0 = blockIdx.y * oz::BM;
-  if (lower_only && n0 >= m0 + oz::BM) return;
+  if (o.lower_only && n0 >= m0 + oz::BM) return;
+  const int num_kb = o.tri_b ? min(num_kb_all, (n0 + oz::BN + oz::KB - 1) / oz::KB) : num_kb_all;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sB = smem;
@@ -755,10 +826,30 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
     }
     if (go && row < M) {
+      if (o.mode == ACC_ROWMAJOR) {
 #pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        const int col = n0 + cbase + t;
-        if (col < N) C[(int64_t)row * ldc + col] = (double)rh[t] + (double)rl[t];
+        for (int t = 0; t < 32; ++t) {
+          const int col = n0 + cbase + t;
+          if (col < N) o.C[(int64_t)row * o.ldc + col] = (double)rh[t] + (double)rl[t];
+        }
+      } else if (o.mode == ACC_COLMAJOR) {  // lanes hold consecutive rows: coalesced per column
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int col = n0 + cbase + t;
+          if (col < N) {
+            const double v = (double)rh[t] + (double)rl[t];
+            o.C[(int64_t)col * o.ldc + row] = v;
+            if (o.C32) o.C32[(int64_t)col * o.ldc + row] = (float)v;
+          }
+        }
+      } else {  // ACC_ROWSQ
+        double sq = 0.0;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const double v = (double)rh[t] + (double)rl[t];
+          if (n0 + cbase + t < N) sq = fma(v, v, sq);
+        }
+        o.sq[((int64_t)blockIdx.x * 2 + (cbase >> 5)) * o.ldc + row] = sq;
       }
     }
   }
@@ -1144,7 +1235,8 @@ static gdml_status syrk_sliced(int64_t k, int64_t K, double* C, int64_t ldc, con
   if (s == GDML_OK) {
     slice(a);
     dim3 grid((unsigned)cdiv(k, oz::BN), (unsigned)cdiv(k, oz::BM));
-    { oz_gemm_acc_kernel<<<grid, kThreadsAcc, kSmemTotal, st>>>(a.map, mapB, (int)a.Rp, (int)a.Rp, (int)k, (int)k, (int)(a.Kp / oz::KB), a.e, a.e, C, ldc, 1, t.err); count_launch(); }
+    const AccOut o{ACC_ROWMAJOR, 1, 0, C, nullptr, nullptr, ldc};
+    { oz_gemm_acc_kernel<<<grid, kThreadsAcc, kSmemTotal, st>>>(a.map, mapB, (int)a.Rp, (int)a.Rp, (int)k, (int)k, (int)(a.Kp / oz::KB), a.e, a.e, o, t.err); count_launch(); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) s = fail(GDML_ERR_CUDA, std::string("sliced syrk launch: ") + cudaGetErrorString(e));
   }
@@ -1177,6 +1269,62 @@ gdml_status oz_syrk_lower_f64(const double* X, int64_t rows, int64_t K, int64_t 
     dim3 g((unsigned)rows, (unsigned)a.nchunks);
     { oz_slice_rows_kernel<<<g, 256, 0, st>>>(X, ldx, K, rows, a.Rp, a.Kp, (bf16*)a.slices, a.e, nullptr, nullptr); count_launch(); }
   }, st);
+}
+
+gdml_status oz_gemm_tall(const double* A, int64_t n, int64_t K, const double* B, int64_t NB, int64_t ldb, bool tri_b,
+                         bool rowsq, double* out, float* out32, cudaStream_t st) {
+  if (n <= 0 || K <= 0 || NB <= 0 || !A || !B || !out) return fail(GDML_ERR_ARG, "oz_gemm_tall: bad arguments");
+  if (NB > ((int64_t)1 << 24) || K > ((int64_t)1 << 24)) return fail(GDML_ERR_ARG, "oz_gemm_tall: sizes too large");
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(oz_gemm_acc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal) !=
+        cudaSuccess)
+      return fail(GDML_ERR_CUDA, "cudaFuncSetAttribute(sliced gemm)");
+    attr_set = true;
+  }
+  // rows of A per panel: the panel's slices (7 x P x Kp BF16) are the only copy of A made
+  const int64_t P = std::min<int64_t>(cdiv(n, oz::BM) * oz::BM, 65536);
+  const int64_t nbt = cdiv(NB, oz::BN);
+  OzMatvec t;
+  OzOperand a, b;
+  double* sq = nullptr;
+  gdml_status s = make_operand(t, b, NB, K, oz::BN, st);
+  if (s == GDML_OK) s = make_operand(t, a, P, K, oz::BM, st);
+  if (s == GDML_OK && rowsq) s = oz_alloc(t, &sq, (size_t)(2 * nbt * n), st);
+  if (s == GDML_OK) s = oz_alloc(t, &t.err, 1, st);
+  if (s == GDML_OK) {
+    slice_rows(B, ldb, b, st);
+    for (int64_t p0 = 0; p0 < n && s == GDML_OK; p0 += P) {
+      const int64_t rows = std::min(P, n - p0);
+      a.rows = rows;  // exponents of this panel are indexed [chunk][rows]
+      {
+        dim3 g((unsigned)cdiv(rows, 16), (unsigned)a.nchunks);
+        oz_slice_cols_kernel<double><<<g, 256, 0, st>>>(A, n, p0, rows, K, a.Rp, a.Kp, (bf16*)a.slices, a.e);
+        count_launch();
+      }
+      AccOut o{rowsq ? ACC_ROWSQ : ACC_COLMAJOR, 0, tri_b ? 1 : 0, rowsq ? nullptr : out + p0,
+               (!rowsq && out32) ? out32 + p0 : nullptr, rowsq ? sq + p0 : nullptr, n};
+      dim3 grid((unsigned)nbt, (unsigned)cdiv(rows, oz::BM));
+      { oz_gemm_acc_kernel<<<grid, kThreadsAcc, kSmemTotal, st>>>(a.map, b.map, (int)a.Rp, (int)b.Rp, (int)rows, (int)NB, (int)(a.Kp / oz::KB), a.e, b.e, o, t.err); count_launch(); }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) s = fail(GDML_ERR_CUDA, std::string("sliced tall gemm launch: ") + cudaGetErrorString(e));
+    }
+    if (s == GDML_OK && rowsq) {
+      oz_rowsq_reduce_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(sq, (int)(2 * nbt), n, out);
+      count_launch();
+    }
+  }
+  if (s == GDML_OK) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, t.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      s = fail(GDML_ERR_CUDA, "sliced tall gemm: synchronise");
+    else if (h)
+      s = fail(GDML_ERR_TIMEOUT, "sliced tall gemm: a tcgen05 pipeline wait timed out");
+  }
+  cudaStreamSynchronize(st);
+  oz_destroy(t);
+  return s;
 }
 
 gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,

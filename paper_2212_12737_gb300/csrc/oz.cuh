@@ -88,6 +88,15 @@ gdml_status oz_syrk_lower(const float* L, int64_t n, int64_t k, double* C, int64
 gdml_status oz_syrk_lower_f64(const double* X, int64_t rows, int64_t K, int64_t ldx, double* C, int64_t ldc,
                               cudaStream_t st);
 
+// C = A B^T for a tall A (n x K, column-major: entry (r, j) at A[j n + r]) and B (NB x K,
+// row-major, row stride ldb; lower triangular when tri_b, so K entries past each row's
+// diagonal are skipped) through the sliced tensor-core GEMM with in-CTA accumulation over
+// all of K (FP64-class).  A is sliced in panels of rows.  rowsq = false: C stored
+// column-major, out[c n + r] (and as FP32 at out32[c n + r] when out32 is not null); out may
+// alias A.  rowsq = true: out[r] = sum_c C[r][c]^2 (n doubles).  Synchronises the stream.
+gdml_status oz_gemm_tall(const double* A, int64_t n, int64_t K, const double* B, int64_t NB, int64_t ldb, bool tri_b,
+                         bool rowsq, double* out, float* out32, cudaStream_t st);
+
 // test hook: C (M x N, FP64) = A (M x K) B (N x K)^T through the sliced tensor-core GEMM
 gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,
                          cudaStream_t st);

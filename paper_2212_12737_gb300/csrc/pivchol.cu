@@ -19,7 +19,9 @@
 
 namespace gdml {
 
-constexpr int kArgBlocks = 2 * kNumSMs;
+constexpr int kArgMaxBlocks = 1024;  // size of the argmax partial buffer
+// two CTAs per SM for the argmax / trace reductions
+inline int arg_blocks() { return std::min(2 * num_sms(), kArgMaxBlocks); }
 constexpr int kArgThreads = 256;
 
 struct ArgMax {
@@ -642,14 +644,14 @@ int pivchol_schur_groups() { return kSchurMaxGroups; }
 void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
   const int64_t rblocks = cdiv(a.n, kSchurRows);
   const bool vec = (a.n % 4) == 0;
-  const unsigned fblocks = (unsigned)std::min<int64_t>(cdiv(a.n, kArgThreads), kArgBlocks);
+  const unsigned fblocks = (unsigned)std::min<int64_t>(cdiv(a.n, kArgThreads), arg_blocks());
   // n % 4 == 0: the Schur sums run through the TMA-staged pass (one partial per row)
   WsPlan plan;
   if (a.err) ws_plan(plan, L, a.n, a.k);
   // one argmax partial per CTA: the staged kernel's grid-stride loop takes any grid size
-  if (plan.grid > kArgBlocks) plan.grid = kArgBlocks;
+  if (plan.grid > arg_blocks()) plan.grid = arg_blocks();
   // step 0's pivot
-  { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(0, a.n, 1, a.d, a.perm, a.chosen, a.pivots, nullptr,
+  { pc_argmax_kernel<<<arg_blocks(), kArgThreads, 0, st>>>(0, a.n, 1, a.d, a.perm, a.chosen, a.pivots, nullptr,
                                                        a.ps, a.part, a.ticket, a.posof); count_launch(); }
   if (plan.ok) {  // two launches per step: the kernel column, then Schur sums + finish
     static bool attr = false;
@@ -676,7 +678,7 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
     // column groups: enough CTAs for ~4 per SM, at least 32 columns per group
     int groups = 0;
     if (m > 0) {
-      const int64_t want = cdiv(4 * kNumSMs, rblocks);
+      const int64_t want = cdiv(4 * (int64_t)num_sms(), rblocks);
       groups = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)kSchurMaxGroups, std::max<int64_t>(1, m / 32)}));
       dim3 g((unsigned)rblocks, (unsigned)groups);
       if (vec)
@@ -692,19 +694,19 @@ void pivchol_run_df(const PivCholArgs& a, float* L, cudaStream_t st) {
 template <typename TL>
 void pivchol_run(const PivCholArgs& a, TL* L, cudaStream_t st) {
   for (int64_t m = 0; m < a.k; ++m) {
-    { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(m, a.n, 1, a.d, a.perm, a.chosen, a.pivots, a.trace,
+    { pc_argmax_kernel<<<arg_blocks(), kArgThreads, 0, st>>>(m, a.n, 1, a.d, a.perm, a.chosen, a.pivots, a.trace,
                                                          a.ps, a.part, a.ticket); count_launch(); }
     a.get_col(a.pivots + m, a.col, &a.ps->stop, st);
     { pc_update_kernel<TL><<<(unsigned)cdiv(a.n, 256), 256, 0, st>>>(m, a.n, L, a.col, a.d, a.chosen, a.ps); count_launch(); }
   }
   // trace after the last step
-  { pc_argmax_kernel<<<kArgBlocks, kArgThreads, 0, st>>>(a.k, a.n, 0, a.d, a.perm, a.chosen, a.pivots, a.trace,
+  { pc_argmax_kernel<<<arg_blocks(), kArgThreads, 0, st>>>(a.k, a.n, 0, a.d, a.perm, a.chosen, a.pivots, a.trace,
                                                        a.ps, a.part, a.ticket); count_launch(); }
 }
 
 template void pivchol_run<double>(const PivCholArgs&, double*, cudaStream_t);
 template void pivchol_run<float>(const PivCholArgs&, float*, cudaStream_t);
 
-int pivchol_part_blocks() { return kArgBlocks; }
+int pivchol_part_blocks() { return kArgMaxBlocks; }
 
 }  // namespace gdml

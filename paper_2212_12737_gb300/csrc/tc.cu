@@ -348,7 +348,7 @@ static gdml_status setup_impl(TcMatvec& tc, const double* Xc, const double* A, i
   const int64_t tiles = cdiv(tc.Dp, tc.bn2) * cdiv(M, BM);
   const int64_t num_kb2 = tc.K2p / span;
   // split K until the grid covers ~3 waves of the SMs (the autotuner can refine it)
-  tc.splits2 = (int)std::max<int64_t>(1, std::min<int64_t>(num_kb2 / 8, cdiv(3 * kNumSMs, std::max<int64_t>(tiles, 1))));
+  tc.splits2 = (int)std::max<int64_t>(1, std::min<int64_t>(num_kb2 / 8, cdiv(3 * (int64_t)num_sms(), std::max<int64_t>(tiles, 1))));
   tc.splits_cap = std::max(tc.splits2, 8);
   TC_TRY(tc_alloc(tc, &tc.U, (size_t)(tc.splits_cap * M * tc.Dp)));
   if (cudaMemsetAsync(xc, 0, M * tc.Dp * sizeof(T), st) != cudaSuccess ||

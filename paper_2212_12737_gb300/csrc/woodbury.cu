@@ -616,13 +616,7 @@ __global__ void __launch_bounds__(kWsThreads, 2)
 void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows) {
   plan = WsPlan();
   if (!L || n < 4 || k < 1 || n % 4 != 0 || n > (int64_t(1) << 30) || k > (int64_t(1) << 30)) return;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-      sms = 1;
-  }
+  const int sms = num_sms();
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(ws_gemv_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmemT) != cudaSuccess ||
@@ -959,6 +953,15 @@ void split_df_inplace(double* a, int64_t count, cudaStream_t st) {
 __global__ void to_float_kernel(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void widen_float_kernel(const float* __restrict__ a, int64_t n, double* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+void widen_float(const float* a, int64_t n, double* b, cudaStream_t st) {
+  { widen_float_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(a, n, b); count_launch(); }
 }
 
 void to_float(const double* a, int64_t n, float* b, cudaStream_t st) {

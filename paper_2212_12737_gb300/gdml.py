@@ -25,7 +25,7 @@ SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3}
 
 EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
-           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_test_oz_gemm", "gdml_test_df_passes", "gdml_tc_check",
+           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_test_oz_gemm", "gdml_test_df_passes", "gdml_test_oz_gemm_tall", "gdml_test_precond_factor", "gdml_tc_check",
            "gdml_launch_count", "gdml_matvec_noalloc", "gdml_pcg_solve_batched", "gdml_autotune",
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
@@ -74,6 +74,8 @@ def load() -> ctypes.CDLL:
         "gdml_test_tc_gemm": [I32, P, P, I32, I32, I32, P, P],
         "gdml_test_oz_gemm": [P, P, I64, I64, I64, P, P],
         "gdml_test_df_passes": [P, I64, I64, P, P, D, I32, P, P, P],
+        "gdml_test_oz_gemm_tall": [P, I64, I64, P, I64, I64, I32, I32, P, P, P],
+        "gdml_test_precond_factor": [P, P],
         "gdml_tc_check": [P],
         "gdml_launch_count": [],
         "gdml_matvec_noalloc": [P, I64, I32, D, D, P, P, I32, P],
@@ -126,6 +128,22 @@ def _ptr(t: torch.Tensor | None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _vec_arg(t: torch.Tensor, n: int, device: torch.device, name: str) -> torch.Tensor:
+    """A float64 vector of n elements on `device`, contiguous: the library reads or writes
+    exactly n doubles at its address, so anything else is rejected here."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{name} must hold {n} elements, got {t.numel()}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
 class Context:
     """One kernel system (Sec. 2.1, Eq. 1) living on the current CUDA device."""
 
@@ -151,14 +169,18 @@ class Context:
             raise GdmlError(st, load().gdml_last_error(self._h).decode())
 
     def _vec(self, out):
-        return torch.empty(self.n, dtype=torch.float64, device=self.device) if out is None else out
+        if out is None:
+            return torch.empty(self.n, dtype=torch.float64, device=self.device)
+        return _vec_arg(out, self.n, self.device, "out")
 
     def matvec(self, v: torch.Tensor, out: torch.Tensor | None = None, add_lambda: bool = True) -> torch.Tensor:
+        _vec_arg(v, self.n, self.device, "v")
         out = self._vec(out)
         self._check(load().gdml_matvec(self._h, _ptr(v), _ptr(out), int(add_lambda)))
         return out
 
     def matvec_fp64(self, v: torch.Tensor, out: torch.Tensor | None = None, add_lambda: bool = True) -> torch.Tensor:
+        _vec_arg(v, self.n, self.device, "v")
         out = self._vec(out)
         self._check(load().gdml_matvec_fp64(self._h, _ptr(v), _ptr(out), int(add_lambda)))
         return out
@@ -205,9 +227,17 @@ class Context:
         return int(r.value), float(j.value)
 
     def precond_apply(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        _vec_arg(r, self.n, self.device, "r")
         out = self._vec(out)
         self._check(load().gdml_precond_apply(self._h, _ptr(r), _ptr(out)))
         return out
+
+    def precond_factor(self) -> torch.Tensor:
+        """The built preconditioner's factor L_k (n x rank) as FP64 (test hook)."""
+        rank, _ = self.precond_info()
+        out = torch.empty(rank, self.n, dtype=torch.float64, device=self.device)
+        self._check(load().gdml_test_precond_factor(self._h, _ptr(out)))
+        return out.t()
 
     def set_inner_rtol(self, v: float):
         self._check(load().gdml_set_inner_rtol(self._h, float(v)))
@@ -215,8 +245,10 @@ class Context:
     def pcg_solve(self, y: torch.Tensor, alpha: torch.Tensor | None = None, rtol: float = 1e-8,
                   max_iter: int = 20000, raise_on_nonconvergence: bool = True):
         """Returns (alpha, iterations, true relative residual, outer refinement steps)."""
+        _vec_arg(y, self.n, self.device, "y")
         if alpha is None:
             alpha = torch.zeros(self.n, dtype=torch.float64, device=self.device)
+        _vec_arg(alpha, self.n, self.device, "alpha")
         it = ctypes.c_int32()
         rel = ctypes.c_double()
         st = load().gdml_pcg_solve(self._h, _ptr(y), _ptr(alpha), float(rtol), int(max_iter), ctypes.byref(it),
@@ -317,6 +349,28 @@ def test_oz_gemm(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     return C
 
 
+def test_oz_gemm_tall(A: torch.Tensor, B: torch.Tensor, tri_b: bool = False, rowsq: bool = False):
+    """The OZAKI build's tall sliced GEMM: C = A B^T with A (n x K) and B (NB x K) FP64 (B lower
+    triangular when tri_b).  Returns C (n x NB) and its FP32 copy, or the row square sums of C
+    (n,) when rowsq."""
+    lib = load()
+    n, K = A.shape
+    NB = B.shape[0]
+    Ac = A.t().contiguous()  # column j at offset j n
+    B = B.contiguous()
+    if rowsq:
+        out = torch.empty(n, dtype=torch.float64, device=A.device)
+        out32 = None
+    else:
+        out = torch.empty(NB, n, dtype=torch.float64, device=A.device)
+        out32 = torch.empty(NB, n, dtype=torch.float32, device=A.device)
+    st = lib.gdml_test_oz_gemm_tall(_ptr(Ac), n, K, _ptr(B), NB, K, int(tri_b), int(rowsq), _ptr(out), _ptr(out32),
+                                    ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
+    if st != 0:
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+    return out if rowsq else (out.t(), out32.t())
+
+
 def test_df_passes(L: torch.Tensor, r: torch.Tensor, u: torch.Tensor, lam: float, staged=True):
     """The two passes over the FP32 factor of the DF64/OZAKI Woodbury apply:
     returns (t, z) with t = L^T r and z = (r - L u) / lam.  L: n x k FP32 (its columns
@@ -348,13 +402,19 @@ def matvec_noalloc(R: torch.Tensor, sigma: float, lam: float, v: torch.Tensor, o
     """K v (+ lam v) with no context and no device allocation inside the library
     (M <= 128 geometries, N <= 24 atoms; scratch is a static device array)."""
     lib = load()
-    if R.dtype != torch.float64 or R.dim() != 3 or R.shape[2] != 3:
+    if R.dtype != torch.float64 or R.dim() != 3 or R.shape[2] != 3 or not R.is_cuda:
         raise ValueError("R must be a float64 CUDA tensor of shape (M, N, 3)")
+    n = 3 * int(R.shape[0]) * int(R.shape[1])
+    _vec_arg(v, n, R.device, "v")
     if out is None:
-        out = torch.empty_like(v)
-    st = lib.gdml_matvec_noalloc(_ptr(R.contiguous()), int(R.shape[0]), int(R.shape[1]), float(sigma), float(lam),
-                                 _ptr(v), _ptr(out), int(add_lambda),
-                                 ctypes.c_void_p(torch.cuda.current_stream(R.device).cuda_stream))
+        out = torch.empty(n, dtype=torch.float64, device=R.device)
+    _vec_arg(out, n, R.device, "out")
+    R = R.contiguous()
+    # the library looks up its static scratch array on the CURRENT device: make it R's
+    with torch.cuda.device(R.device):
+        st = lib.gdml_matvec_noalloc(_ptr(R), int(R.shape[0]), int(R.shape[1]), float(sigma), float(lam),
+                                     _ptr(v), _ptr(out), int(add_lambda),
+                                     ctypes.c_void_p(torch.cuda.current_stream(R.device).cuda_stream))
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())
     return out

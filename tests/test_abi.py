@@ -86,3 +86,23 @@ def test_plain_c_program_uses_the_abi(lib_path, tmp_path):
     assert out.returncode == 0, out.stderr
     k, msg = out.stdout.split(" ", 1)
     assert int(k) == 5833 and "rule_of_thumb_k" in msg
+
+
+def test_binding_rejects_vectors_the_library_would_overrun():
+    """The library reads / writes exactly n doubles at each vector's address, so the binding
+    refuses anything that is not a contiguous float64 vector of n elements on the right device."""
+    import torch
+    from paper_2212_12737_gb300 import gdml
+    cpu = torch.device("cpu")
+    ok = torch.zeros(6, dtype=torch.float64)
+    assert gdml._vec_arg(ok, 6, cpu, "v") is ok
+    with pytest.raises(ValueError, match="float64"):
+        gdml._vec_arg(torch.zeros(6, dtype=torch.float32), 6, cpu, "v")
+    with pytest.raises(ValueError, match="6 elements"):
+        gdml._vec_arg(torch.zeros(5, dtype=torch.float64), 6, cpu, "v")
+    with pytest.raises(ValueError, match="must be on"):
+        gdml._vec_arg(torch.zeros(6, dtype=torch.float64, device="meta"), 6, cpu, "v")
+    with pytest.raises(ValueError, match="contiguous"):
+        gdml._vec_arg(torch.zeros(12, dtype=torch.float64)[::2], 6, cpu, "v")
+    with pytest.raises(TypeError):
+        gdml._vec_arg([0.0] * 6, 6, cpu, "v")

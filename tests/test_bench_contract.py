@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_the_contract_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, timeout=900, cwd=ROOT)
+                          "--warmup", "0", "--workload", "ethanol9_m200"], capture_output=True, text=True,
+                         timeout=900, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -18,7 +19,8 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference"
     assert d["unit"] == "s" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0
-    assert d["config"]["workload"] == "aspirin21_m1000"
+    assert d["config"]["workload"] == "ethanol9_m200"
+    assert d["extrapolated"] is True and d["cpu_baseline"]["iters"] > 0 and d["cpu_baseline"]["blas"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]

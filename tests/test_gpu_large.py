@@ -43,3 +43,37 @@ def test_full_size_matvec_on_sampled_blocks(big, sampled, prec, tol):
     print(f"{prec} matvec at n={w.n}: relative error on sampled blocks {err:.2e}")
     assert err <= tol
     ctx.destroy()
+
+
+def test_full_size_rls_solve_reaches_rtol_by_the_oracle(big):
+    """The 630,000-unknown system end to end in the OZAKI form: the leverage-score
+    preconditioner at k = 5000 (pilot Nystrom factor, its core and the scores on the sliced
+    tensor cores), PCG to a relative residual of 1e-8, and the oracle's own FP64 matvec
+    recomputing the true residual of the GPU's alpha.  The evaluation error of that check
+    is bounded by 8 eps |K|_2 |alpha| / |y|, with |K|_2 from a power iteration."""
+    w = big
+    eps = np.finfo(float).eps
+    R, y = torch.from_numpy(w.R).cuda(), torch.from_numpy(w.y).cuda()
+    ctx = gdml.kernel_setup(R, w.sigma, w.lam, precision="ozaki")
+    tau = ctx.rls_scores(w.k, seed=2).cpu().numpy()
+    assert tau.min() >= -1e-9 and tau.max() <= 1.0 + 1e-9 and tau.sum() <= w.k * (1.0 + 1e-9)
+    piv, _ = ctx.precond_build("rls", w.k, seed=2, pivots=True)
+    p = piv.cpu().numpy()
+    assert len(np.unique(p)) == w.k and p.min() >= 0 and p.max() < w.n
+    rank, _ = ctx.precond_info()
+    assert rank == w.k
+    alpha, iters, rel, _ = ctx.pcg_solve(y, rtol=1e-8, max_iter=20000)
+    ctx.tc_check()
+    v = torch.from_numpy(np.random.default_rng(3).standard_normal(w.n)).cuda()
+    for _ in range(30):
+        v = ctx.matvec(v, add_lambda=False)
+        knorm = float(torch.linalg.norm(v))
+        v = v / knorm
+    ctx.destroy()
+    a = alpha.cpu().numpy()
+    res = np.linalg.norm(w.y - ok.matvec_parallel(w.R, w.sigma, a, w.lam)) / np.linalg.norm(w.y)
+    bound = 8 * eps * knorm * np.linalg.norm(a) / np.linalg.norm(w.y)
+    print(f"n={w.n} rls k={w.k}: {iters} PCG iterations, GPU relres {rel:.2e}, oracle relres {res:.2e} "
+          f"(evaluation bound {bound:.1e})")
+    assert rel <= 1e-8
+    assert res <= 1e-8 + bound

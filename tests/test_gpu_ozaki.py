@@ -7,6 +7,7 @@ import pytest
 import torch
 
 from oracle import kernel as ok
+from oracle import precond as op
 from paper_2212_12737_gb300 import gdml, synth
 
 pytestmark = pytest.mark.gpu
@@ -131,3 +132,64 @@ def test_ozaki_preconditioner_matches_df64():
     rel = np.linalg.norm(za - zb) / np.linalg.norm(za)
     print(f"preconditioner apply, ozaki vs df64 build: {rel:.2e}")
     assert rel <= 1e-6
+
+
+@pytest.mark.parametrize("n,K,NB,tri", [(1, 1, 1, True), (300, 130, 70, False), (1000, 300, 257, True),
+                                        (70000, 520, 130, True)])
+def test_sliced_tall_gemm_matches_fp64(n, K, NB, tri):
+    """The OZAKI build's accumulating GEMM with a column-major tall A: ragged n, K and NB,
+    one and several 256-entry K chunks, two row panels (n > 65,536), the triangular K skip,
+    the column-major FP64 / FP32 store and the row square sums."""
+    rng = np.random.default_rng(n + K + NB)
+    A = rng.standard_normal((n, K)) * 10.0 ** rng.uniform(-3, 3, size=(n, 1))
+    B = rng.standard_normal((NB, K))
+    if tri:
+        B = np.tril(B)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C, C32 = gdml.test_oz_gemm_tall(Ad, Bd, tri_b=tri)
+    C = C.cpu().numpy()
+    ref = A @ B.T
+    # the slices keep 49 bits of each entry below its 256-entry chunk's largest magnitude, so a
+    # chunk's products err by at most ~2^-48 KC max|a| max|b| (dropped slice pairs far below);
+    # the FP64 reference adds its own rounding, 8 eps sum |a||b|
+    bound = 8 * EPS * (np.abs(A) @ np.abs(B).T)
+    for q0 in range(0, K, 256):
+        ma = np.abs(A[:, q0:q0 + 256]).max(axis=1)
+        mb = np.abs(B[:, q0:q0 + 256]).max(axis=1)
+        bound += 2.0 ** -47 * min(256, K - q0) * np.outer(ma, mb)
+    err = (np.abs(C - ref) / np.maximum(bound, 1e-300)).max()
+    print(f"tall sliced gemm {n}x{NB}x{K} tri={tri}: max error / bound = {err:.3f}")
+    assert err <= 1.0
+    assert np.array_equal(C32.cpu().numpy(), C.astype(np.float32))
+    sq = gdml.test_oz_gemm_tall(Ad, Bd, tri_b=tri, rowsq=True).cpu().numpy()
+    own = np.sum(C * C, axis=1)
+    assert np.all(np.abs(sq - own) <= 1e-13 * own)
+
+
+@pytest.mark.parametrize("prec", ["df64", "ozaki"])
+@pytest.mark.parametrize("method,k", [("uniform", 400), ("rls", 150)])
+def test_nystrom_factor_matches_oracle(prec, method, k):
+    """L_k = K_nk L_kk^-T (Eq. 5) element by element against the oracle's factor for the same
+    inducing columns.  DF64 forms it by FP64 substitution, OZAKI as K_nk times the explicit
+    triangular inverse on the sliced tensor cores; both store it in FP32.  Bound per entry:
+    the FP32 rounding 2^-24 |L| plus 64 eps of the products' magnitude |K_nk| |L_kk^-1|^T."""
+    w = synth.workload("ethanol9_m200")
+    ctx = gdml.kernel_setup(torch.from_numpy(w.R).cuda(), w.sigma, w.lam, precision=prec)
+    piv, _ = ctx.precond_build(method, k, seed=2, pivots=True)
+    rank, jit = ctx.precond_info()
+    Lg = ctx.precond_factor().cpu().numpy()
+    ctx.destroy()
+    S = piv.cpu().numpy()
+    K = ok.force_kernel_dense(w.R, w.sigma)
+    Lr, eps = op.nystrom_factor(K[:, S], S)
+    assert rank == k and jit == eps
+    L_kk, _ = op.cholesky_jitter(K[np.ix_(S, S)])
+    Linv = np.linalg.inv(L_kk)
+    # magnitudes of the product K_nk L_kk^-T and of the substitution's error terms
+    mag = np.abs(K[:, S]) @ np.abs(Linv).T + (np.abs(Lr) @ np.abs(L_kk).T) @ np.abs(Linv).T
+    bound = 2.0 ** -24 * np.abs(Lr) + 4 * k * EPS * mag
+    worst = (np.abs(Lg - Lr) / bound).max()
+    print(f"{prec} {method} k={k} (jitter {jit:.1e}): max |L_gpu - L_oracle| / bound = {worst:.3f}")
+    assert worst <= 1.0
+    if jit == 0.0:  # Eq. 5: the rows of L_k at the inducing columns are L_kk (lower triangular)
+        assert np.abs(np.triu(Lg[S], 1)).max() <= 1e-6 * np.abs(Lr).max()

@@ -143,3 +143,25 @@ def test_sampled_rows_equal_full_matvec(tiny):
     full = ok.matvec(R, 1.3, v, 1e-4).reshape(R.shape[0], -1)
     np.testing.assert_allclose(ok.matvec_rows(R, 1.3, v, [2, 0], 1e-4), full[[2, 0]], rtol=0,
                                atol=1e-14 * np.abs(full).max())
+
+
+def test_projection_equals_dense_jacobian_product(tiny):
+    """project(): J_a v_a from the two nonzeros per Jacobian row equals the dense J_a v_a."""
+    R, _ = tiny
+    v = np.random.default_rng(4).standard_normal(R.size)
+    Jac = ok.jacobian(R)
+    dense = np.einsum("apk,ak->ap", Jac, v.reshape(R.shape[0], -1))
+    np.testing.assert_allclose(ok.project(R, v), dense, rtol=0, atol=1e-14 * np.abs(dense).max())
+
+
+def test_parallel_matvec_equals_dense_k(tiny):
+    """matvec_parallel (row blocks in spawned worker processes) equals (K + lam I) v with K
+    assembled densely, and the serial matvec."""
+    from paper_2212_12737_gb300 import synth
+    R = synth.geometries(synth.template(6, 3), 9, 0.2, 4)
+    v = np.random.default_rng(5).standard_normal(R.size)
+    K = ok.force_kernel_dense(R, 1.7)
+    ref = K @ v + 1e-3 * v
+    got = ok.matvec_parallel(R, 1.7, v, 1e-3, workers=2)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    np.testing.assert_allclose(got, ok.matvec(R, 1.7, v, 1e-3), rtol=0, atol=1e-13 * np.abs(ref).max())

@@ -58,6 +58,30 @@ def test_weighted_selection_equal_weights_takes_largest_uniforms():
     assert np.all(op.select_weighted(tau, 100, 5) % 2 == 1)
 
 
+def test_weighted_selection_first_pick_is_proportional_to_weight():
+    """Efraimidis-Spirakis: the smallest key -ln(u_i)/tau_i is index i with probability
+    tau_i / sum(tau).  Over many seeds the first pick's counts fit those probabilities (chi^2);
+    a key with the wrong power of tau (e.g. -ln(u)/tau^2, giving tau^2 / sum tau^2) fails."""
+    from scipy.stats import chisquare
+    tau = np.array([1.0, 2.0, 3.0, 4.0, 10.0])
+    seeds = 4000
+    counts = np.zeros(tau.size)
+    for s in range(seeds):
+        counts[op.select_weighted(tau, 1, s)[0]] += 1
+    assert chisquare(counts, seeds * tau / tau.sum()).pvalue > 1e-4
+    assert chisquare(counts, seeds * tau ** 2 / (tau ** 2).sum()).pvalue < 1e-12
+    # without replacement: the second pick, given the first, is proportional to the rest
+    pair = np.zeros((tau.size, tau.size))
+    for s in range(seeds):
+        a, b = op.select_weighted(tau, 2, s)
+        assert a != b
+        pair[a, b] += 1
+    first = 4  # the heaviest weight is picked first often enough to test its row
+    rest = np.delete(np.arange(tau.size), first)
+    row = pair[first, rest]
+    assert chisquare(row, row.sum() * tau[rest] / tau[rest].sum()).pvalue > 1e-4
+
+
 # ---- Woodbury and Nystrom (Eqs. 3-5) --------------------------------------
 
 def test_woodbury_inverts_dense_p():

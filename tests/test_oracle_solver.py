@@ -94,6 +94,35 @@ def test_pcg_reports_non_convergence(system):
     assert not res.converged and res.iters == 3
 
 
+def test_pcg_restarts_when_the_recurrence_residual_drifts():
+    """The restart branch: one corrupted product makes the recurrence residual r disagree
+    with y - A x; when r passes rtol the true residual does not, and PCG must restart from x
+    (then converge to the exact solution); with no restarts allowed it must report failure."""
+    rng = np.random.default_rng(5)
+    n = 30
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q * np.linspace(1.0, 50.0, n)) @ Q.T
+    y = rng.standard_normal(n)
+    x_star = np.linalg.solve(A, y)
+
+    def make_apply():
+        calls = {"n": 0}
+
+        def apply_A(v):
+            calls["n"] += 1
+            out = A @ v
+            if calls["n"] == 3:  # one wrong product inside the first CG run
+                out = out + 1e-3 * np.linalg.norm(out) * rng.standard_normal(n)
+            return out
+        return apply_A
+
+    res = osv.pcg(make_apply(), lambda r: r, y, rtol=1e-10, max_iter=500, max_restarts=3)
+    assert res.restarts >= 1 and res.converged and res.relres <= 1e-10
+    np.testing.assert_allclose(res.x, x_star, rtol=0, atol=1e-8 * np.abs(x_star).max())
+    res0 = osv.pcg(make_apply(), lambda r: r, y, rtol=1e-10, max_iter=500, max_restarts=0)
+    assert res0.restarts == 0 and not res0.converged and res0.relres > 1e-10
+
+
 # ---- generator (inputs, not method) ---------------------------------------
 
 def test_morse_forces_are_minus_energy_gradient_and_rigid_free():
