@@ -216,6 +216,92 @@ def matvec_parallel(R: np.ndarray, sigma: float, v: np.ndarray, lam: float = 0.0
     return np.concatenate(parts).reshape(-1)
 
 
+# ---- sGDML: permutational symmetries (Sec. 4.3, "Remarks on runtime": the kernel's forward
+# pass grows with the number of symmetries) ------------------------------------------------
+# A symmetry group of the molecule is given as S atom permutations sigma_q (sigma_q[i] = the
+# atom that takes atom i's place).  Permuting the atoms of R_b permutes its descriptor entries:
+# x(R_b^(q))_p = x(R_b)_{pi_q(p)} with pi_q(p) the pair index of (sigma_q(i), sigma_q(j)).  The
+# symmetric scalar kernel is kappa_S(R_a, R_b) = sum_q kappa(x_a, P_q x_b) (no normalisation;
+# the reading is stated in the design doc's R18), so its force kernel is
+#   K_ab = sum_q J_a^T H(x_a, P_q x_b) P_q J_b,
+# where P_q x_b and P_q J_b take rows pi_q(p) of x_b and J_b.
+
+def pair_permutation(N: int, perm) -> np.ndarray:
+    """pi(p) = pair index of (perm[i], perm[j]) for descriptor entry p = (i, j): x(R with atoms
+    permuted by perm)_p = x(R)_pi(p)."""
+    perm = np.asarray(perm, dtype=np.int64)
+    I, J = pair_index(N)
+    a, b = perm[I], perm[J]
+    hi, lo = np.maximum(a, b), np.minimum(a, b)
+    return hi * (hi - 1) // 2 + lo
+
+
+def sym_kernel_value(Ra: np.ndarray, Rb: np.ndarray, sigma: float, perms) -> float:
+    """kappa_S(R_a, R_b) = sum_q kappa(x(R_a), x(R_b with its atoms permuted by perm q)): the
+    scalar symmetric kernel from atomic coordinates (used to pin its force kernel)."""
+    xa = descriptor(Ra[None])[0][0]
+    tot = 0.0
+    for perm in perms:
+        xb = descriptor(np.asarray(Rb)[np.asarray(perm)][None])[0][0]
+        tot += float(matern52(np.linalg.norm(xa - xb), sigma))
+    return tot
+
+
+def force_kernel_dense_sym(R: np.ndarray, sigma: float, perms) -> np.ndarray:
+    """Assemble the n x n symmetric force kernel block by block:
+    K_ab = sum_q J_a^T H(x_a, P_q x_b) P_q J_b."""
+    M, N, _ = R.shape
+    X, _ = descriptor(R)
+    Jac = jacobian(R)
+    B = 3 * N
+    pis = [pair_permutation(N, p) for p in perms]
+    K = np.zeros((M * B, M * B))
+    for a in range(M):
+        for b in range(M):
+            for pi in pis:
+                H = hessian_block(X[a], X[b][pi], sigma)
+                K[a * B:(a + 1) * B, b * B:(b + 1) * B] += Jac[a].T @ H @ Jac[b][pi]
+    return K
+
+
+def matvec_sym(R: np.ndarray, sigma: float, perms, v: np.ndarray, lam: float = 0.0) -> np.ndarray:
+    """Matrix-free (K + lam I) v with the symmetric force kernel: w_b = J_b v_b;
+    u_a = sum_q sum_b H(x_a, P_q x_b) P_q w_b, each H applied from its definition;
+    (K v)_a = J_a^T u_a."""
+    M, N, _ = R.shape
+    B = 3 * N
+    c = np.sqrt(5.0) / sigma
+    X, _ = descriptor(R)
+    W = project(R, v)
+    V = np.asarray(v, dtype=np.float64).reshape(M, B)
+    U = np.zeros_like(W)
+    for pi in (pair_permutation(N, p) for p in perms):
+        Xq, Wq = X[:, pi], W[:, pi]
+        for a in range(M):
+            d = X[a][None, :] - Xq  # d_ab = x_a - P_q x_b
+            r = np.sqrt(np.einsum("bp,bp->b", d, d))
+            S = (c * c / 3.0) * np.exp(-c * r)
+            proj = np.einsum("bp,bp->b", d, Wq)
+            U[a] += (S * (1.0 + c * r)) @ Wq - c * c * ((S * proj) @ d)
+    out = np.empty((M, B))
+    for a in range(M):
+        out[a] = jacobian(R[a:a + 1])[0].T @ U[a] + lam * V[a]
+    return out.reshape(-1)
+
+
+def force_kernel_diag_sym(R: np.ndarray, sigma: float, perms) -> np.ndarray:
+    """diag(K) of the symmetric force kernel: diag of sum_q J_a^T H(x_a, P_q x_a) P_q J_a."""
+    M, N, _ = R.shape
+    X, _ = descriptor(R)
+    Jac = jacobian(R)
+    B = 3 * N
+    out = np.zeros((M, B))
+    for pi in (pair_permutation(N, p) for p in perms):
+        for a in range(M):
+            out[a] += np.diag(Jac[a].T @ hessian_block(X[a], X[a][pi], sigma) @ Jac[a][pi])
+    return out.reshape(-1)
+
+
 def predict_forces(R_query: np.ndarray, R: np.ndarray, sigma: float, alpha: np.ndarray) -> np.ndarray:
     """Forces the trained model predicts for query geometries (Sec. 2.1: queried at a cost
     linear in the training set): f_q = sum_b K(q, b) alpha_b with the force-kernel block
