@@ -574,7 +574,7 @@ def run_gpu(args):
 # (its JSON line's solve.iters).  The FP64 oracle cannot run these solves to the end within a
 # benchmark's time, so the reference arm extrapolates its sampled per-iteration cost with
 # these counts; the GPU arm's own CPU baseline uses the iteration count of its run instead.
-REF_ITERS = {"ethanol9_m200": 595, "aspirin21_m1000": 1578, "mol42_m5000": 3393}
+REF_ITERS = {"ethanol9_m200": 595, "aspirin21_m1000": 1578, "mol42_m5000": 3266}
 
 
 def blas_info() -> dict:

@@ -89,6 +89,29 @@ typedef enum {
 gdml_status gdml_kernel_setup(gdml_ctx** ctx, const double* R_dev, int64_t M, int32_t N,
                               double sigma, double lambda, int32_t precision, void* cuda_stream);
 
+/* A context for the symmetric (sGDML) force kernel.  The paper's runtimes include the
+ * molecules' permutational symmetries, and its kernel's forward pass grows with their number
+ * (Sec. 4.3, "Remarks on runtime").  The kernel is
+ *   K_ab = sum_q J_a^T H(x_a, P_q x_b) P_q J_b,
+ * the force kernel of kappa_S(R_a, R_b) = sum_q kappa(x(R_a), x(R_b with its atoms permuted by
+ * sigma_q)), where P_q permutes descriptor entries: (P_q x)_(i,j) = x_(sigma_q(i), sigma_q(j)).
+ *  perms_host: S x N int32 (host memory), row q = sigma_q; sigma_q[i] is the atom that takes
+ *    atom i's place.  The S rows must form a group: each a permutation of 0..N-1, the identity
+ *    among them, closed under composition, and no row repeated.  1 <= S <= 256.
+ *  precision: GDML_FP64 or GDML_OZAKI when S > 1.
+ *  Every other argument is as for gdml_kernel_setup.
+ * Every entry point then uses the symmetric kernel: matvec, preconditioner builds, PCG and
+ * prediction.  Costs:
+ *  - the matvec's two contractions and the M x M setup tables grow by a factor S;
+ *  - kernel columns (the preconditioner builds) are computed in FP64, which limits N to about
+ *    70 atoms.
+ * S = 1 (the identity alone) gives the plain kernel.
+ * Errors: GDML_ERR_ARG (as gdml_kernel_setup, or perms_host NULL / not a group / a precision
+ * other than FP64 or OZAKI with S > 1), GDML_ERR_OOM, GDML_ERR_CUDA (then *ctx is NULL). */
+gdml_status gdml_kernel_setup_sym(gdml_ctx** ctx, const double* R_dev, int64_t M, int32_t N,
+                                  const int32_t* perms_host, int32_t S, double sigma, double lambda,
+                                  int32_t precision, void* cuda_stream);
+
 /* out = K v (+ lambda v if add_lambda), both length n = 3 N M, in the
  * context's precision (FP64 contexts: FP64; TF32/BF16: tensor-core matvec
  * with FP32 accumulation, result stored as double; DF64: double-float
@@ -222,12 +245,14 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
                                    double* const* alpha_dev, double rtol, int32_t max_iter,
                                    int32_t* iters_out, double* relres_out);
 
-/* Tile autotuner for the matvec of this context's shapes: times every
- * power-of-two K-split (1 .. 8 or more) of the second descriptor contraction
- * (FP64 DGEMM or tcgen05 GEMM) and keeps the fastest.  *choice_out (host, may
- * be NULL) receives it so that a caller can cache it and restore it later with
- * gdml_set_tuning.  Synchronises the context's stream.
- * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA. */
+/* Tile autotuner for the matvec of this context's shapes.  FP64, DF64, TF32 and BF16
+ * contexts: times every power-of-two K-split (1 .. 8 or more) of the second descriptor
+ * contraction (FP64 DGEMM or tcgen05 GEMM) and keeps the fastest.  OZAKI contexts: times the
+ * number of 256-entry K chunks each CTA of the two sliced GEMMs accumulates in registers
+ * (GEMM 1: 1 or all; GEMM 2: 1, 2, 3, 4, 8, ... up to all) and keeps the fastest pair.
+ * *choice_out (host, may be NULL) receives the choice (OZAKI: g1 * 65536 + g2) so that a
+ * caller can cache it and restore it later with gdml_set_tuning.  Synchronises the
+ * context's stream.  Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA. */
 gdml_status gdml_autotune(gdml_ctx* ctx, int32_t* choice_out);
 gdml_status gdml_set_tuning(gdml_ctx* ctx, int32_t splits);
 

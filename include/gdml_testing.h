@@ -24,11 +24,13 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
  * matvec's descriptor contractions, Sec. 2.1, at FP64-class accuracy).  A: M x K,
  * B: N x K, C: M x N, row-major FP64 device arrays, 1 <= M, N, K <= 2^24; every
  * 256-entry chunk of a row of A and B is split into 7 BF16 slices of 7 bits,
- * chunk products are accumulated exactly in FP32 per slice level and the result
- * is returned as FP64.  Synchronises the stream.  Errors: GDML_ERR_ARG,
- * GDML_ERR_OOM, GDML_ERR_CUDA, GDML_ERR_TIMEOUT (a bounded pipeline wait gave up). */
+ * chunk products are accumulated exactly in FP32 per slice level, each CTA adds
+ * chunks_per_cta consecutive chunks in double-float (< 1: the contexts' automatic
+ * choice) and the groups' partials are summed into C as FP64.  Synchronises the stream.
+ * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA, GDML_ERR_TIMEOUT (a bounded pipeline
+ * wait gave up). */
 gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
-                              double* C_dev, void* cuda_stream);
+                              int32_t chunks_per_cta, double* C_dev, void* cuda_stream);
 
 /* The tall product of the OZAKI preconditioner build (Eq. 5's L_k = K_nk L_kk^-T as K_nk
  * times the transposed triangular inverse, and the leverage-score row norms of Sec. 3's
@@ -70,6 +72,32 @@ gdml_status gdml_test_precond_factor(gdml_ctx* ctx, double* L_out_dev);
  * its stream); GDML_ERR_TIMEOUT if a pipeline wait gave up since the last check.
  * FP64 contexts: always GDML_OK. */
 gdml_status gdml_tc_check(gdml_ctx* ctx);
+
+/* Fault injection from the host for the bounded device waits: every mbarrier wait of the
+ * library's tcgen05 / TMA pipelines (the TF32/BF16 and sliced GEMMs, the staged Woodbury
+ * passes and Schur sums) gives up after `polls` polls instead of its default (about 2^26,
+ * seconds).  polls = 0 makes each wait give up at once: the waiting role then issues no copy
+ * and no MMA, records GDML_ERR_TIMEOUT in the kernel's error word (read by gdml_tc_check) and
+ * the CTA still releases its tensor memory, so the context stays usable.  polls = 0xFFFFFFFF
+ * restores the default.  Applies to all contexts and devices' kernels launched after the call
+ * on the current device; not thread-safe with concurrent launches.  Errors: GDML_ERR_CUDA. */
+gdml_status gdml_test_set_wait_limit(uint32_t polls);
+
+/* The FP64 Cholesky of the preconditioner build with the jitter rule of Eq. 5's reading
+ * (if A is not positive definite, eps = 1e-14 tr(A)/k is added to the diagonal and
+ * multiplied by 10 per retry up to 1e-6 tr(A)/k) on a caller matrix: A_dev k x k row-major
+ * FP64 (only its lower triangle is read), L_dev k x k receives the factor in its lower
+ * triangle (the strict upper triangle is unspecified), *eps_out (host) the jitter used.
+ * Synchronises the stream.  Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA,
+ * GDML_ERR_NOT_SPD (still not positive definite at the largest jitter). */
+gdml_status gdml_test_cholesky_jitter(const double* A_dev, int64_t k, double* L_dev, double* eps_out,
+                                      void* cuda_stream);
+
+/* Replaces the context's lambda by any finite value -- zero or negative included, which makes
+ * K + lambda I indefinite, so that a test can drive PCG into its breakdown status
+ * (GDML_ERR_BREAKDOWN: p^T K_lambda p <= 0).  Drops the built preconditioner (rank 0) and the
+ * captured PCG graphs.  Errors: GDML_ERR_ARG (NULL context, non-finite lambda). */
+gdml_status gdml_test_set_lambda(gdml_ctx* ctx, double lambda);
 
 /* Kernel launches this library has executed since it was loaded (all
  * contexts and threads; a kernel inside a CUDA graph counts once per replay).

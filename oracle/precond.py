@@ -41,7 +41,9 @@ def select_uniform(n: int, k: int, seed: int, stream: int = philox.STREAM_UNIFOR
 
 
 def cholesky_jitter(A: np.ndarray) -> tuple[np.ndarray, float]:
-    """Lower Cholesky factor of A, retrying with diagonal jitter (Eq. 5 reading)."""
+    """Lower Cholesky factor of A, retrying with diagonal jitter (Eq. 5 reading): eps =
+    1e-14 tr(A)/k, times 10 per retry, up to 1e-6 tr(A)/k.  A matrix whose trace is not
+    positive gives the rule no scale (it cannot be a nonzero PSD block): it fails at once."""
     k = A.shape[0]
     scale = np.trace(A) / k
     eps = 0.0
@@ -50,6 +52,8 @@ def cholesky_jitter(A: np.ndarray) -> tuple[np.ndarray, float]:
             L = np.linalg.cholesky(A + eps * np.eye(k))
             return L, eps
         except np.linalg.LinAlgError:
+            if not (scale > 0.0 and np.isfinite(scale)):
+                raise
             eps = 1e-14 * scale if eps == 0.0 else eps * 10.0
             if eps > 1e-6 * scale * 1.0000001:
                 raise
@@ -81,26 +85,41 @@ def precond_matrix(L_k: np.ndarray, lam: float) -> np.ndarray:
     return L_k @ L_k.T + lam * np.eye(L_k.shape[0])
 
 
-def pivoted_cholesky(get_col, d: np.ndarray, k: int):
+def pivoted_cholesky(get_col, d: np.ndarray, k: int, forced=None, diag_out: list | None = None):
     """Incomplete Cholesky with greedy diagonal pivoting (App. A.2, Algorithm 1).
 
     get_col(i) returns column i of K; d = diag(K).  Returns (L_k, pivots,
     trace) where trace[m] = sum of the residual diagonal after step m and
     pivots lists the chosen columns in order.  Stops early if the largest
     residual diagonal is not positive (rank reached).
+
+    forced (optional): a sequence of column indices taken as the pivots of steps 0, 1, ...
+    instead of the argmax (to replay another implementation's choices; a forced column must
+    not have been chosen before).  diag_out (optional list): receives, before each step, the
+    residual diagonal d as it stands (a copy), so a replay can compare each forced pivot
+    with that step's maximum.
     """
     d = np.array(d, dtype=np.float64, copy=True)
     n = d.size
     perm = np.arange(n)
+    pos = np.arange(n)  # position of each column in perm
     L = np.zeros((n, k), order="F")  # columns contiguous
     trace = []
     for m in range(k):
+        if diag_out is not None:
+            diag_out.append(d.copy())
         # pivot: largest residual diagonal among the not-yet-chosen positions
         rest = perm[m:]
-        i = m + int(np.argmax(d[rest]))
+        if forced is None:
+            i = m + int(np.argmax(d[rest]))
+        else:
+            i = int(pos[int(forced[m])])
+            if i < m:
+                raise ValueError(f"forced pivot {forced[m]} at step {m} was chosen before")
         if d[perm[i]] <= 0.0:
             return L[:, :m], perm[:m].copy(), np.asarray(trace)
         perm[m], perm[i] = perm[i], perm[m]
+        pos[perm[m]], pos[perm[i]] = m, i
         piv = perm[m]
         lmm = np.sqrt(d[piv])
         L[piv, m] = lmm

@@ -72,7 +72,17 @@ struct gdml_ctx {
   double* diag = nullptr;  // n
   float2* X2 = nullptr;    // M*D: X as float pairs (DF64/OZAKI kernel columns)
   float2* G2 = nullptr;    // M*D*3: G as float pairs
-  double* Xc() const { return V64 + M * D; }
+  // permutational symmetries (sGDML): Ssym atom permutations of a group; the training side of
+  // the kernel then has MB = M Ssym rows, row b Ssym + q = P_q applied to geometry b
+  int Ssym = 1;
+  int64_t MB = 0;
+  int* pis = nullptr;     // Ssym x D: pi_q(p)
+  int* pinv = nullptr;    // Ssym x D: pi_q^-1(p)
+  double* XB = nullptr;   // MB x D: P_q x_b (X itself when Ssym == 1)
+  double* XcA = nullptr;  // M x D: centred descriptors of the rows (the bottom of V64 when Ssym == 1)
+  double* Wa = nullptr;   // M x D: w_a = J_a v_a (Ssym > 1; the top of V64 holds the training side)
+  double* Xc() const { return XcA; }
+  double* XcB() const { return V64 + MB * D; }  // MB x D: the training side's centred descriptors
   TcMatvec tc;  // tensor-core matvec state (TF32/BF16 contexts)
   OzMatvec oz;  // sliced-BF16 tensor-core matvec state (OZAKI contexts)
 
@@ -162,6 +172,19 @@ gdml_status matvec_fp64(gdml_ctx* c, const double* v, double* out, int add_lambd
   const int64_t M = c->M;
   const int D = c->D;
   cudaStream_t st = c->st;
+  if (c->Ssym > 1) {  // the same steps with the training side of MB = M S rows
+    const int64_t MB = c->MB;
+    double* WB = c->V64;  // [W_B ; Xc_B]
+    launch_proj(c->G, c->XcA, v, M, c->N, D, c->Wa, D, c->tb, st);
+    launch_sym_gather(c->Wa, M, D, c->pis, c->Ssym, c->XcB(), WB, c->tb, st);
+    launch_dgemm<double, double>(true, M, MB, D, 1.0, c->XcA, D, WB, D, 0.0, c->T, MB, false, st);
+    launch_beta_rows(c->T, c->S, c->tb, M, MB, c->c, c->P64 + MB, 2 * MB, c->rowsum, st);
+    launch_dgemm<double, double>(false, M, D, 2 * MB, 1.0, c->P64, 2 * MB, c->V64, D, 0.0, c->U, D, false, st,
+                                 c->splitsU, M * D);
+    launch_backproj<double>(c->U, D, c->splitsU, M * D, c->rowsum, c->XcA, c->G, v, M, c->N, D, c->lam, add_lambda,
+                            out, st);
+    return check_launch(c, "matvec_fp64 (symmetries)");
+  }
   double* W = c->V64;
   launch_proj(c->G, c->Xc(), v, M, c->N, D, W, D, c->tb, st);
   // T = Xc W^T
@@ -229,8 +252,19 @@ gdml_status read_status(gdml_ctx* c, int* h) {
   return GDML_OK;
 }
 
+// K[:, cols] (n x ncols, column-major) for the Nystrom factor: in double-float with each
+// geometry's operands reused across the columns (DF64 / OZAKI contexts, whose preconditioner
+// is FP32-stored), else in FP64
 gdml_status get_cols(gdml_ctx* c, const int64_t* cols, int64_t ncols, double* out) {
-  launch_kcol(cols, ncols, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, nullptr, c->st);
+  if (c->Ssym > 1) {
+    if (!launch_kcol_sym(cols, ncols, c->X, c->G, c->S, c->P64, 2 * c->MB, c->M, c->MB, c->N, c->D, c->pis, c->pinv,
+                         c->Ssym, c->c, out, c->n, nullptr, c->st))
+      return ctx_fail(c, GDML_ERR_ARG, "kernel columns with symmetries: descriptor too long for shared memory");
+    return check_launch(c, "kcol (symmetries)");
+  }
+  if (!(c->X2 && launch_kcol_bulk_df(cols, ncols, c->X2, c->G2, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out,
+                                      c->n, c->st)))
+    launch_kcol(cols, ncols, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, nullptr, c->st);
   return check_launch(c, "kcol");
 }
 
@@ -268,6 +302,10 @@ gdml_status chol_jitter(gdml_ctx* c, const double* src, double* work, int64_t k,
     int h = 0;
     TRY(read_status(c, &h));
     if (h == 0) break;
+    // the jitter scale tr/k must be positive (a nonzero PSD block has tr > 0); otherwise
+    // no retry can help, and eps would stay 0 forever
+    if (!(scale > 0.0) || !std::isfinite(scale))
+      return ctx_fail(c, GDML_ERR_NOT_SPD, "Cholesky of the inducing block failed and tr/k is not positive");
     eps = (eps == 0.0) ? 1e-14 * scale : eps * 10.0;
     if (!(eps <= 1e-6 * scale * 1.0000001))
       return ctx_fail(c, GDML_ERR_NOT_SPD, "Cholesky of the inducing block failed even with jitter 1e-6 tr/k");
@@ -580,11 +618,56 @@ gdml_status validate(const gdml_ctx* c) {
 
 }  // namespace
 
-// =================================================================== C ABI
-extern "C" {
+namespace {
 
-gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, int32_t N, double sigma,
-                              double lambda, int32_t precision, void* cuda_stream) {
+// The symmetries must be a group of atom permutations (identity included, closed under
+// composition): only then is K symmetric positive semi-definite.  pis / pinv (S x D) hold the
+// descriptor-entry permutation of each element and its inverse.
+gdml_status check_symmetry_group(const int32_t* perms, int S, int N, std::vector<int>& pis, std::vector<int>& pinv) {
+  if (!perms || S < 1 || S > 256) return fail(GDML_ERR_ARG, "symmetries: need 1 <= S <= 256 permutations");
+  std::vector<std::vector<int>> P(S, std::vector<int>(N));
+  bool has_id = false;
+  for (int q = 0; q < S; ++q) {
+    std::vector<char> seen(N, 0);
+    bool id = true;
+    for (int i = 0; i < N; ++i) {
+      const int v = perms[(int64_t)q * N + i];
+      if (v < 0 || v >= N || seen[v]) return fail(GDML_ERR_ARG, "symmetries: row " + std::to_string(q) + " is not a permutation of the atoms");
+      seen[v] = 1;
+      P[q][i] = v;
+      id = id && v == i;
+    }
+    has_id = has_id || id;
+    for (int r = 0; r < q; ++r)
+      if (P[r] == P[q]) return fail(GDML_ERR_ARG, "symmetries: permutation " + std::to_string(q) + " is listed twice");
+  }
+  if (!has_id) return fail(GDML_ERR_ARG, "symmetries: the identity permutation must be included");
+  std::vector<int> comp(N);
+  for (int q1 = 0; q1 < S; ++q1)
+    for (int q2 = 0; q2 < S; ++q2) {
+      for (int i = 0; i < N; ++i) comp[i] = P[q1][P[q2][i]];
+      bool found = false;
+      for (int r = 0; r < S && !found; ++r) found = P[r] == comp;
+      if (!found) return fail(GDML_ERR_ARG, "symmetries: the permutations are not closed under composition (not a group)");
+    }
+  const int D = N * (N - 1) / 2;
+  pis.assign((size_t)S * D, 0);
+  pinv.assign((size_t)S * D, 0);
+  for (int q = 0; q < S; ++q)
+    for (int i = 1; i < N; ++i)
+      for (int j = 0; j < i; ++j) {
+        const int p = i * (i - 1) / 2 + j;
+        const int a = P[q][i], b = P[q][j];
+        const int hi = std::max(a, b), lo = std::min(a, b);
+        const int pp = hi * (hi - 1) / 2 + lo;
+        pis[(size_t)q * D + p] = pp;
+        pinv[(size_t)q * D + pp] = p;
+      }
+  return GDML_OK;
+}
+
+gdml_status setup_impl(gdml_ctx** out, const double* R_dev, int64_t M, int32_t N, double sigma, double lambda,
+                       int32_t precision, void* cuda_stream, const int32_t* perms, int32_t Ssym) {
   clear_msg();
   if (!out) return fail(GDML_ERR_ARG, "ctx out-pointer is NULL");
   *out = nullptr;
@@ -593,6 +676,12 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   if (!(sigma > 0.0) || !(lambda > 0.0) || !std::isfinite(sigma) || !std::isfinite(lambda))
     return fail(GDML_ERR_ARG, "need sigma > 0 and lambda > 0");
   if (precision < GDML_FP64 || precision > GDML_OZAKI) return fail(GDML_ERR_ARG, "unknown precision");
+  std::vector<int> hpis, hpinv;
+  if (Ssym > 1 || perms) {
+    TRY(check_symmetry_group(perms, Ssym, N, hpis, hpinv));
+    if (Ssym > 1 && precision != GDML_FP64 && precision != GDML_OZAKI)
+      return fail(GDML_ERR_ARG, "symmetries need an FP64 or OZAKI context");
+  }
   std::unique_ptr<gdml_ctx, void (*)(gdml_ctx*)> c(new gdml_ctx(), &gdml_destroy);
   CTRY(c.get(), cudaGetDevice(&c->device));
   c->st = static_cast<cudaStream_t>(cuda_stream);
@@ -606,18 +695,35 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   c->c = std::sqrt(5.0) / sigma;
   c->precision = precision;
   c->inner_rtol = precision == GDML_BF16 ? 1e-3 : 1e-4;
-  const int64_t D = c->D, n = c->n;
+  c->Ssym = Ssym > 1 ? Ssym : 1;
+  const int64_t D = c->D, n = c->n, MB = M * c->Ssym;
+  c->MB = MB;
   gdml_ctx* C = c.get();
+  if (c->Ssym > 1 && ((size_t)N + 6 * (size_t)D) * sizeof(double) > 200 * 1024)
+    return fail(GDML_ERR_ARG, "symmetries: the kernel columns of molecules with more than ~70 atoms are not supported");
   TRY(dalloc(C, &c->R, (size_t)(M * N * 3)));
   TRY(dalloc(C, &c->X, (size_t)(M * D)));
   TRY(dalloc(C, &c->G, (size_t)(M * D * 3)));
-  TRY(dalloc(C, &c->S, (size_t)(M * M)));
-  TRY(dalloc(C, &c->P64, (size_t)(2 * M * M)));
-  TRY(dalloc(C, &c->V64, (size_t)(2 * M * D)));
-  TRY(dalloc(C, &c->T, (size_t)(M * M)));
-  TRY(dalloc(C, &c->tb, (size_t)M));
+  TRY(dalloc(C, &c->S, (size_t)(M * MB)));
+  TRY(dalloc(C, &c->P64, (size_t)(2 * M * MB)));
+  TRY(dalloc(C, &c->V64, (size_t)(2 * MB * D)));
+  TRY(dalloc(C, &c->T, (size_t)(M * MB)));
+  TRY(dalloc(C, &c->tb, (size_t)MB));
   TRY(dalloc(C, &c->rowsum, (size_t)M));
-  c->splitsU = dgemm_splits(M, D, 2 * M);
+  if (c->Ssym > 1) {
+    TRY(dalloc(C, &c->pis, hpis.size()));
+    TRY(dalloc(C, &c->pinv, hpinv.size()));
+    TRY(dalloc(C, &c->XB, (size_t)(MB * D)));
+    TRY(dalloc(C, &c->XcA, (size_t)(M * D)));
+    TRY(dalloc(C, &c->Wa, (size_t)(M * D)));
+    CTRY(C, cudaMemcpyAsync(c->pis, hpis.data(), hpis.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CTRY(C, cudaMemcpyAsync(c->pinv, hpinv.data(), hpinv.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  } else {
+    c->XB = c->X;
+    c->XcA = c->V64 + M * D;
+    c->Wa = c->V64;
+  }
+  c->splitsU = dgemm_splits(M, D, 2 * MB);
   c->splits_cap = std::max(c->splitsU, 8);
   TRY(dalloc(C, &c->U, (size_t)(c->splits_cap * M * D)));
   TRY(dalloc(C, &c->diag, (size_t)n));
@@ -636,9 +742,25 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
   CTRY(C, cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), c->st));
   CTRY(C, cudaMemcpyAsync(c->R, R_dev, M * N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   launch_desc_jac(c->R, M, N, (int)D, c->X, c->G, c->st);
-  launch_center(c->X, M, (int)D, c->Xc(), c->st);
-  launch_dist_tab(c->X, M, (int)D, c->c, c->S, c->P64, 2 * M, c->st);
-  launch_kdiag(c->G, M, N, (int)D, c->c, c->diag, c->st);
+  {  // non-finite coordinates or two atoms at one place give non-finite descriptors
+    int bad = 0;
+    CTRY(C, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+    launch_check_finite(c->X, M * D, c->status, c->st);
+    launch_check_finite(c->G, M * D * 3, c->status, c->st);
+    TRY(check_launch(C, "descriptor check"));
+    TRY(read_status(C, &bad));
+    if (bad) return fail(GDML_ERR_ARG, "geometries must be finite with no two atoms of a geometry at one place");
+  }
+  launch_center(c->X, M, (int)D, c->XcA, c->st);
+  if (c->Ssym > 1) {  // the training side: rows b S + q = P_q x_b, centred on the rows' mean
+    launch_sym_gather(c->X, M, (int)D, c->pis, c->Ssym, nullptr, c->XB, nullptr, c->st);
+    launch_center_like(c->XB, MB, (int)D, c->X, c->XcA, c->XcB(), c->st);
+    launch_dist_tab_cross(c->X, M, c->XB, MB, (int)D, c->c, c->S, c->P64, 2 * MB, c->st);
+    launch_kdiag_sym(c->X, c->G, M, N, (int)D, c->pis, c->pinv, c->Ssym, c->c, c->diag, c->st);
+  } else {
+    launch_dist_tab(c->X, M, (int)D, c->c, c->S, c->P64, 2 * M, c->st);
+    launch_kdiag(c->G, M, N, (int)D, c->c, c->diag, c->st);
+  }
   if (df_precond(c.get())) {
     TRY(dalloc(C, &c->X2, (size_t)(M * D)));
     TRY(dalloc(C, &c->G2, (size_t)(M * D * 3)));
@@ -651,12 +773,34 @@ gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, in
     if (s != GDML_OK) return ctx_fail(C, s, "tensor-core setup: " + last_msg());
   }
   if (precision == GDML_OZAKI) {
-    gdml_status s = oz_setup(c->oz, M, N, (int)D, c->Xc(), c->P64, 2 * M, c->S, c->c, c->st);
+    gdml_status s = oz_setup(c->oz, M, N, (int)D, c->XcA, c->P64, 2 * MB, c->S, c->c, c->st, c->Ssym, c->pis,
+                             c->XcB());
     if (s != GDML_OK) return ctx_fail(C, s, "sliced tensor-core setup: " + last_msg());
   }
   CTRY(C, cudaStreamSynchronize(c->st));
   *out = c.release();
   return GDML_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+gdml_status gdml_kernel_setup(gdml_ctx** out, const double* R_dev, int64_t M, int32_t N, double sigma,
+                              double lambda, int32_t precision, void* cuda_stream) {
+  return setup_impl(out, R_dev, M, N, sigma, lambda, precision, cuda_stream, nullptr, 1);
+}
+
+gdml_status gdml_kernel_setup_sym(gdml_ctx** out, const double* R_dev, int64_t M, int32_t N,
+                                  const int32_t* perms_host, int32_t S, double sigma, double lambda,
+                                  int32_t precision, void* cuda_stream) {
+  if (!perms_host) {
+    clear_msg();
+    if (out) *out = nullptr;
+    return fail(GDML_ERR_ARG, "perms_host is NULL");
+  }
+  return setup_impl(out, R_dev, M, N, sigma, lambda, precision, cuda_stream, perms_host, S);
 }
 
 gdml_status gdml_matvec(gdml_ctx* c, const double* v, double* out, int32_t add_lambda) {
@@ -680,25 +824,31 @@ gdml_status gdml_predict_forces(gdml_ctx* c, const double* R_query, int64_t Q, c
   const int64_t M = c->M;
   const int N = c->N, D = c->D;
   cudaStream_t st = c->st;
+  const int64_t MB = c->MB;  // the training side: M geometries, or M S with symmetries
   Scratch s{c, {}};
   double *Xq = nullptr, *Gq = nullptr, *Xqc = nullptr, *Sq = nullptr, *Tq = nullptr, *Pq = nullptr, *Uq = nullptr,
          *rs = nullptr;
   TRY(s.get(&Xq, (size_t)(Q * D)));
   TRY(s.get(&Gq, (size_t)(Q * D * 3)));
   TRY(s.get(&Xqc, (size_t)(Q * D)));
-  TRY(s.get(&Sq, (size_t)(Q * M)));
-  TRY(s.get(&Tq, (size_t)(Q * M)));
-  TRY(s.get(&Pq, (size_t)(Q * 2 * M)));
+  TRY(s.get(&Sq, (size_t)(Q * MB)));
+  TRY(s.get(&Tq, (size_t)(Q * MB)));
+  TRY(s.get(&Pq, (size_t)(Q * 2 * MB)));
   TRY(s.get(&Uq, (size_t)(Q * D)));
   TRY(s.get(&rs, (size_t)Q));
-  double* W = c->V64;  // [W ; Xc]: W_b = J_b alpha_b over the training set
+  double* W = c->V64;  // [W ; Xc] of the training side: W_b = J_b alpha_b (permuted copies with symmetries)
   launch_desc_jac(R_query, Q, N, D, Xq, Gq, st);
-  launch_center_like(Xq, Q, D, c->X, c->Xc(), Xqc, st);
-  launch_dist_tab_cross(Xq, Q, c->X, M, D, c->c, Sq, Pq, 2 * M, st);
-  launch_proj(c->G, c->Xc(), alpha, M, N, D, W, D, c->tb, st);
-  launch_dgemm<double, double>(true, Q, M, D, 1.0, Xqc, D, W, D, 0.0, Tq, M, false, st);
-  launch_beta_rows(Tq, Sq, c->tb, Q, M, c->c, Pq + M, 2 * M, rs, st);
-  launch_dgemm<double, double>(false, Q, D, 2 * M, 1.0, Pq, 2 * M, c->V64, D, 0.0, Uq, D, false, st);
+  launch_center_like(Xq, Q, D, c->X, c->XcA, Xqc, st);
+  launch_dist_tab_cross(Xq, Q, c->XB, MB, D, c->c, Sq, Pq, 2 * MB, st);
+  if (c->Ssym > 1) {
+    launch_proj(c->G, c->XcA, alpha, M, N, D, c->Wa, D, c->tb, st);
+    launch_sym_gather(c->Wa, M, D, c->pis, c->Ssym, c->XcB(), W, c->tb, st);
+  } else {
+    launch_proj(c->G, c->XcA, alpha, M, N, D, W, D, c->tb, st);
+  }
+  launch_dgemm<double, double>(true, Q, MB, D, 1.0, Xqc, D, W, D, 0.0, Tq, MB, false, st);
+  launch_beta_rows(Tq, Sq, c->tb, Q, MB, c->c, Pq + MB, 2 * MB, rs, st);
+  launch_dgemm<double, double>(false, Q, D, 2 * MB, 1.0, Pq, 2 * MB, c->V64, D, 0.0, Uq, D, false, st);
   launch_backproj<double>(Uq, D, 1, Q * D, rs, Xqc, Gq, nullptr, Q, N, D, 0.0, 0, f, st);
   return check_launch(c, "predict_forces");
 }
@@ -764,6 +914,11 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     a.ticket = ticket;
     a.col = col;
     a.get_col = [c](const int64_t* cols, double* out, const int* stop, cudaStream_t st) {
+      if (c->Ssym > 1) {  // checked to fit at setup
+        (void)launch_kcol_sym(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->MB, c->M, c->MB, c->N, c->D, c->pis, c->pinv,
+                              c->Ssym, c->c, out, c->n, stop, st);
+        return;
+      }
       if (!c->X2 || !launch_kcol_df(cols, 1, c->X2, c->G2, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out,
                                     c->n, stop, st))
         launch_kcol(cols, 1, c->X, c->G, c->S, c->P64, 2 * c->M, c->M, c->N, c->D, c->c, out, c->n, stop, st);
@@ -904,6 +1059,7 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
   TRY(dot(c, c->ys, c->ys, SC_YY));
   TRY(fetch_scalars(c));
   const double ynorm = std::sqrt(c->hsc[SC_YY]);
+  if (!std::isfinite(ynorm)) return ctx_fail(c, GDML_ERR_ARG, "pcg_solve: y is not finite");
   int64_t iters = 0;
   double res = 0.0;
   gdml_status stat = GDML_OK;
@@ -1022,12 +1178,12 @@ gdml_status gdml_test_df_passes(const float* L_dev, int64_t n, int64_t k, const 
 }
 
 gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
-                              double* C_dev, void* stream) {
+                              int32_t chunks_per_cta, double* C_dev, void* stream) {
   clear_msg();
   if (!A_dev || !B_dev || !C_dev || M < 1 || N < 1 || K < 1) return fail(GDML_ERR_ARG, "bad gemm test arguments");
   if (M > ((int64_t)1 << 24) || N > ((int64_t)1 << 24) || K > ((int64_t)1 << 24))
     return fail(GDML_ERR_ARG, "gemm test sizes too large");
-  return oz_gemm_test(A_dev, B_dev, M, N, K, C_dev, static_cast<cudaStream_t>(stream));
+  return oz_gemm_test(A_dev, B_dev, M, N, K, chunks_per_cta, C_dev, static_cast<cudaStream_t>(stream));
 }
 
 gdml_status gdml_test_oz_gemm_tall(const double* A_dev, int64_t n, int64_t K, const double* B_dev, int64_t NB,
@@ -1053,6 +1209,44 @@ gdml_status gdml_test_precond_factor(gdml_ctx* c, double* L_out) {
     CTRY(c, cudaMemcpyAsync(L_out, c->L, count * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   }
   CTRY(c, cudaStreamSynchronize(c->st));
+  return GDML_OK;
+}
+
+gdml_status gdml_test_set_wait_limit(uint32_t polls) {
+  clear_msg();
+  const uint32_t v = polls == 0xFFFFFFFFu ? tc_default_wait_limit() : polls;
+  for (auto fn : {set_wait_limit_oz, set_wait_limit_tc, set_wait_limit_wb, set_wait_limit_pc}) {
+    cudaError_t e = fn(v);
+    if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("set_wait_limit: ") + cudaGetErrorString(e));
+  }
+  return GDML_OK;
+}
+
+gdml_status gdml_test_cholesky_jitter(const double* A_dev, int64_t k, double* L_dev, double* eps_out, void* stream) {
+  clear_msg();
+  if (!A_dev || !L_dev || !eps_out || k < 1 || k > 16384) return fail(GDML_ERR_ARG, "bad cholesky test arguments");
+  gdml_ctx tmp;  // carries the stream, the status word and the error text only
+  tmp.st = static_cast<cudaStream_t>(stream);
+  if (cudaMalloc(&tmp.status, sizeof(int)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(GDML_ERR_OOM, "cholesky test status word");
+  }
+  double eps = 0.0;
+  gdml_status s = chol_jitter(&tmp, A_dev, L_dev, k, &eps);
+  cudaStreamSynchronize(tmp.st);
+  cudaFree(tmp.status);
+  tmp.status = nullptr;
+  *eps_out = eps;
+  return s;
+}
+
+gdml_status gdml_test_set_lambda(gdml_ctx* c, double lambda) {
+  TRY(validate(c));
+  if (!std::isfinite(lambda)) return ctx_fail(c, GDML_ERR_ARG, "set_lambda: lambda must be finite");
+  c->lam = lambda;
+  c->k = 0;  // the preconditioner was built for the old lambda
+  c->ws = WsPlan();
+  drop_graphs(c);
   return GDML_OK;
 }
 
@@ -1095,6 +1289,8 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
     TRY(fetch_scalars(c));
     ynorm[i] = std::sqrt(c->hsc[SC_YY]);
     res[i] = std::sqrt(c->hsc[SC_RR]);
+    if (!std::isfinite(ynorm[i]) || !std::isfinite(res[i]))
+      return fail(GDML_ERR_ARG, "batched solve: y or alpha of system " + std::to_string(i) + " is not finite");
   }
   // one graph for all systems
   cudaGraph_t g = nullptr;
@@ -1225,6 +1421,50 @@ gdml_status gdml_autotune(gdml_ctx* c, int32_t* choice_out) {
   cudaEvent_t e0, e1;
   CTRY(c, cudaEventCreate(&e0));
   CTRY(c, cudaEventCreate(&e1));
+  if (c->precision == GDML_OZAKI) {
+    // the sliced GEMMs' K chunks per CTA (GEMM 1: T = Xc W^T, GEMM 2: U = A W + beta Xc)
+    auto time_mv = [&](float* ms) -> gdml_status {
+      for (int w = 0; w < 2; ++w) TRY(matvec_any(c, v, out, 1, false));
+      CTRY(c, cudaEventRecord(e0, c->st));
+      for (int w = 0; w < 5; ++w) TRY(matvec_any(c, v, out, 1, false));
+      CTRY(c, cudaEventRecord(e1, c->st));
+      CTRY(c, cudaEventSynchronize(e1));
+      cudaEventElapsedTime(ms, e0, e1);
+      return GDML_OK;
+    };
+    const int n1 = (int)c->oz.W1.nchunks, n2 = (int)c->oz.A2.nchunks;
+    std::vector<int> cand2;
+    for (int g = 1; g <= n2; g = g < 4 ? g + 1 : g * 2) cand2.push_back(g);
+    if (cand2.back() != n2) cand2.push_back(n2);
+    int best1 = c->oz.g1, best2 = c->oz.g2;
+    float best_ms = 1e30f;
+    for (int g1 : {1, n1}) {
+      for (int g2 : cand2) {
+        c->oz.g1 = g1;
+        c->oz.g2 = g2;
+        float ms = 0.f;
+        gdml_status ts = time_mv(&ms);
+        if (ts != GDML_OK) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return ts;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best1 = g1;
+          best2 = g2;
+        }
+      }
+      if (n1 == 1) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->oz.g1 = best1;
+    c->oz.g2 = best2;
+    drop_graphs(c);
+    if (choice_out) *choice_out = best1 * 65536 + best2;
+    return GDML_OK;
+  }
   int best = 1;
   float best_ms = 1e30f;
   const bool tcm = c->precision == GDML_TF32 || c->precision == GDML_BF16;
@@ -1255,6 +1495,15 @@ gdml_status gdml_autotune(gdml_ctx* c, int32_t* choice_out) {
 
 gdml_status gdml_set_tuning(gdml_ctx* c, int32_t splits) {
   TRY(validate(c));
+  if (c->precision == GDML_OZAKI) {  // g1 * 65536 + g2: K chunks per CTA of the two sliced GEMMs
+    const int g1 = splits >> 16, g2 = splits & 0xFFFF;
+    if (g1 < 1 || g1 > c->oz.W1.nchunks || g2 < 1 || g2 > c->oz.A2.nchunks)
+      return ctx_fail(c, GDML_ERR_ARG, "chunks per CTA out of range");
+    c->oz.g1 = g1;
+    c->oz.g2 = g2;
+    drop_graphs(c);
+    return GDML_OK;
+  }
   const bool tcm = c->precision == GDML_TF32 || c->precision == GDML_BF16;
   const int cap = tcm ? c->tc.splits_cap : c->splits_cap;
   if (splits < 1 || splits > cap) return ctx_fail(c, GDML_ERR_ARG, "split count out of range");

@@ -539,6 +539,108 @@ __global__ void __launch_bounds__(256) kcol_df_kernel(const int64_t* __restrict_
   }
 }
 
+// Many kernel columns at once (the Nystrom factor's K_nk, Eq. 5): the same double-float
+// arithmetic as kcol_df_kernel, with geometry a's x_a and g_a staged ONCE per CTA and reused by
+// a block of CB columns (W warps, one column at a time each), instead of once per (a, column).
+// grid (M, ceil(ncols / CB)).  Shared memory: 4 D float pairs for geometry a, plus per warp
+// N (w) + 2 D (x_a - x_b, u) float pairs.
+constexpr int kColBlock = 64;
+__global__ void __launch_bounds__(256) kcol_bulk_df_kernel(const int64_t* __restrict__ cols, int64_t ncols,
+                                                           const float2* __restrict__ X2,
+                                                           const float2* __restrict__ G2,
+                                                           const double* __restrict__ S,
+                                                           const double* __restrict__ A, int64_t ldA, int64_t M,
+                                                           int N, int D, double c2, double* __restrict__ out,
+                                                           int64_t ldo) {
+  extern __shared__ float2 shb[];
+  const int W = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* sxa = shb;                                   // D: x_a
+  float2* sga = sxa + D;                               // 3 D: g_a
+  float2* wsp = sga + 3 * D + (size_t)warp * (N + 2 * D);  // N: +-g_b on the pairs (i, j), by partner j
+  float2* dab = wsp + N;                               // D: x_a - x_b
+  float2* u = dab + D;                                 // D
+  const int64_t a = blockIdx.x;
+  const int B = 3 * N;
+  {
+    const float2* Xa = X2 + a * D;
+    const float2* Ga = G2 + a * D * 3;
+    for (int e = threadIdx.x; e < 4 * D; e += blockDim.x) {
+      if (e < D)
+        sxa[e] = Xa[e];
+      else
+        sga[e - D] = Ga[e - D];
+    }
+  }
+  __syncthreads();
+  const int64_t c_end = min(ncols, (int64_t)(blockIdx.y + 1) * kColBlock);
+  for (int64_t c = (int64_t)blockIdx.y * kColBlock + warp; c < c_end; c += W) {
+    const int64_t col = cols[c];
+    const int64_t b = col / B;
+    const int l = (int)(col - b * B), i = l / 3, q = l - 3 * i;
+    const float2* Xb = X2 + b * D;
+    const float2* Gb = G2 + b * D * 3;
+    for (int j = lane; j < N; j += 32) {
+      float2 w = make_float2(0.f, 0.f);
+      if (j != i) {
+        const float2 g = Gb[3 * pair_idx(i, j) + q];
+        w = (i > j) ? dfk_neg(g) : g;
+      }
+      wsp[j] = w;
+    }
+    for (int p = lane; p < D; p += 32) dab[p] = dfk_add(sxa[p], dfk_neg(Xb[p]));  // x_a - x_b
+    __syncwarp();
+    const float2 sab = dfk_mul(dfk_split(c2), dfk_split(S[b * M + a]));
+    const float2 aab = dfk_split(A[b * ldA + a]);
+    float2 sd = make_float2(0.f, 0.f);
+    for (int j = lane; j < N; j += 32)
+      if (j != i) sd = dfk_add(sd, dfk_mul(dab[pair_idx(i, j)], wsp[j]));
+    for (int o = 16; o > 0; o >>= 1)
+      sd = dfk_add(sd, make_float2(__shfl_xor_sync(0xffffffffu, sd.x, o), __shfl_xor_sync(0xffffffffu, sd.y, o)));
+    const float2 coef = dfk_neg(dfk_mul(sab, sd));
+    for (int p = lane; p < D; p += 32) u[p] = dfk_mul(coef, dab[p]);
+    __syncwarp();
+    for (int j = lane; j < N; j += 32)
+      if (j != i) {
+        const int p = pair_idx(i, j);
+        u[p] = dfk_add(u[p], dfk_mul(aab, wsp[j]));
+      }
+    __syncwarp();
+    for (int l2 = lane; l2 < B; l2 += 32) {
+      const int i2 = l2 / 3, q2 = l2 - 3 * i2;
+      float2 s2 = make_float2(0.f, 0.f);
+      for (int j = 0; j < N; ++j) {
+        if (j == i2) continue;
+        const int p = pair_idx(i2, j);
+        const float2 gj = dfk_mul(sga[3 * p + q2], u[p]);
+        s2 = dfk_add(s2, (i2 > j) ? dfk_neg(gj) : gj);
+      }
+      out[c * ldo + a * B + l2] = (double)s2.x + (double)s2.y;
+    }
+    __syncwarp();  // wsp, dab and u are rewritten for the warp's next column
+  }
+}
+
+bool launch_kcol_bulk_df(const int64_t* cols, int64_t ncols, const float2* X2, const float2* G2, const double* S,
+                         const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
+                         cudaStream_t st) {
+  const size_t fixed = 4 * (size_t)D * sizeof(float2), per_warp = ((size_t)N + 2 * (size_t)D) * sizeof(float2);
+  const size_t budget = 200 * 1024;
+  if (fixed + per_warp > budget || ncols < 1 || M > 2147483647 || cdiv(ncols, kColBlock) > 65535) return false;
+  const int W = (int)std::min<size_t>(8, (budget - fixed) / per_warp);
+  const size_t smem = fixed + W * per_warp;
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    if (cudaFuncSetAttribute(kcol_bulk_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return false;
+    attr = smem;
+  }
+  dim3 g((unsigned)M, (unsigned)cdiv(ncols, kColBlock));
+  { kcol_bulk_df_kernel<<<g, 32 * W, smem, st>>>(cols, ncols, X2, G2, S, A, ldA, M, N, D, c * c, out, ldo); count_launch(); }
+  return true;
+}
+
 bool launch_kcol_df(const int64_t* cols, int64_t ncols, const float2* X2, const float2* G2, const double* S,
                     const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
                     const int* stop_flag, cudaStream_t st) {
@@ -642,6 +744,223 @@ void launch_kcol(const int64_t* cols, int64_t ncols, const double* X, const doub
   size_t smem = (2 * (size_t)D + N) * sizeof(double);
   if (smem > 48 * 1024) cudaFuncSetAttribute(kcol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   { kcol_kernel<<<grid, 128, smem, st>>>(cols, ncols, per, X, G, S, A, ldA, M, N, D, c * c, out, ldo, stop_flag); count_launch(); }
+}
+
+// *flag = 1 if any of the count values is not finite (NaN or infinite)
+__global__ void check_finite_kernel(const double* __restrict__ a, int64_t count, int* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(a[i])) {
+      *flag = 1;
+      return;
+    }
+}
+
+void launch_check_finite(const double* a, int64_t count, int* flag, cudaStream_t st) {
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(count, 256), 4 * num_sms()));
+  { check_finite_kernel<<<grid, 256, 0, st>>>(a, count, flag); count_launch(); }
+}
+
+// ---------------------------------------------------------------- permutational symmetries
+// A symmetry group of S atom permutations acts on the descriptor by pis (S x D: pi_q(p) = the
+// pair index of (sigma_q(i), sigma_q(j)) for p = (i, j)) and pinv (its inverse per q).  The
+// symmetric force kernel is K_ab = sum_q J_a^T H(x_a, P_q x_b) P_q J_b with (P_q x)_p = x_pi_q(p);
+// its training side holds row b S + q = P_q applied to geometry b.
+
+// out[b S + q][p] = in[b][pi_q(p)] for the M rows of `in`; with xcB, also
+// t[b S + q] = xcB[b S + q] . out[b S + q].  One CTA (256 threads) per output row.
+__global__ void __launch_bounds__(256) sym_gather_kernel(const double* __restrict__ in, int D,
+                                                         const int* __restrict__ pis, int S,
+                                                         const double* __restrict__ xcB, double* __restrict__ out,
+                                                         double* __restrict__ t) {
+  __shared__ double red[8];
+  const int64_t row = blockIdx.x;
+  const int64_t b = row / S;
+  const int q = (int)(row - b * S);
+  const int* pi = pis + (int64_t)q * D;
+  double part = 0.0;
+  for (int p = threadIdx.x; p < D; p += blockDim.x) {
+    const double v = in[b * D + pi[p]];
+    out[row * D + p] = v;
+    if (xcB) part = fma(xcB[row * D + p], v, part);
+  }
+  if (xcB) {
+    part = block_sum<256>(part, red);
+    if (threadIdx.x == 0) t[row] = part;
+  }
+}
+
+void launch_sym_gather(const double* in, int64_t M, int D, const int* pis, int S, const double* xcB, double* out,
+                       double* t, cudaStream_t st) {
+  { sym_gather_kernel<<<(unsigned)(M * S), 256, 0, st>>>(in, D, pis, S, xcB, out, t); count_launch(); }
+}
+
+// the value of u = J_a e_l on descriptor entry pp (zero unless pp pairs atom i with another):
+// u_(i,j) = -g_(i,j),c for i > j and +g_(i,j),c for i < j
+__device__ __forceinline__ double jac_col_at(const double* __restrict__ g, int pp, int i, int cc) {
+  int I, J;
+  pair_of(pp, I, J);  // I > J
+  if (I == i) return -g[3 * pp + cc];
+  if (J == i) return g[3 * pp + cc];
+  return 0.0;
+}
+
+// diag(K) with symmetries: for column l = 3 i + cc of geometry a, with u = J_a e_l,
+//   diag_{a,l} = sum_q u^T H(x_a, P_q x_a) P_q u = sum_q A_q (u . P_q u) - c^2 S_q (u . d_q)(P_q u . d_q),
+// d_q = x_a - P_q x_a, (P_q u)_p = u_pi(p), so (P_q u) . d = sum_p' u_p' d_pinv(p').
+// One CTA (256 threads) per geometry: d_q and its norm by a CTA reduction, then thread l sums
+// over the N - 1 pairs of atom i.
+__global__ void __launch_bounds__(256) kdiag_sym_kernel(const double* __restrict__ X, const double* __restrict__ G,
+                                                        int N, int D, const int* __restrict__ pis,
+                                                        const int* __restrict__ pinv, int S, double c,
+                                                        double* __restrict__ diag) {
+  extern __shared__ double sdq[];  // D
+  __shared__ double red[8];
+  __shared__ double s_r;
+  const int64_t a = blockIdx.x;
+  const double* Xa = X + a * D;
+  const double* Ga = G + a * D * 3;
+  const int B = 3 * N;
+  double acc[2] = {0.0, 0.0};  // B <= 384: l = threadIdx.x, threadIdx.x + 256
+  for (int q = 0; q < S; ++q) {
+    const int* pi = pis + (int64_t)q * D;
+    const int* pv = pinv + (int64_t)q * D;
+    double part = 0.0;
+    for (int p = threadIdx.x; p < D; p += blockDim.x) {
+      const double d = Xa[p] - Xa[pi[p]];
+      sdq[p] = d;
+      part = fma(d, d, part);
+    }
+    part = block_sum<256>(part, red);  // synchronises: sdq is complete
+    if (threadIdx.x == 0) s_r = sqrt(part);
+    __syncthreads();
+    const double r = s_r;
+    const double Sv = (c * c / 3.0) * exp(-c * r), Av = Sv * (1.0 + c * r);
+    for (int k = 0; k < 2; ++k) {
+      const int l = threadIdx.x + 256 * k;
+      if (l >= B) break;
+      const int i = l / 3, cc = l - 3 * i;
+      double ud = 0.0, vd = 0.0, uv = 0.0;
+      for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const int pp = pair_idx(i, j);
+        const double u = (i > j) ? -Ga[3 * pp + cc] : Ga[3 * pp + cc];
+        ud = fma(u, sdq[pp], ud);
+        vd = fma(u, sdq[pv[pp]], vd);
+        uv = fma(u, jac_col_at(Ga, pi[pp], i, cc), uv);
+      }
+      acc[k] += Av * uv - c * c * Sv * ud * vd;
+    }
+    __syncthreads();  // sdq is rewritten for the next symmetry
+  }
+  for (int k = 0; k < 2; ++k) {
+    const int l = threadIdx.x + 256 * k;
+    if (l < B) diag[a * B + l] = acc[k];
+  }
+}
+
+void launch_kdiag_sym(const double* X, const double* G, int64_t M, int N, int D, const int* pis, const int* pinv,
+                      int S, double c, double* diag, cudaStream_t st) {
+  const size_t smem = (size_t)D * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kdiag_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  { kdiag_sym_kernel<<<(unsigned)M, 256, smem, st>>>(X, G, N, D, pis, pinv, S, c, diag); count_launch(); }
+}
+
+// Kernel columns with symmetries: column (b, l = 3 i + cc), u = J_b e_l, for every geometry a
+//   K[a, col] = J_a^T sum_q [A_q w_q - c^2 S_q (d_q . w_q) d_q],
+// w_q = P_q u ((w_q)_pinv(p') = u_p'), d_q = x_a - P_q x_b, S_q and A_q from the context's
+// tables at (a, b S + q).  One warp per (geometry a, column), W warps per CTA; FP64.
+__global__ void __launch_bounds__(256) kcol_sym_kernel(const int64_t* __restrict__ cols,
+                                                       const double* __restrict__ X, const double* __restrict__ G,
+                                                       const double* __restrict__ Stab,
+                                                       const double* __restrict__ Atab, int64_t ldA, int64_t M,
+                                                       int64_t MB, int N, int D, const int* __restrict__ pis,
+                                                       const int* __restrict__ pinv, int S, double c2,
+                                                       double* __restrict__ out, int64_t ldo,
+                                                       const int* __restrict__ stop_flag) {
+  if (stop_flag && *stop_flag) return;
+  extern __shared__ double shs[];
+  const int W = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* ub = shs + (size_t)warp * (N + 6 * (size_t)D);  // N: u on the pairs (i, j), by partner j
+  double* xa = ub + N;                                    // D
+  double* ga = xa + D;                                    // 3 D
+  double* dq = ga + 3 * D;                                // D
+  double* uacc = dq + D;                                  // D
+  const int64_t c = blockIdx.y;
+  const int64_t col = cols[c];
+  const int B = 3 * N;
+  const int64_t b = col / B;
+  const int l = (int)(col - b * B), i = l / 3, cc = l - 3 * i;
+  const int64_t a = (int64_t)blockIdx.x * W + warp;
+  if (a >= M) return;  // warp-level work only below
+  const double* Xa = X + a * D;
+  const double* Ga = G + a * D * 3;
+  const double* Xb = X + b * D;
+  const double* Gb = G + b * D * 3;
+  for (int j = lane; j < N; j += 32) {
+    double u = 0.0;
+    if (j != i) {
+      const int pp = pair_idx(i, j);
+      u = (i > j) ? -Gb[3 * pp + cc] : Gb[3 * pp + cc];
+    }
+    ub[j] = u;
+  }
+  for (int p = lane; p < D; p += 32) {
+    xa[p] = Xa[p];
+    uacc[p] = 0.0;
+  }
+  for (int e = lane; e < 3 * D; e += 32) ga[e] = Ga[e];
+  __syncwarp();
+  for (int q = 0; q < S; ++q) {
+    const int* pi = pis + (int64_t)q * D;
+    const int* pv = pinv + (int64_t)q * D;
+    for (int p = lane; p < D; p += 32) dq[p] = xa[p] - Xb[pi[p]];
+    __syncwarp();
+    double sd = 0.0;
+    for (int j = lane; j < N; j += 32)
+      if (j != i) sd = fma(ub[j], dq[pv[pair_idx(i, j)]], sd);
+    for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    const double Sq = Stab[a * MB + b * S + q], Aq = Atab[a * ldA + b * S + q];
+    const double coef = -c2 * Sq * sd;
+    for (int p = lane; p < D; p += 32) uacc[p] = fma(coef, dq[p], uacc[p]);
+    __syncwarp();
+    for (int j = lane; j < N; j += 32)
+      if (j != i) {
+        const int p = pv[pair_idx(i, j)];
+        uacc[p] = fma(Aq, ub[j], uacc[p]);
+      }
+    __syncwarp();
+  }
+  for (int l2 = lane; l2 < B; l2 += 32) {
+    const int i2 = l2 / 3, q2 = l2 - 3 * i2;
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (j == i2) continue;
+      const int p = pair_idx(i2, j);
+      const double gj = ga[3 * p + q2] * uacc[p];
+      s += (i2 > j) ? -gj : gj;
+    }
+    out[c * ldo + a * B + l2] = s;
+  }
+}
+
+bool launch_kcol_sym(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* Stab,
+                     const double* Atab, int64_t ldA, int64_t M, int64_t MB, int N, int D, const int* pis,
+                     const int* pinv, int S, double c, double* out, int64_t ldo, const int* stop_flag,
+                     cudaStream_t st) {
+  const size_t per_warp = ((size_t)N + 6 * (size_t)D) * sizeof(double);
+  const int W = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
+  if (W < 1 || ncols < 1 || ncols > 65535) return false;
+  const size_t smem = W * per_warp;
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    if (cudaFuncSetAttribute(kcol_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return false;
+    attr = smem;
+  }
+  dim3 g((unsigned)cdiv(M, W), (unsigned)ncols);
+  { kcol_sym_kernel<<<g, 32 * W, smem, st>>>(cols, X, G, Stab, Atab, ldA, M, MB, N, D, pis, pinv, S, c * c, out, ldo, stop_flag); count_launch(); }
+  return true;
 }
 
 }  // namespace gdml

@@ -25,6 +25,20 @@ void launch_dist_tab(const double* X, int64_t M, int D, double c, double* S, dou
 bool launch_kcol_df(const int64_t* cols, int64_t ncols, const float2* X2, const float2* G2, const double* S,
                     const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
                     const int* stop_flag, cudaStream_t st);
+// many kernel columns at once in double-float (the Nystrom factor's K_nk); false (nothing
+// launched) when geometry a's operands and the per-warp scratch do not fit in 200 KB
+bool launch_kcol_bulk_df(const int64_t* cols, int64_t ncols, const float2* X2, const float2* G2, const double* S,
+                         const double* A, int64_t ldA, int64_t M, int N, int D, double c, double* out, int64_t ldo,
+                         cudaStream_t st);
+// permutational symmetries (pis, pinv: S x D descriptor-entry permutations of the group)
+void launch_sym_gather(const double* in, int64_t M, int D, const int* pis, int S, const double* xcB, double* out,
+                       double* t, cudaStream_t st);
+void launch_kdiag_sym(const double* X, const double* G, int64_t M, int N, int D, const int* pis, const int* pinv,
+                      int S, double c, double* diag, cudaStream_t st);
+bool launch_kcol_sym(const int64_t* cols, int64_t ncols, const double* X, const double* G, const double* Stab,
+                     const double* Atab, int64_t ldA, int64_t M, int64_t MB, int N, int D, const int* pis,
+                     const int* pinv, int S, double c, double* out, int64_t ldo, const int* stop_flag,
+                     cudaStream_t st);
 // each double of x as the float pair (hi, lo)
 void launch_split_df(const double* x, int64_t count, float2* out, cudaStream_t st);
 void launch_kdiag(const double* G, int64_t M, int N, int D, double c, double* diag, cudaStream_t st);
@@ -101,6 +115,14 @@ void launch_dfsyrk(int64_t k, int64_t n, const float* A, int64_t lda, double* C,
 void transpose_square(const double* A, int64_t k, double* At, cudaStream_t st);
 void set_identity(double* A, int64_t k, cudaStream_t st);
 int64_t woodbury_part_size(int64_t n, int64_t k);
+
+// the bounded-wait limit of each translation unit with tcgen05 / TMA pipelines (test hook)
+cudaError_t set_wait_limit_oz(uint32_t polls);
+cudaError_t set_wait_limit_tc(uint32_t polls);
+cudaError_t set_wait_limit_wb(uint32_t polls);
+cudaError_t set_wait_limit_pc(uint32_t polls);
+uint32_t tc_default_wait_limit();
+void launch_check_finite(const double* a, int64_t count, int* flag, cudaStream_t st);
 
 // cg.cu
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,

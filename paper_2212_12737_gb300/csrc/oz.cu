@@ -308,7 +308,8 @@ __global__ void oz_s2_kernel(const double* __restrict__ S, int64_t count, double
 // critical path (try_wait already suspends in hardware for a short while).
 __device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
   const uint32_t addr = tc::smem_u32(bar);
-  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
+  const uint32_t limit = tc::g_wait_limit;
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -334,19 +335,23 @@ __device__ __forceinline__ bool handoff(bool failed) {
   return any != 0;
 }
 
-// grid (ceil(N/64), ceil(M/128), K-chunks).  CTA z accumulates the 2 k-blocks (of
-// 128 K entries, two 128-byte swizzle spans per tile) of chunk z.  Warp 0 loads the 7
-// A slices of each k-block one by one into a 3-deep ring, warp 2 loads the 7 B slices
-// of each k-block as one group and waits on the TMA barriers; warp 1 multiplies A slice
-// i with B slices j = 0..6-i (8 MMAs per pair) into TMEM accumulator i + j, taking each
-// A tile from warp 2 at a named barrier (a wait or any shared-memory read in the
-// MMA-issuing thread stalls the tensor pipe; wide k-blocks halve the handoffs per MMA).
-// Warps 3..10 (two per TMEM lane quarter, 32 columns each) combine the 7 levels, scale
-// by 2^(eA + eB) and store the chunk's double-float partial.
+// grid (ceil(N/64), ceil(M/128), ceil(chunks / G)).  CTA z accumulates the G K-chunks
+// z G .. z G + G - 1, each 2 k-blocks of 128 K entries (two 128-byte swizzle spans per tile).
+// Warp 0 loads the 7 A slices of each k-block one by one into a 3-deep ring, warp 2 loads
+// the 7 B slices of each k-block as one group and waits on the TMA barriers; warp 1
+// multiplies A slice i with B slices j = 0..6-i (8 MMAs per pair) into TMEM accumulator
+// i + j, taking each A tile from warp 2 at a named barrier (a wait or any shared-memory
+// read in the MMA-issuing thread stalls the tensor pipe; wide k-blocks halve the handoffs
+// per MMA).  After each chunk warps 3..10 (two per TMEM lane quarter, 32 columns each)
+// drain the 7 level accumulators, scale the chunk by 2^(eA + eB), add it to running
+// double-float sums held in registers and release the TMEM (tfree) for the next chunk,
+// whose first MMA per level overwrites; after the last chunk they store the group's
+// double-float partial once.
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
-                   int Bp, int M, int N, int num_kb, const int* __restrict__ eA, const int* __restrict__ eB,
-                   float2* __restrict__ out, int64_t ldo, int64_t split_stride, int* __restrict__ err) {
+                   int Bp, int M, int N, int num_kb, int chunks_per_cta, const int* __restrict__ eA,
+                   const int* __restrict__ eB, float2* __restrict__ out, int64_t ldo, int64_t split_stride,
+                   int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sB = smem;
@@ -355,16 +360,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* bempty = bfull + 1;
   uint64_t* afull = bempty + 1;
   uint64_t* aempty = afull + kAStages2;
-  uint64_t* done = aempty + kAStages2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* cdone = aempty + kAStages2;  // the MMAs of a chunk have completed
+  uint64_t* tfree = cdone + 1;           // the epilogue has read a chunk's accumulators
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfree + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float2* stage = reinterpret_cast<float2*>(smem);  // output tile, reuses the operand buffers after the MMAs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * oz::BN, m0 = blockIdx.y * oz::BM;
-  const int kb_begin = blockIdx.z * kKbPerChunk2;
-  const int kb_end = min(num_kb, kb_begin + kKbPerChunk2);
+  const int q_begin = blockIdx.z * chunks_per_cta;
+  const int kb_begin = q_begin * kKbPerChunk2;
+  const int kb_end = min(num_kb, kb_begin + chunks_per_cta * kKbPerChunk2);
   const int nk = kb_end - kb_begin;
+  const int nq = (nk + kKbPerChunk2 - 1) / kKbPerChunk2;  // chunks of this CTA
 
   if (threadIdx.x == 0) {
     tc::mbar_init(bfull, 1);
@@ -373,7 +381,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&afull[s], 1);
       tc::mbar_init(&aempty[s], 1);
     }
-    tc::mbar_init(done, 1);
+    tc::mbar_init(cdone, 1);
+    tc::mbar_init(tfree, 8);  // one arrival per epilogue warp
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -386,6 +395,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  // MMA thread: issued at least one MMA / learned of a failed wait.  A thread that failed
+  // before issuing anything commits nothing, so no asynchronous arrive outlives the CTA.
+  bool mma_any = false, mma_failed = false;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer, A slices
@@ -415,9 +427,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 2) {
     // ---------------- B producer (lane 0) and waiter (whole warp): the MMA warp never touches
     // shared memory in its loop (any shared-memory access of the MMA-issuing thread stalls
-    // the tensor pipe, ~35 cycles per MMA here); this warp waits on the TMA mbarriers and
-    // hands each A tile over through named barrier 2, whose OR-reduction also carries a
-    // failed wait.  It arrives exactly nk * 7 times whatever happens.
+    // the tensor pipe, ~35 cycles per MMA here); this warp waits on the TMA mbarriers (and,
+    // before the first A tile of each chunk after the first, on the epilogue's release of the
+    // accumulators) and hands each A tile over through named barrier 2, whose OR-reduction
+    // also carries a failed wait.  It arrives exactly nk * 7 times whatever happens.
     bool failed = false;
     for (int kb = 0; kb < nk; ++kb) {
       int okw = 1;
@@ -435,7 +448,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::tma_load_2d(sB + j * kBTile2, &mapB, bfull, kx, j * Bp + n0);
             tc::tma_load_2d(sB + j * kBTile2 + kBTile, &mapB, bfull, kx + oz::KB, j * Bp + n0);
           }
-          if (!mbar_wait_spin(bfull, (uint32_t)kb & 1u)) {
+          const int q = kb / kKbPerChunk2;
+          if (q > 0 && kb % kKbPerChunk2 == 0 && !mbar_wait_spin(tfree, (uint32_t)(q - 1) & 1u)) {
+            atomicExch(err, tc::ERR_TIMEOUT_DONE);
+            *abort_flag = 1;
+            okw = 0;
+          }
+          if (okw && !mbar_wait_spin(bfull, (uint32_t)kb & 1u)) {
             atomicExch(err, tc::ERR_TIMEOUT_FULL);
             *abort_flag = 1;
             okw = 0;
@@ -466,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
     const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
-    bool failed = false;
+    bool& failed = mma_failed;
     for (int kb = 0; kb < nk; ++kb) {
       for (int i = 0; i < oz::S; ++i) {
         failed = handoff(false) || failed;
@@ -479,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // step of 32 bytes adds 2, the second 128-byte span of a tile adds span / 16, and
             // B slice j adds j * kBTile2 / 16
             const uint64_t ad = adesc0 + (uint64_t)(s * (kATile2 >> 4));
-            const uint32_t first = (kb > 0 || i > 0) ? 1u : 0u;
+            const uint32_t first = (kb % kKbPerChunk2 != 0 || i > 0) ? 1u : 0u;  // new chunk: overwrite
 #pragma unroll
             for (int j = 0; j < oz::S; ++j) {
               if (i + j < oz::S) {
@@ -496,46 +515,56 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::mma_issue<true>(d, ad + a1 + 6, bj + b1 + 6, idesc, 1u);
               }
             }
+            mma_any = true;
           }
-          tc::mma_commit(&aempty[s]);  // also after a failure: the A producer never starves
+          // also after a failure (the A producer never starves), unless the failure came
+          // before any MMA: then no asynchronous arrive may outlive the CTA
+          if (mma_any || !failed) tc::mma_commit(&aempty[s]);
         }
         __syncwarp();
       }
-      if (lane == 0) tc::mma_commit(bempty);
+      if (lane == 0 && (mma_any || !failed)) {
+        tc::mma_commit(bempty);
+        if (kb % kKbPerChunk2 == kKbPerChunk2 - 1 || kb == nk - 1) tc::mma_commit(cdone);
+      }
       __syncwarp();
     }
-    if (lane == 0) tc::mma_commit(done);
-    __syncwarp();
   } else if (warp >= 3) {
-    // ---------------- epilogue: combine the levels, scale, store the chunk partial
+    // ---------------- epilogue: per chunk, combine the levels, scale, add to running sums
     const int quarter = warp & 3;
     const int cbase = ((warp - 3) >> 2) * 32;  // this warp's 32 of the tile's 64 columns
     const int row = m0 + quarter * 32 + lane;
-    int go = 0;
-    if (lane == 0) {
-      const bool ok = tc::mbar_wait(done, 0);
-      if (!ok) {
-        atomicExch(err, tc::ERR_TIMEOUT_DONE);
-        *abort_flag = 1;
+    float rh[32], rl[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) rh[t] = rl[t] = 0.f;
+    bool go = true;
+    for (int q = 0; q < nq && go; ++q) {
+      int okw = 1;
+      if (lane == 0) {
+        okw = tc::mbar_wait(cdone, (uint32_t)q & 1u) ? 1 : 0;
+        if (!okw) {
+          atomicExch(err, tc::ERR_TIMEOUT_DONE);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) okw = 0;
       }
-      go = ok && !*abort_flag;
-    }
-    go = __shfl_sync(0xffffffffu, go, 0);
-    tc::fence_after_sync();
-    if (go) {
-      const int64_t z = blockIdx.z;
-      const int ea = row < M ? eA[z * M + row] : 0;
-#pragma unroll 1
-      for (int c0 = cbase; c0 < cbase + 32; c0 += 16) {
-        // all 7 levels of these 16 columns in flight at once, one wait
-        uint32_t v[oz::S][16];
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
+        go = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const int64_t zq = q_begin + q;  // chunk index along K
+      const int ea = row < M ? eA[zq * M + row] : 0;
+#pragma unroll
+      for (int c8 = 0; c8 < 32; c8 += 8) {
+        uint32_t v[oz::S][8];
 #pragma unroll
         for (int L = 0; L < oz::S; ++L)
-          tmem_ld16_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * oz::BN + c0), v[L]);
+          tmem_ld8_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * oz::BN + cbase + c8), v[L]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        float h[16], l[16];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
+        for (int t = 0; t < 8; ++t) {
           // levels 4..6 are scaled by 2^-42..2^-56 against the leading level's 2^-14, so a
           // plain FP32 sum of them errs by < 2^-48 of the leading level's range; levels
           // 3..0 are added in double-float
@@ -548,20 +577,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[2][t]), pow2f(-oz::BITS * 4)));
           df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[1][t]), pow2f(-oz::BITS * 3)));
           df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[0][t]), pow2f(-oz::BITS * 2)));
-          h[t] = nk > 0 ? hh : 0.f;
-          l[t] = nk > 0 ? ll : 0.f;
-        }
-        // stage the scaled tile in the (now idle) operand buffers
-        float2* srow = stage + (quarter * 32 + lane) * kStageLd;
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int col = n0 + c0 + t;
-          const int ex = ea + (col < N ? eB[z * N + col] : 0);
-          srow[c0 + t] = make_float2(scale2(h[t], ex), scale2(l[t], ex));
+          const int col = n0 + cbase + c8 + t;
+          const int ex = ea + (col < N ? eB[zq * N + col] : 0);
+          df_add(rh[c8 + t], rl[c8 + t], scale2(hh, ex), scale2(ll, ex));
         }
       }
+      // this warp has read chunk q: release the accumulators
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
     }
-    // coalesced write-out: the 8 epilogue warps sync among themselves (barrier 1)
+    // stage the group's tile in the (now idle) operand buffers, then a coalesced write-out;
+    // the 8 epilogue warps sync among themselves (barrier 1)
+    if (go) {
+      float2* srow = stage + (quarter * 32 + lane) * kStageLd;
+#pragma unroll
+      for (int t = 0; t < 32; ++t) srow[cbase + t] = make_float2(rh[t], rl[t]);
+    }
     asm volatile("bar.sync 1, 256;" ::: "memory");
     if (go) {
       const int et = threadIdx.x - 96;
@@ -575,7 +607,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 1) {
-    if (lane == 0) (void)tc::mbar_wait(done, 0);
+    // the epilogue has waited on every chunk's completion (or a wait gave up)
+    if (lane == 0 && (mma_any || !mma_failed) && nq > 0) (void)tc::mbar_wait_bounded(cdone, (uint32_t)(nq - 1) & 1u);
     __syncwarp();
     tc::fence_after_sync();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
@@ -652,6 +685,9 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  // MMA thread: issued at least one MMA / learned of a failed wait.  A thread that failed
+  // before issuing anything commits nothing, so no asynchronous arrive outlives the CTA.
+  bool mma_any = false, mma_failed = false;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer, A slices (all k-blocks)
@@ -736,7 +772,7 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
     const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
-    bool failed = false;
+    bool& failed = mma_failed;
     for (int kb = 0; kb < num_kb; ++kb) {
       const bool chunk_start = (kb % kKbPerChunk) == 0;
       const int g = kb & 1;
@@ -761,12 +797,15 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
                 tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
               }
             }
+            mma_any = true;
           }
-          tc::mma_commit(&aempty[s]);  // also after a failure: the A producer never starves
+          // also after a failure (the A producer never starves), unless the failure came
+          // before any MMA: then no asynchronous arrive may outlive the CTA
+          if (mma_any || !failed) tc::mma_commit(&aempty[s]);
         }
         __syncwarp();
       }
-      if (lane == 0) {
+      if (lane == 0 && (mma_any || !failed)) {
         tc::mma_commit(&bempty[g]);
         if ((kb % kKbPerChunk) == kKbPerChunk - 1 || kb == num_kb - 1) tc::mma_commit(cdone);
       }
@@ -857,7 +896,8 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
   __syncthreads();
   if (warp == 1) {
     // all MMAs have completed once the last chunk was signalled (or a wait gave up)
-    if (lane == 0 && nchunks > 0) (void)tc::mbar_wait(cdone, (uint32_t)(nchunks - 1) & 1u);
+    if (lane == 0 && (mma_any || !mma_failed) && nchunks > 0)
+      (void)tc::mbar_wait_bounded(cdone, (uint32_t)(nchunks - 1) & 1u);
     __syncwarp();
     tc::fence_after_sync();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
@@ -871,7 +911,7 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
 // (16- and 32-byte loads, one 8-byte store of four BF16 per slice); the 64 threads of a
 // chunk share its exponent and reduce its row sum in a fixed order.
 __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__ Tp, int nsplit, int64_t M,
-                                                      const float2* __restrict__ S2, const float2* __restrict__ t2,
+                                                      int64_t MB, const float2* __restrict__ S2, const float2* __restrict__ t2,
                                                       int64_t Rp, int64_t Kp, bf16* __restrict__ sl,
                                                       int* __restrict__ e, float2* __restrict__ rs2) {
   __shared__ float redm[8];
@@ -880,10 +920,10 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t b0 = (int64_t)blockIdx.y * 1024 + 4 * threadIdx.x; b0 - 4 * threadIdx.x < Kp; b0 += 1024 * gridDim.y) {
     float bh[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
-    if ((M & 3) == 0 && b0 + 3 < M) {  // 16-byte aligned rows; otherwise the scalar path below
+    if ((MB & 3) == 0 && b0 + 3 < MB) {  // 16-byte aligned rows; otherwise the scalar path below
       float th[4] = {0.f, 0.f, 0.f, 0.f}, tl[4] = {0.f, 0.f, 0.f, 0.f};
       for (int s = 0; s < nsplit; ++s) {
-        const float4* pp = reinterpret_cast<const float4*>(Tp + ((int64_t)s * M + a) * M + b0);
+        const float4* pp = reinterpret_cast<const float4*>(Tp + ((int64_t)s * M + a) * MB + b0);
         const float4 p0 = pp[0], p1 = pp[1];
         df_add(th[0], tl[0], p0.x, p0.y);
         df_add(th[1], tl[1], p0.z, p0.w);
@@ -891,7 +931,7 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
         df_add(th[3], tl[3], p1.z, p1.w);
       }
       const float4* tp = reinterpret_cast<const float4*>(t2 + b0);
-      const float4* sp = reinterpret_cast<const float4*>(S2 + a * M + b0);
+      const float4* sp = reinterpret_cast<const float4*>(S2 + a * MB + b0);
       const float4 t0 = tp[0], t1 = tp[1], s0 = sp[0], s1 = sp[1];
       const float tbh[4] = {t0.x, t0.z, t1.x, t1.z}, tbl[4] = {t0.y, t0.w, t1.y, t1.w};
       const float sh[4] = {s0.x, s0.z, s1.x, s1.z}, slo[4] = {s0.y, s0.w, s1.y, s1.w};
@@ -904,15 +944,15 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int64_t b = b0 + q;
-        if (b < M) {
+        if (b < MB) {
           float th = 0.f, tl = 0.f;
           for (int s = 0; s < nsplit; ++s) {
-            const float2 p = Tp[((int64_t)s * M + a) * M + b];
+            const float2 p = Tp[((int64_t)s * M + a) * MB + b];
             df_add(th, tl, p.x, p.y);
           }
           const float2 tb = t2[b];
           df_add(th, tl, -tb.x, -tb.y);
-          const float2 sab = S2[a * M + b];
+          const float2 sab = S2[a * MB + b];
           df_mul(sab.x, sab.y, th, tl, bh[q], bl[q]);
         }
       }
@@ -942,7 +982,7 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
       if ((bits >> 23) == 0) (void)frexpf(m, &ex);
     }
     const int64_t q = (b0 - 4 * (threadIdx.x & 63)) / oz::KC;  // this chunk
-    if ((threadIdx.x & 63) == 0 && q * oz::KC < M) {
+    if ((threadIdx.x & 63) == 0 && q * oz::KC < MB) {
       float h = redp[2 * c].x, l = redp[2 * c].y;
       df_add(h, l, redp[2 * c + 1].x, redp[2 * c + 1].y);
       rs2[q * M + a] = make_float2(h, l);
@@ -1116,8 +1156,19 @@ static void transpose(const double* X, int64_t rows, int64_t cols, int64_t ldx, 
   { oz_transpose_kernel<<<g, dim3(32, 8), 0, st>>>(X, rows, cols, ldx, XT); count_launch(); }
 }
 
+// K chunks per CTA of the matvec GEMM: as many as keep about 8 waves of CTAs on the GPU
+// (one per output tile and chunk group); the epilogue then runs once per group instead of
+// once per chunk and writes one partial per group
+int oz_auto_chunks_per_cta(int64_t tiles, int64_t nchunks) {
+  const int64_t target = 8 * (int64_t)num_sms();
+  const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(nchunks, cdiv(target, std::max<int64_t>(tiles, 1))));
+  return (int)cdiv(nchunks, groups);
+}
+
+// C partials (groups of G chunks, one float2 slab per group at out + z split_stride) of
+// A B^T; *groups_out = number of slabs written
 static gdml_status oz_gemm(const OzOperand& A, const OzOperand& B, float2* out, int64_t ldo, int64_t split_stride,
-                           int* err, cudaStream_t st) {
+                           int* err, cudaStream_t st, int G, int* groups_out = nullptr) {
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal2) != cudaSuccess)
@@ -1125,41 +1176,53 @@ static gdml_status oz_gemm(const OzOperand& A, const OzOperand& B, float2* out, 
     attr_set = true;
   }
   if (A.Kp != B.Kp) return fail(GDML_ERR_ARG, "sliced gemm: K mismatch");
-  dim3 grid((unsigned)cdiv(B.rows, oz::BN), (unsigned)cdiv(A.rows, oz::BM), (unsigned)A.nchunks);
   if (A.Kp % kKB2 != 0) return fail(GDML_ERR_ARG, "sliced gemm: K padding");
-  { oz_gemm_kernel<<<grid, kThreads, kSmemTotal2, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / kKB2), A.e, B.e, out, ldo, split_stride, err); count_launch(); }
+  G = std::max(1, std::min<int>(G, (int)A.nchunks));
+  const int groups = (int)cdiv(A.nchunks, G);
+  dim3 grid((unsigned)cdiv(B.rows, oz::BN), (unsigned)cdiv(A.rows, oz::BM), (unsigned)groups);
+  { oz_gemm_kernel<<<grid, kThreads, kSmemTotal2, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / kKB2), G, A.e, B.e, out, ldo, split_stride, err); count_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("sliced gemm launch: ") + cudaGetErrorString(e));
+  if (groups_out) *groups_out = groups;
   return GDML_OK;
 }
 
 gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, const double* A, int64_t ldA,
-                     const double* S, double c, cudaStream_t st) {
-  if (M > (int64_t)1 << 24 || D > (1 << 20)) return fail(GDML_ERR_ARG, "system too large for the sliced path");
+                     const double* S, double c, cudaStream_t st, int Ssym, const int* pis, const double* XcB) {
+  if (Ssym < 1 || (Ssym > 1 && (!pis || !XcB))) return fail(GDML_ERR_ARG, "sliced setup: bad symmetry arguments");
+  const int64_t MB = M * Ssym;
+  if (MB > (int64_t)1 << 24 || D > (1 << 20)) return fail(GDML_ERR_ARG, "system too large for the sliced path");
   oz.M = M;
+  oz.MB = MB;
   oz.N = N;
   oz.D = D;
+  oz.S = Ssym;
+  oz.pis = pis;
+  oz.XcB = Ssym > 1 ? XcB : Xc;
   OZ_TRY(make_operand(oz, oz.Xc1, M, D, oz::BM, st));
-  OZ_TRY(make_operand(oz, oz.W1, M, D, oz::BN, st));
-  OZ_TRY(make_operand(oz, oz.A2, M, M, oz::BM, st));
-  OZ_TRY(make_operand(oz, oz.WT2, D, M, oz::BN, st));
-  OZ_TRY(make_operand(oz, oz.B2, M, M, oz::BM, st));
-  OZ_TRY(make_operand(oz, oz.XT2, D, M, oz::BN, st));
+  OZ_TRY(make_operand(oz, oz.W1, MB, D, oz::BN, st));
+  OZ_TRY(make_operand(oz, oz.A2, M, MB, oz::BM, st));
+  OZ_TRY(make_operand(oz, oz.WT2, D, MB, oz::BN, st));
+  OZ_TRY(make_operand(oz, oz.B2, M, MB, oz::BM, st));
+  OZ_TRY(make_operand(oz, oz.XT2, D, MB, oz::BN, st));
   OZ_TRY(oz_alloc(oz, &oz.W, (size_t)(M * D), st));
-  OZ_TRY(oz_alloc(oz, &oz.WT, (size_t)(M * D), st));
-  OZ_TRY(oz_alloc(oz, &oz.t, (size_t)M, st));
-  OZ_TRY(oz_alloc(oz, &oz.t2, (size_t)M, st));
-  OZ_TRY(oz_alloc(oz, &oz.S2, (size_t)(M * M), st));
-  OZ_TRY(oz_alloc(oz, &oz.Tp, (size_t)(oz.W1.nchunks * M * M), st));
+  if (Ssym > 1) OZ_TRY(oz_alloc(oz, &oz.WB, (size_t)(MB * D), st));
+  OZ_TRY(oz_alloc(oz, &oz.WT, (size_t)(MB * D), st));
+  OZ_TRY(oz_alloc(oz, &oz.t, (size_t)MB, st));
+  OZ_TRY(oz_alloc(oz, &oz.t2, (size_t)MB, st));
+  OZ_TRY(oz_alloc(oz, &oz.S2, (size_t)(M * MB), st));
+  OZ_TRY(oz_alloc(oz, &oz.Tp, (size_t)(oz.W1.nchunks * M * MB), st));
   OZ_TRY(oz_alloc(oz, &oz.Up, (size_t)(2 * oz.A2.nchunks * M * D), st));
   OZ_TRY(oz_alloc(oz, &oz.rs2, (size_t)(oz.A2.nchunks * M), st));
   OZ_TRY(oz_alloc(oz, &oz.err, 1, st));
-  // fixed operands: Xc (GEMM 1 A), A (GEMM 2 A, segment 1), Xc^T (GEMM 2 B, segment 2), c^2 S
+  oz.g1 = oz_auto_chunks_per_cta(cdiv(MB, oz::BN) * cdiv(M, oz::BM), oz.W1.nchunks);
+  oz.g2 = oz_auto_chunks_per_cta(cdiv(D, oz::BN) * cdiv(M, oz::BM), oz.A2.nchunks);
+  // fixed operands: Xc (GEMM 1 A), A (GEMM 2 A, segment 1), XcB^T (GEMM 2 B, segment 2), c^2 S
   slice_rows(Xc, D, oz.Xc1, st);
   slice_rows(A, ldA, oz.A2, st);
-  transpose(Xc, M, D, D, oz.WT, st);
-  slice_rows(oz.WT, M, oz.XT2, st);
-  { oz_s2_kernel<<<(unsigned)cdiv(M * M, 256), 256, 0, st>>>(S, M * M, c * c, oz.S2); count_launch(); }
+  transpose(oz.XcB, MB, D, D, oz.WT, st);
+  slice_rows(oz.WT, MB, oz.XT2, st);
+  { oz_s2_kernel<<<(unsigned)cdiv(M * MB, 256), 256, 0, st>>>(S, M * MB, c * c, oz.S2); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced setup kernels");
   oz.ready = true;
   return GDML_OK;
@@ -1168,28 +1231,35 @@ gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, co
 gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
                       int add_lambda, double lam, cudaStream_t st) {
   if (!oz.ready) return fail(GDML_ERR_STATE, "sliced matvec not set up");
-  const int64_t M = oz.M;
+  const int64_t M = oz.M, MB = oz.MB;
   const int D = oz.D;
-  if (oz.W1.Kp <= oz::KC) {  // one chunk per row: projection and slicing in one kernel
+  const double* WB = oz.W;  // the training side's projection (MB x D)
+  if (oz.S > 1) {  // w_b = J_b v_b, then row b S + q = P_q w_b with t = xc_(bS+q) . w_(bS+q)
+    launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
+    launch_sym_gather(oz.W, M, D, oz.pis, oz.S, oz.XcB, oz.WB, oz.t, st);
+    slice_rows(oz.WB, D, oz.W1, st, oz.t, oz.t2);
+    WB = oz.WB;
+  } else if (oz.W1.Kp <= oz::KC) {  // one chunk per row: projection and slicing in one kernel
     { oz_proj_slice_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(double), st>>>(G, Xc, v, M, oz.N, D, oz.W, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
   } else {
     launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
     slice_rows(oz.W, D, oz.W1, st, oz.t, oz.t2);
   }
-  transpose(oz.W, M, D, D, oz.WT, st);
-  slice_rows(oz.WT, M, oz.WT2, st);
-  OZ_TRY(oz_gemm(oz.Xc1, oz.W1, oz.Tp, M, M * M, oz.err, st));
+  transpose(WB, MB, D, D, oz.WT, st);
+  slice_rows(oz.WT, MB, oz.WT2, st);
+  int groups1 = 0, groups2 = 0;
+  OZ_TRY(oz_gemm(oz.Xc1, oz.W1, oz.Tp, MB, M * MB, oz.err, st, oz.g1, &groups1));
   {
     dim3 g((unsigned)M, (unsigned)cdiv(oz.B2.Kp, 1024));
-    { oz_beta_kernel<<<g, 256, 0, st>>>(oz.Tp, (int)oz.W1.nchunks, M, oz.S2, oz.t2, oz.B2.Rp, oz.B2.Kp, (bf16*)oz.B2.slices, oz.B2.e, oz.rs2); count_launch(); }
+    { oz_beta_kernel<<<g, 256, 0, st>>>(oz.Tp, groups1, M, MB, oz.S2, oz.t2, oz.B2.Rp, oz.B2.Kp, (bf16*)oz.B2.slices, oz.B2.e, oz.rs2); count_launch(); }
   }
   const int64_t nch = oz.A2.nchunks;
-  OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st));
-  OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + nch * M * D, D, M * D, oz.err, st));
+  OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st, oz.g2, &groups2));
+  OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + (int64_t)groups2 * M * D, D, M * D, oz.err, st, oz.g2));
   const size_t smem = 3 * (size_t)D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { oz_backproj_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, (int)(2 * nch), M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
+  { oz_backproj_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced matvec kernels");
   return GDML_OK;
 }
@@ -1327,12 +1397,16 @@ gdml_status oz_gemm_tall(const double* A, int64_t n, int64_t K, const double* B,
   return s;
 }
 
-gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,
+cudaError_t set_wait_limit_oz(uint32_t polls) { return tc::set_wait_limit_here(polls); }
+uint32_t tc_default_wait_limit() { return tc::kSpinLimit; }
+
+gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, int G, double* C,
                          cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return fail(GDML_ERR_ARG, "oz_gemm_test: empty sizes");
   OzMatvec t;
   OzOperand a, b;
   float2* part = nullptr;
+  int groups = 0;
   gdml_status s = make_operand(t, a, M, K, oz::BM, st);
   if (s == GDML_OK) s = make_operand(t, b, N, K, oz::BN, st);
   if (s == GDML_OK) s = oz_alloc(t, &part, (size_t)(a.nchunks * M * N), st);
@@ -1340,10 +1414,11 @@ gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N,
   if (s == GDML_OK) {
     slice_rows(A, K, a, st);
     slice_rows(B, K, b, st);
-    s = oz_gemm(a, b, part, N, M * N, t.err, st);
+    if (G < 1) G = oz_auto_chunks_per_cta(cdiv(N, oz::BN) * cdiv(M, oz::BM), a.nchunks);
+    s = oz_gemm(a, b, part, N, M * N, t.err, st, G, &groups);
   }
   if (s == GDML_OK) {
-    { oz_sum_partials_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(part, (int)a.nchunks, M * N, C); count_launch(); }
+    { oz_sum_partials_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(part, groups, M * N, C); count_launch(); }
     int h = 0;
     if (cudaMemcpyAsync(&h, t.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

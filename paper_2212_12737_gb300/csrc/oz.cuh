@@ -51,8 +51,12 @@ struct OzOperand {
 
 struct OzMatvec {
   bool ready = false;
-  int64_t M = 0;
+  int64_t M = 0;   // rows a (the geometries)
+  int64_t MB = 0;  // training-side rows: M, or M S with S permutational symmetries (row b S + q)
   int N = 0, D = 0;
+  int S = 1;                     // symmetries
+  const int* pis = nullptr;      // S x D descriptor-entry permutations (S > 1)
+  const double* XcB = nullptr;   // MB x D centred training-side descriptors (S > 1)
   OzOperand Xc1;  // GEMM 1 A: Xc (rows a, K = D), fixed
   OzOperand W1;   // GEMM 1 B: W (rows b, K = D), per matvec
   OzOperand A2;   // GEMM 2 segment 1 A: A (rows a, K = b), fixed
@@ -60,7 +64,8 @@ struct OzMatvec {
   OzOperand B2;   // GEMM 2 segment 2 A: beta (rows a, K = b), per matvec
   OzOperand XT2;  // GEMM 2 segment 2 B: Xc^T (rows d, K = b), fixed
   double* W = nullptr;    // M x D (FP64 projection)
-  double* WT = nullptr;   // D x M
+  double* WB = nullptr;   // MB x D: the projection on the training side (S > 1)
+  double* WT = nullptr;   // D x MB
   double* t = nullptr;    // M: t_b = xc_b . w_b
   float2* t2 = nullptr;   // M: t_b as a double-float pair
   float2* S2 = nullptr;   // M x M: c^2 S_ab as double-float pairs
@@ -68,11 +73,16 @@ struct OzMatvec {
   float2* Up = nullptr;   // [2 * A2.nchunks][M][D] partials of U
   float2* rs2 = nullptr;  // [A2.nchunks][M] partial row sums of beta
   int* err = nullptr;
+  int g1 = 1, g2 = 1;  // K chunks per CTA of GEMM 1 and GEMM 2 (tuned by gdml_autotune)
   std::vector<void*> allocs;
 };
 
+// Xc: the M rows' centred descriptors.  Without symmetries (S = 1) the training side is the
+// same M geometries (XcB = Xc, A and S are M x M).  With S > 1 symmetries the training side has
+// MB = M S rows b S + q (XcB: MB x D, pis: S x D device permutations), A and S are M x MB.
 gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, const double* A, int64_t ldA,
-                     const double* S, double c, cudaStream_t st);
+                     const double* S, double c, cudaStream_t st, int Ssym = 1, const int* pis = nullptr,
+                     const double* XcB = nullptr);
 // out = K v (+ lambda v); G, Xc: the context's FP64 Jacobian factors and centred descriptors
 gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
                       int add_lambda, double lam, cudaStream_t st);
@@ -97,8 +107,11 @@ gdml_status oz_syrk_lower_f64(const double* X, int64_t rows, int64_t K, int64_t 
 gdml_status oz_gemm_tall(const double* A, int64_t n, int64_t K, const double* B, int64_t NB, int64_t ldb, bool tri_b,
                          bool rowsq, double* out, float* out32, cudaStream_t st);
 
-// test hook: C (M x N, FP64) = A (M x K) B (N x K)^T through the sliced tensor-core GEMM
-gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* C,
+// test hook: C (M x N, FP64) = A (M x K) B (N x K)^T through the sliced tensor-core GEMM with G
+// K-chunks per CTA (G < 1: the automatic choice)
+gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, int G, double* C,
                          cudaStream_t st);
+// K chunks per CTA that keep about 8 waves of CTAs for `tiles` output tiles
+int oz_auto_chunks_per_cta(int64_t tiles, int64_t nchunks);
 
 }  // namespace gdml

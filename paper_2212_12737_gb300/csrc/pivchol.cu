@@ -709,4 +709,6 @@ template void pivchol_run<float>(const PivCholArgs&, float*, cudaStream_t);
 
 int pivchol_part_blocks() { return kArgMaxBlocks; }
 
+cudaError_t set_wait_limit_pc(uint32_t polls) { return tc::set_wait_limit_here(polls); }
+
 }  // namespace gdml

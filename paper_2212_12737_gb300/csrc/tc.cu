@@ -473,4 +473,6 @@ gdml_status tc_gemm_test(int bf16, const double* A, const double* B, int M, int 
   return bf16 ? gemm_test_impl<true>(A, B, M, N, K, C, st) : gemm_test_impl<false>(A, B, M, N, K, C, st);
 }
 
+cudaError_t set_wait_limit_tc(uint32_t polls) { return tc::set_wait_limit_here(polls); }
+
 }  // namespace gdml

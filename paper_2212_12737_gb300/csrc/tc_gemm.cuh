@@ -26,6 +26,14 @@ constexpr int BK_BYTES = 128;    // one 128-byte swizzle span of K per stage
 constexpr int NUM_THREADS = 192;
 constexpr uint32_t kSpinLimit = 1u << 26;  // bounded waits (seconds, not forever)
 
+// Polls of every bounded wait of this translation unit: kSpinLimit unless a test lowers it
+// (gdml_test_set_wait_limit; 0 makes each wait give up at once, before any copy or MMA of the
+// waiting role is issued).  Each translation unit holds its own copy.
+static __constant__ uint32_t g_wait_limit = kSpinLimit;
+static inline cudaError_t set_wait_limit_here(uint32_t polls) {
+  return cudaMemcpyToSymbol(g_wait_limit, &polls, sizeof(polls));
+}
+
 enum : int { ERR_NONE = 0, ERR_TIMEOUT_FULL = 1, ERR_TIMEOUT_EMPTY = 2, ERR_TIMEOUT_DONE = 3 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -43,6 +51,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 
 // Bounded wait for the phase with the given parity; returns false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const uint32_t limit = g_wait_limit;
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+// Wait with the fixed bound kSpinLimit whatever g_wait_limit says: for a thread that waits on
+// its own MMAs before the CTA releases its tensor memory and exits.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   const uint32_t addr = smem_u32(bar);
   for (uint32_t it = 0; it < kSpinLimit; ++it) {
     uint32_t done;
@@ -192,6 +218,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  // MMA thread: issued at least one MMA / a wait gave up.  A thread that gave up before
+  // issuing anything commits nothing, so no asynchronous arrive outlives the CTA.
+  bool mma_any = false, mma_failed = false;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -236,10 +265,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         mma_issue<BF16>(tmem, make_sw128_desc(sa + kk * 32), make_sw128_desc(sb + kk * 32), idesc,
                         (i > 0 || kk > 0) ? 1u : 0u);
       }
+      mma_any = true;
       mma_commit(&empty[s]);  // stage reusable once these MMAs have read it
     }
-    (void)ok;
-    mma_commit(done);  // arrives when every MMA issued above has completed
+    mma_failed = !ok;
+    // arrives when every MMA issued above has completed
+    if (mma_any || ok) mma_commit(done);
   } else if (warp >= 2) {
     // ---------------- epilogue
     const int quarter = warp & 3;
@@ -273,7 +304,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     // the accumulator must be idle before it is released (already true unless a wait timed out)
-    if (lane == 0) (void)mbar_wait(done, 0);
+    if (lane == 0 && (mma_any || !mma_failed)) (void)mbar_wait_bounded(done, 0);
     __syncwarp();
     fence_after_sync();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),

@@ -968,4 +968,6 @@ void to_float(const double* a, int64_t n, float* b, cudaStream_t st) {
   { to_float_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(a, n, b); count_launch(); }
 }
 
+cudaError_t set_wait_limit_wb(uint32_t polls) { return tc::set_wait_limit_here(polls); }
+
 }  // namespace gdml

@@ -45,7 +45,8 @@ namespace {
 
 __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t addr = tc::smem_u32(bar);
-  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
+  const uint32_t limit = tc::g_wait_limit;
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

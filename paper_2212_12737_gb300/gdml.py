@@ -23,9 +23,10 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 
 PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "df64": 3, "ozaki": 4}
 SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3}
 
-EXPORTS = ["gdml_kernel_setup", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
+EXPORTS = ["gdml_kernel_setup", "gdml_kernel_setup_sym", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
-           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_test_oz_gemm", "gdml_test_df_passes", "gdml_test_oz_gemm_tall", "gdml_test_precond_factor", "gdml_tc_check",
+           "gdml_last_error", "gdml_destroy", "gdml_test_tc_gemm", "gdml_test_oz_gemm", "gdml_test_df_passes", "gdml_test_oz_gemm_tall", "gdml_test_precond_factor", "gdml_test_set_wait_limit",
+           "gdml_test_cholesky_jitter", "gdml_test_set_lambda", "gdml_tc_check",
            "gdml_launch_count", "gdml_matvec_noalloc", "gdml_pcg_solve_batched", "gdml_autotune",
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
@@ -61,6 +62,7 @@ def load() -> ctypes.CDLL:
     P, I64, I32, D, U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64
     sig = {
         "gdml_kernel_setup": [ctypes.POINTER(P), P, I64, I32, D, D, I32, P],
+        "gdml_kernel_setup_sym": [ctypes.POINTER(P), P, I64, I32, P, I32, D, D, I32, P],
         "gdml_matvec": [P, P, P, I32],
         "gdml_matvec_fp64": [P, P, P, I32],
         "gdml_precond_build": [P, I32, I64, U64, P, P],
@@ -72,10 +74,13 @@ def load() -> ctypes.CDLL:
         "gdml_last_error": [P],
         "gdml_destroy": [P],
         "gdml_test_tc_gemm": [I32, P, P, I32, I32, I32, P, P],
-        "gdml_test_oz_gemm": [P, P, I64, I64, I64, P, P],
+        "gdml_test_oz_gemm": [P, P, I64, I64, I64, I32, P, P],
         "gdml_test_df_passes": [P, I64, I64, P, P, D, I32, P, P, P],
         "gdml_test_oz_gemm_tall": [P, I64, I64, P, I64, I64, I32, I32, P, P, P],
         "gdml_test_precond_factor": [P, P],
+        "gdml_test_set_wait_limit": [ctypes.c_uint32],
+        "gdml_test_cholesky_jitter": [P, I64, P, ctypes.POINTER(D), P],
+        "gdml_test_set_lambda": [P, D],
         "gdml_tc_check": [P],
         "gdml_launch_count": [],
         "gdml_matvec_noalloc": [P, I64, I32, D, D, P, P, I32, P],
@@ -147,7 +152,8 @@ def _vec_arg(t: torch.Tensor, n: int, device: torch.device, name: str) -> torch.
 class Context:
     """One kernel system (Sec. 2.1, Eq. 1) living on the current CUDA device."""
 
-    def __init__(self, R: torch.Tensor, sigma: float, lam: float, precision: str = "fp64", stream=None):
+    def __init__(self, R: torch.Tensor, sigma: float, lam: float, precision: str = "fp64", stream=None,
+                 perms=None):
         lib = load()
         if R.dtype != torch.float64 or R.dim() != 3 or R.shape[2] != 3:
             raise ValueError("R must be a float64 CUDA tensor of shape (M, N, 3)")
@@ -157,8 +163,18 @@ class Context:
         self.device = R.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(R.device)
         h = ctypes.c_void_p()
-        st = lib.gdml_kernel_setup(ctypes.byref(h), _ptr(R), self.M, self.N, float(sigma), float(lam),
-                                   PRECISION[precision], ctypes.c_void_p(self.stream.cuda_stream))
+        if perms is None:
+            st = lib.gdml_kernel_setup(ctypes.byref(h), _ptr(R), self.M, self.N, float(sigma), float(lam),
+                                       PRECISION[precision], ctypes.c_void_p(self.stream.cuda_stream))
+        else:  # permutational symmetries: S x N atom permutations forming a group
+            import numpy as np
+            P = np.ascontiguousarray(np.asarray(perms, dtype=np.int32))
+            if P.ndim != 2 or P.shape[1] != self.N:
+                raise ValueError(f"perms must have shape (S, {self.N})")
+            st = lib.gdml_kernel_setup_sym(ctypes.byref(h), _ptr(R), self.M, self.N,
+                                           P.ctypes.data_as(ctypes.c_void_p), int(P.shape[0]), float(sigma),
+                                           float(lam), PRECISION[precision],
+                                           ctypes.c_void_p(self.stream.cuda_stream))
         if st != 0:
             raise GdmlError(st, lib.gdml_last_error(None).decode())
         self._h = h
@@ -239,6 +255,10 @@ class Context:
         self._check(load().gdml_test_precond_factor(self._h, _ptr(out)))
         return out.t()
 
+    def test_set_lambda(self, lam: float):
+        """Replace lambda (test hook; lam <= 0 makes K + lam I indefinite); drops the preconditioner."""
+        self._check(load().gdml_test_set_lambda(self._h, float(lam)))
+
     def set_inner_rtol(self, v: float):
         self._check(load().gdml_set_inner_rtol(self._h, float(v)))
 
@@ -299,8 +319,10 @@ class Context:
             pass
 
 
-def kernel_setup(R, sigma, lam, precision="fp64", stream=None) -> Context:
-    return Context(R, sigma, lam, precision, stream)
+def kernel_setup(R, sigma, lam, precision="fp64", stream=None, perms=None) -> Context:
+    """A context for one kernel system; perms (S x N atom permutations forming a group) selects
+    the symmetric (sGDML) kernel."""
+    return Context(R, sigma, lam, precision, stream, perms)
 
 
 def matvec(ctx: Context, v, out=None, add_lambda=True):
@@ -334,15 +356,16 @@ def test_tc_gemm(A: torch.Tensor, B: torch.Tensor, bf16: bool = False) -> torch.
     return C
 
 
-def test_oz_gemm(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
-    """C = A B^T through the sliced-BF16 tensor-core GEMM (FP64-class accuracy)."""
+def test_oz_gemm(A: torch.Tensor, B: torch.Tensor, chunks_per_cta: int = 0) -> torch.Tensor:
+    """C = A B^T through the sliced-BF16 tensor-core GEMM (FP64-class accuracy); chunks_per_cta
+    256-entry K chunks accumulated per CTA (0: automatic)."""
     lib = load()
     A = A.contiguous()
     B = B.contiguous()
     M, K = A.shape
     N = B.shape[0]
     C = torch.empty(M, N, dtype=torch.float64, device=A.device)
-    st = lib.gdml_test_oz_gemm(_ptr(A), _ptr(B), M, N, K, _ptr(C),
+    st = lib.gdml_test_oz_gemm(_ptr(A), _ptr(B), M, N, K, int(chunks_per_cta), _ptr(C),
                                ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())
@@ -390,6 +413,29 @@ def test_df_passes(L: torch.Tensor, r: torch.Tensor, u: torch.Tensor, lam: float
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())
     return t, z
+
+
+def test_set_wait_limit(polls: int | None):
+    """Every bounded device wait gives up after `polls` polls (0: at once); None restores the default."""
+    lib = load()
+    st = lib.gdml_test_set_wait_limit(0xFFFFFFFF if polls is None else int(polls))
+    if st != 0:
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+
+
+def test_cholesky_jitter(A: torch.Tensor):
+    """The library's FP64 Cholesky with the jitter retries of the preconditioner build on A (k x k):
+    returns (lower factor, jitter)."""
+    lib = load()
+    A = A.contiguous()
+    k = A.shape[0]
+    L = torch.zeros_like(A)
+    eps = ctypes.c_double()
+    st = lib.gdml_test_cholesky_jitter(_ptr(A), k, _ptr(L), ctypes.byref(eps),
+                                       ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
+    if st != 0:
+        raise GdmlError(st, lib.gdml_last_error(None).decode())
+    return torch.tril(L), float(eps.value)
 
 
 def launch_count() -> int:

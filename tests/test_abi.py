@@ -106,3 +106,38 @@ def test_binding_rejects_vectors_the_library_would_overrun():
         gdml._vec_arg(torch.zeros(12, dtype=torch.float64)[::2], 6, cpu, "v")
     with pytest.raises(TypeError):
         gdml._vec_arg([0.0] * 6, 6, cpu, "v")
+
+
+def test_symmetry_groups_are_checked_on_the_host(lib_path):
+    """gdml_kernel_setup_sym rejects permutation sets that are not a group before any device work
+    (no GPU needed): not a permutation, identity missing, not closed, repeated rows, S out of range."""
+    try:
+        lib = ctypes.CDLL(lib_path)
+    except OSError as e:
+        pytest.skip(f"cannot dlopen: {e}")
+    import numpy as np
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    fn = lib.gdml_kernel_setup_sym
+    fn.argtypes = [ctypes.POINTER(P), P, I64, I32, P, I32, D, D, I32, P]
+    fn.restype = ctypes.c_int
+    lib.gdml_last_error.restype = ctypes.c_char_p
+    lib.gdml_last_error.argtypes = [P]
+    fake_R = ctypes.c_void_p(0x1000)  # never dereferenced: the group is checked first
+    idn = list(range(5))
+    cases = {
+        "not a permutation": [idn, [0, 0, 2, 3, 4]],
+        "identity": [[1, 0, 2, 3, 4]],
+        "closed under composition": [idn, [1, 2, 0, 3, 4]],
+        "twice": [idn, idn],
+    }
+    for word, perms in cases.items():
+        arr = np.ascontiguousarray(np.asarray(perms, dtype=np.int32))
+        h = ctypes.c_void_p()
+        st = fn(ctypes.byref(h), fake_R, 3, 5, arr.ctypes.data_as(ctypes.c_void_p), arr.shape[0], 1.0, 1e-6, 0, None)
+        assert st == 1 and not h.value, word
+        assert word in lib.gdml_last_error(None).decode(), (word, lib.gdml_last_error(None))
+    arr = np.ascontiguousarray(np.asarray([idn, [1, 0, 2, 3, 4]], dtype=np.int32))
+    h = ctypes.c_void_p()
+    for prec in (1, 2, 3):  # TF32, BF16, DF64 do not take symmetries
+        assert fn(ctypes.byref(h), fake_R, 3, 5, arr.ctypes.data_as(ctypes.c_void_p), 2, 1.0, 1e-6, prec, None) == 1
+    assert fn(ctypes.byref(h), fake_R, 3, 5, None, 2, 1.0, 1e-6, 0, None) == 1

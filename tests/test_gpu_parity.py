@@ -244,22 +244,52 @@ def test_zero_rhs_and_iteration_cap_and_bad_args(prec):
     ctx.destroy()
 
 
-@pytest.mark.parametrize("prec", ["ozaki"])
-def test_df_pivoted_cholesky_at_full_size_matches_oracle(prec):
-    """The DF64/OZAKI Algorithm 1 at n = 63,000: 256-row chunks of the fused Schur + finish
-    pass.  L is stored in FP32 there, which perturbs the residual diagonal by ~1e-7 of its
-    scale: pivots must agree up to a first divergence at a near-tie of that size, and the
-    trace to 1e-6 up to it."""
+@pytest.mark.parametrize("prec,k", [("ozaki", 400)])
+def test_df_pivoted_cholesky_full_depth_replay_at_full_size(prec, k):
+    """Algorithm 1 in the DF64/OZAKI form at n = 63,000 to k = 400: 256-row chunks of the
+    fused Schur + finish pass, past m ~ 380 where it streams the first m columns evict-first.
+    The oracle replays the GPU's pivot sequence (forced) and at EVERY step the GPU's pivot
+    must be the residual diagonal's maximum up to what the FP32 storage of L perturbs
+    (1e-6 of the largest diagonal); the residual traces must agree to that storage error."""
     w = synth.workload("aspirin21_m1000")
-    k = 48
     ctx = gdml.kernel_setup(dev(w.R), w.sigma, w.lam, precision=prec)
     piv, tr = ctx.precond_build("pivchol", k, pivots=True, trace=True)
-    get_col = ok.column_getter(w.R, w.sigma)
-    L, rpiv, rtr, diags = oracle_pivchol_with_diags(get_col, ok.force_kernel_diag(w.R, w.sigma), k)
-    gp = piv.cpu().numpy()
-    m = len(rpiv) if np.array_equal(gp, rpiv) else int(np.argmax(gp != rpiv))
-    if m < len(rpiv):
-        assert abs(diags[m][gp[m]] - diags[m][rpiv[m]]) <= 1e-6 * diags[0].max(), f"pivot {m} differs"
-    assert m >= 8
-    np.testing.assert_allclose(tr.cpu().numpy()[:m], rtr[:m], rtol=1e-6, atol=1e-9 * rtr[0])
     ctx.destroy()
+    gp = piv.cpu().numpy()
+    d0 = ok.force_kernel_diag(w.R, w.sigma)
+    diags = []
+    L, rp, rtr = op.pivoted_cholesky(ok.column_getter(w.R, w.sigma), d0, k, forced=gp, diag_out=diags)
+    assert np.array_equal(rp, gp) and len(diags) == k
+    tol = 1e-6 * d0.max()
+    worst = 0.0
+    for m in range(k):
+        dm = diags[m]
+        dm[gp[:m]] = -np.inf
+        worst = max(worst, dm.max() - dm[gp[m]])
+        assert dm[gp[m]] >= dm.max() - tol, f"step {m}: pivot {gp[m]} is {dm.max() - dm[gp[m]]:.2e} below the max"
+    print(f"{prec} Algorithm 1 replay, k={k}: largest shortfall of a GPU pivot {worst:.2e} (tol {tol:.2e})")
+    # each stored l_ij is an FP32 rounding (2^-24 relative) and sum_j l_ij^2 <= K_ii, so every
+    # residual diagonal may move by 2 2^-24 K_ii and the trace by 2^-23 tr(K)
+    np.testing.assert_allclose(tr.cpu().numpy(), rtr, rtol=0, atol=2.0 ** -23 * d0.sum())
+
+
+def test_headline_ozaki_solution_by_the_oracle():
+    """aspirin21_m1000 in the OZAKI form with the pivoted-Cholesky preconditioner at k = 2000:
+    the oracle's own FP64 matvec recomputes the true residual of the GPU's alpha."""
+    w = synth.workload("aspirin21_m1000")
+    ctx = gdml.kernel_setup(dev(w.R), w.sigma, w.lam, precision="ozaki")
+    ctx.precond_build("pivchol", w.k)
+    alpha, iters, rel, _ = ctx.pcg_solve(dev(w.y), rtol=1e-8)
+    ctx.tc_check()
+    v = dev(np.random.default_rng(3).standard_normal(w.n))
+    for _ in range(30):
+        v = ctx.matvec(v, add_lambda=False)
+        knorm = float(torch.linalg.norm(v))
+        v = v / knorm
+    ctx.destroy()
+    a = alpha.cpu().numpy()
+    res = np.linalg.norm(w.y - ok.matvec(w.R, w.sigma, a, w.lam)) / np.linalg.norm(w.y)
+    bound = 8 * EPS * knorm * np.linalg.norm(a) / np.linalg.norm(w.y)
+    print(f"aspirin21_m1000 ozaki: {iters} iterations, GPU relres {rel:.2e}, oracle relres {res:.2e} "
+          f"(bound {bound:.1e})")
+    assert rel <= 1e-8 and res <= 1e-8 + bound

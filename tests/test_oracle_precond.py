@@ -144,6 +144,45 @@ def test_pivoted_cholesky_steps_match_explicit_schur_complements(tiny):
     np.testing.assert_allclose((L @ L.T)[:, piv], K[:, piv], atol=1e-10 * np.abs(K).max())
 
 
+def test_pivoted_cholesky_forced_replay_reproduces_free_run(tiny):
+    """Forcing Algorithm 1's own free choices reproduces it exactly (same factor, pivots,
+    trace), and the recorded residual diagonals are those the free run took its argmax of;
+    forcing a different (valid) column changes the factor and is checked like any other."""
+    R, _ = tiny
+    K = ok.force_kernel_dense(R, 1.2)
+    k = 12
+    diags = []
+    L, piv, tr = op.pivoted_cholesky(lambda i: K[:, i], np.diag(K), k, diag_out=diags)
+    L2, piv2, tr2 = op.pivoted_cholesky(lambda i: K[:, i], np.diag(K), k, forced=piv)
+    assert np.array_equal(piv2, piv) and np.array_equal(L2, L) and np.array_equal(tr2, tr)
+    assert len(diags) == k and np.array_equal(diags[0], np.diag(K))
+    for m in range(k):
+        dm = diags[m].copy()
+        dm[piv[:m]] = -np.inf
+        assert piv[m] == int(np.argmax(dm))
+    other = list(piv)
+    other[3] = int(np.setdiff1d(np.arange(K.shape[0]), piv)[0])
+    L3, piv3, _ = op.pivoted_cholesky(lambda i: K[:, i], np.diag(K), k, forced=other)
+    assert np.array_equal(piv3, other)
+    np.testing.assert_allclose((L3 @ L3.T)[:, piv3], K[:, piv3], atol=1e-10 * np.abs(K).max())
+    with pytest.raises(ValueError):
+        op.pivoted_cholesky(lambda i: K[:, i], np.diag(K), 3, forced=[piv[0], piv[1], piv[0]])
+
+
+def test_cholesky_jitter_rule():
+    """The jitter reading of Eq. 5's factorisation: none for SPD, eps = 1e-14 tr/k for an
+    exactly singular PSD matrix, failure for indefinite ones (also with tr <= 0)."""
+    A = spd(6, 2)
+    L, eps = op.cholesky_jitter(A)
+    assert eps == 0.0 and np.allclose(L @ L.T, A, atol=1e-14)
+    S = np.diag([3.0, 2.0, 1.0, 0.0])
+    L, eps = op.cholesky_jitter(S)
+    assert eps == pytest.approx(1e-14 * 6.0 / 4) and np.allclose(L @ L.T, S + eps * np.eye(4), atol=1e-15)
+    for A in (np.diag([2.0, -1.0]), np.diag([1.0, -1.0]), np.diag([-1.0, -2.0]), np.zeros((2, 2))):
+        with pytest.raises(np.linalg.LinAlgError):
+            op.cholesky_jitter(A)
+
+
 def test_nystrom_on_pivots_equals_incomplete_cholesky(tiny):
     """Sec. 3: Nystrom with the same inducing columns is the incomplete Cholesky."""
     R, _ = tiny
