@@ -55,7 +55,7 @@ def parse():
                          "passes of the DF64/OZAKI apply on a random FP32 factor of the workload's n x k")
     ap.add_argument("--rows", type=int, default=1, choices=[1, 128, 256],
                     help="--only passes: row-chunk size of the staged passes (1: automatic)")
-    ap.add_argument("--suite", default=None, choices=["batched", "learned"],
+    ap.add_argument("--suite", default=None, choices=["batched", "learned", "sym"],
                     help="many uneven systems: per-system solves vs one batched graph solve")
     ap.add_argument("--suite-count", type=int, default=64)
     ap.add_argument("--suite-mmax", type=int, default=2000, help="cap on M (geometries) per system")
@@ -324,6 +324,67 @@ def run_learned(args):
                                   "iters_without_referee": it_raw, "relres_without_referee": rel_raw},
                       "uniform": {"iters": it_u, "relres": rel_u}}), flush=True)
     sc.destroy()
+
+
+def run_sym(args):
+    """sGDML: the symmetric force kernel with the group S3 of atoms 0, 1, 2 (6 permutations, the
+    size of a methyl group's symmetries) against the plain kernel on the same system: matvec time
+    in FP64 and OZAKI, and the OZAKI solve (setup, pivoted-Cholesky build, PCG to 1e-8)."""
+    import itertools
+
+    import torch
+
+    from paper_2212_12737_gb300 import gdml, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = synth.workload(args.workload)
+    idn = list(range(w.N))
+    group = []
+    for p3 in itertools.permutations((0, 1, 2)):
+        g = list(idn)
+        g[0], g[1], g[2] = p3
+        group.append(g)
+    R = torch.from_numpy(w.R).to(dev)
+    y = torch.from_numpy(w.y).to(dev)
+    v = torch.randn(w.n, dtype=torch.float64, device=dev)
+    out = torch.empty_like(v)
+    st = torch.cuda.current_stream(dev)
+
+    def mv_ms(ctx, reps):
+        for _ in range(2):
+            ctx.matvec(v, out)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s.record(st)
+        for _ in range(reps):
+            ctx.matvec(v, out)
+        e.record(st)
+        torch.cuda.synchronize(dev)
+        return s.elapsed_time(e) / reps
+
+    res = {"suite": "sym", "workload": f"{w.name}: n={w.n}, {w.select} k={w.k}, lambda={w.lam}", "S": len(group),
+           "group": "S3 on atoms 0, 1, 2"}
+    for prec in ("fp64", "ozaki"):
+        for label, perms in (("plain", None), ("sym", group)):
+            ctx = gdml.kernel_setup(R, w.sigma, w.lam, precision=prec, perms=perms)
+            res[f"{prec}_{label}_matvec_ms"] = mv_ms(ctx, 3 if prec == "fp64" else 20)
+            ctx.destroy()
+    for label, perms in (("plain", None), ("sym", group)):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx = gdml.kernel_setup(R, w.sigma, w.lam, precision="ozaki", perms=perms)
+        ctx.precond_build(w.select, w.k, seed=2)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        _, it, rel, _ = ctx.pcg_solve(y, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
+        t2 = time.perf_counter()
+        ctx.tc_check()
+        ctx.destroy()
+        res[f"ozaki_{label}_solve"] = {"s": t2 - t0, "setup_build_s": t1 - t0, "pcg_s": t2 - t1, "iters": it,
+                                       "relres": rel, "converged": rel <= RTOL}
+    print(json.dumps(res), flush=True)
 
 
 def max_over_ranks(t: float, world: int, device) -> float:
@@ -757,6 +818,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.suite == "learned":
         run_learned(a)
+    elif a.suite == "sym":
+        run_sym(a)
     elif a.suite:
         run_suite(a)
     elif a.only != "solve":

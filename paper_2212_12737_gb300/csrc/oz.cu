@@ -41,7 +41,8 @@ constexpr int kBTile2 = 2 * kBTile;              // 16 KB: two spans of 64 rows
 constexpr int kBGroup2 = oz::S * kBTile2;        // 112 KB
 constexpr int kAStages2 = 3;
 constexpr int kSmemData2 = kBGroup2 + kAStages2 * kATile2;  // 208 KB
-constexpr int kSmemTotal2 = kSmemData2 + 1024 + 256;
+constexpr int kExpStage = oz::BM + oz::BN;         // a chunk's row and column exponents
+constexpr int kSmemTotal2 = kSmemData2 + 1024 + 256 + 2 * kExpStage * 4;
 constexpr int kKbPerChunk2 = oz::KC / kKB2;      // 2
 static_assert(oz::BM * kStageLd * 8 <= kSmemData2, "output staging fits the operand buffers");
 static_assert(kSmemTotal2 <= 227 * 1024, "shared memory per CTA");
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tfree = cdone + 1;           // the epilogue has read a chunk's accumulators
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfree + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* sexp = reinterpret_cast<int*>(smem + kSmemData2 + 256);  // [2][rows 128 | columns 64] exponents
   float2* stage = reinterpret_cast<float2*>(smem);  // output tile, reuses the operand buffers after the MMAs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -534,11 +536,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3;
     const int cbase = ((warp - 3) >> 2) * 32;  // this warp's 32 of the tile's 64 columns
     const int row = m0 + quarter * 32 + lane;
+    const int et = threadIdx.x - 96;           // 0..255 over the epilogue warps
+    // a chunk's 128 row and 64 column exponents into shared memory, one coalesced load each,
+    // a chunk ahead of its drain (the drain then reads no global memory)
+    auto load_exps = [&](int q) {
+      int* dst = sexp + (q & 1) * kExpStage;
+      const int64_t zq = q_begin + q;
+      if (et < oz::BM)
+        dst[et] = m0 + et < M ? eA[zq * M + m0 + et] : 0;
+      else if (et < kExpStage)
+        dst[et] = n0 + et - oz::BM < N ? eB[zq * N + n0 + et - oz::BM] : 0;
+    };
+    if (nq > 0) load_exps(0);
     float rh[32], rl[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) rh[t] = rl[t] = 0.f;
     bool go = true;
-    for (int q = 0; q < nq && go; ++q) {
+    // every epilogue warp passes named barrier 1 exactly nq + 1 times, whatever fails: after a
+    // failed wait a warp keeps looping without waiting or reading the accumulators
+    for (int q = 0; q < nq; ++q) {
+      // chunk q's exponents are visible, and chunk q - 1's buffer may be refilled
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (q + 1 < nq) load_exps(q + 1);
+      if (!go) continue;
       int okw = 1;
       if (lane == 0) {
         okw = tc::mbar_wait(cdone, (uint32_t)q & 1u) ? 1 : 0;
@@ -551,11 +571,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) {
         go = false;
-        break;
+        continue;
       }
       tc::fence_after_sync();
-      const int64_t zq = q_begin + q;  // chunk index along K
-      const int ea = row < M ? eA[zq * M + row] : 0;
+      const int* ex = sexp + (q & 1) * kExpStage;
+      const int ea = ex[quarter * 32 + lane];
 #pragma unroll
       for (int c8 = 0; c8 < 32; c8 += 8) {
         uint32_t v[oz::S][8];
@@ -577,9 +597,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[2][t]), pow2f(-oz::BITS * 4)));
           df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[1][t]), pow2f(-oz::BITS * 3)));
           df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[0][t]), pow2f(-oz::BITS * 2)));
-          const int col = n0 + cbase + c8 + t;
-          const int ex = ea + (col < N ? eB[zq * N + col] : 0);
-          df_add(rh[c8 + t], rl[c8 + t], scale2(hh, ex), scale2(ll, ex));
+          const int e2 = ea + ex[oz::BM + cbase + c8 + t];
+          df_add(rh[c8 + t], rl[c8 + t], scale2(hh, e2), scale2(ll, e2));
         }
       }
       // this warp has read chunk q: release the accumulators
