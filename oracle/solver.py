@@ -34,6 +34,10 @@ class PCGResult:
     converged: bool
     restarts: int
     history: list
+    # CG coefficients of the first run (before any restart): gamma_j = rho_j / p_j^T A p_j and
+    # beta_j = rho_{j+1} / rho_j, the entries of the Lanczos matrix of P^-1 A (oracle.spectrum)
+    gammas: list = dataclasses.field(default_factory=list)
+    betas: list = dataclasses.field(default_factory=list)
 
 
 def pcg(apply_A, apply_Pinv, y: np.ndarray, rtol: float = 1e-8, max_iter: int | None = None,
@@ -46,10 +50,11 @@ def pcg(apply_A, apply_Pinv, y: np.ndarray, rtol: float = 1e-8, max_iter: int | 
     ynorm = float(np.linalg.norm(y))
     x = np.zeros(n)
     if ynorm == 0.0:
-        return PCGResult(x, 0, 0.0, True, 0, [])
+        return PCGResult(x, 0, 0.0, True, 0, [], [], [])
     it = 0
     restarts = 0
     hist = []
+    gammas, betas = [], []
     r = y.copy()
     while True:
         z = apply_Pinv(r)
@@ -61,6 +66,8 @@ def pcg(apply_A, apply_Pinv, y: np.ndarray, rtol: float = 1e-8, max_iter: int | 
             if not pq > 0.0:
                 raise FloatingPointError("PCG breakdown: p^T A p <= 0")
             gamma = rho / pq
+            if restarts == 0:
+                gammas.append(gamma)
             x += gamma * p
             r -= gamma * q
             it += 1
@@ -70,10 +77,12 @@ def pcg(apply_A, apply_Pinv, y: np.ndarray, rtol: float = 1e-8, max_iter: int | 
                 break
             z = apply_Pinv(r)
             rho_new = float(r @ z)
+            if restarts == 0:
+                betas.append(rho_new / rho)
             p = z + (rho_new / rho) * p
             rho = rho_new
         r = y - apply_A(x)
         true_rel = float(np.linalg.norm(r)) / ynorm
         if true_rel <= rtol or it >= max_iter or restarts >= max_restarts:
-            return PCGResult(x, it, true_rel, true_rel <= rtol, restarts, hist)
+            return PCGResult(x, it, true_rel, true_rel <= rtol, restarts, hist, gammas, betas)
         restarts += 1
