@@ -63,7 +63,7 @@ typedef enum {
 /* OZAKI: the two descriptor contractions run on the BF16 tensor cores with
  * FP64-class accuracy.  Each 256-entry chunk of an operand row is scaled by a
  * power of two and cut into 7 exact BF16 integer slices of 7 bits (49 bits);
- * slice pairs whose products are kept (i + j <= 8) are accumulated exactly in
+ * slice pairs whose products are kept (i + j <= 8 counting slices from 1: 28 of 49) are accumulated exactly in
  * FP32 per level, combined in double-float and summed across chunks (the
  * error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012; ~1e-14 relative
  * matvec error).  Preconditioner and PCG as for DF64.  Operand magnitudes must
@@ -75,7 +75,8 @@ typedef enum {
   GDML_SEL_UNIFORM = 0, /* k distinct columns, uniformly at random */
   GDML_SEL_RLS = 1,     /* sampled without replacement by estimated ridge leverage scores */
   GDML_SEL_PIVCHOL = 2, /* incomplete Cholesky with greedy diagonal pivoting (Alg. 1) */
-  GDML_SEL_WEIGHTED = 3 /* sampled without replacement by given per-geometry scores (learned scorer) */
+  GDML_SEL_WEIGHTED = 3, /* sampled without replacement by given per-geometry scores (learned scorer) */
+  GDML_SEL_SVD = 4       /* the k dominant eigenpairs of K: the optimal rank-k reference (Sec. 2.2, App. A.1) */
 } gdml_select;
 
 /* Build a context for one kernel system (Sec. 2.1, Eq. 1).
@@ -147,13 +148,22 @@ gdml_status gdml_predict_forces(gdml_ctx* ctx, const double* R_query_dev, int64_
  *  pivots_dev (may be NULL): k int64 column indices in selection order
  *    (uniform/rls: ascending key; pivchol: pivot order of Alg. 1).
  *  resid_trace_dev (may be NULL): k doubles; for pivchol the sum of the
- *    residual diagonal after each step (monotone, Sec. 3), else zeros.
+ *    residual diagonal after each step (monotone, Sec. 3), for SVD see below,
+ *    else zeros.
  * Uniform/RLS: L_k = K_nk L_kk^-T with K_kk = L_kk L_kk^T (Eq. 5); if that
  * Cholesky fails, jitter eps = 1e-14 tr(K_kk)/k is added and multiplied by 10
  * per retry up to 1e-6 tr(K_kk)/k.  Pivchol: L_k from Alg. 1 (stops early,
  * with a smaller rank, if the largest residual diagonal is <= 0).
+ * SVD (GDML_SEL_SVD; the paper's optimal but O(n^3)-costly reference, for small n): K is
+ * PSD, so its SVD is its eigendecomposition K = U Sigma U^T; the preconditioner is
+ * P = U_k Sigma_k U_k^T + lambda I, i.e. L_k = U_k Sigma_k^(1/2) (the k largest eigenvalues,
+ * negative rounding clamped to 0).  K is assembled densely from the kernel columns and
+ * decomposed by cuSOLVER's syevd (loaded from libcusolver on first use); n <= 24576, and
+ * about 24 n^2 bytes of device memory are allocated and freed inside the call.  No pivots
+ * (pivots_dev receives -1); resid_trace_dev[m] = tr(K) minus the m + 1 largest eigenvalues.
  * Then C = lambda I + L_k^T L_k and its FP64 Cholesky factor (Eq. 4).
- * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_NOT_SPD, GDML_ERR_CUDA. */
+ * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_NOT_SPD, GDML_ERR_CUDA (also when libcusolver
+ * cannot be loaded for GDML_SEL_SVD). */
 gdml_status gdml_precond_build(gdml_ctx* ctx, int32_t method, int64_t k, uint64_t seed,
                                int64_t* pivots_dev, double* resid_trace_dev);
 
@@ -216,6 +226,24 @@ gdml_status gdml_precond_apply(gdml_ctx* ctx, const double* r_dev, double* z_dev
  * GDML_ERR_BREAKDOWN, GDML_ERR_ARG, GDML_ERR_CUDA. */
 gdml_status gdml_pcg_solve(gdml_ctx* ctx, const double* y_dev, double* alpha_dev, double rtol,
                            int32_t max_iter, int32_t* iters_out, double* relres_out);
+
+/* Spectrum diagnostics of the last gdml_pcg_solve (Sec. 4.1, Fig. 3: the convergence of PCG
+ * follows the spectrum of P^-1 K_lambda).  The first CG run of that solve (before any
+ * true-residual restart; for TF32/BF16 contexts the first inner solve) recorded its step
+ * lengths gamma_j = rho_j / p_j^T K_lambda p_j and ratios beta_j = rho_(j+1) / rho_j on the
+ * device.  They define the Lanczos tridiagonal matrix T_m of P^-1 K_lambda,
+ *   T[0,0] = 1/gamma_0, T[j,j] = 1/gamma_j + beta_(j-1)/gamma_(j-1),
+ *   T[j,j+1] = T[j+1,j] = sqrt(beta_j)/gamma_j   (m = the run's iterations, at most 20000),
+ * whose eigenvalues (Ritz values) lie within the spectrum of P^-1 K_lambda and converge to its
+ * extreme eigenvalues as the run proceeds; theta_max / theta_min estimates cond(P^-1 K_lambda)
+ * from below.  Host arithmetic (bisection on Sturm counts, O(m) per bisection step).
+ *  count (0..1024): how many of the largest Ritz values to write to ritz_host (host array,
+ *    descending; entries beyond m are NaN); ritz_host may be NULL when count is 0.
+ *  theta_min, theta_max, steps_out (host, each may be NULL): the extreme Ritz values and m.
+ * Errors: GDML_ERR_STATE (no solve recorded coefficients: none yet, the last solve had y = 0
+ * or was batched), GDML_ERR_ARG, GDML_ERR_CUDA. */
+gdml_status gdml_pcg_spectrum(gdml_ctx* ctx, int32_t count, double* ritz_host, double* theta_min, double* theta_max,
+                              int32_t* steps_out);
 
 /* Inner tolerance of the mixed-precision refinement (default 1e-3 for BF16,
  * 1e-4 for TF32; ignored in FP64 contexts).

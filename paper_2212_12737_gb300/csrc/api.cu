@@ -44,6 +44,12 @@ int num_sms() {
 
 using namespace gdml;
 
+// iterations of a solve whose CG coefficients are kept for gdml_pcg_spectrum (320 KB per context)
+constexpr int64_t kHistCap = 20000;
+// largest n of the SVD preconditioner: dense K (8 n^2 bytes) and syevd's workspace of ~2 n^2
+// doubles (its size is a 32-bit int)
+constexpr int64_t kSvdMaxN = 24576;
+
 struct gdml_ctx {
   int device = 0;
   cudaStream_t st = nullptr;
@@ -110,6 +116,12 @@ struct gdml_ctx {
   double* hsc = nullptr;      // pinned host mirror of scalars
   int64_t* ictl = nullptr;    // device loop control (IC_*)
   int64_t* hictl = nullptr;   // pinned host mirror
+  // CG coefficients (gamma_j, beta_j) of the first CG run of the last gdml_pcg_solve: the Lanczos
+  // matrix behind gdml_pcg_spectrum
+  double* hist = nullptr;     // 2 * hist_cap doubles
+  int64_t hist_cap = 0;
+  int64_t hist_len = 0;       // iterations recorded
+  bool hist_arm = false;      // the next pcg_core run records
   cudaStream_t cap = nullptr;             // private stream used only to capture graphs
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // PCG loop graphs: [0] context precision, [1] FP64
   int64_t gbody[2] = {0, 0};                       // kernels per captured iteration
@@ -495,10 +507,10 @@ gdml_status pcg_body(gdml_ctx* c, double* x, bool fp64_mv, cudaGraphConditionalH
   TRY(matvec_any(c, c->p, c->q, 1, fp64_mv));
   TRY(dot(c, c->p, c->q, SC_PQ));
   // x, r update fused with r.r and the loop's end test
-  launch_update_xr_rr(x, c->r, c->p, c->q, n, c->sc, c->status, c->partial, c->ticket, c->ictl, h, 1, c->st);
+  launch_update_xr_rr(x, c->r, c->p, c->q, n, c->sc, c->status, c->partial, c->ticket, c->ictl, h, 1, c->hist, c->st);
   TRY(apply_precond(c, c->r, c->z));
   TRY(dot(c, c->r, c->z, SC_RHO_NEW));
-  launch_update_p_rho(c->p, c->z, n, c->sc, c->ticket, c->st);
+  launch_update_p_rho(c->p, c->z, n, c->sc, c->ticket, c->ictl, c->hist, c->st);
   return check_launch(c, "pcg body");
 }
 
@@ -576,8 +588,9 @@ gdml_status pcg_core(gdml_ctx* c, const double* b, double* x, double tol_abs, in
     TRY(dot(c, c->r, c->z, SC_RHO));
     c->hictl[IC_ITER] = 0;
     c->hictl[IC_MAXIT] = max_iter - it;
+    c->hictl[IC_HCAP] = c->hist_arm ? std::min<int64_t>(c->hist_cap, max_iter - it) : 0;
     c->hsc[SC_TOL2] = tol_abs * tol_abs;
-    CTRY(c, cudaMemcpyAsync(c->ictl, c->hictl, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CTRY(c, cudaMemcpyAsync(c->ictl, c->hictl, 3 * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     CTRY(c, cudaMemcpyAsync(c->sc + SC_TOL2, c->hsc + SC_TOL2, sizeof(double), cudaMemcpyHostToDevice, st));
     CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), st));
     cudaGraphExec_t ex = nullptr;
@@ -589,6 +602,10 @@ gdml_status pcg_core(gdml_ctx* c, const double* b, double* x, double tol_abs, in
     TRY(fetch_scalars(c));  // synchronises
     it += c->hictl[IC_ITER];
     count_launch(c->hictl[IC_ITER] * c->gbody[fp64_mv && c->precision != GDML_FP64 ? 1 : 0]);
+    if (c->hist_arm) {  // only the first run of a solve forms one Lanczos process
+      c->hist_len = std::min(c->hictl[IC_ITER], c->hist_cap);
+      c->hist_arm = false;
+    }
     res = std::sqrt(c->hsc[SC_RR]);
     if (hst || !std::isfinite(res)) {
       // an inner solve of the refinement stops at the last good iterate (its
@@ -735,6 +752,9 @@ gdml_status setup_impl(gdml_ctx** out, const double* R_dev, int64_t M, int32_t N
   TRY(dalloc(C, &c->werr, 1));
   CTRY(C, cudaMemsetAsync(c->werr, 0, sizeof(int), c->st));
   TRY(dalloc(C, &c->ictl, IC_COUNT));
+  CTRY(C, cudaMemsetAsync(c->ictl, 0, IC_COUNT * sizeof(int64_t), c->st));
+  c->hist_cap = kHistCap;
+  TRY(dalloc(C, &c->hist, (size_t)(2 * c->hist_cap)));
   CTRY(C, cudaMallocHost(&c->hsc, SC_COUNT * sizeof(double)));
   CTRY(C, cudaMallocHost(&c->hictl, IC_COUNT * sizeof(int64_t)));
   CTRY(C, cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), c->st));
@@ -858,8 +878,11 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
   TRY(validate(c));
   const int64_t n = c->n;
   if (k < 1 || k > n || k > 16384) return ctx_fail(c, GDML_ERR_ARG, "need 1 <= k <= min(n, 16384)");
-  if (method < GDML_SEL_UNIFORM || method > GDML_SEL_WEIGHTED) return ctx_fail(c, GDML_ERR_ARG, "unknown method");
+  if (method < GDML_SEL_UNIFORM || method > GDML_SEL_SVD) return ctx_fail(c, GDML_ERR_ARG, "unknown method");
   if (method == GDML_SEL_WEIGHTED && !geometry_scores) return ctx_fail(c, GDML_ERR_ARG, "scores are NULL");
+  if (method == GDML_SEL_SVD && n > kSvdMaxN)
+    return ctx_fail(c, GDML_ERR_ARG, "the SVD preconditioner needs n <= " + std::to_string(kSvdMaxN) +
+                                         " (a dense eigendecomposition of K)");
   c->k = 0;
   c->ws = WsPlan();
   c->jitter = 0.0;
@@ -940,6 +963,34 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     CTRY(c, cudaStreamSynchronize(c->st));
     rank = hps.rank;
     if (rank < 1) return ctx_fail(c, GDML_ERR_NOT_SPD, "diag(K) has no positive entry");
+  } else if (method == GDML_SEL_SVD) {
+    // dense K from the kernel columns, its eigendecomposition, L_k = U_k Sigma_k^(1/2); no
+    // pivots (left at -1); trace[m] = tr(K) - (sum of the m + 1 largest eigenvalues)
+    double *Kd = nullptr, *w = nullptr;
+    int64_t* cols = nullptr;
+    TRY(s.get(&Kd, (size_t)(n * n)));
+    TRY(s.get(&w, (size_t)n));
+    TRY(s.get(&cols, (size_t)n));
+    std::vector<int64_t> hcols(n);
+    for (int64_t i = 0; i < n; ++i) hcols[i] = i;
+    CTRY(c, cudaMemcpyAsync(cols, hcols.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+    constexpr int64_t kBlock = 4096;
+    for (int64_t j0 = 0; j0 < n; j0 += kBlock) TRY(get_cols(c, cols + j0, std::min(kBlock, n - j0), Kd + j0 * n));
+    const std::string e = eigh_dense(Kd, n, w, c->st);
+    if (!e.empty()) return ctx_fail(c, GDML_ERR_CUDA, "SVD preconditioner: " + e);
+    launch_svd_factor(Kd, w, n, k, c->L, c->st);
+    TRY(check_launch(c, "SVD factor"));
+    std::vector<double> hw(n), htr(k);
+    CTRY(c, cudaMemcpyAsync(hw.data(), w, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CTRY(c, cudaStreamSynchronize(c->st));
+    double rest = 0.0;  // ascending: the eigenvalues below the top m + 1
+    for (int64_t i = 0; i < n - k; ++i) rest += hw[i];
+    for (int64_t m = k - 1; m >= 0; --m) {
+      htr[m] = rest;
+      if (m > 0) rest += hw[n - 1 - m];
+    }
+    CTRY(c, cudaMemcpyAsync(trace, htr.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    if (df_precond(c)) to_float(c->L, n * k, c->Lf, c->st);
   } else {
     uint64_t* key = nullptr;
     int64_t* idx = nullptr;
@@ -1034,6 +1085,33 @@ gdml_status gdml_precond_apply(gdml_ctx* c, const double* r, double* z) {
   return apply_precond(c, r, z);
 }
 
+gdml_status gdml_pcg_spectrum(gdml_ctx* c, int32_t count, double* ritz_host, double* theta_min, double* theta_max,
+                              int32_t* steps_out) {
+  TRY(validate(c));
+  if (count < 0 || count > 1024 || (count > 0 && !ritz_host))
+    return ctx_fail(c, GDML_ERR_ARG, "pcg_spectrum: need 0 <= count <= 1024 and ritz_host for count > 0");
+  if (c->hist_len < 1) return ctx_fail(c, GDML_ERR_STATE, "pcg_spectrum: no recorded PCG run (solve first)");
+  const int64_t m_rec = c->hist_len;
+  std::vector<double> h(2 * m_rec);
+  CTRY(c, cudaMemcpyAsync(h.data(), c->hist, 2 * m_rec * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  std::vector<double> g(m_rec), b(m_rec);
+  int64_t m = 0;  // the valid prefix: positive finite steps, non-negative finite ratios between them
+  for (; m < m_rec; ++m) {
+    g[m] = h[2 * m];
+    b[m] = h[2 * m + 1];
+    if (!(g[m] > 0.0 && std::isfinite(g[m]))) break;
+    if (m > 0 && !(b[m - 1] >= 0.0 && std::isfinite(b[m - 1]))) break;
+  }
+  if (m < 1) return ctx_fail(c, GDML_ERR_STATE, "pcg_spectrum: the recorded run has no valid CG step");
+  double tmin = 0.0, tmax = 0.0;
+  lanczos_ritz(g.data(), b.data(), m, count, ritz_host, &tmin, &tmax);
+  if (theta_min) *theta_min = tmin;
+  if (theta_max) *theta_max = tmax;
+  if (steps_out) *steps_out = (int32_t)m;
+  return GDML_OK;
+}
+
 gdml_status gdml_set_inner_rtol(gdml_ctx* c, double v) {
   TRY(validate(c));
   if (!(v > 0.0 && v < 1.0)) return ctx_fail(c, GDML_ERR_ARG, "inner_rtol must be in (0, 1)");
@@ -1063,6 +1141,8 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
   int64_t iters = 0;
   double res = 0.0;
   gdml_status stat = GDML_OK;
+  c->hist_len = 0;
+  c->hist_arm = true;  // the first CG run below records its coefficients
   if (ynorm == 0.0) {
     CTRY(c, cudaMemsetAsync(alpha, 0, n * sizeof(double), st));
     c->last_outer = 0;
@@ -1114,6 +1194,7 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
     }
     c->last_outer = outer;
   }
+  c->hist_arm = false;
   CTRY(c, cudaStreamSynchronize(st));
   if (c->precision == GDML_TF32 || c->precision == GDML_BF16 || c->precision == GDML_OZAKI) {
     gdml_status ts = c->precision == GDML_OZAKI ? oz_check(c->oz, st) : tc_check(c->tc, st);
@@ -1352,6 +1433,8 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
       active[i] = ynorm[i] > 0.0 && res[i] > tol && iters[i] < max_iter && restarts[i] <= max_rs;
       c->hictl[IC_ITER] = 0;
       c->hictl[IC_MAXIT] = active[i] ? max_iter - iters[i] : 0;
+      c->hictl[IC_HCAP] = 0;  // batched solves record no Lanczos coefficients
+      c->hist_len = 0;
       c->hsc[SC_TOL2] = tol * tol;
       if (active[i]) {
         ++n_active;
@@ -1359,7 +1442,7 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
         CTRY(c, cudaMemcpyAsync(c->p, c->z, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
         TRY(dot(c, c->r, c->z, SC_RHO));
       }
-      CTRY(c, cudaMemcpyAsync(c->ictl, c->hictl, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+      CTRY(c, cudaMemcpyAsync(c->ictl, c->hictl, 3 * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
       CTRY(c, cudaMemcpyAsync(c->sc + SC_TOL2, c->hsc + SC_TOL2, sizeof(double), cudaMemcpyHostToDevice, c->st));
       CTRY(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
       CTRY(c, cudaStreamSynchronize(c->st));

@@ -57,13 +57,15 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const double* __restri
 // keep the WHILE node running while |r|^2 > tol^2, the residual is finite, no breakdown was
 // flagged and the iteration cap is not reached.
 // A breakdown (pq not positive and finite) flags status and leaves x, r untouched.
+// With hist, the last CTA records gamma of this iteration (the Lanczos matrix of the run).
 __global__ void __launch_bounds__(kDotThreads) update_xr_rr_kernel(double* __restrict__ x, double* __restrict__ r,
                                                                    const double* __restrict__ p,
                                                                    const double* __restrict__ q, int64_t n,
                                                                    double* __restrict__ sc, int* __restrict__ status,
                                                                    double* __restrict__ partial,
                                                                    unsigned* __restrict__ ticket, int64_t* ictl,
-                                                                   cudaGraphConditionalHandle h, int check) {
+                                                                   cudaGraphConditionalHandle h, int check,
+                                                                   double* __restrict__ hist) {
   __shared__ double red[kDotThreads / 32];
   __shared__ bool last;
   const double pq = sc[SC_PQ];
@@ -99,6 +101,7 @@ __global__ void __launch_bounds__(kDotThreads) update_xr_rr_kernel(double* __res
     sc[SC_RR] = tot;
     *ticket = 0u;
     if (check) {
+      if (hist && ictl[IC_ITER] < ictl[IC_HCAP]) hist[2 * ictl[IC_ITER]] = gamma;
       const int64_t it = ictl[IC_ITER] + 1;
       ictl[IC_ITER] = it;
       const bool go = (tot > sc[SC_TOL2]) && isfinite(tot) && (it < ictl[IC_MAXIT]) && ok && (*status == 0);
@@ -107,10 +110,13 @@ __global__ void __launch_bounds__(kDotThreads) update_xr_rr_kernel(double* __res
   }
 }
 
-// p = z + (rho_new / rho) p, then rho <- rho_new in the last CTA (after every CTA has read it)
+// p = z + (rho_new / rho) p, then rho <- rho_new in the last CTA (after every CTA has read it);
+// with hist it also records the ratio of the iteration just counted by update_xr_rr_kernel
 __global__ void __launch_bounds__(256) update_p_rho_kernel(double* __restrict__ p, const double* __restrict__ z,
                                                            int64_t n, double* __restrict__ sc,
-                                                           unsigned* __restrict__ ticket) {
+                                                           unsigned* __restrict__ ticket,
+                                                           const int64_t* __restrict__ ictl,
+                                                           double* __restrict__ hist) {
   __shared__ bool last;
   const double beta = sc[SC_RHO_NEW] / sc[SC_RHO];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -122,6 +128,10 @@ __global__ void __launch_bounds__(256) update_p_rho_kernel(double* __restrict__ 
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
+    if (hist) {
+      const int64_t j = ictl[IC_ITER] - 1;
+      if (j >= 0 && j < ictl[IC_HCAP]) hist[2 * j + 1] = beta;
+    }
     sc[SC_RHO] = sc[SC_RHO_NEW];
     *ticket = 0u;
   }
@@ -158,11 +168,12 @@ void launch_dot(const double* x, const double* y, int64_t n, double* partial, un
 }
 void launch_update_xr_rr(double* x, double* r, const double* p, const double* q, int64_t n, double* sc, int* status,
                          double* partial, unsigned* ticket, int64_t* ictl, cudaGraphConditionalHandle h, int check,
-                         cudaStream_t st) {
-  { update_xr_rr_kernel<<<dot_blocks(), kDotThreads, 0, st>>>(x, r, p, q, n, sc, status, partial, ticket, ictl, h, check); count_launch(); }
+                         double* hist, cudaStream_t st) {
+  { update_xr_rr_kernel<<<dot_blocks(), kDotThreads, 0, st>>>(x, r, p, q, n, sc, status, partial, ticket, ictl, h, check, hist); count_launch(); }
 }
-void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, cudaStream_t st) {
-  { update_p_rho_kernel<<<4 * num_sms(), 256, 0, st>>>(p, z, n, sc, ticket); count_launch(); }
+void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, const int64_t* ictl,
+                         double* hist, cudaStream_t st) {
+  { update_p_rho_kernel<<<4 * num_sms(), 256, 0, st>>>(p, z, n, sc, ticket, ictl, hist); count_launch(); }
 }
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st) {
   { axpby_kernel<<<4 * num_sms(), 256, 0, st>>>(y, x, a, b, n); count_launch(); }

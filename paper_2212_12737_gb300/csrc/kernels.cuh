@@ -4,6 +4,7 @@
 #include <cuda.h>
 
 #include <functional>
+#include <string>
 
 #include "common.cuh"
 
@@ -11,8 +12,9 @@ namespace gdml {
 
 // scalar slots of the PCG state (device array of doubles)
 enum { SC_RHO = 0, SC_PQ = 1, SC_RR = 2, SC_RHO_NEW = 3, SC_YY = 4, SC_TOL2 = 5, SC_COUNT = 8 };
-// integer control words of the PCG loop (device int64 array)
-enum { IC_ITER = 0, IC_MAXIT = 1, IC_COUNT = 4 };
+// integer control words of the PCG loop (device int64 array); IC_HCAP: how many iterations of
+// the running loop may record their CG coefficients (0: none)
+enum { IC_ITER = 0, IC_MAXIT = 1, IC_HCAP = 2, IC_COUNT = 4 };
 
 // geom.cu
 void launch_desc_jac(const double* R, int64_t M, int N, int D, double* X, double* G, cudaStream_t st);
@@ -128,15 +130,31 @@ void launch_check_finite(const double* a, int64_t count, int* flag, cudaStream_t
 void launch_dot(const double* x, const double* y, int64_t n, double* partial, unsigned* ticket, double* out,
                 cudaStream_t st);
 // x += gamma p; r -= gamma q; sc[RR] = r.r (dot_kernel's partition and order); check != 0: also
-// the end-of-iteration test of the graph-captured loop (conditional handle h)
+// the end-of-iteration test of the graph-captured loop (conditional handle h).  hist (may be
+// null): hist[2 j] = gamma of loop iteration j while j < ictl[IC_HCAP]
 void launch_update_xr_rr(double* x, double* r, const double* p, const double* q, int64_t n, double* sc, int* status,
                          double* partial, unsigned* ticket, int64_t* ictl, cudaGraphConditionalHandle h, int check,
-                         cudaStream_t st);
-// p = z + (rho_new / rho) p; rho <- rho_new
-void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, cudaStream_t st);
+                         double* hist, cudaStream_t st);
+// p = z + (rho_new / rho) p; rho <- rho_new.  hist (may be null): hist[2 j + 1] = rho_new / rho of
+// loop iteration j = ictl[IC_ITER] - 1 while j < ictl[IC_HCAP]
+void launch_update_p_rho(double* p, const double* z, int64_t n, double* sc, unsigned* ticket, const int64_t* ictl,
+                         double* hist, cudaStream_t st);
 void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
 cudaError_t add_pcg_gate_node(cudaGraph_t g, cudaGraphNode_t* node, const double* sc, const int64_t* ictl,
                               cudaGraphConditionalHandle h);
+
+// spectrum.cu
+// L[:, j] = U[:, n - 1 - j] sqrt(max(w[n - 1 - j], 0)) for j < k: the factor of the rank-k SVD
+// preconditioner from an ascending eigendecomposition (U column-major n x n, L column-major)
+void launch_svd_factor(const double* U, const double* w, int64_t n, int64_t k, double* L, cudaStream_t st);
+// dense symmetric eigendecomposition in place (A column-major n x n, lower triangle read;
+// eigenvectors overwrite A, ascending eigenvalues in w).  Returns an empty string on success,
+// else what failed.
+std::string eigh_dense(double* A, int64_t n, double* w, cudaStream_t st);
+// Ritz values of the Lanczos matrix T_m of m CG steps (gamma_j, beta_j; see gdml_pcg_spectrum):
+// its smallest and largest eigenvalue and its `count` largest in descending order
+void lanczos_ritz(const double* gamma, const double* beta, int64_t m, int64_t count, double* top, double* tmin,
+                  double* tmax);
 
 // select.cu
 int64_t select_scratch_len(int64_t n);

@@ -21,7 +21,7 @@ _lib = None
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 5: "ERR_BREAKDOWN",
           6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
 PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "df64": 3, "ozaki": 4}
-SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3}
+SELECT = {"uniform": 0, "rls": 1, "pivchol": 2, "weighted": 3, "svd": 4}
 
 EXPORTS = ["gdml_kernel_setup", "gdml_kernel_setup_sym", "gdml_matvec", "gdml_matvec_fp64", "gdml_precond_build", "gdml_precond_info",
            "gdml_precond_apply", "gdml_pcg_solve", "gdml_set_inner_rtol", "gdml_last_outer_steps",
@@ -31,7 +31,7 @@ EXPORTS = ["gdml_kernel_setup", "gdml_kernel_setup_sym", "gdml_matvec", "gdml_ma
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
            "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy", "gdml_rule_of_thumb_k",
-           "gdml_predict_forces"]
+           "gdml_predict_forces", "gdml_pcg_spectrum"]
 
 # Table 1 (Sec. 4.3): molecule -> (m, k_min) of the rule of thumb, fitted at n = 31k;
 # "default" is the row for molecules without fitted parameters.
@@ -99,6 +99,7 @@ def load() -> ctypes.CDLL:
         "gdml_scorer_destroy": [P],
         "gdml_rule_of_thumb_k": [I64, D, D, ctypes.POINTER(I64)],
         "gdml_predict_forces": [P, P, I64, P, P],
+        "gdml_pcg_spectrum": [P, I32, P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -279,9 +280,21 @@ class Context:
             self._check(st)
         return alpha, int(it.value), float(rel.value), int(outer.value)
 
+    def pcg_spectrum(self, count: int = 0):
+        """Ritz values of the last solve's first CG run (the Lanczos matrix of P^-1 K_lambda):
+        (theta_min, theta_max, steps, the `count` largest in descending order as a NumPy array)."""
+        import numpy as np
+        top = np.full(max(int(count), 0), np.nan)
+        tmin, tmax, steps = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        ptr = top.ctypes.data_as(ctypes.c_void_p) if count > 0 else None
+        self._check(load().gdml_pcg_spectrum(self._h, int(count), ptr, ctypes.byref(tmin), ctypes.byref(tmax),
+                                             ctypes.byref(steps)))
+        return float(tmin.value), float(tmax.value), int(steps.value), top
+
     def autotune(self, cache: str | None = None) -> int:
-        """Pick the fastest K-split of the matvec's second contraction for this
-        context's shapes; with a cache file, reuse / record the choice there."""
+        """Time the matvec's tunable tile parameters for this context's shapes and keep the
+        fastest (FP64 / TF32 / BF16: the K-split of the second contraction; OZAKI: the K chunks
+        each CTA of the sliced GEMMs accumulates); with a cache file, reuse / record the choice."""
         import json
         key = f"M{self.M}_N{self.N}_{self.precision}"
         table = {}
