@@ -250,7 +250,19 @@ gdml_status gdml_pcg_spectrum(gdml_ctx* ctx, int32_t count, double* ritz_host, d
  * Errors: GDML_ERR_ARG unless 0 < inner_rtol < 1. */
 gdml_status gdml_set_inner_rtol(gdml_ctx* ctx, double inner_rtol);
 
-/* Outer refinement steps of the last gdml_pcg_solve (1 for FP64 contexts).
+/* Slice levels of the matvec inside the PCG loop of an OZAKI context: mixed precision with a
+ * cheaper inner operator and FP64 true residuals.  levels = 7 (the default) is the full product;
+ * levels < 7 keeps only the slice pairs i + j < levels (slices counted from 0) in both
+ * contractions: fewer tensor-core products (28, 21, 15, 10 for 7, 6, 5, 4 levels) and a matvec
+ * error of roughly 2^-(7 levels - 2) relative to |K||v| instead of ~1e-14.  The recurrence then
+ * solves a slightly perturbed system; gdml_pcg_solve recomputes the true residual with the FP64
+ * matvec whenever the recurrence passes and restarts PCG from alpha (at most 10 times), so the
+ * reported residual is the FP64 one.  gdml_matvec and the build are not affected.
+ * Errors: GDML_ERR_ARG (not an OZAKI context, levels outside 1..7). */
+gdml_status gdml_set_inner_levels(gdml_ctx* ctx, int32_t levels);
+
+/* Outer refinement steps of the last gdml_pcg_solve: for FP64, DF64 and OZAKI contexts the
+ * number of PCG runs (1 + true-residual restarts); for TF32/BF16 the refinement steps.
  * Errors: GDML_ERR_ARG (NULL context). */
 gdml_status gdml_last_outer_steps(const gdml_ctx* ctx, int32_t* outer_out);
 

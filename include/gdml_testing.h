@@ -26,11 +26,13 @@ gdml_status gdml_test_tc_gemm(int32_t bf16, const double* A_dev, const double* B
  * 256-entry chunk of a row of A and B is split into 7 BF16 slices of 7 bits,
  * chunk products are accumulated exactly in FP32 per slice level, each CTA adds
  * chunks_per_cta consecutive chunks in double-float (< 1: the contexts' automatic
- * choice) and the groups' partials are summed into C as FP64.  Synchronises the stream.
+ * choice) and the groups' partials are summed into C as FP64.  levels (1..7) keeps the
+ * slice pairs i + j < levels only (0-based slices; 7 is the full product, fewer give the
+ * cheaper product of gdml_set_inner_levels).  Synchronises the stream.
  * Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA, GDML_ERR_TIMEOUT (a bounded pipeline
  * wait gave up). */
 gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
-                              int32_t chunks_per_cta, double* C_dev, void* cuda_stream);
+                              int32_t chunks_per_cta, int32_t levels, double* C_dev, void* cuda_stream);
 
 /* The tall product of the OZAKI preconditioner build (Eq. 5's L_k = K_nk L_kk^-T as K_nk
  * times the transposed triangular inverse, and the leverage-score row norms of Sec. 3's

@@ -59,6 +59,8 @@ struct gdml_ctx {
   int precision = GDML_FP64;
   double inner_rtol = 1e-4;
   int last_outer = 0;
+  int inner_lev = 7;       // OZAKI: slice levels of the PCG loop's matvec (gdml_set_inner_levels)
+  int last_restarts = 0;   // true-residual restarts of the last pcg_core call
   std::string err;
   std::vector<void*> allocs;
 
@@ -225,11 +227,12 @@ gdml_status matvec_df(gdml_ctx* c, const double* v, double* out, int add_lambda)
   return check_launch(c, "matvec_df");
 }
 
-gdml_status matvec_any(gdml_ctx* c, const double* v, double* out, int add_lambda, bool force_fp64) {
+// lev: slice levels of an OZAKI context's matvec (7: the full, FP64-class product)
+gdml_status matvec_any(gdml_ctx* c, const double* v, double* out, int add_lambda, bool force_fp64, int lev = 7) {
   if (force_fp64 || c->precision == GDML_FP64) return matvec_fp64(c, v, out, add_lambda);
   if (c->precision == GDML_DF64) return matvec_df(c, v, out, add_lambda);
   if (c->precision == GDML_OZAKI) {
-    gdml_status s = oz_matvec(c->oz, c->G, c->Xc(), v, out, add_lambda, c->lam, c->st);
+    gdml_status s = oz_matvec(c->oz, c->G, c->Xc(), v, out, add_lambda, c->lam, c->st, lev);
     if (s != GDML_OK) return ctx_fail(c, s, "sliced tensor-core matvec: " + last_msg());
     return check_launch(c, "matvec_oz");
   }
@@ -504,7 +507,7 @@ void drop_graphs(gdml_ctx* c) {
 //   rho' = r.z; p = z + (rho'/rho) p; rho = rho'.
 gdml_status pcg_body(gdml_ctx* c, double* x, bool fp64_mv, cudaGraphConditionalHandle h) {
   const int64_t n = c->n;
-  TRY(matvec_any(c, c->p, c->q, 1, fp64_mv));
+  TRY(matvec_any(c, c->p, c->q, 1, fp64_mv, c->inner_lev));
   TRY(dot(c, c->p, c->q, SC_PQ));
   // x, r update fused with r.r and the loop's end test
   launch_update_xr_rr(x, c->r, c->p, c->q, n, c->sc, c->status, c->partial, c->ticket, c->ictl, h, 1, c->hist, c->st);
@@ -625,6 +628,7 @@ gdml_status pcg_core(gdml_ctx* c, const double* b, double* x, double tol_abs, in
   }
   *iters = it;
   *res_out = res;
+  c->last_restarts = restarts;
   return out;
 }
 
@@ -1112,6 +1116,15 @@ gdml_status gdml_pcg_spectrum(gdml_ctx* c, int32_t count, double* ritz_host, dou
   return GDML_OK;
 }
 
+gdml_status gdml_set_inner_levels(gdml_ctx* c, int32_t levels) {
+  TRY(validate(c));
+  if (c->precision != GDML_OZAKI) return ctx_fail(c, GDML_ERR_ARG, "inner levels apply to OZAKI contexts only");
+  if (levels < 1 || levels > 7) return ctx_fail(c, GDML_ERR_ARG, "inner levels must be in 1..7");
+  if (levels != c->inner_lev) drop_graphs(c);  // the captured loop bakes the GEMMs' level count in
+  c->inner_lev = levels;
+  return GDML_OK;
+}
+
 gdml_status gdml_set_inner_rtol(gdml_ctx* c, double v) {
   TRY(validate(c));
   if (!(v > 0.0 && v < 1.0)) return ctx_fail(c, GDML_ERR_ARG, "inner_rtol must be in (0, 1)");
@@ -1153,7 +1166,7 @@ gdml_status gdml_pcg_solve(gdml_ctx* c, const double* y, double* alpha, double r
     CTRY(c, cudaMemcpyAsync(c->x, alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     stat = pcg_core(c, c->ys, c->x, rtol * ynorm, max_iter, fp64, true, fp64 ? 3 : 10, &iters, &res);
     CTRY(c, cudaMemcpyAsync(alpha, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    c->last_outer = 1;
+    c->last_outer = 1 + c->last_restarts;
   } else {
     // FP64 iterative refinement around the tensor-core PCG
     double* dx = c->x;
@@ -1259,12 +1272,13 @@ gdml_status gdml_test_df_passes(const float* L_dev, int64_t n, int64_t k, const 
 }
 
 gdml_status gdml_test_oz_gemm(const double* A_dev, const double* B_dev, int64_t M, int64_t N, int64_t K,
-                              int32_t chunks_per_cta, double* C_dev, void* stream) {
+                              int32_t chunks_per_cta, int32_t levels, double* C_dev, void* stream) {
   clear_msg();
   if (!A_dev || !B_dev || !C_dev || M < 1 || N < 1 || K < 1) return fail(GDML_ERR_ARG, "bad gemm test arguments");
   if (M > ((int64_t)1 << 24) || N > ((int64_t)1 << 24) || K > ((int64_t)1 << 24))
     return fail(GDML_ERR_ARG, "gemm test sizes too large");
-  return oz_gemm_test(A_dev, B_dev, M, N, K, chunks_per_cta, C_dev, static_cast<cudaStream_t>(stream));
+  if (levels < 1 || levels > 7) return fail(GDML_ERR_ARG, "gemm test: levels outside 1..7");
+  return oz_gemm_test(A_dev, B_dev, M, N, K, chunks_per_cta, levels, C_dev, static_cast<cudaStream_t>(stream));
 }
 
 gdml_status gdml_test_oz_gemm_tall(const double* A_dev, int64_t n, int64_t K, const double* B_dev, int64_t NB,

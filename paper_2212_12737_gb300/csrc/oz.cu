@@ -21,7 +21,10 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kThreads = 352;  // warp 0 TMA (A), warp 1 MMA, warp 2 TMA (B), warps 3..10 epilogue
+// matvec GEMM: warp 0 TMA (A), warp 1 MMA, warp 2 TMA (B) and every wait, warps 3.. epilogue
+// (kEpiWarps: 4 per TMEM lane quarter, 16 of the tile's 64 columns each)
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 32 * (3 + kEpiWarps);
 constexpr int kAStages = 6;
 constexpr int kATile = oz::BM * 128;     // 16 KB: 128 rows x one 128-byte K span
 constexpr int kBTile = oz::BN * 128;     // 8 KB
@@ -33,19 +36,19 @@ constexpr int kKbPerChunk = oz::KC / oz::KB;
 constexpr int kWaiterWarp = 11;           // the accumulating GEMM's extra warp: mbarrier waits
 constexpr int kThreadsAcc = 32 * 12;
 constexpr int kStageLd = oz::BN + 1;  // padded row of the staged output tile (float2)
-// matvec GEMM: k-blocks of 128 (two 128-byte swizzle spans per tile), so each mbarrier
-// wait of the MMA thread covers 8 MMAs per slice pair; one B group, 3-deep A ring
-constexpr int kKB2 = 2 * oz::KB;                 // 128 K entries per k-block
-constexpr int kATile2 = 2 * kATile;              // 32 KB: two spans of 128 rows
-constexpr int kBTile2 = 2 * kBTile;              // 16 KB: two spans of 64 rows
-constexpr int kBGroup2 = oz::S * kBTile2;        // 112 KB
-constexpr int kAStages2 = 3;
-constexpr int kSmemData2 = kBGroup2 + kAStages2 * kATile2;  // 208 KB
-constexpr int kExpStage = oz::BM + oz::BN;         // a chunk's row and column exponents
-constexpr int kSmemTotal2 = kSmemData2 + 1024 + 256 + 2 * kExpStage * 4;
-constexpr int kKbPerChunk2 = oz::KC / kKB2;      // 2
-static_assert(oz::BM * kStageLd * 8 <= kSmemData2, "output staging fits the operand buffers");
-static_assert(kSmemTotal2 <= 227 * 1024, "shared memory per CTA");
+// matvec GEMM: k-blocks of 64 K entries (one 128-byte swizzle span per tile).  The B group of
+// a k-block (7 slices, 56 KB) is double-buffered; the A slices stream through a 6-deep ring.
+constexpr int kBGroupM = oz::S * kBTile;                               // 56 KB
+constexpr int kBStagesM = 2;
+constexpr int kAStagesM = 6;
+constexpr int kSmemDataM = kBStagesM * kBGroupM + kAStagesM * kATile;  // 208 KB
+constexpr int kExpStage = oz::BM + oz::BN;                             // a chunk's row and column exponents
+constexpr int kSmemTotalM = kSmemDataM + 1024 + 256 + 2 * kExpStage * 4;
+constexpr int kKbPerChunkM = oz::KC / oz::KB;                          // 4
+constexpr int kEpiCols = oz::BN * 4 / kEpiWarps;                       // 16 columns per epilogue warp
+static_assert(oz::BM * kStageLd * 8 <= kSmemDataM, "output staging fits the operand buffers");
+static_assert(kSmemTotalM <= 227 * 1024, "shared memory per CTA");
+static_assert(kEpiCols % 8 == 0, "epilogue columns in groups of 8");
 static_assert(oz::BM * kStageLd * 8 <= kSmemData, "output staging fits the operand buffers");
 static_assert(oz::S * oz::BN <= (int)kTmemCols, "one TMEM accumulator per level");
 static_assert(kSmemTotal <= 227 * 1024, "shared memory per CTA");
@@ -337,54 +340,63 @@ __device__ __forceinline__ bool handoff(bool failed) {
 }
 
 // grid (ceil(N/64), ceil(M/128), ceil(chunks / G)).  CTA z accumulates the G K-chunks
-// z G .. z G + G - 1, each 2 k-blocks of 128 K entries (two 128-byte swizzle spans per tile).
-// Warp 0 loads the 7 A slices of each k-block one by one into a 3-deep ring, warp 2 loads
-// the 7 B slices of each k-block as one group and waits on the TMA barriers; warp 1
-// multiplies A slice i with B slices j = 0..6-i (8 MMAs per pair) into TMEM accumulator
-// i + j, taking each A tile from warp 2 at a named barrier (a wait or any shared-memory
-// read in the MMA-issuing thread stalls the tensor pipe; wide k-blocks halve the handoffs
-// per MMA).  After each chunk warps 3..10 (two per TMEM lane quarter, 32 columns each)
-// drain the 7 level accumulators, scale the chunk by 2^(eA + eB), add it to running
-// double-float sums held in registers and release the TMEM (tfree) for the next chunk,
-// whose first MMA per level overwrites; after the last chunk they store the group's
-// double-float partial once.
+// z G .. z G + G - 1, each 4 k-blocks of 64 K entries.
+//  * Warp 0 loads the 7 A slice tiles of each k-block (16 KB each) into a 6-deep ring, in the
+//    order 6, 5, ..., 0.
+//  * Warp 2 loads the B group of each k-block (its 7 slices, 56 KB) into one of two buffers,
+//    the next k-block's group while the current one is multiplied, and does every mbarrier
+//    wait of the MMA side: it hands each A tile to warp 1 at named barrier 2 (a wait or any
+//    shared-memory read in the MMA-issuing thread stalls the tensor pipe).
+//  * Warp 1 multiplies A slice i with B slices j = 0..6-i (4 MMAs per pair) into TMEM
+//    accumulator i + j ("level"); the first k-block of a chunk overwrites level i with its
+//    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.
+//  * The epilogue warps drain a finished chunk level by level, 6 down to 0 (levels 6..4 summed
+//    in FP32, 3..0 added in double-float, then scaled by 2^(eA + eB) into running
+//    double-float sums held in registers), releasing each level as soon as it is read
+//    (tfree[L]).  A slice i of the next chunk needs levels i..6 only, so its MMAs start while
+//    the drain is still on the lower levels.  After the last chunk they store the group's
+//    double-float partial once.
+// nlev (1..7) keeps the levels below nlev only (slices 0..nlev-1, pairs i + j < nlev): a cheaper,
+// less accurate product for an inner solve; nlev = 7 is the full product.
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
                    int Bp, int M, int N, int num_kb, int chunks_per_cta, const int* __restrict__ eA,
                    const int* __restrict__ eB, float2* __restrict__ out, int64_t ldo, int64_t split_stride,
-                   int* __restrict__ err) {
+                   int* __restrict__ err, int nlev) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sB = smem;
-  uint8_t* sA = smem + kBGroup2;
-  uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + kSmemData2);
-  uint64_t* bempty = bfull + 1;
-  uint64_t* afull = bempty + 1;
-  uint64_t* aempty = afull + kAStages2;
-  uint64_t* cdone = aempty + kAStages2;  // the MMAs of a chunk have completed
-  uint64_t* tfree = cdone + 1;           // the epilogue has read a chunk's accumulators
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfree + 1);
+  uint8_t* sB = smem;                           // [2] B groups
+  uint8_t* sA = smem + kBStagesM * kBGroupM;    // [6] A tiles
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + kSmemDataM);  // [2]
+  uint64_t* bempty = bfull + kBStagesM;                               // [2]
+  uint64_t* afull = bempty + kBStagesM;                               // [6]
+  uint64_t* aempty = afull + kAStagesM;                               // [6]
+  uint64_t* cdone = aempty + kAStagesM;  // the MMAs of a chunk have completed
+  uint64_t* tfree = cdone + 1;           // [7] the epilogue has read level L of a chunk
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfree + oz::S);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  int* sexp = reinterpret_cast<int*>(smem + kSmemData2 + 256);  // [2][rows 128 | columns 64] exponents
+  int* sexp = reinterpret_cast<int*>(smem + kSmemDataM + 256);  // [2][rows 128 | columns 64] exponents
   float2* stage = reinterpret_cast<float2*>(smem);  // output tile, reuses the operand buffers after the MMAs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * oz::BN, m0 = blockIdx.y * oz::BM;
   const int q_begin = blockIdx.z * chunks_per_cta;
-  const int kb_begin = q_begin * kKbPerChunk2;
-  const int kb_end = min(num_kb, kb_begin + chunks_per_cta * kKbPerChunk2);
+  const int kb_begin = q_begin * kKbPerChunkM;
+  const int kb_end = min(num_kb, kb_begin + chunks_per_cta * kKbPerChunkM);
   const int nk = kb_end - kb_begin;
-  const int nq = (nk + kKbPerChunk2 - 1) / kKbPerChunk2;  // chunks of this CTA
+  const int nq = (nk + kKbPerChunkM - 1) / kKbPerChunkM;  // chunks of this CTA
 
   if (threadIdx.x == 0) {
-    tc::mbar_init(bfull, 1);
-    tc::mbar_init(bempty, 1);
-    for (int s = 0; s < kAStages2; ++s) {
+    for (int s = 0; s < kBStagesM; ++s) {
+      tc::mbar_init(&bfull[s], 1);
+      tc::mbar_init(&bempty[s], 1);
+    }
+    for (int s = 0; s < kAStagesM; ++s) {
       tc::mbar_init(&afull[s], 1);
       tc::mbar_init(&aempty[s], 1);
     }
     tc::mbar_init(cdone, 1);
-    tc::mbar_init(tfree, 8);  // one arrival per epilogue warp
+    for (int L = 0; L < oz::S; ++L) tc::mbar_init(&tfree[L], kEpiWarps);  // one arrival per epilogue warp
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -402,14 +414,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   bool mma_any = false, mma_failed = false;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer, A slices
+    // ---------------- TMA producer, A slices (order 6, 5, ..., 0 within each k-block)
+    int a_issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
-      const int kx = (kb_begin + kb) * kKB2;
+      const int kx = (kb_begin + kb) * oz::KB;
       bool ok = true;
-      for (int i = 0; i < oz::S; ++i) {
-        const int ai = kb * oz::S + i;
-        const int s = ai % kAStages2;
-        const uint32_t ph = (uint32_t)(ai / kAStages2) & 1u;
+      for (int pos = 0; pos < nlev; ++pos) {
+        const int ai = kb * nlev + pos;
+        const int s = ai % kAStagesM;
+        const uint32_t ph = (uint32_t)(ai / kAStagesM) & 1u;
         if (!mbar_wait_spin(&aempty[s], ph ^ 1u)) {
           atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
           *abort_flag = 1;
@@ -420,57 +433,75 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        tc::mbar_expect_tx(&afull[s], kATile2);
-        tc::tma_load_2d(sA + s * kATile2, &mapA, &afull[s], kx, i * Ap + m0);
-        tc::tma_load_2d(sA + s * kATile2 + kATile, &mapA, &afull[s], kx + oz::KB, i * Ap + m0);
+        tc::mbar_expect_tx(&afull[s], kATile);
+        tc::tma_load_2d(sA + s * kATile, &mapA, &afull[s], kx, (nlev - 1 - pos) * Ap + m0);
+        a_issued = ai + 1;
       }
       if (!ok) break;
     }
+    // no copy may outlive the CTA: after a failure nobody waits for the last tiles issued
+    // (earlier ones were consumed before their slot was refilled); bounded waits
+    for (int ai = max(0, a_issued - kAStagesM); ai < a_issued; ++ai)
+      (void)tc::mbar_wait_bounded(&afull[ai % kAStagesM], (uint32_t)(ai / kAStagesM) & 1u);
   } else if (warp == 2) {
-    // ---------------- B producer (lane 0) and waiter (whole warp): the MMA warp never touches
-    // shared memory in its loop (any shared-memory access of the MMA-issuing thread stalls
-    // the tensor pipe, ~35 cycles per MMA here); this warp waits on the TMA mbarriers (and,
-    // before the first A tile of each chunk after the first, on the epilogue's release of the
-    // accumulators) and hands each A tile over through named barrier 2, whose OR-reduction
-    // also carries a failed wait.  It arrives exactly nk * 7 times whatever happens.
+    // ---------------- B producer (lane 0) and waiter (whole warp).  The group of k-block kb + 1
+    // goes into the buffer of k-block kb - 1 once that one's MMAs have completed (checked after
+    // the second A hand-off of k-block kb, when they normally have).  Before the first k-block
+    // of chunk q > 0, A slice i also waits for the epilogue's release of level i of chunk q - 1.
+    // The warp arrives at named barrier 2 exactly nk * 7 times whatever happens, and a failed
+    // wait travels in the barrier's OR-reduction.
     bool failed = false;
-    for (int kb = 0; kb < nk; ++kb) {
-      int okw = 1;
-      if (lane == 0 && !failed) {
-        if (!mbar_wait_spin(bempty, ((uint32_t)kb & 1u) ^ 1u)) {
+    int b_issued = 0, b_waited = 0;  // lane 0: B groups issued / whose arrival was waited for
+    auto issue_b = [&](int kb) {  // lane 0; the buffer is known to be free
+      b_issued = kb + 1;
+      const int st2 = kb & 1;
+      const int kx = (kb_begin + kb) * oz::KB;
+      tc::mbar_expect_tx(&bfull[st2], nlev * kBTile);
+      for (int j = 0; j < nlev; ++j)
+        tc::tma_load_2d(sB + st2 * kBGroupM + j * kBTile, &mapB, &bfull[st2], kx, j * Bp + n0);
+    };
+    {
+      // the first wait comes before the first copy (a fresh buffer's previous phase counts
+      // as complete), so a wait that gives up at once leaves nothing in flight
+      int ok0 = 1;
+      if (lane == 0 && nk > 0) {
+        if (!mbar_wait_spin(&bempty[0], 1u)) {
           atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
           *abort_flag = 1;
-          okw = 0;
-        } else if (*abort_flag) {
+          ok0 = 0;
+        } else {
+          issue_b(0);
+          if (nk > 1) issue_b(1);
+        }
+      }
+      failed = !__shfl_sync(0xffffffffu, ok0, 0);
+    }
+    for (int kb = 0; kb < nk; ++kb) {
+      const int q = kb / kKbPerChunkM;
+      const bool chunk_start = kb % kKbPerChunkM == 0 && q > 0;
+      int okw = 1;
+      if (lane == 0 && !failed) {
+        if (!mbar_wait_spin(&bfull[kb & 1], (uint32_t)(kb >> 1) & 1u)) {
+          atomicExch(err, tc::ERR_TIMEOUT_FULL);
+          *abort_flag = 1;
           okw = 0;
         } else {
-          const int kx = (kb_begin + kb) * kKB2;
-          tc::mbar_expect_tx(bfull, kBGroup2);
-          for (int j = 0; j < oz::S; ++j) {
-            tc::tma_load_2d(sB + j * kBTile2, &mapB, bfull, kx, j * Bp + n0);
-            tc::tma_load_2d(sB + j * kBTile2 + kBTile, &mapB, bfull, kx + oz::KB, j * Bp + n0);
-          }
-          const int q = kb / kKbPerChunk2;
-          if (q > 0 && kb % kKbPerChunk2 == 0 && !mbar_wait_spin(tfree, (uint32_t)(q - 1) & 1u)) {
-            atomicExch(err, tc::ERR_TIMEOUT_DONE);
-            *abort_flag = 1;
-            okw = 0;
-          }
-          if (okw && !mbar_wait_spin(bfull, (uint32_t)kb & 1u)) {
-            atomicExch(err, tc::ERR_TIMEOUT_FULL);
-            *abort_flag = 1;
-            okw = 0;
-          }
+          b_waited = kb + 1;
+          if (*abort_flag) okw = 0;
         }
       }
       failed = failed || !__shfl_sync(0xffffffffu, okw, 0);
-      for (int i = 0; i < oz::S; ++i) {
-        const int ai = kb * oz::S + i;
-        const int s = ai % kAStages2;
-        const uint32_t ph = (uint32_t)(ai / kAStages2) & 1u;
+      for (int pos = 0; pos < nlev; ++pos) {
+        const int ai = kb * nlev + pos;
+        const int s = ai % kAStagesM;
+        const uint32_t ph = (uint32_t)(ai / kAStagesM) & 1u;
         int oka = 1;
         if (lane == 0 && !failed) {
-          if (!mbar_wait_spin(&afull[s], ph)) {
+          if (chunk_start && !mbar_wait_spin(&tfree[nlev - 1 - pos], (uint32_t)(q - 1) & 1u)) {
+            atomicExch(err, tc::ERR_TIMEOUT_DONE);
+            *abort_flag = 1;
+            oka = 0;
+          } else if (!mbar_wait_spin(&afull[s], ph)) {
             atomicExch(err, tc::ERR_TIMEOUT_FULL);
             *abort_flag = 1;
             oka = 0;
@@ -480,8 +511,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         failed = failed || !__shfl_sync(0xffffffffu, oka, 0);
         (void)handoff(failed);
+        if (pos == min(1, nlev - 1) && kb >= 1 && kb + 1 < nk) {
+          int okb = 1;
+          if (lane == 0 && !failed) {
+            if (!mbar_wait_spin(&bempty[(kb - 1) & 1], (uint32_t)((kb - 1) >> 1) & 1u)) {
+              atomicExch(err, tc::ERR_TIMEOUT_EMPTY);
+              *abort_flag = 1;
+              okb = 0;
+            } else if (*abort_flag) {
+              okb = 0;
+            } else {
+              issue_b(kb + 1);
+            }
+          }
+          failed = failed || !__shfl_sync(0xffffffffu, okb, 0);
+        }
       }
     }
+    // no copy may outlive the CTA: B groups issued but not waited for (after a failure)
+    if (lane == 0)
+      for (int kb = b_waited; kb < b_issued; ++kb)
+        (void)tc::mbar_wait_bounded(&bfull[kb & 1], (uint32_t)(kb >> 1) & 1u);
   } else if (warp == 1) {
     // ---------------- MMA issuer (lane 0; the whole warp meets the waiter at barrier 2)
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
@@ -489,32 +539,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
     bool& failed = mma_failed;
     for (int kb = 0; kb < nk; ++kb) {
-      for (int i = 0; i < oz::S; ++i) {
+      const bool chunk_first = kb % kKbPerChunkM == 0;
+      for (int pos = 0; pos < nlev; ++pos) {
+        const int i = nlev - 1 - pos;
         failed = handoff(false) || failed;
         tc::fence_after_sync();
-        const int ai = kb * oz::S + i;
-        const int s = ai % kAStages2;
+        const int ai = kb * nlev + pos;
+        const int s = ai % kAStagesM;
         if (lane == 0) {
           if (!failed) {
             // descriptors are linear in the start address (bits 0..13 = address / 16): a K
-            // step of 32 bytes adds 2, the second 128-byte span of a tile adds span / 16, and
-            // B slice j adds j * kBTile2 / 16
-            const uint64_t ad = adesc0 + (uint64_t)(s * (kATile2 >> 4));
-            const uint32_t first = (kb % kKbPerChunk2 != 0 || i > 0) ? 1u : 0u;  // new chunk: overwrite
+            // step of 32 bytes adds 2, B slice j of buffer b adds (b * group + j * tile) / 16
+            const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
+            const uint64_t bg = bdesc0 + (uint64_t)((kb & 1) * (kBGroupM >> 4));
 #pragma unroll
             for (int j = 0; j < oz::S; ++j) {
-              if (i + j < oz::S) {
+              if (i + j < nlev) {
                 const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
-                const uint64_t bj = bdesc0 + (uint64_t)(j * (kBTile2 >> 4));
-                constexpr uint64_t a1 = kATile >> 4, b1 = kBTile >> 4;
-                tc::mma_issue<true>(d, ad, bj, idesc, first);
+                const uint64_t bj = bg + (uint64_t)(j * (kBTile >> 4));
+                const uint32_t acc = (chunk_first && j == 0) ? 0u : 1u;  // level i's first MMA of the chunk
+                tc::mma_issue<true>(d, ad, bj, idesc, acc);
                 tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
                 tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
                 tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
-                tc::mma_issue<true>(d, ad + a1, bj + b1, idesc, 1u);
-                tc::mma_issue<true>(d, ad + a1 + 2, bj + b1 + 2, idesc, 1u);
-                tc::mma_issue<true>(d, ad + a1 + 4, bj + b1 + 4, idesc, 1u);
-                tc::mma_issue<true>(d, ad + a1 + 6, bj + b1 + 6, idesc, 1u);
               }
             }
             mma_any = true;
@@ -526,17 +573,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
       }
       if (lane == 0 && (mma_any || !failed)) {
-        tc::mma_commit(bempty);
-        if (kb % kKbPerChunk2 == kKbPerChunk2 - 1 || kb == nk - 1) tc::mma_commit(cdone);
+        tc::mma_commit(&bempty[kb & 1]);
+        if (kb % kKbPerChunkM == kKbPerChunkM - 1 || kb == nk - 1) tc::mma_commit(cdone);
       }
       __syncwarp();
     }
   } else if (warp >= 3) {
-    // ---------------- epilogue: per chunk, combine the levels, scale, add to running sums
+    // ---------------- epilogue: per chunk, level by level (6 .. 0), then scale and add
     const int quarter = warp & 3;
-    const int cbase = ((warp - 3) >> 2) * 32;  // this warp's 32 of the tile's 64 columns
-    const int row = m0 + quarter * 32 + lane;
-    const int et = threadIdx.x - 96;           // 0..255 over the epilogue warps
+    const int cbase = ((warp - 3) >> 2) * kEpiCols;  // this warp's columns of the tile's 64
+    const int et = threadIdx.x - 96;                 // 0 .. 32 kEpiWarps - 1
+    constexpr int kEpiThreads = 32 * kEpiWarps;
     // a chunk's 128 row and 64 column exponents into shared memory, one coalesced load each,
     // a chunk ahead of its drain (the drain then reads no global memory)
     auto load_exps = [&](int q) {
@@ -548,15 +595,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         dst[et] = n0 + et - oz::BM < N ? eB[zq * N + n0 + et - oz::BM] : 0;
     };
     if (nq > 0) load_exps(0);
-    float rh[32], rl[32];
+    float rh[kEpiCols], rl[kEpiCols], hh[kEpiCols], ll[kEpiCols];
 #pragma unroll
-    for (int t = 0; t < 32; ++t) rh[t] = rl[t] = 0.f;
+    for (int t = 0; t < kEpiCols; ++t) rh[t] = rl[t] = 0.f;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cbase;
+    auto release = [&](int L) {  // this warp has read level L of the chunk
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&tfree[L])) : "memory");
+    };
     bool go = true;
     // every epilogue warp passes named barrier 1 exactly nq + 1 times, whatever fails: after a
     // failed wait a warp keeps looping without waiting or reading the accumulators
     for (int q = 0; q < nq; ++q) {
       // chunk q's exponents are visible, and chunk q - 1's buffer may be refilled
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
       if (q + 1 < nq) load_exps(q + 1);
       if (!go) continue;
       int okw = 1;
@@ -574,49 +628,52 @@ __global__ void __launch_bounds__(kThreads, 1)
         continue;
       }
       tc::fence_after_sync();
+      // levels 6..4 are scaled by 2^-56..2^-42 against the leading level's 2^-14, so a plain
+      // FP32 sum of them errs by < 2^-48 of the leading level's range; levels 3..0 are added
+      // in double-float
+#pragma unroll
+      for (int t = 0; t < kEpiCols; ++t) ll[t] = 0.f;
+#pragma unroll
+      for (int L = oz::S - 1; L >= 0; --L) {
+        if (L >= nlev) continue;
+        const float sc = pow2f(-oz::BITS * (L + 2));
+#pragma unroll
+        for (int c8 = 0; c8 < kEpiCols; c8 += 8) {
+          uint32_t v[8];
+          tmem_ld8_nowait(lane_base + (uint32_t)(L * oz::BN + c8), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const float x = __fmul_rn(__uint_as_float(v[t]), sc);
+            if (L == nlev - 1) {
+              hh[c8 + t] = x;
+            } else if (L >= 4) {
+              hh[c8 + t] = __fadd_rn(hh[c8 + t], x);
+            } else {
+              df_add_f(hh[c8 + t], ll[c8 + t], x);
+            }
+          }
+        }
+        release(L);
+      }
       const int* ex = sexp + (q & 1) * kExpStage;
       const int ea = ex[quarter * 32 + lane];
 #pragma unroll
-      for (int c8 = 0; c8 < 32; c8 += 8) {
-        uint32_t v[oz::S][8];
-#pragma unroll
-        for (int L = 0; L < oz::S; ++L)
-          tmem_ld8_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * oz::BN + cbase + c8), v[L]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          // levels 4..6 are scaled by 2^-42..2^-56 against the leading level's 2^-14, so a
-          // plain FP32 sum of them errs by < 2^-48 of the leading level's range; levels
-          // 3..0 are added in double-float
-          const float f4 = __uint_as_float(v[4][t]), f5 = __uint_as_float(v[5][t]), f6 = __uint_as_float(v[6][t]);
-          float tail = __fmul_rn(f6, pow2f(-oz::BITS * 8));
-          tail = __fadd_rn(tail, __fmul_rn(f5, pow2f(-oz::BITS * 7)));
-          tail = __fadd_rn(tail, __fmul_rn(f4, pow2f(-oz::BITS * 6)));
-          float hh = tail, ll = 0.f;
-          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[3][t]), pow2f(-oz::BITS * 5)));
-          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[2][t]), pow2f(-oz::BITS * 4)));
-          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[1][t]), pow2f(-oz::BITS * 3)));
-          df_add_f(hh, ll, __fmul_rn(__uint_as_float(v[0][t]), pow2f(-oz::BITS * 2)));
-          const int e2 = ea + ex[oz::BM + cbase + c8 + t];
-          df_add(rh[c8 + t], rl[c8 + t], scale2(hh, e2), scale2(ll, e2));
-        }
+      for (int t = 0; t < kEpiCols; ++t) {
+        const int e2 = ea + ex[oz::BM + cbase + t];
+        df_add(rh[t], rl[t], scale2(hh[t], e2), scale2(ll[t], e2));
       }
-      // this warp has read chunk q: release the accumulators
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
     }
     // stage the group's tile in the (now idle) operand buffers, then a coalesced write-out;
-    // the 8 epilogue warps sync among themselves (barrier 1)
+    // the epilogue warps sync among themselves (barrier 1)
     if (go) {
       float2* srow = stage + (quarter * 32 + lane) * kStageLd;
 #pragma unroll
-      for (int t = 0; t < 32; ++t) srow[cbase + t] = make_float2(rh[t], rl[t]);
+      for (int t = 0; t < kEpiCols; ++t) srow[cbase + t] = make_float2(rh[t], rl[t]);
     }
-    asm volatile("bar.sync 1, 256;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
     if (go) {
-      const int et = threadIdx.x - 96;
-      for (int idx = et; idx < oz::BM * oz::BN; idx += 256) {
+      for (int idx = et; idx < oz::BM * oz::BN; idx += kEpiThreads) {
         const int rr = idx / oz::BN, cc = idx % oz::BN;
         const int grow = m0 + rr, gcol = n0 + cc;
         if (grow < M && gcol < N) out[blockIdx.z * split_stride + (int64_t)grow * ldo + gcol] = stage[rr * kStageLd + cc];
@@ -1187,19 +1244,20 @@ int oz_auto_chunks_per_cta(int64_t tiles, int64_t nchunks) {
 // C partials (groups of G chunks, one float2 slab per group at out + z split_stride) of
 // A B^T; *groups_out = number of slabs written
 static gdml_status oz_gemm(const OzOperand& A, const OzOperand& B, float2* out, int64_t ldo, int64_t split_stride,
-                           int* err, cudaStream_t st, int G, int* groups_out = nullptr) {
+                           int* err, cudaStream_t st, int G, int* groups_out = nullptr, int nlev = oz::S) {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal2) != cudaSuccess)
+    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotalM) != cudaSuccess)
       return fail(GDML_ERR_CUDA, "cudaFuncSetAttribute(sliced gemm)");
     attr_set = true;
   }
   if (A.Kp != B.Kp) return fail(GDML_ERR_ARG, "sliced gemm: K mismatch");
-  if (A.Kp % kKB2 != 0) return fail(GDML_ERR_ARG, "sliced gemm: K padding");
+  if (A.Kp % oz::KB != 0) return fail(GDML_ERR_ARG, "sliced gemm: K padding");
+  if (nlev < 1 || nlev > oz::S) return fail(GDML_ERR_ARG, "sliced gemm: levels outside 1..7");
   G = std::max(1, std::min<int>(G, (int)A.nchunks));
   const int groups = (int)cdiv(A.nchunks, G);
   dim3 grid((unsigned)cdiv(B.rows, oz::BN), (unsigned)cdiv(A.rows, oz::BM), (unsigned)groups);
-  { oz_gemm_kernel<<<grid, kThreads, kSmemTotal2, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / kKB2), G, A.e, B.e, out, ldo, split_stride, err); count_launch(); }
+  { oz_gemm_kernel<<<grid, kThreads, kSmemTotalM, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / oz::KB), G, A.e, B.e, out, ldo, split_stride, err, nlev); count_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("sliced gemm launch: ") + cudaGetErrorString(e));
   if (groups_out) *groups_out = groups;
@@ -1248,7 +1306,7 @@ gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, co
 }
 
 gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
-                      int add_lambda, double lam, cudaStream_t st) {
+                      int add_lambda, double lam, cudaStream_t st, int lev) {
   if (!oz.ready) return fail(GDML_ERR_STATE, "sliced matvec not set up");
   const int64_t M = oz.M, MB = oz.MB;
   const int D = oz.D;
@@ -1267,14 +1325,14 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
   transpose(WB, MB, D, D, oz.WT, st);
   slice_rows(oz.WT, MB, oz.WT2, st);
   int groups1 = 0, groups2 = 0;
-  OZ_TRY(oz_gemm(oz.Xc1, oz.W1, oz.Tp, MB, M * MB, oz.err, st, oz.g1, &groups1));
+  OZ_TRY(oz_gemm(oz.Xc1, oz.W1, oz.Tp, MB, M * MB, oz.err, st, oz.g1, &groups1, lev));
   {
     dim3 g((unsigned)M, (unsigned)cdiv(oz.B2.Kp, 1024));
     { oz_beta_kernel<<<g, 256, 0, st>>>(oz.Tp, groups1, M, MB, oz.S2, oz.t2, oz.B2.Rp, oz.B2.Kp, (bf16*)oz.B2.slices, oz.B2.e, oz.rs2); count_launch(); }
   }
   const int64_t nch = oz.A2.nchunks;
-  OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st, oz.g2, &groups2));
-  OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + (int64_t)groups2 * M * D, D, M * D, oz.err, st, oz.g2));
+  OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st, oz.g2, &groups2, lev));
+  OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + (int64_t)groups2 * M * D, D, M * D, oz.err, st, oz.g2, nullptr, lev));
   const size_t smem = 3 * (size_t)D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1419,8 +1477,8 @@ gdml_status oz_gemm_tall(const double* A, int64_t n, int64_t K, const double* B,
 cudaError_t set_wait_limit_oz(uint32_t polls) { return tc::set_wait_limit_here(polls); }
 uint32_t tc_default_wait_limit() { return tc::kSpinLimit; }
 
-gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, int G, double* C,
-                         cudaStream_t st) {
+gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, int G, int nlev,
+                         double* C, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return fail(GDML_ERR_ARG, "oz_gemm_test: empty sizes");
   OzMatvec t;
   OzOperand a, b;
@@ -1434,7 +1492,7 @@ gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N,
     slice_rows(A, K, a, st);
     slice_rows(B, K, b, st);
     if (G < 1) G = oz_auto_chunks_per_cta(cdiv(N, oz::BN) * cdiv(M, oz::BM), a.nchunks);
-    s = oz_gemm(a, b, part, N, M * N, t.err, st, G, &groups);
+    s = oz_gemm(a, b, part, N, M * N, t.err, st, G, &groups, nlev);
   }
   if (s == GDML_OK) {
     { oz_sum_partials_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(part, groups, M * N, C); count_launch(); }

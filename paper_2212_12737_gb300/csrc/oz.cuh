@@ -83,9 +83,11 @@ struct OzMatvec {
 gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, const double* A, int64_t ldA,
                      const double* S, double c, cudaStream_t st, int Ssym = 1, const int* pis = nullptr,
                      const double* XcB = nullptr);
-// out = K v (+ lambda v); G, Xc: the context's FP64 Jacobian factors and centred descriptors
+// out = K v (+ lambda v); G, Xc: the context's FP64 Jacobian factors and centred descriptors.
+// lev < 7 keeps only the slice pairs i + j < lev in both contractions (a cheaper, less accurate
+// matvec for an inner solve)
 gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
-                      int add_lambda, double lam, cudaStream_t st);
+                      int add_lambda, double lam, cudaStream_t st, int lev = oz::S);
 gdml_status oz_check(OzMatvec& oz, cudaStream_t st);
 void oz_destroy(OzMatvec& oz);
 
@@ -108,9 +110,9 @@ gdml_status oz_gemm_tall(const double* A, int64_t n, int64_t K, const double* B,
                          bool rowsq, double* out, float* out32, cudaStream_t st);
 
 // test hook: C (M x N, FP64) = A (M x K) B (N x K)^T through the sliced tensor-core GEMM with G
-// K-chunks per CTA (G < 1: the automatic choice)
-gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, int G, double* C,
-                         cudaStream_t st);
+// K-chunks per CTA (G < 1: the automatic choice), keeping the slice pairs i + j < nlev
+gdml_status oz_gemm_test(const double* A, const double* B, int64_t M, int64_t N, int64_t K, int G, int nlev,
+                         double* C, cudaStream_t st);
 // K chunks per CTA that keep about 8 waves of CTAs for `tiles` output tiles
 int oz_auto_chunks_per_cta(int64_t tiles, int64_t nchunks);
 

@@ -31,7 +31,7 @@ EXPORTS = ["gdml_kernel_setup", "gdml_kernel_setup_sym", "gdml_matvec", "gdml_ma
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
            "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy", "gdml_rule_of_thumb_k",
-           "gdml_predict_forces", "gdml_pcg_spectrum"]
+           "gdml_predict_forces", "gdml_pcg_spectrum", "gdml_set_inner_levels"]
 
 # Table 1 (Sec. 4.3): molecule -> (m, k_min) of the rule of thumb, fitted at n = 31k;
 # "default" is the row for molecules without fitted parameters.
@@ -70,11 +70,12 @@ def load() -> ctypes.CDLL:
         "gdml_precond_apply": [P, P, P],
         "gdml_pcg_solve": [P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D)],
         "gdml_set_inner_rtol": [P, D],
+        "gdml_set_inner_levels": [P, I32],
         "gdml_last_outer_steps": [P, ctypes.POINTER(I32)],
         "gdml_last_error": [P],
         "gdml_destroy": [P],
         "gdml_test_tc_gemm": [I32, P, P, I32, I32, I32, P, P],
-        "gdml_test_oz_gemm": [P, P, I64, I64, I64, I32, P, P],
+        "gdml_test_oz_gemm": [P, P, I64, I64, I64, I32, I32, P, P],
         "gdml_test_df_passes": [P, I64, I64, P, P, D, I32, P, P, P],
         "gdml_test_oz_gemm_tall": [P, I64, I64, P, I64, I64, I32, I32, P, P, P],
         "gdml_test_precond_factor": [P, P],
@@ -260,6 +261,10 @@ class Context:
         """Replace lambda (test hook; lam <= 0 makes K + lam I indefinite); drops the preconditioner."""
         self._check(load().gdml_test_set_lambda(self._h, float(lam)))
 
+    def set_inner_levels(self, levels: int):
+        """OZAKI contexts: slice levels (1..7) of the matvec inside the PCG loop."""
+        self._check(load().gdml_set_inner_levels(self._h, int(levels)))
+
     def set_inner_rtol(self, v: float):
         self._check(load().gdml_set_inner_rtol(self._h, float(v)))
 
@@ -369,16 +374,17 @@ def test_tc_gemm(A: torch.Tensor, B: torch.Tensor, bf16: bool = False) -> torch.
     return C
 
 
-def test_oz_gemm(A: torch.Tensor, B: torch.Tensor, chunks_per_cta: int = 0) -> torch.Tensor:
+def test_oz_gemm(A: torch.Tensor, B: torch.Tensor, chunks_per_cta: int = 0, levels: int = 7) -> torch.Tensor:
     """C = A B^T through the sliced-BF16 tensor-core GEMM (FP64-class accuracy); chunks_per_cta
-    256-entry K chunks accumulated per CTA (0: automatic)."""
+    256-entry K chunks accumulated per CTA (0: automatic); levels < 7 keeps the slice pairs
+    i + j < levels only."""
     lib = load()
     A = A.contiguous()
     B = B.contiguous()
     M, K = A.shape
     N = B.shape[0]
     C = torch.empty(M, N, dtype=torch.float64, device=A.device)
-    st = lib.gdml_test_oz_gemm(_ptr(A), _ptr(B), M, N, K, int(chunks_per_cta), _ptr(C),
+    st = lib.gdml_test_oz_gemm(_ptr(A), _ptr(B), M, N, K, int(chunks_per_cta), int(levels), _ptr(C),
                                ctypes.c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
     if st != 0:
         raise GdmlError(st, lib.gdml_last_error(None).decode())
