@@ -201,8 +201,9 @@ def run_op(args):
 
 def run_suite(args):
     """Many uneven systems (N in {9,12,15,21,42}, M in [100, mmax], sigma in
-    {5,10,20,40}, lambda in {1e-10,1e-8}, uniform k = M/10): per-system FP64
-    solves one after another vs one batched graph solve, after autotuning."""
+    {5,10,20,40}, lambda in {1e-10,1e-8}, uniform k = M/10): per-system FP64 solves
+    one after another (the reference launches) against the mixed-precision OZAKI form,
+    per system and as one batched graph solve, each context autotuned first."""
     import torch
 
     from paper_2212_12737_gb300 import gdml, synth
@@ -211,49 +212,48 @@ def run_suite(args):
     dev = torch.device("cuda", 0)
     suite = synth.batched_suite(args.suite_count, mmax=args.suite_mmax)
     cache = os.path.join(ROOT, "paper_2212_12737_gb300", "lib", "tuning.json")
-    ctxs, ys = [], []
-    t0 = time.perf_counter()
-    for w in suite:
-        c = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam)
-        c.autotune(cache)
-        c.precond_build("uniform", w.k, seed=2)
-        ctxs.append(c)
-        ys.append(torch.from_numpy(w.y).to(dev))
-    torch.cuda.synchronize(dev)
-    t_setup = time.perf_counter() - t0
-    # warm both paths once (graph capture, instantiation)
-    def seq():
-        out = []
+    ys = [torch.from_numpy(w.y).to(dev) for w in suite]
+    res = {"suite": "batched", "systems": len(suite), "total_unknowns": sum(w.n for w in suite),
+           "mmax": args.suite_mmax, "max_iter": args.suite_maxiter}
+    for prec in ("fp64", "ozaki"):
+        ctxs = []
+        t0 = time.perf_counter()
+        for w in suite:
+            c = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam, precision=prec)
+            c.autotune(cache)
+            c.precond_build("uniform", w.k, seed=2)
+            ctxs.append(c)
+        torch.cuda.synchronize(dev)
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        seq = []
         for c, y in zip(ctxs, ys):
             _, it, rel, _ = c.pcg_solve(y, rtol=RTOL, max_iter=args.suite_maxiter, raise_on_nonconvergence=False)
-            out.append((it, rel))
-        return out
-    t0 = time.perf_counter()
-    res_seq = seq()
-    torch.cuda.synchronize(dev)
-    t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    _, its, rels = gdml.pcg_solve_batched(ctxs, ys, rtol=RTOL, max_iter=args.suite_maxiter,
-                                          raise_on_nonconvergence=False)
-    torch.cuda.synchronize(dev)
-    t_bat = time.perf_counter() - t0
-    n_tot = sum(w.n for w in suite)
-    print(json.dumps({
-        "suite": "batched", "systems": len(suite), "total_unknowns": n_tot, "mmax": args.suite_mmax,
-        "max_iter": args.suite_maxiter,
-        "setup_and_build_s": t_setup, "per_system_solves_s": t_seq, "batched_graph_solve_s": t_bat,
-        "speedup": t_seq / t_bat, "iters_total": int(sum(its)),
-        "converged": int(sum(r <= RTOL for r in rels)), "max_relres": max(rels),
-        "same_iterations_as_per_system": all(a == b[0] for a, b in zip(its, res_seq))}), flush=True)
-    for c in ctxs:
-        c.destroy()
+            seq.append((it, rel))
+        torch.cuda.synchronize(dev)
+        t_seq = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, its, rels = gdml.pcg_solve_batched(ctxs, ys, rtol=RTOL, max_iter=args.suite_maxiter,
+                                              raise_on_nonconvergence=False)
+        torch.cuda.synchronize(dev)
+        t_bat = time.perf_counter() - t0
+        res[prec] = {"setup_autotune_build_s": t_setup, "per_system_solves_s": t_seq, "batched_graph_solve_s": t_bat,
+                     "iters_total": int(sum(its)), "converged": int(sum(r <= RTOL for r in rels)),
+                     "max_relres": max(rels),
+                     "batched_same_iterations_as_per_system": all(a == b[0] for a, b in zip(its, seq))}
+        for c in ctxs:
+            c.destroy()
+    res["mixed_batched_vs_fp64_per_system_speedup"] = (res["fp64"]["per_system_solves_s"]
+                                                        / res["ozaki"]["batched_graph_solve_s"])
+    print(json.dumps(res), flush=True)
 
 
 def run_learned(args):
-    """Learned inducing-column scorer: train on per-geometry ridge-leverage
-    labels of --suite-count training systems of the same molecule (other noise
-    seeds), select k columns for the headline system, and compare PCG
-    iterations / solve time with pivoted Cholesky (the fallback and referee)."""
+    """Learned inducing-column scorer: train on EXACT per-geometry ridge-leverage
+    labels of training systems of the same molecule (other noise seeds) at reduced M
+    (M = 100: exact scores need a dense eigendecomposition of K), select k columns for
+    the headline system, and compare PCG iterations / solve time with pivoted Cholesky
+    (the fallback and referee)."""
     import torch
 
     from paper_2212_12737_gb300 import gdml, synth
@@ -264,13 +264,15 @@ def run_learned(args):
     k = base["k"]
     t0 = time.perf_counter()
     Xs, ys = [], []
-    for s in range(args.suite_count):
+    m_train = 100
+    n_train = min(args.suite_count, 20)
+    for s in range(n_train):
         cfg = dict(base)
-        w = synth.make_workload(f"train{s}", cfg["N"], cfg["M"], cfg["noise"], cfg["sigma"], cfg["lam"], k,
-                                "uniform", template_seed=0, noise_seed=100 + s)
+        w = synth.make_workload(f"train{s}", cfg["N"], m_train, cfg["noise"], cfg["sigma"], cfg["lam"],
+                                min(k, 3 * cfg["N"] * m_train), "uniform", template_seed=0, noise_seed=100 + s)
         c = gdml.kernel_setup(torch.from_numpy(w.R).to(dev), w.sigma, w.lam)
         Xs.append(c.descriptors())
-        ys.append(gdml.geometry_labels(c, k))
+        ys.append(gdml.geometry_labels(c, exact=True))
         c.destroy()
     torch.cuda.synchronize(dev)
     t_labels = time.perf_counter() - t0
@@ -317,7 +319,8 @@ def run_learned(args):
     c.precond_build("uniform", k, seed=2)
     _, it_u, rel_u, _ = c.pcg_solve(yv, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
     c.destroy()
-    print(json.dumps({"suite": "learned", "workload": args.workload, "k": k, "train_systems": args.suite_count,
+    print(json.dumps({"suite": "learned", "workload": args.workload, "k": k, "train_systems": n_train,
+                      "train_geometries_per_system": m_train, "labels": "exact ridge leverage scores",
                       "label_s": t_labels, "train_s": t_train, "train_loss": loss,
                       "pivchol": {"s": t_pc, "iters": it_pc, "relres": rel_pc},
                       "learned": {"s": t_l, "iters": it_l, "relres": rel_l, "used": used,
@@ -401,7 +404,12 @@ def max_over_ranks(t: float, world: int, device) -> float:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the roofline's unit,
 # from one ncu capture each (profiles/), keyed by (workload, precision, unit).  A unit whose
 # kernels changed since the capture has no entry (traffic null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/woodbury_apply_dram_aspirin21_m1000_k2000_ozaki.md (cold-cache capture of one apply)
+    ("aspirin21_m1000", "ozaki", "apply"): 1.1116e9,
+    # the same capture scaled to n = 630,000, k = 5000: passes by n k, k x k core by k^2
+    ("mol42_m5000", "ozaki", "apply"): 2.587e10,
+}
 
 
 def run_gpu(args):
@@ -647,7 +655,7 @@ def run_gpu(args):
 # (its JSON line's solve.iters).  The FP64 oracle cannot run these solves to the end within a
 # benchmark's time, so the reference arm extrapolates its sampled per-iteration cost with
 # these counts; the GPU arm's own CPU baseline uses the iteration count of its run instead.
-REF_ITERS = {"ethanol9_m200": 595, "aspirin21_m1000": 1578, "mol42_m5000": 3266}
+REF_ITERS = {"ethanol9_m200": 595, "aspirin21_m1000": 1578, "mol42_m5000": 3254}
 
 
 def blas_info() -> dict:

@@ -196,6 +196,20 @@ gdml_status gdml_precond_build_scored(gdml_ctx* ctx, const double* geometry_scor
  * GDML_ERR_NOT_SPD, GDML_ERR_CUDA. */
 gdml_status gdml_rls_scores(gdml_ctx* ctx, int64_t k, uint64_t seed, double* tau_dev);
 
+/* Per-geometry ridge-leverage mass, the training label of the learned scorer:
+ * labels[a] = sum over the 3N columns i of geometry a of tau_i (summed in index order).
+ *  exact != 0: the exact scores tau_i = (K (K + lambda I)^-1)_ii = sum_j U_ij^2 s_j / (s_j + lambda)
+ *    from the eigendecomposition K = U diag(s) U^T (dense K from the kernel columns, cuSOLVER
+ *    syevd; negative rounding of s clamped to 0; n <= 24576, ~24 n^2 bytes of temporary device
+ *    memory).  At lambda far below the rounding of K's small eigenvalues (~n eps |K|) the scores
+ *    of those eigen-directions are as uncertain as the eigenvalues themselves.  k, seed unused.
+ *  exact == 0: the Nystrom estimate of gdml_rls_scores (pilot k, seed), which invalidates any
+ *    built preconditioner.
+ * labels_dev: M doubles.  Synchronises the stream.
+ * Errors: GDML_ERR_ARG (NULL labels_dev, n too large for exact, k outside [1, min(n, 16384)]),
+ * GDML_ERR_OOM, GDML_ERR_NOT_SPD, GDML_ERR_CUDA. */
+gdml_status gdml_rls_labels(gdml_ctx* ctx, int32_t exact, int64_t k, uint64_t seed, double* labels_dev);
+
 /* The inverse-distance descriptors x_a (M x D doubles, row a = geometry a).
  * Errors: GDML_ERR_ARG (NULL context or X_dev), GDML_ERR_CUDA. */
 gdml_status gdml_descriptors(const gdml_ctx* ctx, double* X_dev);

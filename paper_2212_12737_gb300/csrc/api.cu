@@ -877,6 +877,20 @@ gdml_status gdml_predict_forces(gdml_ctx* c, const double* R_query, int64_t Q, c
   return check_launch(c, "predict_forces");
 }
 
+// Dense K (column-major n x n, from the kernel columns in blocks of 4096) and its ascending
+// eigendecomposition in place: Kd holds the eigenvectors, w the eigenvalues (n <= kSvdMaxN)
+static gdml_status dense_eigh(gdml_ctx* c, double* Kd, double* w, int64_t* cols) {
+  const int64_t n = c->n;
+  std::vector<int64_t> hcols(n);
+  for (int64_t i = 0; i < n; ++i) hcols[i] = i;
+  CTRY(c, cudaMemcpyAsync(cols, hcols.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+  constexpr int64_t kBlock = 4096;
+  for (int64_t j0 = 0; j0 < n; j0 += kBlock) TRY(get_cols(c, cols + j0, std::min(kBlock, n - j0), Kd + j0 * n));
+  const std::string e = eigh_dense(Kd, n, w, c->st);
+  if (!e.empty()) return ctx_fail(c, GDML_ERR_CUDA, "dense eigendecomposition of K: " + e);
+  return GDML_OK;
+}
+
 static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, uint64_t seed, int64_t* pivots_dev,
                                       double* resid_trace_dev, const double* geometry_scores) {
   TRY(validate(c));
@@ -975,13 +989,7 @@ static gdml_status precond_build_impl(gdml_ctx* c, int32_t method, int64_t k, ui
     TRY(s.get(&Kd, (size_t)(n * n)));
     TRY(s.get(&w, (size_t)n));
     TRY(s.get(&cols, (size_t)n));
-    std::vector<int64_t> hcols(n);
-    for (int64_t i = 0; i < n; ++i) hcols[i] = i;
-    CTRY(c, cudaMemcpyAsync(cols, hcols.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
-    constexpr int64_t kBlock = 4096;
-    for (int64_t j0 = 0; j0 < n; j0 += kBlock) TRY(get_cols(c, cols + j0, std::min(kBlock, n - j0), Kd + j0 * n));
-    const std::string e = eigh_dense(Kd, n, w, c->st);
-    if (!e.empty()) return ctx_fail(c, GDML_ERR_CUDA, "SVD preconditioner: " + e);
+    TRY(dense_eigh(c, Kd, w, cols));
     launch_svd_factor(Kd, w, n, k, c->L, c->st);
     TRY(check_launch(c, "SVD factor"));
     std::vector<double> hw(n), htr(k);
@@ -1062,6 +1070,33 @@ gdml_status gdml_rls_scores(gdml_ctx* c, int64_t k, uint64_t seed, double* tau_d
   TRY(s.get(&Kkk, (size_t)(k * k)));
   TRY(s.get(&work, (size_t)(k * k)));
   TRY(rls_estimate(c, k, seed, S, Kkk, work, key, idx, tau_dev));
+  CTRY(c, cudaStreamSynchronize(c->st));
+  return GDML_OK;
+}
+
+gdml_status gdml_rls_labels(gdml_ctx* c, int32_t exact, int64_t k, uint64_t seed, double* labels_dev) {
+  TRY(validate(c));
+  const int64_t n = c->n;
+  if (!labels_dev) return ctx_fail(c, GDML_ERR_ARG, "labels_dev is NULL");
+  Scratch s{c, {}};
+  double* tau = nullptr;
+  TRY(s.get(&tau, (size_t)n));
+  if (exact) {
+    if (n > kSvdMaxN)
+      return ctx_fail(c, GDML_ERR_ARG, "exact leverage scores need n <= " + std::to_string(kSvdMaxN) +
+                                           " (a dense eigendecomposition of K)");
+    double *Kd = nullptr, *w = nullptr;
+    int64_t* cols = nullptr;
+    TRY(s.get(&Kd, (size_t)(n * n)));
+    TRY(s.get(&w, (size_t)n));
+    TRY(s.get(&cols, (size_t)n));
+    TRY(dense_eigh(c, Kd, w, cols));
+    launch_rls_from_eigen(Kd, w, n, c->lam, tau, c->st);
+  } else {
+    TRY(gdml_rls_scores(c, k, seed, tau));
+  }
+  launch_group_sums(tau, c->M, c->B, labels_dev, c->st);
+  TRY(check_launch(c, "rls labels"));
   CTRY(c, cudaStreamSynchronize(c->st));
   return GDML_OK;
 }

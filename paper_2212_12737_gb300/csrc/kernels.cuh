@@ -151,6 +151,11 @@ void launch_svd_factor(const double* U, const double* w, int64_t n, int64_t k, d
 // eigenvectors overwrite A, ascending eigenvalues in w).  Returns an empty string on success,
 // else what failed.
 std::string eigh_dense(double* A, int64_t n, double* w, cudaStream_t st);
+// exact ridge leverage scores tau_i = sum_j U_ij^2 w_j^+ / (w_j^+ + lam) from an ascending
+// eigendecomposition (U column-major n x n)
+void launch_rls_from_eigen(const double* U, const double* w, int64_t n, double lam, double* tau, cudaStream_t st);
+// out[a] = sum of the per consecutive entries of group a (index order)
+void launch_group_sums(const double* in, int64_t groups, int per, double* out, cudaStream_t st);
 // Ritz values of the Lanczos matrix T_m of m CG steps (gamma_j, beta_j; see gdml_pcg_spectrum):
 // its smallest and largest eigenvalue and its `count` largest in descending order
 void lanczos_ritz(const double* gamma, const double* beta, int64_t m, int64_t count, double* top, double* tmin,

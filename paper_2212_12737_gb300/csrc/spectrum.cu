@@ -165,3 +165,43 @@ void lanczos_ritz(const double* gamma, const double* beta, int64_t m, int64_t co
 }
 
 }  // namespace gdml
+
+namespace gdml {
+
+namespace {
+
+// tau_i = sum_j U_ij^2 max(w_j, 0) / (max(w_j, 0) + lam): the exact ridge leverage scores
+// diag(K (K + lam I)^-1) from K = U diag(w) U^T (U column-major, thread i walks row i)
+__global__ void rls_from_eigen_kernel(const double* __restrict__ U, const double* __restrict__ w, int64_t n, double lam,
+                                      double* __restrict__ tau) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    const double wj = fmax(w[j], 0.0);
+    const double u = U[j * n + i];
+    s = fma(u * u, wj / (wj + lam), s);
+  }
+  tau[i] = s;
+}
+
+// out[a] = sum of in[a * per .. a * per + per - 1], in index order (one thread per group)
+__global__ void group_sums_kernel(const double* __restrict__ in, int64_t groups, int per, double* __restrict__ out) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= groups) return;
+  double s = 0.0;
+  for (int c = 0; c < per; ++c) s += in[a * per + c];
+  out[a] = s;
+}
+
+}  // namespace
+
+void launch_rls_from_eigen(const double* U, const double* w, int64_t n, double lam, double* tau, cudaStream_t st) {
+  { rls_from_eigen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, w, n, lam, tau); count_launch(); }
+}
+
+void launch_group_sums(const double* in, int64_t groups, int per, double* out, cudaStream_t st) {
+  { group_sums_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(in, groups, per, out); count_launch(); }
+}
+
+}  // namespace gdml

@@ -31,7 +31,7 @@ EXPORTS = ["gdml_kernel_setup", "gdml_kernel_setup_sym", "gdml_matvec", "gdml_ma
            "gdml_set_tuning", "gdml_precond_build_scored", "gdml_rls_scores", "gdml_descriptors",
            "gdml_scorer_create", "gdml_scorer_fit_scaling", "gdml_scorer_train", "gdml_scorer_predict",
            "gdml_scorer_params", "gdml_scorer_grad", "gdml_scorer_destroy", "gdml_rule_of_thumb_k",
-           "gdml_predict_forces", "gdml_pcg_spectrum", "gdml_set_inner_levels"]
+           "gdml_predict_forces", "gdml_pcg_spectrum", "gdml_set_inner_levels", "gdml_rls_labels"]
 
 # Table 1 (Sec. 4.3): molecule -> (m, k_min) of the rule of thumb, fitted at n = 31k;
 # "default" is the row for molecules without fitted parameters.
@@ -71,6 +71,7 @@ def load() -> ctypes.CDLL:
         "gdml_pcg_solve": [P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D)],
         "gdml_set_inner_rtol": [P, D],
         "gdml_set_inner_levels": [P, I32],
+        "gdml_rls_labels": [P, I32, I64, U64, P],
         "gdml_last_outer_steps": [P, ctypes.POINTER(I32)],
         "gdml_last_error": [P],
         "gdml_destroy": [P],
@@ -568,11 +569,13 @@ class Scorer:
             pass
 
 
-def geometry_labels(ctx: Context, k: int, seed: int = 2) -> torch.Tensor:
-    """Per-geometry ridge-leverage mass: the sum of the estimated scores of the
-    geometry's 3N columns (the training label of the learned scorer)."""
-    tau = ctx.rls_scores(k, seed)
-    return tau.view(ctx.M, 3 * ctx.N).sum(dim=1)
+def geometry_labels(ctx: Context, k: int = 0, seed: int = 2, exact: bool = False) -> torch.Tensor:
+    """Per-geometry ridge-leverage mass (the training label of the learned scorer): the sum of
+    the scores of the geometry's 3N columns, exact (dense eigendecomposition, small n) or the
+    Nystrom estimate with pilot k, computed and summed in the library."""
+    out = torch.empty(ctx.M, dtype=torch.float64, device=ctx.device)
+    ctx._check(load().gdml_rls_labels(ctx._h, 1 if exact else 0, int(k), int(seed), _ptr(out)))
+    return out
 
 
 def solve_learned(ctx: Context, scorer: Scorer, y, k: int, seed: int = 2, rtol: float = 1e-8,
