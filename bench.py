@@ -614,8 +614,10 @@ def run_gpu(args):
             forms_solve[f"ozaki_inner_levels_{lev}"] = ph
 
     cpu = None
+    config1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, head["iters"])
+        config1 = config1_line(dev)
 
     if rank == 0:
         line = {
@@ -644,6 +646,7 @@ def run_gpu(args):
             "clocks": clocks,
             "forms": forms,
             "forms_solve": forms_solve,
+            "config1": config1,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -763,6 +766,57 @@ def oracle_sample(w, iters: int) -> dict:
 
 def _sample_cmdline(workload: str, iters: int) -> list:
     return [sys.executable, os.path.abspath(__file__), "--cpu-sample", workload, "--ref-iters", str(iters)]
+
+
+def config1_line(dev) -> dict:
+    """The smallest system (ethanol9_m200: N = 9, M = 200, n = 5400, uniform k = 100,
+    lambda = 1e-10): the GPU solve (setup, build, PCG to 1e-8) in FP64 and OZAKI against the
+    paper's "analytic" baseline -- the oracle's dense K and Cholesky solve on the host, timed
+    in full -- and the oracle's matrix-free PCG, timed on 30 iterations and scaled by the GPU's
+    iteration count."""
+    import numpy as np
+    import torch
+
+    from oracle import kernel as ok
+    from oracle import precond as op
+    from oracle import solver as osv
+    from paper_2212_12737_gb300 import gdml, synth
+
+    w = synth.workload("ethanol9_m200")
+    R, y = torch.from_numpy(w.R).to(dev), torch.from_numpy(w.y).to(dev)
+    out = {"workload": f"{w.name}: n={w.n}, {w.select} k={w.k}, lambda={w.lam}, rtol={RTOL}"}
+    for prec in ("fp64", "ozaki"):
+        best = None
+        for _ in range(3):  # the first call captures the PCG graph
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ctx = gdml.kernel_setup(R, w.sigma, w.lam, precision=prec)
+            ctx.precond_build(w.select, w.k, seed=2)
+            _, it, rel, _ = ctx.pcg_solve(y, rtol=RTOL, max_iter=20000, raise_on_nonconvergence=False)
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter() - t0
+            ctx.destroy()
+            best = t if best is None else min(best, t)
+        out[f"gpu_{prec}"] = {"s": best, "iters": it, "relres": rel}
+    t0 = time.perf_counter()
+    K = ok.force_kernel_dense(w.R, w.sigma)
+    t1 = time.perf_counter()
+    alpha = osv.solve_exact(K, w.lam, w.y)
+    t2 = time.perf_counter()
+    rel_cf = float(np.linalg.norm(w.y - K @ alpha - w.lam * alpha) / np.linalg.norm(w.y))
+    S = op.select_uniform(w.n, w.k, 2)
+    L, _ = op.nystrom_factor(K[:, S], S)
+    LC = op.woodbury_core(L, w.lam)
+    t3 = time.perf_counter()
+    res = osv.pcg(lambda v: ok.matvec(w.R, w.sigma, v, w.lam), lambda r: op.woodbury_apply(L, LC, w.lam, r),
+                  w.y, rtol=1e-30, max_iter=30, max_restarts=0)
+    t4 = time.perf_counter()
+    out["cpu_closed_form"] = {"s": t2 - t0, "assemble_K_s": t1 - t0, "cholesky_solve_s": t2 - t1,
+                              "relres": rel_cf, "cores": os.cpu_count(), "kind": "oracle"}
+    out["cpu_pcg_extrapolated"] = {"s": (t4 - t3) / res.iters * out["gpu_fp64"]["iters"],
+                                   "sampled_iterations": res.iters, "per_iteration_s": (t4 - t3) / res.iters,
+                                   "iters": out["gpu_fp64"]["iters"], "kind": "oracle", "extrapolated": True}
+    return out
 
 
 def cpu_baseline(w, gpu_iters: int) -> dict:

@@ -46,6 +46,7 @@ constexpr int kExpStage = oz::BM + oz::BN;                             // a chun
 constexpr int kSmemTotalM = kSmemDataM + 1024 + 256 + 2 * kExpStage * 4;
 constexpr int kKbPerChunkM = oz::KC / oz::KB;                          // 4
 constexpr int kEpiCols = oz::BN * 4 / kEpiWarps;                       // 16 columns per epilogue warp
+constexpr int kTilesPerHandoff = 2;  // A tiles the waiter hands to the MMA warp per named-barrier meeting
 static_assert(oz::BM * kStageLd * 8 <= kSmemDataM, "output staging fits the operand buffers");
 static_assert(kSmemTotalM <= 227 * 1024, "shared memory per CTA");
 static_assert(kEpiCols % 8 == 0, "epilogue columns in groups of 8");
@@ -495,27 +496,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       failed = failed || !__shfl_sync(0xffffffffu, okw, 0);
-      for (int pos = 0; pos < nlev; ++pos) {
-        const int ai = kb * nlev + pos;
-        const int s = ai % kAStagesM;
-        const uint32_t ph = (uint32_t)(ai / kAStagesM) & 1u;
+#pragma unroll
+      for (int p0 = 0; p0 < nlev; p0 += kTilesPerHandoff) {
         int oka = 1;
         if (lane == 0 && !failed) {
-          if (chunk_start && !mbar_wait_spin(&tfree[nlev - 1 - pos], (uint32_t)(q - 1) & 1u)) {
-            atomicExch(err, tc::ERR_TIMEOUT_DONE);
-            *abort_flag = 1;
-            oka = 0;
-          } else if (!mbar_wait_spin(&afull[s], ph)) {
-            atomicExch(err, tc::ERR_TIMEOUT_FULL);
-            *abort_flag = 1;
-            oka = 0;
-          } else if (*abort_flag) {
-            oka = 0;
+#pragma unroll
+          for (int pos = p0; pos < min(p0 + kTilesPerHandoff, nlev); ++pos) {
+            const int ai = kb * nlev + pos;
+            const int s = ai % kAStagesM;
+            const uint32_t ph = (uint32_t)(ai / kAStagesM) & 1u;
+            if (!oka) break;
+            if (chunk_start && !mbar_wait_spin(&tfree[nlev - 1 - pos], (uint32_t)(q - 1) & 1u)) {
+              atomicExch(err, tc::ERR_TIMEOUT_DONE);
+              *abort_flag = 1;
+              oka = 0;
+            } else if (!mbar_wait_spin(&afull[s], ph)) {
+              atomicExch(err, tc::ERR_TIMEOUT_FULL);
+              *abort_flag = 1;
+              oka = 0;
+            } else if (*abort_flag) {
+              oka = 0;
+            }
           }
         }
         failed = failed || !__shfl_sync(0xffffffffu, oka, 0);
         (void)handoff(failed);
-        if (pos == min(1, nlev - 1) && kb >= 1 && kb + 1 < nk) {
+        if (p0 + kTilesPerHandoff > min(1, nlev - 1) && p0 <= min(1, nlev - 1) && kb >= 1 && kb + 1 < nk) {
           int okb = 1;
           if (lane == 0 && !failed) {
             if (!mbar_wait_spin(&bempty[(kb - 1) & 1], (uint32_t)((kb - 1) >> 1) & 1u)) {
@@ -544,10 +550,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool& failed = mma_failed;
     for (int kb = 0; kb < nk; ++kb) {
       const bool chunk_first = kb % kKbPerChunkM == 0;
-      for (int pos = 0; pos < nlev; ++pos) {
-        const int i = nlev - 1 - pos;
+#pragma unroll
+      for (int p0 = 0; p0 < nlev; p0 += kTilesPerHandoff) {
         failed = handoff(false) || failed;
         tc::fence_after_sync();
+#pragma unroll
+        for (int pos = p0; pos < min(p0 + kTilesPerHandoff, nlev); ++pos) {
+        const int i = nlev - 1 - pos;
         const int ai = kb * nlev + pos;
         const int s = ai % kAStagesM;
         if (lane == 0) {
@@ -573,6 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // also after a failure (the A producer never starves), unless the failure came
           // before any MMA: then no asynchronous arrive may outlive the CTA
           if (mma_any || !failed) tc::mma_commit(&aempty[s]);
+        }
         }
         __syncwarp();
       }
