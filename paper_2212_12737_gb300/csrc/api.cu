@@ -107,6 +107,7 @@ struct gdml_ctx {
   double* wt = nullptr;
   WsPlan ws;              // TMA-staged passes over Lf (DF64/OZAKI contexts)
   int* werr = nullptr;    // error word of the staged passes
+  unsigned* wbar = nullptr;  // [2] grid-barrier counters of the fused Woodbury core (kept zero)
   int64_t cap_k = 0;
 
   // PCG state
@@ -477,7 +478,7 @@ gdml_status apply_precond(gdml_ctx* c, const double* r, double* z) {
   }
   if (df_precond(c))
     woodbury_apply_df(c->Lf, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt,
-                      reinterpret_cast<float2*>(c->rsplit), &c->ws, c->werr, c->st);
+                      reinterpret_cast<float2*>(c->rsplit), &c->ws, c->werr, c->wbar, c->st);
   else
     woodbury_apply<double>(c->L, c->n, c->k, c->Cfull, c->Cinv, c->lam, r, z, c->wpart, c->wt, c->st);
   return check_launch(c, "woodbury_apply");
@@ -755,6 +756,9 @@ gdml_status setup_impl(gdml_ctx** out, const double* R_dev, int64_t M, int32_t N
   TRY(dalloc(C, &c->status, 1));
   TRY(dalloc(C, &c->werr, 1));
   CTRY(C, cudaMemsetAsync(c->werr, 0, sizeof(int), c->st));
+  TRY(dalloc(C, &c->wbar, 2));
+  CTRY(C, cudaMemsetAsync(c->wbar, 0, 2 * sizeof(unsigned), c->st));
+  if (df_precond(C)) (void)coop_graph_capture_ok();  // once per process, before any capture
   TRY(dalloc(C, &c->ictl, IC_COUNT));
   CTRY(C, cudaMemsetAsync(c->ictl, 0, IC_COUNT * sizeof(int64_t), c->st));
   c->hist_cap = kHistCap;

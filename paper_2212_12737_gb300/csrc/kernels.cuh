@@ -102,9 +102,14 @@ struct WsPlan {
 // fills plan for L (plan.ok = false where the staged passes do not apply: n % 4 != 0, k = 0,
 // or the CUDA driver rejects the map); rows: 128 or 256 to force the chunk size, else automatic
 void ws_plan(WsPlan& plan, const float* L, int64_t n, int64_t k, int rows = 0);
+// whether this driver captures cooperative launches into graphs (checked once per process,
+// outside any capture; the fused Woodbury core needs it)
+bool coop_graph_capture_ok();
+// bar: two zeroed words (the fused core's grid barrier; nullptr: separate launches for the
+// k-vector steps)
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                        const double* r, double* z, double* part, double* t, float2* rs, const WsPlan* plan,
-                       int* err, cudaStream_t st);
+                       int* err, unsigned* bar, cudaStream_t st);
 // the two L passes alone (test hook): t = L^T r and z = (r - L u) / lambda, staged (plan) or
 // register-streamed (plan == nullptr); part: woodbury_part_size(n, k) doubles, t2: k float pairs
 void df_passes(const float* L, int64_t n, int64_t k, const double* r, const double* u, double lam, double* t,

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 #include "kernels.cuh"
 #include "oz.cuh"
@@ -287,6 +288,69 @@ __global__ void __launch_bounds__(256) oz_proj_slice_kernel(const double* __rest
   slice_write(xs, ex, sl, a, p, Rp, Kp);
 }
 
+// The same for rows of up to kProjChunks chunks (D <= 1024): one CTA of 256 threads per
+// geometry, every load of the row (3 G entries and xc per descriptor) issued before the first
+// chunk is computed; per chunk, w, its exponent (a CTA reduction) and its slices.  W and the
+// slices are those of the separate projection and slicing; t sums thread by thread over the
+// chunks, then over the CTA in a fixed order.
+constexpr int kProjChunks = 4;
+__global__ void __launch_bounds__(256) oz_proj_slice_multi_kernel(const double* __restrict__ G,
+                                                                  const double* __restrict__ Xc,
+                                                                  const double* __restrict__ v, int64_t M, int N,
+                                                                  int D, int nchunks, double* __restrict__ W,
+                                                                  double* __restrict__ t, float2* __restrict__ t2,
+                                                                  int64_t Rp, int64_t Kp, bf16* __restrict__ sl,
+                                                                  int* __restrict__ e) {
+  extern __shared__ double sv[];  // 3N
+  __shared__ float red[8];
+  __shared__ double redt[8];
+  const int64_t a = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int B = 3 * N;
+  const double* Ga = G + a * D * 3;
+  double g[kProjChunks][3], xc[kProjChunks];
+#pragma unroll
+  for (int q = 0; q < kProjChunks; ++q) {
+    const int p = q * oz::KC + tid;
+    const bool in = q < nchunks && p < D;
+    g[q][0] = in ? Ga[3 * p] : 0.0;
+    g[q][1] = in ? Ga[3 * p + 1] : 0.0;
+    g[q][2] = in ? Ga[3 * p + 2] : 0.0;
+    xc[q] = in ? Xc[a * D + p] : 0.0;
+  }
+  for (int l = tid; l < B; l += blockDim.x) sv[l] = v[a * B + l];
+  __syncthreads();
+  double part = 0.0;
+#pragma unroll
+  for (int q = 0; q < kProjChunks; ++q) {
+    if (q >= nchunks) break;
+    const int p = q * oz::KC + tid;
+    double w = 0.0;
+    if (p < D) {
+      int i, j;
+      pair_of(p, i, j);
+      w = -(g[q][0] * (sv[3 * i] - sv[3 * j]) + g[q][1] * (sv[3 * i + 1] - sv[3 * j + 1]) +
+            g[q][2] * (sv[3 * i + 2] - sv[3 * j + 2]));
+      W[a * D + p] = w;
+    }
+    part = fma(xc[q], w, part);
+    const float2 xs = split_d(w);
+    const int ex = chunk_exponent(fabsf(xs.x), red);  // contains a __syncthreads
+    if (tid == 0) e[q * M + a] = ex;
+    slice_write(xs, ex, sl, a, p, Rp, Kp);
+    __syncthreads();  // red is reused by the next chunk's reduction
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) redt[warp] = part;
+  __syncthreads();
+  if (tid == 0) {
+    double s2 = redt[0];
+    for (int k = 1; k < 8; ++k) s2 += redt[k];
+    t[a] = s2;
+    t2[a] = split_d(s2);
+  }
+}
+
 // XT (cols x rows) = X^T, X rows x cols with row stride ldx (32 x 32 tiles)
 __global__ void oz_transpose_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                                     double* __restrict__ XT) {
@@ -348,9 +412,10 @@ __device__ __forceinline__ bool handoff(bool failed) {
 //    the next k-block's group while the current one is multiplied, and does every mbarrier
 //    wait of the MMA side: it hands each A tile to warp 1 at named barrier 2 (a wait or any
 //    shared-memory read in the MMA-issuing thread stalls the tensor pipe).
-//  * Warp 1 multiplies A slice i with B slices j = 0..6-i (4 MMAs per pair) into TMEM
+//  * Warp 1 multiplies A slice i with B slices j = 0..6-i (4 MMAs per K step of 16) into TMEM
 //    accumulator i + j ("level"); the first k-block of a chunk overwrites level i with its
-//    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.
+//    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.  Pairs (i, j) and
+//    (i, j + 1) for j >= 1 go into one N = 128 MMA (19 MMAs per K step instead of 28).
 //  * The epilogue warps drain a finished chunk level by level, 6 down to 0 (levels 6..4 summed
 //    in FP32, 3..0 added in double-float, then scaled by 2^(eA + eB) into running
 //    double-float sums held in registers), releasing each level as soon as it is read
@@ -545,6 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (lane 0; the whole warp meets the waiter at barrier 2)
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
+    constexpr uint32_t idesc2 = tc::make_idesc(1, 2 * oz::BN);  // two adjacent slices, two levels
     const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
     bool& failed = mma_failed;
@@ -565,16 +631,34 @@ __global__ void __launch_bounds__(kThreads, 1)
             // step of 32 bytes adds 2, B slice j of buffer b adds (b * group + j * tile) / 16
             const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
             const uint64_t bg = bdesc0 + (uint64_t)((kb & 1) * (kBGroupM >> 4));
+            {  // pair (i, 0) -> level i; a chunk's first k-block overwrites the level here
+              const uint32_t d = tmem + (uint32_t)(i * oz::BN);
+              const uint32_t acc = chunk_first ? 0u : 1u;
+              tc::mma_issue<true>(d, ad, bg, idesc, acc);
+              tc::mma_issue<true>(d, ad + 2, bg + 2, idesc, 1u);
+              tc::mma_issue<true>(d, ad + 4, bg + 4, idesc, 1u);
+              tc::mma_issue<true>(d, ad + 6, bg + 6, idesc, 1u);
+            }
+            // pairs (i, j) and (i, j + 1), j = 1, 3, 5: levels i + j and i + j + 1 are adjacent
+            // 64-column blocks of TMEM and B slices j, j + 1 adjacent 64-row tiles, so one
+            // N = 128 MMA computes both (A read once).  Both levels were first written by an
+            // earlier slice of this k-block (the order is 6, 5, ..., 0), so these accumulate.
 #pragma unroll
-            for (int j = 0; j < oz::S; ++j) {
+            for (int j = 1; j < oz::S; j += 2) {
               if (i + j < nlev) {
                 const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
                 const uint64_t bj = bg + (uint64_t)(j * (kBTile >> 4));
-                const uint32_t acc = (chunk_first && j == 0) ? 0u : 1u;  // level i's first MMA of the chunk
-                tc::mma_issue<true>(d, ad, bj, idesc, acc);
-                tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
-                tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
-                tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+                if (i + j + 1 < nlev) {
+                  tc::mma_issue<true>(d, ad, bj, idesc2, 1u);
+                  tc::mma_issue<true>(d, ad + 2, bj + 2, idesc2, 1u);
+                  tc::mma_issue<true>(d, ad + 4, bj + 4, idesc2, 1u);
+                  tc::mma_issue<true>(d, ad + 6, bj + 6, idesc2, 1u);
+                } else {
+                  tc::mma_issue<true>(d, ad, bj, idesc, 1u);
+                  tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
+                  tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
+                  tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+                }
               }
             }
             mma_any = true;
@@ -1112,11 +1196,12 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
 }
 
 // (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a); U_a and rowsum_a summed from
-// their double-float partials, the rest in FP64.  One CTA per geometry: thread p forms the
+// their double-float partials, the rest in FP64.  One CTA per geometry (one thread per
+// descriptor up to D = 1024, so every load of the geometry is in flight at once): thread p forms the
 // descriptor's term w_p = g_p u_p (its three coordinate derivatives times u_p; coalesced
 // loads of G), then thread (i, c) sums the N - 1 pair terms of atom i from shared memory
 // (the derivative of x_p with respect to its first atom i > j carries the minus sign).
-__global__ void __launch_bounds__(256) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
+__global__ void __launch_bounds__(1024, 1) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
                                                           const float2* __restrict__ rs2, int nrs,
                                                           const double* __restrict__ Xc, const double* __restrict__ G,
                                                           const double* __restrict__ v, int N, double lam,
@@ -1246,13 +1331,25 @@ static void transpose(const double* X, int64_t rows, int64_t cols, int64_t ldx, 
   { oz_transpose_kernel<<<g, dim3(32, 8), 0, st>>>(X, rows, cols, ldx, XT); count_launch(); }
 }
 
-// K chunks per CTA of the matvec GEMM: as many as keep about 8 waves of CTAs on the GPU
-// (one per output tile and chunk group); the epilogue then runs once per group instead of
-// once per chunk and writes one partial per group
+// K chunks per CTA of the matvec GEMM.  Time ~ whole waves of CTAs x (chunks per CTA + a fixed
+// per-CTA cost of about half a chunk: start-up, drain, write-out); the G minimising it, the
+// larger G (fewer groups, fewer partials for the consumer to read) on ties.  A partial last
+// wave costs as much as a full one, so e.g. 560 tiles x 20 chunks prefers one group of 20
+// (3.7 waves -> 4) to three groups of 7 (11.05 waves -> 12).
 int oz_auto_chunks_per_cta(int64_t tiles, int64_t nchunks) {
-  const int64_t target = 8 * (int64_t)num_sms();
-  const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(nchunks, cdiv(target, std::max<int64_t>(tiles, 1))));
-  return (int)cdiv(nchunks, groups);
+  const int64_t sms = num_sms();
+  tiles = std::max<int64_t>(tiles, 1);
+  int best = 1;
+  int64_t best_cost = INT64_MAX;
+  for (int64_t G = 1; G <= std::max<int64_t>(nchunks, 1); ++G) {
+    const int64_t groups = cdiv(nchunks, G), geff = cdiv(nchunks, groups);
+    const int64_t cost = cdiv(tiles * groups, sms) * (2 * geff + 1);  // in half chunks
+    if (cost <= best_cost) {
+      best_cost = cost;
+      best = (int)G;
+    }
+  }
+  return best;
 }
 
 // C partials (groups of G chunks, one float2 slab per group at out + z split_stride) of
@@ -1338,6 +1435,8 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
     WB = oz.WB;
   } else if (oz.W1.Kp <= oz::KC) {  // one chunk per row: projection and slicing in one kernel
     { oz_proj_slice_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(double), st>>>(G, Xc, v, M, oz.N, D, oz.W, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
+  } else if (oz.W1.nchunks <= kProjChunks) {  // up to 4 chunks per row: likewise, chunk by chunk
+    { oz_proj_slice_multi_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(double), st>>>(G, Xc, v, M, oz.N, D, (int)oz.W1.nchunks, oz.W, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
   } else {
     launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
     slice_rows(oz.W, D, oz.W1, st, oz.t, oz.t2);
@@ -1356,7 +1455,7 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
   const size_t smem = 3 * (size_t)D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { oz_backproj_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
+  { oz_backproj_kernel<<<(unsigned)M, (unsigned)std::min<int64_t>(1024, 32 * cdiv(D, 32)), smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced matvec kernels");
   return GDML_OK;
 }

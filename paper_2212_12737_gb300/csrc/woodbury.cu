@@ -762,16 +762,11 @@ __device__ __forceinline__ float4 ld_evict_last(const float4* p, uint64_t policy
                : "l"(p), "l"(policy));
   return v;
 }
-__global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restrict__ A, int64_t k,
-                                                           const float2* __restrict__ x, int mode,
-                                                           const double* __restrict__ t, double* __restrict__ y,
-                                                           float2* __restrict__ y2) {
-  __shared__ __align__(16) float2 xs[kSymvRowsMaxK];
-  for (int64_t j = threadIdx.x; j < k; j += 256) xs[j] = x[j];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-  if (i >= k) return;
+// Row i of the product, by one warp (xs: the vector in shared memory, k even); the result as
+// symv_df_kernel's modes: 0  y = A x;  1  y2 = t - A x;  2  y += A x (y2: float pairs of y)
+__device__ __forceinline__ void symv_row_df(const float2* __restrict__ A, int64_t k, const float2* xs, int mode,
+                                            const double* __restrict__ t, double* __restrict__ y,
+                                            float2* __restrict__ y2, int64_t i, int lane) {
   const float4* row = reinterpret_cast<const float4*>(A + i * k);  // k even: 16-byte aligned rows
   const float4* xv4 = reinterpret_cast<const float4*>(xs);
   const int64_t nq = k / 2;  // float4 pieces per row (two entries each)
@@ -833,6 +828,18 @@ __global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restr
   y2[i] = make_float2(vh, (float)(v - (double)vh));
 }
 
+__global__ void __launch_bounds__(256) symv_df_rows_kernel(const float2* __restrict__ A, int64_t k,
+                                                           const float2* __restrict__ x, int mode,
+                                                           const double* __restrict__ t, double* __restrict__ y,
+                                                           float2* __restrict__ y2) {
+  __shared__ __align__(16) float2 xs[kSymvRowsMaxK];
+  for (int64_t j = threadIdx.x; j < k; j += 256) xs[j] = x[j];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i < k) symv_row_df(A, k, xs, mode, t, y, y2, i, lane);
+}
+
 static void symv_df(const float2* A, int64_t k, const float2* x, int mode, const double* t, double* y, float2* y2,
                     cudaStream_t st) {
   if ((k & 1) == 0 && k <= kSymvRowsMaxK)
@@ -846,12 +853,8 @@ static void symv_df(const float2* A, int64_t k, const float2* x, int mode, const
 // t[j] = sum of the chunk partials (as reduce_chunks_kernel), also split into t2[j]; PAIRS:
 // the partials are double-float pairs (float2) rather than doubles
 template <bool PAIRS>
-__global__ void __launch_bounds__(256) reduce_chunks_df_kernel(const double* __restrict__ part, int64_t nchunks,
-                                                               int64_t k, double* __restrict__ t,
-                                                               float2* __restrict__ t2) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * 8 + warp;
-  if (j >= k) return;
+__device__ __forceinline__ void reduce_row_df(const double* __restrict__ part, int64_t nchunks,
+                                              double* __restrict__ t, float2* __restrict__ t2, int64_t j, int lane) {
   double s = 0.0;
   if (PAIRS) {
     const float2* pj = reinterpret_cast<const float2*>(part) + j * nchunks;
@@ -868,6 +871,90 @@ __global__ void __launch_bounds__(256) reduce_chunks_df_kernel(const double* __r
     t[j] = s;
     const float sh = (float)s;
     t2[j] = make_float2(sh, (float)(s - (double)sh));
+  }
+}
+
+template <bool PAIRS>
+__global__ void __launch_bounds__(256) reduce_chunks_df_kernel(const double* __restrict__ part, int64_t nchunks,
+                                                               int64_t k, double* __restrict__ t,
+                                                               float2* __restrict__ t2) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * 8 + warp;
+  if (j < k) reduce_row_df<PAIRS>(part, nchunks, t, t2, j, lane);
+}
+
+// ---------------------------------------------------------------- fused Woodbury core
+// The k-vector steps between the two passes over L in one cooperative launch (one CTA per SM):
+//   t = sum of the L^T r chunk partials (float pairs); u = C^-1 t; e = t - C u; u += C^-1 e,
+// each row by one warp with the arithmetic of reduce_row_df / symv_row_df (so the results are
+// those of the separate launches), separated by a grid-wide barrier.  The barrier counts
+// arrivals in bar[0]; every wait is bounded (g_wait_limit polls, then err is set and the CTA
+// skips the rest), and the last CTA to leave resets bar[0] and bar[1] for the next launch.
+constexpr int kCoreMaxK = 16384;  // the vector staged per CTA: k float pairs of shared memory
+
+__device__ __forceinline__ bool core_grid_barrier(unsigned* bar, unsigned target, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    ok = 0;
+    const uint32_t limit = tc::g_wait_limit;
+    for (uint32_t it = 0; it < limit; ++it) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+    if (!ok) atomicExch(err, tc::ERR_TIMEOUT_DONE);
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) woodbury_core_fused_kernel(const double* __restrict__ part, int64_t nchunks,
+                                                                  int64_t k, const float2* __restrict__ Cinv,
+                                                                  const float2* __restrict__ C, double* t,
+                                                                  float2* t2, double* u, float2* u2, float2* e2,
+                                                                  unsigned* bar, int* err) {
+  extern __shared__ __align__(16) float2 xs[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + warp, nw = (int64_t)gridDim.x * 8;
+  bool ok = true;
+  // rows go to warps the same way in every phase, so t[i] and u[i] are re-read by the warp that
+  // wrote them; the staged vectors come from every CTA and are read past L1 after the barrier
+  for (int64_t j = gw; j < k; j += nw) reduce_row_df<true>(part, nchunks, t, t2, j, lane);
+  ok = core_grid_barrier(bar, gridDim.x, err);
+  if (ok) {  // u = C^-1 t
+    for (int64_t j = threadIdx.x; j < k; j += 256) xs[j] = __ldcg(t2 + j);
+    __syncthreads();
+    for (int64_t i = gw; i < k; i += nw) symv_row_df(Cinv, k, xs, 0, t, u, u2, i, lane);
+    ok = core_grid_barrier(bar, 2 * gridDim.x, err);
+  }
+  if (ok) {  // e = t - C u
+    for (int64_t j = threadIdx.x; j < k; j += 256) xs[j] = __ldcg(u2 + j);
+    __syncthreads();
+    for (int64_t i = gw; i < k; i += nw) symv_row_df(C, k, xs, 1, t, nullptr, e2, i, lane);
+    ok = core_grid_barrier(bar, 3 * gridDim.x, err);
+  }
+  if (ok) {  // u += C^-1 e
+    for (int64_t j = threadIdx.x; j < k; j += 256) xs[j] = __ldcg(e2 + j);
+    __syncthreads();
+    for (int64_t i = gw; i < k; i += nw) symv_row_df(Cinv, k, xs, 2, t, u, u2, i, lane);
+  }
+  // the last CTA out resets the counters (no CTA reads them again in this launch)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(bar + 1, 1u) == gridDim.x - 1) {
+      bar[0] = 0u;
+      bar[1] = 0u;
+      __threadfence();
+    }
   }
 }
 
@@ -908,9 +995,76 @@ static void df_pass_n(const float* L, int64_t n, int64_t k, const float2* u2, co
   { gemv_n_df_finish_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(zp, n, r, inv_lam, z); count_launch(); }
 }
 
+// A trivial cooperative kernel, to learn once whether this driver accepts cooperative launches
+// inside captured graphs (the PCG loop is one)
+__global__ void coop_probe_kernel(int* x) {
+  if (threadIdx.x == 0 && x) *x = 1;
+}
+
+bool coop_graph_capture_ok() {
+  static int state = -1;
+  if (state >= 0) return state == 1;
+  state = 0;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(32);
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int* none = nullptr;
+    const bool launched = cudaLaunchKernelEx(&cfg, coop_probe_kernel, none) == cudaSuccess;
+    ok = cudaStreamEndCapture(s, &g) == cudaSuccess && launched && g;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(s);
+  (void)cudaGetLastError();
+  state = ok ? 1 : 0;
+  return ok;
+}
+
+// the fused core applies to the staged L^T r pass (float-pair partials), an even k that fits
+// the staged vector, and a driver that captures cooperative launches
+static bool core_fusable(const WsPlan* plan, const float* L, int64_t n, int64_t k, const unsigned* bar) {
+  return bar && ws_usable(plan, L, n, k) && (k & 1) == 0 && k <= kCoreMaxK && coop_graph_capture_ok();
+}
+
+static void launch_core_fused(const double* part, int64_t nchunks, int64_t k, const float2* Ci2, const float2* C2,
+                              double* t, float2* t2, double* u, float2* u2, float2* e2, unsigned* bar, int* err,
+                              cudaStream_t st) {
+  const size_t smem = (size_t)k * sizeof(float2);
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    cudaFuncSetAttribute(woodbury_core_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)num_sms());  // one CTA per SM: all co-resident
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute a;
+  a.id = cudaLaunchAttributeCooperative;
+  a.val.cooperative = 1;
+  cfg.attrs = &a;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, woodbury_core_fused_kernel, part, nchunks, k, Ci2, C2, t, t2, u, u2, e2, bar, err);
+  count_launch();
+}
+
 void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, const double* Cinv, double lam,
                        const double* r, double* z, double* part, double* t, float2* rs, const WsPlan* plan,
-                       int* err, cudaStream_t st) {
+                       int* err, unsigned* bar, cudaStream_t st) {
   double* u = t + k;
   float2* t2 = reinterpret_cast<float2*>(t + 3 * k);
   float2* e2 = reinterpret_cast<float2*>(t + 4 * k);
@@ -918,6 +1072,13 @@ void woodbury_apply_df(const float* L, int64_t n, int64_t k, const double* C, co
   const float2* Ci2 = reinterpret_cast<const float2*>(Cinv);
   const float2* C2 = reinterpret_cast<const float2*>(C);
   { split_df_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(r, n, rs); count_launch(); }
+  if (core_fusable(plan, L, n, k, bar)) {
+    // L^T r partials, then the reduction and the three k x k products in one launch
+    { ws_gemv_t_kernel<<<plan->grid_t, kWsThreads, kWsSmemT, st>>>(plan->mapT, n, k, plan->ru, plan->nru, plan->ncr, plan->cpr, rs, reinterpret_cast<float2*>(part), err); count_launch(); }
+    launch_core_fused(part, plan->nru, k, Ci2, C2, t, t2, u, u2, e2, bar, err, st);
+    df_pass_n(L, n, k, u2, r, 1.0 / lam, z, part, plan, err, st);
+    return;
+  }
   df_pass_t(L, n, k, rs, part, t, t2, plan, err, st);
   // u = C^-1 t, refined once with the residual t - C u (see woodbury_apply)
   symv_df(Ci2, k, t2, 0, t, u, u2, st);
