@@ -415,7 +415,8 @@ __device__ __forceinline__ bool handoff(bool failed) {
 //  * Warp 1 multiplies A slice i with B slices j = 0..6-i (4 MMAs per K step of 16) into TMEM
 //    accumulator i + j ("level"); the first k-block of a chunk overwrites level i with its
 //    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.  Pairs (i, j) and
-//    (i, j + 1) for j >= 1 go into one N = 128 MMA (19 MMAs per K step instead of 28).
+//    (i, j + 1) go into one N = 128 MMA: 16 MMAs per K step instead of 28 (19 in a chunk's
+//    first k-block, where pair (i, 0) stays alone).
 //  * The epilogue warps drain a finished chunk level by level, 6 down to 0 (levels 6..4 summed
 //    in FP32, 3..0 added in double-float, then scaled by 2^(eA + eB) into running
 //    double-float sums held in registers), releasing each level as soon as it is read
@@ -631,35 +632,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             // step of 32 bytes adds 2, B slice j of buffer b adds (b * group + j * tile) / 16
             const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
             const uint64_t bg = bdesc0 + (uint64_t)((kb & 1) * (kBGroupM >> 4));
-            {  // pair (i, 0) -> level i; a chunk's first k-block overwrites the level here
-              const uint32_t d = tmem + (uint32_t)(i * oz::BN);
-              const uint32_t acc = chunk_first ? 0u : 1u;
-              tc::mma_issue<true>(d, ad, bg, idesc, acc);
-              tc::mma_issue<true>(d, ad + 2, bg + 2, idesc, 1u);
-              tc::mma_issue<true>(d, ad + 4, bg + 4, idesc, 1u);
-              tc::mma_issue<true>(d, ad + 6, bg + 6, idesc, 1u);
-            }
-            // pairs (i, j) and (i, j + 1), j = 1, 3, 5: levels i + j and i + j + 1 are adjacent
-            // 64-column blocks of TMEM and B slices j, j + 1 adjacent 64-row tiles, so one
-            // N = 128 MMA computes both (A read once).  Both levels were first written by an
-            // earlier slice of this k-block (the order is 6, 5, ..., 0), so these accumulate.
+            // descriptors of the four K steps: A + 2t, B + 2t
+            auto mma4 = [&](uint32_t d, uint64_t bj, uint32_t id, uint32_t acc0) {
+              tc::mma_issue<true>(d, ad, bj, id, acc0);
+              tc::mma_issue<true>(d, ad + 2, bj + 2, id, 1u);
+              tc::mma_issue<true>(d, ad + 4, bj + 4, id, 1u);
+              tc::mma_issue<true>(d, ad + 6, bj + 6, id, 1u);
+            };
+            // Pairs (i, j) and (i, j + 1) go into one N = 128 MMA: levels i + j and i + j + 1 are
+            // adjacent 64-column blocks of TMEM and B slices j, j + 1 adjacent 64-row tiles, so
+            // A is read once for both.
+            if (chunk_first) {
+              // the first k-block of a chunk overwrites level i with pair (i, 0) alone; levels
+              // above i were first written by an earlier slice of this k-block (the order is
+              // 6, 5, ..., 0), so pairs from j = 1 on accumulate
+              mma4(tmem + (uint32_t)(i * oz::BN), bg, idesc, 0u);
 #pragma unroll
-            for (int j = 1; j < oz::S; j += 2) {
-              if (i + j < nlev) {
-                const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
-                const uint64_t bj = bg + (uint64_t)(j * (kBTile >> 4));
-                if (i + j + 1 < nlev) {
-                  tc::mma_issue<true>(d, ad, bj, idesc2, 1u);
-                  tc::mma_issue<true>(d, ad + 2, bj + 2, idesc2, 1u);
-                  tc::mma_issue<true>(d, ad + 4, bj + 4, idesc2, 1u);
-                  tc::mma_issue<true>(d, ad + 6, bj + 6, idesc2, 1u);
-                } else {
-                  tc::mma_issue<true>(d, ad, bj, idesc, 1u);
-                  tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
-                  tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
-                  tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
-                }
-              }
+              for (int j = 1; j < oz::S; j += 2)
+                if (i + j < nlev)
+                  mma4(tmem + (uint32_t)((i + j) * oz::BN), bg + (uint64_t)(j * (kBTile >> 4)),
+                       i + j + 1 < nlev ? idesc2 : idesc, 1u);
+            } else {
+#pragma unroll
+              for (int j = 0; j < oz::S; j += 2)
+                if (i + j < nlev)
+                  mma4(tmem + (uint32_t)((i + j) * oz::BN), bg + (uint64_t)(j * (kBTile >> 4)),
+                       i + j + 1 < nlev ? idesc2 : idesc, 1u);
             }
             mma_any = true;
           }
@@ -1196,12 +1194,12 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
 }
 
 // (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a); U_a and rowsum_a summed from
-// their double-float partials, the rest in FP64.  One CTA per geometry (one thread per
-// descriptor up to D = 1024, so every load of the geometry is in flight at once): thread p forms the
+// their double-float partials, the rest in FP64.  One CTA of 256 threads per geometry (one
+// 864-thread CTA per geometry measured 1.8x slower at D = 861): thread p forms the
 // descriptor's term w_p = g_p u_p (its three coordinate derivatives times u_p; coalesced
 // loads of G), then thread (i, c) sums the N - 1 pair terms of atom i from shared memory
 // (the derivative of x_p with respect to its first atom i > j carries the minus sign).
-__global__ void __launch_bounds__(1024, 1) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
+__global__ void __launch_bounds__(256) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
                                                           const float2* __restrict__ rs2, int nrs,
                                                           const double* __restrict__ Xc, const double* __restrict__ G,
                                                           const double* __restrict__ v, int N, double lam,
@@ -1455,7 +1453,7 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
   const size_t smem = 3 * (size_t)D * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { oz_backproj_kernel<<<(unsigned)M, (unsigned)std::min<int64_t>(1024, 32 * cdiv(D, 32)), smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
+  { oz_backproj_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced matvec kernels");
   return GDML_OK;
 }

@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(256) reduce_chunks_df_kernel(const double* __r
 }
 
 // ---------------------------------------------------------------- fused Woodbury core
-// The k-vector steps between the two passes over L in one cooperative launch (one CTA per SM):
+// The k-vector steps between the two passes over L in one cooperative launch (all CTAs resident):
 //   t = sum of the L^T r chunk partials (float pairs); u = C^-1 t; e = t - C u; u += C^-1 e,
 // each row by one warp with the arithmetic of reduce_row_df / symv_row_df (so the results are
 // those of the separate launches), separated by a grid-wide barrier.  The barrier counts
@@ -1048,8 +1048,14 @@ static void launch_core_fused(const double* part, int64_t nchunks, int64_t k, co
     cudaFuncSetAttribute(woodbury_core_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = smem;
   }
+  // as many CTAs as can be resident at once (at most 4 per SM): the cooperative launch needs
+  // them co-resident, and more warps keep more of each phase's row loads in flight
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, woodbury_core_fused_kernel, 256, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)num_sms());  // one CTA per SM: all co-resident
+  cfg.gridDim = dim3((unsigned)(num_sms() * std::min(per_sm, 4)));
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
