@@ -48,6 +48,7 @@ constexpr int kSmemTotalM = kSmemDataM + 1024 + 256 + 2 * kExpStage * 4;
 constexpr int kKbPerChunkM = oz::KC / oz::KB;                          // 4
 constexpr int kEpiCols = oz::BN * 4 / kEpiWarps;                       // 16 columns per epilogue warp
 constexpr int kTilesPerHandoff = 2;  // A tiles the waiter hands to the MMA warp per named-barrier meeting
+constexpr int kLevelsPerMma = 4;     // slice pairs (adjacent levels) per MMA: N = 64 x 4 = 256 at most
 static_assert(oz::BM * kStageLd * 8 <= kSmemDataM, "output staging fits the operand buffers");
 static_assert(kSmemTotalM <= 227 * 1024, "shared memory per CTA");
 static_assert(kEpiCols % 8 == 0, "epilogue columns in groups of 8");
@@ -414,9 +415,9 @@ __device__ __forceinline__ bool handoff(bool failed) {
 //    shared-memory read in the MMA-issuing thread stalls the tensor pipe).
 //  * Warp 1 multiplies A slice i with B slices j = 0..6-i (4 MMAs per K step of 16) into TMEM
 //    accumulator i + j ("level"); the first k-block of a chunk overwrites level i with its
-//    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.  Pairs (i, j) and
-//    (i, j + 1) go into one N = 128 MMA: 16 MMAs per K step instead of 28 (19 in a chunk's
-//    first k-block, where pair (i, 0) stays alone).
+//    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.  Up to four
+//    consecutive pairs (i, j .. j + 3) go into one MMA of N = 64 .. 256: 10 MMAs per K step
+//    instead of 28 (14 in a chunk's first k-block, where pair (i, 0) stays alone).
 //  * The epilogue warps drain a finished chunk level by level, 6 down to 0 (levels 6..4 summed
 //    in FP32, 3..0 added in double-float, then scaled by 2^(eA + eB) into running
 //    double-float sums held in registers), releasing each level as soon as it is read
@@ -611,7 +612,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (lane 0; the whole warp meets the waiter at barrier 2)
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
-    constexpr uint32_t idesc2 = tc::make_idesc(1, 2 * oz::BN);  // two adjacent slices, two levels
+    constexpr uint32_t idesc2 = tc::make_idesc(1, 2 * oz::BN);  // 2, 3, 4 adjacent slices and levels
+    constexpr uint32_t idesc3 = tc::make_idesc(1, 3 * oz::BN);
+    constexpr uint32_t idesc4 = tc::make_idesc(1, 4 * oz::BN);
     const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
     bool& failed = mma_failed;
@@ -639,26 +642,22 @@ __global__ void __launch_bounds__(kThreads, 1)
               tc::mma_issue<true>(d, ad + 4, bj + 4, id, 1u);
               tc::mma_issue<true>(d, ad + 6, bj + 6, id, 1u);
             };
-            // Pairs (i, j) and (i, j + 1) go into one N = 128 MMA: levels i + j and i + j + 1 are
-            // adjacent 64-column blocks of TMEM and B slices j, j + 1 adjacent 64-row tiles, so
-            // A is read once for both.
-            if (chunk_first) {
-              // the first k-block of a chunk overwrites level i with pair (i, 0) alone; levels
-              // above i were first written by an earlier slice of this k-block (the order is
-              // 6, 5, ..., 0), so pairs from j = 1 on accumulate
-              mma4(tmem + (uint32_t)(i * oz::BN), bg, idesc, 0u);
+            // Up to kLevelsPerMma consecutive pairs (i, j) .. (i, j + g - 1) go into one MMA of
+            // N = 64 g: their levels i + j .. i + j + g - 1 are adjacent 64-column blocks of TMEM
+            // and B slices j .. j + g - 1 adjacent 64-row tiles, so A is read once for all g.
+            auto group = [&](int j, uint32_t acc0) {
+              const int g = min(kLevelsPerMma, nlev - i - j);
+              const uint32_t id = g == 1 ? idesc : g == 2 ? idesc2 : g == 3 ? idesc3 : idesc4;
+              mma4(tmem + (uint32_t)((i + j) * oz::BN), bg + (uint64_t)(j * (kBTile >> 4)), id, acc0);
+            };
+            // the first k-block of a chunk overwrites level i with pair (i, 0) alone; levels
+            // above i were first written by an earlier slice of this k-block (the order is
+            // 6, 5, ..., 0), so the pairs from j = 1 on accumulate
+            const int j0 = chunk_first ? 1 : 0;
+            if (chunk_first) mma4(tmem + (uint32_t)(i * oz::BN), bg, idesc, 0u);
 #pragma unroll
-              for (int j = 1; j < oz::S; j += 2)
-                if (i + j < nlev)
-                  mma4(tmem + (uint32_t)((i + j) * oz::BN), bg + (uint64_t)(j * (kBTile >> 4)),
-                       i + j + 1 < nlev ? idesc2 : idesc, 1u);
-            } else {
-#pragma unroll
-              for (int j = 0; j < oz::S; j += 2)
-                if (i + j < nlev)
-                  mma4(tmem + (uint32_t)((i + j) * oz::BN), bg + (uint64_t)(j * (kBTile >> 4)),
-                       i + j + 1 < nlev ? idesc2 : idesc, 1u);
-            }
+            for (int m = 0; m * kLevelsPerMma < oz::S; ++m)
+              if (i + j0 + m * kLevelsPerMma < nlev) group(j0 + m * kLevelsPerMma, 1u);
             mma_any = true;
           }
           // also after a failure (the A producer never starves), unless the failure came
@@ -942,6 +941,9 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (lane 0; the whole warp meets the waiter at barrier 2)
     constexpr uint32_t idesc = tc::make_idesc(1, oz::BN);
+    constexpr uint32_t idesc2 = tc::make_idesc(1, 2 * oz::BN);
+    constexpr uint32_t idesc3 = tc::make_idesc(1, 3 * oz::BN);
+    constexpr uint32_t idesc4 = tc::make_idesc(1, 4 * oz::BN);
     const uint64_t adesc0 = tc::make_sw128_desc(tc::smem_u32(sA));
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
     bool& failed = mma_failed;
@@ -957,16 +959,21 @@ __global__ void __launch_bounds__(kThreadsAcc, 1)
           if (!failed) {
             const uint64_t ad = adesc0 + (uint64_t)(s * (kATile >> 4));
             const uint64_t bd = bdesc0 + (uint64_t)(g * oz::S * (kBTile >> 4));
+            // slice 0 is the first to reach every level, so in a chunk's first k-block its MMAs
+            // overwrite and all later ones accumulate; up to four pairs (i, j .. j + 3), i.e.
+            // adjacent levels and adjacent B slices, go into one MMA of N = 64 .. 256
             const uint32_t first = (!chunk_start || i > 0) ? 1u : 0u;
 #pragma unroll
-            for (int j = 0; j < oz::S; ++j) {
+            for (int j = 0; j < oz::S; j += kLevelsPerMma) {
               if (i + j < oz::S) {
+                const int gl = min(kLevelsPerMma, oz::S - i - j);
+                const uint32_t id = gl == 1 ? idesc : gl == 2 ? idesc2 : gl == 3 ? idesc3 : idesc4;
                 const uint32_t d = tmem + (uint32_t)((i + j) * oz::BN);
                 const uint64_t bj = bd + (uint64_t)(j * (kBTile >> 4));
-                tc::mma_issue<true>(d, ad, bj, idesc, first);
-                tc::mma_issue<true>(d, ad + 2, bj + 2, idesc, 1u);
-                tc::mma_issue<true>(d, ad + 4, bj + 4, idesc, 1u);
-                tc::mma_issue<true>(d, ad + 6, bj + 6, idesc, 1u);
+                tc::mma_issue<true>(d, ad, bj, id, first);
+                tc::mma_issue<true>(d, ad + 2, bj + 2, id, 1u);
+                tc::mma_issue<true>(d, ad + 4, bj + 4, id, 1u);
+                tc::mma_issue<true>(d, ad + 6, bj + 6, id, 1u);
               }
             }
             mma_any = true;
