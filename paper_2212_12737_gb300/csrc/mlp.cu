@@ -3,10 +3,10 @@
 // per-geometry ridge leverage scores this library computes (Sec. 3, "Leverage
 // score sampling"; the scorer replaces their O(k^2 n) estimate at selection time).
 //
-// Storage: FP32 master parameters and Adam moments; BF16 copies of the weights
-// and of the activations feed the contractions, which accumulate in FP32.
-// All contractions here are small (B x D x H with H = 256), so they run as
-// tiled SIMT kernels; none of them is on the PCG solve's loop.
+// Storage: FP32 master parameters and Adam moments; BF16 copies of the weights, of the
+// activations and of the back-propagated gradients feed the five contractions (two forward,
+// three backward), which run on the tcgen05 tensor cores with FP32 accumulation
+// (tc_gemm_bf16); none of them is on the PCG solve's loop.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc.cuh"
 #include "../../include/gdml.h"
 
 namespace gdml {
@@ -29,74 +30,58 @@ __device__ __forceinline__ float ld(const T* p, int64_t i) {
   else return (float)p[i];
 }
 
-// C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]); A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
-// 64 x 64 tile, 256 threads x (4 x 4), K steps of 16, FP32 accumulation.
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A,
-                                                   int64_t sam, int64_t sak, const TB* __restrict__ B,
-                                                   int64_t sbk, int64_t sbn, const float* __restrict__ bias,
-                                                   float* __restrict__ C, int64_t ldc) {
-  __shared__ float As[16][65], Bs[16][65];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
-  float acc[4][4] = {};
-  for (int64_t k0 = 0; k0 < K; k0 += 16) {
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      const int r = e >> 4, kk = e & 15;
-      const int64_t gm = m0 + r, gk = k0 + kk;
-      As[kk][r] = (gm < M && gk < K) ? ld(A, gm * sam + gk * sak) : 0.f;
-      const int64_t gn = n0 + r;
-      Bs[kk][r] = (gn < N && gk < K) ? ld(B, gk * sbk + gn * sbn) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
-      if (gm < M && gn < N) C[gm * ldc + gn] = acc[i][j] + (bias ? bias[gn] : 0.f);
-    }
-}
-
-template <typename TA, typename TB>
-void gemm(int64_t M, int64_t N, int64_t K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
-          int64_t sbn, const float* bias, float* C, int64_t ldc, cudaStream_t st) {
-  dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64));
-  { gemm_kernel<TA, TB><<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, C, ldc); count_launch(); }
-}
+// Operand layouts for the tcgen05 GEMMs (C = A B^T, BF16 operands with row strides that are
+// multiples of 8 elements): the weights as BF16 copies W1b (H x Dp), W2b (H x Hp) and W2t = W2^T;
+// per batch Xs (B x Dp), A1 (B x Hp), dZ2b (B x Hp) and the transposed XsT (D x Bt),
+// A1T (H x Bt), dZ2T (H x Bt), dZ1T (H x Bt) for the weight gradients, whose K is the batch.
+inline int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// Xs = bf16((X - mu) / sd)
+// Xs = bf16((X - mu) / sd), row stride ldx, and (XsT) its transpose with row stride ldt
 __global__ void standardize_kernel(const double* __restrict__ X, int64_t B, int D, const float* __restrict__ mu,
-                                   const float* __restrict__ sd, bf16* __restrict__ Xs) {
+                                   const float* __restrict__ sd, bf16* __restrict__ Xs, int64_t ldx,
+                                   bf16* __restrict__ XsT, int64_t ldt) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= B * D) return;
-  const int d = (int)(e % D);
-  Xs[e] = __float2bfloat16(((float)X[e] - mu[d]) / sd[d]);
+  const int64_t b = e / D;
+  const int d = (int)(e - b * D);
+  const bf16 v = __float2bfloat16(((float)X[e] - mu[d]) / sd[d]);
+  Xs[b * ldx + d] = v;
+  if (XsT) XsT[d * ldt + b] = v;
 }
 
-// A = bf16(gelu(Z)), Z kept in FP32 for the backward pass
-__global__ void gelu_kernel(const float* __restrict__ Z, int64_t n, bf16* __restrict__ A) {
+// A = bf16(gelu(Z)) (Z: B x H FP32, kept for the backward pass) with row stride lda, and (AT)
+// its transpose with row stride ldt
+__global__ void gelu_kernel(const float* __restrict__ Z, int64_t B, int H, bf16* __restrict__ A, int64_t lda,
+                            bf16* __restrict__ AT, int64_t ldt) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < n) A[e] = __float2bfloat16(gelu(Z[e]));
+  if (e >= B * H) return;
+  const int64_t b = e / H;
+  const int h = (int)(e - b * H);
+  const bf16 v = __float2bfloat16(gelu(Z[e]));
+  A[b * lda + h] = v;
+  if (AT) AT[h * ldt + b] = v;
+}
+
+// BF16 copies of the weights in the GEMMs' layouts: W1b (H x Dp), W2b (H x Hp), W2t = W2^T
+__global__ void pack_weights_kernel(const float* __restrict__ W1, const float* __restrict__ W2, int D, int H,
+                                    int64_t Dp, int64_t Hp, bf16* __restrict__ W1b, bf16* __restrict__ W2b,
+                                    bf16* __restrict__ W2t) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n1 = (int64_t)H * D, n2 = (int64_t)H * H;
+  if (e < n1) {
+    const int64_t h = e / D, d = e - h * D;
+    W1b[h * Dp + d] = __float2bfloat16(W1[e]);
+  } else if (e < n1 + n2) {
+    const int64_t f = e - n1, r = f / H, c = f - r * H;
+    const bf16 v = __float2bfloat16(W2[f]);
+    W2b[r * Hp + c] = v;
+    W2t[c * Hp + r] = v;
+  }
 }
 
 // out[b] = A2[b,:] . w3 + b3   (one warp per row)
@@ -130,18 +115,31 @@ __global__ void loss_kernel(const float* __restrict__ out, const double* __restr
   if (threadIdx.x == 0) *loss = red[0] / (float)B;
 }
 
-// dZ2[b,h] = dout[b] * w3[h] * gelu'(Z2[b,h])
+// dZ2[b,h] = dout[b] * w3[h] * gelu'(Z2[b,h]) (FP32, for the bias gradient) and its BF16
+// roundings for the GEMMs: dZ2b (row stride ldb) and the transpose dZ2T (row stride ldt)
 __global__ void head_back_kernel(const float* __restrict__ dout, const bf16* __restrict__ w3,
-                                 const float* __restrict__ Z2, int64_t B, int H, float* __restrict__ dZ2) {
+                                 const float* __restrict__ Z2, int64_t B, int H, float* __restrict__ dZ2,
+                                 bf16* __restrict__ dZ2b, int64_t ldb, bf16* __restrict__ dZ2T, int64_t ldt) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= B * H) return;
-  const int h = (int)(e % H);
-  dZ2[e] = dout[e / H] * __bfloat162float(w3[h]) * gelu_grad(Z2[e]);
+  const int64_t b = e / H;
+  const int h = (int)(e - b * H);
+  const float g = dout[b] * __bfloat162float(w3[h]) * gelu_grad(Z2[e]);
+  dZ2[e] = g;
+  const bf16 gb = __float2bfloat16(g);
+  dZ2b[b * ldb + h] = gb;
+  dZ2T[h * ldt + b] = gb;
 }
 
-__global__ void gelu_back_kernel(float* __restrict__ dA, const float* __restrict__ Z, int64_t n) {
+// dZ1 = dA1 * gelu'(Z1) in place (FP32) and its BF16 transpose dZ1T (row stride ldt)
+__global__ void gelu_back_kernel(float* __restrict__ dA, const float* __restrict__ Z, int64_t B, int H,
+                                 bf16* __restrict__ dZT, int64_t ldt) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < n) dA[e] *= gelu_grad(Z[e]);
+  if (e >= B * H) return;
+  const float g = dA[e] * gelu_grad(Z[e]);
+  dA[e] = g;
+  const int64_t b = e / H;
+  dZT[(e - b * H) * ldt + b] = __float2bfloat16(g);
 }
 
 // g[j] = sum_b M[b, j] (column sums, fixed order per column)
@@ -242,8 +240,12 @@ struct gdml_scorer {
   bf16* pb = nullptr;
   float *mu = nullptr, *sd = nullptr;  // feature standardisation (device, D)
   float ym = 0.f, ysd = 1.f;           // label standardisation
-  int64_t cap = 0;                     // batch capacity of the buffers below
-  bf16 *Xs = nullptr, *A1 = nullptr, *A2 = nullptr;
+  int64_t Dp = 0, Hp = 0;              // row strides of the BF16 GEMM operands (multiples of 8)
+  bf16 *W1b = nullptr, *W2b = nullptr, *W2t = nullptr;  // BF16 weights in the GEMMs' layouts
+  int* err = nullptr;                  // device word set by a timed-out tensor-core pipeline wait
+  int64_t cap = 0, Bt = 0;             // batch capacity of the buffers below; Bt = pad8(cap)
+  bf16 *Xs = nullptr, *A1 = nullptr, *A2 = nullptr, *dZ2b = nullptr;
+  bf16 *XsT = nullptr, *A1T = nullptr, *dZ2T = nullptr, *dZ1T = nullptr;
   float *Z1 = nullptr, *Z2 = nullptr, *out = nullptr, *dout = nullptr, *dZ1 = nullptr, *dZ2 = nullptr,
         *loss = nullptr;
   int64_t step = 0;
@@ -281,7 +283,8 @@ gdml_status salloc(gdml_scorer* s, T** ptr, size_t count) {
 gdml_status ensure_batch(gdml_scorer* s, int64_t B) {
   if (B <= s->cap) return GDML_OK;
   for (void** q : {(void**)&s->Xs, (void**)&s->A1, (void**)&s->A2, (void**)&s->Z1, (void**)&s->Z2, (void**)&s->out,
-                   (void**)&s->dout, (void**)&s->dZ1, (void**)&s->dZ2}) {
+                   (void**)&s->dout, (void**)&s->dZ1, (void**)&s->dZ2, (void**)&s->dZ2b, (void**)&s->XsT,
+                   (void**)&s->A1T, (void**)&s->dZ2T, (void**)&s->dZ1T}) {
     if (*q) {
       cudaFree(*q);
       for (auto& a : s->allocs)
@@ -290,8 +293,14 @@ gdml_status ensure_batch(gdml_scorer* s, int64_t B) {
     }
   }
   const int D = s->D, H = s->H;
-  STRY(salloc(s, &s->Xs, (size_t)(B * D)));
-  STRY(salloc(s, &s->A1, (size_t)(B * H)));
+  const int64_t Bt = pad8(B);
+  STRY(salloc(s, &s->Xs, (size_t)(B * s->Dp)));
+  STRY(salloc(s, &s->A1, (size_t)(B * s->Hp)));
+  STRY(salloc(s, &s->dZ2b, (size_t)(B * s->Hp)));
+  STRY(salloc(s, &s->XsT, (size_t)(D * Bt)));
+  STRY(salloc(s, &s->A1T, (size_t)(H * Bt)));
+  STRY(salloc(s, &s->dZ2T, (size_t)(H * Bt)));
+  STRY(salloc(s, &s->dZ1T, (size_t)(H * Bt)));
   STRY(salloc(s, &s->A2, (size_t)(B * H)));
   STRY(salloc(s, &s->Z1, (size_t)(B * H)));
   STRY(salloc(s, &s->Z2, (size_t)(B * H)));
@@ -300,27 +309,52 @@ gdml_status ensure_batch(gdml_scorer* s, int64_t B) {
   STRY(salloc(s, &s->dZ1, (size_t)(B * H)));
   STRY(salloc(s, &s->dZ2, (size_t)(B * H)));
   s->cap = B;
+  s->Bt = Bt;
   return GDML_OK;
 }
 
-// forward on rows X[0..B) (FP64, B x D) -> s->out (standardised prediction)
-void forward(gdml_scorer* s, const double* X, int64_t B) {
+// BF16 copies of W1 and W2 in the GEMMs' layouts, after every change of the FP32 parameters
+void pack_weights(gdml_scorer* s) {
+  const int64_t n = (int64_t)s->H * s->D + (int64_t)s->H * s->H;
+  { pack_weights_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s->st>>>(s->W1(), s->W2(), s->D, s->H, s->Dp, s->Hp, s->W1b, s->W2b, s->W2t); count_launch(); }
+}
+
+// read (and clear) the device error word after the stream has drained
+gdml_status check_err(gdml_scorer* s) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->st) != cudaSuccess ||
+      cudaStreamSynchronize(s->st) != cudaSuccess)
+    return fail(GDML_ERR_CUDA, "scorer: reading the error word");
+  if (h) {
+    cudaMemsetAsync(s->err, 0, sizeof(int), s->st);
+    return fail(GDML_ERR_TIMEOUT, "scorer: a tensor-core pipeline wait timed out");
+  }
+  return GDML_OK;
+}
+
+// forward on rows X[0..B) (FP64, B x D) -> s->out (standardised prediction); with `keep_t` the
+// transposed BF16 activations for the weight gradients are written too
+gdml_status forward(gdml_scorer* s, const double* X, int64_t B, bool keep_t) {
   const int D = s->D, H = s->H;
+  const int64_t Dp = s->Dp, Hp = s->Hp, Bt = s->Bt;
   cudaStream_t st = s->st;
-  { standardize_kernel<<<(unsigned)cdiv(B * D, 256), 256, 0, st>>>(X, B, D, s->mu, s->sd, s->Xs); count_launch(); }
+  { standardize_kernel<<<(unsigned)cdiv(B * D, 256), 256, 0, st>>>(X, B, D, s->mu, s->sd, s->Xs, Dp, keep_t ? s->XsT : nullptr, Bt); count_launch(); }
   // Z1 = Xs W1^T + b1
-  gemm<bf16, bf16>(B, H, D, s->Xs, D, 1, s->pb, 1, D, s->b1(), s->Z1, H, st);
-  { gelu_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->Z1, B * H, s->A1); count_launch(); }
-  gemm<bf16, bf16>(B, H, H, s->A1, H, 1, s->pb + s->off_W2(), 1, H, s->b2(), s->Z2, H, st);
-  { gelu_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->Z2, B * H, s->A2); count_launch(); }
+  STRY(tc_gemm_bf16(s->Xs, Dp, s->W1b, Dp, (int)B, H, D, s->Z1, H, s->b1(), s->err, st));
+  { gelu_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->Z1, B, H, s->A1, Hp, keep_t ? s->A1T : nullptr, Bt); count_launch(); }
+  // Z2 = A1 W2^T + b2
+  STRY(tc_gemm_bf16(s->A1, Hp, s->W2b, Hp, (int)B, H, H, s->Z2, H, s->b2(), s->err, st));
+  { gelu_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->Z2, B, H, s->A2, H, nullptr, 0); count_launch(); }
   { head_kernel<<<(unsigned)cdiv(B, 8), 256, 0, st>>>(s->A2, B, H, s->pb + s->off_w3(), s->b3(), s->out); count_launch(); }
+  return GDML_OK;
 }
 
 // loss and gradient (into s->g) on one batch
-void backward(gdml_scorer* s, const double* X, const double* y, int64_t B) {
+gdml_status backward(gdml_scorer* s, const double* X, const double* y, int64_t B) {
   const int D = s->D, H = s->H;
+  const int64_t Hp = s->Hp, Bt = s->Bt;
   cudaStream_t st = s->st;
-  forward(s, X, B);
+  STRY(forward(s, X, B, true));
   { loss_kernel<<<1, 256, 0, st>>>(s->out, y, B, s->ym, s->ysd, s->dout, s->loss); count_launch(); }
   float* g = s->g;
   float* gW1 = g;
@@ -330,16 +364,17 @@ void backward(gdml_scorer* s, const double* X, const double* y, int64_t B) {
   float* gw3 = gb2 + H;
   float* gb3 = gw3 + H;
   { head_wgrad_kernel<<<(unsigned)cdiv(H, 256), 256, 0, st>>>(s->A2, s->dout, B, H, gw3, gb3); count_launch(); }
-  { head_back_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->dout, s->pb + s->off_w3(), s->Z2, B, H, s->dZ2); count_launch(); }
+  { head_back_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->dout, s->pb + s->off_w3(), s->Z2, B, H, s->dZ2, s->dZ2b, Hp, s->dZ2T, Bt); count_launch(); }
   // gW2[h][k] = sum_b dZ2[b][h] A1[b][k]
-  gemm<float, bf16>(H, H, B, s->dZ2, 1, H, s->A1, H, 1, nullptr, gW2, H, st);
+  STRY(tc_gemm_bf16(s->dZ2T, Bt, s->A1T, Bt, H, H, (int)B, gW2, H, nullptr, s->err, st));
   { colsum_kernel<<<(unsigned)cdiv(H, 256), 256, 0, st>>>(s->dZ2, B, H, gb2); count_launch(); }
-  // dA1 = dZ2 W2 ; dZ1 = dA1 * gelu'(Z1)
-  gemm<float, bf16>(B, H, H, s->dZ2, H, 1, s->pb + s->off_W2(), H, 1, nullptr, s->dZ1, H, st);
-  { gelu_back_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->dZ1, s->Z1, B * H); count_launch(); }
+  // dA1[b][k] = sum_h dZ2[b][h] W2[h][k]; dZ1 = dA1 * gelu'(Z1)
+  STRY(tc_gemm_bf16(s->dZ2b, Hp, s->W2t, Hp, (int)B, H, H, s->dZ1, H, nullptr, s->err, st));
+  { gelu_back_kernel<<<(unsigned)cdiv(B * H, 256), 256, 0, st>>>(s->dZ1, s->Z1, B, H, s->dZ1T, Bt); count_launch(); }
   // gW1[h][d] = sum_b dZ1[b][h] Xs[b][d]
-  gemm<float, bf16>(H, D, B, s->dZ1, 1, H, s->Xs, D, 1, nullptr, gW1, D, st);
+  STRY(tc_gemm_bf16(s->dZ1T, Bt, s->XsT, Bt, H, D, (int)B, gW1, D, nullptr, s->err, st));
   { colsum_kernel<<<(unsigned)cdiv(H, 256), 256, 0, st>>>(s->dZ1, B, H, gb1); count_launch(); }
+  return GDML_OK;
 }
 
 }  // namespace
@@ -363,7 +398,14 @@ gdml_status gdml_scorer_create(gdml_scorer** out, int32_t D, int32_t hidden, uin
   STRY(salloc(S, &S->mu, (size_t)D));
   STRY(salloc(S, &S->sd, (size_t)D));
   STRY(salloc(S, &S->loss, 1));
+  S->Dp = pad8(D);
+  S->Hp = pad8(hidden);
+  STRY(salloc(S, &S->W1b, (size_t)(hidden * S->Dp)));
+  STRY(salloc(S, &S->W2b, (size_t)(hidden * S->Hp)));
+  STRY(salloc(S, &S->W2t, (size_t)(hidden * S->Hp)));
+  STRY(salloc(S, &S->err, 1));
   cudaStream_t st = S->st;
+  cudaMemsetAsync(S->err, 0, sizeof(int), st);
   auto init = [&](float* q, int64_t n, float a, uint64_t sd) {
     { init_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(q, n, a, sd); count_launch(); }
   };
@@ -376,6 +418,7 @@ gdml_status gdml_scorer_create(gdml_scorer** out, int32_t D, int32_t hidden, uin
   cudaMemsetAsync(S->m, 0, S->nparam * sizeof(float), st);
   cudaMemsetAsync(S->v, 0, S->nparam * sizeof(float), st);
   { to_bf16_kernel<<<(unsigned)cdiv(S->nparam, 256), 256, 0, st>>>(S->p, S->pb, S->nparam); count_launch(); }
+  pack_weights(S);
   std::vector<float> ones(D, 1.f);
   cudaMemsetAsync(S->mu, 0, D * sizeof(float), st);
   cudaMemcpyAsync(S->sd, ones.data(), D * sizeof(float), cudaMemcpyHostToDevice, st);
@@ -424,12 +467,14 @@ gdml_status gdml_scorer_train(gdml_scorer* s, const double* X_dev, const double*
   for (int ep = 0; ep < epochs; ++ep) {
     for (int64_t b0 = 0; b0 < B; b0 += bs) {
       const int64_t nb = std::min<int64_t>(bs, B - b0);
-      backward(s, X_dev + b0 * s->D, y_dev + b0, nb);
+      STRY(backward(s, X_dev + b0 * s->D, y_dev + b0, nb));
       ++s->step;
       const float bc1 = 1.f - std::pow(0.9f, (float)s->step), bc2 = 1.f - std::pow(0.999f, (float)s->step);
       { adam_kernel<<<(unsigned)cdiv(s->nparam, 256), 256, 0, s->st>>>(s->p, s->g, s->m, s->v, s->pb, s->nparam, (float)lr, bc1, bc2); count_launch(); }
+      pack_weights(s);
     }
   }
+  STRY(check_err(s));
   if (cudaMemcpyAsync(&last, s->loss, sizeof(float), cudaMemcpyDeviceToHost, s->st) != cudaSuccess ||
       cudaStreamSynchronize(s->st) != cudaSuccess)
     return fail(GDML_ERR_CUDA, "scorer: train");
@@ -445,11 +490,11 @@ gdml_status gdml_scorer_predict(gdml_scorer* s, const double* X_dev, int64_t B, 
   std::vector<float> h((size_t)bs);
   for (int64_t b0 = 0; b0 < B; b0 += bs) {
     const int64_t nb = std::min<int64_t>(bs, B - b0);
-    forward(s, X_dev + b0 * s->D, nb);
+    STRY(forward(s, X_dev + b0 * s->D, nb, false));
     launch_destandardize(s->out, nb, s->ym, s->ysd, out_dev + b0, s->st);
   }
   if (cudaStreamSynchronize(s->st) != cudaSuccess) return fail(GDML_ERR_CUDA, "scorer: predict");
-  return GDML_OK;
+  return check_err(s);
 }
 
 // Test hook: loss (host) and gradient (device, nparam floats) on one batch.
@@ -458,13 +503,13 @@ gdml_status gdml_scorer_grad(gdml_scorer* s, const double* X_dev, const double* 
   clear_msg();
   if (!s || !X_dev || !y_dev || B < 1) return fail(GDML_ERR_ARG, "scorer: bad arguments");
   STRY(ensure_batch(s, B));
-  backward(s, X_dev, y_dev, B);
+  STRY(backward(s, X_dev, y_dev, B));
   float l = 0.f;
   if (grad_dev) cudaMemcpyAsync(grad_dev, s->g, s->nparam * sizeof(float), cudaMemcpyDeviceToDevice, s->st);
   cudaMemcpyAsync(&l, s->loss, sizeof(float), cudaMemcpyDeviceToHost, s->st);
   if (cudaStreamSynchronize(s->st) != cudaSuccess) return fail(GDML_ERR_CUDA, "scorer: grad");
   if (loss_out) *loss_out = l;
-  return GDML_OK;
+  return check_err(s);
 }
 
 // Get (set = 0) or set (set = 1) the flat FP32 parameters (device, nparam floats).
@@ -475,6 +520,7 @@ gdml_status gdml_scorer_params(gdml_scorer* s, float* params_dev, int32_t set, i
   if (set) {
     cudaMemcpyAsync(s->p, params_dev, s->nparam * sizeof(float), cudaMemcpyDeviceToDevice, s->st);
     { to_bf16_kernel<<<(unsigned)cdiv(s->nparam, 256), 256, 0, s->st>>>(s->p, s->pb, s->nparam); count_launch(); }
+    pack_weights(s);
   } else {
     cudaMemcpyAsync(params_dev, s->p, s->nparam * sizeof(float), cudaMemcpyDeviceToDevice, s->st);
   }

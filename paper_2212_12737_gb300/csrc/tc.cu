@@ -468,6 +468,34 @@ static gdml_status gemm_test_impl(const double* A, const double* B, int M, int N
   return s;
 }
 
+// C[row][col] = bias[col] + sum_k A[row][k] B[col][k], FP32, for any M, N, K (rows beyond M and
+// columns beyond N are masked; K beyond the operands reads the TMA fill value, zero)
+struct EpiStoreBias {
+  float* C;
+  int64_t ld;
+  const float* bias;
+  __device__ __forceinline__ void operator()(int row, int col0, float (&v)[32], int valid, int) const {
+    float* dst = C + (int64_t)row * ld + col0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < valid) dst[j] = v[j] + (bias ? bias[col0 + j] : 0.f);
+  }
+};
+
+gdml_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K, float* C,
+                         int64_t ldc, const float* bias, int* err, cudaStream_t st) {
+  if (M < 1 || N < 1 || K < 1 || lda % 8 || ldb % 8 || lda < K || ldb < K ||
+      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+    return fail(GDML_ERR_ARG, "tc_gemm_bf16: operands need 16-byte aligned bases and strides >= K, multiples of 8");
+  CUtensorMap mA, mB;
+  const int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  if (!make_kmajor_map(&mA, A, true, (uint64_t)K, (uint64_t)M, (uint64_t)lda, BM) ||
+      !make_kmajor_map(&mB, B, true, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, (uint32_t)bn))
+    return fail(GDML_ERR_CUDA, "tc_gemm_bf16: cuTensorMapEncodeTiled failed");
+  EpiStoreBias e{C, ldc, bias};
+  return gemm_dispatch_bn<true>(bn, mA, mB, M, N, (int)cdiv(K, 64), 1, e, err, st);
+}
+
 gdml_status tc_gemm_test(int bf16, const double* A, const double* B, int M, int N, int K, double* C,
                          cudaStream_t st) {
   return bf16 ? gemm_test_impl<true>(A, B, M, N, K, C, st) : gemm_test_impl<false>(A, B, M, N, K, C, st);

@@ -58,6 +58,12 @@ bool make_kmajor_map(CUtensorMap* m, const void* base, bool bf16, uint64_t K, ui
 bool make_f32_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
                   uint32_t box_inner, uint32_t box_outer);
 
+// C (M x N, FP32, row stride ldc) = A B^T (+ bias per column) on the tcgen05 tensor cores (BF16
+// operands, FP32 accumulation): A M x K, B N x K, row-major BF16 with row strides lda, ldb that
+// are multiples of 8 elements and 16-byte aligned bases; any M, N, K.  err: a device int that a
+// bounded pipeline wait sets (checked by the caller).
+gdml_status tc_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K, float* C,
+                         int64_t ldc, const float* bias, int* err, cudaStream_t st);
 // test hook: C (M x N, fp64) = A (M x K) B (N x K)^T with operands rounded to TF32 / BF16
 gdml_status tc_gemm_test(int bf16, const double* A, const double* B, int M, int N, int K, double* C,
                          cudaStream_t st);

@@ -1,7 +1,9 @@
-"""Learned inducing-column scorer: BF16 MLP kernels against a PyTorch CPU FP32
-reference with the same BF16 roundings (straight-through gradients), the
-RLS labels against the oracle, and the learned selection with pivoted
-Cholesky as fallback and referee."""
+"""Learned inducing-column scorer: BF16 MLP kernels (the five contractions on the tcgen05
+tensor cores) against a PyTorch CPU FP32 reference with the same forward BF16 roundings
+(straight-through gradients). The GPU's backward pass also rounds the back-propagated
+gradients to BF16 (they are tensor-core operands): relative 2^-9 per entry, well inside the
+gradient tolerance. Then the RLS labels against the oracle, and the learned selection with
+pivoted Cholesky as fallback and referee."""
 import numpy as np
 import pytest
 import torch
