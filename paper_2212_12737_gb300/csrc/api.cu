@@ -233,7 +233,7 @@ gdml_status matvec_any(gdml_ctx* c, const double* v, double* out, int add_lambda
   if (force_fp64 || c->precision == GDML_FP64) return matvec_fp64(c, v, out, add_lambda);
   if (c->precision == GDML_DF64) return matvec_df(c, v, out, add_lambda);
   if (c->precision == GDML_OZAKI) {
-    gdml_status s = oz_matvec(c->oz, c->G, c->Xc(), v, out, add_lambda, c->lam, c->st, lev);
+    gdml_status s = oz_matvec(c->oz, c->G, c->G2, c->Xc(), v, out, add_lambda, c->lam, c->st, lev);
     if (s != GDML_OK) return ctx_fail(c, s, "sliced tensor-core matvec: " + last_msg());
     return check_launch(c, "matvec_oz");
   }

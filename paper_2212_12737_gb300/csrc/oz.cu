@@ -189,6 +189,10 @@ __global__ void __launch_bounds__(256) oz_slice_rows_f32_kernel(const float* __r
   slice_write(make_float2(x, 0.f), ex, sl, row, k, Rp, Kp);
 }
 
+// an entry as a float pair (hi, lo) with hi + lo = x (FP64: rounded to 48 bits)
+__device__ __forceinline__ float2 as_pair(double x) { return split_d(x); }
+__device__ __forceinline__ float2 as_pair(float2 x) { return x; }
+
 // Slicing of a COLUMN-major source: operand row r (r < rows) is row r0 + r of the n x K
 // matrix whose column j starts at src + j ld, i.e. entry (r, j) = src[j ld + r0 + r].  One
 // CTA per 16 rows and one 256-entry chunk: coalesced reads down the columns into a shared
@@ -208,9 +212,9 @@ __global__ void __launch_bounds__(256) oz_slice_cols_kernel(const T* __restrict_
     for (int jj = tid / RB; jj < oz::KC; jj += 256 / RB) {
       const int64_t j = q * oz::KC + jj;
       const int64_t row = rb + r;
-      double x = 0.0;
-      if (j < K && row < rows) x = (double)src[j * ld + r0 + row];
-      tile[jj][r] = split_d(x);
+      float2 x = make_float2(0.f, 0.f);
+      if (j < K && row < rows) x = as_pair(src[j * ld + r0 + row]);
+      tile[jj][r] = x;
     }
   }
   __syncthreads();
@@ -242,113 +246,99 @@ __global__ void oz_rowsq_reduce_kernel(const double* __restrict__ sq, int slots,
   out[i] = s;
 }
 
-// W_a = J_a v_a and t_a = xc_a . w_a (as the FP64 projection), fused with the slicing of
-// row a of W into GEMM 1's B operand when it is one chunk (Kp <= 256): one CTA per geometry,
-// thread p holds w_p, the chunk exponent and t_a are CTA reductions; t_a is also written as
-// a double-float pair.
-__global__ void __launch_bounds__(256) oz_proj_slice_kernel(const double* __restrict__ G, const double* __restrict__ Xc,
-                                                            const double* __restrict__ v, int64_t M, int N, int D,
-                                                            double* __restrict__ W, double* __restrict__ t,
-                                                            float2* __restrict__ t2, int64_t Rp, int64_t Kp,
-                                                            bf16* __restrict__ sl, int* __restrict__ e) {
-  extern __shared__ double sv[];  // 3N
-  __shared__ float red[8];
-  __shared__ double redt[8];
-  const int64_t a = blockIdx.x;
-  const int p = threadIdx.x, warp = p >> 5, lane = p & 31;
-  const int B = 3 * N;
-  const double* Ga = G + a * D * 3;
-  double g0 = 0.0, g1 = 0.0, g2 = 0.0, xc = 0.0;
-  if (p < D) {
-    g0 = Ga[3 * p];
-    g1 = Ga[3 * p + 1];
-    g2 = Ga[3 * p + 2];
-    xc = Xc[a * D + p];
-  }
-  for (int l = p; l < B; l += blockDim.x) sv[l] = v[a * B + l];
-  __syncthreads();
-  double w = 0.0;
-  if (p < D) {
-    int i, j;
-    pair_of(p, i, j);
-    w = -(g0 * (sv[3 * i] - sv[3 * j]) + g1 * (sv[3 * i + 1] - sv[3 * j + 1]) + g2 * (sv[3 * i + 2] - sv[3 * j + 2]));
-    W[a * D + p] = w;
-  }
-  double part = xc * w;
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (lane == 0) redt[warp] = part;
-  const float2 xs = split_d(w);
-  const int ex = chunk_exponent(fabsf(xs.x), red);  // contains a __syncthreads (redt visible)
-  if (p == 0) {
-    double s = redt[0];
-    for (int k = 1; k < 8; ++k) s += redt[k];
-    t[a] = s;
-    t2[a] = split_d(s);
-    e[a] = ex;  // chunk 0 of row a
-  }
-  slice_write(xs, ex, sl, a, p, Rp, Kp);
+// (h, l) = (ah, al) - (bh, bl)
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float& h, float& l) {
+  float s, e;
+  two_sum(ah, -bh, s, e);
+  e = __fadd_rn(e, __fsub_rn(al, bl));
+  fast_two_sum(s, e, h, l);
 }
 
-// The same for rows of up to kProjChunks chunks (D <= 1024): one CTA of 256 threads per
-// geometry, every load of the row (3 G entries and xc per descriptor) issued before the first
-// chunk is computed; per chunk, w, its exponent (a CTA reduction) and its slices.  W and the
-// slices are those of the separate projection and slicing; t sums thread by thread over the
-// chunks, then over the CTA in a fixed order.
+// Sum of (h, l) over the 256 threads of the CTA in double-float, in a fixed order (valid in
+// thread 0); red2 holds 8 pairs.
+__device__ __forceinline__ void cta_df_sum(float& h, float& l, float2* red2) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, oh, ol);
+  }
+  if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = make_float2(h, l);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    h = red2[0].x;
+    l = red2[0].y;
+    for (int w = 1; w < 8; ++w) df_add(h, l, red2[w].x, red2[w].y);
+  }
+}
+
+// The projection W_a = J_a v_a, t_a = xc_a . w_a (the matvec's first step, Sec. 2.1) in
+// double-float arithmetic, fused with the slicing of row a of W into GEMM 1's B operand
+// (rows of up to kProjChunks 256-entry chunks).  GB300's FP64 pipe runs at ~1/64 of the FP32
+// rate, so the FP64 form of this kernel was FP64-pipe bound; here every operation is an
+// FP32 error-free transformation (TwoSum, FMA-based TwoProduct) on float pairs, ~2^-48
+// relative, below the slicing's own 2^-43 per chunk.  G2, Xc2: the Jacobian factors and the
+// centred descriptors as float pairs; v is split once per geometry in shared memory.  One
+// CTA of 256 threads per geometry, every load of the row issued before the first chunk;
+// per chunk, w as a float pair (also stored, Wf, for GEMM 2's transposed operand), its
+// exponent (a CTA reduction of the high parts) and its slices.
 constexpr int kProjChunks = 4;
-__global__ void __launch_bounds__(256) oz_proj_slice_multi_kernel(const double* __restrict__ G,
-                                                                  const double* __restrict__ Xc,
-                                                                  const double* __restrict__ v, int64_t M, int N,
-                                                                  int D, int nchunks, double* __restrict__ W,
-                                                                  double* __restrict__ t, float2* __restrict__ t2,
-                                                                  int64_t Rp, int64_t Kp, bf16* __restrict__ sl,
-                                                                  int* __restrict__ e) {
-  extern __shared__ double sv[];  // 3N
+__global__ void __launch_bounds__(256) oz_proj_slice_df_kernel(const float2* __restrict__ G2,
+                                                               const float2* __restrict__ Xc2,
+                                                               const double* __restrict__ v, int64_t M, int N, int D,
+                                                               int nchunks, float2* __restrict__ Wf,
+                                                               double* __restrict__ t, float2* __restrict__ t2,
+                                                               int64_t Rp, int64_t Kp, bf16* __restrict__ sl,
+                                                               int* __restrict__ e) {
+  extern __shared__ float2 sv2[];  // 3N
   __shared__ float red[8];
-  __shared__ double redt[8];
+  __shared__ float2 red2[8];
   const int64_t a = blockIdx.x;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   const int B = 3 * N;
-  const double* Ga = G + a * D * 3;
-  double g[kProjChunks][3], xc[kProjChunks];
+  const float2* Ga = G2 + a * D * 3;
+  float2 g[kProjChunks][3], xc[kProjChunks];
 #pragma unroll
   for (int q = 0; q < kProjChunks; ++q) {
     const int p = q * oz::KC + tid;
     const bool in = q < nchunks && p < D;
-    g[q][0] = in ? Ga[3 * p] : 0.0;
-    g[q][1] = in ? Ga[3 * p + 1] : 0.0;
-    g[q][2] = in ? Ga[3 * p + 2] : 0.0;
-    xc[q] = in ? Xc[a * D + p] : 0.0;
+    const float2 z = make_float2(0.f, 0.f);
+    g[q][0] = in ? Ga[3 * p] : z;
+    g[q][1] = in ? Ga[3 * p + 1] : z;
+    g[q][2] = in ? Ga[3 * p + 2] : z;
+    xc[q] = in ? Xc2[a * D + p] : z;
   }
-  for (int l = tid; l < B; l += blockDim.x) sv[l] = v[a * B + l];
+  for (int l = tid; l < B; l += blockDim.x) sv2[l] = split_d(v[a * B + l]);
   __syncthreads();
-  double part = 0.0;
+  float th = 0.f, tl = 0.f;
 #pragma unroll
   for (int q = 0; q < kProjChunks; ++q) {
     if (q >= nchunks) break;
     const int p = q * oz::KC + tid;
-    double w = 0.0;
+    float wh = 0.f, wl = 0.f;
     if (p < D) {
       int i, j;
       pair_of(p, i, j);
-      w = -(g[q][0] * (sv[3 * i] - sv[3 * j]) + g[q][1] * (sv[3 * i + 1] - sv[3 * j + 1]) +
-            g[q][2] * (sv[3 * i + 2] - sv[3 * j + 2]));
-      W[a * D + p] = w;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {  // w -= g_c (v_ic - v_jc)
+        const float2 vi = sv2[3 * i + c], vj = sv2[3 * j + c];
+        float dh, dl, ph, pl;
+        df_sub(vi.x, vi.y, vj.x, vj.y, dh, dl);
+        df_mul(g[q][c].x, g[q][c].y, dh, dl, ph, pl);
+        df_add(wh, wl, -ph, -pl);
+      }
+      Wf[a * D + p] = make_float2(wh, wl);
+      float ph, pl;
+      df_mul(xc[q].x, xc[q].y, wh, wl, ph, pl);
+      df_add(th, tl, ph, pl);
     }
-    part = fma(xc[q], w, part);
-    const float2 xs = split_d(w);
-    const int ex = chunk_exponent(fabsf(xs.x), red);  // contains a __syncthreads
+    const int ex = chunk_exponent(fabsf(wh), red);  // contains a __syncthreads
     if (tid == 0) e[q * M + a] = ex;
-    slice_write(xs, ex, sl, a, p, Rp, Kp);
+    slice_write(make_float2(wh, wl), ex, sl, a, p, Rp, Kp);
     __syncthreads();  // red is reused by the next chunk's reduction
   }
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (lane == 0) redt[warp] = part;
-  __syncthreads();
+  cta_df_sum(th, tl, red2);
   if (tid == 0) {
-    double s2 = redt[0];
-    for (int k = 1; k < 8; ++k) s2 += redt[k];
-    t[a] = s2;
-    t2[a] = split_d(s2);
+    t[a] = (double)th + (double)tl;
+    t2[a] = make_float2(th, tl);
   }
 }
 
@@ -1200,23 +1190,53 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
   }
 }
 
-// (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a); U_a and rowsum_a summed from
-// their double-float partials, the rest in FP64.  One CTA of 256 threads per geometry (one
-// 864-thread CTA per geometry measured 1.8x slower at D = 861): thread p forms the
-// descriptor's term w_p = g_p u_p (its three coordinate derivatives times u_p; coalesced
-// loads of G), then thread (i, c) sums the N - 1 pair terms of atom i from shared memory
-// (the derivative of x_p with respect to its first atom i > j carries the minus sign).
-__global__ void __launch_bounds__(256) oz_backproj_kernel(const float2* __restrict__ Up, int nsplit, int64_t M, int D,
-                                                          const float2* __restrict__ rs2, int nrs,
-                                                          const double* __restrict__ Xc, const double* __restrict__ G,
-                                                          const double* __restrict__ v, int N, double lam,
-                                                          int add_lambda, double* __restrict__ out) {
-  extern __shared__ double w3[];  // [D][3]: first (U_ap, xc_ap, -), then the terms g_p u_p
-  __shared__ double rs;
+// (K v)_a = J_a^T (U_a - rowsum_a xc_a) (+ lambda v_a) in double-float arithmetic (the FP64
+// form of this kernel was bound by GB300's FP64 pipe).  U_a and rowsum_a are summed from
+// their double-float partials; xc_a and the Jacobian factors come as float pairs (Xc2, G2).
+// One CTA of 256 threads per geometry: thread p issues every load of its descriptors
+// (up to kBackDesc per thread in registers, the rest in a loop), forms w_p = g_p u_p with
+// u_p = U_ap - rowsum_a xc_ap; then two lanes per output (atom i, coordinate c) sum halves
+// of the N - 1 pair terms from shared memory (the derivative of x_p with respect to its
+// first atom i > j carries the minus sign), combined by one shuffle; the FP64 result is
+// hi + lo (+ lambda v in FP64).
+constexpr int kBackDesc = 4;
+__global__ void __launch_bounds__(256) oz_backproj_df_kernel(const float2* __restrict__ Up, int nsplit, int64_t M,
+                                                             int D, const float2* __restrict__ rs2, int nrs,
+                                                             const float2* __restrict__ Xc2,
+                                                             const float2* __restrict__ G2,
+                                                             const double* __restrict__ v, int N, double lam,
+                                                             int add_lambda, double* __restrict__ out) {
+  extern __shared__ float2 w3f[];  // [D][3]: the terms g_p u_p
+  __shared__ float2 rs;
   const int64_t a = blockIdx.x;
-  if (threadIdx.x < 32) {
+  const int tid = threadIdx.x;
+  const float2* Ga = G2 + a * D * 3;
+  const float2* Ua = Up + a * D;
+  const int64_t sstride = M * D;
+  const float2 z = make_float2(0.f, 0.f);
+  // the first kBackDesc descriptors of this thread: every load in one round
+  float2 g[kBackDesc][3], xc[kBackDesc], u[kBackDesc];
+#pragma unroll
+  for (int q = 0; q < kBackDesc; ++q) {
+    const int p = q * 256 + tid;
+    const bool in = p < D;
+    g[q][0] = in ? Ga[3 * p] : z;
+    g[q][1] = in ? Ga[3 * p + 1] : z;
+    g[q][2] = in ? Ga[3 * p + 2] : z;
+    xc[q] = in ? Xc2[a * D + p] : z;
+    u[q] = in ? Ua[p] : z;
+  }
+  for (int s = 1; s < nsplit; ++s) {
+#pragma unroll
+    for (int q = 0; q < kBackDesc; ++q) {
+      const int p = q * 256 + tid;
+      const float2 w = p < D ? Ua[s * sstride + p] : z;
+      df_add(u[q].x, u[q].y, w.x, w.y);
+    }
+  }
+  if (tid < 32) {
     float h = 0.f, l = 0.f;
-    for (int q = threadIdx.x; q < nrs; q += 32) {
+    for (int q = tid; q < nrs; q += 32) {
       const float2 p = rs2[(int64_t)q * M + a];
       df_add(h, l, p.x, p.y);
     }
@@ -1224,52 +1244,59 @@ __global__ void __launch_bounds__(256) oz_backproj_kernel(const float2* __restri
       const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
       df_add(h, l, oh, ol);
     }
-    if (threadIdx.x == 0) rs = (double)h + (double)l;
-  }
-  // every load of the geometry in one round: U partials, xc_p and (first descriptor of each
-  // thread, the only one when D <= blockDim) g_p into registers
-  const double* Ga = G + a * D * 3;
-  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-  if ((int)threadIdx.x < D) {
-    g0 = Ga[3 * threadIdx.x];
-    g1 = Ga[3 * threadIdx.x + 1];
-    g2 = Ga[3 * threadIdx.x + 2];
-  }
-  for (int p = threadIdx.x; p < D; p += blockDim.x) {
-    float h = 0.f, l = 0.f;
-    for (int s = 0; s < nsplit; ++s) {
-      const float2 u = Up[((int64_t)s * M + a) * D + p];
-      df_add(h, l, u.x, u.y);
-    }
-    w3[3 * p] = (double)h + (double)l;
-    w3[3 * p + 1] = Xc[a * D + p];
+    if (tid == 0) rs = make_float2(h, l);
   }
   __syncthreads();
-  for (int p = threadIdx.x; p < D; p += blockDim.x) {
-    const double u = w3[3 * p] - rs * w3[3 * p + 1];
-    if (p >= (int)blockDim.x) {  // later descriptors of this thread (D > blockDim)
-      g0 = Ga[3 * p];
-      g1 = Ga[3 * p + 1];
-      g2 = Ga[3 * p + 2];
+  const float2 r = rs;
+  auto term = [&](int p, float2 uu, const float2 (&gg)[3], float2 xx) {
+    float ph, pl, uh = uu.x, ul = uu.y;
+    df_mul(r.x, r.y, xx.x, xx.y, ph, pl);
+    df_add(uh, ul, -ph, -pl);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float wh, wl;
+      df_mul(gg[c].x, gg[c].y, uh, ul, wh, wl);
+      w3f[3 * p + c] = make_float2(wh, wl);
     }
-    w3[3 * p] = g0 * u;
-    w3[3 * p + 1] = g1 * u;
-    w3[3 * p + 2] = g2 * u;
+  };
+#pragma unroll
+  for (int q = 0; q < kBackDesc; ++q) {
+    const int p = q * 256 + tid;
+    if (p < D) term(p, u[q], g[q], xc[q]);
+  }
+  for (int p = kBackDesc * 256 + tid; p < D; p += 256) {  // D > 1024: the rest, one at a time
+    float2 uu = Ua[p];
+    for (int s = 1; s < nsplit; ++s) {
+      const float2 w = Ua[s * sstride + p];
+      df_add(uu.x, uu.y, w.x, w.y);
+    }
+    const float2 gg[3] = {Ga[3 * p], Ga[3 * p + 1], Ga[3 * p + 2]};
+    term(p, uu, gg, Xc2[a * D + p]);
   }
   __syncthreads();
   const int B = 3 * N;
-  for (int l = threadIdx.x; l < B; l += blockDim.x) {
-    const int i = l / 3, qd = l - 3 * i;
-    double s = 0.0;
-#pragma unroll 4
-    for (int j = 0; j < N; ++j) {
-      const bool skip = j == i;
-      const int p = skip ? 0 : (i > j ? i * (i - 1) / 2 + j : j * (j - 1) / 2 + i);
-      const double wj = w3[3 * p + qd];
-      s += skip ? 0.0 : ((i > j) ? -wj : wj);
+  const int half = tid & 1;
+  for (int o0 = 0; o0 < B; o0 += 128) {  // every lane pair runs the same trip count
+    const int o = o0 + (tid >> 1);
+    float h = 0.f, l = 0.f;
+    if (o < B) {
+      const int i = o / 3, qd = o - 3 * i;
+      for (int j = half; j < N; j += 2) {
+        if (j == i) continue;
+        const float2 w = w3f[3 * pair_idx(i, j) + qd];
+        if (i > j)
+          df_add(h, l, -w.x, -w.y);
+        else
+          df_add(h, l, w.x, w.y);
+      }
     }
-    if (add_lambda) s = fma(lam, v[a * B + l], s);
-    out[a * B + l] = s;
+    const float oh = __shfl_xor_sync(0xffffffffu, h, 1), ol = __shfl_xor_sync(0xffffffffu, l, 1);
+    df_add(h, l, oh, ol);
+    if (o < B && half == 0) {
+      double s = (double)h + (double)l;
+      if (add_lambda) s = fma(lam, v[a * B + o], s);
+      out[a * B + o] = s;
+    }
   }
 }
 
@@ -1405,6 +1432,8 @@ gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, co
   OZ_TRY(make_operand(oz, oz.B2, M, MB, oz::BM, st));
   OZ_TRY(make_operand(oz, oz.XT2, D, MB, oz::BN, st));
   OZ_TRY(oz_alloc(oz, &oz.W, (size_t)(M * D), st));
+  OZ_TRY(oz_alloc(oz, &oz.Wf, (size_t)(M * D), st));
+  OZ_TRY(oz_alloc(oz, &oz.Xc2, (size_t)(M * D), st));
   if (Ssym > 1) OZ_TRY(oz_alloc(oz, &oz.WB, (size_t)(MB * D), st));
   OZ_TRY(oz_alloc(oz, &oz.WT, (size_t)(MB * D), st));
   OZ_TRY(oz_alloc(oz, &oz.t, (size_t)MB, st));
@@ -1416,8 +1445,10 @@ gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, co
   OZ_TRY(oz_alloc(oz, &oz.err, 1, st));
   oz.g1 = oz_auto_chunks_per_cta(cdiv(MB, oz::BN) * cdiv(M, oz::BM), oz.W1.nchunks);
   oz.g2 = oz_auto_chunks_per_cta(cdiv(D, oz::BN) * cdiv(M, oz::BM), oz.A2.nchunks);
-  // fixed operands: Xc (GEMM 1 A), A (GEMM 2 A, segment 1), XcB^T (GEMM 2 B, segment 2), c^2 S
+  // fixed operands: Xc (GEMM 1 A), A (GEMM 2 A, segment 1), XcB^T (GEMM 2 B, segment 2), c^2 S;
+  // Xc as float pairs for the projection and the back-projection
   slice_rows(Xc, D, oz.Xc1, st);
+  launch_split_df(Xc, M * D, oz.Xc2, st);
   slice_rows(A, ldA, oz.A2, st);
   transpose(oz.XcB, MB, D, D, oz.WT, st);
   slice_rows(oz.WT, MB, oz.XT2, st);
@@ -1427,27 +1458,30 @@ gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, co
   return GDML_OK;
 }
 
-gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
-                      int add_lambda, double lam, cudaStream_t st, int lev) {
+gdml_status oz_matvec(OzMatvec& oz, const double* G, const float2* G2, const double* Xc, const double* v,
+                      double* out, int add_lambda, double lam, cudaStream_t st, int lev) {
   if (!oz.ready) return fail(GDML_ERR_STATE, "sliced matvec not set up");
+  if (!G2) return fail(GDML_ERR_ARG, "sliced matvec: the float-pair Jacobian factors are missing");
   const int64_t M = oz.M, MB = oz.MB;
   const int D = oz.D;
-  const double* WB = oz.W;  // the training side's projection (MB x D)
   if (oz.S > 1) {  // w_b = J_b v_b, then row b S + q = P_q w_b with t = xc_(bS+q) . w_(bS+q)
     launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
     launch_sym_gather(oz.W, M, D, oz.pis, oz.S, oz.XcB, oz.WB, oz.t, st);
     slice_rows(oz.WB, D, oz.W1, st, oz.t, oz.t2);
-    WB = oz.WB;
-  } else if (oz.W1.Kp <= oz::KC) {  // one chunk per row: projection and slicing in one kernel
-    { oz_proj_slice_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(double), st>>>(G, Xc, v, M, oz.N, D, oz.W, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
-  } else if (oz.W1.nchunks <= kProjChunks) {  // up to 4 chunks per row: likewise, chunk by chunk
-    { oz_proj_slice_multi_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(double), st>>>(G, Xc, v, M, oz.N, D, (int)oz.W1.nchunks, oz.W, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
+    transpose(oz.WB, MB, D, D, oz.WT, st);
+    slice_rows(oz.WT, MB, oz.WT2, st);
+  } else if (oz.W1.nchunks <= kProjChunks) {
+    // projection and slicing of W's rows in one kernel (double-float), then W^T's rows sliced
+    // straight from the float pairs of W (a column slicing: no transposed copy)
+    { oz_proj_slice_df_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(float2), st>>>(G2, oz.Xc2, v, M, oz.N, D, (int)oz.W1.nchunks, oz.Wf, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
+    dim3 g((unsigned)cdiv(D, 16), (unsigned)oz.WT2.nchunks);
+    { oz_slice_cols_kernel<float2><<<g, 256, 0, st>>>(oz.Wf, D, 0, D, MB, oz.WT2.Rp, oz.WT2.Kp, (bf16*)oz.WT2.slices, oz.WT2.e); count_launch(); }
   } else {
     launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
     slice_rows(oz.W, D, oz.W1, st, oz.t, oz.t2);
+    transpose(oz.W, MB, D, D, oz.WT, st);
+    slice_rows(oz.WT, MB, oz.WT2, st);
   }
-  transpose(WB, MB, D, D, oz.WT, st);
-  slice_rows(oz.WT, MB, oz.WT2, st);
   int groups1 = 0, groups2 = 0;
   OZ_TRY(oz_gemm(oz.Xc1, oz.W1, oz.Tp, MB, M * MB, oz.err, st, oz.g1, &groups1, lev));
   {
@@ -1457,10 +1491,10 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const dou
   const int64_t nch = oz.A2.nchunks;
   OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st, oz.g2, &groups2, lev));
   OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + (int64_t)groups2 * M * D, D, M * D, oz.err, st, oz.g2, nullptr, lev));
-  const size_t smem = 3 * (size_t)D * sizeof(double);
+  const size_t smem = 3 * (size_t)D * sizeof(float2);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(oz_backproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { oz_backproj_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, Xc, G, v, oz.N, lam, add_lambda, out); count_launch(); }
+    cudaFuncSetAttribute(oz_backproj_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  { oz_backproj_df_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, oz.Xc2, G2, v, oz.N, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced matvec kernels");
   return GDML_OK;
 }

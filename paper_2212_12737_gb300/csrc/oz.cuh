@@ -19,8 +19,8 @@
 //     2^(eA + eB), giving one double-float partial per chunk; partials are summed
 //     by the consumer.
 //
-// The nonlinear step between the GEMMs (beta = c^2 S (T - t)) and the
-// back-projection run in double-float / FP64.  Relative error of the matvec is
+// The projection, the nonlinear step between the GEMMs (beta = c^2 S (T - t)) and the
+// back-projection run in double-float arithmetic (GB300's FP64 pipe is ~1/64 of its FP32 rate).  Relative error of the matvec is
 // ~1e-14 (FP64-class), so the plain PCG reaches 1e-8 at lambda = 1e-10.
 #pragma once
 #include <cuda.h>
@@ -64,6 +64,8 @@ struct OzMatvec {
   OzOperand B2;   // GEMM 2 segment 2 A: beta (rows a, K = b), per matvec
   OzOperand XT2;  // GEMM 2 segment 2 B: Xc^T (rows d, K = b), fixed
   double* W = nullptr;    // M x D (FP64 projection)
+  float2* Wf = nullptr;   // M x D: the projection as float pairs (double-float path, S = 1)
+  float2* Xc2 = nullptr;  // M x D: the centred descriptors as float pairs
   double* WB = nullptr;   // MB x D: the projection on the training side (S > 1)
   double* WT = nullptr;   // D x MB
   double* t = nullptr;    // M: t_b = xc_b . w_b
@@ -83,11 +85,12 @@ struct OzMatvec {
 gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, const double* A, int64_t ldA,
                      const double* S, double c, cudaStream_t st, int Ssym = 1, const int* pis = nullptr,
                      const double* XcB = nullptr);
-// out = K v (+ lambda v); G, Xc: the context's FP64 Jacobian factors and centred descriptors.
-// lev < 7 keeps only the slice pairs i + j < lev in both contractions (a cheaper, less accurate
-// matvec for an inner solve)
-gdml_status oz_matvec(OzMatvec& oz, const double* G, const double* Xc, const double* v, double* out,
-                      int add_lambda, double lam, cudaStream_t st, int lev = oz::S);
+// out = K v (+ lambda v); G, Xc: the context's FP64 Jacobian factors and centred descriptors,
+// G2 the Jacobian factors as float pairs (the projection and back-projection run in
+// double-float arithmetic).  lev < 7 keeps only the slice pairs i + j < lev in both
+// contractions (a cheaper, less accurate matvec for an inner solve)
+gdml_status oz_matvec(OzMatvec& oz, const double* G, const float2* G2, const double* Xc, const double* v,
+                      double* out, int add_lambda, double lam, cudaStream_t st, int lev = oz::S);
 gdml_status oz_check(OzMatvec& oz, cudaStream_t st);
 void oz_destroy(OzMatvec& oz);
 
