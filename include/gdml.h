@@ -303,7 +303,8 @@ gdml_status gdml_pcg_solve_batched(gdml_ctx* const* ctxs, int32_t count, const d
  * contexts: times every power-of-two K-split (1 .. 8 or more) of the second descriptor
  * contraction (FP64 DGEMM or tcgen05 GEMM) and keeps the fastest.  OZAKI contexts: times the
  * number of 256-entry K chunks each CTA of the two sliced GEMMs accumulates in registers
- * (GEMM 1: 1 or all; GEMM 2: 1, 2, 3, 4, 8, ... up to all) and keeps the fastest pair.
+ * (GEMM 1: 1 or all; GEMM 2: 1, 2, 3, 4, 8, ... up to all, counting the chunks of both of its
+ * K segments when they run as one product) and keeps the fastest pair.
  * *choice_out (host, may be NULL) receives the choice (OZAKI: g1 * 65536 + g2) so that a
  * caller can cache it and restore it later with gdml_set_tuning.  Synchronises the
  * context's stream.  Errors: GDML_ERR_ARG, GDML_ERR_OOM, GDML_ERR_CUDA. */

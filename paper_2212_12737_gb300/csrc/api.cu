@@ -1568,7 +1568,7 @@ gdml_status gdml_autotune(gdml_ctx* c, int32_t* choice_out) {
       cudaEventElapsedTime(ms, e0, e1);
       return GDML_OK;
     };
-    const int n1 = (int)c->oz.W1.nchunks, n2 = (int)c->oz.A2.nchunks;
+    const int n1 = (int)c->oz.W1.nchunks, n2 = (int)c->oz.nch2;
     std::vector<int> cand2;
     for (int g = 1; g <= n2; g = g < 4 ? g + 1 : g * 2) cand2.push_back(g);
     if (cand2.back() != n2) cand2.push_back(n2);
@@ -1633,7 +1633,7 @@ gdml_status gdml_set_tuning(gdml_ctx* c, int32_t splits) {
   TRY(validate(c));
   if (c->precision == GDML_OZAKI) {  // g1 * 65536 + g2: K chunks per CTA of the two sliced GEMMs
     const int g1 = splits >> 16, g2 = splits & 0xFFFF;
-    if (g1 < 1 || g1 > c->oz.W1.nchunks || g2 < 1 || g2 > c->oz.A2.nchunks)
+    if (g1 < 1 || g1 > c->oz.W1.nchunks || g2 < 1 || g2 > c->oz.nch2)
       return ctx_fail(c, GDML_ERR_ARG, "chunks per CTA out of range");
     c->oz.g1 = g1;
     c->oz.g2 = g2;

@@ -423,7 +423,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int Ap,
                    int Bp, int M, int N, int num_kb, int chunks_per_cta, const int* __restrict__ eA,
                    const int* __restrict__ eB, float2* __restrict__ out, int64_t ldo, int64_t split_stride,
-                   int* __restrict__ err) {
+                   int* __restrict__ err, const __grid_constant__ CUtensorMap mapA2,
+                   const __grid_constant__ CUtensorMap mapB2, int Ap2, int Bp2, const int* __restrict__ eA2,
+                   const int* __restrict__ eB2, int kb_split) {
   constexpr int nlev = NLEV;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -479,7 +481,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- TMA producer, A slices (order 6, 5, ..., 0 within each k-block)
     int a_issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
-      const int kx = (kb_begin + kb) * oz::KB;
+      // k-blocks from kb_split on belong to the second K segment (its own operands)
+      const int gk = kb_begin + kb;
+      const bool seg2 = gk >= kb_split;
+      const CUtensorMap* mA = seg2 ? &mapA2 : &mapA;
+      const int kx = (seg2 ? gk - kb_split : gk) * oz::KB;
+      const int ap = seg2 ? Ap2 : Ap;
       bool ok = true;
       for (int pos = 0; pos < nlev; ++pos) {
         const int ai = kb * nlev + pos;
@@ -496,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc::mbar_expect_tx(&afull[s], kATile);
-        tc::tma_load_2d(sA + s * kATile, &mapA, &afull[s], kx, (nlev - 1 - pos) * Ap + m0);
+        tc::tma_load_2d(sA + s * kATile, mA, &afull[s], kx, (nlev - 1 - pos) * ap + m0);
         a_issued = ai + 1;
       }
       if (!ok) break;
@@ -517,10 +524,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto issue_b = [&](int kb) {  // lane 0; the buffer is known to be free
       b_issued = kb + 1;
       const int st2 = kb & 1;
-      const int kx = (kb_begin + kb) * oz::KB;
+      const int gk = kb_begin + kb;
+      const bool seg2 = gk >= kb_split;
+      const CUtensorMap* mB = seg2 ? &mapB2 : &mapB;
+      const int kx = (seg2 ? gk - kb_split : gk) * oz::KB;
+      const int bp = seg2 ? Bp2 : Bp;
       tc::mbar_expect_tx(&bfull[st2], nlev * kBTile);
       for (int j = 0; j < nlev; ++j)
-        tc::tma_load_2d(sB + st2 * kBGroupM + j * kBTile, &mapB, &bfull[st2], kx, j * Bp + n0);
+        tc::tma_load_2d(sB + st2 * kBGroupM + j * kBTile, mB, &bfull[st2], kx, j * bp + n0);
     };
     {
       // the first wait comes before the first copy (a fresh buffer's previous phase counts
@@ -671,13 +682,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kEpiThreads = 32 * kEpiWarps;
     // a chunk's 128 row and 64 column exponents into shared memory, one coalesced load each,
     // a chunk ahead of its drain (the drain then reads no global memory)
+    // chunks of the first K segment (a single segment may end on a half chunk: round up)
+    const int nch1 = (kb_split + kKbPerChunkM - 1) / kKbPerChunkM;
     auto load_exps = [&](int q) {
       int* dst = sexp + (q & 1) * kExpStage;
-      const int64_t zq = q_begin + q;
+      const int64_t zg = q_begin + q;
+      const bool seg2 = zg >= nch1;
+      const int* ea = seg2 ? eA2 : eA;
+      const int* eb = seg2 ? eB2 : eB;
+      const int64_t zq = seg2 ? zg - nch1 : zg;
       if (et < oz::BM)
-        dst[et] = m0 + et < M ? eA[zq * M + m0 + et] : 0;
+        dst[et] = m0 + et < M ? ea[zq * M + m0 + et] : 0;
       else if (et < kExpStage)
-        dst[et] = n0 + et - oz::BM < N ? eB[zq * N + n0 + et - oz::BM] : 0;
+        dst[et] = n0 + et - oz::BM < N ? eb[zq * N + n0 + et - oz::BM] : 0;
     };
     if (nq > 0) load_exps(0);
     float rh[kEpiCols], rl[kEpiCols], hh[kEpiCols], ll[kEpiCols];
@@ -1385,9 +1402,11 @@ int oz_auto_chunks_per_cta(int64_t tiles, int64_t nchunks) {
 }
 
 // C partials (groups of G chunks, one float2 slab per group at out + z split_stride) of
-// A B^T; *groups_out = number of slabs written
+// A B^T, or with a second pair (A2, B2) of A B^T + A2 B2^T as one product over the
+// concatenated K (A2 has A's rows, B2 B's); *groups_out = number of slabs written
 static gdml_status oz_gemm(const OzOperand& A, const OzOperand& B, float2* out, int64_t ldo, int64_t split_stride,
-                           int* err, cudaStream_t st, int G, int* groups_out = nullptr, int nlev = oz::S) {
+                           int* err, cudaStream_t st, int G, int* groups_out = nullptr, int nlev = oz::S,
+                           const OzOperand* A2 = nullptr, const OzOperand* B2 = nullptr) {
   static bool attr_set = false;
   if (!attr_set) {
     for (auto fn : {oz_gemm_kernel<1>, oz_gemm_kernel<2>, oz_gemm_kernel<3>, oz_gemm_kernel<4>, oz_gemm_kernel<5>,
@@ -1397,16 +1416,25 @@ static gdml_status oz_gemm(const OzOperand& A, const OzOperand& B, float2* out, 
     attr_set = true;
   }
   if (A.Kp != B.Kp) return fail(GDML_ERR_ARG, "sliced gemm: K mismatch");
-  if (A.Kp % oz::KB != 0) return fail(GDML_ERR_ARG, "sliced gemm: K padding");
+  if (A.Kp % oz::KB != 0 || (A2 && A.Kp % oz::KC != 0)) return fail(GDML_ERR_ARG, "sliced gemm: K padding");
   if (nlev < 1 || nlev > oz::S) return fail(GDML_ERR_ARG, "sliced gemm: levels outside 1..7");
-  G = std::max(1, std::min<int>(G, (int)A.nchunks));
-  const int groups = (int)cdiv(A.nchunks, G);
+  if (!A2 != !B2) return fail(GDML_ERR_ARG, "sliced gemm: the second segment needs both operands");
+  const OzOperand& SA = A2 ? *A2 : A;
+  const OzOperand& SB = B2 ? *B2 : B;
+  if (A2 && (SA.Kp != SB.Kp || SA.Kp % oz::KB != 0 || SA.rows != A.rows || SB.rows != B.rows))
+    return fail(GDML_ERR_ARG, "sliced gemm: second segment shape mismatch");
+  const int kb1 = (int)(A.Kp / oz::KB);
+  const int num_kb = kb1 + (A2 ? (int)(SA.Kp / oz::KB) : 0);
+  const int64_t nchunks = A.nchunks + (A2 ? SA.nchunks : 0);
+  G = std::max(1, std::min<int>(G, (int)nchunks));
+  const int groups = (int)cdiv(nchunks, G);
   dim3 grid((unsigned)cdiv(B.rows, oz::BN), (unsigned)cdiv(A.rows, oz::BM), (unsigned)groups);
   static void (*const kern[])(const CUtensorMap, const CUtensorMap, int, int, int, int, int, int, const int*,
-                              const int*, float2*, int64_t, int64_t, int*) = {
+                              const int*, float2*, int64_t, int64_t, int*, const CUtensorMap, const CUtensorMap, int,
+                              int, const int*, const int*, int) = {
       oz_gemm_kernel<1>, oz_gemm_kernel<2>, oz_gemm_kernel<3>, oz_gemm_kernel<4>,
       oz_gemm_kernel<5>, oz_gemm_kernel<6>, oz_gemm_kernel<7>};
-  { kern[nlev - 1]<<<grid, kThreads, kSmemTotalM, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, (int)(A.Kp / oz::KB), G, A.e, B.e, out, ldo, split_stride, err); count_launch(); }
+  { kern[nlev - 1]<<<grid, kThreads, kSmemTotalM, st>>>(A.map, B.map, (int)A.Rp, (int)B.Rp, (int)A.rows, (int)B.rows, num_kb, G, A.e, B.e, out, ldo, split_stride, err, SA.map, SB.map, (int)SA.Rp, (int)SB.Rp, SA.e, SB.e, A2 ? kb1 : num_kb); count_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GDML_ERR_CUDA, std::string("sliced gemm launch: ") + cudaGetErrorString(e));
   if (groups_out) *groups_out = groups;
@@ -1444,7 +1472,9 @@ gdml_status oz_setup(OzMatvec& oz, int64_t M, int N, int D, const double* Xc, co
   OZ_TRY(oz_alloc(oz, &oz.rs2, (size_t)(oz.A2.nchunks * M), st));
   OZ_TRY(oz_alloc(oz, &oz.err, 1, st));
   oz.g1 = oz_auto_chunks_per_cta(cdiv(MB, oz::BN) * cdiv(M, oz::BM), oz.W1.nchunks);
-  oz.g2 = oz_auto_chunks_per_cta(cdiv(D, oz::BN) * cdiv(M, oz::BM), oz.A2.nchunks);
+  oz.u_merged = oz.A2.Kp % oz::KC == 0;
+  oz.nch2 = oz.u_merged ? 2 * oz.A2.nchunks : oz.A2.nchunks;
+  oz.g2 = oz_auto_chunks_per_cta(cdiv(D, oz::BN) * cdiv(M, oz::BM), oz.nch2);
   // fixed operands: Xc (GEMM 1 A), A (GEMM 2 A, segment 1), XcB^T (GEMM 2 B, segment 2), c^2 S;
   // Xc as float pairs for the projection and the back-projection
   slice_rows(Xc, D, oz.Xc1, st);
@@ -1489,12 +1519,21 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const float2* G2, const dou
     { oz_beta_kernel<<<g, 256, 0, st>>>(oz.Tp, groups1, M, MB, oz.S2, oz.t2, oz.B2.Rp, oz.B2.Kp, (bf16*)oz.B2.slices, oz.B2.e, oz.rs2); count_launch(); }
   }
   const int64_t nch = oz.A2.nchunks;
-  OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st, oz.g2, &groups2, lev));
-  OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + (int64_t)groups2 * M * D, D, M * D, oz.err, st, oz.g2, nullptr, lev));
+  // U = A W + beta Xc: one product over the two K segments (when the first ends on a chunk
+  // boundary), else two launches whose partials follow one another
+  int nsplit2 = 0;
+  if (oz.u_merged) {
+    OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st, oz.g2, &groups2, lev, &oz.B2, &oz.XT2));
+    nsplit2 = groups2;
+  } else {
+    OZ_TRY(oz_gemm(oz.A2, oz.WT2, oz.Up, D, M * D, oz.err, st, oz.g2, &groups2, lev));
+    OZ_TRY(oz_gemm(oz.B2, oz.XT2, oz.Up + (int64_t)groups2 * M * D, D, M * D, oz.err, st, oz.g2, nullptr, lev));
+    nsplit2 = 2 * groups2;
+  }
   const size_t smem = 3 * (size_t)D * sizeof(float2);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(oz_backproj_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  { oz_backproj_df_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, 2 * groups2, M, D, oz.rs2, (int)nch, oz.Xc2, G2, v, oz.N, lam, add_lambda, out); count_launch(); }
+  { oz_backproj_df_kernel<<<(unsigned)M, 256, smem, st>>>(oz.Up, nsplit2, M, D, oz.rs2, (int)nch, oz.Xc2, G2, v, oz.N, lam, add_lambda, out); count_launch(); }
   if (cudaGetLastError() != cudaSuccess) return fail(GDML_ERR_CUDA, "sliced matvec kernels");
   return GDML_OK;
 }

@@ -2,7 +2,8 @@
 //
 // The two descriptor contractions of K v (the same algebra as the FP64 path),
 //   GEMM 1:  T = Xc W^T                              (M x M, K = D)
-//   GEMM 2:  U = A W + beta Xc                       (M x D, K = M, two segments)
+//   GEMM 2:  U = A W + beta Xc                       (M x D, K = M, two segments run as
+//                                                     one product over the concatenated K)
 // are computed by an error-free splitting in the manner of Ozaki, Ogita, Oishi and
 // Rump (2012), "Error-free transformations of matrix multiplication by using fast
 // routines of matrix multiplication and its applications":
@@ -76,6 +77,10 @@ struct OzMatvec {
   float2* rs2 = nullptr;  // [A2.nchunks][M] partial row sums of beta
   int* err = nullptr;
   int g1 = 1, g2 = 1;  // K chunks per CTA of GEMM 1 and GEMM 2 (tuned by gdml_autotune)
+  // GEMM 2's two segments (A W and beta Xc) run as one product over the concatenated K when
+  // the first ends on a 256-entry chunk boundary; nch2 = GEMM 2's chunks per output
+  bool u_merged = false;
+  int64_t nch2 = 0;
   std::vector<void*> allocs;
 };
 

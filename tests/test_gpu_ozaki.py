@@ -77,11 +77,15 @@ def test_sliced_gemm_row_scales_and_zero_rows():
 
 @pytest.mark.parametrize("name,N,M,sigma", [("tiny_N5_M3", 5, 3, 1.0), ("single_geometry_N6_M1", 6, 1, 2.0),
                                             ("two_atoms_N2_M7", 2, 7, 1.5), ("ragged_N7_M150", 7, 150, 3.0), ("ethanol9_m200", 9, 200, 10.0),
-                                            ("wide_N30_M64", 30, 64, 15.0), ("aspirin21_m1000", 21, 1000, 20.0)])
+                                            ("wide_N30_M64", 30, 64, 15.0), ("wider_N48_M40", 48, 40, 25.0),
+                                            ("aspirin21_m1000", 21, 1000, 20.0)])
 def test_ozaki_matvec_is_fp64_class(name, N, M, sigma):
-    """D = N(N - 1)/2 up to 435: one and several 256-entry chunks per descriptor row (the
-    projection fused with the slicing of W, or not), one or two descriptors per thread in
-    the back-projection."""
+    """D = N(N - 1)/2 up to 1128: one and several 256-entry chunks per descriptor row (the
+    projection fused with the slicing of W up to 4 chunks, the unfused FP64 projection
+    beyond), one to five descriptors per thread in the back-projection (the fifth through
+    its loop).  M <= 64 pads U's K to 128 entries, not to a whole 256-entry chunk, so U's two
+    products run as two launches; larger M runs them as one product over the concatenated
+    K."""
     if name.startswith("aspirin"):
         R = synth.workload("aspirin21_m1000").R
     else:
