@@ -38,7 +38,8 @@ constexpr int kWaiterWarp = 11;           // the accumulating GEMM's extra warp:
 constexpr int kThreadsAcc = 32 * 12;
 constexpr int kStageLd = oz::BN + 1;  // padded row of the staged output tile (float2)
 // matvec GEMM: k-blocks of 64 K entries (one 128-byte swizzle span per tile).  The B group of
-// a k-block (7 slices, 56 KB) is double-buffered; the A slices stream through a 6-deep ring.
+// a k-block (7 slices, 56 KB) is double-buffered; the A slices stream through a 6-deep ring
+// (a 7-deep ring, one whole k-block of look-ahead at 226.75 KB, measured no faster).
 constexpr int kBGroupM = oz::S * kBTile;                               // 56 KB
 constexpr int kBStagesM = 2;
 constexpr int kAStagesM = 6;
@@ -110,7 +111,10 @@ __device__ __forceinline__ float scale2(float x, int e) {
 
 // Slices of one entry (hi + lo) of a chunk whose magnitudes are all below 2^ex:
 // s_i = rint(y), y <- (y - s_i) * 2^7, starting from y = x 2^(7 - ex).  All
-// steps are exact; |s_1| <= 128 and |s_i| <= 64 for i > 1.
+// steps are exact; |s_1| <= 128 and |s_i| <= 64 for i > 1.  (y_h, y_l) stays normalised
+// (|y_l| <= ulp(y_h) / 2), and y_h - s_i is exact and either 0 or at least ulp(y_h), so
+// the exact sum (y_h - s_i) + y_l comes from Fast2Sum (its operand order holds or the
+// first operand is 0).
 __device__ __forceinline__ void slice_write(float2 xs, int ex, bf16* __restrict__ sl, int64_t row, int64_t k,
                                             int64_t Rp, int64_t Kp) {
   if (k >= Kp) return;
@@ -121,7 +125,7 @@ __device__ __forceinline__ void slice_write(float2 xs, int ex, bf16* __restrict_
     const float s = rintf(yh);
     sl[((int64_t)i * Rp + row) * Kp + k] = __float2bfloat16_rn(s);
     float h, l;
-    two_sum(__fsub_rn(yh, s), yl, h, l);
+    fast_two_sum(__fsub_rn(yh, s), yl, h, l);
     yh = __fmul_rn(h, up);
     yl = __fmul_rn(l, up);
   }
@@ -195,18 +199,19 @@ __device__ __forceinline__ float2 as_pair(float2 x) { return x; }
 
 // Slicing of a COLUMN-major source: operand row r (r < rows) is row r0 + r of the n x K
 // matrix whose column j starts at src + j ld, i.e. entry (r, j) = src[j ld + r0 + r].  One
-// CTA per 16 rows and one 256-entry chunk: coalesced reads down the columns into a shared
-// tile, a per-row exponent, then slice rows written along K (coalesced).
-template <typename T>
+// CTA per RB rows (16, or 4 when 16 would leave most SMs idle) and one 256-entry chunk:
+// coalesced reads down the columns into a shared tile, a per-row exponent, then slice rows
+// written along K (coalesced).
+template <typename T, int RB = 16>
 __global__ void __launch_bounds__(256) oz_slice_cols_kernel(const T* __restrict__ src, int64_t ld, int64_t r0,
                                                             int64_t rows, int64_t K, int64_t Rp, int64_t Kp,
                                                             bf16* __restrict__ sl, int* __restrict__ e) {
-  constexpr int RB = 16;
+  static_assert(RB <= 16 && 256 % RB == 0, "rows per CTA");
   __shared__ float2 tile[oz::KC][RB + 1];
   __shared__ int ex_s[RB];
   const int64_t rb = (int64_t)blockIdx.x * RB, q = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  {  // load: 16 threads per column read 16 consecutive rows
+  {  // load: RB threads per column read RB consecutive rows
     const int r = tid % RB;
 #pragma unroll 4
     for (int jj = tid / RB; jj < oz::KC; jj += 256 / RB) {
@@ -221,9 +226,10 @@ __global__ void __launch_bounds__(256) oz_slice_cols_kernel(const T* __restrict_
   {  // exponent of each row: warp w takes rows 2w and 2w + 1, 16 lanes per row
     const int r = 2 * warp + (lane >> 4);
     float m = 0.f;
-    for (int jj = lane & 15; jj < oz::KC; jj += 16) m = fmaxf(m, fabsf(tile[jj][r].x));
+    if (r < RB)
+      for (int jj = lane & 15; jj < oz::KC; jj += 16) m = fmaxf(m, fabsf(tile[jj][r].x));
     for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((lane & 15) == 0) {
+    if ((lane & 15) == 0 && r < RB) {
       int ex = 0;
       if (m > 0.f) (void)frexpf(m, &ex);
       ex_s[r] = ex;
@@ -403,7 +409,7 @@ __device__ __forceinline__ bool handoff(bool failed) {
 //    the next k-block's group while the current one is multiplied, and does every mbarrier
 //    wait of the MMA side: it hands each A tile to warp 1 at named barrier 2 (a wait or any
 //    shared-memory read in the MMA-issuing thread stalls the tensor pipe).
-//  * Warp 1 multiplies A slice i with B slices j = 0..6-i (4 MMAs per K step of 16) into TMEM
+//  * Warp 1 multiplies A slice i with B slices j = 0..6-i (per K step of 16) into TMEM
 //    accumulator i + j ("level"); the first k-block of a chunk overwrites level i with its
 //    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.  Up to four
 //    consecutive pairs (i, j .. j + 3) go into one MMA of N = 64 .. 256: 10 MMAs per K step
@@ -430,11 +436,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sB = smem;                           // [2] B groups
-  uint8_t* sA = smem + kBStagesM * kBGroupM;    // [6] A tiles
+  uint8_t* sA = smem + kBStagesM * kBGroupM;    // [kAStagesM] A tiles
   uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + kSmemDataM);  // [2]
   uint64_t* bempty = bfull + kBStagesM;                               // [2]
-  uint64_t* afull = bempty + kBStagesM;                               // [6]
-  uint64_t* aempty = afull + kAStagesM;                               // [6]
+  uint64_t* afull = bempty + kBStagesM;                               // [kAStagesM]
+  uint64_t* aempty = afull + kAStagesM;                               // [kAStagesM]
   uint64_t* cdone = aempty + kAStagesM;  // the MMAs of a chunk have completed
   uint64_t* tfree = cdone + 1;           // [7] the epilogue has read level L of a chunk
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfree + oz::S);
@@ -1107,8 +1113,14 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
   for (int64_t b0 = (int64_t)blockIdx.y * 1024 + 4 * threadIdx.x; b0 - 4 * threadIdx.x < Kp; b0 += 1024 * gridDim.y) {
     float bh[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
     if ((MB & 3) == 0 && b0 + 3 < MB) {  // 16-byte aligned rows; otherwise the scalar path below
-      float th[4] = {0.f, 0.f, 0.f, 0.f}, tl[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int s = 0; s < nsplit; ++s) {
+      float th[4], tl[4];
+      {  // the first partial as it is (a normalised pair), the others added
+        const float4* pp = reinterpret_cast<const float4*>(Tp + a * MB + b0);
+        const float4 p0 = pp[0], p1 = pp[1];
+        th[0] = p0.x, tl[0] = p0.y, th[1] = p0.z, tl[1] = p0.w;
+        th[2] = p1.x, tl[2] = p1.y, th[3] = p1.z, tl[3] = p1.w;
+      }
+      for (int s = 1; s < nsplit; ++s) {
         const float4* pp = reinterpret_cast<const float4*>(Tp + ((int64_t)s * M + a) * MB + b0);
         const float4 p0 = pp[0], p1 = pp[1];
         df_add(th[0], tl[0], p0.x, p0.y);
@@ -1177,10 +1189,20 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
     // 7 slices of the four entries, one 8-byte store each
     if (b0 < Kp) {
       float yh[4], yl[4];
+      const int sh7 = oz::BITS - ex;
+      if (sh7 >= -126 && sh7 <= 127) {  // one power of two for the eight scalings
+        const float f = pow2f(sh7);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        yh[u] = scale2(bh[u], oz::BITS - ex);
-        yl[u] = scale2(bl[u], oz::BITS - ex);
+        for (int u = 0; u < 4; ++u) {
+          yh[u] = __fmul_rn(bh[u], f);
+          yl[u] = __fmul_rn(bl[u], f);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          yh[u] = scale2(bh[u], sh7);
+          yl[u] = scale2(bl[u], sh7);
+        }
       }
       const float up = (float)(1 << oz::BITS);
       bf16* dst = sl + a * Kp + b0;
@@ -1192,7 +1214,7 @@ __global__ void __launch_bounds__(256) oz_beta_kernel(const float2* __restrict__
         for (int u = 0; u < 4; ++u) {
           sv[u] = rintf(yh[u]);
           float h, l;
-          two_sum(__fsub_rn(yh[u], sv[u]), yl[u], h, l);
+          fast_two_sum(__fsub_rn(yh[u], sv[u]), yl[u], h, l);  // exact: see slice_write
           yh[u] = __fmul_rn(h, up);
           yl[u] = __fmul_rn(l, up);
         }
@@ -1504,8 +1526,13 @@ gdml_status oz_matvec(OzMatvec& oz, const double* G, const float2* G2, const dou
     // projection and slicing of W's rows in one kernel (double-float), then W^T's rows sliced
     // straight from the float pairs of W (a column slicing: no transposed copy)
     { oz_proj_slice_df_kernel<<<(unsigned)M, oz::KC, 3 * oz.N * sizeof(float2), st>>>(G2, oz.Xc2, v, M, oz.N, D, (int)oz.W1.nchunks, oz.Wf, oz.t, oz.t2, oz.W1.Rp, oz.W1.Kp, (bf16*)oz.W1.slices, oz.W1.e); count_launch(); }
-    dim3 g((unsigned)cdiv(D, 16), (unsigned)oz.WT2.nchunks);
-    { oz_slice_cols_kernel<float2><<<g, 256, 0, st>>>(oz.Wf, D, 0, D, MB, oz.WT2.Rp, oz.WT2.Kp, (bf16*)oz.WT2.slices, oz.WT2.e); count_launch(); }
+    if (cdiv(D, 16) * oz.WT2.nchunks >= 2 * num_sms()) {
+      dim3 g((unsigned)cdiv(D, 16), (unsigned)oz.WT2.nchunks);
+      { oz_slice_cols_kernel<float2, 16><<<g, 256, 0, st>>>(oz.Wf, D, 0, D, MB, oz.WT2.Rp, oz.WT2.Kp, (bf16*)oz.WT2.slices, oz.WT2.e); count_launch(); }
+    } else {
+      dim3 g((unsigned)cdiv(D, 4), (unsigned)oz.WT2.nchunks);
+      { oz_slice_cols_kernel<float2, 4><<<g, 256, 0, st>>>(oz.Wf, D, 0, D, MB, oz.WT2.Rp, oz.WT2.Kp, (bf16*)oz.WT2.slices, oz.WT2.e); count_launch(); }
+    }
   } else {
     launch_proj(G, Xc, v, M, oz.N, D, oz.W, D, oz.t, st);
     slice_rows(oz.W, D, oz.W1, st, oz.t, oz.t2);
