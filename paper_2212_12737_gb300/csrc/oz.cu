@@ -148,6 +148,16 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
                : "r"(taddr));
 }
 
+// zeros into 16 columns of one TMEM lane quarter (32x32b.x16), then wait for the stores
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1};\n tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
 // largest |x| of the CTA (256 threads), and the exponent ex with every |x| < 2^ex
 __device__ __forceinline__ int chunk_exponent(float m, float* red) {
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -410,16 +420,19 @@ __device__ __forceinline__ bool handoff(bool failed) {
 //    wait of the MMA side: it hands each A tile to warp 1 at named barrier 2 (a wait or any
 //    shared-memory read in the MMA-issuing thread stalls the tensor pipe).
 //  * Warp 1 multiplies A slice i with B slices j = 0..6-i (per K step of 16) into TMEM
-//    accumulator i + j ("level"); the first k-block of a chunk overwrites level i with its
-//    pair (i, 0), the first to reach that level in the order 6, 5, ..., 0.  Up to four
-//    consecutive pairs (i, j .. j + 3) go into one MMA of N = 64 .. 256: 10 MMAs per K step
-//    instead of 28 (14 in a chunk's first k-block, where pair (i, 0) stays alone).
+//    accumulator i + j ("level").  Up to four consecutive pairs (i, j .. j + 3) go into one
+//    MMA of N = 64 .. 256: 10 MMAs per K step instead of 28.  The CTA's first k-block
+//    overwrites level i with its pair (i, 0), the first to reach that level in the order
+//    6, 5, ..., 0 (14 MMAs per K step there, where pair (i, 0) stays alone); every later
+//    chunk accumulates from its first MMA into levels the epilogue has zeroed.  The tensor
+//    unit pays a fixed cost per MMA instruction on top of its N-proportional work, so the
+//    instruction count, not only the flop, sets the speed.
 //  * The epilogue warps drain a finished chunk level by level, 6 down to 0 (levels 6..4 summed
 //    in FP32, 3..0 added in double-float, then scaled by 2^(eA + eB) into running
-//    double-float sums held in registers), releasing each level as soon as it is read
-//    (tfree[L]).  A slice i of the next chunk needs levels i..6 only, so its MMAs start while
-//    the drain is still on the lower levels.  After the last chunk they store the group's
-//    double-float partial once.
+//    double-float sums held in registers), writing zeros into each level after reading it and
+//    releasing it at once (tfree[L]).  A slice i of the next chunk needs levels i..6 only, so
+//    its MMAs start while the drain is still on the lower levels.  After the last chunk they
+//    store the group's double-float partial once.
 // NLEV (1..7) keeps the levels below NLEV only (slices 0..NLEV-1, pairs i + j < NLEV): a cheaper,
 // less accurate product for an inner solve; NLEV = 7 is the full product.  A compile-time count
 // lets the tile loop unroll, so the MMA-issuing thread runs straight-line code (with a run-time
@@ -626,7 +639,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t bdesc0 = tc::make_sw128_desc(tc::smem_u32(sB));
     bool& failed = mma_failed;
     for (int kb = 0; kb < nk; ++kb) {
-      const bool chunk_first = kb % kKbPerChunkM == 0;
+      // only the CTA's first k-block overwrites: the epilogue zeroes each level as it drains a
+      // chunk, so the MMAs of every later chunk accumulate from the start
+      const bool chunk_first = kb == 0;
 #pragma unroll
       for (int p0 = 0; p0 < nlev; p0 += kTilesPerHandoff) {
         failed = handoff(false) || failed;
@@ -657,8 +672,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t id = g == 1 ? idesc : g == 2 ? idesc2 : g == 3 ? idesc3 : idesc4;
               mma4(tmem + (uint32_t)((i + j) * oz::BN), bg + (uint64_t)(j * (kBTile >> 4)), id, acc0);
             };
-            // the first k-block of a chunk overwrites level i with pair (i, 0) alone; levels
-            // above i were first written by an earlier slice of this k-block (the order is
+            // the CTA's first k-block overwrites level i with pair (i, 0) alone; levels above
+            // i were first written by an earlier slice of this k-block (the order is
             // 6, 5, ..., 0), so the pairs from j = 1 on accumulate
             const int j0 = chunk_first ? 1 : 0;
             if (chunk_first) mma4(tmem + (uint32_t)(i * oz::BN), bg, idesc, 0u);
@@ -762,6 +777,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
+        // level L starts from zero in the next chunk: its MMAs then all accumulate
+        static_assert(kEpiCols == 16, "one 16-column zero store per level");
+        tmem_zero16(lane_base + (uint32_t)(L * oz::BN));
         release(L);
       }
       const int* ex = sexp + (q & 1) * kExpStage;
