@@ -148,6 +148,22 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
                : "r"(taddr));
 }
 
+// packed FP32 pairs (two independent lanes per instruction, round to nearest even)
+__device__ __forceinline__ float2 pf_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pf_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pf_sub(float2 a, float2 b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(*reinterpret_cast<const uint64_t*>(&a)),
+      "l"(*reinterpret_cast<const uint64_t*>(&b)));
+  return *reinterpret_cast<const float2*>(&d);
+}
+// TwoSum on both lanes: s + e = a + b exactly
+__device__ __forceinline__ void pf_two_sum(float2 a, float2 b, float2& s, float2& e) {
+  s = pf_add(a, b);
+  const float2 bb = pf_sub(s, a);
+  e = pf_add(pf_sub(a, pf_sub(s, bb)), pf_sub(b, bb));
+}
+
 // zeros into 16 columns of one TMEM lane quarter (32x32b.x16), then wait for the stores
 __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
   const uint32_t z = 0u;
@@ -753,34 +769,54 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::fence_after_sync();
       // levels 6..4 are scaled by 2^-56..2^-42 against the leading level's 2^-14, so a plain
       // FP32 sum of them errs by < 2^-48 of the leading level's range; levels 3..0 are added
-      // in double-float
+      // by TwoSum with the errors gathered in the low word (renormalised once after level 0).
+      // Packed FP32 pairs halve the drain's instructions: its warps share the issue slots of
+      // the MMA warp while the next chunk starts
 #pragma unroll
       for (int t = 0; t < kEpiCols; ++t) ll[t] = 0.f;
 #pragma unroll
       for (int L = oz::S - 1; L >= 0; --L) {
         if (L >= nlev) continue;
         const float sc = pow2f(-oz::BITS * (L + 2));
+        const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
         for (int c8 = 0; c8 < kEpiCols; c8 += 8) {
           uint32_t v[8];
           tmem_ld8_nowait(lane_base + (uint32_t)(L * oz::BN + c8), v);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const float x = __fmul_rn(__uint_as_float(v[t]), sc);
+          for (int t = 0; t < 8; t += 2) {
+            const float2 x = pf_mul(make_float2(__uint_as_float(v[t]), __uint_as_float(v[t + 1])), sc2);
+            float2 h = make_float2(hh[c8 + t], hh[c8 + t + 1]);
             if (L == nlev - 1) {
-              hh[c8 + t] = x;
+              h = x;
             } else if (L >= 4) {
-              hh[c8 + t] = __fadd_rn(hh[c8 + t], x);
+              h = pf_add(h, x);
             } else {
-              df_add_f(hh[c8 + t], ll[c8 + t], x);
+              float2 sum, e;
+              pf_two_sum(h, x, sum, e);
+              const float2 l = pf_add(make_float2(ll[c8 + t], ll[c8 + t + 1]), e);
+              ll[c8 + t] = l.x;
+              ll[c8 + t + 1] = l.y;
+              h = sum;
             }
+            hh[c8 + t] = h.x;
+            hh[c8 + t + 1] = h.y;
           }
         }
         // level L starts from zero in the next chunk: its MMAs then all accumulate
         static_assert(kEpiCols == 16, "one 16-column zero store per level");
         tmem_zero16(lane_base + (uint32_t)(L * oz::BN));
         release(L);
+      }
+#pragma unroll
+      for (int t = 0; t < kEpiCols; t += 2) {  // renormalise the level sum (TwoSum: any order)
+        float2 sum, e;
+        pf_two_sum(make_float2(hh[t], hh[t + 1]), make_float2(ll[t], ll[t + 1]), sum, e);
+        hh[t] = sum.x;
+        hh[t + 1] = sum.y;
+        ll[t] = e.x;
+        ll[t + 1] = e.y;
       }
       const int* ex = sexp + (q & 1) * kExpStage;
       const int ea = ex[quarter * 32 + lane];
