@@ -440,9 +440,9 @@ __device__ __forceinline__ bool handoff(bool failed) {
 //    MMA of N = 64 .. 256: 10 MMAs per K step instead of 28.  The CTA's first k-block
 //    overwrites level i with its pair (i, 0), the first to reach that level in the order
 //    6, 5, ..., 0 (14 MMAs per K step there, where pair (i, 0) stays alone); every later
-//    chunk accumulates from its first MMA into levels the epilogue has zeroed.  The tensor
-//    unit pays a fixed cost per MMA instruction on top of its N-proportional work, so the
-//    instruction count, not only the flop, sets the speed.
+//    chunk accumulates from its first MMA into levels the epilogue has zeroed.  Fewer, wider
+//    MMAs measured faster at every step (28 -> 16 -> 10 per K step): the issuing thread's
+//    progress, not a bandwidth, paces the pipeline.
 //  * The epilogue warps drain a finished chunk level by level, 6 down to 0 (levels 6..4 summed
 //    in FP32, 3..0 added in double-float, then scaled by 2^(eA + eB) into running
 //    double-float sums held in registers), writing zeros into each level after reading it and
